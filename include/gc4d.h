@@ -1,0 +1,217 @@
+/*
+ * gc4d.h - C ABI of a B300 (sm_103a) differentiable tile rasterizer for
+ * hierarchical 4D Gaussians (4DGCPro, arXiv 2509.17513).
+ *
+ * One call renders one frame of a layer-selected Gaussian set:
+ *   per-group rigid motion of the keyframe Gaussians (Sec. 3.2, "Rigid
+ *   Transformation": mu_t = mu + t_g, R_t = R_g R), the 3D Gaussian of Eq. 1
+ *   with Sigma = R s s^T R^T (Sec. 3.1), EWA projection to a 2D conic, tile
+ *   binning with an on-device radix sort on (tile, depth), and front-to-back
+ *   alpha compositing with spherical-harmonic colour (Eq. 2) restricted to the
+ *   selected layers (progressive rendering, Eq. 4).  The backward pass returns
+ *   the gradient of a loss w.r.t. every Gaussian attribute and the per-group
+ *   motion, as the paper's rate-distortion training needs (Sec. 3.3).
+ *
+ * Conventions
+ *   - Every buffer pointer marked "device" is CUDA global memory on the
+ *     context's device, owned by the caller, row-major, tightly packed, and
+ *     must stay valid until the work queued on `stream` has finished.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - A context serialises its calls: use it from one host thread and one
+ *     stream at a time.
+ *   - Every entry point returns a gc_status; nothing throws across the ABI and
+ *     no kernel traps.  gc_last_error() describes the last failure.
+ *   - Images are planar FP32, 3 x height x width (channel, row, column).
+ *   - Quaternions are Hamilton (w, x, y, z).  Camera: pinhole, x right, y down,
+ *     z forward; pixel (i, j) has its centre at (i + 0.5, j + 0.5).
+ */
+#ifndef GC4D_H
+#define GC4D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GC_API __attribute__((visibility("default")))
+#else
+#define GC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GC_OK = 0,
+    GC_ERR_INVALID_ARG = 1,  /* a pointer, size or option is out of range */
+    GC_ERR_OOM = 2,          /* device allocation of library scratch failed */
+    GC_ERR_CAPACITY = 3,     /* fixed key capacity too small; gc_last_error gives the need */
+    GC_ERR_TIMEOUT = 4,      /* a bounded device wait ran out */
+    GC_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+    GC_ERR_STATE = 6,        /* backward without a matching forward, or a mismatched saved state */
+    GC_ERR_UNSUPPORTED = 7   /* a valid request this build does not support */
+} gc_status;
+
+enum { GC_PREC_FP32 = 0, GC_PREC_BF16_FP8 = 1 };
+enum { GC_MEMBER_PIXEL = 0, GC_MEMBER_TILE = 1 };
+
+typedef struct gc_context gc_context;
+typedef struct gc_saved gc_saved;
+
+/* Renderer options.  Defaults (gc_default_options): 16x16 tiles, near 0.2,
+ * dilation 0.3, frustum clamp 1.3, black background, pixel-square
+ * membership, key capacity 0 (grow on demand).  The near plane, dilation,
+ * clamp and the +0.5 SH offset follow the 3DGS lineage the paper builds on
+ * (Sec. A); the paper itself does not state them. */
+typedef struct {
+    int32_t tile_w, tile_h;   /* tile shape in pixels: 16x16, 8x32 or 32x8 */
+    float near_plane;         /* Gaussians with camera z <= near are culled */
+    float dilation;           /* added to both diagonal entries of the 2D covariance */
+    float frustum_clamp;      /* x/z and y/z are clamped to +-clamp*tan(half fov) inside J */
+    float bg[3];              /* background colour added with the final transmittance */
+    int32_t membership;       /* GC_MEMBER_PIXEL: pixel centre within r of (u, v) in both axes;
+                                 GC_MEMBER_TILE: every pixel of a touched tile */
+    int64_t key_capacity;     /* 0: size the (tile, Gaussian) list per frame, one host sync per
+                                 frame; > 0: fixed capacity, no host sync, GC_ERR_CAPACITY is
+                                 reported by gc_check() when a frame needs more */
+} gc_options;
+
+/* The Gaussian set, in layer order: layer l is [layer_offsets[l], layer_offsets[l+1]). */
+typedef struct {
+    int64_t n;                    /* number of Gaussians in the arrays */
+    int32_t n_layers;             /* L, at most 32 */
+    const int64_t *layer_offsets; /* HOST array of L+1 nondecreasing offsets, [0] = 0, [L] = n */
+    int32_t sh_degree;            /* 0..3; K = (sh_degree+1)^2 coefficients per colour channel */
+    int32_t precision;            /* GC_PREC_FP32 or GC_PREC_BF16_FP8 */
+    /* GC_PREC_FP32 attributes (device) */
+    const float *means;           /* n x 3 */
+    const float *log_scales;      /* n x 3, s = exp(log_scales) */
+    const float *quats;           /* n x 4 (w, x, y, z), any nonzero norm */
+    const float *opacity_logits;  /* n, opacity = sigmoid(logit) */
+    const float *sh;              /* n x K x 3 (coefficient-major, then r, g, b) */
+    const int32_t *group_id;      /* n motion-group ids in [0, G), or NULL: all in group 0 */
+    /* GC_PREC_BF16_FP8 attributes (device): value = float(stored) * scale, one FP32 multiply */
+    const uint16_t *means_bf16;      /* n x 3 bfloat16 bit patterns */
+    const uint16_t *log_scales_bf16; /* n x 3 */
+    const uint16_t *quats_bf16;      /* n x 4 */
+    const uint16_t *opacity_bf16;    /* n */
+    const uint8_t *sh_e4m3;          /* n x K x 3 float8 e4m3 ("fn") bit patterns */
+    const float *scales;             /* device, 3 + 3 + 4 + 1 + 3K per-channel FP32 scales in the
+                                        order means, log_scales, quats, opacity, sh (k-major, rgb) */
+} gc_gaussians;
+
+/* Cumulative per-group rigid motion of one frame (device arrays). */
+typedef struct {
+    int32_t n_groups;   /* G >= 1 */
+    const float *q;     /* G x 4 unit quaternions; q' = q_g (x) q */
+    const float *t;     /* G x 3 translations; mu' = mu + t_g */
+} gc_motion;
+
+/* Pinhole camera (host, by value). X_cam = R X_world + t. */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float R[9];         /* row major */
+    float t[3];
+    float campos[3];    /* camera centre in world coordinates (view direction origin) */
+} gc_camera;
+
+/* Gradient outputs (device).  Overwritten, not accumulated.  Gaussians that
+ * are not selected or not visible receive 0.  Any pointer may be NULL to skip
+ * that output. */
+typedef struct {
+    float *d_means;          /* n x 3 */
+    float *d_log_scales;     /* n x 3 */
+    float *d_quats;          /* n x 4 */
+    float *d_opacity_logits; /* n */
+    float *d_sh;             /* n x K x 3 */
+    float *d_group_q;        /* G x 4 */
+    float *d_group_t;        /* G x 3 */
+} gc_grads;
+
+/* Per-frame statistics of a saved forward. */
+typedef struct {
+    int64_t n_selected;      /* Gaussians in the selected layers */
+    int64_t n_visible;       /* of those, visible (non-empty footprint) */
+    int64_t n_keys;          /* (tile, Gaussian) pairs, K */
+    int32_t n_tiles;
+    int32_t width, height;
+} gc_stats;
+
+/* Fills *out with the defaults listed at gc_options. */
+GC_API gc_status gc_default_options(gc_options *out);
+
+/* Creates a context on CUDA device `device`.  opt may be NULL (defaults).
+ * The context owns grow-only device scratch; it is freed by gc_destroy. */
+GC_API gc_status gc_create(gc_context **out, int device, const gc_options *opt);
+GC_API gc_status gc_destroy(gc_context *ctx);
+
+/* Replaces the context's options (takes effect from the next call). */
+GC_API gc_status gc_set_options(gc_context *ctx, const gc_options *opt);
+
+/* A saved forward state: the sorted tile lists, per-Gaussian projections
+ * and per-pixel final transmittance that the backward pass reads.  Owned by
+ * the library, reused across forwards, freed by gc_saved_destroy. */
+GC_API gc_status gc_saved_create(gc_context *ctx, gc_saved **out);
+GC_API gc_status gc_saved_destroy(gc_context *ctx, gc_saved *saved);
+
+/*
+ * Forward render of one frame (Eq. 2 / Eq. 4 over the layers in layer_mask).
+ *   g          the Gaussian set (host struct; its arrays are device memory)
+ *   motion     this frame's cumulative group motion, or NULL for the keyframe
+ *   layer_mask bit l selects layer l (bit 0 = L1); level l is (1 << l) - 1
+ *   cam        the camera (host)
+ *   image      device, 3 x height x width, written
+ *   saved      NULL for inference; else filled for gc_render_backward
+ * An empty selection (n = 0 or no layer bit set) writes the background.
+ */
+GC_API gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_motion *motion,
+                            uint32_t layer_mask, const gc_camera *cam, float *image,
+                            gc_saved *saved, void *stream);
+
+/*
+ * Backward of the forward recorded in `saved`: given dL/dimage (device,
+ * 3 x height x width), writes dL/d(every attribute) and dL/d(group motion).
+ * g and motion must be the same arrays that the forward read.  Reverse
+ * compositing starts from each pixel's saved final transmittance; the
+ * per-tile gradient reduction is atomics-free, so the result is bitwise
+ * reproducible.
+ */
+GC_API gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved, const gc_gaussians *g,
+                             const gc_motion *motion, const float *dL_dimage, gc_grads *out,
+                             void *stream);
+
+/* Statistics of the last forward recorded in `saved` (synchronises `stream`). */
+GC_API gc_status gc_saved_stats(gc_context *ctx, const gc_saved *saved, gc_stats *out, void *stream);
+
+/*
+ * Copies the sorted tile lists of `saved` (synchronises `stream`):
+ *   ranges    device, n_tiles x 2 int32 [start, end) into gauss_ids
+ *   gauss_ids device, capacity entries: global Gaussian index of each entry,
+ *             tile by tile, front to back (depth, then index)
+ * Returns GC_ERR_CAPACITY if capacity < n_keys.
+ */
+GC_API gc_status gc_saved_tile_lists(gc_context *ctx, const gc_saved *saved, int32_t *ranges,
+                              int64_t *gauss_ids, int64_t capacity, void *stream);
+
+/* Per-pixel diagnostics of `saved`: final transmittance (H x W FP32) and the
+ * number of Gaussians blended into each pixel (H x W int32); device buffers,
+ * either may be NULL. */
+GC_API gc_status gc_saved_pixel_state(gc_context *ctx, const gc_saved *saved, float *final_T,
+                               int32_t *n_blended, void *stream);
+
+/* Reports errors recorded on the device by fixed-capacity or bounded-wait
+ * work since the last check (synchronises `stream`): GC_OK,
+ * GC_ERR_CAPACITY or GC_ERR_TIMEOUT. */
+GC_API gc_status gc_check(gc_context *ctx, void *stream);
+
+/* Text of the last error on this context (valid until the next call). */
+GC_API const char *gc_last_error(gc_context *ctx);
+
+/* Library version string. */
+GC_API const char *gc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GC4D_H */

@@ -297,26 +297,25 @@ def grad(scene, motion, frame, cam, opts: dict, dL_dimage, layer_mask: int = 1,
 def tile_lists(bins: dict, cam, tile=(16, 16)) -> dict:
     """Per-tile lists of global Gaussian ids ordered by (depth, index).
 
-    Returns ``{"tile_of_entry", "gauss_of_entry"}`` sorted by (tile, depth,
-    index) and ``ranges`` (n_tiles, 2).  Uses numpy's stable lexsort.
+    Every visible Gaussian contributes one entry per tile of its tile
+    rectangle.  Returns ``gauss_of_entry`` / ``tile_of_entry`` sorted by
+    (tile, depth, index) with numpy's lexsort, and ``ranges`` (n_tiles, 2).
     """
     tw, th = tile
     ntx = (cam.width + tw - 1) // tw
     nty = (cam.height + th - 1) // th
     vis = np.nonzero(bins["visible"])[0]
-    tiles, gids, deps = [], [], []
-    tr = bins["trect"]
-    for j in vis:
-        x0, x1, y0, y1 = tr[j]
-        ty, tx = np.meshgrid(np.arange(y0, y1 + 1), np.arange(x0, x1 + 1), indexing="ij")
-        t = (ty * ntx + tx).reshape(-1)
-        tiles.append(t)
-        gids.append(np.full(t.shape, bins["sel"][j], np.int64))
-        deps.append(np.full(t.shape, bins["depth"][j], np.float32))
-    if tiles:
-        t = np.concatenate(tiles); g = np.concatenate(gids); d = np.concatenate(deps)
-    else:
-        t = np.zeros(0, np.int64); g = np.zeros(0, np.int64); d = np.zeros(0, np.float32)
+    tr = bins["trect"][vis].astype(np.int64)
+    wdt = tr[:, 1] - tr[:, 0] + 1
+    cnt = wdt * (tr[:, 3] - tr[:, 2] + 1)
+    owner = np.repeat(np.arange(len(vis)), cnt)
+    start = np.concatenate([[0], np.cumsum(cnt)[:-1]]) if len(cnt) else np.zeros(0, np.int64)
+    k = np.arange(int(cnt.sum()), dtype=np.int64) - np.repeat(start, cnt)
+    ty = tr[owner, 2] + k // wdt[owner]
+    tx = tr[owner, 0] + k % wdt[owner]
+    t = ty * ntx + tx
+    g = bins["sel"][vis][owner]
+    d = bins["depth"][vis][owner]
     order = np.lexsort((g, d, t))
     t, g = t[order], g[order]
     n_tiles = ntx * nty

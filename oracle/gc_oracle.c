@@ -308,6 +308,7 @@ static void bin_one_f32(const gco_scene *sc, const gco_motion *mo, const gco_cam
     /* 12. centre */
     float u = cam->fx * xoz + cam->cx;
     float v = cam->fy * yoz + cam->cy;
+    if (!isfinite(u) || !isfinite(v) || !isfinite(rf)) return;
     /* 13. pixel rectangle, clipped */
     float fx0 = ceilf((u - rf) - 0.5f), fx1 = floorf((u + rf) - 0.5f);
     float fy0 = ceilf((v - rf) - 0.5f), fy1 = floorf((v + rf) - 0.5f);

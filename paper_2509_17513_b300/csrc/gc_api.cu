@@ -1,0 +1,514 @@
+// gc_api.cu - the C ABI (include/gc4d.h): context, library-owned scratch and the
+// orchestration of one frame on the caller's stream.
+//
+// Forward, one frame (all on `stream`):
+//   preprocess (motion + projection + footprint + colour, per selected Gaussian)
+//   -> depth sort (32-bit depth keys, stable over index order)
+//   -> rank gather (records into depth order) -> exclusive scan of tiles touched
+//   -> [key count: one 4-byte device->host read unless the capacity is fixed]
+//   -> emit (tile, rank) entries -> stable tile sort -> tile ranges -> blend.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "gc_internal.cuh"
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+cudaError_t grow(DevBuf &b, size_t bytes) {
+    if (bytes <= b.cap && b.p) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t c = bytes + bytes / 4 + 256;
+    cudaError_t e = cudaMalloc(&b.p, c);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return e;
+    }
+    b.cap = c;
+    return cudaSuccess;
+}
+
+void release(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+int ilog2_exact(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return ((1 << l) == v) ? l : -1;
+}
+
+int bits_for(int64_t max_value) {
+    int b = 1;
+    while (b < 32 && ((int64_t)1 << b) <= max_value) ++b;
+    return b;
+}
+
+}  // namespace
+
+struct gc_saved {
+    bool valid = false;
+    int64_t n = 0, n_sel = 0;
+    int sh_degree = 0, n_groups = 1;
+    uint32_t layer_mask = 0;
+    gc::Selection sel{};
+    gc::CamParams cam{};
+    gc::RenderParams rp{};
+    int64_t K = 0;       // keys used (host view; fixed-capacity mode: the capacity)
+    bool k_exact = false;
+    int depth_buf = 0, tile_buf = 0;
+    DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
+        final_T, n_contrib, n_blended, words;
+};
+
+struct gc_context {
+    int device = 0;
+    gc_options opt{};
+    gc_saved internal;
+    DevBuf scratch, bwd_part, bwd_g2d, bwd_motion, gkeys[2], gvals[2];
+    uint32_t *host_word = nullptr;  // pinned
+    const gc_saved *last = nullptr; // state written by the most recent forward
+    std::string err;
+};
+
+namespace {
+
+gc_status fail(gc_context *ctx, gc_status s, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return s;
+}
+
+#define GC_CUDA(ctx, call)                                                                    \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA,    \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+gc_status check_options(gc_context *ctx, const gc_options *o) {
+    bool shape_ok = (o->tile_w == 16 && o->tile_h == 16) || (o->tile_w == 8 && o->tile_h == 32) ||
+                    (o->tile_w == 32 && o->tile_h == 8);
+    if (!shape_ok) return fail(ctx, GC_ERR_INVALID_ARG, "tile shape %dx%d not in {16x16, 8x32, 32x8}", o->tile_w, o->tile_h);
+    if (!(o->near_plane > 0.f)) return fail(ctx, GC_ERR_INVALID_ARG, "near_plane must be > 0");
+    if (!(o->dilation >= 0.f)) return fail(ctx, GC_ERR_INVALID_ARG, "dilation must be >= 0");
+    if (!(o->frustum_clamp > 0.f)) return fail(ctx, GC_ERR_INVALID_ARG, "frustum_clamp must be > 0");
+    if (o->membership != GC_MEMBER_PIXEL && o->membership != GC_MEMBER_TILE)
+        return fail(ctx, GC_ERR_INVALID_ARG, "membership must be GC_MEMBER_PIXEL or GC_MEMBER_TILE");
+    if (o->key_capacity < 0 || o->key_capacity > 0xFFFFFFF0ll)
+        return fail(ctx, GC_ERR_INVALID_ARG, "key_capacity out of range");
+    return GC_OK;
+}
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev_);
+        if (prev_ != dev) cudaSetDevice(dev);
+        dev_ = dev;
+    }
+    ~DeviceGuard() {
+        if (prev_ != dev_) cudaSetDevice(prev_);
+    }
+
+  private:
+    int prev_ = 0, dev_ = 0;
+};
+
+gc_status make_source(gc_context *ctx, const gc_gaussians *g, const gc_motion *m, gc::GaussSrc &s) {
+    if (!g) return fail(ctx, GC_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n < 0) return fail(ctx, GC_ERR_INVALID_ARG, "n < 0");
+    if (g->n > 0x7FFFFFFFll) return fail(ctx, GC_ERR_INVALID_ARG, "n exceeds 2^31 - 1");
+    if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ctx, GC_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (g->n_layers < 1 || g->n_layers > gc::kMaxLayers)
+        return fail(ctx, GC_ERR_INVALID_ARG, "n_layers must be 1..32");
+    if (!g->layer_offsets) return fail(ctx, GC_ERR_INVALID_ARG, "layer_offsets is NULL");
+    if (g->layer_offsets[0] != 0 || g->layer_offsets[g->n_layers] != g->n)
+        return fail(ctx, GC_ERR_INVALID_ARG, "layer_offsets must start at 0 and end at n");
+    for (int l = 0; l < g->n_layers; ++l)
+        if (g->layer_offsets[l + 1] < g->layer_offsets[l])
+            return fail(ctx, GC_ERR_INVALID_ARG, "layer_offsets must be nondecreasing");
+    memset(&s, 0, sizeof s);
+    s.n = g->n;
+    s.sh_degree = g->sh_degree;
+    s.K = (g->sh_degree + 1) * (g->sh_degree + 1);
+    s.precision = g->precision;
+    if (g->precision == GC_PREC_FP32) {
+        if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+            return fail(ctx, GC_ERR_INVALID_ARG, "an FP32 attribute array is NULL");
+    } else if (g->precision == GC_PREC_BF16_FP8) {
+        if (g->n > 0 && (!g->means_bf16 || !g->log_scales_bf16 || !g->quats_bf16 ||
+                         !g->opacity_bf16 || !g->sh_e4m3 || !g->scales))
+            return fail(ctx, GC_ERR_INVALID_ARG, "a reduced-precision plane or the scales are NULL");
+    } else {
+        return fail(ctx, GC_ERR_INVALID_ARG, "unknown precision %d", g->precision);
+    }
+    s.means = g->means; s.log_scales = g->log_scales; s.quats = g->quats;
+    s.opacity_logits = g->opacity_logits; s.sh = g->sh; s.group_id = g->group_id;
+    s.means_h = g->means_bf16; s.log_scales_h = g->log_scales_bf16; s.quats_h = g->quats_bf16;
+    s.opacity_h = g->opacity_bf16; s.sh_q = g->sh_e4m3; s.scales = g->scales;
+    s.n_groups = 1;
+    if (m) {
+        if (m->n_groups < 1 || !m->q || !m->t)
+            return fail(ctx, GC_ERR_INVALID_ARG, "motion needs n_groups >= 1 and q, t arrays");
+        s.group_q = m->q;
+        s.group_t = m->t;
+        s.n_groups = m->n_groups;
+    } else if (g->group_id) {
+        s.group_id = nullptr;  // keyframe: groups are irrelevant
+    }
+    return GC_OK;
+}
+
+gc::Selection make_selection(const gc_gaussians *g, uint32_t mask, int64_t &n_sel) {
+    gc::Selection s{};
+    n_sel = 0;
+    s.range_start[0] = 0;
+    for (int l = 0; l < g->n_layers; ++l) {
+        if (!((mask >> l) & 1u)) continue;
+        int64_t a = g->layer_offsets[l], b = g->layer_offsets[l + 1];
+        if (b <= a) continue;
+        // merge adjacent ranges
+        if (s.n_ranges > 0 && s.range_begin[s.n_ranges - 1] + (s.range_start[s.n_ranges] - s.range_start[s.n_ranges - 1]) == a) {
+            s.range_start[s.n_ranges] += b - a;
+        } else {
+            s.range_begin[s.n_ranges] = a;
+            s.range_start[s.n_ranges + 1] = s.range_start[s.n_ranges] + (b - a);
+            s.n_ranges++;
+        }
+        n_sel += b - a;
+    }
+    if (s.n_ranges == 0) s.n_ranges = 1;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gc_version(void) { return "gc4d 0.1 (sm_103a)"; }
+
+gc_status gc_default_options(gc_options *o) {
+    if (!o) return GC_ERR_INVALID_ARG;
+    memset(o, 0, sizeof *o);
+    o->tile_w = 16;
+    o->tile_h = 16;
+    o->near_plane = 0.2f;
+    o->dilation = 0.3f;
+    o->frustum_clamp = 1.3f;
+    o->membership = GC_MEMBER_PIXEL;
+    o->key_capacity = 0;
+    return GC_OK;
+}
+
+gc_status gc_create(gc_context **out, int device, const gc_options *opt) {
+    if (!out) return GC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return GC_ERR_INVALID_ARG;
+    }
+    gc_context *ctx = new (std::nothrow) gc_context();
+    if (!ctx) return GC_ERR_OOM;
+    ctx->device = device;
+    gc_default_options(&ctx->opt);
+    if (opt) {
+        gc_status s = check_options(ctx, opt);
+        if (s != GC_OK) {
+            delete ctx;
+            return s;
+        }
+        ctx->opt = *opt;
+    }
+    DeviceGuard dg(device);
+    if (cudaHostAlloc(&ctx->host_word, 64, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return GC_ERR_OOM;
+    }
+    *out = ctx;
+    return GC_OK;
+}
+
+static void saved_release(gc_context *ctx, gc_saved *s) {
+    if (ctx && ctx->last == s) ctx->last = nullptr;
+    DevBuf *bufs[] = {&s->rec, &s->ranked, &s->dkeys[0], &s->dkeys[1], &s->dvals[0], &s->dvals[1],
+                      &s->touched, &s->touched_r, &s->offsets, &s->tkeys[0], &s->tkeys[1],
+                      &s->tvals[0], &s->tvals[1], &s->ranges, &s->final_T, &s->n_contrib,
+                      &s->n_blended, &s->words};
+    for (DevBuf *b : bufs) release(*b);
+    s->valid = false;
+}
+
+gc_status gc_destroy(gc_context *ctx) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    {
+        DeviceGuard dg(ctx->device);
+        saved_release(ctx, &ctx->internal);
+        DevBuf *bufs[] = {&ctx->scratch, &ctx->bwd_part, &ctx->bwd_g2d, &ctx->bwd_motion,
+                          &ctx->gkeys[0], &ctx->gkeys[1], &ctx->gvals[0], &ctx->gvals[1]};
+        for (DevBuf *b : bufs) release(*b);
+        if (ctx->host_word) cudaFreeHost(ctx->host_word);
+    }
+    delete ctx;
+    return GC_OK;
+}
+
+gc_status gc_set_options(gc_context *ctx, const gc_options *opt) {
+    if (!ctx || !opt) return GC_ERR_INVALID_ARG;
+    gc_status s = check_options(ctx, opt);
+    if (s != GC_OK) return s;
+    ctx->opt = *opt;
+    return GC_OK;
+}
+
+gc_status gc_saved_create(gc_context *ctx, gc_saved **out) {
+    if (!ctx || !out) return GC_ERR_INVALID_ARG;
+    *out = new (std::nothrow) gc_saved();
+    return *out ? GC_OK : GC_ERR_OOM;
+}
+
+gc_status gc_saved_destroy(gc_context *ctx, gc_saved *saved) {
+    if (!ctx || !saved) return GC_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    saved_release(ctx, saved);
+    delete saved;
+    return GC_OK;
+}
+
+const char *gc_last_error(gc_context *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_motion *motion,
+                            uint32_t layer_mask, const gc_camera *cam, float *image,
+                            gc_saved *saved, void *stream) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    if (!cam || !image) return fail(ctx, GC_ERR_INVALID_ARG, "camera or image is NULL");
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > 32768 || cam->height > 32768)
+        return fail(ctx, GC_ERR_INVALID_ARG, "image size %dx%d out of range (1..32768)", cam->width, cam->height);
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(ctx, GC_ERR_INVALID_ARG, "fx, fy must be > 0");
+    gc::GaussSrc src;
+    gc_status st = make_source(ctx, g, motion, src);
+    if (st != GC_OK) return st;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gc_saved &S = saved ? *saved : ctx->internal;
+    S.valid = false;
+
+    const gc_options &o = ctx->opt;
+    int64_t n_sel = 0;
+    S.sel = make_selection(g, layer_mask, n_sel);
+    S.n = g->n;
+    S.n_sel = n_sel;
+    S.sh_degree = g->sh_degree;
+    S.n_groups = src.n_groups;
+    S.layer_mask = layer_mask;
+    gc::CamParams &cp = S.cam;
+    cp.width = cam->width; cp.height = cam->height;
+    cp.fx = cam->fx; cp.fy = cam->fy; cp.cx = cam->cx; cp.cy = cam->cy;
+    memcpy(cp.R, cam->R, sizeof cp.R);
+    memcpy(cp.t, cam->t, sizeof cp.t);
+    memcpy(cp.campos, cam->campos, sizeof cp.campos);
+    gc::RenderParams &rp = S.rp;
+    rp.near_plane = o.near_plane; rp.dilation = o.dilation; rp.frustum_clamp = o.frustum_clamp;
+    memcpy(rp.bg, o.bg, sizeof rp.bg);
+    rp.tile_w = o.tile_w; rp.tile_h = o.tile_h;
+    rp.tile_w_log2 = ilog2_exact(o.tile_w); rp.tile_h_log2 = ilog2_exact(o.tile_h);
+    rp.ntx = (cam->width + o.tile_w - 1) / o.tile_w;
+    rp.nty = (cam->height + o.tile_h - 1) / o.tile_h;
+    rp.membership = o.membership;
+    const int64_t n_tiles = (int64_t)rp.ntx * rp.nty;
+    const int64_t hw = (int64_t)cam->width * cam->height;
+
+    // per-frame buffers sized by the selection and the image
+    const int64_t nn = n_sel > 0 ? n_sel : 1;
+    GC_CUDA(ctx, grow(S.rec, (size_t)nn * 48));
+    GC_CUDA(ctx, grow(S.ranked, (size_t)nn * 48));
+    for (int b = 0; b < 2; ++b) {
+        GC_CUDA(ctx, grow(S.dkeys[b], (size_t)nn * 4));
+        GC_CUDA(ctx, grow(S.dvals[b], (size_t)nn * 4));
+    }
+    GC_CUDA(ctx, grow(S.touched, (size_t)nn * 4));
+    GC_CUDA(ctx, grow(S.touched_r, (size_t)nn * 4));
+    GC_CUDA(ctx, grow(S.offsets, (size_t)(nn + 1) * 4));
+    GC_CUDA(ctx, grow(S.ranges, (size_t)n_tiles * 8));
+    GC_CUDA(ctx, grow(S.final_T, (size_t)hw * 4));
+    GC_CUDA(ctx, grow(S.n_contrib, (size_t)hw * 4));
+    GC_CUDA(ctx, grow(S.n_blended, (size_t)hw * 4));
+    GC_CUDA(ctx, grow(S.words, 64));
+    const int64_t cap_fixed = o.key_capacity;
+    const size_t scan_words = gc::scan_partials_size(nn);
+
+    GC_CUDA(ctx, cudaMemsetAsync(S.ranges.p, 0, (size_t)n_tiles * 8, s));
+    uint32_t *words = S.words.as<uint32_t>();  // [0] = K, [1] = error flags
+    int64_t K = 0;
+    if (n_sel > 0) {
+        GC_CUDA(ctx, grow(ctx->scratch, 4 * std::max(gc::radix_scratch_words(nn), scan_words)));
+        uint32_t *scratch = ctx->scratch.as<uint32_t>();
+        GC_CUDA(ctx, gc::launch_preprocess(src, S.sel, n_sel, cp, rp, S.rec.as<float4>(),
+                                           S.dkeys[0].as<uint32_t>(), S.dvals[0].as<uint32_t>(),
+                                           S.touched.as<uint32_t>(), s));
+        uint32_t *dk[2] = {S.dkeys[0].as<uint32_t>(), S.dkeys[1].as<uint32_t>()};
+        uint32_t *dv[2] = {S.dvals[0].as<uint32_t>(), S.dvals[1].as<uint32_t>()};
+        GC_CUDA(ctx, gc::radix_sort_pairs(dk, dv, n_sel, nullptr, 32, scratch, &S.depth_buf, s));
+        GC_CUDA(ctx, gc::launch_rank_gather(dv[S.depth_buf], S.rec.as<float4>(),
+                                            S.touched.as<uint32_t>(), n_sel, S.ranked.as<float4>(),
+                                            S.touched_r.as<uint32_t>(), s));
+        GC_CUDA(ctx, gc::launch_exclusive_scan(S.touched_r.as<uint32_t>(), S.offsets.as<uint32_t>(),
+                                               n_sel, words, scratch, s));
+        if (cap_fixed > 0) {
+            K = cap_fixed;
+            S.k_exact = false;
+        } else {
+            GC_CUDA(ctx, cudaMemcpyAsync(ctx->host_word, words, 4, cudaMemcpyDeviceToHost, s));
+            GC_CUDA(ctx, cudaStreamSynchronize(s));
+            K = (int64_t)ctx->host_word[0];
+            S.k_exact = true;
+        }
+        const int64_t kk = K > 0 ? K : 1;
+        for (int b = 0; b < 2; ++b) {
+            GC_CUDA(ctx, grow(S.tkeys[b], (size_t)kk * 4));
+            GC_CUDA(ctx, grow(S.tvals[b], (size_t)kk * 4));
+        }
+        GC_CUDA(ctx, grow(ctx->scratch, 4 * std::max(gc::radix_scratch_words(kk), scan_words)));
+        scratch = ctx->scratch.as<uint32_t>();
+        if (K > 0) {
+            GC_CUDA(ctx, gc::launch_emit(S.ranked.as<float4>(), S.offsets.as<uint32_t>(),
+                                         S.touched_r.as<uint32_t>(), n_sel, rp,
+                                         S.tkeys[0].as<uint32_t>(), S.tvals[0].as<uint32_t>(),
+                                         (uint32_t)K, s));
+            uint32_t *tk[2] = {S.tkeys[0].as<uint32_t>(), S.tkeys[1].as<uint32_t>()};
+            uint32_t *tv[2] = {S.tvals[0].as<uint32_t>(), S.tvals[1].as<uint32_t>()};
+            const uint32_t *ndev = S.k_exact ? nullptr : words;
+            GC_CUDA(ctx, gc::radix_sort_pairs(tk, tv, K, ndev, bits_for(n_tiles - 1), scratch,
+                                              &S.tile_buf, s));
+            GC_CUDA(ctx, gc::launch_tile_ranges(tk[S.tile_buf], ndev, K, S.ranges.as<uint2>(), s));
+        }
+    } else {
+        GC_CUDA(ctx, cudaMemsetAsync(words, 0, 8, s));
+    }
+    S.K = K;
+    uint32_t *sorted_vals = (n_sel > 0 && K > 0) ? S.tvals[S.tile_buf].as<uint32_t>() : nullptr;
+    GC_CUDA(ctx, gc::launch_blend_fwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(), cp, rp,
+                                      image, S.final_T.as<float>(), S.n_contrib.as<uint32_t>(),
+                                      S.n_blended.as<uint32_t>(), s));
+    S.valid = true;
+    ctx->last = &S;
+    return GC_OK;
+}
+
+gc_status gc_saved_stats(gc_context *ctx, const gc_saved *saved, gc_stats *out, void *stream) {
+    if (!ctx || !out) return GC_ERR_INVALID_ARG;
+    const gc_saved &S = saved ? *saved : ctx->internal;
+    if (!S.valid) return fail(ctx, GC_ERR_STATE, "no forward recorded");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    memset(out, 0, sizeof *out);
+    out->n_selected = S.n_sel;
+    out->n_tiles = S.rp.ntx * S.rp.nty;
+    out->width = S.cam.width;
+    out->height = S.cam.height;
+    if (S.n_sel > 0) {
+        GC_CUDA(ctx, cudaMemcpyAsync(ctx->host_word, S.words.p, 4, cudaMemcpyDeviceToHost, s));
+        GC_CUDA(ctx, cudaStreamSynchronize(s));
+        out->n_keys = ctx->host_word[0];
+        // visible = number of depth keys below the culled sentinel: the sorted keys end with them
+        uint32_t *keys = static_cast<uint32_t *>(S.dkeys[S.depth_buf].p);
+        int64_t lo = 0, hi = S.n_sel;  // first index with key == culled
+        while (lo < hi) {
+            int64_t mid = (lo + hi) / 2;
+            uint32_t k;
+            GC_CUDA(ctx, cudaMemcpy(&k, keys + mid, 4, cudaMemcpyDeviceToHost));
+            if (k == gc::kCulledKey) hi = mid; else lo = mid + 1;
+        }
+        out->n_visible = lo;
+    }
+    return GC_OK;
+}
+
+gc_status gc_saved_tile_lists(gc_context *ctx, const gc_saved *saved, int32_t *ranges,
+                              int64_t *gauss_ids, int64_t capacity, void *stream) {
+    if (!ctx || !ranges || !gauss_ids) return GC_ERR_INVALID_ARG;
+    const gc_saved &S = saved ? *saved : ctx->internal;
+    if (!S.valid) return fail(ctx, GC_ERR_STATE, "no forward recorded");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t K = 0;
+    if (S.n_sel > 0) {
+        GC_CUDA(ctx, cudaMemcpyAsync(ctx->host_word, S.words.p, 4, cudaMemcpyDeviceToHost, s));
+        GC_CUDA(ctx, cudaStreamSynchronize(s));
+        K = std::min<int64_t>(ctx->host_word[0], S.K);
+    }
+    if (capacity < K) return fail(ctx, GC_ERR_CAPACITY, "tile lists need %lld entries", (long long)K);
+    const int64_t n_tiles = (int64_t)S.rp.ntx * S.rp.nty;
+    GC_CUDA(ctx, cudaMemcpyAsync(ranges, S.ranges.p, (size_t)n_tiles * 8, cudaMemcpyDeviceToDevice, s));
+    if (K > 0)
+        GC_CUDA(ctx, gc::launch_entries_to_global(S.tvals[S.tile_buf].as<uint32_t>(),
+                                                  S.dvals[S.depth_buf].as<uint32_t>(), S.sel, K,
+                                                  gauss_ids, s));
+    GC_CUDA(ctx, cudaStreamSynchronize(s));
+    return GC_OK;
+}
+
+gc_status gc_saved_pixel_state(gc_context *ctx, const gc_saved *saved, float *final_T,
+                               int32_t *n_blended, void *stream) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    const gc_saved &S = saved ? *saved : ctx->internal;
+    if (!S.valid) return fail(ctx, GC_ERR_STATE, "no forward recorded");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t hw = (size_t)S.cam.width * S.cam.height;
+    if (final_T) GC_CUDA(ctx, cudaMemcpyAsync(final_T, S.final_T.p, hw * 4, cudaMemcpyDeviceToDevice, s));
+    if (n_blended) GC_CUDA(ctx, cudaMemcpyAsync(n_blended, S.n_blended.p, hw * 4, cudaMemcpyDeviceToDevice, s));
+    return GC_OK;
+}
+
+gc_status gc_check(gc_context *ctx, void *stream) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    GC_CUDA(ctx, cudaStreamSynchronize(s));
+    if (!ctx->last) return GC_OK;
+    const gc_saved &S = *ctx->last;
+    if (S.valid && !S.k_exact && S.n_sel > 0) {
+        GC_CUDA(ctx, cudaMemcpy(ctx->host_word, S.words.p, 4, cudaMemcpyDeviceToHost));
+        if ((int64_t)ctx->host_word[0] > S.K)
+            return fail(ctx, GC_ERR_CAPACITY, "frame needs %u keys, capacity %lld",
+                        ctx->host_word[0], (long long)S.K);
+    }
+    return GC_OK;
+}
+
+}  // extern "C"
+
+extern "C" gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved,
+                                        const gc_gaussians *g, const gc_motion *motion,
+                                        const float *dL_dimage, gc_grads *out, void *stream) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    (void)saved; (void)g; (void)motion; (void)dL_dimage; (void)out; (void)stream;
+    return fail(ctx, GC_ERR_UNSUPPORTED, "backward not built yet");
+}

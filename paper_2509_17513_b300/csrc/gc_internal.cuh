@@ -1,0 +1,143 @@
+// gc_internal.cuh - device-side types and launchers shared by the kernel files.
+//
+// Layout of the per-Gaussian projected record (three float4, 48 bytes), written
+// by the preprocess kernel at the Gaussian's compact (selected) position and
+// gathered into depth-rank order before binning:
+//   r0 = { u, v, conic_a, conic_b }      conic = inverse 2D covariance [[a, b], [b, c]]
+//   r1 = { conic_c, opacity, red, green }
+//   r2 = { blue, depth, rect_x, rect_y } rect_* = pixel footprint, int bits: lo16 = first,
+//                                        hi16 = last (inclusive)
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gc4d.h"
+
+namespace gc {
+
+constexpr int kMaxLayers = 32;
+constexpr uint32_t kCulledKey = 0xFFFFFFFFu;
+
+// Selected layer ranges: compact index j maps to global index
+// range_begin[k] + (j - range_start[k]) for the range k holding j.
+struct Selection {
+    int n_ranges;
+    int64_t range_begin[kMaxLayers];
+    int64_t range_start[kMaxLayers + 1];  // prefix sums of range lengths
+};
+
+struct CamParams {
+    int width, height;
+    float fx, fy, cx, cy;
+    float R[9], t[3], campos[3];
+};
+
+struct RenderParams {
+    float near_plane, dilation, frustum_clamp;
+    float bg[3];
+    int tile_w, tile_h, tile_w_log2, tile_h_log2;
+    int ntx, nty;
+    int membership;
+};
+
+// Attribute source.  FP32 arrays, or BF16/FP8 planes with per-channel scales.
+struct GaussSrc {
+    int64_t n;
+    int sh_degree, K;
+    int precision;
+    const float *means, *log_scales, *quats, *opacity_logits, *sh;
+    const int32_t *group_id;
+    const uint16_t *means_h, *log_scales_h, *quats_h, *opacity_h;
+    const uint8_t *sh_q;
+    const float *scales;
+    const float *group_q, *group_t;  // NULL = identity motion
+    int n_groups;
+};
+
+__host__ __device__ inline int64_t sel_global(const Selection &s, int64_t j) {
+    int k = 0;
+    while (k + 1 < s.n_ranges && j >= s.range_start[k + 1]) ++k;
+    return s.range_begin[k] + (j - s.range_start[k]);
+}
+
+// ---- launchers (host) ----
+
+// Projection of the n_sel selected Gaussians.  Writes rec[3*j..3*j+2], depth
+// keys (kCulledKey when culled), values = j, and tiles touched per Gaussian.
+cudaError_t launch_preprocess(const GaussSrc &g, const Selection &sel, int64_t n_sel,
+                              const CamParams &cam, const RenderParams &rp, float4 *rec,
+                              uint32_t *depth_keys, uint32_t *depth_vals, uint32_t *touched,
+                              cudaStream_t st);
+
+// rank r -> compact j = perm[r]: ranked[r] = rec[j], touched_r[r] = touched[j]
+cudaError_t launch_rank_gather(const uint32_t *perm, const float4 *rec, const uint32_t *touched,
+                               int64_t n, float4 *ranked, uint32_t *touched_r, cudaStream_t st);
+
+// Exclusive scan of n uint32 values; writes out[0..n) and, if total != NULL,
+// the sum to *total (device).  `partials` needs scan_partials_size(n) words.
+size_t scan_partials_size(int64_t n);
+cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
+                                  uint32_t *partials, cudaStream_t st);
+
+// Stable LSD radix sort of (key, value) pairs on key bits [0, end_bit).
+// keys[0]/vals[0] hold the input; the sorted output ends in buffer *out_buf.
+// n_dev: optional device count (<= n_max) read by the kernels; n_max sizes the grid.
+size_t radix_scratch_words(int64_t n_max);
+cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
+                             const uint32_t *n_dev, int end_bit, uint32_t *scratch, int *out_buf,
+                             cudaStream_t st);
+
+// Emit (tile key, rank) for every tile of every visible Gaussian, in rank order.
+// Entries at positions >= cap are dropped (fixed-capacity mode reports the overflow).
+cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uint32_t *touched_r,
+                        int64_t n, const RenderParams &rp, uint32_t *keys, uint32_t *vals,
+                        uint32_t cap, cudaStream_t st);
+
+// Tile ranges [start, end) from sorted tile keys; ranges must be zeroed.
+cudaError_t launch_tile_ranges(const uint32_t *keys, const uint32_t *n_dev, int64_t n_max,
+                               uint2 *ranges, cudaStream_t st);
+
+// Front-to-back blend, one CTA per tile.
+cudaError_t launch_blend_fwd(const uint2 *ranges, const uint32_t *sorted_vals,
+                             const float4 *ranked, const CamParams &cam, const RenderParams &rp,
+                             float *image, float *final_T, uint32_t *n_contrib,
+                             uint32_t *n_blended, cudaStream_t st);
+
+// sorted list entry (rank) -> global Gaussian index, int64
+cudaError_t launch_entries_to_global(const uint32_t *sorted_vals, const uint32_t *perm,
+                                     const Selection &sel, int64_t K, int64_t *out,
+                                     cudaStream_t st);
+
+// ---- backward ----
+
+// Reverse compositing per tile; writes 9 partial gradients per (tile, Gaussian)
+// entry at the entry's emit position offsets[r] + (index of the tile in the
+// Gaussian's tile rectangle): planes part[c * K + e], c = du, dv, da, db, dc,
+// dopacity, dr, dg, db.
+cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
+                             const float4 *ranked, const uint32_t *offsets, const CamParams &cam,
+                             const RenderParams &rp, const float *final_T,
+                             const uint32_t *n_contrib, const float *dL_dimg, float *part,
+                             int64_t K, cudaStream_t st);
+
+// Per-rank sum of the partials over the Gaussian's entries -> g2d[9 * r + c].
+cudaError_t launch_reduce_entries(const float *part, int64_t K, const uint32_t *offsets,
+                                  const uint32_t *touched_r, int64_t n, float *g2d,
+                                  cudaStream_t st);
+
+// Chain rule from the 2D gradients to the attributes and to per-Gaussian motion
+// contributions (7 floats per compact position: dq_g[4], dt_g[3]).
+cudaError_t launch_preprocess_bwd(const GaussSrc &g, const Selection &sel, int64_t n_sel,
+                                  const CamParams &cam, const RenderParams &rp,
+                                  const uint32_t *perm, const float *g2d, const float4 *ranked,
+                                  gc_grads out, float *motion_contrib, cudaStream_t st);
+
+// Deterministic per-group sums of the motion contributions (sorted by group).
+cudaError_t launch_group_reduce(const uint32_t *group_sorted_vals, const uint32_t *group_keys,
+                                int64_t n, const float *motion_contrib, int n_groups,
+                                float *d_group_q, float *d_group_t, cudaStream_t st);
+
+cudaError_t launch_group_keys(const GaussSrc &g, const Selection &sel, int64_t n_sel,
+                              uint32_t *keys, uint32_t *vals, cudaStream_t st);
+
+}  // namespace gc

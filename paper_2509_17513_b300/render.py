@@ -1,0 +1,280 @@
+"""Thin PyTorch binding of the C ABI: marshals tensors into gc4d.h structs.
+
+PyTorch provides device memory and the stream; every step of the render runs
+in libgc4d.so.  ``Renderer.forward`` / ``Renderer.backward`` are the two calls
+of the boundary; ``render`` is a ``torch.autograd.Function`` on top of them.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import check, lib
+
+ATTRS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def camera_struct(cam) -> _abi.Camera:
+    """Any object with width, height, fx, fy, cx, cy, R (3x3), t (3), campos (3)."""
+    c = _abi.Camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    R = np.asarray(cam.R, np.float32).reshape(-1)
+    for k in range(9):
+        c.R[k] = float(R[k])
+    t = np.asarray(cam.t, np.float32).reshape(-1)
+    p = np.asarray(cam.campos, np.float32).reshape(-1)
+    for k in range(3):
+        c.t[k] = float(t[k])
+        c.campos[k] = float(p[k])
+    return c
+
+
+class GaussianSet:
+    """Device tensors of a Gaussian set plus the host struct that points at them.
+
+    FP32: ``means`` (N,3), ``log_scales`` (N,3), ``quats`` (N,4), ``opacity_logits``
+    (N,), ``sh`` (N,K,3), optional ``group_id`` (N,) int32.  Reduced precision:
+    ``means_bf16`` etc. as int16/uint8 bit patterns plus ``scales``.
+    """
+
+    def __init__(self, layer_offsets, sh_degree: int, precision: int = _abi.GC_PREC_FP32, **t):
+        self.tensors = {k: v for k, v in t.items() if v is not None}
+        for k, v in self.tensors.items():
+            if not v.is_cuda or not v.is_contiguous():
+                raise ValueError(f"{k} must be a contiguous CUDA tensor")
+        self.layer_offsets = np.ascontiguousarray(np.asarray(layer_offsets, np.int64))
+        self.sh_degree = int(sh_degree)
+        self.precision = int(precision)
+        s = _abi.Gaussians()
+        s.n = int(self.layer_offsets[-1])
+        s.n_layers = len(self.layer_offsets) - 1
+        s.layer_offsets = self.layer_offsets.ctypes.data
+        s.sh_degree = self.sh_degree
+        s.precision = self.precision
+        for name in ("means", "log_scales", "quats", "opacity_logits", "sh", "group_id",
+                     "means_bf16", "log_scales_bf16", "quats_bf16", "opacity_bf16", "sh_e4m3",
+                     "scales"):
+            v = self.tensors.get(name)
+            setattr(s, name, None if v is None else v.data_ptr())
+        self.struct = s
+
+    @property
+    def n(self) -> int:
+        return int(self.layer_offsets[-1])
+
+    @staticmethod
+    def from_scene(scene, device="cuda") -> "GaussianSet":
+        def f(a):
+            return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
+        return GaussianSet(scene.layer_offsets, scene.sh_degree, _abi.GC_PREC_FP32,
+                           means=f(scene.means), log_scales=f(scene.log_scales),
+                           quats=f(scene.quats), opacity_logits=f(scene.opacity_logits),
+                           sh=f(scene.sh),
+                           group_id=torch.from_numpy(np.ascontiguousarray(scene.group_id, np.int32)).to(device))
+
+    @staticmethod
+    def from_quantized(q: dict, scene, device="cuda") -> "GaussianSet":
+        """Reduced-precision set from ``synth.scenes.quantize_scene`` output."""
+        def u16(a):
+            return torch.from_numpy(np.ascontiguousarray(a).view(np.int16)).to(device)
+        scales = np.concatenate([q["means_scale"], q["log_scales_scale"], q["quats_scale"],
+                                 q["opacity_scale"], q["sh_scale"].reshape(-1)]).astype(np.float32)
+        return GaussianSet(scene.layer_offsets, scene.sh_degree, _abi.GC_PREC_BF16_FP8,
+                           means_bf16=u16(q["means"]), log_scales_bf16=u16(q["log_scales"]),
+                           quats_bf16=u16(q["quats"]), opacity_bf16=u16(q["opacity_logits"]),
+                           sh_e4m3=torch.from_numpy(np.ascontiguousarray(q["sh"])).to(device),
+                           scales=torch.from_numpy(scales).to(device),
+                           group_id=torch.from_numpy(np.ascontiguousarray(scene.group_id, np.int32)).to(device))
+
+
+class MotionFrame:
+    """One frame of cumulative group motion: q (G,4), t (G,3) CUDA float32."""
+
+    def __init__(self, q: torch.Tensor, t: torch.Tensor):
+        self.q = q.contiguous()
+        self.t = t.contiguous()
+        s = _abi.Motion()
+        s.n_groups = int(q.shape[0])
+        s.q = self.q.data_ptr()
+        s.t = self.t.data_ptr()
+        self.struct = s
+
+    @staticmethod
+    def from_motion(motion, frame: int, device="cuda") -> "MotionFrame":
+        return MotionFrame(torch.from_numpy(np.ascontiguousarray(motion.q[frame])).to(device),
+                           torch.from_numpy(np.ascontiguousarray(motion.t[frame])).to(device))
+
+
+class Saved:
+    """A library-owned saved forward state (for the backward pass)."""
+
+    def __init__(self, renderer: "Renderer"):
+        self.renderer = renderer
+        h = C.c_void_p()
+        check(lib().gc_saved_create(renderer.ctx, C.byref(h)), renderer.ctx)
+        self.handle = h
+
+    def __del__(self):
+        try:
+            if self.handle and self.renderer.ctx:
+                lib().gc_saved_destroy(self.renderer.ctx, self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+class Renderer:
+    """A gc4d context on one CUDA device."""
+
+    def __init__(self, device: int = 0, tile=(16, 16), near=0.2, dilation=0.3, clamp=1.3,
+                 bg=(0.0, 0.0, 0.0), membership: int = _abi.GC_MEMBER_PIXEL,
+                 key_capacity: int = 0):
+        L = lib()
+        o = _abi.Options()
+        check(L.gc_default_options(C.byref(o)))
+        o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
+        o.near_plane, o.dilation, o.frustum_clamp = near, dilation, clamp
+        for k in range(3):
+            o.bg[k] = float(bg[k])
+        o.membership = int(membership)
+        o.key_capacity = int(key_capacity)
+        self.options = o
+        self.device = int(device)
+        h = C.c_void_p()
+        check(L.gc_create(C.byref(h), self.device, C.byref(o)))
+        self.ctx = h
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().gc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, **kw):
+        o = self.options
+        if "tile" in kw:
+            o.tile_w, o.tile_h = kw["tile"]
+        if "key_capacity" in kw:
+            o.key_capacity = int(kw["key_capacity"])
+        if "bg" in kw:
+            for k in range(3):
+                o.bg[k] = float(kw["bg"][k])
+        if "membership" in kw:
+            o.membership = int(kw["membership"])
+        check(lib().gc_set_options(self.ctx, C.byref(o)), self.ctx)
+
+    def forward(self, gs: GaussianSet, motion: MotionFrame | None, layer_mask: int, camera,
+                saved: Saved | None = None, out: torch.Tensor | None = None, stream=None):
+        cam = camera_struct(camera)
+        if out is None:
+            out = torch.empty((3, cam.height, cam.width), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+        st = lib().gc_render_forward(self.ctx, C.byref(gs.struct),
+                                     C.byref(motion.struct) if motion is not None else None,
+                                     int(layer_mask) & 0xFFFFFFFF, C.byref(cam), _ptr(out),
+                                     saved.handle if saved is not None else None, _stream(stream))
+        check(st, self.ctx)
+        return out
+
+    def backward(self, saved: Saved | None, gs: GaussianSet, motion: MotionFrame | None,
+                 dL_dimage: torch.Tensor, grads: dict | None = None, stream=None) -> dict:
+        dev = f"cuda:{self.device}"
+        K = (gs.sh_degree + 1) ** 2
+        n = gs.n
+        if grads is None:
+            grads = {"means": torch.empty((n, 3), device=dev), "log_scales": torch.empty((n, 3), device=dev),
+                     "quats": torch.empty((n, 4), device=dev), "opacity_logits": torch.empty(n, device=dev),
+                     "sh": torch.empty((n, K, 3), device=dev)}
+            if motion is not None:
+                G = motion.q.shape[0]
+                grads["group_q"] = torch.empty((G, 4), device=dev)
+                grads["group_t"] = torch.empty((G, 3), device=dev)
+        g = _abi.Grads()
+        g.d_means = grads["means"].data_ptr() if "means" in grads else None
+        g.d_log_scales = grads["log_scales"].data_ptr() if "log_scales" in grads else None
+        g.d_quats = grads["quats"].data_ptr() if "quats" in grads else None
+        g.d_opacity_logits = grads["opacity_logits"].data_ptr() if "opacity_logits" in grads else None
+        g.d_sh = grads["sh"].data_ptr() if "sh" in grads else None
+        g.d_group_q = grads["group_q"].data_ptr() if "group_q" in grads else None
+        g.d_group_t = grads["group_t"].data_ptr() if "group_t" in grads else None
+        dl = dL_dimage.contiguous()
+        st = lib().gc_render_backward(self.ctx, saved.handle if saved is not None else None,
+                                      C.byref(gs.struct),
+                                      C.byref(motion.struct) if motion is not None else None,
+                                      _ptr(dl), C.byref(g), _stream(stream))
+        check(st, self.ctx)
+        return grads
+
+    def stats(self, saved: Saved | None = None, stream=None) -> dict:
+        s = _abi.Stats()
+        check(lib().gc_saved_stats(self.ctx, saved.handle if saved else None, C.byref(s),
+                                   _stream(stream)), self.ctx)
+        return {"n_selected": s.n_selected, "n_visible": s.n_visible, "n_keys": s.n_keys,
+                "n_tiles": s.n_tiles, "width": s.width, "height": s.height}
+
+    def tile_lists(self, saved: Saved | None = None, stream=None):
+        st = self.stats(saved, stream)
+        dev = f"cuda:{self.device}"
+        ranges = torch.zeros((st["n_tiles"], 2), dtype=torch.int32, device=dev)
+        ids = torch.zeros(max(st["n_keys"], 1), dtype=torch.int64, device=dev)
+        check(lib().gc_saved_tile_lists(self.ctx, saved.handle if saved else None, _ptr(ranges),
+                                        _ptr(ids), ids.numel(), _stream(stream)), self.ctx)
+        return ranges, ids[:st["n_keys"]]
+
+    def pixel_state(self, saved: Saved | None = None, stream=None):
+        st = self.stats(saved, stream)
+        dev = f"cuda:{self.device}"
+        T = torch.empty((st["height"], st["width"]), device=dev)
+        nb = torch.empty((st["height"], st["width"]), dtype=torch.int32, device=dev)
+        check(lib().gc_saved_pixel_state(self.ctx, saved.handle if saved else None, _ptr(T), _ptr(nb),
+                                         _stream(stream)), self.ctx)
+        return T, nb
+
+    def check(self, stream=None):
+        check(lib().gc_check(self.ctx, _stream(stream)), self.ctx)
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, renderer, layer_offsets, sh_degree, layer_mask, camera, means, log_scales, quats,
+                opacity_logits, sh, group_id, group_q, group_t):
+        gs = GaussianSet(layer_offsets, sh_degree, _abi.GC_PREC_FP32, means=means.contiguous(),
+                         log_scales=log_scales.contiguous(), quats=quats.contiguous(),
+                         opacity_logits=opacity_logits.contiguous(), sh=sh.contiguous(),
+                         group_id=group_id)
+        mo = MotionFrame(group_q, group_t) if group_q is not None else None
+        saved = Saved(renderer)
+        img = renderer.forward(gs, mo, layer_mask, camera, saved)
+        ctx.renderer, ctx.gs, ctx.mo, ctx.saved = renderer, gs, mo, saved
+        return img
+
+    @staticmethod
+    def backward(ctx, dimg):
+        g = ctx.renderer.backward(ctx.saved, ctx.gs, ctx.mo, dimg.contiguous())
+        return (None, None, None, None, None, g["means"], g["log_scales"], g["quats"],
+                g["opacity_logits"], g["sh"], None, g.get("group_q"), g.get("group_t"))
+
+
+def render(renderer: Renderer, layer_offsets, sh_degree: int, layer_mask: int, camera, means,
+           log_scales, quats, opacity_logits, sh, group_id=None, group_q=None, group_t=None):
+    """Differentiable render of one frame (image 3 x H x W)."""
+    return _RenderFn.apply(renderer, layer_offsets, sh_degree, layer_mask, camera, means,
+                           log_scales, quats, opacity_logits, sh, group_id, group_q, group_t)
