@@ -194,11 +194,38 @@ GC_API gc_status gc_saved_stats(gc_context *ctx, const gc_saved *saved, gc_stats
 GC_API gc_status gc_saved_tile_lists(gc_context *ctx, const gc_saved *saved, int32_t *ranges,
                               int64_t *gauss_ids, int64_t capacity, void *stream);
 
-/* Per-pixel diagnostics of `saved`: final transmittance (H x W FP32) and the
- * number of Gaussians blended into each pixel (H x W int32); device buffers,
- * either may be NULL. */
+/* Per-pixel diagnostics of `saved` (device buffers, H x W, any may be NULL):
+ * final transmittance (FP32), number of Gaussians blended into the pixel and
+ * number of tile-list entries the pixel walked before it stopped (int32). */
 GC_API gc_status gc_saved_pixel_state(gc_context *ctx, const gc_saved *saved, float *final_T,
-                               int32_t *n_blended, void *stream);
+                                      int32_t *n_blended, int32_t *n_walked, void *stream);
+
+/* Stages timed by the profiler (CUDA events recorded on the call's stream
+ * between stages). */
+enum {
+    GC_STAGE_PREPROCESS = 0,   /* motion + projection + footprint + colour */
+    GC_STAGE_DEPTH_SORT = 1,   /* radix sort of the depth keys */
+    GC_STAGE_SCAN = 2,         /* rank gather + exclusive scan of tiles touched */
+    GC_STAGE_EMIT = 3,         /* (tile, rank) entries */
+    GC_STAGE_TILE_SORT = 4,    /* radix sort of the tile keys */
+    GC_STAGE_RANGES = 5,       /* per-tile [start, end) */
+    GC_STAGE_BLEND = 6,        /* forward compositing */
+    GC_STAGE_BLEND_BWD = 7,    /* reverse compositing + per-tile reduction */
+    GC_STAGE_REDUCE = 8,       /* per-Gaussian sum of the tile partials */
+    GC_STAGE_PREPROCESS_BWD = 9, /* chain rule to the attributes */
+    GC_STAGE_GROUP_REDUCE = 10,  /* per-group motion gradient */
+    GC_N_STAGES = 11
+};
+
+/* Enables (1) or disables (0) per-stage event timing on this context. */
+GC_API gc_status gc_profile_enable(gc_context *ctx, int enable);
+
+/* Reads and resets the profile: per stage the summed milliseconds and the
+ * number of timed calls (arrays of GC_N_STAGES; either may be NULL), and the
+ * number of kernels the library launched since the last read on this
+ * context.  Waits for the recorded events. */
+GC_API gc_status gc_profile_read(gc_context *ctx, double *stage_ms, int64_t *stage_calls,
+                                 uint64_t *kernel_launches);
 
 /* Reports errors recorded on the device by fixed-capacity or bounded-wait
  * work since the last check (synchronises `stream`): GC_OK,

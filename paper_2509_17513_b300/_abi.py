@@ -23,6 +23,9 @@ GC_ERR_UNSUPPORTED = 7
 STATUS_NAMES = {0: "GC_OK", 1: "GC_ERR_INVALID_ARG", 2: "GC_ERR_OOM", 3: "GC_ERR_CAPACITY",
                 4: "GC_ERR_TIMEOUT", 5: "GC_ERR_CUDA", 6: "GC_ERR_STATE", 7: "GC_ERR_UNSUPPORTED"}
 
+STAGES = ("preprocess", "depth_sort", "scan", "emit", "tile_sort", "ranges", "blend",
+          "blend_bwd", "reduce", "preprocess_bwd", "group_reduce")
+
 GC_PREC_FP32 = 0
 GC_PREC_BF16_FP8 = 1
 GC_MEMBER_PIXEL = 0
@@ -79,7 +82,9 @@ SIGNATURES = {
     "gc_render_backward": (C.c_int, [P, P, P, P, P, P, P]),
     "gc_saved_stats": (C.c_int, [P, P, P, P]),
     "gc_saved_tile_lists": (C.c_int, [P, P, P, P, C.c_int64, P]),
-    "gc_saved_pixel_state": (C.c_int, [P, P, P, P, P]),
+    "gc_saved_pixel_state": (C.c_int, [P, P, P, P, P, P]),
+    "gc_profile_enable": (C.c_int, [P, C.c_int]),
+    "gc_profile_read": (C.c_int, [P, P, P, P]),
     "gc_check": (C.c_int, [P, P]),
     "gc_last_error": (C.c_char_p, [P]),
     "gc_version": (C.c_char_p, []),

@@ -10,11 +10,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "gc_internal.cuh"
 
@@ -75,11 +77,26 @@ struct gc_saved {
     bool k_exact = false;
     int depth_buf = 0, tile_buf = 0;
     DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
-        final_T, n_contrib, n_blended, words;
+        final_T, n_contrib, n_blended, n_walked, words;
+};
+
+namespace gc {
+static std::atomic<uint64_t> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace gc
+
+struct ProfMark {
+    int stage;  // -1: end of a call
+    int event;  // index into the event pool
 };
 
 struct gc_context {
     int device = 0;
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_pool;
+    std::vector<ProfMark> prof_marks;
+    uint64_t launch_base = 0;
     gc_options opt{};
     gc_saved internal;
     DevBuf scratch, bwd_part, bwd_g2d, bwd_motion, gkeys[2], gvals[2];
@@ -109,6 +126,20 @@ gc_status fail(gc_context *ctx, gc_status s, const char *fmt, ...) {
             return fail((ctx), e_ == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA,    \
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
+
+// Records a stage boundary on the stream when profiling is on.
+cudaError_t prof_mark(gc_context *ctx, cudaStream_t s, int stage) {
+    if (!ctx->prof_on) return cudaSuccess;
+    const size_t idx = ctx->prof_marks.size();
+    if (idx >= ctx->prof_pool.size()) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        ctx->prof_pool.push_back(e);
+    }
+    ctx->prof_marks.push_back({stage, (int)idx});
+    return cudaEventRecord(ctx->prof_pool[idx], s);
+}
 
 gc_status check_options(gc_context *ctx, const gc_options *o) {
     bool shape_ok = (o->tile_w == 16 && o->tile_h == 16) || (o->tile_w == 8 && o->tile_h == 32) ||
@@ -260,7 +291,7 @@ static void saved_release(gc_context *ctx, gc_saved *s) {
     DevBuf *bufs[] = {&s->rec, &s->ranked, &s->dkeys[0], &s->dkeys[1], &s->dvals[0], &s->dvals[1],
                       &s->touched, &s->touched_r, &s->offsets, &s->tkeys[0], &s->tkeys[1],
                       &s->tvals[0], &s->tvals[1], &s->ranges, &s->final_T, &s->n_contrib,
-                      &s->n_blended, &s->words};
+                      &s->n_blended, &s->n_walked, &s->words};
     for (DevBuf *b : bufs) release(*b);
     s->valid = false;
 }
@@ -274,6 +305,7 @@ gc_status gc_destroy(gc_context *ctx) {
                           &ctx->gkeys[0], &ctx->gkeys[1], &ctx->gvals[0], &ctx->gvals[1]};
         for (DevBuf *b : bufs) release(*b);
         if (ctx->host_word) cudaFreeHost(ctx->host_word);
+        for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     }
     delete ctx;
     return GC_OK;
@@ -359,6 +391,7 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
     GC_CUDA(ctx, grow(S.final_T, (size_t)hw * 4));
     GC_CUDA(ctx, grow(S.n_contrib, (size_t)hw * 4));
     GC_CUDA(ctx, grow(S.n_blended, (size_t)hw * 4));
+    GC_CUDA(ctx, grow(S.n_walked, (size_t)hw * 4));
     GC_CUDA(ctx, grow(S.words, 64));
     const int64_t cap_fixed = o.key_capacity;
     const size_t scan_words = gc::scan_partials_size(nn);
@@ -369,12 +402,15 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
     if (n_sel > 0) {
         GC_CUDA(ctx, grow(ctx->scratch, 4 * std::max(gc::radix_scratch_words(nn), scan_words)));
         uint32_t *scratch = ctx->scratch.as<uint32_t>();
+        GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_PREPROCESS));
         GC_CUDA(ctx, gc::launch_preprocess(src, S.sel, n_sel, cp, rp, S.rec.as<float4>(),
                                            S.dkeys[0].as<uint32_t>(), S.dvals[0].as<uint32_t>(),
                                            S.touched.as<uint32_t>(), s));
         uint32_t *dk[2] = {S.dkeys[0].as<uint32_t>(), S.dkeys[1].as<uint32_t>()};
         uint32_t *dv[2] = {S.dvals[0].as<uint32_t>(), S.dvals[1].as<uint32_t>()};
+        GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_DEPTH_SORT));
         GC_CUDA(ctx, gc::radix_sort_pairs(dk, dv, n_sel, nullptr, 32, scratch, &S.depth_buf, s));
+        GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_SCAN));
         GC_CUDA(ctx, gc::launch_rank_gather(dv[S.depth_buf], S.rec.as<float4>(),
                                             S.touched.as<uint32_t>(), n_sel, S.ranked.as<float4>(),
                                             S.touched_r.as<uint32_t>(), s));
@@ -397,6 +433,7 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
         GC_CUDA(ctx, grow(ctx->scratch, 4 * std::max(gc::radix_scratch_words(kk), scan_words)));
         scratch = ctx->scratch.as<uint32_t>();
         if (K > 0) {
+            GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_EMIT));
             GC_CUDA(ctx, gc::launch_emit(S.ranked.as<float4>(), S.offsets.as<uint32_t>(),
                                          S.touched_r.as<uint32_t>(), n_sel, rp,
                                          S.tkeys[0].as<uint32_t>(), S.tvals[0].as<uint32_t>(),
@@ -404,8 +441,10 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
             uint32_t *tk[2] = {S.tkeys[0].as<uint32_t>(), S.tkeys[1].as<uint32_t>()};
             uint32_t *tv[2] = {S.tvals[0].as<uint32_t>(), S.tvals[1].as<uint32_t>()};
             const uint32_t *ndev = S.k_exact ? nullptr : words;
+            GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_TILE_SORT));
             GC_CUDA(ctx, gc::radix_sort_pairs(tk, tv, K, ndev, bits_for(n_tiles - 1), scratch,
                                               &S.tile_buf, s));
+            GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_RANGES));
             GC_CUDA(ctx, gc::launch_tile_ranges(tk[S.tile_buf], ndev, K, S.ranges.as<uint2>(), s));
         }
     } else {
@@ -413,9 +452,11 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
     }
     S.K = K;
     uint32_t *sorted_vals = (n_sel > 0 && K > 0) ? S.tvals[S.tile_buf].as<uint32_t>() : nullptr;
+    GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_BLEND));
     GC_CUDA(ctx, gc::launch_blend_fwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(), cp, rp,
                                       image, S.final_T.as<float>(), S.n_contrib.as<uint32_t>(),
-                                      S.n_blended.as<uint32_t>(), s));
+                                      S.n_blended.as<uint32_t>(), S.n_walked.as<uint32_t>(), s));
+    GC_CUDA(ctx, prof_mark(ctx, s, -1));
     S.valid = true;
     ctx->last = &S;
     return GC_OK;
@@ -475,7 +516,7 @@ gc_status gc_saved_tile_lists(gc_context *ctx, const gc_saved *saved, int32_t *r
 }
 
 gc_status gc_saved_pixel_state(gc_context *ctx, const gc_saved *saved, float *final_T,
-                               int32_t *n_blended, void *stream) {
+                               int32_t *n_blended, int32_t *n_walked, void *stream) {
     if (!ctx) return GC_ERR_INVALID_ARG;
     const gc_saved &S = saved ? *saved : ctx->internal;
     if (!S.valid) return fail(ctx, GC_ERR_STATE, "no forward recorded");
@@ -484,6 +525,37 @@ gc_status gc_saved_pixel_state(gc_context *ctx, const gc_saved *saved, float *fi
     size_t hw = (size_t)S.cam.width * S.cam.height;
     if (final_T) GC_CUDA(ctx, cudaMemcpyAsync(final_T, S.final_T.p, hw * 4, cudaMemcpyDeviceToDevice, s));
     if (n_blended) GC_CUDA(ctx, cudaMemcpyAsync(n_blended, S.n_blended.p, hw * 4, cudaMemcpyDeviceToDevice, s));
+    if (n_walked) GC_CUDA(ctx, cudaMemcpyAsync(n_walked, S.n_walked.p, hw * 4, cudaMemcpyDeviceToDevice, s));
+    return GC_OK;
+}
+
+gc_status gc_profile_enable(gc_context *ctx, int enable) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    ctx->prof_on = enable != 0;
+    return GC_OK;
+}
+
+gc_status gc_profile_read(gc_context *ctx, double *stage_ms, int64_t *stage_calls,
+                          uint64_t *kernel_launches) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    if (stage_ms) for (int k = 0; k < GC_N_STAGES; ++k) stage_ms[k] = 0.0;
+    if (stage_calls) for (int k = 0; k < GC_N_STAGES; ++k) stage_calls[k] = 0;
+    if (!ctx->prof_marks.empty()) {
+        GC_CUDA(ctx, cudaEventSynchronize(ctx->prof_pool[ctx->prof_marks.back().event]));
+        for (size_t i = 0; i + 1 < ctx->prof_marks.size(); ++i) {
+            const ProfMark &a = ctx->prof_marks[i], &b = ctx->prof_marks[i + 1];
+            if (a.stage < 0) continue;
+            float ms = 0.f;
+            GC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->prof_pool[a.event], ctx->prof_pool[b.event]));
+            if (stage_ms) stage_ms[a.stage] += ms;
+            if (stage_calls) stage_calls[a.stage] += 1;
+        }
+    }
+    ctx->prof_marks.clear();
+    const uint64_t now = gc::launches_total();
+    if (kernel_launches) *kernel_launches = now - ctx->launch_base;
+    ctx->launch_base = now;
     return GC_OK;
 }
 

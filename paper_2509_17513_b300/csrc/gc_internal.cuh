@@ -60,6 +60,10 @@ __host__ __device__ inline int64_t sel_global(const Selection &s, int64_t j) {
     return s.range_begin[k] + (j - s.range_start[k]);
 }
 
+// Kernel launches issued by this library (all contexts), for accounting.
+void note_launches(int n);
+uint64_t launches_total();
+
 // ---- launchers (host) ----
 
 // Projection of the n_sel selected Gaussians.  Writes rec[3*j..3*j+2], depth
@@ -97,11 +101,12 @@ cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uin
 cudaError_t launch_tile_ranges(const uint32_t *keys, const uint32_t *n_dev, int64_t n_max,
                                uint2 *ranges, cudaStream_t st);
 
-// Front-to-back blend, one CTA per tile.
+// Front-to-back blend, one CTA per tile.  Per pixel: final transmittance, list
+// position after the last blended entry, number blended, number of entries walked.
 cudaError_t launch_blend_fwd(const uint2 *ranges, const uint32_t *sorted_vals,
                              const float4 *ranked, const CamParams &cam, const RenderParams &rp,
                              float *image, float *final_T, uint32_t *n_contrib,
-                             uint32_t *n_blended, cudaStream_t st);
+                             uint32_t *n_blended, uint32_t *n_walked, cudaStream_t st);
 
 // sorted list entry (rank) -> global Gaussian index, int64
 cudaError_t launch_entries_to_global(const uint32_t *sorted_vals, const uint32_t *perm,

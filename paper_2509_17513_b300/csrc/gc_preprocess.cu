@@ -244,6 +244,7 @@ cudaError_t launch_preprocess(const GaussSrc &g, const Selection &sel, int64_t n
     unsigned blocks = (unsigned)((n_sel + 255) / 256);
     k_preprocess<<<blocks, 256, 0, st>>>(g, sel, n_sel, cam, rp, rec, depth_keys, depth_vals,
                                          touched);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -252,6 +253,7 @@ cudaError_t launch_rank_gather(const uint32_t *perm, const float4 *rec, const ui
     if (n <= 0) return cudaSuccess;
     k_rank_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(perm, rec, touched, n, ranked,
                                                               touched_r);
+    note_launches(1);
     return cudaGetLastError();
 }
 

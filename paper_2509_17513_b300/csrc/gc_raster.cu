@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(256) k_blend_fwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, int W, int H, int ntx, float bg0, float bg1, float bg2,
     int membership, float *__restrict__ image, float *__restrict__ final_T,
-    uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ n_blended) {
+    uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ n_blended,
+    uint32_t *__restrict__ n_walked) {
     static_assert(TW * TH == 256, "tile must hold 256 pixels");
     __shared__ float4 sA[256];  // u, v, conic a, conic b
     __shared__ float4 sB[256];  // conic c, opacity, red, green
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd(
 
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     bool done = !inside;
-    uint32_t last = 0, nb = 0;
+    uint32_t last = 0, nb = 0, walked = 0;
 
     for (int b = 0; b < n; b += 256) {
         if (__syncthreads_count(done) == 256) break;
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd(
                 const float Tn = T * (1.f - alpha);
                 if (Tn < 1e-4f) {
                     done = true;
+                    walked = (uint32_t)(b + k + 1);
                     break;
                 }
                 const float w = alpha * T;
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(256) k_blend_fwd(
         final_T[p] = T;
         n_contrib[p] = last;
         if (n_blended) n_blended[p] = nb;
+        if (n_walked) n_walked[p] = done ? walked : (uint32_t)n;
     }
 }
 
@@ -194,6 +197,7 @@ cudaError_t launch_entries_to_global(const uint32_t *sorted_vals, const uint32_t
     if (K <= 0) return cudaSuccess;
     int64_t blocks = std::min<int64_t>((K + 255) / 256, 148 * 16);
     k_entries_to_global<<<(unsigned)blocks, 256, 0, st>>>(sorted_vals, perm, sel, K, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -204,6 +208,7 @@ cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uin
     const int64_t threads = ((n + 31) / 32) * 32;
     k_emit<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
         ranked, offsets, touched_r, n, rp.tile_w_log2, rp.tile_h_log2, rp.ntx, cap, keys, vals);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -213,18 +218,19 @@ cudaError_t launch_tile_ranges(const uint32_t *keys, const uint32_t *n_dev, int6
     int64_t blocks = (n_max + 255) / 256;
     if (blocks > 148 * 32) blocks = 148 * 32;
     k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(keys, n_dev, n_max, ranges);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_blend_fwd(const uint2 *ranges, const uint32_t *sorted_vals,
                              const float4 *ranked, const CamParams &cam, const RenderParams &rp,
                              float *image, float *final_T, uint32_t *n_contrib,
-                             uint32_t *n_blended, cudaStream_t st) {
+                             uint32_t *n_blended, uint32_t *n_walked, cudaStream_t st) {
     const unsigned tiles = (unsigned)(rp.ntx * rp.nty);
     if (tiles == 0) return cudaSuccess;
 #define GC_BLEND_ARGS                                                                          \
     ranges, sorted_vals, ranked, cam.width, cam.height, rp.ntx, rp.bg[0], rp.bg[1], rp.bg[2], \
-        rp.membership, image, final_T, n_contrib, n_blended
+        rp.membership, image, final_T, n_contrib, n_blended, n_walked
     if (rp.tile_w == 16 && rp.tile_h == 16)
         k_blend_fwd<16, 16><<<tiles, 256, 0, st>>>(GC_BLEND_ARGS);
     else if (rp.tile_w == 8 && rp.tile_h == 32)
@@ -233,6 +239,7 @@ cudaError_t launch_blend_fwd(const uint2 *ranges, const uint32_t *sorted_vals,
         k_blend_fwd<32, 8><<<tiles, 256, 0, st>>>(GC_BLEND_ARGS);
     else
         return cudaErrorInvalidValue;
+    note_launches(1);
 #undef GC_BLEND_ARGS
     return cudaGetLastError();
 }

@@ -231,8 +231,11 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
     }
     int64_t nb = (n + kScanChunk - 1) / kScanChunk;
     k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, partials);
+    note_launches(1);
     k_scan_partials<<<1, 1024, 0, st>>>(partials, nb, total);
+    note_launches(1);
     k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, partials);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -258,12 +261,14 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
         uint32_t mask = (1u << bits) - 1u;
         k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(keys[cur], n_dev, n_max, shift, mask, counts,
                                                        nblocks);
+        note_launches(1);
         cudaError_t e = launch_exclusive_scan(counts, counts, (int64_t)256 * nblocks, nullptr,
                                               partials, st);
         if (e != cudaSuccess) return e;
         k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(keys[cur], vals[cur], keys[cur ^ 1],
                                                           vals[cur ^ 1], n_dev, n_max, shift, mask,
                                                           counts, nblocks);
+        note_launches(1);
         cur ^= 1;
     }
     *out_buf = cur;

@@ -239,14 +239,29 @@ class Renderer:
                                         _ptr(ids), ids.numel(), _stream(stream)), self.ctx)
         return ranges, ids[:st["n_keys"]]
 
-    def pixel_state(self, saved: Saved | None = None, stream=None):
+    def pixel_state(self, saved: Saved | None = None, stream=None, with_walked: bool = False):
+        """(final T, blended count[, walked count]) per pixel of the saved forward."""
         st = self.stats(saved, stream)
         dev = f"cuda:{self.device}"
         T = torch.empty((st["height"], st["width"]), device=dev)
         nb = torch.empty((st["height"], st["width"]), dtype=torch.int32, device=dev)
+        nw = torch.empty((st["height"], st["width"]), dtype=torch.int32, device=dev) if with_walked else None
         check(lib().gc_saved_pixel_state(self.ctx, saved.handle if saved else None, _ptr(T), _ptr(nb),
-                                         _stream(stream)), self.ctx)
-        return T, nb
+                                         _ptr(nw), _stream(stream)), self.ctx)
+        return (T, nb, nw) if with_walked else (T, nb)
+
+    def profile(self, enable: bool = True):
+        check(lib().gc_profile_enable(self.ctx, 1 if enable else 0), self.ctx)
+
+    def profile_read(self) -> dict:
+        """Per-stage summed ms and call counts since the last read, and kernel launches."""
+        ms = (C.c_double * len(_abi.STAGES))()
+        calls = (C.c_int64 * len(_abi.STAGES))()
+        launches = C.c_uint64()
+        check(lib().gc_profile_read(self.ctx, ms, calls, C.byref(launches)), self.ctx)
+        return {"stage_ms": {n: ms[i] for i, n in enumerate(_abi.STAGES)},
+                "stage_calls": {n: calls[i] for i, n in enumerate(_abi.STAGES)},
+                "kernel_launches": int(launches.value)}
 
     def check(self, stream=None):
         check(lib().gc_check(self.ctx, _stream(stream)), self.ctx)
