@@ -80,6 +80,7 @@ SIGNATURES = {
     "gc_saved_destroy": (C.c_int, [P, P]),
     "gc_render_forward": (C.c_int, [P, P, P, C.c_uint32, P, P, P, P]),
     "gc_render_backward": (C.c_int, [P, P, P, P, P, P, P]),
+    "gc_render_forward_noalloc": (C.c_int, [P, P, P, C.c_uint32, P, P, P, C.c_char_p, C.c_size_t]),
     "gc_saved_stats": (C.c_int, [P, P, P, P]),
     "gc_saved_tile_lists": (C.c_int, [P, P, P, P, C.c_int64, P]),
     "gc_saved_pixel_state": (C.c_int, [P, P, P, P, P, P]),
