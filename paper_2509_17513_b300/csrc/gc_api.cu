@@ -69,6 +69,9 @@ struct gc_saved {
     bool valid = false;
     int64_t n = 0, n_sel = 0;
     int sh_degree = 0, n_groups = 1;
+    bool has_motion = false;
+    int n_layers = 0;
+    int64_t layer_offsets[gc::kMaxLayers + 1] = {};
     uint32_t layer_mask = 0;
     gc::Selection sel{};
     gc::CamParams cam{};
@@ -99,7 +102,7 @@ struct gc_context {
     uint64_t launch_base = 0;
     gc_options opt{};
     gc_saved internal;
-    DevBuf scratch, bwd_part, bwd_g2d, bwd_motion, gkeys[2], gvals[2];
+    DevBuf scratch, bwd_part, bwd_g2d, bwd_motion, bwd_rmax, bwd_group;
     uint32_t *host_word = nullptr;  // pinned
     const gc_saved *last = nullptr; // state written by the most recent forward
     std::string err;
@@ -302,7 +305,7 @@ gc_status gc_destroy(gc_context *ctx) {
         DeviceGuard dg(ctx->device);
         saved_release(ctx, &ctx->internal);
         DevBuf *bufs[] = {&ctx->scratch, &ctx->bwd_part, &ctx->bwd_g2d, &ctx->bwd_motion,
-                          &ctx->gkeys[0], &ctx->gkeys[1], &ctx->gvals[0], &ctx->gvals[1]};
+                          &ctx->bwd_rmax, &ctx->bwd_group};
         for (DevBuf *b : bufs) release(*b);
         if (ctx->host_word) cudaFreeHost(ctx->host_word);
         for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
@@ -358,6 +361,9 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
     S.n_sel = n_sel;
     S.sh_degree = g->sh_degree;
     S.n_groups = src.n_groups;
+    S.has_motion = motion != nullptr;
+    S.n_layers = g->n_layers;
+    for (int l = 0; l <= g->n_layers; ++l) S.layer_offsets[l] = g->layer_offsets[l];
     S.layer_mask = layer_mask;
     gc::CamParams &cp = S.cam;
     cp.width = cam->width; cp.height = cam->height;
@@ -581,6 +587,66 @@ extern "C" gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved,
                                         const gc_gaussians *g, const gc_motion *motion,
                                         const float *dL_dimage, gc_grads *out, void *stream) {
     if (!ctx) return GC_ERR_INVALID_ARG;
-    (void)saved; (void)g; (void)motion; (void)dL_dimage; (void)out; (void)stream;
-    return fail(ctx, GC_ERR_UNSUPPORTED, "backward not built yet");
+    if (!dL_dimage || !out) return fail(ctx, GC_ERR_INVALID_ARG, "dL_dimage or grads is NULL");
+    const gc_saved &S = saved ? *saved : ctx->internal;
+    if (!S.valid) return fail(ctx, GC_ERR_STATE, "no forward recorded in this saved state");
+    gc::GaussSrc src;
+    gc_status st = make_source(ctx, g, motion, src);
+    if (st != GC_OK) return st;
+    if (g->n != S.n || g->sh_degree != S.sh_degree || g->n_layers != S.n_layers)
+        return fail(ctx, GC_ERR_STATE, "the Gaussian set differs from the one of the saved forward");
+    if ((motion != nullptr) != S.has_motion || (motion && motion->n_groups != S.n_groups))
+        return fail(ctx, GC_ERR_STATE, "the motion differs from the one of the saved forward");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K3 = 3 * (g->sh_degree + 1) * (g->sh_degree + 1);
+
+    // Gaussians outside the selected layers receive zero gradient
+    for (int l = 0; l < S.n_layers; ++l) {
+        if ((S.layer_mask >> l) & 1u) continue;
+        const int64_t a = S.layer_offsets[l], b = S.layer_offsets[l + 1];
+        if (b <= a) continue;
+        if (out->d_means) GC_CUDA(ctx, cudaMemsetAsync(out->d_means + 3 * a, 0, (size_t)(b - a) * 12, s));
+        if (out->d_log_scales) GC_CUDA(ctx, cudaMemsetAsync(out->d_log_scales + 3 * a, 0, (size_t)(b - a) * 12, s));
+        if (out->d_quats) GC_CUDA(ctx, cudaMemsetAsync(out->d_quats + 4 * a, 0, (size_t)(b - a) * 16, s));
+        if (out->d_opacity_logits) GC_CUDA(ctx, cudaMemsetAsync(out->d_opacity_logits + a, 0, (size_t)(b - a) * 4, s));
+        if (out->d_sh) GC_CUDA(ctx, cudaMemsetAsync(out->d_sh + (int64_t)K3 * a, 0, (size_t)(b - a) * K3 * 4, s));
+    }
+    const int G = S.has_motion ? S.n_groups : 0;
+    if (S.n_sel == 0) {
+        if (G && out->d_group_q) GC_CUDA(ctx, cudaMemsetAsync(out->d_group_q, 0, (size_t)G * 16, s));
+        if (G && out->d_group_t) GC_CUDA(ctx, cudaMemsetAsync(out->d_group_t, 0, (size_t)G * 12, s));
+        return GC_OK;
+    }
+    const int64_t K = S.K > 0 ? S.K : 1;
+    const int64_t n_tiles = (int64_t)S.rp.ntx * S.rp.nty;
+    GC_CUDA(ctx, grow(ctx->bwd_part, (size_t)K * 9 * 4));
+    GC_CUDA(ctx, grow(ctx->bwd_g2d, (size_t)S.n_sel * 9 * 4));
+    GC_CUDA(ctx, grow(ctx->bwd_motion, (size_t)S.n_sel * 7 * 4));
+    GC_CUDA(ctx, grow(ctx->bwd_rmax, (size_t)n_tiles * 4));
+    if (G) GC_CUDA(ctx, grow(ctx->bwd_group, gc::group_partial_floats(S.n_sel, G) * 4));
+    const uint32_t *sorted_vals = S.K > 0 ? S.tvals[S.tile_buf].as<uint32_t>() : nullptr;
+
+    GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_BLEND_BWD));
+    GC_CUDA(ctx, gc::launch_blend_bwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(),
+                                      S.offsets.as<uint32_t>(), S.cam, S.rp, S.final_T.as<float>(),
+                                      S.n_contrib.as<uint32_t>(), dL_dimage, ctx->bwd_part.as<float>(),
+                                      K, ctx->bwd_rmax.as<int32_t>(), s));
+    GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_REDUCE));
+    GC_CUDA(ctx, gc::launch_reduce_entries(ctx->bwd_part.as<float>(), K, S.offsets.as<uint32_t>(),
+                                           S.touched_r.as<uint32_t>(), S.ranked.as<float4>(),
+                                           ctx->bwd_rmax.as<int32_t>(), S.rp, S.n_sel,
+                                           ctx->bwd_g2d.as<float>(), s));
+    GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_PREPROCESS_BWD));
+    GC_CUDA(ctx, gc::launch_preprocess_bwd(src, S.sel, S.n_sel, S.cam, S.rp,
+                                           S.dvals[S.depth_buf].as<uint32_t>(), ctx->bwd_g2d.as<float>(),
+                                           S.touched_r.as<uint32_t>(), *out,
+                                           G ? ctx->bwd_motion.as<float>() : nullptr, s));
+    if (G) {
+        GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_GROUP_REDUCE));
+        GC_CUDA(ctx, gc::launch_group_reduce(ctx->bwd_motion.as<float>(), src.group_id, S.sel, S.n_sel, G,
+                                             ctx->bwd_group.as<float>(), out->d_group_q, out->d_group_t, s));
+    }
+    GC_CUDA(ctx, prof_mark(ctx, s, -1));
+    return GC_OK;
 }

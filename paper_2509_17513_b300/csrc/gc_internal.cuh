@@ -118,31 +118,33 @@ cudaError_t launch_entries_to_global(const uint32_t *sorted_vals, const uint32_t
 // Reverse compositing per tile; writes 9 partial gradients per (tile, Gaussian)
 // entry at the entry's emit position offsets[r] + (index of the tile in the
 // Gaussian's tile rectangle): planes part[c * K + e], c = du, dv, da, db, dc,
-// dopacity, dr, dg, db.
+// dopacity, dr, dg, db.  Entries behind every pixel's last blended one are not
+// written; tile_rmax[t] = largest rank that may have contributed to tile t (-1: none).
 cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
                              const float4 *ranked, const uint32_t *offsets, const CamParams &cam,
                              const RenderParams &rp, const float *final_T,
                              const uint32_t *n_contrib, const float *dL_dimg, float *part,
-                             int64_t K, cudaStream_t st);
+                             int64_t K, int32_t *tile_rmax, cudaStream_t st);
 
 // Per-rank sum of the partials over the Gaussian's entries -> g2d[9 * r + c].
 cudaError_t launch_reduce_entries(const float *part, int64_t K, const uint32_t *offsets,
-                                  const uint32_t *touched_r, int64_t n, float *g2d,
-                                  cudaStream_t st);
+                                  const uint32_t *touched_r, const float4 *ranked,
+                                  const int32_t *tile_rmax, const RenderParams &rp, int64_t n,
+                                  float *g2d, cudaStream_t st);
 
-// Chain rule from the 2D gradients to the attributes and to per-Gaussian motion
-// contributions (7 floats per compact position: dq_g[4], dt_g[3]).
+// Chain rule from the 2D gradients (by rank) to the attributes (by global index)
+// and to per-Gaussian motion terms (7 floats per compact position: dq_g[4], dt_g[3]).
 cudaError_t launch_preprocess_bwd(const GaussSrc &g, const Selection &sel, int64_t n_sel,
                                   const CamParams &cam, const RenderParams &rp,
-                                  const uint32_t *perm, const float *g2d, const float4 *ranked,
-                                  gc_grads out, float *motion_contrib, cudaStream_t st);
+                                  const uint32_t *perm, const float *g2d,
+                                  const uint32_t *touched_r, gc_grads out, float *motion_contrib,
+                                  cudaStream_t st);
 
-// Deterministic per-group sums of the motion contributions (sorted by group).
-cudaError_t launch_group_reduce(const uint32_t *group_sorted_vals, const uint32_t *group_keys,
-                                int64_t n, const float *motion_contrib, int n_groups,
+// Deterministic per-group sums of the motion terms.  `partial` needs
+// group_partial_floats(n_sel, n_groups) floats.
+size_t group_partial_floats(int64_t n_sel, int n_groups);
+cudaError_t launch_group_reduce(const float *motion_contrib, const int32_t *group_id,
+                                const Selection &sel, int64_t n_sel, int n_groups, float *partial,
                                 float *d_group_q, float *d_group_t, cudaStream_t st);
-
-cudaError_t launch_group_keys(const GaussSrc &g, const Selection &sel, int64_t n_sel,
-                              uint32_t *keys, uint32_t *vals, cudaStream_t st);
 
 }  // namespace gc

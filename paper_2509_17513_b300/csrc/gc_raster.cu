@@ -12,6 +12,7 @@
 
 #include <algorithm>
 
+#include "gc_blend.cuh"
 #include "gc_internal.cuh"
 
 namespace gc {
@@ -149,12 +150,13 @@ __global__ void __launch_bounds__(256) k_blend_fwd(
                 const float4 a = sA[k];
                 const float4 bb = sB[k];
                 const float dx = pcx - a.x, dy = pcy - a.y;
-                const float power = -0.5f * (a.z * dx * dx + bb.x * dy * dy) - a.w * dx * dy;
+                const float power = blend_power(a.z, a.w, bb.x, dx, dy);
                 if (power > 0.f) continue;
-                const float alpha = fminf(0.99f, bb.y * __expf(power));
-                if (alpha < (1.f / 255.f)) continue;
+                float G;
+                const float alpha = fminf(kAlphaMax, blend_raw_alpha(bb.y, power, G));
+                if (alpha < kAlphaMin) continue;
                 const float Tn = T * (1.f - alpha);
-                if (Tn < 1e-4f) {
+                if (Tn < kTStop) {
                     done = true;
                     walked = (uint32_t)(b + k + 1);
                     break;
