@@ -19,7 +19,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -29,13 +28,15 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "Mpixel/s at 1920x1080, forward, layer levels L1-L6 (300k-Gaussian hierarchical scene)"
+METRIC = ("Mpixel/s at 1920x1080, forward (fwd_bwd: forward + backward), layer levels L1-L6, "
+          "300k-Gaussian hierarchical scene")
 UNIT = "Mpixel/s"
 WORKLOAD = ("hier1080: 300k Gaussians in 6 layers of 50k, SH degree 3, 64 motion groups, "
             "30 frames x levels L1..L6 = 180 renders of 1920x1080 per step")
 FP32_LANES_PER_SM = 128
 N_SMS = 148
 BLEND_FLOPS_PER_PAIR = 26  # FP32 ops of one compositing step (Eq. 2), see the design doc
+BLEND_BWD_FLOPS_PER_PAIR = 48  # FP32 ops of one reverse compositing step incl. its share of the reduction
 SORT_BYTES_PER_KEY_PASS = 20  # histogram read 4 B + scatter read 8 B + write 8 B
 
 
@@ -122,6 +123,30 @@ def load_traffic(kernel: str):
 
 # --------------------------------------------------------------------------- GPU arm
 
+def roofline_for(stage, per_launch_ms, work, peaks, peak_kind):
+    """Roofline object of the dominant stage.  `work`: algorithmic FLOPs (ALU stages)
+    or bytes (HBM stages) of one launch."""
+    alu = {"blend": ("k_blend_fwd", BLEND_FLOPS_PER_PAIR), "blend_bwd": ("k_blend_bwd", BLEND_BWD_FLOPS_PER_PAIR)}
+    hbm = {"tile_sort": "k_radix_scatter", "emit": "k_emit", "reduce": "k_reduce_entries",
+           "depth_sort": "k_radix_scatter"}
+    if stage in alu:
+        peak = N_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        achieved = work / (per_launch_ms / 1e3) / 1e12
+        kern = alu[stage][0]
+        return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": load_traffic(kern), "kernel": kern,
+                "launch_ms": round(per_launch_ms, 4),
+                "peak_source": f"derived, not measured: {N_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                               f"x {peaks.get('sm_max_mhz', 2032.0)} MHz max SM clock ({peak_kind} file)"}
+    if stage in hbm:
+        achieved = work / (per_launch_ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": load_traffic(hbm[stage]),
+                "kernel": hbm[stage], "launch_ms": round(per_launch_ms, 4),
+                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    return None
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -145,6 +170,9 @@ def run_gpu(args):
     gs = gc.GaussianSet.from_scene(w.scene, dev)
     motions = [gc.MotionFrame.from_motion(w.motion, f, dev) for f in range(args.frames)]
     ring = [torch.empty((3, H, W), device=dev) for _ in range(4)]
+    saved = gc.Saved(r)
+    upstream = (torch.randn((3, H, W), generator=torch.Generator().manual_seed(7)) * 1e-3).to(dev)
+    grads = None
 
     # capacity for the (tile, Gaussian) lists: the largest frame of the workload, plus slack
     kmax = 0
@@ -154,108 +182,112 @@ def run_gpu(args):
     cap = int(kmax * 1.05) + 4096
     r.set_options(key_capacity=cap)
 
-    def step():
+    def step_fwd():
         for i, (f, lv) in enumerate(reqs):
             r.forward(gs, motions[f], scenes.level_mask(lv), w.cameras[f], out=ring[i % 4])
 
+    def step_fwd_bwd():
+        nonlocal grads
+        for i, (f, lv) in enumerate(reqs):
+            r.forward(gs, motions[f], scenes.level_mask(lv), w.cameras[f], saved, out=ring[i % 4])
+            grads = r.backward(saved, gs, motions[f], upstream, grads)
+
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
-        step()
+        step_fwd()
+        step_fwd_bwd()
     r.check()
     torch.cuda.synchronize()
 
-    # walked (pixel, entry) pairs of the blend for one step (deterministic; not timed)
-    walked_pairs = 0
-    keys_total = 0
+    # algorithmic work of one step (deterministic; measured outside the timed regions)
+    walked_pairs = bwd_pairs = keys_total = 0
     for (f, lv) in reqs:
         r.forward(gs, motions[f], scenes.level_mask(lv), w.cameras[f], out=ring[0])
-        _, _, walked = r.pixel_state(with_walked=True)
+        _, _, walked, contrib = r.pixel_state(with_walked=True)
         walked_pairs += int(walked.sum(dtype=torch.int64).item())
+        bwd_pairs += int(contrib.sum(dtype=torch.int64).item())
         keys_total += r.stats()["n_keys"]
     keys_mean = keys_total / len(reqs)
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, events on the rendering stream, L2 flushed between steps
-    clocks = ClockSampler(local)
-    r.profile(True)
-    r.profile_read()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    total_ms = 0.0
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    prof = r.profile_read()
-    r.profile(False)
-    r.check()
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    def timed(step):
+        """K steps, CUDA events on the rendering stream, L2 flushed between steps."""
+        clocks = ClockSampler(local)
+        r.profile(True)
+        r.profile_read()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        total = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        prof = r.profile_read()
+        r.profile(False)
+        r.check()
+        if world > 1:
+            t = torch.tensor([total], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total, prof, clk
 
-    pixels_per_step = len(reqs) * W * H
-    value = pixels_per_step * args.steps * world / (total_ms / 1e3) / 1e6
-    ms_per_step = total_ms / args.steps
-
-    # ---- roofline of the dominant stage
     peaks, peak_kind = measured_peaks()
-    st_ms = prof["stage_ms"]
-    st_calls = prof["stage_calls"]
-    dom = max(st_ms, key=lambda k: st_ms[k])
-    share = {k: round(v / max(1e-9, sum(st_ms.values())), 4) for k, v in st_ms.items() if v > 0}
-    roof = None
-    if dom == "blend":
-        per_launch_ms = st_ms["blend"] / max(1, st_calls["blend"])
-        flops_per_launch = walked_pairs / len(reqs) * BLEND_FLOPS_PER_PAIR
-        achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
-        peak = N_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-        tr = load_traffic("k_blend_fwd")
-        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": tr, "kernel": "k_blend_fwd",
-                "peak_source": f"derived: {N_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                               f"{peaks.get('sm_max_mhz', 2032.0)} MHz ({peak_kind} clock)"}
-    else:
-        per_launch_ms = st_ms[dom] / max(1, st_calls[dom])
-        nbytes = {"tile_sort": 2 * SORT_BYTES_PER_KEY_PASS * keys_mean,
-                  "emit": 8 * keys_mean}.get(dom)
-        if nbytes:
-            achieved = nbytes / (per_launch_ms / 1e3) / 1e9
-            roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                    "traffic": load_traffic(dom), "kernel": dom,
-                    "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)"}
+    pixels_per_step = len(reqs) * W * H
 
-    # ---- end to end through the public API: pinned host inputs in, images out
+    def summary(total_ms, prof):
+        st_ms, st_calls = prof["stage_ms"], prof["stage_calls"]
+        dom = max(st_ms, key=lambda k: st_ms[k])
+        per_launch = st_ms[dom] / max(1, st_calls[dom])
+        work = {"blend": walked_pairs / len(reqs) * BLEND_FLOPS_PER_PAIR,
+                "blend_bwd": bwd_pairs / len(reqs) * BLEND_BWD_FLOPS_PER_PAIR,
+                "tile_sort": 2 * SORT_BYTES_PER_KEY_PASS * keys_mean,
+                "emit": 8 * keys_mean, "reduce": 40 * keys_mean}.get(dom, 0.0)
+        tot = max(1e-9, sum(st_ms.values()))
+        return {"value": round(pixels_per_step * args.steps * world / (total_ms / 1e3) / 1e6, 1),
+                "ms_per_step": round(total_ms / args.steps, 3),
+                "fps": round(len(reqs) * args.steps * world / (total_ms / 1e3), 1),
+                "stage_ms_per_render": {k: round(v / max(1, st_calls[k]), 4) for k, v in st_ms.items() if v > 0},
+                "stage_share": {k: round(v / tot, 4) for k, v in st_ms.items() if v > 0},
+                "gpu_launches": prof["kernel_launches"],
+                "roofline": roofline_for(dom, per_launch, work, peaks, peak_kind)}
+
+    fwd_ms, fwd_prof, clk = timed(step_fwd)
+    fwd = summary(fwd_ms, fwd_prof)
+    fb_ms, fb_prof, clk_fb = timed(step_fwd_bwd)
+    fb = summary(fb_ms, fb_prof)
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, r, w, reqs, W, H, dev, stream)
 
-    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+    line = {"metric": METRIC, "value": fwd["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": fwd["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded scene shaped like the paper's workload; no dataset)",
             "config": {"workload": WORKLOAD, "n_gaussians": w.scene.n, "width": W, "height": H,
                        "renders_per_step": len(reqs), "tile": "16x16", "key_capacity": cap,
                        "l2": "flushed (256 MB write) between steps, outside the timed events",
                        "parallelism": f"replicas x{world}"},
-            "fps": round(len(reqs) * args.steps * world / (total_ms / 1e3), 1),
-            "stage_ms_per_render": {k: round(v / max(1, st_calls[k]), 4) for k, v in st_ms.items() if v > 0},
-            "stage_share": share,
-            "gpu_launches": prof["kernel_launches"],
-            "walked_pairs_per_step": walked_pairs,
-            "keys_per_render": round(keys_mean),
-            "roofline": roof, "clocks": clk, "e2e": e2e}
+            "fps": fwd["fps"],
+            "stage_ms_per_render": fwd["stage_ms_per_render"], "stage_share": fwd["stage_share"],
+            "gpu_launches": fwd["gpu_launches"],
+            "roofline": fwd["roofline"], "clocks": clk, "e2e": e2e,
+            "fwd_bwd": {"metric": "Mpixel/s at 1920x1080, forward + backward (upstream dL/dimage given)",
+                        "value": fb["value"], "unit": UNIT, "ms_per_step": fb["ms_per_step"],
+                        "fps": fb["fps"], "stage_ms_per_render": fb["stage_ms_per_render"],
+                        "stage_share": fb["stage_share"], "gpu_launches": fb["gpu_launches"],
+                        "roofline": fb["roofline"], "clocks": clk_fb},
+            "work_per_step": {"blend_walked_pairs": walked_pairs, "blend_bwd_pairs": bwd_pairs,
+                              "keys_per_render": round(keys_mean)}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:

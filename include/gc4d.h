@@ -180,7 +180,7 @@ GC_API gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const
  *
  * Same result as gc_render_forward with the same options (opt may be NULL for
  * the defaults; key_capacity is ignored), no saved state.  All scratch lives in
- * one static device array of about 22 MiB inside the library, which every GPU
+ * one static device array of about 22.5 MiB inside the library, which every GPU
  * that loads the library holds until the process exits.  Limits: at most
  * 32,768 selected Gaussians, 1,048,576 (tile, Gaussian) pairs, 262,144 pixels
  * and 4,096 tiles; larger requests return GC_ERR_CAPACITY with a message in
@@ -223,10 +223,13 @@ GC_API gc_status gc_saved_tile_lists(gc_context *ctx, const gc_saved *saved, int
                               int64_t *gauss_ids, int64_t capacity, void *stream);
 
 /* Per-pixel diagnostics of `saved` (device buffers, H x W, any may be NULL):
- * final transmittance (FP32), number of Gaussians blended into the pixel and
- * number of tile-list entries the pixel walked before it stopped (int32). */
+ * final transmittance (FP32), number of Gaussians blended into the pixel,
+ * number of tile-list entries the pixel walked before it stopped, and the
+ * list position just after its last blended entry (where the backward pass
+ * starts; int32). */
 GC_API gc_status gc_saved_pixel_state(gc_context *ctx, const gc_saved *saved, float *final_T,
-                                      int32_t *n_blended, int32_t *n_walked, void *stream);
+                                      int32_t *n_blended, int32_t *n_walked, int32_t *n_contrib,
+                                      void *stream);
 
 /* Stages timed by the profiler (CUDA events recorded on the call's stream
  * between stages). */

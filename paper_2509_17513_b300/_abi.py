@@ -83,7 +83,7 @@ SIGNATURES = {
     "gc_render_forward_noalloc": (C.c_int, [P, P, P, C.c_uint32, P, P, P, C.c_char_p, C.c_size_t]),
     "gc_saved_stats": (C.c_int, [P, P, P, P]),
     "gc_saved_tile_lists": (C.c_int, [P, P, P, P, C.c_int64, P]),
-    "gc_saved_pixel_state": (C.c_int, [P, P, P, P, P, P]),
+    "gc_saved_pixel_state": (C.c_int, [P, P, P, P, P, P, P]),
     "gc_profile_enable": (C.c_int, [P, C.c_int]),
     "gc_profile_read": (C.c_int, [P, P, P, P]),
     "gc_check": (C.c_int, [P, P]),

@@ -80,7 +80,7 @@ struct gc_saved {
     bool k_exact = false;
     int depth_buf = 0, tile_buf = 0;
     DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
-        final_T, n_contrib, n_blended, n_walked, words;
+        final_T, n_contrib, n_blended, n_walked, words, tile_diff;
 };
 
 namespace gc {
@@ -294,7 +294,7 @@ static void saved_release(gc_context *ctx, gc_saved *s) {
     DevBuf *bufs[] = {&s->rec, &s->ranked, &s->dkeys[0], &s->dkeys[1], &s->dvals[0], &s->dvals[1],
                       &s->touched, &s->touched_r, &s->offsets, &s->tkeys[0], &s->tkeys[1],
                       &s->tvals[0], &s->tvals[1], &s->ranges, &s->final_T, &s->n_contrib,
-                      &s->n_blended, &s->n_walked, &s->words};
+                      &s->n_blended, &s->n_walked, &s->words, &s->tile_diff};
     for (DevBuf *b : bufs) release(*b);
     s->valid = false;
 }
@@ -398,7 +398,13 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
     GC_CUDA(ctx, grow(S.n_contrib, (size_t)hw * 4));
     GC_CUDA(ctx, grow(S.n_blended, (size_t)hw * 4));
     GC_CUDA(ctx, grow(S.n_walked, (size_t)hw * 4));
-    GC_CUDA(ctx, grow(S.words, 64));
+    if (!S.words.p) {
+        GC_CUDA(ctx, grow(S.words, 64));
+        GC_CUDA(ctx, cudaMemsetAsync(S.words.p, 0, 64, s));
+    }
+    const bool diff_ranges = gc::tile_diff_fits(rp.ntx, rp.nty);
+    const size_t diff_bytes = (size_t)(rp.ntx + 1) * (rp.nty + 1) * 4;
+    if (diff_ranges) GC_CUDA(ctx, grow(S.tile_diff, diff_bytes));
     const int64_t cap_fixed = o.key_capacity;
     const size_t scan_words = gc::scan_partials_size(nn);
 
@@ -409,13 +415,15 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
         GC_CUDA(ctx, grow(ctx->scratch, 4 * std::max(gc::radix_scratch_words(nn), scan_words)));
         uint32_t *scratch = ctx->scratch.as<uint32_t>();
         GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_PREPROCESS));
+        if (diff_ranges) GC_CUDA(ctx, cudaMemsetAsync(S.tile_diff.p, 0, diff_bytes, s));
         GC_CUDA(ctx, gc::launch_preprocess(src, S.sel, n_sel, cp, rp, S.rec.as<float4>(),
                                            S.dkeys[0].as<uint32_t>(), S.dvals[0].as<uint32_t>(),
-                                           S.touched.as<uint32_t>(), s));
+                                           S.touched.as<uint32_t>(),
+                                           diff_ranges ? S.tile_diff.as<int32_t>() : nullptr, s));
         uint32_t *dk[2] = {S.dkeys[0].as<uint32_t>(), S.dkeys[1].as<uint32_t>()};
         uint32_t *dv[2] = {S.dvals[0].as<uint32_t>(), S.dvals[1].as<uint32_t>()};
         GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_DEPTH_SORT));
-        GC_CUDA(ctx, gc::radix_sort_pairs(dk, dv, n_sel, nullptr, 32, scratch, &S.depth_buf, s));
+        GC_CUDA(ctx, gc::radix_sort_pairs(dk, dv, n_sel, nullptr, 32, scratch, &S.depth_buf, s, words + 1));
         GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_SCAN));
         GC_CUDA(ctx, gc::launch_rank_gather(dv[S.depth_buf], S.rec.as<float4>(),
                                             S.touched.as<uint32_t>(), n_sel, S.ranked.as<float4>(),
@@ -449,12 +457,16 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
             const uint32_t *ndev = S.k_exact ? nullptr : words;
             GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_TILE_SORT));
             GC_CUDA(ctx, gc::radix_sort_pairs(tk, tv, K, ndev, bits_for(n_tiles - 1), scratch,
-                                              &S.tile_buf, s));
+                                              &S.tile_buf, s, words + 1, /*keys_out=*/!diff_ranges));
             GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_RANGES));
-            GC_CUDA(ctx, gc::launch_tile_ranges(tk[S.tile_buf], ndev, K, S.ranges.as<uint2>(), s));
+            if (diff_ranges)
+                GC_CUDA(ctx, gc::launch_tile_ranges_from_diff(S.tile_diff.as<int32_t>(), rp.ntx, rp.nty,
+                                                              words, (uint32_t)K, S.ranges.as<uint2>(), s));
+            else
+                GC_CUDA(ctx, gc::launch_tile_ranges(tk[S.tile_buf], ndev, K, S.ranges.as<uint2>(), s));
         }
     } else {
-        GC_CUDA(ctx, cudaMemsetAsync(words, 0, 8, s));
+        GC_CUDA(ctx, cudaMemsetAsync(words, 0, 4, s));
     }
     S.K = K;
     uint32_t *sorted_vals = (n_sel > 0 && K > 0) ? S.tvals[S.tile_buf].as<uint32_t>() : nullptr;
@@ -522,7 +534,8 @@ gc_status gc_saved_tile_lists(gc_context *ctx, const gc_saved *saved, int32_t *r
 }
 
 gc_status gc_saved_pixel_state(gc_context *ctx, const gc_saved *saved, float *final_T,
-                               int32_t *n_blended, int32_t *n_walked, void *stream) {
+                               int32_t *n_blended, int32_t *n_walked, int32_t *n_contrib,
+                               void *stream) {
     if (!ctx) return GC_ERR_INVALID_ARG;
     const gc_saved &S = saved ? *saved : ctx->internal;
     if (!S.valid) return fail(ctx, GC_ERR_STATE, "no forward recorded");
@@ -532,6 +545,7 @@ gc_status gc_saved_pixel_state(gc_context *ctx, const gc_saved *saved, float *fi
     if (final_T) GC_CUDA(ctx, cudaMemcpyAsync(final_T, S.final_T.p, hw * 4, cudaMemcpyDeviceToDevice, s));
     if (n_blended) GC_CUDA(ctx, cudaMemcpyAsync(n_blended, S.n_blended.p, hw * 4, cudaMemcpyDeviceToDevice, s));
     if (n_walked) GC_CUDA(ctx, cudaMemcpyAsync(n_walked, S.n_walked.p, hw * 4, cudaMemcpyDeviceToDevice, s));
+    if (n_contrib) GC_CUDA(ctx, cudaMemcpyAsync(n_contrib, S.n_contrib.p, hw * 4, cudaMemcpyDeviceToDevice, s));
     return GC_OK;
 }
 
@@ -572,6 +586,14 @@ gc_status gc_check(gc_context *ctx, void *stream) {
     GC_CUDA(ctx, cudaStreamSynchronize(s));
     if (!ctx->last) return GC_OK;
     const gc_saved &S = *ctx->last;
+    if (S.words.p) {
+        uint32_t w[2];
+        GC_CUDA(ctx, cudaMemcpy(w, S.words.p, 8, cudaMemcpyDeviceToHost));
+        if (w[1]) {
+            GC_CUDA(ctx, cudaMemset(static_cast<uint32_t *>(S.words.p) + 1, 0, 4));
+            return fail(ctx, GC_ERR_TIMEOUT, "a bounded device wait ran out (error word %#x)", w[1]);
+        }
+    }
     if (S.valid && !S.k_exact && S.n_sel > 0) {
         GC_CUDA(ctx, cudaMemcpy(ctx->host_word, S.words.p, 4, cudaMemcpyDeviceToHost));
         if ((int64_t)ctx->host_word[0] > S.K)
@@ -633,14 +655,13 @@ extern "C" gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved,
                                       S.n_contrib.as<uint32_t>(), dL_dimage, ctx->bwd_part.as<float>(),
                                       K, ctx->bwd_rmax.as<int32_t>(), s));
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_REDUCE));
-    GC_CUDA(ctx, gc::launch_reduce_entries(ctx->bwd_part.as<float>(), K, S.offsets.as<uint32_t>(),
+    GC_CUDA(ctx, gc::launch_reduce_entries(ctx->bwd_part.as<float>(), S.offsets.as<uint32_t>(),
                                            S.touched_r.as<uint32_t>(), S.ranked.as<float4>(),
-                                           ctx->bwd_rmax.as<int32_t>(), S.rp, S.n_sel,
-                                           ctx->bwd_g2d.as<float>(), s));
+                                           ctx->bwd_rmax.as<int32_t>(), S.dvals[S.depth_buf].as<uint32_t>(),
+                                           S.rp, S.n_sel, ctx->bwd_g2d.as<float>(), s));
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_PREPROCESS_BWD));
-    GC_CUDA(ctx, gc::launch_preprocess_bwd(src, S.sel, S.n_sel, S.cam, S.rp,
-                                           S.dvals[S.depth_buf].as<uint32_t>(), ctx->bwd_g2d.as<float>(),
-                                           S.touched_r.as<uint32_t>(), *out,
+    GC_CUDA(ctx, gc::launch_preprocess_bwd(src, S.sel, S.n_sel, S.cam, S.rp, ctx->bwd_g2d.as<float>(),
+                                           S.touched.as<uint32_t>(), *out,
                                            G ? ctx->bwd_motion.as<float>() : nullptr, s));
     if (G) {
         GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_GROUP_REDUCE));

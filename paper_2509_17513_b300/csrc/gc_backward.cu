@@ -35,46 +35,101 @@ __device__ __forceinline__ void rect_of(float4 r2, int &x0, int &x1, int &y0, in
     y1 = (int)(ry >> 16);
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(256) k_blend_bwd(
+// Per-pixel reverse state.
+struct BwdPix {
+    float T, A0, A1, A2, g0, g1, g2;
+    uint32_t last;
+};
+
+// Reverse step of Eq. 2 for one pixel and list entry k; adds the pixel's nine partial
+// derivatives (du, dv, da, db, dc, dopacity, dr, dg, db) to v.  Returns whether the
+// entry was blended into the pixel.
+__device__ __forceinline__ bool bwd_step(BwdPix &P, float pcx, float pcy, const float4 &a,
+                                         const float4 &bb, const float4 &nat, float blue, float *v) {
+    const float dx = pcx - a.x, dy = pcy - a.y;
+    const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
+    if (p2 > 0.f) return false;
+    float G;
+    const float a0 = blend_raw_alpha(bb.y, p2, G);
+    const float alpha = fminf(kAlphaMax, a0);
+    if (alpha < kAlphaMin) return false;
+    P.T = P.T / (1.f - alpha);
+    const float w = alpha * P.T;
+    v[6] += w * P.g0;
+    v[7] += w * P.g1;
+    v[8] += w * P.g2;
+    const float dal = P.T * (P.g0 * (bb.z - P.A0) + P.g1 * (bb.w - P.A1) + P.g2 * (blue - P.A2));
+    P.A0 = fmaf(alpha, bb.z - P.A0, P.A0);
+    P.A1 = fmaf(alpha, bb.w - P.A1, P.A1);
+    P.A2 = fmaf(alpha, blue - P.A2, P.A2);
+    if (!(a0 > kAlphaMax)) {
+        v[5] += G * dal;
+        const float dp = alpha * dal;  // dL/dpower (natural exponent)
+        v[0] += (nat.x * dx + nat.y * dy) * dp;
+        v[1] += (nat.y * dx + nat.z * dy) * dp;
+        v[2] += -0.5f * dx * dx * dp;
+        v[3] += -dx * dy * dp;
+        v[4] += -0.5f * dy * dy * dp;
+    }
+    return true;
+}
+
+#ifndef GC_BWD_PPT
+#define GC_BWD_PPT 1  // pixels per thread in the backward blend (1 measured fastest on B300)
+#endif
+
+// Reverse compositing, one CTA per tile of TW x TH = 256 pixels with 256 / PPT
+// threads, each owning PPT vertically adjacent pixels.  For every list entry, the
+// nine partials are summed over the thread's pixels, then over the warp with a
+// transposing butterfly (values 0-7 spread over lane groups, 9 shuffles) plus a
+// plain butterfly for value 8, then over the warps in order.
+template <int TW, int TH, int PPT>
+__global__ void __launch_bounds__(256 / PPT) k_blend_bwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, int ntx,
     int tw_log2, int th_log2, float bg0, float bg1, float bg2, int membership,
     const float *__restrict__ final_T, const uint32_t *__restrict__ n_contrib,
     const float *__restrict__ dimg, float *__restrict__ part, int64_t K,
     int32_t *__restrict__ tile_rmax) {
-    __shared__ float4 sA[256];   // u, v, conic a, conic b
-    __shared__ float4 sB[256];   // conic c, opacity, red, green
+    constexpr int NT = 256 / PPT;
+    constexpr int NW = NT / 32;
+    __shared__ float4 sA[256];   // u, v, A, B (pre-scaled conic)
+    __shared__ float4 sB[256];   // C, opacity, red, green
     __shared__ float4 sC[256];   // blue, column mask, row mask, entry index (bits)
-    __shared__ float wpart[32][8][9];
+    __shared__ float4 sD[256];   // natural conic a, b, c
+    __shared__ float wpart[32][NW][9];
     __shared__ uint32_t s_last_max;
 
     const int tile = blockIdx.x;
     const int tx = tile % ntx, ty = tile / ntx;
-    const int lx = threadIdx.x % TW, ly = threadIdx.x / TW;
-    const int px = tx * TW + lx, py = ty * TH + ly;
-    const bool inside = px < W && py < H;
+    const int lx = threadIdx.x % TW, lyb = PPT * (threadIdx.x / TW);
+    const int px = tx * TW + lx;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
-    const uint32_t xbit = 1u << lx, ybit = 1u << ly;
+    const float pcx = (float)px + 0.5f;
+    const uint32_t xbit = 1u << lx;
     const uint2 range = ranges[tile];
+    const size_t hw = (size_t)W * H;
 
-    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    uint32_t last = 0;
-    if (inside) {
-        const size_t hw = (size_t)W * H, p = (size_t)py * W + px;
-        T = final_T[p];
-        last = n_contrib[p];
-        g0 = dimg[p];
-        g1 = dimg[hw + p];
-        g2 = dimg[2 * hw + p];
+    BwdPix P[PPT];
+    uint32_t my_last = 0;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const int py = ty * TH + lyb + i;
+        P[i] = {1.f, bg0, bg1, bg2, 0.f, 0.f, 0.f, 0u};
+        if (px < W && py < H) {
+            const size_t p = (size_t)py * W + px;
+            P[i].T = final_T[p];
+            P[i].last = n_contrib[p];
+            P[i].g0 = dimg[p];
+            P[i].g1 = dimg[hw + p];
+            P[i].g2 = dimg[2 * hw + p];
+        }
+        my_last = max(my_last, P[i].last);
     }
-    float A0 = bg0, A1 = bg1, A2 = bg2;  // colour behind, normalised by the transmittance
 
     if (threadIdx.x == 0) s_last_max = 0;
     __syncthreads();
-    // max over the tile of the list position after the last blended entry
-    uint32_t wmax = __reduce_max_sync(0xffffffffu, last);
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, my_last);
     if (lane == 0) atomicMax(&s_last_max, wmax);
     __syncthreads();
     const int n_active = (int)s_last_max;
@@ -84,8 +139,10 @@ __global__ void __launch_bounds__(256) k_blend_bwd(
     for (int hi = n_active; hi > 0; hi -= 256) {
         const int lo = max(hi - 256, 0);
         __syncthreads();
-        {
-            const int k = lo + (int)threadIdx.x;
+#pragma unroll
+        for (int h = 0; h < PPT; ++h) {
+            const int slot = (int)threadIdx.x + NT * h;
+            const int k = lo + slot;
             if (k < hi) {
                 const uint32_t r = sorted_vals[range.x + k];
                 const float4 a = ranked[3 * (size_t)r];
@@ -96,15 +153,16 @@ __global__ void __launch_bounds__(256) k_blend_bwd(
                 uint32_t cm = 0xffffffffu, rm = 0xffffffffu;
                 if (membership == GC_MEMBER_PIXEL) {
                     const int lx0 = max(x0 - tx * TW, 0), lx1 = min(x1 - tx * TW, TW - 1);
-                    const int ly0 = max(y0 - ty * TH, 0), ly1 = min(y1 - ty * TH, TH - 1);
+                    const int ly0r = max(y0 - ty * TH, 0), ly1r = min(y1 - ty * TH, TH - 1);
                     cm = (lx1 >= lx0) ? ((0xffffffffu >> (31 - lx1)) & (0xffffffffu << lx0)) : 0u;
-                    rm = (ly1 >= ly0) ? ((0xffffffffu >> (31 - ly1)) & (0xffffffffu << ly0)) : 0u;
+                    rm = (ly1r >= ly0r) ? ((0xffffffffu >> (31 - ly1r)) & (0xffffffffu << ly0r)) : 0u;
                 }
                 const int tx0 = x0 >> tw_log2, ty0 = y0 >> th_log2, twid = (x1 >> tw_log2) - tx0 + 1;
                 const uint32_t e = offsets[r] + (uint32_t)((ty - ty0) * twid + (tx - tx0));
-                sA[threadIdx.x] = a;
-                sB[threadIdx.x] = bb;
-                sC[threadIdx.x] = make_float4(c.x, __uint_as_float(cm), __uint_as_float(rm), __uint_as_float(e));
+                sA[slot] = a;
+                sB[slot] = bb;
+                sC[slot] = make_float4(c.x, __uint_as_float(cm), __uint_as_float(rm), __uint_as_float(e));
+                sD[slot] = make_float4(a.z * kUnscaleDiag, a.w * kUnscaleOff, bb.x * kUnscaleDiag, 0.f);
             }
         }
         __syncthreads();
@@ -115,77 +173,80 @@ __global__ void __launch_bounds__(256) k_blend_bwd(
                 float v[9];
 #pragma unroll
                 for (int c = 0; c < 9; ++c) v[c] = 0.f;
+                const float4 c4 = sC[s];
+                const uint32_t rm = __float_as_uint(c4.z) >> lyb;
+                const bool col = (__float_as_uint(c4.y) & xbit) != 0;
+                bool any = false;
+#pragma unroll
+                for (int i = 0; i < PPT; ++i) any = any || (col && (uint32_t)k < P[i].last && ((rm >> i) & 1u));
                 bool contrib = false;
-                if ((uint32_t)k < last) {
-                    const float4 c4 = sC[s];
-                    if ((__float_as_uint(c4.y) & xbit) && (__float_as_uint(c4.z) & ybit)) {
-                        const float4 a = sA[s];
-                        const float4 bb = sB[s];
-                        const float dx = pcx - a.x, dy = pcy - a.y;
-                        const float power = blend_power(a.z, a.w, bb.x, dx, dy);
-                        if (!(power > 0.f)) {
-                            float G;
-                            const float a0 = blend_raw_alpha(bb.y, power, G);
-                            const float alpha = fminf(kAlphaMax, a0);
-                            if (!(alpha < kAlphaMin)) {
-                                contrib = true;
-                                T = T / (1.f - alpha);
-                                const float w = alpha * T;
-                                v[6] = w * g0;
-                                v[7] = w * g1;
-                                v[8] = w * g2;
-                                const float dal = T * (g0 * (bb.z - A0) + g1 * (bb.w - A1) + g2 * (c4.x - A2));
-                                A0 = alpha * bb.z + (1.f - alpha) * A0;
-                                A1 = alpha * bb.w + (1.f - alpha) * A1;
-                                A2 = alpha * c4.x + (1.f - alpha) * A2;
-                                if (!(a0 > kAlphaMax)) {
-                                    v[5] = G * dal;
-                                    const float dp = alpha * dal;
-                                    v[0] = (a.z * dx + a.w * dy) * dp;
-                                    v[1] = (a.w * dx + bb.x * dy) * dp;
-                                    v[2] = -0.5f * dx * dx * dp;
-                                    v[3] = -dx * dy * dp;
-                                    v[4] = -0.5f * dy * dy * dp;
-                                }
-                            }
+                if (any) {
+                    const float4 a = sA[s], bb = sB[s], nat = sD[s];
+#pragma unroll
+                    for (int i = 0; i < PPT; ++i)
+                        if (col && (uint32_t)k < P[i].last && ((rm >> i) & 1u))
+                            contrib |= bwd_step(P[i], pcx, (float)(ty * TH + lyb + i) + 0.5f, a, bb, nat, c4.x, v);
+                }
+                float out0 = 0.f, out8 = 0.f;
+                if (__any_sync(0xffffffffu, contrib)) {
+                    // values 0..7: transposing butterfly; lane l ends with value (l >> 2) & 7
+                    {
+                        const bool up = lane & 16;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float send = up ? v[i] : v[i + 4];
+                            const float keep = up ? v[i + 4] : v[i];
+                            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
                         }
                     }
-                }
-                if (__any_sync(0xffffffffu, contrib)) {
+                    {
+                        const bool up = lane & 8;
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) {
-                        float x = v[c];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                        v[c] = x;
+                        for (int i = 0; i < 2; ++i) {
+                            const float send = up ? v[i] : v[i + 2];
+                            const float keep = up ? v[i + 2] : v[i];
+                            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                        }
                     }
-                }
-                float mine = 0.f;
+                    {
+                        const bool up = lane & 4;
+                        const float send = up ? v[0] : v[1];
+                        const float keep = up ? v[1] : v[0];
+                        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                    }
+                    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+                    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+                    out0 = v[0];
+                    float x = v[8];
 #pragma unroll
-                for (int c = 0; c < 9; ++c)
-                    if (lane == c) mine = v[c];
-                if (lane < 9) wpart[k - gbot][warp][lane] = mine;
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                    out8 = x;
+                }
+                if ((lane & 3) == 0) wpart[k - gbot][warp][lane >> 2] = out0;
+                if (lane == 1) wpart[k - gbot][warp][8] = out8;
             }
             __syncthreads();
-            for (int idx = threadIdx.x; idx < (gtop - gbot) * 9; idx += 256) {
+            for (int idx = threadIdx.x; idx < (gtop - gbot) * 9; idx += NT) {
                 const int q = idx / 9, c = idx - q * 9;
-                float acc = 0.f;
+                float acc = wpart[q][0][c];
 #pragma unroll
-                for (int w = 0; w < 8; ++w) acc += wpart[q][w][c];
+                for (int w2 = 1; w2 < NW; ++w2) acc += wpart[q][w2][c];
                 const uint32_t e = __float_as_uint(sC[gbot + q - lo].w);
-                part[(int64_t)c * K + e] = acc;
+                part[(int64_t)e * 9 + c] = acc;
             }
             __syncthreads();
         }
     }
 }
 
-// One warp per rank: sum of the Gaussian's partials over its tiles.
+// One warp per rank: sum of the Gaussian's partials over its tiles (entry-major
+// partials, nine floats per entry); the result goes to the Gaussian's compact
+// position j = perm[r].
 __global__ void __launch_bounds__(256) k_reduce_entries(
-    const float *__restrict__ part, int64_t K, const uint32_t *__restrict__ offsets,
+    const float *__restrict__ part, const uint32_t *__restrict__ offsets,
     const uint32_t *__restrict__ touched_r, const float4 *__restrict__ ranked,
-    const int32_t *__restrict__ tile_rmax, int tw_log2, int th_log2, int ntx, int64_t n,
-    float *__restrict__ g2d) {
+    const int32_t *__restrict__ tile_rmax, const uint32_t *__restrict__ perm, int tw_log2,
+    int th_log2, int ntx, int64_t n, float *__restrict__ g2d) {
     const int lane = threadIdx.x & 31;
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= n) return;
@@ -201,8 +262,9 @@ __global__ void __launch_bounds__(256) k_reduce_entries(
         for (uint32_t j = lane; j < cnt; j += 32) {
             const int t = (ty0 + (int)(j / (uint32_t)twid)) * ntx + tx0 + (int)(j % (uint32_t)twid);
             if ((int64_t)r <= (int64_t)tile_rmax[t]) {
+                const float *p = part + (int64_t)(off + j) * 9;
 #pragma unroll
-                for (int c = 0; c < 9; ++c) acc[c] += part[(int64_t)c * K + off + j];
+                for (int c = 0; c < 9; ++c) acc[c] += p[c];
             }
         }
     }
@@ -213,7 +275,11 @@ __global__ void __launch_bounds__(256) k_reduce_entries(
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         acc[c] = x;
     }
-    if (lane < 9) g2d[9 * r + lane] = acc[lane];
+    float mine = 0.f;
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+        if (lane == c) mine = acc[c];
+    if (lane < 9) g2d[9 * (int64_t)perm[r] + lane] = mine;
 }
 
 __device__ __forceinline__ float bf16f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
@@ -226,15 +292,15 @@ __device__ __forceinline__ float sh_coeff(const GaussSrc &G, int64_t i, int k, i
     return __fmul_rn(__half2float(__half(hr)), G.scales[11 + 3 * k + c]);
 }
 
+// Thread per selected Gaussian in index order (coalesced attribute reads and
+// gradient writes); g2d and touched are by compact position.
 __global__ void __launch_bounds__(128) k_preprocess_bwd(GaussSrc G, Selection sel, int64_t n_sel,
                                                         CamParams cam, RenderParams rp,
-                                                        const uint32_t *__restrict__ perm,
                                                         const float *__restrict__ g2d,
-                                                        const uint32_t *__restrict__ touched_r,
+                                                        const uint32_t *__restrict__ touched,
                                                         gc_grads out, float *__restrict__ mcontrib) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_sel) return;
-    const int64_t j = perm[r];
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_sel) return;
     const int64_t i = sel_global(sel, j);
     const int K = G.K;
     float mu[3], ls[3], q[4], logit;
@@ -251,11 +317,11 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(GaussSrc G, Selection se
         logit = __fmul_rn(bf16f(G.opacity_h[i]), G.scales[10]);
     }
     const int g = (G.group_q && G.group_id) ? G.group_id[i] : 0;
-    const bool visible = touched_r[r] != 0;
+    const bool visible = touched[j] != 0;
     float dmu[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
     float dlogit = 0.f, dgq[4] = {0.f, 0.f, 0.f, 0.f};
     if (visible) {
-        const float *d = g2d + 9 * r;
+        const float *d = g2d + 9 * j;
         float gq[4] = {1.f, 0.f, 0.f, 0.f}, gt[3] = {0.f, 0.f, 0.f};
         if (G.group_q) {
             for (int k = 0; k < 4; ++k) gq[k] = G.group_q[4 * g + k];
@@ -417,11 +483,11 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(GaussSrc G, Selection se
     }
 }
 
-constexpr int kGroupChunk = 1024;
+constexpr int kGroupChunk = 256;
 
-// Per chunk of 1024 compact positions, each thread sums the motion terms of the
+// Per chunk of 256 compact positions, each thread sums the motion terms of the
 // chunk's members of the groups it owns, in position order.
-__global__ void __launch_bounds__(256) k_group_partial(const float *__restrict__ mcontrib,
+__global__ void __launch_bounds__(128) k_group_partial(const float *__restrict__ mcontrib,
                                                        const int32_t *__restrict__ group_id,
                                                        Selection sel, int64_t n_sel, int n_groups,
                                                        float *__restrict__ partial) {
@@ -449,18 +515,28 @@ __global__ void __launch_bounds__(256) k_group_partial(const float *__restrict__
     }
 }
 
+// One thread per (group, component): the chunk partials summed in chunk order.
 __global__ void k_group_final(const float *__restrict__ partial, int n_chunks, int n_groups,
                               float *__restrict__ d_gq, float *__restrict__ d_gt) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_groups) return;
-    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int b = 0; b < n_chunks; ++b) {
-        const float *p = partial + ((int64_t)b * n_groups + g) * 7;
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_groups * 7) return;
+    const int g = id / 7, c = id - g * 7;
+    float acc = 0.f;
+    const int64_t stride = (int64_t)n_groups * 7;
+    int b = 0;
+    for (; b + 8 <= n_chunks; b += 8) {
+        float v[8];
 #pragma unroll
-        for (int c = 0; c < 7; ++c) acc[c] += p[c];
+        for (int u = 0; u < 8; ++u) v[u] = partial[(int64_t)(b + u) * stride + id];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
     }
-    if (d_gq) for (int c = 0; c < 4; ++c) d_gq[4 * g + c] = acc[c];
-    if (d_gt) for (int c = 0; c < 3; ++c) d_gt[3 * g + c] = acc[4 + c];
+    for (; b < n_chunks; ++b) acc += partial[(int64_t)b * stride + id];
+    if (c < 4) {
+        if (d_gq) d_gq[4 * g + c] = acc;
+    } else if (d_gt) {
+        d_gt[3 * g + (c - 4)] = acc;
+    }
 }
 
 }  // namespace
@@ -476,12 +552,13 @@ cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
     ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp.ntx, rp.tile_w_log2,       \
         rp.tile_h_log2, rp.bg[0], rp.bg[1], rp.bg[2], rp.membership, final_T, n_contrib,      \
         dL_dimg, part, K, tile_rmax
+    constexpr int kThreads = 256 / GC_BWD_PPT;
     if (rp.tile_w == 16 && rp.tile_h == 16)
-        k_blend_bwd<16, 16><<<tiles, 256, 0, st>>>(GC_BWD_ARGS);
+        k_blend_bwd<16, 16, GC_BWD_PPT><<<tiles, kThreads, 0, st>>>(GC_BWD_ARGS);
     else if (rp.tile_w == 8 && rp.tile_h == 32)
-        k_blend_bwd<8, 32><<<tiles, 256, 0, st>>>(GC_BWD_ARGS);
+        k_blend_bwd<8, 32, GC_BWD_PPT><<<tiles, kThreads, 0, st>>>(GC_BWD_ARGS);
     else if (rp.tile_w == 32 && rp.tile_h == 8)
-        k_blend_bwd<32, 8><<<tiles, 256, 0, st>>>(GC_BWD_ARGS);
+        k_blend_bwd<32, 8, GC_BWD_PPT><<<tiles, kThreads, 0, st>>>(GC_BWD_ARGS);
     else
         return cudaErrorInvalidValue;
 #undef GC_BWD_ARGS
@@ -489,26 +566,25 @@ cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_entries(const float *part, int64_t K, const uint32_t *offsets,
+cudaError_t launch_reduce_entries(const float *part, const uint32_t *offsets,
                                   const uint32_t *touched_r, const float4 *ranked,
-                                  const int32_t *tile_rmax, const RenderParams &rp, int64_t n,
-                                  float *g2d, cudaStream_t st) {
+                                  const int32_t *tile_rmax, const uint32_t *perm,
+                                  const RenderParams &rp, int64_t n, float *g2d, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int64_t threads = n * 32;
     k_reduce_entries<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-        part, K, offsets, touched_r, ranked, tile_rmax, rp.tile_w_log2, rp.tile_h_log2, rp.ntx, n, g2d);
+        part, offsets, touched_r, ranked, tile_rmax, perm, rp.tile_w_log2, rp.tile_h_log2, rp.ntx, n, g2d);
     note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_preprocess_bwd(const GaussSrc &g, const Selection &sel, int64_t n_sel,
-                                  const CamParams &cam, const RenderParams &rp,
-                                  const uint32_t *perm, const float *g2d,
-                                  const uint32_t *touched_r, gc_grads out, float *motion_contrib,
+                                  const CamParams &cam, const RenderParams &rp, const float *g2d,
+                                  const uint32_t *touched, gc_grads out, float *motion_contrib,
                                   cudaStream_t st) {
     if (n_sel <= 0) return cudaSuccess;
-    k_preprocess_bwd<<<(unsigned)((n_sel + 127) / 128), 128, 0, st>>>(g, sel, n_sel, cam, rp, perm, g2d,
-                                                                       touched_r, out, motion_contrib);
+    k_preprocess_bwd<<<(unsigned)((n_sel + 127) / 128), 128, 0, st>>>(g, sel, n_sel, cam, rp, g2d, touched,
+                                                                       out, motion_contrib);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -523,10 +599,10 @@ cudaError_t launch_group_reduce(const float *motion_contrib, const int32_t *grou
                                 float *d_group_q, float *d_group_t, cudaStream_t st) {
     const int chunks = (int)((n_sel + kGroupChunk - 1) / kGroupChunk);
     if (chunks > 0) {
-        k_group_partial<<<chunks, 256, 0, st>>>(motion_contrib, group_id, sel, n_sel, n_groups, partial);
+        k_group_partial<<<chunks, 128, 0, st>>>(motion_contrib, group_id, sel, n_sel, n_groups, partial);
         note_launches(1);
     }
-    k_group_final<<<(n_groups + 127) / 128, 128, 0, st>>>(partial, chunks, n_groups, d_group_q, d_group_t);
+    k_group_final<<<(n_groups * 7 + 127) / 128, 128, 0, st>>>(partial, chunks, n_groups, d_group_q, d_group_t);
     note_launches(1);
     return cudaGetLastError();
 }

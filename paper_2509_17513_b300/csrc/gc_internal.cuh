@@ -3,8 +3,9 @@
 // Layout of the per-Gaussian projected record (three float4, 48 bytes), written
 // by the preprocess kernel at the Gaussian's compact (selected) position and
 // gathered into depth-rank order before binning:
-//   r0 = { u, v, conic_a, conic_b }      conic = inverse 2D covariance [[a, b], [b, c]]
-//   r1 = { conic_c, opacity, red, green }
+//   r0 = { u, v, A, B }                  conic = inverse 2D covariance [[a, b], [b, c]],
+//   r1 = { C, opacity, red, green }      stored pre-scaled: A = -a log2e/2, B = -b log2e,
+//                                        C = -c log2e/2 (gc_blend.cuh)
 //   r2 = { blue, depth, rect_x, rect_y } rect_* = pixel footprint, int bits: lo16 = first,
 //                                        hi16 = last (inclusive)
 #pragma once
@@ -67,11 +68,23 @@ uint64_t launches_total();
 // ---- launchers (host) ----
 
 // Projection of the n_sel selected Gaussians.  Writes rec[3*j..3*j+2], depth
-// keys (kCulledKey when culled), values = j, and tiles touched per Gaussian.
+// keys (kCulledKey when culled), values = j, and tiles touched per Gaussian.  If
+// tile_diff != NULL (a zeroed (nty+1) x (ntx+1) int grid), every visible Gaussian
+// adds its tile rectangle to it as a 2D difference (four integer atomics), so that
+// its 2D prefix sum is the number of list entries of every tile.
 cudaError_t launch_preprocess(const GaussSrc &g, const Selection &sel, int64_t n_sel,
                               const CamParams &cam, const RenderParams &rp, float4 *rec,
                               uint32_t *depth_keys, uint32_t *depth_vals, uint32_t *touched,
-                              cudaStream_t st);
+                              int32_t *tile_diff, cudaStream_t st);
+
+// Tile ranges from the difference grid: 2D prefix sum -> per-tile counts ->
+// exclusive scan in tile order.  If the device key count exceeds `cap`, every
+// range is left empty (the overflow is reported separately).  Returns
+// cudaErrorNotSupported when the grid does not fit in shared memory.
+cudaError_t launch_tile_ranges_from_diff(const int32_t *tile_diff, int ntx, int nty,
+                                         const uint32_t *total_dev, uint32_t cap, uint2 *ranges,
+                                         cudaStream_t st);
+bool tile_diff_fits(int ntx, int nty);
 
 // rank r -> compact j = perm[r]: ranked[r] = rec[j], touched_r[r] = touched[j]
 cudaError_t launch_rank_gather(const uint32_t *perm, const float4 *rec, const uint32_t *touched,
@@ -86,10 +99,13 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
 // Stable LSD radix sort of (key, value) pairs on key bits [0, end_bit).
 // keys[0]/vals[0] hold the input; the sorted output ends in buffer *out_buf.
 // n_dev: optional device count (<= n_max) read by the kernels; n_max sizes the grid.
+// keys_out = false: the last pass writes only the values (the sorted keys are not kept).
+// Buffers must hold n_max rounded up to 4 elements (tiles are copied in 16-byte units).
+// A bounded wait that runs out sets kErrTimeout in *err (device word).
 size_t radix_scratch_words(int64_t n_max);
 cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
                              const uint32_t *n_dev, int end_bit, uint32_t *scratch, int *out_buf,
-                             cudaStream_t st);
+                             cudaStream_t st, uint32_t *err, bool keys_out = true);
 
 // Emit (tile key, rank) for every tile of every visible Gaussian, in rank order.
 // Entries at positions >= cap are dropped (fixed-capacity mode reports the overflow).
@@ -116,28 +132,29 @@ cudaError_t launch_entries_to_global(const uint32_t *sorted_vals, const uint32_t
 // ---- backward ----
 
 // Reverse compositing per tile; writes 9 partial gradients per (tile, Gaussian)
-// entry at the entry's emit position offsets[r] + (index of the tile in the
-// Gaussian's tile rectangle): planes part[c * K + e], c = du, dv, da, db, dc,
-// dopacity, dr, dg, db.  Entries behind every pixel's last blended one are not
-// written; tile_rmax[t] = largest rank that may have contributed to tile t (-1: none).
+// entry at the entry's emit position e = offsets[r] + (index of the tile in the
+// Gaussian's tile rectangle): part[9 * e + c], c = du, dv, da, db, dc, dopacity,
+// dr, dg, db.  Entries behind every pixel's last blended one are not written;
+// tile_rmax[t] = largest rank that may have contributed to tile t (-1: none).
 cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
                              const float4 *ranked, const uint32_t *offsets, const CamParams &cam,
                              const RenderParams &rp, const float *final_T,
                              const uint32_t *n_contrib, const float *dL_dimg, float *part,
                              int64_t K, int32_t *tile_rmax, cudaStream_t st);
 
-// Per-rank sum of the partials over the Gaussian's entries -> g2d[9 * r + c].
-cudaError_t launch_reduce_entries(const float *part, int64_t K, const uint32_t *offsets,
+// Per-rank sum of the partials over the Gaussian's entries -> g2d[9 * j + c] at the
+// Gaussian's compact position j = perm[r].
+cudaError_t launch_reduce_entries(const float *part, const uint32_t *offsets,
                                   const uint32_t *touched_r, const float4 *ranked,
-                                  const int32_t *tile_rmax, const RenderParams &rp, int64_t n,
-                                  float *g2d, cudaStream_t st);
+                                  const int32_t *tile_rmax, const uint32_t *perm,
+                                  const RenderParams &rp, int64_t n, float *g2d, cudaStream_t st);
 
-// Chain rule from the 2D gradients (by rank) to the attributes (by global index)
-// and to per-Gaussian motion terms (7 floats per compact position: dq_g[4], dt_g[3]).
+// Chain rule from the 2D gradients (by compact position) to the attributes (by
+// global index) and to per-Gaussian motion terms (7 floats per compact position:
+// dq_g[4], dt_g[3]).  touched[j] != 0 marks visible Gaussians.
 cudaError_t launch_preprocess_bwd(const GaussSrc &g, const Selection &sel, int64_t n_sel,
-                                  const CamParams &cam, const RenderParams &rp,
-                                  const uint32_t *perm, const float *g2d,
-                                  const uint32_t *touched_r, gc_grads out, float *motion_contrib,
+                                  const CamParams &cam, const RenderParams &rp, const float *g2d,
+                                  const uint32_t *touched, gc_grads out, float *motion_contrib,
                                   cudaStream_t st);
 
 // Deterministic per-group sums of the motion terms.  `partial` needs

@@ -10,7 +10,7 @@
 // grow-only scratch) nor allocate after start-up.  This entry point serves them
 // with a fixed, stated maximum problem size.
 //
-// The scratch is g_noalloc_scratch below (kScratchBytes, about 22 MiB).  Every GPU
+// The scratch is g_noalloc_scratch below (kScratchBytes, about 22.5 MiB).  Every GPU
 // that loads this module holds it until the process exits.  In host code the
 // array's name is only a host-side stand-in, so the device address is looked up
 // once per device with cudaGetSymbolAddress (with that device current) and
@@ -58,8 +58,8 @@ constexpr size_t kOffFinalT = kOffRanges + al(kMaxTiles * 8);
 constexpr size_t kOffNContrib = kOffFinalT + al(kMaxPixels * 4);
 constexpr size_t kOffWords = kOffNContrib + al(kMaxPixels * 4);
 constexpr size_t kOffSortScratch = kOffWords + 256;
-// radix histograms (256 per 4096-key block) + their scan partials, with slack
-constexpr size_t kSortScratchBytes = al((256 * ((kMaxKeys + 4095) / 4096) + 1024) * 4);
+// radix histograms (256 per block of at least 2048 keys) + their scan partials, with slack
+constexpr size_t kSortScratchBytes = al((256 * ((kMaxKeys + 2047) / 2048) + 1024) * 4);
 constexpr size_t kScratchBytes = kOffSortScratch + kSortScratchBytes;
 
 }  // namespace
@@ -241,14 +241,16 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
     uint32_t *words = reinterpret_cast<uint32_t *>(base + kOffWords);
     uint32_t *sort_scratch = reinterpret_cast<uint32_t *>(base + kOffSortScratch);
 
-    // the tile ranges must start at zero: the array keeps the previous call's values
+    // the tile ranges and the error word must start at zero: the array keeps the previous
+    // call's values
     NA_CUDA(cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 8, s));
+    NA_CUDA(cudaMemsetAsync(words, 0, 8, s));
     int64_t K = 0;
     int tile_buf = 0;
     if (n_sel > 0) {
         int depth_buf = 0;
-        NA_CUDA(gc::launch_preprocess(src, sel, n_sel, cp, rp, rec, dk[0], dv[0], touched, s));
-        NA_CUDA(gc::radix_sort_pairs(dk, dv, n_sel, nullptr, 32, sort_scratch, &depth_buf, s));
+        NA_CUDA(gc::launch_preprocess(src, sel, n_sel, cp, rp, rec, dk[0], dv[0], touched, nullptr, s));
+        NA_CUDA(gc::radix_sort_pairs(dk, dv, n_sel, nullptr, 32, sort_scratch, &depth_buf, s, words + 1));
         NA_CUDA(gc::launch_rank_gather(dv[depth_buf], rec, touched, n_sel, ranked, touched_r, s));
         NA_CUDA(gc::launch_exclusive_scan(touched_r, offsets, n_sel, words, sort_scratch, s));
         uint32_t k_host = 0;  // stack variable: no host allocation
@@ -262,7 +264,7 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
         if (K > 0) {
             NA_CUDA(gc::launch_emit(ranked, offsets, touched_r, n_sel, rp, tk[0], tv[0], (uint32_t)K, s));
             NA_CUDA(gc::radix_sort_pairs(tk, tv, K, nullptr, key_bits(n_tiles - 1), sort_scratch,
-                                         &tile_buf, s));
+                                         &tile_buf, s, words + 1));
             NA_CUDA(gc::launch_tile_ranges(tk[tile_buf], nullptr, K, ranges, s));
         }
     }

@@ -9,6 +9,7 @@
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
+#include "gc_blend.cuh"
 #include "gc_internal.cuh"
 #include "gc_sh.cuh"
 
@@ -68,7 +69,8 @@ __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, i
                                                     float4 *__restrict__ rec,
                                                     uint32_t *__restrict__ depth_keys,
                                                     uint32_t *__restrict__ depth_vals,
-                                                    uint32_t *__restrict__ touched) {
+                                                    uint32_t *__restrict__ touched,
+                                                    int32_t *__restrict__ tile_diff) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_sel) return;
     const int64_t i = sel_global(sel, j);
@@ -194,6 +196,13 @@ __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, i
         const int ty0 = y0 >> rp.tile_h_log2, ty1 = y1 >> rp.tile_h_log2;
         ntouch = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
         key = __float_as_uint(cz);
+        if (tile_diff) {
+            const int gw = rp.ntx + 1;
+            atomicAdd(&tile_diff[ty0 * gw + tx0], 1);
+            atomicAdd(&tile_diff[ty0 * gw + tx1 + 1], -1);
+            atomicAdd(&tile_diff[(ty1 + 1) * gw + tx0], -1);
+            atomicAdd(&tile_diff[(ty1 + 1) * gw + tx1 + 1], 1);
+        }
 
         // colour (free FP32 arithmetic)
         float dxv = m0 - cam.campos[0], dyv = m1 - cam.campos[1], dzv = m2 - cam.campos[2];
@@ -208,8 +217,9 @@ __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, i
             rgb[c] = fmaxf(acc + 0.5f, 0.f);
         }
         const float op = 1.0f / (1.0f + expf(-A.logit));
-        r0 = make_float4(u, v, ia, ib);
-        r1 = make_float4(ic, op, rgb[0], rgb[1]);
+        // conic stored pre-scaled for the blend's base-2 exponent (see gc_blend.cuh)
+        r0 = make_float4(u, v, __fmul_rn(ia, -0.5f * kLog2e), __fmul_rn(ib, -kLog2e));
+        r1 = make_float4(__fmul_rn(ic, -0.5f * kLog2e), op, rgb[0], rgb[1]);
         r2 = make_float4(rgb[2], cz, __int_as_float(x0 | (x1 << 16)), __int_as_float(y0 | (y1 << 16)));
     } while (0);
 
@@ -239,11 +249,11 @@ __global__ void __launch_bounds__(256) k_rank_gather(const uint32_t *__restrict_
 cudaError_t launch_preprocess(const GaussSrc &g, const Selection &sel, int64_t n_sel,
                               const CamParams &cam, const RenderParams &rp, float4 *rec,
                               uint32_t *depth_keys, uint32_t *depth_vals, uint32_t *touched,
-                              cudaStream_t st) {
+                              int32_t *tile_diff, cudaStream_t st) {
     if (n_sel <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((n_sel + 255) / 256);
     k_preprocess<<<blocks, 256, 0, st>>>(g, sel, n_sel, cam, rp, rec, depth_keys, depth_vals,
-                                         touched);
+                                         touched, tile_diff);
     note_launches(1);
     return cudaGetLastError();
 }

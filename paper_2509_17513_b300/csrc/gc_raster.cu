@@ -89,97 +89,208 @@ __global__ void k_tile_ranges(const uint32_t *__restrict__ keys, const uint32_t 
     }
 }
 
-// Front-to-back compositing (Eq. 2), one CTA per tile of TW x TH = 256 pixels.
-// Each batch of up to 256 list entries is staged in shared memory (one entry
-// per thread, gathered from the depth-ranked records), then every pixel walks
-// the batch.  A pixel stops when blending the next Gaussian would take its
-// transmittance below 1e-4; the CTA leaves as soon as all its pixels stopped.
-template <int TW, int TH>
-__global__ void __launch_bounds__(256) k_blend_fwd(
+// Per-pixel front-to-back state.
+struct FwdPix {
+    float T, C0, C1, C2;
+    uint32_t last, nb, walked;
+    bool done;
+};
+
+// One compositing step of Eq. 2 for one pixel and the staged Gaussian (a, bb, blue).
+__device__ __forceinline__ void fwd_step(FwdPix &P, float pcx, float pcy, const float4 &a,
+                                         const float4 &bb, float blue, uint32_t idx) {
+    const float dx = pcx - a.x, dy = pcy - a.y;
+    const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
+    if (p2 > 0.f) return;
+    float G;
+    const float alpha = fminf(kAlphaMax, blend_raw_alpha(bb.y, p2, G));
+    if (alpha < kAlphaMin) return;
+    const float Tn = P.T * (1.f - alpha);
+    if (Tn < kTStop) {
+        P.done = true;
+        P.walked = idx + 1;
+        return;
+    }
+    const float w = alpha * P.T;
+    P.C0 = fmaf(bb.z, w, P.C0);
+    P.C1 = fmaf(bb.w, w, P.C1);
+    P.C2 = fmaf(blue, w, P.C2);
+    P.T = Tn;
+    P.last = idx + 1;
+    ++P.nb;
+}
+
+#ifndef GC_FWD_PPT
+#define GC_FWD_PPT 1  // pixels per thread in the forward blend (1 measured fastest on B300)
+#endif
+
+// Front-to-back compositing (Eq. 2), one CTA per tile of TW x TH = 256 pixels with
+// 256 / PPT threads; thread t owns the PPT vertically adjacent pixels
+// (t % TW, PPT * (t / TW) + i), so each staged Gaussian is read from shared memory
+// once per PPT pixels.  Batches of up to 256 list entries are staged in shared
+// memory (gathered from the depth-ranked records); a pixel stops when blending the
+// next Gaussian would take its transmittance below 1e-4, the CTA as soon as all its
+// pixels did.
+template <int TW, int TH, int PPT>
+__global__ void __launch_bounds__(256 / PPT) k_blend_fwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, int W, int H, int ntx, float bg0, float bg1, float bg2,
     int membership, float *__restrict__ image, float *__restrict__ final_T,
     uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ n_blended,
     uint32_t *__restrict__ n_walked) {
     static_assert(TW * TH == 256, "tile must hold 256 pixels");
-    __shared__ float4 sA[256];  // u, v, conic a, conic b
-    __shared__ float4 sB[256];  // conic c, opacity, red, green
+    constexpr int NT = 256 / PPT;
+    __shared__ float4 sA[256];  // u, v, A, B
+    __shared__ float4 sB[256];  // C, opacity, red, green
     __shared__ float4 sC[256];  // blue, column mask, row mask, -
 
     const int tile = blockIdx.x;
     const int tx = tile % ntx, ty = tile / ntx;
-    const int lx = threadIdx.x % TW, ly = threadIdx.x / TW;
-    const int px = tx * TW + lx, py = ty * TH + ly;
-    const bool inside = px < W && py < H;
-    const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
-    const uint32_t xbit = 1u << lx, ybit = 1u << ly;
+    const int lx = threadIdx.x % TW, lyb = PPT * (threadIdx.x / TW);
+    const int px = tx * TW + lx;
+    const float pcx = (float)px + 0.5f;
+    const uint32_t xbit = 1u << lx;
     const uint2 range = ranges[tile];
     const int n = (int)(range.y - range.x);
 
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    bool done = !inside;
-    uint32_t last = 0, nb = 0, walked = 0;
+    FwdPix P[PPT];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) P[i] = {1.f, 0.f, 0.f, 0.f, 0u, 0u, 0u, !(px < W && ty * TH + lyb + i < H)};
+    auto all_done = [&]() {
+        bool d = true;
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) d = d && P[i].done;
+        return d;
+    };
 
     for (int b = 0; b < n; b += 256) {
-        if (__syncthreads_count(done) == 256) break;
-        const int idx = b + (int)threadIdx.x;
-        if (idx < n) {
-            const uint32_t r = sorted_vals[range.x + idx];
-            const float4 a = ranked[3 * (size_t)r];
-            const float4 bb = ranked[3 * (size_t)r + 1];
-            const float4 c = ranked[3 * (size_t)r + 2];
-            uint32_t cm = 0xffffffffu, rm = 0xffffffffu;
-            if (membership == GC_MEMBER_PIXEL) {
-                int x0, x1, y0, y1;
-                unpack_rect(c, x0, x1, y0, y1);
-                const int lx0 = max(x0 - tx * TW, 0), lx1 = min(x1 - tx * TW, TW - 1);
-                const int ly0 = max(y0 - ty * TH, 0), ly1 = min(y1 - ty * TH, TH - 1);
-                cm = (lx1 >= lx0) ? ((0xffffffffu >> (31 - lx1)) & (0xffffffffu << lx0)) : 0u;
-                rm = (ly1 >= ly0) ? ((0xffffffffu >> (31 - ly1)) & (0xffffffffu << ly0)) : 0u;
+        if (__syncthreads_count(all_done()) == NT) break;
+#pragma unroll
+        for (int h = 0; h < PPT; ++h) {
+            const int slot = (int)threadIdx.x + NT * h;
+            const int idx = b + slot;
+            if (idx < n) {
+                const uint32_t r = sorted_vals[range.x + idx];
+                const float4 a = ranked[3 * (size_t)r];
+                const float4 bb = ranked[3 * (size_t)r + 1];
+                const float4 c = ranked[3 * (size_t)r + 2];
+                uint32_t cm = 0xffffffffu, rm = 0xffffffffu;
+                if (membership == GC_MEMBER_PIXEL) {
+                    int x0, x1, y0, y1;
+                    unpack_rect(c, x0, x1, y0, y1);
+                    const int lx0 = max(x0 - tx * TW, 0), lx1 = min(x1 - tx * TW, TW - 1);
+                    const int ly0r = max(y0 - ty * TH, 0), ly1r = min(y1 - ty * TH, TH - 1);
+                    cm = (lx1 >= lx0) ? ((0xffffffffu >> (31 - lx1)) & (0xffffffffu << lx0)) : 0u;
+                    rm = (ly1r >= ly0r) ? ((0xffffffffu >> (31 - ly1r)) & (0xffffffffu << ly0r)) : 0u;
+                }
+                sA[slot] = a;
+                sB[slot] = bb;
+                sC[slot] = make_float4(c.x, __uint_as_float(cm), __uint_as_float(rm), 0.f);
             }
-            sA[threadIdx.x] = a;
-            sB[threadIdx.x] = bb;
-            sC[threadIdx.x] = make_float4(c.x, __uint_as_float(cm), __uint_as_float(rm), 0.f);
         }
         __syncthreads();
         const int cnt = min(256, n - b);
-        if (!done) {
-            for (int k = 0; k < cnt; ++k) {
-                const float4 c = sC[k];
-                if (!(__float_as_uint(c.y) & xbit) || !(__float_as_uint(c.z) & ybit)) continue;
-                const float4 a = sA[k];
-                const float4 bb = sB[k];
-                const float dx = pcx - a.x, dy = pcy - a.y;
-                const float power = blend_power(a.z, a.w, bb.x, dx, dy);
-                if (power > 0.f) continue;
-                float G;
-                const float alpha = fminf(kAlphaMax, blend_raw_alpha(bb.y, power, G));
-                if (alpha < kAlphaMin) continue;
-                const float Tn = T * (1.f - alpha);
-                if (Tn < kTStop) {
-                    done = true;
-                    walked = (uint32_t)(b + k + 1);
-                    break;
-                }
-                const float w = alpha * T;
-                C0 = fmaf(bb.z, w, C0);
-                C1 = fmaf(bb.w, w, C1);
-                C2 = fmaf(c.x, w, C2);
-                T = Tn;
-                last = (uint32_t)(b + k + 1);
-                ++nb;
-            }
+        for (int k = 0; k < cnt; ++k) {
+            if (all_done()) break;
+            const float4 c = sC[k];
+            if (!(__float_as_uint(c.y) & xbit)) continue;
+            const uint32_t rm = __float_as_uint(c.z) >> lyb;  // bit i: row lyb + i of the tile
+            bool any = false;
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) any = any || (!P[i].done && ((rm >> i) & 1u));
+            if (!any) continue;
+            const float4 a = sA[k];
+            const float4 bb = sB[k];
+            const uint32_t idx = (uint32_t)(b + k);
+#pragma unroll
+            for (int i = 0; i < PPT; ++i)
+                if (!P[i].done && ((rm >> i) & 1u))
+                    fwd_step(P[i], pcx, (float)(ty * TH + lyb + i) + 0.5f, a, bb, c.x, idx);
         }
     }
-    if (inside) {
-        const size_t hw = (size_t)W * H, p = (size_t)py * W + px;
-        image[p] = fmaf(T, bg0, C0);
-        image[hw + p] = fmaf(T, bg1, C1);
-        image[2 * hw + p] = fmaf(T, bg2, C2);
-        final_T[p] = T;
-        n_contrib[p] = last;
-        if (n_blended) n_blended[p] = nb;
-        if (n_walked) n_walked[p] = done ? walked : (uint32_t)n;
+    const size_t hw = (size_t)W * H;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const int py = ty * TH + lyb + i;
+        if (px < W && py < H) {
+            const size_t p = (size_t)py * W + px;
+            image[p] = fmaf(P[i].T, bg0, P[i].C0);
+            image[hw + p] = fmaf(P[i].T, bg1, P[i].C1);
+            image[2 * hw + p] = fmaf(P[i].T, bg2, P[i].C2);
+            final_T[p] = P[i].T;
+            n_contrib[p] = P[i].last;
+            if (n_blended) n_blended[p] = P[i].nb;
+            if (n_walked) n_walked[p] = P[i].done ? P[i].walked : (uint32_t)n;
+        }
+    }
+}
+
+// Single CTA: 2D inclusive prefix of the tile difference grid (rows, then columns)
+// gives the entry count of every tile; an exclusive scan in tile order gives the
+// ranges of the tile-sorted list.
+__global__ void __launch_bounds__(1024) k_tile_ranges_from_diff(const int32_t *__restrict__ diff,
+                                                                int ntx, int nty,
+                                                                const uint32_t *total_dev,
+                                                                uint32_t cap,
+                                                                uint2 *__restrict__ ranges) {
+    extern __shared__ int32_t g[];
+    __shared__ uint32_t ws[33];
+    const int gw = ntx + 1, gh = nty + 1;
+    const int cells = gw * gh;
+    for (int k = threadIdx.x; k < cells; k += blockDim.x) g[k] = diff[k];
+    __syncthreads();
+    for (int r = threadIdx.x; r < gh; r += blockDim.x) {
+        int acc = 0;
+        for (int c = 0; c < gw; ++c) {
+            acc += g[r * gw + c];
+            g[r * gw + c] = acc;
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < gw; c += blockDim.x) {
+        int acc = 0;
+        for (int r = 0; r < gh; ++r) {
+            acc += g[r * gw + c];
+            g[r * gw + c] = acc;
+        }
+    }
+    __syncthreads();
+    const bool overflow = total_dev && (*total_dev > cap);
+    const int T = ntx * nty;
+    const int per = (T + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int start = (int)threadIdx.x * per;
+    uint32_t s = 0;
+    for (int q = 0; q < per; ++q) {
+        const int t = start + q;
+        if (t < T) s += (uint32_t)g[(t / ntx) * gw + (t % ntx)];
+    }
+    // block exclusive scan of the per-thread sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = ws[lane];
+        uint32_t wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        ws[lane] = wi - w;
+    }
+    __syncthreads();
+    uint32_t run = ws[warp] + inc - s;
+    for (int q = 0; q < per; ++q) {
+        const int t = start + q;
+        if (t < T) {
+            const uint32_t c = (uint32_t)g[(t / ntx) * gw + (t % ntx)];
+            ranges[t] = overflow ? make_uint2(0u, 0u) : make_uint2(run, run + c);
+            run += c;
+        }
     }
 }
 
@@ -214,6 +325,25 @@ cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uin
     return cudaGetLastError();
 }
 
+bool tile_diff_fits(int ntx, int nty) {
+    return (size_t)(ntx + 1) * (size_t)(nty + 1) * 4 <= 200 * 1024;
+}
+
+cudaError_t launch_tile_ranges_from_diff(const int32_t *tile_diff, int ntx, int nty,
+                                         const uint32_t *total_dev, uint32_t cap, uint2 *ranges,
+                                         cudaStream_t st) {
+    if (!tile_diff_fits(ntx, nty)) return cudaErrorNotSupported;
+    const size_t smem = (size_t)(ntx + 1) * (nty + 1) * 4;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_ranges_from_diff,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_tile_ranges_from_diff<<<1, 1024, smem, st>>>(tile_diff, ntx, nty, total_dev, cap, ranges);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tile_ranges(const uint32_t *keys, const uint32_t *n_dev, int64_t n_max,
                                uint2 *ranges, cudaStream_t st) {
     if (n_max <= 0) return cudaSuccess;
@@ -233,12 +363,13 @@ cudaError_t launch_blend_fwd(const uint2 *ranges, const uint32_t *sorted_vals,
 #define GC_BLEND_ARGS                                                                          \
     ranges, sorted_vals, ranked, cam.width, cam.height, rp.ntx, rp.bg[0], rp.bg[1], rp.bg[2], \
         rp.membership, image, final_T, n_contrib, n_blended, n_walked
+    constexpr int kThreads = 256 / GC_FWD_PPT;
     if (rp.tile_w == 16 && rp.tile_h == 16)
-        k_blend_fwd<16, 16><<<tiles, 256, 0, st>>>(GC_BLEND_ARGS);
+        k_blend_fwd<16, 16, GC_FWD_PPT><<<tiles, kThreads, 0, st>>>(GC_BLEND_ARGS);
     else if (rp.tile_w == 8 && rp.tile_h == 32)
-        k_blend_fwd<8, 32><<<tiles, 256, 0, st>>>(GC_BLEND_ARGS);
+        k_blend_fwd<8, 32, GC_FWD_PPT><<<tiles, kThreads, 0, st>>>(GC_BLEND_ARGS);
     else if (rp.tile_w == 32 && rp.tile_h == 8)
-        k_blend_fwd<32, 8><<<tiles, 256, 0, st>>>(GC_BLEND_ARGS);
+        k_blend_fwd<32, 8, GC_FWD_PPT><<<tiles, kThreads, 0, st>>>(GC_BLEND_ARGS);
     else
         return cudaErrorInvalidValue;
     note_launches(1);

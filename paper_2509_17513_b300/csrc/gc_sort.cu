@@ -5,11 +5,12 @@
 // launches) and each radix digit is histogram -> scan -> scatter.  So no kernel
 // can hang on a missing predecessor, and every result is deterministic.
 //
-// Scatter stability: each warp owns a contiguous 512-key segment of its CTA's
-// 4096-key tile and ranks its keys row by row with __match_any_sync, so the
-// global order of equal digits is (CTA, warp, row, lane) = input order.
+// Scatter stability: each warp owns a contiguous segment of its CTA's tile
+// (kSortItems rows of 32 keys) and ranks its keys row by row (ballot multisplit),
+// so the global order of equal digits is (CTA, warp, row, lane) = input order.
 #include <cuda_runtime.h>
 
+#include "gc_async.cuh"
 #include "gc_internal.cuh"
 
 namespace gc {
@@ -17,12 +18,14 @@ namespace gc {
 namespace {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanRows = 16;
-constexpr int kScanChunk = kScanThreads * kScanRows;  // 4096
+constexpr int kScanChunk = kScanThreads * 16;  // 4096, 16 contiguous elements per thread
 
+#ifndef GC_SORT_ITEMS
+#define GC_SORT_ITEMS 8  // keys per thread in a radix tile
+#endif
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096
+constexpr int kSortItems = GC_SORT_ITEMS;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
 constexpr int kWarps = kSortThreads / 32;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -63,17 +66,46 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *w
     return res;
 }
 
+// Thread-contiguous chunk layout: thread t of a chunk owns elements
+// [16 t, 16 t + 16), read with 16-byte loads when the chunk is full and aligned.
+__device__ __forceinline__ void load16(const uint32_t *in, int64_t start, int64_t n, bool vec,
+                                       uint32_t *x) {
+    if (vec && start + 16 <= n) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(in + start);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 v = p[q];
+            x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) x[q] = (start + q < n) ? in[start + q] : 0u;
+    }
+}
+
+__device__ __forceinline__ void store16(uint32_t *out, int64_t start, int64_t n, bool vec,
+                                        const uint32_t *x) {
+    if (vec && start + 16 <= n) {
+        uint4 *p = reinterpret_cast<uint4 *>(out + start);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) p[q] = make_uint4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (start + q < n) out[start + q] = x[q];
+    }
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ in,
-                                                              int64_t n,
+                                                              int64_t n, bool vec,
                                                               uint32_t *__restrict__ partials) {
     __shared__ uint32_t red[kScanThreads / 32];
-    const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    const int64_t start = (int64_t)blockIdx.x * kScanChunk + 16 * (int64_t)threadIdx.x;
+    uint32_t x[16];
+    load16(in, start, n, vec, x);
     uint32_t s = 0;
-#pragma unroll 4
-    for (int r = 0; r < kScanRows; ++r) {
-        int64_t i = base + (int64_t)r * kScanThreads + threadIdx.x;
-        if (i < n) s += in[i];
-    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s += x[q];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -102,19 +134,53 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *partials, int6
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *in, uint32_t *out,
-                                                            int64_t n,
+                                                            int64_t n, bool vec,
                                                             const uint32_t *__restrict__ partials) {
     __shared__ uint32_t ws[33];
-    const int64_t base = (int64_t)blockIdx.x * kScanChunk;
-    uint32_t carry = partials[blockIdx.x];
-    for (int r = 0; r < kScanRows; ++r) {
-        int64_t i = base + (int64_t)r * kScanThreads + threadIdx.x;
-        uint32_t x = (i < n) ? in[i] : 0u;
+    const int64_t start = (int64_t)blockIdx.x * kScanChunk + 16 * (int64_t)threadIdx.x;
+    uint32_t x[16];
+    load16(in, start, n, vec, x);
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const uint32_t v = x[q];
+        x[q] = s;
+        s += v;
+    }
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan<kScanThreads>(s, ws, &tot) + partials[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] += ex;
+    store16(out, start, n, vec, x);
+}
+
+// Whole scan in one CTA of 1024 threads for n <= kSmallScan: chunks of 16384
+// elements, 16 contiguous per thread (16-byte loads), one block scan per chunk.
+constexpr int64_t kSmallScan = 1024 * 16 * 8;
+
+__global__ void __launch_bounds__(1024) k_scan_single(const uint32_t *in, uint32_t *out, int64_t n,
+                                                      bool vec, uint32_t *total) {
+    __shared__ uint32_t ws[33];
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < n; base += 16 * 1024) {
+        const int64_t start = base + 16 * (int64_t)threadIdx.x;
+        uint32_t x[16];
+        load16(in, start, n, vec, x);
+        uint32_t s = 0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const uint32_t v = x[q];
+            x[q] = s;
+            s += v;
+        }
         uint32_t tot;
-        uint32_t ex = block_exclusive_scan<kScanThreads>(x, ws, &tot);
-        if (i < n) out[i] = carry + ex;
+        const uint32_t ex = block_exclusive_scan<1024>(s, ws, &tot) + carry;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) x[q] += ex;
+        store16(out, start, n, vec, x);
         carry += tot;
     }
+    if (threadIdx.x == 0 && total) *total = carry;
 }
 
 __device__ __forceinline__ int64_t device_count(const uint32_t *n_dev, int64_t n_max) {
@@ -123,99 +189,172 @@ __device__ __forceinline__ int64_t device_count(const uint32_t *n_dev, int64_t n
     return n < n_max ? n : n_max;
 }
 
-// Per-CTA digit histogram, digit-major: counts[d * nblocks + b].
+// Peers of this lane: the lanes of the warp whose digit equals this lane's, among the
+// lanes in `valid` (warp multisplit by one ballot per digit bit).
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, int bits, uint32_t valid) {
+    uint32_t peers = valid;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if (b < bits) {
+            const uint32_t bit = (d >> b) & 1u;
+            const uint32_t t = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? t : ~t;
+        }
+    }
+    return peers;
+}
+
+// Per-CTA digit histogram, digit-major: counts[d * nblocks + b].  Keys are read with
+// 16-byte loads when the tile is full; each warp counts into its own shared row.
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__restrict__ keys,
                                                              const uint32_t *n_dev, int64_t n_max,
                                                              int shift, uint32_t mask,
                                                              uint32_t *__restrict__ counts,
                                                              int nblocks) {
-    __shared__ uint32_t hist[256];
-    hist[threadIdx.x] = 0;
+    __shared__ uint32_t wh[kWarps][256];
+    const int warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0;
     __syncthreads();
     const int64_t n = device_count(n_dev, n_max);
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    const uint32_t lt = lanemask_lt();
-#pragma unroll 4
-    for (int r = 0; r < kSortItems; ++r) {
-        int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-        bool valid = i < n;
-        uint32_t d = valid ? ((keys[i] >> shift) & mask) : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (valid && (peers & lt) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+    if (base + kSortTile <= n) {
+        const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + base);
+#pragma unroll
+        for (int r = 0; r < kSortItems / 4; ++r) {
+            const uint4 q = k4[r * kSortThreads + threadIdx.x];
+            atomicAdd(&wh[warp][(q.x >> shift) & mask], 1u);
+            atomicAdd(&wh[warp][(q.y >> shift) & mask], 1u);
+            atomicAdd(&wh[warp][(q.z >> shift) & mask], 1u);
+            atomicAdd(&wh[warp][(q.w >> shift) & mask], 1u);
+        }
+    } else {
+        for (int r = 0; r < kSortItems; ++r) {
+            const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+            if (i < n) atomicAdd(&wh[warp][(keys[i] >> shift) & mask], 1u);
+        }
     }
     __syncthreads();
-    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = hist[threadIdx.x];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) tot += wh[w][threadIdx.x];
+    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = tot;
 }
 
+// Stable scatter, persistent: each CTA walks tiles t = blockIdx.x, + gridDim.x, ...
+// A tile's keys and values arrive in shared memory by two bulk asynchronous copies
+// (cp.async.bulk, completed on an mbarrier), double-buffered so the next tile streams
+// in while this one is ranked.  Every warp ranks its contiguous 256-key segment row by
+// row (ballot multisplit), the CTA turns warp counts into offsets, places keys and
+// values digit-sorted back into the tile's buffer and writes them out in contiguous
+// runs.  keys_out may be NULL (last pass of a sort whose keys are not kept).
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *n_dev,
-    int64_t n_max, int shift, uint32_t mask, const uint32_t *__restrict__ scanned, int nblocks) {
+    int64_t n_max, int shift, uint32_t mask, const uint32_t *__restrict__ scanned, int nblocks,
+    uint32_t *err) {
+    __shared__ __align__(128) uint32_t sk[2][kSortTile];
+    __shared__ __align__(128) uint32_t sv[2][kSortTile];
     __shared__ uint32_t wcnt[kWarps][256];
     __shared__ uint32_t dstart[256];
     __shared__ uint32_t gbase[256];
     __shared__ uint32_t ws[33];
-    __shared__ uint32_t skeys[kSortTile];
-    __shared__ uint32_t svals[kSortTile];
+    __shared__ __align__(8) uint64_t bar[2];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n = device_count(n_dev, n_max);
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    if (base >= n) return;
-    const int nvalid = (int)((n - base) < kSortTile ? (n - base) : kSortTile);
-    for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wcnt[0][0])[k] = 0;
-    __syncthreads();
-
+    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    const int bits = __popc(mask);
     const uint32_t lt = lanemask_lt();
-    uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
-    const int64_t wbase = base + (int64_t)warp * (32 * kSortItems);
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        int64_t i = wbase + r * 32 + lane;
-        bool valid = i < n;
-        key[r] = valid ? keys_in[i] : 0u;
-        val[r] = valid ? vals_in[i] : 0u;
-        uint32_t d = valid ? ((key[r] >> shift) & mask) : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = valid ? wcnt[warp][d] : 0u;
-        __syncwarp();
-        if (valid && (peers & lt) == 0) wcnt[warp][d] = before + (uint32_t)__popc(peers);
-        __syncwarp();
-        loc[r] = before + (uint32_t)__popc(peers & lt);
+    if ((int)blockIdx.x >= ntiles) return;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
     }
     __syncthreads();
-    {
-        const int d = threadIdx.x;
-        uint32_t s = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            uint32_t c = wcnt[w][d];
-            wcnt[w][d] = s;
-            s += c;
+    auto issue = [&](int t, int stage) {  // one thread
+        const int64_t base = (int64_t)t * kSortTile;
+        const int nv = (int)((n - base) < kSortTile ? (n - base) : kSortTile);
+        const uint32_t bytes = (uint32_t)((nv * 4 + 15) & ~15);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&bar[stage], 2 * bytes);
+        bulk_copy_g2s(sk[stage], keys_in + base, bytes, &bar[stage]);
+        bulk_copy_g2s(sv[stage], vals_in + base, bytes, &bar[stage]);
+    };
+    if (threadIdx.x == 0) issue(blockIdx.x, 0);
+
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int stage = it & 1;
+        const int64_t base = (int64_t)t * kSortTile;
+        const int nvalid = (int)((n - base) < kSortTile ? (n - base) : kSortTile);
+        const bool has_next = t + (int)gridDim.x < ntiles;
+        if (threadIdx.x == 0 && has_next) issue(t + gridDim.x, stage ^ 1);
+        for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wcnt[0][0])[k] = 0;
+        const bool ok = mbar_wait_bounded(&bar[stage], (uint32_t)(it >> 1) & 1u);
+        if (__syncthreads_or(!ok)) {
+            // a copy did not complete in time: record it, let in-flight copies land, leave
+            if (threadIdx.x == 0) {
+                atomicOr(err, kErrTimeout);
+                mbar_wait_bounded(&bar[stage], (uint32_t)(it >> 1) & 1u);
+                if (has_next) mbar_wait_bounded(&bar[stage ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
+            }
+            __syncthreads();
+            return;
         }
-        uint32_t tot;
-        uint32_t st = block_exclusive_scan<kSortThreads>(s, ws, &tot);
-        dstart[d] = st;
-        gbase[d] = scanned[(int64_t)d * nblocks + blockIdx.x];
-    }
-    __syncthreads();
+        uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
+        const int wseg = warp * (32 * kSortItems);
 #pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        int64_t i = wbase + r * 32 + lane;
-        if (i < n) {
-            uint32_t d = (key[r] >> shift) & mask;
-            uint32_t pos = dstart[d] + wcnt[warp][d] + loc[r];
-            skeys[pos] = key[r];
-            svals[pos] = val[r];
+        for (int r = 0; r < kSortItems; ++r) {
+            const int li = wseg + r * 32 + lane;
+            const bool valid = li < nvalid;
+            key[r] = valid ? sk[stage][li] : 0xffffffffu;
+            val[r] = valid ? sv[stage][li] : 0u;
+            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+            const uint32_t d = (key[r] >> shift) & mask;
+            const uint32_t peers = digit_peers(d, bits, vmask);
+            const uint32_t before = valid ? wcnt[warp][d] : 0u;
+            __syncwarp();
+            if (valid && (peers & lt) == 0) wcnt[warp][d] = before + (uint32_t)__popc(peers);
+            __syncwarp();
+            loc[r] = before + (uint32_t)__popc(peers & lt);
         }
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < nvalid; p += kSortThreads) {
-        uint32_t k = skeys[p];
-        uint32_t d = (k >> shift) & mask;
-        uint32_t o = gbase[d] + (uint32_t)p - dstart[d];
-        keys_out[o] = k;
-        vals_out[o] = svals[p];
+        __syncthreads();
+        {
+            const int d = threadIdx.x;
+            uint32_t s = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t c = wcnt[w][d];
+                wcnt[w][d] = s;
+                s += c;
+            }
+            uint32_t tot;
+            const uint32_t st = block_exclusive_scan<kSortThreads>(s, ws, &tot);
+            dstart[d] = st;
+            gbase[d] = scanned[(int64_t)d * nblocks + t];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            const int li = wseg + r * 32 + lane;
+            if (li < nvalid) {
+                const uint32_t d = (key[r] >> shift) & mask;
+                const uint32_t pos = dstart[d] + wcnt[warp][d] + loc[r];
+                sk[stage][pos] = key[r];
+                sv[stage][pos] = val[r];
+            }
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < nvalid; p += kSortThreads) {
+            const uint32_t k = sk[stage][p];
+            const uint32_t d = (k >> shift) & mask;
+            const uint32_t o = gbase[d] + (uint32_t)p - dstart[d];
+            if (keys_out) keys_out[o] = k;
+            vals_out[o] = sv[stage][p];
+        }
+        __syncthreads();
     }
 }
 
@@ -229,12 +368,18 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
         if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
         return cudaSuccess;
     }
+    const bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    if (n <= kSmallScan) {
+        k_scan_single<<<1, 1024, 0, st>>>(in, out, n, vec, total);
+        note_launches(1);
+        return cudaGetLastError();
+    }
     int64_t nb = (n + kScanChunk - 1) / kScanChunk;
-    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, partials);
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, vec, partials);
     note_launches(1);
     k_scan_partials<<<1, 1024, 0, st>>>(partials, nb, total);
     note_launches(1);
-    k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, partials);
+    k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, vec, partials);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -247,29 +392,36 @@ size_t radix_scratch_words(int64_t n_max) {
 
 cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
                              const uint32_t *n_dev, int end_bit, uint32_t *scratch, int *out_buf,
-                             cudaStream_t st) {
+                             cudaStream_t st, uint32_t *err, bool keys_out) {
     int cur = 0;
     if (n_max <= 0 || end_bit <= 0) {
         *out_buf = 0;
         return cudaSuccess;
     }
-    int nblocks = (int)((n_max + kSortTile - 1) / kSortTile);
+    const int nblocks = (int)((n_max + kSortTile - 1) / kSortTile);
+    const int grid = nblocks < 148 * 4 ? nblocks : 148 * 4;
     uint32_t *counts = scratch;
     uint32_t *partials = scratch + (size_t)256 * nblocks;
-    for (int shift = 0; shift < end_bit; shift += 8) {
-        int bits = end_bit - shift < 8 ? end_bit - shift : 8;
-        uint32_t mask = (1u << bits) - 1u;
+    // balanced digit widths: ceil(end_bit / 8) passes of nearly equal width
+    const int passes = (end_bit + 7) / 8;
+    int shift = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int bits = (end_bit - shift + (passes - pass) - 1) / (passes - pass);
+        const uint32_t mask = (1u << bits) - 1u;
         k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(keys[cur], n_dev, n_max, shift, mask, counts,
                                                        nblocks);
         note_launches(1);
         cudaError_t e = launch_exclusive_scan(counts, counts, (int64_t)256 * nblocks, nullptr,
                                               partials, st);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(keys[cur], vals[cur], keys[cur ^ 1],
-                                                          vals[cur ^ 1], n_dev, n_max, shift, mask,
-                                                          counts, nblocks);
+        const bool last = pass == passes - 1;
+        k_radix_scatter<<<grid, kSortThreads, 0, st>>>(keys[cur], vals[cur],
+                                                       (last && !keys_out) ? nullptr : keys[cur ^ 1],
+                                                       vals[cur ^ 1], n_dev, n_max, shift, mask,
+                                                       counts, nblocks, err);
         note_launches(1);
         cur ^= 1;
+        shift += bits;
     }
     *out_buf = cur;
     return cudaGetLastError();

@@ -240,15 +240,17 @@ class Renderer:
         return ranges, ids[:st["n_keys"]]
 
     def pixel_state(self, saved: Saved | None = None, stream=None, with_walked: bool = False):
-        """(final T, blended count[, walked count]) per pixel of the saved forward."""
+        """(final T, blended count[, walked count, list position after the last blended])."""
         st = self.stats(saved, stream)
         dev = f"cuda:{self.device}"
-        T = torch.empty((st["height"], st["width"]), device=dev)
-        nb = torch.empty((st["height"], st["width"]), dtype=torch.int32, device=dev)
-        nw = torch.empty((st["height"], st["width"]), dtype=torch.int32, device=dev) if with_walked else None
+        shape = (st["height"], st["width"])
+        T = torch.empty(shape, device=dev)
+        nb = torch.empty(shape, dtype=torch.int32, device=dev)
+        nw = torch.empty(shape, dtype=torch.int32, device=dev) if with_walked else None
+        nc = torch.empty(shape, dtype=torch.int32, device=dev) if with_walked else None
         check(lib().gc_saved_pixel_state(self.ctx, saved.handle if saved else None, _ptr(T), _ptr(nb),
-                                         _ptr(nw), _stream(stream)), self.ctx)
-        return (T, nb, nw) if with_walked else (T, nb)
+                                         _ptr(nw), _ptr(nc), _stream(stream)), self.ctx)
+        return (T, nb, nw, nc) if with_walked else (T, nb)
 
     def profile(self, enable: bool = True):
         check(lib().gc_profile_enable(self.ctx, 1 if enable else 0), self.ctx)
