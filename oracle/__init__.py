@@ -325,6 +325,18 @@ def tile_lists(bins: dict, cam, tile=(16, 16)) -> dict:
             "n_tiles": n_tiles}
 
 
+def tile_list(bins: dict, cam, tile_id: int, tile=(16, 16)) -> np.ndarray:
+    """The (depth, index)-ordered global ids of one tile's list (cheap for big scenes)."""
+    tw, th = tile
+    ntx = (cam.width + tw - 1) // tw
+    tx, ty = tile_id % ntx, tile_id // ntx
+    tr = bins["trect"]
+    m = (bins["visible"] == 1) & (tr[:, 0] <= tx) & (tr[:, 1] >= tx) & (tr[:, 2] <= ty) & (tr[:, 3] >= ty)
+    j = np.nonzero(m)[0]
+    order = np.lexsort((bins["sel"][j], bins["depth"][j]))
+    return bins["sel"][j][order]
+
+
 def quat_to_rot(q) -> np.ndarray:
     q = np.ascontiguousarray(q, np.float64)
     R = np.zeros(9)

@@ -493,7 +493,7 @@ static int member(const gc_prep *P, const gco_options *op, int64_t j, int px, in
 static int prep_build(gc_prep *P, const gco_scene *sc, const gco_motion *mo, const gco_camera *cam,
                       const gco_options *op, const int64_t *sel, int64_t n_sel,
                       const int32_t *visible, const float *depth, const int32_t *rect,
-                      const int32_t *trect) {
+                      const int32_t *trect, int direct) {
     memset(P, 0, sizeof *P);
     P->rect = rect; P->trect = trect;
     int64_t nv = 0;
@@ -509,8 +509,10 @@ static int prep_build(gc_prep *P, const gco_scene *sc, const gco_motion *mo, con
 #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n_sel; ++j)
         if (visible[j]) geom_d(sc, mo, cam, op, sel[j], &P->geo[j]);
-    /* rows covered: pixel rows of the footprint (square mode) or of the tile rows */
+    /* rows covered: pixel rows of the footprint (square mode) or of the tile rows.
+       With direct != 0 no buckets are built: pixels scan the whole sorted list. */
     int H = cam->height;
+    if (direct) { P->row_start = NULL; P->row_list = NULL; return 0; }
     P->row_start = (int64_t *)calloc((size_t)H + 1, sizeof(int64_t));
     if (!P->row_start) return -1;
     for (int64_t k = 0; k < nv; ++k) {
@@ -556,8 +558,10 @@ static void composite_pixel(const gc_prep *P, const gco_options *op, int px, int
     double sig = 0;
     double pcx = px + 0.5, pcy = py + 0.5;
     int64_t ns = 0;
-    for (int64_t k = P->row_start[py]; k < P->row_start[py + 1]; ++k) {
-        int64_t j = P->row_list[k];
+    const int64_t kb = P->row_start ? P->row_start[py] : 0;
+    const int64_t ke = P->row_start ? P->row_start[py + 1] : P->nvis;
+    for (int64_t k = kb; k < ke; ++k) {
+        int64_t j = P->row_start ? P->row_list[k] : P->order[k];
         if (!member(P, op, j, px, py)) continue;
         const gc_geom *G = &P->geo[j];
         double dx = pcx - G->u, dy = pcy - G->v;
@@ -604,7 +608,10 @@ API int gco_render_f64(const gco_scene *sc, const gco_motion *mo, const gco_came
                        double *out_sig) {
     gc_prep P;
     sh_init();
-    if (prep_build(&P, sc, mo, cam, op, sel, n_sel, visible, depth, rect, trect)) { prep_free(&P); return -1; }
+    /* sampled pixels over a large scene: scan the sorted list per pixel instead of
+       building per-row buckets (same visiting order, same result) */
+    int direct = n_pix > 0 && n_pix * 64 < (int64_t)cam->height * cam->width && n_sel > 200000;
+    if (prep_build(&P, sc, mo, cam, op, sel, n_sel, visible, depth, rect, trect, direct)) { prep_free(&P); return -1; }
     int64_t W = cam->width, H = cam->height;
     int64_t total = n_pix > 0 ? n_pix : W * H;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -647,7 +654,7 @@ API int gco_grad_f64(const gco_scene *sc, const gco_motion *mo, const gco_camera
                      double *d_sh, double *d_gq, double *d_gt, double *d2d) {
     gc_prep P;
     sh_init();
-    if (prep_build(&P, sc, mo, cam, op, sel, n_sel, visible, depth, rect, trect)) { prep_free(&P); return -1; }
+    if (prep_build(&P, sc, mo, cam, op, sel, n_sel, visible, depth, rect, trect, 0)) { prep_free(&P); return -1; }
     int64_t W = cam->width, H = cam->height;
     int nthreads = 1;
 #ifdef _OPENMP
