@@ -1,68 +1,12 @@
-// gc_preprocess.cu - per-Gaussian motion, activation, EWA projection, footprint and
-// SH colour (4DGCPro Sec. 3.1 / 3.2), one thread per selected Gaussian.
-//
-// The values that decide integers - visibility, the depth key and the pixel
-// footprint - follow the binning specification op by op: every operation is a
-// separately rounded IEEE binary32 op (__fmul_rn / __fadd_rn / __fdiv_rn /
-// __fsqrt_rn are never fused into FMA), and s = (float)exp((double)log_s).
-// Colour (SH) is free arithmetic: it only feeds continuous values.
-#include <cuda_fp8.h>
+// gc_preprocess.cu - single-frame preprocess (one thread per selected Gaussian,
+// projection in gc_project.cuh) and the gather of records into depth order.
 #include <cuda_runtime.h>
 
-#include "gc_blend.cuh"
-#include "gc_internal.cuh"
-#include "gc_sh.cuh"
+#include "gc_project.cuh"
 
 namespace gc {
 
 namespace {
-
-__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
-
-__device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
-
-__device__ __forceinline__ float e4m3_to_f32(uint8_t b) {
-    __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3);
-    return __half2float(__half(hr));
-}
-
-// Loads the attributes of global Gaussian i (dequantised for BF16/FP8).
-struct Attr {
-    float mu[3], ls[3], q[4], logit;
-    int g;
-};
-
-__device__ __forceinline__ void load_attr(const GaussSrc &G, int64_t i, Attr &a) {
-    if (G.precision == GC_PREC_FP32) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            a.mu[k] = G.means[3 * i + k];
-            a.ls[k] = G.log_scales[3 * i + k];
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) a.q[k] = G.quats[4 * i + k];
-        a.logit = G.opacity_logits[i];
-    } else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            a.mu[k] = fmul(bf16_to_f32(G.means_h[3 * i + k]), G.scales[k]);
-            a.ls[k] = fmul(bf16_to_f32(G.log_scales_h[3 * i + k]), G.scales[3 + k]);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) a.q[k] = fmul(bf16_to_f32(G.quats_h[4 * i + k]), G.scales[6 + k]);
-        a.logit = fmul(bf16_to_f32(G.opacity_h[i]), G.scales[10]);
-    }
-    a.g = G.group_id ? G.group_id[i] : 0;
-}
-
-__device__ __forceinline__ float load_sh(const GaussSrc &G, int64_t i, int k, int c) {
-    int64_t idx = (i * G.K + k) * 3 + c;
-    if (G.precision == GC_PREC_FP32) return G.sh[idx];
-    return fmul(e4m3_to_f32(G.sh_q[idx]), G.scales[11 + 3 * k + c]);
-}
 
 __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, int64_t n_sel,
                                                     CamParams cam, RenderParams rp,
@@ -74,160 +18,21 @@ __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, i
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_sel) return;
     const int64_t i = sel_global(sel, j);
-    Attr A;
-    load_attr(G, i, A);
+    Proj P;
+    project_gaussian(G, i, G.group_q, G.group_t, G.n_groups, cam, rp, P);
+    rec[3 * j] = P.r0;
+    rec[3 * j + 1] = P.r1;
+    rec[3 * j + 2] = P.r2;
+    depth_keys[j] = P.key;
     depth_vals[j] = (uint32_t)j;
-    uint32_t key = kCulledKey, ntouch = 0;
-    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
-
-    do {
-        float gq[4] = {1.f, 0.f, 0.f, 0.f}, gt[3] = {0.f, 0.f, 0.f};
-        if (G.group_q && (A.g < 0 || A.g >= G.n_groups)) break;  // invalid group id: culled
-        if (G.group_q) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) gq[k] = G.group_q[4 * A.g + k];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) gt[k] = G.group_t[3 * A.g + k];
-        }
-        // 1. moved mean
-        const float m0 = fadd(A.mu[0], gt[0]), m1 = fadd(A.mu[1], gt[1]), m2 = fadd(A.mu[2], gt[2]);
-        // 2. p = q_g (x) q
-        const float a0 = gq[0], a1 = gq[1], a2 = gq[2], a3 = gq[3];
-        const float b0 = A.q[0], b1 = A.q[1], b2 = A.q[2], b3 = A.q[3];
-        float p0 = fmul(a0, b0); p0 = fsub(p0, fmul(a1, b1)); p0 = fsub(p0, fmul(a2, b2)); p0 = fsub(p0, fmul(a3, b3));
-        float p1 = fmul(a0, b1); p1 = fadd(p1, fmul(a1, b0)); p1 = fadd(p1, fmul(a2, b3)); p1 = fsub(p1, fmul(a3, b2));
-        float p2 = fmul(a0, b2); p2 = fsub(p2, fmul(a1, b3)); p2 = fadd(p2, fmul(a2, b0)); p2 = fadd(p2, fmul(a3, b1));
-        float p3 = fmul(a0, b3); p3 = fadd(p3, fmul(a1, b2)); p3 = fsub(p3, fmul(a2, b1)); p3 = fadd(p3, fmul(a3, b0));
-        // 3. normalise
-        float n2 = fmul(p0, p0); n2 = fadd(n2, fmul(p1, p1)); n2 = fadd(n2, fmul(p2, p2)); n2 = fadd(n2, fmul(p3, p3));
-        if (!(n2 > 0.f)) break;
-        const float nn = __fsqrt_rn(n2);
-        const float w = fdiv(p0, nn), x = fdiv(p1, nn), y = fdiv(p2, nn), z = fdiv(p3, nn);
-        // 4. rotation
-        const float xx = fmul(x, x), yy = fmul(y, y), zz = fmul(z, z);
-        const float xy = fmul(x, y), xz = fmul(x, z), yz = fmul(y, z);
-        const float wx = fmul(w, x), wy = fmul(w, y), wz = fmul(w, z);
-        float R[9];
-        R[0] = fsub(1.f, fmul(2.f, fadd(yy, zz))); R[1] = fmul(2.f, fsub(xy, wz)); R[2] = fmul(2.f, fadd(xz, wy));
-        R[3] = fmul(2.f, fadd(xy, wz)); R[4] = fsub(1.f, fmul(2.f, fadd(xx, zz))); R[5] = fmul(2.f, fsub(yz, wx));
-        R[6] = fmul(2.f, fsub(xz, wy)); R[7] = fmul(2.f, fadd(yz, wx)); R[8] = fsub(1.f, fmul(2.f, fadd(xx, yy)));
-        // 5. scales, correctly rounded to FP32 through FP64
-        float s[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) s[k] = (float)exp((double)A.ls[k]);
-        // 6-7. M = R diag(s), Sigma = M M^T
-        float M[9];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) M[3 * r + c] = fmul(R[3 * r + c], s[c]);
-        float S[9];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = r; c < 3; ++c) {
-                float acc = fmul(M[3 * r], M[3 * c]);
-                acc = fadd(acc, fmul(M[3 * r + 1], M[3 * c + 1]));
-                acc = fadd(acc, fmul(M[3 * r + 2], M[3 * c + 2]));
-                S[3 * r + c] = acc;
-                S[3 * c + r] = acc;
-            }
-        // 8. camera point
-        float cp[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            float acc = fmul(cam.R[3 * r], m0);
-            acc = fadd(acc, fmul(cam.R[3 * r + 1], m1));
-            acc = fadd(acc, fmul(cam.R[3 * r + 2], m2));
-            cp[r] = fadd(acc, cam.t[r]);
-        }
-        const float cz = cp[2];
-        if (!(cz > rp.near_plane)) break;
-        // 9. clamped Jacobian, T = J W, Sigma2 = T Sigma T^T
-        const float xoz = fdiv(cp[0], cz), yoz = fdiv(cp[1], cz);
-        const float limx = fmul(rp.frustum_clamp, fdiv(fmul(0.5f, (float)cam.width), cam.fx));
-        const float limy = fmul(rp.frustum_clamp, fdiv(fmul(0.5f, (float)cam.height), cam.fy));
-        const float xt = fminf(limx, fmaxf(-limx, xoz));
-        const float yt = fminf(limy, fmaxf(-limy, yoz));
-        const float J00 = fdiv(cam.fx, cz), J11 = fdiv(cam.fy, cz);
-        const float J02 = -fdiv(fmul(cam.fx, xt), cz), J12 = -fdiv(fmul(cam.fy, yt), cz);
-        float T[6];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            T[c] = fadd(fmul(J00, cam.R[c]), fmul(J02, cam.R[6 + c]));
-            T[3 + c] = fadd(fmul(J11, cam.R[3 + c]), fmul(J12, cam.R[6 + c]));
-        }
-        float U[6];
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float acc = fmul(T[3 * r], S[c]);
-                acc = fadd(acc, fmul(T[3 * r + 1], S[3 + c]));
-                acc = fadd(acc, fmul(T[3 * r + 2], S[6 + c]));
-                U[3 * r + c] = acc;
-            }
-        float ca = fmul(U[0], T[0]); ca = fadd(ca, fmul(U[1], T[1])); ca = fadd(ca, fmul(U[2], T[2])); ca = fadd(ca, rp.dilation);
-        float cb = fmul(U[0], T[3]); cb = fadd(cb, fmul(U[1], T[4])); cb = fadd(cb, fmul(U[2], T[5]));
-        float cc = fmul(U[3], T[3]); cc = fadd(cc, fmul(U[4], T[4])); cc = fadd(cc, fmul(U[5], T[5])); cc = fadd(cc, rp.dilation);
-        // 10. conic
-        const float det = fsub(fmul(ca, cc), fmul(cb, cb));
-        if (!(det > 0.f)) break;
-        const float ia = fdiv(cc, det), ib = -fdiv(cb, det), ic = fdiv(ca, det);
-        // 11. radius
-        const float mid = fmul(0.5f, fadd(ca, cc));
-        const float disc = fsub(fmul(mid, mid), det);
-        const float lam = fadd(mid, __fsqrt_rn(fmaxf(0.f, disc)));
-        const float rf = ceilf(fmul(3.f, __fsqrt_rn(lam)));
-        // 12. centre
-        const float u = fadd(fmul(cam.fx, xoz), cam.cx);
-        const float v = fadd(fmul(cam.fy, yoz), cam.cy);
-        if (!isfinite(u) || !isfinite(v) || !isfinite(rf)) break;
-        // 13. clipped pixel rectangle
-        float fx0 = ceilf(fsub(fsub(u, rf), 0.5f)), fx1 = floorf(fsub(fadd(u, rf), 0.5f));
-        float fy0 = ceilf(fsub(fsub(v, rf), 0.5f)), fy1 = floorf(fsub(fadd(v, rf), 0.5f));
-        fx0 = fmaxf(fx0, 0.f);
-        fy0 = fmaxf(fy0, 0.f);
-        fx1 = fminf(fx1, (float)(cam.width - 1));
-        fy1 = fminf(fy1, (float)(cam.height - 1));
-        if (!(fx0 <= fx1) || !(fy0 <= fy1)) break;
-        const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
-        const int tx0 = x0 >> rp.tile_w_log2, tx1 = x1 >> rp.tile_w_log2;
-        const int ty0 = y0 >> rp.tile_h_log2, ty1 = y1 >> rp.tile_h_log2;
-        ntouch = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-        key = __float_as_uint(cz);
-        if (tile_diff) {
-            const int gw = rp.ntx + 1;
-            atomicAdd(&tile_diff[ty0 * gw + tx0], 1);
-            atomicAdd(&tile_diff[ty0 * gw + tx1 + 1], -1);
-            atomicAdd(&tile_diff[(ty1 + 1) * gw + tx0], -1);
-            atomicAdd(&tile_diff[(ty1 + 1) * gw + tx1 + 1], 1);
-        }
-
-        // colour (free FP32 arithmetic)
-        float dxv = m0 - cam.campos[0], dyv = m1 - cam.campos[1], dzv = m2 - cam.campos[2];
-        float inv = 1.0f / sqrtf(dxv * dxv + dyv * dyv + dzv * dzv);
-        float Y[16];
-        sh_basis(G.sh_degree, dxv * inv, dyv * inv, dzv * inv, Y);
-        float rgb[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float acc = 0.f;
-            for (int k = 0; k < G.K; ++k) acc = fmaf(Y[k], load_sh(G, i, k, c), acc);
-            rgb[c] = fmaxf(acc + 0.5f, 0.f);
-        }
-        const float op = 1.0f / (1.0f + expf(-A.logit));
-        // conic stored pre-scaled for the blend's base-2 exponent (see gc_blend.cuh)
-        r0 = make_float4(u, v, __fmul_rn(ia, -0.5f * kLog2e), __fmul_rn(ib, -kLog2e));
-        r1 = make_float4(__fmul_rn(ic, -0.5f * kLog2e), op, rgb[0], rgb[1]);
-        r2 = make_float4(rgb[2], cz, __int_as_float(x0 | (x1 << 16)), __int_as_float(y0 | (y1 << 16)));
-    } while (0);
-
-    rec[3 * j] = r0;
-    rec[3 * j + 1] = r1;
-    rec[3 * j + 2] = r2;
-    depth_keys[j] = key;
-    touched[j] = ntouch;
+    touched[j] = P.ntouch;
+    if (tile_diff && P.ntouch) {
+        const int gw = rp.ntx + 1;
+        atomicAdd(&tile_diff[P.ty0 * gw + P.tx0], 1);
+        atomicAdd(&tile_diff[P.ty0 * gw + P.tx1 + 1], -1);
+        atomicAdd(&tile_diff[(P.ty1 + 1) * gw + P.tx0], -1);
+        atomicAdd(&tile_diff[(P.ty1 + 1) * gw + P.tx1 + 1], 1);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_rank_gather(const uint32_t *__restrict__ perm,

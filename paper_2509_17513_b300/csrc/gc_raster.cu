@@ -12,20 +12,12 @@
 
 #include <algorithm>
 
-#include "gc_blend.cuh"
-#include "gc_internal.cuh"
+#include "gc_tile.cuh"
 
 namespace gc {
 
 namespace {
 
-__device__ __forceinline__ void unpack_rect(float4 r2, int &x0, int &x1, int &y0, int &y1) {
-    const uint32_t rx = __float_as_uint(r2.z), ry = __float_as_uint(r2.w);
-    x0 = (int)(rx & 0xffffu);
-    x1 = (int)(rx >> 16);
-    y0 = (int)(ry & 0xffffu);
-    y1 = (int)(ry >> 16);
-}
 
 // One warp emits the entries of 32 consecutive ranks, lanes striding over the
 // warp's contiguous output range (coalesced writes, balanced across lanes).
@@ -89,48 +81,11 @@ __global__ void k_tile_ranges(const uint32_t *__restrict__ keys, const uint32_t 
     }
 }
 
-// Per-pixel front-to-back state.
-struct FwdPix {
-    float T, C0, C1, C2;
-    uint32_t last, nb, walked;
-    bool done;
-};
-
-// One compositing step of Eq. 2 for one pixel and the staged Gaussian (a, bb, blue).
-__device__ __forceinline__ void fwd_step(FwdPix &P, float pcx, float pcy, const float4 &a,
-                                         const float4 &bb, float blue, uint32_t idx) {
-    const float dx = pcx - a.x, dy = pcy - a.y;
-    const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
-    if (p2 > 0.f) return;
-    float G;
-    const float alpha = fminf(kAlphaMax, blend_raw_alpha(bb.y, p2, G));
-    if (alpha < kAlphaMin) return;
-    const float Tn = P.T * (1.f - alpha);
-    if (Tn < kTStop) {
-        P.done = true;
-        P.walked = idx + 1;
-        return;
-    }
-    const float w = alpha * P.T;
-    P.C0 = fmaf(bb.z, w, P.C0);
-    P.C1 = fmaf(bb.w, w, P.C1);
-    P.C2 = fmaf(blue, w, P.C2);
-    P.T = Tn;
-    P.last = idx + 1;
-    ++P.nb;
-}
-
 #ifndef GC_FWD_PPT
 #define GC_FWD_PPT 1  // pixels per thread in the forward blend (1 measured fastest on B300)
 #endif
 
-// Front-to-back compositing (Eq. 2), one CTA per tile of TW x TH = 256 pixels with
-// 256 / PPT threads; thread t owns the PPT vertically adjacent pixels
-// (t % TW, PPT * (t / TW) + i), so each staged Gaussian is read from shared memory
-// once per PPT pixels.  Batches of up to 256 list entries are staged in shared
-// memory (gathered from the depth-ranked records); a pixel stops when blending the
-// next Gaussian would take its transmittance below 1e-4, the CTA as soon as all its
-// pixels did.
+// One CTA per tile of a single image.
 template <int TW, int TH, int PPT>
 __global__ void __launch_bounds__(256 / PPT) k_blend_fwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
@@ -138,91 +93,10 @@ __global__ void __launch_bounds__(256 / PPT) k_blend_fwd(
     int membership, float *__restrict__ image, float *__restrict__ final_T,
     uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ n_blended,
     uint32_t *__restrict__ n_walked) {
-    static_assert(TW * TH == 256, "tile must hold 256 pixels");
-    constexpr int NT = 256 / PPT;
-    __shared__ float4 sA[256];  // u, v, A, B
-    __shared__ float4 sB[256];  // C, opacity, red, green
-    __shared__ float4 sC[256];  // blue, column mask, row mask, -
-
+    __shared__ float4 sA[256], sB[256], sC[256];
     const int tile = blockIdx.x;
-    const int tx = tile % ntx, ty = tile / ntx;
-    const int lx = threadIdx.x % TW, lyb = PPT * (threadIdx.x / TW);
-    const int px = tx * TW + lx;
-    const float pcx = (float)px + 0.5f;
-    const uint32_t xbit = 1u << lx;
-    const uint2 range = ranges[tile];
-    const int n = (int)(range.y - range.x);
-
-    FwdPix P[PPT];
-#pragma unroll
-    for (int i = 0; i < PPT; ++i) P[i] = {1.f, 0.f, 0.f, 0.f, 0u, 0u, 0u, !(px < W && ty * TH + lyb + i < H)};
-    auto all_done = [&]() {
-        bool d = true;
-#pragma unroll
-        for (int i = 0; i < PPT; ++i) d = d && P[i].done;
-        return d;
-    };
-
-    for (int b = 0; b < n; b += 256) {
-        if (__syncthreads_count(all_done()) == NT) break;
-#pragma unroll
-        for (int h = 0; h < PPT; ++h) {
-            const int slot = (int)threadIdx.x + NT * h;
-            const int idx = b + slot;
-            if (idx < n) {
-                const uint32_t r = sorted_vals[range.x + idx];
-                const float4 a = ranked[3 * (size_t)r];
-                const float4 bb = ranked[3 * (size_t)r + 1];
-                const float4 c = ranked[3 * (size_t)r + 2];
-                uint32_t cm = 0xffffffffu, rm = 0xffffffffu;
-                if (membership == GC_MEMBER_PIXEL) {
-                    int x0, x1, y0, y1;
-                    unpack_rect(c, x0, x1, y0, y1);
-                    const int lx0 = max(x0 - tx * TW, 0), lx1 = min(x1 - tx * TW, TW - 1);
-                    const int ly0r = max(y0 - ty * TH, 0), ly1r = min(y1 - ty * TH, TH - 1);
-                    cm = (lx1 >= lx0) ? ((0xffffffffu >> (31 - lx1)) & (0xffffffffu << lx0)) : 0u;
-                    rm = (ly1r >= ly0r) ? ((0xffffffffu >> (31 - ly1r)) & (0xffffffffu << ly0r)) : 0u;
-                }
-                sA[slot] = a;
-                sB[slot] = bb;
-                sC[slot] = make_float4(c.x, __uint_as_float(cm), __uint_as_float(rm), 0.f);
-            }
-        }
-        __syncthreads();
-        const int cnt = min(256, n - b);
-        for (int k = 0; k < cnt; ++k) {
-            if (all_done()) break;
-            const float4 c = sC[k];
-            if (!(__float_as_uint(c.y) & xbit)) continue;
-            const uint32_t rm = __float_as_uint(c.z) >> lyb;  // bit i: row lyb + i of the tile
-            bool any = false;
-#pragma unroll
-            for (int i = 0; i < PPT; ++i) any = any || (!P[i].done && ((rm >> i) & 1u));
-            if (!any) continue;
-            const float4 a = sA[k];
-            const float4 bb = sB[k];
-            const uint32_t idx = (uint32_t)(b + k);
-#pragma unroll
-            for (int i = 0; i < PPT; ++i)
-                if (!P[i].done && ((rm >> i) & 1u))
-                    fwd_step(P[i], pcx, (float)(ty * TH + lyb + i) + 0.5f, a, bb, c.x, idx);
-        }
-    }
-    const size_t hw = (size_t)W * H;
-#pragma unroll
-    for (int i = 0; i < PPT; ++i) {
-        const int py = ty * TH + lyb + i;
-        if (px < W && py < H) {
-            const size_t p = (size_t)py * W + px;
-            image[p] = fmaf(P[i].T, bg0, P[i].C0);
-            image[hw + p] = fmaf(P[i].T, bg1, P[i].C1);
-            image[2 * hw + p] = fmaf(P[i].T, bg2, P[i].C2);
-            final_T[p] = P[i].T;
-            n_contrib[p] = P[i].last;
-            if (n_blended) n_blended[p] = P[i].nb;
-            if (n_walked) n_walked[p] = P[i].done ? P[i].walked : (uint32_t)n;
-        }
-    }
+    blend_fwd_tile<TW, TH, PPT>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, W, H, bg0, bg1,
+                                bg2, membership, image, final_T, n_contrib, n_blended, n_walked, sA, sB, sC);
 }
 
 // Single CTA: 2D inclusive prefix of the tile difference grid (rows, then columns)
