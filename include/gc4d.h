@@ -116,8 +116,8 @@ typedef struct {
     float campos[3];    /* camera centre in world coordinates (view direction origin) */
 } gc_camera;
 
-/* Gradient outputs (device).  Overwritten, not accumulated.  Gaussians that
- * are not selected or not visible receive 0.  Any pointer may be NULL to skip
+/* Gradient outputs (device).  Overwritten (gc_render_batch_backward can also add
+ * into them).  Gaussians that are not selected or not visible receive 0.  Any pointer may be NULL to skip
  * that output. */
 typedef struct {
     float *d_means;          /* n x 3 */
@@ -208,6 +208,57 @@ GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, const gc_gauss
 GC_API gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved, const gc_gaussians *g,
                              const gc_motion *motion, const float *dL_dimage, gc_grads *out,
                              void *stream);
+
+/* One render of a batch (host struct). */
+typedef struct {
+    gc_camera camera;     /* its own pose, intrinsics and resolution */
+    int32_t frame;        /* index into the batch's motion frames, or -1 for the keyframe */
+    uint32_t layer_mask;  /* layers rendered (bit l = layer l + 1), as in gc_render_forward */
+    float *image;         /* device, 3 x height x width, written */
+} gc_request;
+
+/*
+ * Batched forward: renders n_req requests of one Gaussian set, each with its own
+ * camera, resolution, motion frame and layer mask - the many views, frames and
+ * uneven levels that the paper's layer-wise rate-distortion training renders per
+ * step (Sec. 3.3) and that multi-view playback needs.  Work is merged across the
+ * requests: one preprocess launch over all (request, Gaussian) pairs, segmented
+ * depth and tile sorts (each request sorted on its own, in shared launches), and one
+ * persistent blend kernel whose CTAs pull tiles of all images from a work counter.
+ * Each image equals what gc_render_forward returns for that request alone, bit for
+ * bit.  frames: host array of n_frames motion tables (device arrays inside), may be
+ * NULL when every request uses frame -1.  saved: NULL, or a state for
+ * gc_render_batch_backward.  With key_capacity 0 the call reads one count from the
+ * device (a host sync); with a fixed capacity it does not (overflow is reported by
+ * gc_check).
+ *
+ * CUDA graphs: with a fixed capacity the call may be captured on `stream`.  The
+ * capture must follow an eager call with the same requests, options and saved
+ * state (it sizes the buffers and uploads the request table; the captured call
+ * allocates, copies and synchronises nothing).  From then on that saved state is
+ * bound to the graph: later calls on it must use the same requests, and it must
+ * outlive the graph.  A captured call with other requests or sizes fails with
+ * GC_ERR_STATE.
+ */
+GC_API gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians *g,
+                                         const gc_motion *frames, int32_t n_frames,
+                                         const gc_request *reqs, int32_t n_req, gc_saved *saved,
+                                         void *stream);
+
+/*
+ * Batched backward of the batch recorded in `saved`.  dL_dimages: host array of
+ * n_req device pointers (3 x height x width each).  Attribute gradients are summed
+ * over the requests in request order (deterministic); the motion gradient is per
+ * (frame, group): out->d_group_q is n_frames x G x 4, out->d_group_t n_frames x G x 3.
+ * accumulate = 0 overwrites the gradient buffers; 1 adds this batch's gradients to
+ * them (one addition per element), so that a step split into several batches sums
+ * its gradients in batch order.  Graph capture follows the rules of the forward
+ * (the same dL_dimages pointers as the preceding eager call).
+ */
+GC_API gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *saved,
+                                          const gc_gaussians *g, const gc_motion *frames,
+                                          int32_t n_frames, const float *const *dL_dimages,
+                                          int32_t accumulate, gc_grads *out, void *stream);
 
 /* Statistics of the last forward recorded in `saved` (synchronises `stream`). */
 GC_API gc_status gc_saved_stats(gc_context *ctx, const gc_saved *saved, gc_stats *out, void *stream);

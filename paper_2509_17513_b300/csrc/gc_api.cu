@@ -20,68 +20,7 @@
 
 #include "gc_internal.cuh"
 
-namespace {
-
-struct DevBuf {
-    void *p = nullptr;
-    size_t cap = 0;
-    template <class T>
-    T *as() const { return static_cast<T *>(p); }
-};
-
-cudaError_t grow(DevBuf &b, size_t bytes) {
-    if (bytes <= b.cap && b.p) return cudaSuccess;
-    if (b.p) cudaFree(b.p);
-    b.p = nullptr;
-    b.cap = 0;
-    size_t c = bytes + bytes / 4 + 256;
-    cudaError_t e = cudaMalloc(&b.p, c);
-    if (e != cudaSuccess) {
-        b.p = nullptr;
-        cudaGetLastError();
-        return e;
-    }
-    b.cap = c;
-    return cudaSuccess;
-}
-
-void release(DevBuf &b) {
-    if (b.p) cudaFree(b.p);
-    b.p = nullptr;
-    b.cap = 0;
-}
-
-int ilog2_exact(int v) {
-    int l = 0;
-    while ((1 << l) < v) ++l;
-    return ((1 << l) == v) ? l : -1;
-}
-
-int bits_for(int64_t max_value) {
-    int b = 1;
-    while (b < 32 && ((int64_t)1 << b) <= max_value) ++b;
-    return b;
-}
-
-}  // namespace
-
-struct gc_saved {
-    bool valid = false;
-    int64_t n = 0, n_sel = 0;
-    int sh_degree = 0, n_groups = 1;
-    bool has_motion = false;
-    int n_layers = 0;
-    int64_t layer_offsets[gc::kMaxLayers + 1] = {};
-    uint32_t layer_mask = 0;
-    gc::Selection sel{};
-    gc::CamParams cam{};
-    gc::RenderParams rp{};
-    int64_t K = 0;       // keys used (host view; fixed-capacity mode: the capacity)
-    bool k_exact = false;
-    int depth_buf = 0, tile_buf = 0;
-    DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
-        final_T, n_contrib, n_blended, n_walked, words, tile_diff;
-};
+#include "gc_state.cuh"
 
 namespace gc {
 static std::atomic<uint64_t> g_launches{0};
@@ -89,158 +28,6 @@ void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_
 uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace gc
 
-struct ProfMark {
-    int stage;  // -1: end of a call
-    int event;  // index into the event pool
-};
-
-struct gc_context {
-    int device = 0;
-    bool prof_on = false;
-    std::vector<cudaEvent_t> prof_pool;
-    std::vector<ProfMark> prof_marks;
-    uint64_t launch_base = 0;
-    gc_options opt{};
-    gc_saved internal;
-    DevBuf scratch, bwd_part, bwd_g2d, bwd_motion, bwd_rmax, bwd_group;
-    uint32_t *host_word = nullptr;  // pinned
-    const gc_saved *last = nullptr; // state written by the most recent forward
-    std::string err;
-};
-
-namespace {
-
-gc_status fail(gc_context *ctx, gc_status s, const char *fmt, ...) {
-    if (ctx) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
-        va_end(ap);
-        ctx->err = buf;
-    }
-    return s;
-}
-
-#define GC_CUDA(ctx, call)                                                                    \
-    do {                                                                                      \
-        cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess)                                                                \
-            return fail((ctx), e_ == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA,    \
-                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-    } while (0)
-
-// Records a stage boundary on the stream when profiling is on.
-cudaError_t prof_mark(gc_context *ctx, cudaStream_t s, int stage) {
-    if (!ctx->prof_on) return cudaSuccess;
-    const size_t idx = ctx->prof_marks.size();
-    if (idx >= ctx->prof_pool.size()) {
-        cudaEvent_t e;
-        cudaError_t err = cudaEventCreate(&e);
-        if (err != cudaSuccess) return err;
-        ctx->prof_pool.push_back(e);
-    }
-    ctx->prof_marks.push_back({stage, (int)idx});
-    return cudaEventRecord(ctx->prof_pool[idx], s);
-}
-
-gc_status check_options(gc_context *ctx, const gc_options *o) {
-    bool shape_ok = (o->tile_w == 16 && o->tile_h == 16) || (o->tile_w == 8 && o->tile_h == 32) ||
-                    (o->tile_w == 32 && o->tile_h == 8);
-    if (!shape_ok) return fail(ctx, GC_ERR_INVALID_ARG, "tile shape %dx%d not in {16x16, 8x32, 32x8}", o->tile_w, o->tile_h);
-    if (!(o->near_plane > 0.f)) return fail(ctx, GC_ERR_INVALID_ARG, "near_plane must be > 0");
-    if (!(o->dilation >= 0.f)) return fail(ctx, GC_ERR_INVALID_ARG, "dilation must be >= 0");
-    if (!(o->frustum_clamp > 0.f)) return fail(ctx, GC_ERR_INVALID_ARG, "frustum_clamp must be > 0");
-    if (o->membership != GC_MEMBER_PIXEL && o->membership != GC_MEMBER_TILE)
-        return fail(ctx, GC_ERR_INVALID_ARG, "membership must be GC_MEMBER_PIXEL or GC_MEMBER_TILE");
-    if (o->key_capacity < 0 || o->key_capacity > 0xFFFFFFF0ll)
-        return fail(ctx, GC_ERR_INVALID_ARG, "key_capacity out of range");
-    return GC_OK;
-}
-
-class DeviceGuard {
-  public:
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev_);
-        if (prev_ != dev) cudaSetDevice(dev);
-        dev_ = dev;
-    }
-    ~DeviceGuard() {
-        if (prev_ != dev_) cudaSetDevice(prev_);
-    }
-
-  private:
-    int prev_ = 0, dev_ = 0;
-};
-
-gc_status make_source(gc_context *ctx, const gc_gaussians *g, const gc_motion *m, gc::GaussSrc &s) {
-    if (!g) return fail(ctx, GC_ERR_INVALID_ARG, "gaussians is NULL");
-    if (g->n < 0) return fail(ctx, GC_ERR_INVALID_ARG, "n < 0");
-    if (g->n > 0x7FFFFFFFll) return fail(ctx, GC_ERR_INVALID_ARG, "n exceeds 2^31 - 1");
-    if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ctx, GC_ERR_INVALID_ARG, "sh_degree must be 0..3");
-    if (g->n_layers < 1 || g->n_layers > gc::kMaxLayers)
-        return fail(ctx, GC_ERR_INVALID_ARG, "n_layers must be 1..32");
-    if (!g->layer_offsets) return fail(ctx, GC_ERR_INVALID_ARG, "layer_offsets is NULL");
-    if (g->layer_offsets[0] != 0 || g->layer_offsets[g->n_layers] != g->n)
-        return fail(ctx, GC_ERR_INVALID_ARG, "layer_offsets must start at 0 and end at n");
-    for (int l = 0; l < g->n_layers; ++l)
-        if (g->layer_offsets[l + 1] < g->layer_offsets[l])
-            return fail(ctx, GC_ERR_INVALID_ARG, "layer_offsets must be nondecreasing");
-    memset(&s, 0, sizeof s);
-    s.n = g->n;
-    s.sh_degree = g->sh_degree;
-    s.K = (g->sh_degree + 1) * (g->sh_degree + 1);
-    s.precision = g->precision;
-    if (g->precision == GC_PREC_FP32) {
-        if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
-            return fail(ctx, GC_ERR_INVALID_ARG, "an FP32 attribute array is NULL");
-    } else if (g->precision == GC_PREC_BF16_FP8) {
-        if (g->n > 0 && (!g->means_bf16 || !g->log_scales_bf16 || !g->quats_bf16 ||
-                         !g->opacity_bf16 || !g->sh_e4m3 || !g->scales))
-            return fail(ctx, GC_ERR_INVALID_ARG, "a reduced-precision plane or the scales are NULL");
-    } else {
-        return fail(ctx, GC_ERR_INVALID_ARG, "unknown precision %d", g->precision);
-    }
-    s.means = g->means; s.log_scales = g->log_scales; s.quats = g->quats;
-    s.opacity_logits = g->opacity_logits; s.sh = g->sh; s.group_id = g->group_id;
-    s.means_h = g->means_bf16; s.log_scales_h = g->log_scales_bf16; s.quats_h = g->quats_bf16;
-    s.opacity_h = g->opacity_bf16; s.sh_q = g->sh_e4m3; s.scales = g->scales;
-    s.n_groups = 1;
-    if (m) {
-        if (m->n_groups < 1 || !m->q || !m->t)
-            return fail(ctx, GC_ERR_INVALID_ARG, "motion needs n_groups >= 1 and q, t arrays");
-        s.group_q = m->q;
-        s.group_t = m->t;
-        s.n_groups = m->n_groups;
-    } else if (g->group_id) {
-        s.group_id = nullptr;  // keyframe: groups are irrelevant
-    }
-    return GC_OK;
-}
-
-gc::Selection make_selection(const gc_gaussians *g, uint32_t mask, int64_t &n_sel) {
-    gc::Selection s{};
-    n_sel = 0;
-    s.range_start[0] = 0;
-    for (int l = 0; l < g->n_layers; ++l) {
-        if (!((mask >> l) & 1u)) continue;
-        int64_t a = g->layer_offsets[l], b = g->layer_offsets[l + 1];
-        if (b <= a) continue;
-        // merge adjacent ranges
-        if (s.n_ranges > 0 && s.range_begin[s.n_ranges - 1] + (s.range_start[s.n_ranges] - s.range_start[s.n_ranges - 1]) == a) {
-            s.range_start[s.n_ranges] += b - a;
-        } else {
-            s.range_begin[s.n_ranges] = a;
-            s.range_start[s.n_ranges + 1] = s.range_start[s.n_ranges] + (b - a);
-            s.n_ranges++;
-        }
-        n_sel += b - a;
-    }
-    if (s.n_ranges == 0) s.n_ranges = 1;
-    return s;
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -353,6 +140,7 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
     cudaStream_t s = (cudaStream_t)stream;
     gc_saved &S = saved ? *saved : ctx->internal;
     S.valid = false;
+    if (S.batch) batch_invalidate(S);
 
     const gc_options &o = ctx->opt;
     int64_t n_sel = 0;
@@ -594,6 +382,7 @@ gc_status gc_check(gc_context *ctx, void *stream) {
             return fail(ctx, GC_ERR_TIMEOUT, "a bounded device wait ran out (error word %#x)", w[1]);
         }
     }
+    if (S.batch && S.batch.get() && !S.valid) return batch_check(ctx, S);
     if (S.valid && !S.k_exact && S.n_sel > 0) {
         GC_CUDA(ctx, cudaMemcpy(ctx->host_word, S.words.p, 4, cudaMemcpyDeviceToHost));
         if ((int64_t)ctx->host_word[0] > S.K)

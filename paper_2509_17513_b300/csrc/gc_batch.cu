@@ -1,0 +1,989 @@
+// gc_batch.cu - batched forward and backward over many requests (camera, resolution,
+// motion frame, layer mask) of one Gaussian set: the per-step workload of the
+// paper's layer-wise rate-distortion training (Sec. 3.3) and of multi-view playback.
+//
+// Layout.  Requests are concatenated in every index space, each padded to the radix
+// tile (radix_tile_keys() keys) so that no sort block straddles two requests:
+//   items    (request, selected Gaussian) pairs, request-major, padded;
+//   entries  (tile, Gaussian) pairs, request-major, each request padded (pad keys sort
+//            last and are never referenced by a tile range);
+//   tiles    request-major global tile index; pixels request-major.
+// Steps (all on one stream, no host sync with a fixed key capacity):
+//   preprocess over all items -> segmented depth sort (each request on its own) ->
+//   rank gather -> scan of tiles touched -> per-request entry bases -> emit -> pad fill
+//   -> segmented tile sort (local tile ids) -> per-request tile ranges from the
+//   difference grids -> persistent blend: CTAs take tiles of all images from a work
+//   counter (an atomic ticket, no waiting on other CTAs).
+// Every image equals the single-request render bit for bit: the same projection, the
+// same stable orders and the same per-tile blend run on the same data.
+#include <cuda_runtime.h>
+
+#include "gc_chain.cuh"
+#include "gc_project.cuh"
+#include "gc_state.cuh"
+#include "gc_tile.cuh"
+
+namespace gc {
+
+struct BatchReq {
+    CamParams cam;
+    RenderParams rp;
+    Selection sel;
+    int64_t n_sel;
+    int64_t item_base;
+    int64_t tile_base;
+    int64_t pixel_base;
+    int64_t diff_base;
+    const float *group_q, *group_t;
+    int n_groups;
+    int frame;
+    float *image;
+};
+
+namespace {
+
+// Last q with base[q] <= x, over q in [0, n).
+__device__ __forceinline__ int find_req(const int64_t *base, int n, int64_t x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_batch_preprocess(GaussSrc G, const BatchReq *__restrict__ reqs,
+                                                          const int64_t *__restrict__ item_base, int n_req,
+                                                          int64_t n_items, float4 *__restrict__ rec,
+                                                          uint32_t *__restrict__ keys,
+                                                          uint32_t *__restrict__ vals,
+                                                          uint32_t *__restrict__ touched,
+                                                          int32_t *__restrict__ diff) {
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= n_items) return;
+    const int q = find_req(item_base, n_req, item);
+    const BatchReq &R = reqs[q];
+    const int64_t j = item - R.item_base;
+    vals[item] = (uint32_t)item;
+    Proj P;
+    if (j < R.n_sel) {
+        project_gaussian(G, sel_global(R.sel, j), R.group_q, R.group_t, R.n_groups, R.cam, R.rp, P);
+    } else {
+        P.key = kCulledKey;
+        P.ntouch = 0;
+        P.r0 = P.r1 = P.r2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    rec[3 * item] = P.r0;
+    rec[3 * item + 1] = P.r1;
+    rec[3 * item + 2] = P.r2;
+    keys[item] = P.key;
+    touched[item] = P.ntouch;
+    if (P.ntouch) {
+        int32_t *d = diff + R.diff_base;
+        const int gw = R.rp.ntx + 1;
+        atomicAdd(&d[P.ty0 * gw + P.tx0], 1);
+        atomicAdd(&d[P.ty0 * gw + P.tx1 + 1], -1);
+        atomicAdd(&d[(P.ty1 + 1) * gw + P.tx0], -1);
+        atomicAdd(&d[(P.ty1 + 1) * gw + P.tx1 + 1], 1);
+    }
+}
+
+// Per request: entry count K_q, padded entry base, the shift from the unpadded scan
+// offsets, and the entry segments in radix-block units.  words[2] = padded total.
+// If the padded total exceeds `cap`, every entry segment is made empty so that the
+// tile sort stays inside its buffers (nothing is emitted; gc_check reports it).
+__global__ void k_batch_entry_bases(const uint32_t *__restrict__ offsets, const uint32_t *total,
+                                    const int64_t *__restrict__ item_base, int n_req, int64_t n_items,
+                                    uint32_t tile_keys, uint32_t cap, uint32_t *__restrict__ ebase,
+                                    uint32_t *__restrict__ eshift, uint32_t *__restrict__ ecount,
+                                    uint32_t *__restrict__ seg_entries, uint32_t *words) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    auto off = [&](int64_t idx) -> uint32_t { return idx < n_items ? offsets[idx] : *total; };
+    uint64_t eb = 0;
+    for (int q = 0; q < n_req; ++q) {
+        const uint32_t a = off(item_base[q]), b = off(item_base[q + 1]);
+        const uint64_t kq = b - a;
+        ebase[q] = (uint32_t)eb;
+        eshift[q] = (uint32_t)(eb - a);
+        ecount[q] = (uint32_t)kq;
+        seg_entries[q] = (uint32_t)(eb / tile_keys);
+        eb += (kq + tile_keys - 1) / tile_keys * tile_keys;
+    }
+    const uint32_t padded = (uint32_t)(eb > 0xFFFFFFFFull ? 0xFFFFFFFFull : eb);
+    ebase[n_req] = padded;
+    seg_entries[n_req] = (uint32_t)(eb / tile_keys);
+    if (padded > cap)
+        for (int q = 0; q <= n_req; ++q) seg_entries[q] = 0u;
+    words[2] = padded;
+}
+
+// One warp emits the entries of 32 consecutive ranks (one request: requests are
+// padded to the radix tile); entry e = offsets[r] + eshift[q] + index of the tile in
+// the Gaussian's tile rectangle; key = the request's local tile id, value = r.
+__global__ void __launch_bounds__(256) k_batch_emit(const float4 *__restrict__ ranked,
+                                                    const uint32_t *__restrict__ offsets,
+                                                    const uint32_t *__restrict__ touched_r,
+                                                    const BatchReq *__restrict__ reqs,
+                                                    const int64_t *__restrict__ item_base, int n_req,
+                                                    const uint32_t *__restrict__ eshift, int64_t n,
+                                                    uint32_t cap, const uint32_t *padded_total,
+                                                    uint32_t *__restrict__ keys,
+                                                    uint32_t *__restrict__ vals) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wbase = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - lane;
+    if (wbase >= n) return;
+    if (*padded_total > cap) return;  // overflow: reported by gc_check, nothing emitted
+    const int q = find_req(item_base, n_req, wbase);
+    const int ntx = reqs[q].rp.ntx, twl = reqs[q].rp.tile_w_log2, thl = reqs[q].rp.tile_h_log2;
+    const uint32_t shift = eshift[q];
+    const int64_t r = wbase + lane;
+    const bool valid = r < n;
+    const uint32_t cnt = valid ? touched_r[r] : 0u;
+    const uint32_t off = valid ? offsets[r] : 0xffffffffu;
+    int tx0 = 0, ty0 = 0, twid = 1;
+    if (valid && cnt) {
+        int x0, x1, y0, y1;
+        unpack_rect(ranked[3 * r + 2], x0, x1, y0, y1);
+        tx0 = x0 >> twl;
+        ty0 = y0 >> thl;
+        twid = (x1 >> twl) - tx0 + 1;
+    }
+    const uint32_t start = __shfl_sync(0xffffffffu, off, 0);
+    const uint32_t end = __reduce_max_sync(0xffffffffu, valid ? off + cnt : 0u);
+    for (uint32_t e0 = start; e0 < end; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t o = __shfl_sync(0xffffffffu, off, owner + step);
+            if (o <= e) owner += step;
+        }
+        const uint32_t oo = __shfl_sync(0xffffffffu, off, owner);
+        const int otw = __shfl_sync(0xffffffffu, twid, owner);
+        const int otx = __shfl_sync(0xffffffffu, tx0, owner);
+        const int oty = __shfl_sync(0xffffffffu, ty0, owner);
+        if (e < end) {
+            const uint32_t k = e - oo;
+            const uint32_t ty = (uint32_t)oty + k / (uint32_t)otw;
+            const uint32_t tx = (uint32_t)otx + k % (uint32_t)otw;
+            keys[e + shift] = ty * (uint32_t)ntx + tx;
+            vals[e + shift] = (uint32_t)(wbase + owner);
+        }
+    }
+}
+
+// Pad keys after every request's entries (they sort to the end of the segment).
+__global__ void k_batch_pad_fill(const uint32_t *__restrict__ ebase, const uint32_t *__restrict__ ecount,
+                                 uint32_t cap, const uint32_t *padded_total, uint32_t *__restrict__ keys,
+                                 uint32_t *__restrict__ vals) {
+    if (*padded_total > cap) return;
+    const int q = blockIdx.x;
+    const uint32_t a = ebase[q] + ecount[q], b = ebase[q + 1];
+    for (uint32_t e = a + threadIdx.x; e < b; e += blockDim.x) {
+        keys[e] = 0xffffffffu;
+        vals[e] = 0u;
+    }
+}
+
+// One CTA per request: the request's tile ranges from its difference grid.
+__global__ void __launch_bounds__(1024) k_batch_ranges(const BatchReq *__restrict__ reqs,
+                                                       const int32_t *__restrict__ diff,
+                                                       const uint32_t *__restrict__ ebase,
+                                                       const uint32_t *padded_total, uint32_t cap,
+                                                       uint2 *__restrict__ ranges) {
+    extern __shared__ int32_t g[];
+    __shared__ uint32_t ws[33];
+    const BatchReq &R = reqs[blockIdx.x];
+    const int ntx = R.rp.ntx, nty = R.rp.nty;
+    const int gw = ntx + 1, gh = nty + 1, cells = gw * gh;
+    const int32_t *src = diff + R.diff_base;
+    for (int k = threadIdx.x; k < cells; k += blockDim.x) g[k] = src[k];
+    __syncthreads();
+    for (int r = threadIdx.x; r < gh; r += blockDim.x) {
+        int acc = 0;
+        for (int c = 0; c < gw; ++c) {
+            acc += g[r * gw + c];
+            g[r * gw + c] = acc;
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < gw; c += blockDim.x) {
+        int acc = 0;
+        for (int r = 0; r < gh; ++r) {
+            acc += g[r * gw + c];
+            g[r * gw + c] = acc;
+        }
+    }
+    __syncthreads();
+    const bool overflow = *padded_total > cap;
+    const int T = ntx * nty;
+    const int per = (T + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int start = (int)threadIdx.x * per;
+    uint32_t s = 0;
+    for (int q = 0; q < per; ++q) {
+        const int t = start + q;
+        if (t < T) s += (uint32_t)g[(t / ntx) * gw + (t % ntx)];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = ws[lane];
+        uint32_t wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        ws[lane] = wi - w;
+    }
+    __syncthreads();
+    uint32_t run = ebase[blockIdx.x] + ws[warp] + inc - s;
+    uint2 *out = ranges + R.tile_base;
+    for (int q = 0; q < per; ++q) {
+        const int t = start + q;
+        if (t < T) {
+            const uint32_t c = (uint32_t)g[(t / ntx) * gw + (t % ntx)];
+            out[t] = overflow ? make_uint2(0u, 0u) : make_uint2(run, run + c);
+            run += c;
+        }
+    }
+}
+
+// Persistent blend: each CTA repeatedly takes the next global tile from the work
+// counter (atomic ticket) and blends it with its request's parameters.
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) k_batch_blend_fwd(const BatchReq *__restrict__ reqs,
+                                                         const int64_t *__restrict__ tile_base, int n_req,
+                                                         int64_t n_tiles, const uint2 *__restrict__ ranges,
+                                                         const uint32_t *__restrict__ sorted_vals,
+                                                         const float4 *__restrict__ ranked,
+                                                         float *__restrict__ final_T,
+                                                         uint32_t *__restrict__ n_contrib,
+                                                         unsigned long long *counter) {
+    __shared__ float4 sA[256], sB[256], sC[256];
+    __shared__ long long s_tile;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long t = s_tile;
+        __syncthreads();
+        if (t >= n_tiles) break;
+        const int q = find_req(tile_base, n_req, t);
+        const BatchReq &R = reqs[q];
+        const int local = (int)(t - R.tile_base);
+        const int ntx = R.rp.ntx;
+        blend_fwd_tile<TW, TH, 1>(local % ntx, local / ntx, ranges[t], sorted_vals, ranked, R.cam.width,
+                                  R.cam.height, R.rp.bg[0], R.rp.bg[1], R.rp.bg[2], R.rp.membership, R.image,
+                                  final_T + R.pixel_base, n_contrib + R.pixel_base, nullptr, nullptr, sA, sB,
+                                  sC);
+    }
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) k_batch_blend_bwd(const BatchReq *__restrict__ reqs,
+                                                         const int64_t *__restrict__ tile_base, int n_req,
+                                                         int64_t n_tiles, const uint2 *__restrict__ ranges,
+                                                         const uint32_t *__restrict__ sorted_vals,
+                                                         const float4 *__restrict__ ranked,
+                                                         const uint32_t *__restrict__ offsets,
+                                                         const uint32_t *__restrict__ eshift,
+                                                         const float *__restrict__ final_T,
+                                                         const uint32_t *__restrict__ n_contrib,
+                                                         const float *const *__restrict__ dimgs,
+                                                         float *__restrict__ part, int32_t *__restrict__ rmax,
+                                                         unsigned long long *counter) {
+    __shared__ float4 sA[256], sB[256], sC[256], sD[256];
+    __shared__ float wpart[32 * 8 * 9];
+    __shared__ uint32_t s_last_max;
+    __shared__ long long s_tile;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long t = s_tile;
+        __syncthreads();
+        if (t >= n_tiles) break;
+        const int q = find_req(tile_base, n_req, t);
+        const BatchReq &R = reqs[q];
+        const int local = (int)(t - R.tile_base);
+        const int ntx = R.rp.ntx;
+        blend_bwd_tile<TW, TH, 1>(local % ntx, local / ntx, ranges[t], sorted_vals, ranked, offsets, eshift[q],
+                                  R.cam.width, R.cam.height, R.rp.tile_w_log2, R.rp.tile_h_log2, R.rp.bg[0],
+                                  R.rp.bg[1], R.rp.bg[2], R.rp.membership, final_T + R.pixel_base,
+                                  n_contrib + R.pixel_base, dimgs[q], part, rmax + t, sA, sB, sC, sD, wpart,
+                                  &s_last_max);
+        __syncthreads();
+    }
+}
+
+// One warp per rank: the Gaussian's partials over its tiles -> g2d at its item.
+__global__ void __launch_bounds__(256) k_batch_reduce(const float *__restrict__ part,
+                                                      const uint32_t *__restrict__ offsets,
+                                                      const uint32_t *__restrict__ touched_r,
+                                                      const float4 *__restrict__ ranked,
+                                                      const int32_t *__restrict__ rmax,
+                                                      const uint32_t *__restrict__ perm,
+                                                      const BatchReq *__restrict__ reqs,
+                                                      const int64_t *__restrict__ item_base, int n_req,
+                                                      const uint32_t *__restrict__ eshift, int64_t n,
+                                                      float *__restrict__ g2d) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= n) return;
+    const int q = find_req(item_base, n_req, r);
+    const BatchReq &R = reqs[q];
+    const uint32_t cnt = touched_r[r];
+    float acc[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[c] = 0.f;
+    if (cnt) {
+        const uint32_t off = offsets[r] + eshift[q];
+        int x0, x1, y0, y1;
+        unpack_rect(ranked[3 * r + 2], x0, x1, y0, y1);
+        const int twl = R.rp.tile_w_log2, thl = R.rp.tile_h_log2, ntx = R.rp.ntx;
+        const int tx0 = x0 >> twl, ty0 = y0 >> thl, twid = (x1 >> twl) - tx0 + 1;
+        const int32_t *rm = rmax + R.tile_base;
+        for (uint32_t j = lane; j < cnt; j += 32) {
+            const int t = (ty0 + (int)(j / (uint32_t)twid)) * ntx + tx0 + (int)(j % (uint32_t)twid);
+            if (r <= (int64_t)rm[t]) {
+                const float *p = part + (int64_t)(off + j) * 9;
+#pragma unroll
+                for (int c = 0; c < 9; ++c) acc[c] += p[c];
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        float x = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        acc[c] = x;
+    }
+    float mine = 0.f;
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+        if (lane == c) mine = acc[c];
+    if (lane < 9) g2d[9 * (int64_t)perm[r] + lane] = mine;
+}
+
+// Compact position of global Gaussian i in a selection, or -1.
+__device__ __forceinline__ int64_t sel_local(const Selection &s, int64_t i) {
+    for (int k = 0; k < s.n_ranges; ++k) {
+        const int64_t len = s.range_start[k + 1] - s.range_start[k];
+        if (i >= s.range_begin[k] && i < s.range_begin[k] + len) return s.range_start[k] + (i - s.range_begin[k]);
+    }
+    return -1;
+}
+
+// Thread per Gaussian: the chain rule for every request that sees it, summed in
+// request order; per-item motion terms for the group sums.
+__global__ void __launch_bounds__(128) k_batch_preprocess_bwd(GaussSrc G, const BatchReq *__restrict__ reqs,
+                                                              int n_req, int64_t n,
+                                                              const float *__restrict__ g2d,
+                                                              const uint32_t *__restrict__ touched,
+                                                              gc_grads out, int accumulate,
+                                                              float *__restrict__ mcontrib) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int K3 = 3 * G.K;
+    GradAcc acc;
+    for (int k = 0; k < 3; ++k) { acc.dmu[k] = 0.f; acc.dls[k] = 0.f; }
+    for (int k = 0; k < 4; ++k) acc.dq[k] = 0.f;
+    acc.dlogit = 0.f;
+    for (int k = 0; k < K3; ++k) acc.dsh[k] = 0.f;
+    const int g = G.group_id ? G.group_id[i] : 0;
+    for (int q = 0; q < n_req; ++q) {
+        const BatchReq &R = reqs[q];
+        if (R.n_sel == 0) continue;
+        const int64_t j = sel_local(R.sel, i);
+        if (j < 0) continue;
+        const int64_t item = R.item_base + j;
+        float m7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (touched[item] != 0) chain_rule(G, i, R.group_q, R.group_t, g, R.cam, R.rp, g2d + 9 * item, acc, m7);
+        if (mcontrib)
+            for (int k = 0; k < 7; ++k) mcontrib[7 * item + k] = m7[k];
+    }
+    auto put = [accumulate](float *p, float v) { *p = accumulate ? __fadd_rn(*p, v) : v; };
+    if (out.d_means) for (int k = 0; k < 3; ++k) put(&out.d_means[3 * i + k], acc.dmu[k]);
+    if (out.d_log_scales) for (int k = 0; k < 3; ++k) put(&out.d_log_scales[3 * i + k], acc.dls[k]);
+    if (out.d_quats) for (int k = 0; k < 4; ++k) put(&out.d_quats[4 * i + k], acc.dq[k]);
+    if (out.d_opacity_logits) put(&out.d_opacity_logits[i], acc.dlogit);
+    if (out.d_sh) for (int k = 0; k < K3; ++k) put(&out.d_sh[i * K3 + k], acc.dsh[k]);
+}
+
+constexpr int kBatchChunk = 256;
+
+// Per chunk of 256 items (one request), per group: the motion terms of the chunk's
+// members in item order.  Keyframe requests and padding contribute zero.
+__global__ void __launch_bounds__(128) k_batch_group_partial(const float *__restrict__ mcontrib,
+                                                             const int32_t *__restrict__ group_id,
+                                                             const BatchReq *__restrict__ reqs,
+                                                             const int64_t *__restrict__ item_base, int n_req,
+                                                             int n_groups, float *__restrict__ partial) {
+    __shared__ int s_gid[kBatchChunk];
+    __shared__ float s_val[kBatchChunk * 7];
+    const int64_t base = (int64_t)blockIdx.x * kBatchChunk;
+    const int q = find_req(item_base, n_req, base);
+    const BatchReq &R = reqs[q];
+    const int64_t j0 = base - R.item_base;
+    const bool use = R.frame >= 0;
+    for (int k = threadIdx.x; k < kBatchChunk; k += blockDim.x) {
+        const int64_t j = j0 + k;
+        s_gid[k] = (use && j < R.n_sel) ? (group_id ? group_id[sel_global(R.sel, j)] : 0) : -1;
+    }
+    for (int k = threadIdx.x; k < kBatchChunk * 7; k += blockDim.x) s_val[k] = mcontrib[base * 7 + k];
+    __syncthreads();
+    for (int gg = threadIdx.x; gg < n_groups; gg += blockDim.x) {
+        float a[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < kBatchChunk; ++k) {
+            if (s_gid[k] == gg) {
+#pragma unroll
+                for (int c = 0; c < 7; ++c) a[c] += s_val[7 * k + c];
+            }
+        }
+        float *o = partial + ((int64_t)blockIdx.x * n_groups + gg) * 7;
+#pragma unroll
+        for (int c = 0; c < 7; ++c) o[c] = a[c];
+    }
+}
+
+// Thread per (frame, group, component): requests of that frame in order, their chunks in order.
+__global__ void k_batch_group_final(const float *__restrict__ partial, const BatchReq *__restrict__ reqs,
+                                    const int64_t *__restrict__ item_base, int n_req, int n_frames,
+                                    int n_groups, int accumulate, float *__restrict__ d_gq,
+                                    float *__restrict__ d_gt) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_frames * n_groups * 7) return;
+    const int f = id / (n_groups * 7), rest = id - f * n_groups * 7;
+    const int g = rest / 7, c = rest - g * 7;
+    float acc = 0.f;
+    for (int q = 0; q < n_req; ++q) {
+        if (reqs[q].frame != f) continue;
+        const int64_t c0 = item_base[q] / kBatchChunk, c1 = item_base[q + 1] / kBatchChunk;
+        for (int64_t ch = c0; ch < c1; ++ch) acc += partial[(ch * n_groups + g) * 7 + c];
+    }
+    float *p = nullptr;
+    if (c < 4) {
+        if (d_gq) p = &d_gq[((int64_t)f * n_groups + g) * 4 + c];
+    } else if (d_gt) {
+        p = &d_gt[((int64_t)f * n_groups + g) * 3 + (c - 4)];
+    }
+    if (p) *p = accumulate ? __fadd_rn(*p, acc) : acc;
+}
+
+}  // namespace
+}  // namespace gc
+
+
+// --------------------------------------------------------------------------- host side
+
+struct BatchState {
+    bool valid = false;
+    bool bound = false;  // captured into a CUDA graph: buffers and request table are fixed
+    int n_req = 0, n_frames = 0, n_groups = 1;
+    bool has_motion = false;
+    int64_t n = 0;
+    int sh_degree = 0, n_layers = 0;
+    std::vector<gc::BatchReq> reqs;    // request table on the device (last upload)
+    std::vector<const float *> dimgs;  // dL/dimage pointers on the device (last upload)
+    gc::BatchReq *staging = nullptr;   // pinned upload buffers
+    size_t staging_cap = 0;
+    int64_t *staging_base = nullptr;
+    size_t staging_base_cap = 0;
+    const float **staging_dimg = nullptr;
+    size_t staging_dimg_cap = 0;
+    cudaEvent_t staged = nullptr;      // last upload from the pinned buffers
+    int64_t n_items = 0, n_tiles = 0, n_pixels = 0, diff_cells = 0, K_cap = 0;
+    int max_cells = 0, key_bits = 1, depth_buf = 0, tile_buf = 0;
+    bool k_exact = false;
+    gc_options opt{};
+    DevBuf reqs_dev, item_base, tile_base, seg_items, ebase, eshift, ecount, seg_entries, dimg_dev;
+    DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
+        final_T, n_contrib, diff, words, counter, scratch;
+    DevBuf part, g2d, mcontrib, rmax, gpartial;
+
+    ~BatchState() {
+        DevBuf *bufs[] = {&reqs_dev, &item_base, &tile_base, &seg_items, &ebase, &eshift, &ecount,
+                          &seg_entries, &dimg_dev, &rec, &ranked, &dkeys[0], &dkeys[1], &dvals[0],
+                          &dvals[1], &touched, &touched_r, &offsets, &tkeys[0], &tkeys[1], &tvals[0],
+                          &tvals[1], &ranges, &final_T, &n_contrib, &diff, &words, &counter, &scratch,
+                          &part, &g2d, &mcontrib, &rmax, &gpartial};
+        for (DevBuf *b : bufs) release(*b);
+        if (staging) cudaFreeHost(staging);
+        if (staging_base) cudaFreeHost(staging_base);
+        if (staging_dimg) cudaFreeHost(staging_dimg);
+        if (staged) cudaEventDestroy(staged);
+    }
+};
+
+namespace {
+
+template <class T>
+gc_status grow_pinned(gc_context *ctx, T *&p, size_t &cap, size_t count) {
+    if (count <= cap && p) return GC_OK;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaHostAlloc((void **)&p, count * sizeof(T), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, GC_ERR_OOM, "pinned staging allocation failed");
+    }
+    cap = count;
+    return GC_OK;
+}
+
+bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusActive;
+}
+
+// Buffer sizing: eager calls grow; a captured call or a state bound to a graph may
+// only use buffers that are already large enough.
+struct Sizer {
+    gc_context *ctx;
+    bool fixed;
+    gc_status st = GC_OK;
+    bool operator()(DevBuf &b, size_t bytes) {
+        if (st != GC_OK) return false;
+        if (b.p && bytes <= b.cap) return true;
+        if (fixed) {
+            st = fail(ctx, GC_ERR_STATE,
+                      "a captured or graph-bound batch needs larger buffers than its eager call sized");
+            return false;
+        }
+        const cudaError_t e = grow(b, bytes);
+        if (e != cudaSuccess) {
+            st = fail(ctx, e == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA, "batch buffer: %s",
+                      cudaGetErrorString(e));
+            return false;
+        }
+        return true;
+    }
+};
+
+gc_status build_table(gc_context *ctx, const gc_gaussians *g, const gc_motion *frames, int n_frames,
+                      int n_groups, const gc_request *reqs, int n_req, const gc_options &o,
+                      std::vector<gc::BatchReq> &tab, int64_t &items, int64_t &tiles, int64_t &pixels,
+                      int64_t &cells, int &max_cells, int &kbits) {
+    const int64_t T = gc::radix_tile_keys();
+    tab.assign(n_req, gc::BatchReq{});
+    items = tiles = pixels = cells = 0;
+    max_cells = 0;
+    kbits = 1;
+    for (int q = 0; q < n_req; ++q) {
+        const gc_request &rq = reqs[q];
+        const gc_camera *cam = &rq.camera;
+        if (!rq.image) return fail(ctx, GC_ERR_INVALID_ARG, "request %d has no image", q);
+        if (cam->width <= 0 || cam->height <= 0 || cam->width > 32768 || cam->height > 32768 ||
+            !(cam->fx > 0.f) || !(cam->fy > 0.f))
+            return fail(ctx, GC_ERR_INVALID_ARG, "request %d has an invalid camera", q);
+        if (rq.frame < -1 || rq.frame >= n_frames)
+            return fail(ctx, GC_ERR_INVALID_ARG, "request %d: frame %d out of range", q, rq.frame);
+        gc::BatchReq &R = tab[q];
+        memset(&R, 0, sizeof R);  // padding bytes too: tables are compared bytewise
+        R.cam.width = cam->width;
+        R.cam.height = cam->height;
+        R.cam.fx = cam->fx;
+        R.cam.fy = cam->fy;
+        R.cam.cx = cam->cx;
+        R.cam.cy = cam->cy;
+        memcpy(R.cam.R, cam->R, sizeof R.cam.R);
+        memcpy(R.cam.t, cam->t, sizeof R.cam.t);
+        memcpy(R.cam.campos, cam->campos, sizeof R.cam.campos);
+        R.rp.near_plane = o.near_plane;
+        R.rp.dilation = o.dilation;
+        R.rp.frustum_clamp = o.frustum_clamp;
+        memcpy(R.rp.bg, o.bg, sizeof R.rp.bg);
+        R.rp.tile_w = o.tile_w;
+        R.rp.tile_h = o.tile_h;
+        R.rp.tile_w_log2 = ilog2_exact(o.tile_w);
+        R.rp.tile_h_log2 = ilog2_exact(o.tile_h);
+        R.rp.ntx = (cam->width + o.tile_w - 1) / o.tile_w;
+        R.rp.nty = (cam->height + o.tile_h - 1) / o.tile_h;
+        R.rp.membership = o.membership;
+        int64_t n_sel = 0;
+        R.sel = make_selection(g, rq.layer_mask, n_sel);
+        R.n_sel = n_sel;
+        R.item_base = items;
+        items += (n_sel + T - 1) / T * T;
+        R.tile_base = tiles;
+        tiles += (int64_t)R.rp.ntx * R.rp.nty;
+        R.pixel_base = pixels;
+        pixels += (int64_t)cam->width * cam->height;
+        R.diff_base = cells;
+        const int c = (R.rp.ntx + 1) * (R.rp.nty + 1);
+        cells += c;
+        max_cells = std::max(max_cells, c);
+        kbits = std::max(kbits, bits_for((int64_t)R.rp.ntx * R.rp.nty - 1));
+        R.frame = rq.frame;
+        R.n_groups = 1;
+        if (rq.frame >= 0) {
+            R.group_q = frames[rq.frame].q;
+            R.group_t = frames[rq.frame].t;
+            R.n_groups = n_groups;
+        }
+        R.image = rq.image;
+    }
+    if ((size_t)max_cells * 4 > 200 * 1024)
+        return fail(ctx, GC_ERR_UNSUPPORTED, "image too large for the batched tile-range kernel");
+    if (items > 0x7FFFFFFFll) return fail(ctx, GC_ERR_INVALID_ARG, "more than 2^31 - 1 (request, Gaussian) pairs");
+    return GC_OK;
+}
+
+}  // namespace
+
+void batch_invalidate(gc_saved &S) {
+    if (S.batch) S.batch->valid = false;
+}
+
+gc_status batch_check(gc_context *ctx, const gc_saved &S) {
+    if (!S.batch || !S.batch->valid || !S.batch->words.p) return GC_OK;
+    const BatchState &B = *S.batch;
+    uint32_t w[3];
+    GC_CUDA(ctx, cudaMemcpy(w, B.words.p, 12, cudaMemcpyDeviceToHost));
+    if (w[1]) {
+        GC_CUDA(ctx, cudaMemset(static_cast<uint32_t *>(B.words.p) + 1, 0, 4));
+        return fail(ctx, GC_ERR_TIMEOUT, "a bounded device wait ran out (error word %#x)", w[1]);
+    }
+    if (!B.k_exact && (int64_t)w[2] > B.K_cap)
+        return fail(ctx, GC_ERR_CAPACITY, "batch needs %u keys (padded), capacity %lld", w[2], (long long)B.K_cap);
+    return GC_OK;
+}
+
+extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians *g,
+                                             const gc_motion *frames, int32_t n_frames,
+                                             const gc_request *reqs, int32_t n_req, gc_saved *saved,
+                                             void *stream) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    if (!reqs || n_req <= 0) return fail(ctx, GC_ERR_INVALID_ARG, "no requests");
+    if (n_frames < 0 || (n_frames > 0 && !frames)) return fail(ctx, GC_ERR_INVALID_ARG, "bad motion frames");
+    gc::GaussSrc src;
+    gc_status st = make_source(ctx, g, n_frames > 0 ? &frames[0] : nullptr, src);
+    if (st != GC_OK) return st;
+    src.group_id = g->group_id;  // motion applies per request
+    const int n_groups = n_frames > 0 ? frames[0].n_groups : 1;
+    for (int f = 0; f < n_frames; ++f)
+        if (frames[f].n_groups != n_groups || !frames[f].q || !frames[f].t)
+            return fail(ctx, GC_ERR_INVALID_ARG, "motion frames must share n_groups and have q, t");
+    const gc_options &o = ctx->opt;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool capturing = stream_capturing(s);
+    if (capturing && o.key_capacity <= 0)
+        return fail(ctx, GC_ERR_INVALID_ARG, "graph capture needs a fixed key_capacity");
+    gc_saved &S = saved ? *saved : ctx->internal;
+    if (!S.batch) S.batch = std::make_shared<BatchState>();
+    BatchState &B = *S.batch;
+    const int64_t T = gc::radix_tile_keys();
+
+    std::vector<gc::BatchReq> tab;
+    int64_t items, tiles, pixels, cells;
+    int max_cells, kbits;
+    if ((st = build_table(ctx, g, frames, n_frames, n_groups, reqs, n_req, o, tab, items, tiles, pixels, cells,
+                          max_cells, kbits)) != GC_OK)
+        return st;
+    const bool same_table = B.reqs_dev.p && (int)B.reqs.size() == n_req &&
+                            memcmp(B.reqs.data(), tab.data(), sizeof(gc::BatchReq) * n_req) == 0;
+    const bool fixed = capturing || B.bound;
+    if (fixed && !same_table)
+        return fail(ctx, GC_ERR_STATE,
+                    capturing ? "a captured batch must repeat the requests of the preceding eager call"
+                              : "this saved state is bound to a CUDA graph; use the same requests or another state");
+    if (fixed && (o.key_capacity != B.K_cap || memcmp(&o, &B.opt, sizeof o) != 0))
+        return fail(ctx, GC_ERR_STATE, "options changed since the batch was bound to a graph");
+    S.valid = false;  // the single-frame part of this state no longer describes the last forward
+    B.valid = false;
+    B.n_req = n_req;
+    B.n_frames = n_frames;
+    B.n_groups = n_groups;
+    B.has_motion = n_frames > 0;
+    B.n = g->n;
+    B.sh_degree = g->sh_degree;
+    B.n_layers = g->n_layers;
+    B.n_items = items;
+    B.n_tiles = tiles;
+    B.n_pixels = pixels;
+    B.diff_cells = cells;
+    B.max_cells = max_cells;
+    B.key_bits = kbits;
+    B.opt = o;
+
+    Sizer need{ctx, fixed};
+    need(B.reqs_dev, sizeof(gc::BatchReq) * n_req);
+    need(B.item_base, 8 * (n_req + 1));
+    need(B.tile_base, 8 * (n_req + 1));
+    need(B.seg_items, 4 * (n_req + 1));
+    const int64_t ni = items > 0 ? items : 1;
+    need(B.rec, (size_t)ni * 48);
+    need(B.ranked, (size_t)ni * 48);
+    for (int b = 0; b < 2; ++b) {
+        need(B.dkeys[b], (size_t)ni * 4);
+        need(B.dvals[b], (size_t)ni * 4);
+    }
+    need(B.touched, (size_t)ni * 4);
+    need(B.touched_r, (size_t)ni * 4);
+    need(B.offsets, (size_t)(ni + 1) * 4);
+    need(B.ebase, 4 * (n_req + 1));
+    need(B.eshift, 4 * (n_req + 1));
+    need(B.ecount, 4 * (n_req + 1));
+    need(B.seg_entries, 4 * (n_req + 1));
+    need(B.ranges, (size_t)tiles * 8);
+    need(B.final_T, (size_t)pixels * 4);
+    need(B.n_contrib, (size_t)pixels * 4);
+    need(B.diff, (size_t)cells * 4);
+    need(B.counter, 16);
+    const bool fresh_words = !B.words.p;
+    need(B.words, 64);
+    need(B.scratch, 4 * std::max(gc::radix_scratch_words(ni), gc::scan_partials_size(ni)));
+    if (need.st != GC_OK) return need.st;
+    uint32_t *words = B.words.as<uint32_t>();  // [0] unpadded keys, [1] errors, [2] padded keys
+    if (fresh_words) GC_CUDA(ctx, cudaMemsetAsync(B.words.p, 0, 64, s));
+
+    if (!same_table) {  // upload the request table and the base arrays (eager calls only)
+        if (B.staged) GC_CUDA(ctx, cudaEventSynchronize(B.staged));
+        else GC_CUDA(ctx, cudaEventCreateWithFlags(&B.staged, cudaEventDisableTiming));
+        if ((st = grow_pinned(ctx, B.staging, B.staging_cap, (size_t)n_req)) != GC_OK) return st;
+        if ((st = grow_pinned(ctx, B.staging_base, B.staging_base_cap, (size_t)3 * (n_req + 1))) != GC_OK) return st;
+        memcpy(B.staging, tab.data(), sizeof(gc::BatchReq) * n_req);
+        int64_t *ib = B.staging_base, *tb = B.staging_base + (n_req + 1);
+        uint32_t *si = reinterpret_cast<uint32_t *>(B.staging_base + 2 * (n_req + 1));
+        for (int q = 0; q < n_req; ++q) {
+            ib[q] = tab[q].item_base;
+            tb[q] = tab[q].tile_base;
+            si[q] = (uint32_t)(tab[q].item_base / T);
+        }
+        ib[n_req] = items;
+        tb[n_req] = tiles;
+        si[n_req] = (uint32_t)(items / T);
+        GC_CUDA(ctx, cudaMemcpyAsync(B.reqs_dev.p, B.staging, sizeof(gc::BatchReq) * n_req,
+                                     cudaMemcpyHostToDevice, s));
+        GC_CUDA(ctx, cudaMemcpyAsync(B.item_base.p, ib, 8 * (n_req + 1), cudaMemcpyHostToDevice, s));
+        GC_CUDA(ctx, cudaMemcpyAsync(B.tile_base.p, tb, 8 * (n_req + 1), cudaMemcpyHostToDevice, s));
+        GC_CUDA(ctx, cudaMemcpyAsync(B.seg_items.p, si, 4 * (n_req + 1), cudaMemcpyHostToDevice, s));
+        GC_CUDA(ctx, cudaEventRecord(B.staged, s));
+        B.reqs = tab;
+    }
+    const bool prof = !capturing;
+    auto mark = [&](int stage) -> cudaError_t { return prof ? prof_mark(ctx, s, stage) : cudaSuccess; };
+
+    GC_CUDA(ctx, mark(GC_STAGE_PREPROCESS));
+    GC_CUDA(ctx, cudaMemsetAsync(B.diff.p, 0, (size_t)cells * 4, s));
+    const gc::BatchReq *rq_dev = B.reqs_dev.as<gc::BatchReq>();
+    const int64_t *ib_dev = B.item_base.as<int64_t>(), *tb_dev = B.tile_base.as<int64_t>();
+    uint32_t *scratch = B.scratch.as<uint32_t>();
+    if (items > 0) {
+        gc::k_batch_preprocess<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(
+            src, rq_dev, ib_dev, n_req, items, B.rec.as<float4>(), B.dkeys[0].as<uint32_t>(),
+            B.dvals[0].as<uint32_t>(), B.touched.as<uint32_t>(), B.diff.as<int32_t>());
+        gc::note_launches(1);
+        GC_CUDA(ctx, cudaGetLastError());
+        GC_CUDA(ctx, mark(GC_STAGE_DEPTH_SORT));
+        uint32_t *dk[2] = {B.dkeys[0].as<uint32_t>(), B.dkeys[1].as<uint32_t>()};
+        uint32_t *dv[2] = {B.dvals[0].as<uint32_t>(), B.dvals[1].as<uint32_t>()};
+        GC_CUDA(ctx, gc::radix_sort_pairs(dk, dv, items, nullptr, 32, scratch, &B.depth_buf, s, words + 1, true,
+                                          B.seg_items.as<uint32_t>(), n_req));
+        GC_CUDA(ctx, mark(GC_STAGE_SCAN));
+        GC_CUDA(ctx, gc::launch_rank_gather(dv[B.depth_buf], B.rec.as<float4>(), B.touched.as<uint32_t>(), items,
+                                            B.ranked.as<float4>(), B.touched_r.as<uint32_t>(), s));
+        GC_CUDA(ctx, gc::launch_exclusive_scan(B.touched_r.as<uint32_t>(), B.offsets.as<uint32_t>(), items, words,
+                                               scratch, s));
+    } else {
+        GC_CUDA(ctx, cudaMemsetAsync(words, 0, 4, s));
+    }
+    const uint32_t cap_hint = o.key_capacity > 0 ? (uint32_t)o.key_capacity : 0xFFFFFFFFu;
+    gc::k_batch_entry_bases<<<1, 1, 0, s>>>(B.offsets.as<uint32_t>(), words, ib_dev, n_req, items, (uint32_t)T,
+                                            cap_hint, B.ebase.as<uint32_t>(), B.eshift.as<uint32_t>(),
+                                            B.ecount.as<uint32_t>(), B.seg_entries.as<uint32_t>(), words);
+    gc::note_launches(1);
+    GC_CUDA(ctx, cudaGetLastError());
+    int64_t K;
+    if (o.key_capacity > 0) {
+        K = o.key_capacity;
+        B.k_exact = false;
+    } else {
+        GC_CUDA(ctx, cudaMemcpyAsync(ctx->host_word, words + 2, 4, cudaMemcpyDeviceToHost, s));
+        GC_CUDA(ctx, cudaStreamSynchronize(s));
+        K = ctx->host_word[0];
+        if (K >= 0xFFFFFFFFll) return fail(ctx, GC_ERR_CAPACITY, "batch needs more than 2^32 - 1 keys");
+        B.k_exact = true;
+    }
+    const int64_t kk = K > 0 ? K : 1;
+    for (int b = 0; b < 2; ++b) {
+        need(B.tkeys[b], (size_t)kk * 4 + 16);
+        need(B.tvals[b], (size_t)kk * 4 + 16);
+    }
+    need(B.scratch, 4 * std::max(gc::radix_scratch_words(kk), gc::scan_partials_size(ni)));
+    if (need.st != GC_OK) return need.st;
+    scratch = B.scratch.as<uint32_t>();
+    B.K_cap = K;
+    if (K > 0 && items > 0) {
+        GC_CUDA(ctx, mark(GC_STAGE_EMIT));
+        const int64_t threads = ((items + 31) / 32) * 32;
+        gc::k_batch_emit<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+            B.ranked.as<float4>(), B.offsets.as<uint32_t>(), B.touched_r.as<uint32_t>(), rq_dev, ib_dev, n_req,
+            B.eshift.as<uint32_t>(), items, (uint32_t)K, words + 2, B.tkeys[0].as<uint32_t>(),
+            B.tvals[0].as<uint32_t>());
+        gc::note_launches(1);
+        gc::k_batch_pad_fill<<<n_req, 256, 0, s>>>(B.ebase.as<uint32_t>(), B.ecount.as<uint32_t>(), (uint32_t)K,
+                                                   words + 2, B.tkeys[0].as<uint32_t>(), B.tvals[0].as<uint32_t>());
+        gc::note_launches(1);
+        GC_CUDA(ctx, cudaGetLastError());
+        GC_CUDA(ctx, mark(GC_STAGE_TILE_SORT));
+        uint32_t *tk[2] = {B.tkeys[0].as<uint32_t>(), B.tkeys[1].as<uint32_t>()};
+        uint32_t *tv[2] = {B.tvals[0].as<uint32_t>(), B.tvals[1].as<uint32_t>()};
+        GC_CUDA(ctx, gc::radix_sort_pairs(tk, tv, K, words + 2, kbits, scratch, &B.tile_buf, s, words + 1, false,
+                                          B.seg_entries.as<uint32_t>(), n_req));
+    }
+    GC_CUDA(ctx, mark(GC_STAGE_RANGES));
+    {
+        const size_t smem = (size_t)max_cells * 4;
+        if (smem > 48 * 1024 && !capturing)
+            GC_CUDA(ctx, cudaFuncSetAttribute(gc::k_batch_ranges, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        gc::k_batch_ranges<<<n_req, 1024, smem, s>>>(rq_dev, B.diff.as<int32_t>(), B.ebase.as<uint32_t>(), words + 2,
+                                                     (uint32_t)K, B.ranges.as<uint2>());
+        gc::note_launches(1);
+        GC_CUDA(ctx, cudaGetLastError());
+    }
+    GC_CUDA(ctx, mark(GC_STAGE_BLEND));
+    GC_CUDA(ctx, cudaMemsetAsync(B.counter.p, 0, 8, s));
+    {
+        const uint32_t *sv = (K > 0 && items > 0) ? B.tvals[B.tile_buf].as<uint32_t>() : nullptr;
+        const unsigned grid = (unsigned)std::min<int64_t>(std::max<int64_t>(tiles, 1), 148 * 6);
+        unsigned long long *ctr = B.counter.as<unsigned long long>();
+#define GC_BB_ARGS rq_dev, tb_dev, n_req, tiles, B.ranges.as<uint2>(), sv, B.ranked.as<float4>(), \
+                   B.final_T.as<float>(), B.n_contrib.as<uint32_t>(), ctr
+        if (o.tile_w == 16) gc::k_batch_blend_fwd<16, 16><<<grid, 256, 0, s>>>(GC_BB_ARGS);
+        else if (o.tile_w == 8) gc::k_batch_blend_fwd<8, 32><<<grid, 256, 0, s>>>(GC_BB_ARGS);
+        else gc::k_batch_blend_fwd<32, 8><<<grid, 256, 0, s>>>(GC_BB_ARGS);
+#undef GC_BB_ARGS
+        gc::note_launches(1);
+        GC_CUDA(ctx, cudaGetLastError());
+    }
+    GC_CUDA(ctx, mark(-1));
+    if (capturing) B.bound = true;
+    B.valid = true;
+    ctx->last = &S;
+    return GC_OK;
+}
+
+extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *saved,
+                                              const gc_gaussians *g, const gc_motion *frames,
+                                              int32_t n_frames, const float *const *dL_dimages,
+                                              int32_t accumulate, gc_grads *out, void *stream) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    if (!dL_dimages || !out) return fail(ctx, GC_ERR_INVALID_ARG, "dL_dimages or grads is NULL");
+    if (accumulate != 0 && accumulate != 1) return fail(ctx, GC_ERR_INVALID_ARG, "accumulate must be 0 or 1");
+    const gc_saved &S = saved ? *saved : ctx->internal;
+    if (!S.batch || !S.batch->valid) return fail(ctx, GC_ERR_STATE, "no batched forward recorded");
+    BatchState &B = *S.batch;
+    if (n_frames < 0 || (n_frames > 0 && !frames)) return fail(ctx, GC_ERR_INVALID_ARG, "bad motion frames");
+    gc::GaussSrc src;
+    gc_status st = make_source(ctx, g, n_frames > 0 ? &frames[0] : nullptr, src);
+    if (st != GC_OK) return st;
+    src.group_id = g->group_id;
+    if (g->n != B.n || g->sh_degree != B.sh_degree || g->n_layers != B.n_layers)
+        return fail(ctx, GC_ERR_STATE, "the Gaussian set differs from the one of the batched forward");
+    if (n_frames != B.n_frames || (n_frames > 0 && frames[0].n_groups != B.n_groups))
+        return fail(ctx, GC_ERR_STATE, "the motion frames differ from the forward's");
+    const int n_req = B.n_req;
+    for (int q = 0; q < n_req; ++q)
+        if (!dL_dimages[q]) return fail(ctx, GC_ERR_INVALID_ARG, "dL_dimages[%d] is NULL", q);
+    for (int q = 0; q < n_req; ++q) {
+        const int f = B.reqs[q].frame;
+        if (f >= 0 && (B.reqs[q].group_q != frames[f].q || B.reqs[q].group_t != frames[f].t))
+            return fail(ctx, GC_ERR_STATE, "the motion frames differ from the forward's");
+    }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool capturing = stream_capturing(s);
+    const bool fixed = capturing || B.bound;
+    const bool same_dimg = B.dimg_dev.p && (int)B.dimgs.size() == n_req &&
+                           std::equal(B.dimgs.begin(), B.dimgs.end(), dL_dimages);
+    if (fixed && !same_dimg)
+        return fail(ctx, GC_ERR_STATE, "a graph-bound batch backward must use the dL_dimages of its eager call");
+    const int64_t items = B.n_items, ni = items > 0 ? items : 1, K = B.K_cap > 0 ? B.K_cap : 1;
+    const int G = B.has_motion ? B.n_groups : 0;
+    const int64_t chunks = items / gc::kBatchChunk;
+    Sizer need{ctx, fixed};
+    need(B.dimg_dev, sizeof(float *) * n_req);
+    need(B.part, (size_t)K * 9 * 4 + 64);
+    need(B.g2d, (size_t)ni * 9 * 4);
+    need(B.mcontrib, (size_t)ni * 7 * 4);
+    need(B.rmax, (size_t)std::max<int64_t>(B.n_tiles, 1) * 4);
+    if (G) need(B.gpartial, (size_t)std::max<int64_t>(chunks, 1) * G * 7 * 4);
+    if (need.st != GC_OK) return need.st;
+    if (!same_dimg) {
+        if (B.staged) GC_CUDA(ctx, cudaEventSynchronize(B.staged));
+        else GC_CUDA(ctx, cudaEventCreateWithFlags(&B.staged, cudaEventDisableTiming));
+        if ((st = grow_pinned(ctx, B.staging_dimg, B.staging_dimg_cap, (size_t)n_req)) != GC_OK) return st;
+        for (int q = 0; q < n_req; ++q) B.staging_dimg[q] = dL_dimages[q];
+        GC_CUDA(ctx, cudaMemcpyAsync(B.dimg_dev.p, B.staging_dimg, sizeof(float *) * n_req, cudaMemcpyHostToDevice, s));
+        GC_CUDA(ctx, cudaEventRecord(B.staged, s));
+        B.dimgs.assign(dL_dimages, dL_dimages + n_req);
+    }
+    const bool prof = !capturing;
+    auto mark = [&](int stage) -> cudaError_t { return prof ? prof_mark(ctx, s, stage) : cudaSuccess; };
+    const gc::BatchReq *rq_dev = B.reqs_dev.as<gc::BatchReq>();
+    const int64_t *ib_dev = B.item_base.as<int64_t>(), *tb_dev = B.tile_base.as<int64_t>();
+
+    GC_CUDA(ctx, mark(GC_STAGE_BLEND_BWD));
+    if (G) GC_CUDA(ctx, cudaMemsetAsync(B.mcontrib.p, 0, (size_t)ni * 7 * 4, s));
+    GC_CUDA(ctx, cudaMemsetAsync(B.counter.p, 0, 8, s));
+    {
+        const uint32_t *sv = (B.K_cap > 0 && items > 0) ? B.tvals[B.tile_buf].as<uint32_t>() : nullptr;
+        const unsigned grid = (unsigned)std::min<int64_t>(std::max<int64_t>(B.n_tiles, 1), 148 * 4);
+        unsigned long long *ctr = B.counter.as<unsigned long long>();
+#define GC_BB_ARGS rq_dev, tb_dev, n_req, B.n_tiles, B.ranges.as<uint2>(), sv, B.ranked.as<float4>(),            \
+                   B.offsets.as<uint32_t>(), B.eshift.as<uint32_t>(), B.final_T.as<float>(),                     \
+                   B.n_contrib.as<uint32_t>(), B.dimg_dev.as<const float *>(), B.part.as<float>(),              \
+                   B.rmax.as<int32_t>(), ctr
+        if (B.opt.tile_w == 16) gc::k_batch_blend_bwd<16, 16><<<grid, 256, 0, s>>>(GC_BB_ARGS);
+        else if (B.opt.tile_w == 8) gc::k_batch_blend_bwd<8, 32><<<grid, 256, 0, s>>>(GC_BB_ARGS);
+        else gc::k_batch_blend_bwd<32, 8><<<grid, 256, 0, s>>>(GC_BB_ARGS);
+#undef GC_BB_ARGS
+        gc::note_launches(1);
+        GC_CUDA(ctx, cudaGetLastError());
+    }
+    if (items > 0) {
+        GC_CUDA(ctx, mark(GC_STAGE_REDUCE));
+        gc::k_batch_reduce<<<(unsigned)((items * 32 + 255) / 256), 256, 0, s>>>(
+            B.part.as<float>(), B.offsets.as<uint32_t>(), B.touched_r.as<uint32_t>(), B.ranked.as<float4>(),
+            B.rmax.as<int32_t>(), B.dvals[B.depth_buf].as<uint32_t>(), rq_dev, ib_dev, n_req,
+            B.eshift.as<uint32_t>(), items, B.g2d.as<float>());
+        gc::note_launches(1);
+        GC_CUDA(ctx, cudaGetLastError());
+    }
+    GC_CUDA(ctx, mark(GC_STAGE_PREPROCESS_BWD));
+    if (g->n > 0) {
+        gc::k_batch_preprocess_bwd<<<(unsigned)((g->n + 127) / 128), 128, 0, s>>>(
+            src, rq_dev, n_req, g->n, B.g2d.as<float>(), B.touched.as<uint32_t>(), *out, accumulate,
+            G ? B.mcontrib.as<float>() : nullptr);
+        gc::note_launches(1);
+        GC_CUDA(ctx, cudaGetLastError());
+    }
+    if (G) {
+        GC_CUDA(ctx, mark(GC_STAGE_GROUP_REDUCE));
+        if (chunks > 0) {
+            gc::k_batch_group_partial<<<(unsigned)chunks, 128, 0, s>>>(B.mcontrib.as<float>(), g->group_id, rq_dev,
+                                                                       ib_dev, n_req, G, B.gpartial.as<float>());
+            gc::note_launches(1);
+        }
+        const int nt = B.n_frames * G * 7;
+        gc::k_batch_group_final<<<(nt + 127) / 128, 128, 0, s>>>(B.gpartial.as<float>(), rq_dev, ib_dev, n_req,
+                                                                B.n_frames, G, accumulate, out->d_group_q,
+                                                                out->d_group_t);
+        gc::note_launches(1);
+        GC_CUDA(ctx, cudaGetLastError());
+    }
+    GC_CUDA(ctx, mark(-1));
+    return GC_OK;
+}

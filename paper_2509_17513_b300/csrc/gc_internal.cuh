@@ -102,10 +102,14 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
 // keys_out = false: the last pass writes only the values (the sorted keys are not kept).
 // Buffers must hold n_max rounded up to 4 elements (tiles are copied in 16-byte units).
 // A bounded wait that runs out sets kErrTimeout in *err (device word).
+// Segmented mode (seg_block0 != NULL, device array of n_seg + 1 block indices in units
+// of radix_tile_keys()): every segment is sorted on its own and stays in place.
 size_t radix_scratch_words(int64_t n_max);
+int radix_tile_keys();
 cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
                              const uint32_t *n_dev, int end_bit, uint32_t *scratch, int *out_buf,
-                             cudaStream_t st, uint32_t *err, bool keys_out = true);
+                             cudaStream_t st, uint32_t *err, bool keys_out = true,
+                             const uint32_t *seg_block0 = nullptr, int n_seg = 0);
 
 // Emit (tile key, rank) for every tile of every visible Gaussian, in rank order.
 // Entries at positions >= cap are dropped (fixed-capacity mode reports the overflow).

@@ -189,6 +189,26 @@ __device__ __forceinline__ int64_t device_count(const uint32_t *n_dev, int64_t n
     return n < n_max ? n : n_max;
 }
 
+// Index of (digit d, block b) in the histogram array.  Without segments the layout
+// is digit-major over all blocks.  With segments (seg_block0: S+1 nondecreasing block
+// indices, segment s = blocks [seg_block0[s], seg_block0[s+1])), each segment owns a
+// contiguous digit-major region in segment order, so one exclusive scan over the
+// array yields offsets that keep every segment within its own range; blocks past the
+// last segment hold zero counts after all segments.
+__device__ __forceinline__ int64_t count_index(uint32_t d, int b, int nblocks, const uint32_t *seg_block0,
+                                               int n_seg) {
+    if (!seg_block0) return (int64_t)d * nblocks + b;
+    const int total = (int)seg_block0[n_seg];
+    if (b >= total) return (int64_t)256 * b + d;
+    int lo = 0, hi = n_seg - 1;  // last segment with seg_block0[s] <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int)seg_block0[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const int b0 = (int)seg_block0[lo], nb = (int)seg_block0[lo + 1] - b0;
+    return (int64_t)256 * b0 + (int64_t)d * nb + (b - b0);
+}
+
 // Peers of this lane: the lanes of the warp whose digit equals this lane's, among the
 // lanes in `valid` (warp multisplit by one ballot per digit bit).
 __device__ __forceinline__ uint32_t digit_peers(uint32_t d, int bits, uint32_t valid) {
@@ -210,7 +230,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
                                                              const uint32_t *n_dev, int64_t n_max,
                                                              int shift, uint32_t mask,
                                                              uint32_t *__restrict__ counts,
-                                                             int nblocks) {
+                                                             int nblocks, const uint32_t *seg_block0,
+                                                             int n_seg) {
     __shared__ uint32_t wh[kWarps][256];
     const int warp = threadIdx.x >> 5;
     for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0;
@@ -237,7 +258,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
     uint32_t tot = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) tot += wh[w][threadIdx.x];
-    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = tot;
+    counts[count_index(threadIdx.x, blockIdx.x, nblocks, seg_block0, n_seg)] = tot;
 }
 
 // Stable scatter, persistent: each CTA walks tiles t = blockIdx.x, + gridDim.x, ...
@@ -251,7 +272,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *n_dev,
     int64_t n_max, int shift, uint32_t mask, const uint32_t *__restrict__ scanned, int nblocks,
-    uint32_t *err) {
+    uint32_t *err, const uint32_t *seg_block0, int n_seg) {
     __shared__ __align__(128) uint32_t sk[2][kSortTile];
     __shared__ __align__(128) uint32_t sv[2][kSortTile];
     __shared__ uint32_t wcnt[kWarps][256];
@@ -333,7 +354,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
             uint32_t tot;
             const uint32_t st = block_exclusive_scan<kSortThreads>(s, ws, &tot);
             dstart[d] = st;
-            gbase[d] = scanned[(int64_t)d * nblocks + t];
+            gbase[d] = scanned[count_index(d, t, nblocks, seg_block0, n_seg)];
         }
         __syncthreads();
 #pragma unroll
@@ -384,6 +405,8 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
     return cudaGetLastError();
 }
 
+int radix_tile_keys() { return kSortTile; }
+
 size_t radix_scratch_words(int64_t n_max) {
     int64_t nb = (n_max + kSortTile - 1) / kSortTile;
     if (nb < 1) nb = 1;
@@ -392,7 +415,8 @@ size_t radix_scratch_words(int64_t n_max) {
 
 cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
                              const uint32_t *n_dev, int end_bit, uint32_t *scratch, int *out_buf,
-                             cudaStream_t st, uint32_t *err, bool keys_out) {
+                             cudaStream_t st, uint32_t *err, bool keys_out,
+                             const uint32_t *seg_block0, int n_seg) {
     int cur = 0;
     if (n_max <= 0 || end_bit <= 0) {
         *out_buf = 0;
@@ -409,7 +433,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
         const int bits = (end_bit - shift + (passes - pass) - 1) / (passes - pass);
         const uint32_t mask = (1u << bits) - 1u;
         k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(keys[cur], n_dev, n_max, shift, mask, counts,
-                                                       nblocks);
+                                                       nblocks, seg_block0, n_seg);
         note_launches(1);
         cudaError_t e = launch_exclusive_scan(counts, counts, (int64_t)256 * nblocks, nullptr,
                                               partials, st);
@@ -418,7 +442,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
         k_radix_scatter<<<grid, kSortThreads, 0, st>>>(keys[cur], vals[cur],
                                                        (last && !keys_out) ? nullptr : keys[cur ^ 1],
                                                        vals[cur ^ 1], n_dev, n_max, shift, mask,
-                                                       counts, nblocks, err);
+                                                       counts, nblocks, err, seg_block0, n_seg);
         note_launches(1);
         cur ^= 1;
         shift += bits;

@@ -223,6 +223,72 @@ class Renderer:
         check(st, self.ctx)
         return grads
 
+    # ---- batched requests -------------------------------------------------------------
+
+    def batch_forward(self, gs: GaussianSet, frames: list, requests: list, saved: Saved | None = None,
+                      outs: list | None = None, stream=None) -> list:
+        """Renders every request (camera, frame index or -1, layer mask) of one Gaussian set
+        in one batched pass; returns one (3, H, W) image per request."""
+        dev = f"cuda:{self.device}"
+        n = len(requests)
+        reqs = (_abi.Request * n)()
+        if outs is None:
+            outs = []
+            for cam, _, _ in requests:
+                outs.append(torch.empty((3, int(cam.height), int(cam.width)), dtype=torch.float32, device=dev))
+        for q, (cam, frame, mask) in enumerate(requests):
+            reqs[q].camera = camera_struct(cam)
+            reqs[q].frame = int(frame)
+            reqs[q].layer_mask = int(mask) & 0xFFFFFFFF
+            reqs[q].image = outs[q].data_ptr()
+        fr = (_abi.Motion * max(len(frames), 1))()
+        for f, m in enumerate(frames):
+            fr[f] = m.struct
+        st = lib().gc_render_batch_forward(self.ctx, C.byref(gs.struct), fr if frames else None, len(frames),
+                                           reqs, n, saved.handle if saved is not None else None,
+                                           _stream(stream))
+        check(st, self.ctx)
+        return outs
+
+    def batch_grads(self, gs: GaussianSet, frames: list) -> dict:
+        """Zeroed gradient buffers for batch_backward."""
+        dev = f"cuda:{self.device}"
+        K = (gs.sh_degree + 1) ** 2
+        n = gs.n
+        g = {"means": torch.zeros((n, 3), device=dev), "log_scales": torch.zeros((n, 3), device=dev),
+             "quats": torch.zeros((n, 4), device=dev), "opacity_logits": torch.zeros(n, device=dev),
+             "sh": torch.zeros((n, K, 3), device=dev)}
+        if frames:
+            G = frames[0].q.shape[0]
+            g["group_q"] = torch.zeros((len(frames), G, 4), device=dev)
+            g["group_t"] = torch.zeros((len(frames), G, 3), device=dev)
+        return g
+
+    def batch_backward(self, saved: Saved | None, gs: GaussianSet, frames: list, dL_dimages: list,
+                       grads: dict | None = None, accumulate: bool = False, stream=None) -> dict:
+        """Gradients of a batched forward, summed over its requests in order; the motion
+        gradients are per (frame, group).  accumulate=True adds into `grads`."""
+        if grads is None:
+            grads = self.batch_grads(gs, frames)
+        g = self._grads_struct(grads)
+        dls = [d.contiguous() for d in dL_dimages]
+        ptrs = (C.c_void_p * len(dls))(*[d.data_ptr() for d in dls])
+        fr = (_abi.Motion * max(len(frames), 1))()
+        for f, m in enumerate(frames):
+            fr[f] = m.struct
+        st = lib().gc_render_batch_backward(self.ctx, saved.handle if saved is not None else None,
+                                            C.byref(gs.struct), fr if frames else None, len(frames), ptrs,
+                                            1 if accumulate else 0, C.byref(g), _stream(stream))
+        check(st, self.ctx)
+        return grads
+
+    @staticmethod
+    def _grads_struct(grads: dict) -> _abi.Grads:
+        g = _abi.Grads()
+        for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "group_q", "group_t"):
+            setattr(g, "d_" + k, grads[k].data_ptr() if k in grads else None)
+        return g
+
     def stats(self, saved: Saved | None = None, stream=None) -> dict:
         s = _abi.Stats()
         check(lib().gc_saved_stats(self.ctx, saved.handle if saved else None, C.byref(s),

@@ -1,0 +1,258 @@
+"""Batched requests (many cameras, resolutions, motion frames and layer masks of one
+Gaussian set in one pass): parity with the single-request path and with the oracle.
+
+* every batched image equals gc_render_forward of that request alone, bit for bit
+  (same projection, same stable orders, same per-tile blend);
+* one request of the batch against the FP64 oracle directly (max |pixel| <= 1e-4 on
+  non-ambiguous pixels);
+* batched gradients against the oracle's FP64 gradients summed over the requests
+  (relative L2 <= 1e-4, every element within 1e-3 max|g| + 1e-6), motion gradients per
+  (frame, group); and against the in-order sum of single-request GPU gradients;
+* fixed key capacity: a CUDA graph of forward + backward replays to the eager result;
+  overflow is reported by gc_check; accumulate=1 over two half batches equals one batch.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import scenes
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+@pytest.fixture(scope="module")
+def gc():
+    import paper_2509_17513_b300 as gc
+    return gc
+
+
+@pytest.fixture(scope="module")
+def small():
+    rng = np.random.default_rng(71)
+    scene = scenes.make_hier_scene(rng, 6000, 6, 3, 16)
+    motion = scenes.random_motion(rng, 16, 3)
+    reqs = [
+        scenes.Request(scenes.orbit_camera(0.3, 4.0, 200, 150), 1, 0b111111),
+        scenes.Request(scenes.orbit_camera(1.9, 4.5, 96, 64), -1, 0b000001),
+        scenes.Request(scenes.orbit_camera(4.0, 3.5, 131, 77), 2, 0b000111),   # ragged tiles
+        scenes.Request(scenes.orbit_camera(0.3, 4.0, 64, 48), 0, 0),           # empty selection
+        scenes.Request(scenes.orbit_camera(5.5, 4.2, 160, 120), 1, 0b110110),  # non-prefix mask
+        scenes.Request(scenes.orbit_camera(2.6, 4.0, 120, 90), 2, 0b011111),
+    ]
+    return scene, motion, reqs
+
+
+def _frames(gc, motion):
+    return [gc.MotionFrame.from_motion(motion, f) for f in range(motion.q.shape[0])]
+
+
+def _batch_triplets(reqs):
+    return [(r.camera, r.frame, r.layer_mask) for r in reqs]
+
+
+def _single(gc, r, gs, frames, req, up=None):
+    saved = gc.Saved(r)
+    mo = frames[req.frame] if req.frame >= 0 else None
+    img = r.forward(gs, mo, req.layer_mask, req.camera, saved)
+    g = None
+    if up is not None:
+        g = r.backward(saved, gs, mo, up)
+    return img, g
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 32), (32, 8)])
+def test_batch_images_equal_single_renders(gc, small, tile):
+    scene, motion, reqs = small
+    r = gc.Renderer(0, tile=tile, bg=(0.1, 0.2, 0.3))
+    gs = gc.GaussianSet.from_scene(scene)
+    frames = _frames(gc, motion)
+    saved = gc.Saved(r)
+    imgs = r.batch_forward(gs, frames, _batch_triplets(reqs), saved)
+    r.check()
+    for q, req in enumerate(reqs):
+        one, _ = _single(gc, r, gs, frames, req)
+        assert torch.equal(imgs[q], one), (tile, q)
+
+
+def test_batch_request_against_oracle(gc, small):
+    scene, motion, reqs = small
+    r = gc.Renderer(0)
+    gs = gc.GaussianSet.from_scene(scene)
+    imgs = r.batch_forward(gs, _frames(gc, motion), _batch_triplets(reqs))
+    torch.cuda.synchronize()
+    for q in (0, 2, 4):
+        req = reqs[q]
+        ref = oracle.render(scene, motion if req.frame >= 0 else None, max(req.frame, 0), req.camera,
+                            oracle.default_options(), req.layer_mask)
+        g = imgs[q].cpu().numpy().astype(np.float64)
+        ok = ~ref["ambiguous"]
+        assert np.abs(g - ref["image"]).max(axis=0)[ok].max() <= 1e-4, q
+
+
+def _upstreams(reqs, refs, seed):
+    rng = np.random.default_rng(seed)
+    ups = []
+    for req, ref in zip(reqs, refs):
+        cam = req.camera
+        up = rng.normal(0, 1, (3, cam.height, cam.width)) * (~ref["ambiguous"])[None]
+        ups.append(up.astype(np.float32))
+    return ups
+
+
+def test_batch_backward_matches_oracle_and_single_sum(gc, small):
+    scene, motion, reqs = small
+    opts = oracle.default_options()
+    refs, bins = [], []
+    for req in reqs:
+        mo = motion if req.frame >= 0 else None
+        b = oracle.bin_f32(scene, mo, max(req.frame, 0), req.camera, opts, req.layer_mask)
+        bins.append(b)
+        refs.append(oracle.render(scene, mo, max(req.frame, 0), req.camera, opts, req.layer_mask, bins=b))
+    ups = _upstreams(reqs, refs, 5)
+
+    r = gc.Renderer(0)
+    gs = gc.GaussianSet.from_scene(scene)
+    frames = _frames(gc, motion)
+    saved = gc.Saved(r)
+    r.batch_forward(gs, frames, _batch_triplets(reqs), saved)
+    dls = [torch.from_numpy(u).cuda() for u in ups]
+    got = r.batch_backward(saved, gs, frames, dls)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy().astype(np.float64) for k, v in got.items()}
+
+    # oracle: FP64 gradients of every request, summed; motion per (frame, group)
+    n_frames, G = motion.q.shape[0], motion.q.shape[1]
+    want = {k: 0.0 for k in NAMES}
+    want["group_q"] = np.zeros((n_frames, G, 4))
+    want["group_t"] = np.zeros((n_frames, G, 3))
+    for req, up, b in zip(reqs, ups, bins):
+        mo = motion if req.frame >= 0 else None
+        og = oracle.grad(scene, mo, max(req.frame, 0), req.camera, opts, up.astype(np.float64),
+                         req.layer_mask, bins=b)
+        for k in NAMES:
+            want[k] = want[k] + og[k]
+        if req.frame >= 0:
+            want["group_q"][req.frame] += og["group_q"]
+            want["group_t"][req.frame] += og["group_t"]
+    for k in NAMES + ("group_q", "group_t"):
+        a, b = got[k], np.asarray(want[k]).reshape(got[k].shape)
+        nb = np.linalg.norm(b)
+        assert nb > 0, k
+        assert np.linalg.norm(a - b) / nb <= 1e-4, (k, np.linalg.norm(a - b) / nb)
+        assert np.abs(a - b).max() <= 1e-3 * np.abs(b).max() + 1e-6, k
+
+    # the in-order sum of single-request GPU gradients (FP32): equal up to the order of
+    # the float additions inside each Gaussian's chain rule
+    acc = {k: torch.zeros_like(torch.from_numpy(got[k])).cuda().float() for k in got}
+    for q, req in enumerate(reqs):
+        _, g = _single(gc, r, gs, frames, req, dls[q])
+        for k in NAMES:
+            acc[k] += g[k]
+        if req.frame >= 0:
+            acc["group_q"][req.frame] += g["group_q"]
+            acc["group_t"][req.frame] += g["group_t"]
+    for k in acc:
+        a = got[k]
+        b = acc[k].cpu().numpy().astype(np.float64)
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max() + 1e-7, k
+
+
+def test_batch_graph_replay_and_capacity(gc, small):
+    scene, motion, reqs = small
+    gs = gc.GaussianSet.from_scene(scene)
+    frames = _frames(gc, motion)
+    trip = _batch_triplets(reqs)
+    # exact key count from an auto-capacity pass
+    r0 = gc.Renderer(0)
+    s0 = gc.Saved(r0)
+    ref_imgs = r0.batch_forward(gs, frames, trip, s0)
+    dls = [torch.randn_like(x) for x in ref_imgs]
+    ref_g = r0.batch_backward(s0, gs, frames, dls)
+    torch.cuda.synchronize()
+
+    r = gc.Renderer(0, key_capacity=400_000)
+    saved = gc.Saved(r)
+    stream = torch.cuda.Stream()
+    outs = [torch.empty_like(x) for x in ref_imgs]
+    grads = r.batch_grads(gs, frames)
+    with torch.cuda.stream(stream):
+        r.batch_forward(gs, frames, trip, saved, outs=outs)        # eager: sizes and uploads
+        r.batch_backward(saved, gs, frames, dls, grads=grads)
+    stream.synchronize()
+    r.check(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        r.batch_forward(gs, frames, trip, saved, outs=outs)
+        r.batch_backward(saved, gs, frames, dls, grads=grads)
+    for o in outs:
+        o.zero_()
+    for v in grads.values():
+        v.fill_(7.0)
+    graph.replay()
+    torch.cuda.synchronize()
+    r.check()
+    for a, b in zip(outs, ref_imgs):
+        assert torch.equal(a, b)
+    for k in ref_g:
+        assert torch.equal(grads[k], ref_g[k]), k
+    # a bound state refuses other requests
+    with pytest.raises(gc.GCError):
+        r.batch_forward(gs, frames, trip[:3], saved)
+    del graph
+
+    # too small a capacity: nothing emitted, reported by gc_check
+    rs = gc.Renderer(0, key_capacity=2048)
+    ss = gc.Saved(rs)
+    rs.batch_forward(gs, frames, trip, ss)
+    with pytest.raises(gc.GCError, match="capacity"):
+        rs.check()
+
+
+def test_batch_accumulate_over_half_batches(gc, small):
+    scene, motion, reqs = small
+    gs = gc.GaussianSet.from_scene(scene)
+    frames = _frames(gc, motion)
+    trip = _batch_triplets(reqs)
+    r = gc.Renderer(0)
+    s_all, s_a, s_b = gc.Saved(r), gc.Saved(r), gc.Saved(r)
+    imgs = r.batch_forward(gs, frames, trip, s_all)
+    dls = [torch.randn_like(x) for x in imgs]
+    full = r.batch_backward(s_all, gs, frames, dls)
+    r.batch_forward(gs, frames, trip[:3], s_a)
+    r.batch_forward(gs, frames, trip[3:], s_b)
+    acc = r.batch_grads(gs, frames)
+    r.batch_backward(s_a, gs, frames, dls[:3], grads=acc)
+    r.batch_backward(s_b, gs, frames, dls[3:], grads=acc, accumulate=True)
+    torch.cuda.synchronize()
+    for k in full:
+        a, b = acc[k], full[k]
+        assert torch.allclose(a, b, rtol=0, atol=1e-5 * float(b.abs().max()) + 1e-7), k
+
+
+def test_batch_workload_at_scale(gc):
+    """500k Gaussians, 16 views x 8 frames = 128 requests of mixed level and resolution:
+    eight sampled requests equal their single-request renders bit for bit; gradients are
+    finite and the backward is deterministic."""
+    w = scenes.batch()
+    gs = gc.GaussianSet.from_scene(w.scene)
+    frames = _frames(gc, w.motion)
+    trip = [(q.camera, q.frame, q.layer_mask) for q in w.requests]
+    r = gc.Renderer(0)
+    saved = gc.Saved(r)
+    imgs = r.batch_forward(gs, frames, trip, saved)
+    r.check()
+    for q in (0, 9, 31, 50, 77, 100, 126, 127):
+        one, _ = _single(gc, r, gs, frames, w.requests[q])
+        assert torch.equal(imgs[q], one), q
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    dls = [torch.randn(x.shape, generator=gen, device="cuda") for x in imgs]
+    g1 = r.batch_backward(saved, gs, frames, dls)
+    g1 = {k: v.clone() for k, v in g1.items()}
+    g2 = r.batch_backward(saved, gs, frames, dls)
+    torch.cuda.synchronize()
+    for k in g1:
+        assert torch.isfinite(g1[k]).all(), k
+        assert torch.equal(g1[k], g2[k]), k
