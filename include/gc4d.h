@@ -260,6 +260,56 @@ GC_API gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *saved
                                           int32_t n_frames, const float *const *dL_dimages,
                                           int32_t accumulate, gc_grads *out, void *stream);
 
+/*
+ * Batch graphs: a whole training or playback step over many requests as one CUDA
+ * graph.  The requests are split into consecutive batches of `depth` (the batch
+ * depth); the graph holds, per batch, one gc_render_batch_forward and, when
+ * dL_dimages is not NULL, one gc_render_batch_backward (the first batch overwrites
+ * `grads`, the others add to them, so the gradient is summed over all requests in
+ * order).  Creation runs the step eagerly (with key_capacity 0 it first measures
+ * every batch's key count and fixes the capacity at the largest plus 5 %), then
+ * captures it; launching replays every kernel with no host work.  The graph reads
+ * and writes the same device arrays as at creation (Gaussians, motion, images,
+ * dL_dimages, grads): update their contents in place.  It owns its saved states and
+ * must be destroyed before the context.  Overflow and bounded-wait timeouts are
+ * reported by gc_batch_graph_check.  The context's options (tile shape, ...) are
+ * read at creation and restored afterwards.
+ */
+typedef struct gc_batch_graph gc_batch_graph;
+
+GC_API gc_status gc_batch_graph_create(gc_context *ctx, const gc_gaussians *g, const gc_motion *frames,
+                                       int32_t n_frames, const gc_request *reqs, int32_t n_req,
+                                       int32_t depth, const float *const *dL_dimages, gc_grads *grads,
+                                       void *stream, gc_batch_graph **out);
+GC_API gc_status gc_batch_graph_launch(gc_batch_graph *graph, void *stream);
+/* Key capacity per batch, kernel nodes in the graph, number of batches; any may be NULL. */
+GC_API gc_status gc_batch_graph_info(const gc_batch_graph *graph, int64_t *key_capacity,
+                                     int64_t *kernel_nodes, int32_t *n_batches);
+/* Synchronises `stream`; GC_ERR_CAPACITY or GC_ERR_TIMEOUT if a replay overflowed or timed out. */
+GC_API gc_status gc_batch_graph_check(gc_batch_graph *graph, void *stream);
+GC_API gc_status gc_batch_graph_destroy(gc_batch_graph *graph);
+
+/* One measured configuration of the autotuner. */
+typedef struct {
+    int32_t tile_w, tile_h;  /* tile shape */
+    int32_t depth;           /* requests per batch */
+    int64_t key_capacity;    /* per-batch key capacity the graph used */
+    float ms;                /* mean time of one graph launch (the whole step) */
+} gc_tune_entry;
+
+/*
+ * Autotuner over tile shape {16x16, 8x32, 32x8} x batch depth (depths[0..n_depths)):
+ * builds the batch graph of every configuration, times `iters` launches after one
+ * warm-up with CUDA events on `stream`, and writes 3 * n_depths entries (shape-major).
+ * The fastest is returned in *best and its tile shape is set in the context's
+ * options.  Images and gradients are written as a side effect.
+ */
+GC_API gc_status gc_tune_batch(gc_context *ctx, const gc_gaussians *g, const gc_motion *frames,
+                               int32_t n_frames, const gc_request *reqs, int32_t n_req,
+                               const float *const *dL_dimages, gc_grads *grads, const int32_t *depths,
+                               int32_t n_depths, int32_t iters, gc_tune_entry *entries,
+                               gc_tune_entry *best, void *stream);
+
 /* Statistics of the last forward recorded in `saved` (synchronises `stream`). */
 GC_API gc_status gc_saved_stats(gc_context *ctx, const gc_saved *saved, gc_stats *out, void *stream);
 

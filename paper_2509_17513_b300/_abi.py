@@ -68,6 +68,11 @@ class Request(C.Structure):
     _fields_ = [("camera", Camera), ("frame", C.c_int32), ("layer_mask", C.c_uint32), ("image", C.c_void_p)]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("depth", C.c_int32),
+                ("key_capacity", C.c_int64), ("ms", C.c_float)]
+
+
 class Stats(C.Structure):
     _fields_ = [("n_selected", C.c_int64), ("n_visible", C.c_int64), ("n_keys", C.c_int64),
                 ("n_tiles", C.c_int32), ("width", C.c_int32), ("height", C.c_int32)]
@@ -87,6 +92,12 @@ SIGNATURES = {
     "gc_render_forward_noalloc": (C.c_int, [P, P, P, C.c_uint32, P, P, P, C.c_char_p, C.c_size_t]),
     "gc_render_batch_forward": (C.c_int, [P, P, P, C.c_int32, P, C.c_int32, P, P]),
     "gc_render_batch_backward": (C.c_int, [P, P, P, P, C.c_int32, P, C.c_int32, P, P]),
+    "gc_batch_graph_create": (C.c_int, [P, P, P, C.c_int32, P, C.c_int32, C.c_int32, P, P, P, P]),
+    "gc_batch_graph_launch": (C.c_int, [P, P]),
+    "gc_batch_graph_info": (C.c_int, [P, P, P, P]),
+    "gc_batch_graph_check": (C.c_int, [P, P]),
+    "gc_batch_graph_destroy": (C.c_int, [P]),
+    "gc_tune_batch": (C.c_int, [P, P, P, C.c_int32, P, C.c_int32, P, P, P, C.c_int32, C.c_int32, P, P, P]),
     "gc_saved_stats": (C.c_int, [P, P, P, P]),
     "gc_saved_tile_lists": (C.c_int, [P, P, P, P, C.c_int64, P]),
     "gc_saved_pixel_state": (C.c_int, [P, P, P, P, P, P, P]),

@@ -91,6 +91,7 @@ gc_status gc_destroy(gc_context *ctx) {
     {
         DeviceGuard dg(ctx->device);
         saved_release(ctx, &ctx->internal);
+        ctx->internal.batch.reset();
         DevBuf *bufs[] = {&ctx->scratch, &ctx->bwd_part, &ctx->bwd_g2d, &ctx->bwd_motion,
                           &ctx->bwd_rmax, &ctx->bwd_group};
         for (DevBuf *b : bufs) release(*b);

@@ -987,3 +987,250 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
     GC_CUDA(ctx, mark(-1));
     return GC_OK;
 }
+
+// --------------------------------------------------------------------------- graphs
+
+struct gc_batch_graph {
+    gc_context *ctx = nullptr;
+    std::vector<gc_saved *> states;  // one per batch of `depth` requests
+    int depth = 0, n_req = 0;
+    bool backward = false;
+    int64_t key_capacity = 0;
+    int64_t kernel_nodes = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void graph_free(gc_batch_graph *G) {
+    if (!G) return;
+    DeviceGuard dg(G->ctx->device);
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    for (gc_saved *s : G->states) gc_saved_destroy(G->ctx, s);
+    if (G->own_stream) cudaStreamDestroy(G->own_stream);
+    delete G;
+}
+
+// One pass over all batches: forwards, then backwards (the first overwrites the
+// gradients, the others add to them, so the step's gradient is summed in order).
+gc_status graph_pass(gc_batch_graph *G, const gc_gaussians *g, const gc_motion *frames, int n_frames,
+                     const gc_request *reqs, const float *const *dL, gc_grads *grads, cudaStream_t s) {
+    gc_status st;
+    const int nb = (int)G->states.size();
+    for (int b = 0; b < nb; ++b) {
+        const int q0 = b * G->depth, cnt = std::min(G->depth, G->n_req - q0);
+        if ((st = gc_render_batch_forward(G->ctx, g, frames, n_frames, reqs + q0, cnt, G->states[b], s)) != GC_OK)
+            return st;
+    }
+    if (G->backward)
+        for (int b = 0; b < nb; ++b) {
+            const int q0 = b * G->depth;
+            if ((st = gc_render_batch_backward(G->ctx, G->states[b], g, frames, n_frames, dL + q0, b > 0 ? 1 : 0,
+                                               grads, s)) != GC_OK)
+                return st;
+        }
+    return GC_OK;
+}
+
+}  // namespace
+
+extern "C" gc_status gc_batch_graph_create(gc_context *ctx, const gc_gaussians *g, const gc_motion *frames,
+                                           int32_t n_frames, const gc_request *reqs, int32_t n_req,
+                                           int32_t depth, const float *const *dL_dimages, gc_grads *grads,
+                                           void *stream, gc_batch_graph **out) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    if (!out) return fail(ctx, GC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!reqs || n_req <= 0) return fail(ctx, GC_ERR_INVALID_ARG, "no requests");
+    if (depth <= 0) return fail(ctx, GC_ERR_INVALID_ARG, "depth must be >= 1");
+    if (dL_dimages && !grads) return fail(ctx, GC_ERR_INVALID_ARG, "a backward graph needs gradient buffers");
+    DeviceGuard dg(ctx->device);
+    gc_batch_graph *G = new (std::nothrow) gc_batch_graph();
+    if (!G) return fail(ctx, GC_ERR_OOM, "graph handle");
+    G->ctx = ctx;
+    G->depth = std::min<int>(depth, n_req);
+    G->n_req = n_req;
+    G->backward = dL_dimages != nullptr;
+    const int nb = (n_req + G->depth - 1) / G->depth;
+    gc_status st = GC_OK;
+    for (int b = 0; b < nb && st == GC_OK; ++b) {
+        gc_saved *s = nullptr;
+        st = gc_saved_create(ctx, &s);
+        if (st == GC_OK) G->states.push_back(s);
+    }
+    const gc_options saved_opt = ctx->opt;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto bail = [&](gc_status e) {
+        ctx->opt = saved_opt;
+        graph_free(G);
+        return e;
+    };
+    if (st != GC_OK) return bail(fail(ctx, st, "saved state allocation failed"));
+    if (!s) {  // capture needs a stream other than the legacy default one
+        if (cudaStreamCreateWithFlags(&G->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(ctx, GC_ERR_CUDA, "stream creation failed"));
+        }
+        s = G->own_stream;
+    }
+    // 1. key capacity: the caller's, or the largest batch's exact need plus 5 %
+    int64_t cap = saved_opt.key_capacity;
+    if (cap <= 0) {
+        ctx->opt.key_capacity = 0;
+        for (int b = 0; b < nb; ++b) {
+            const int q0 = b * G->depth, cnt = std::min(G->depth, n_req - q0);
+            if ((st = gc_render_batch_forward(ctx, g, frames, n_frames, reqs + q0, cnt, G->states[b], s)) != GC_OK)
+                return bail(st);
+            cap = std::max<int64_t>(cap, G->states[b]->batch->K_cap);
+        }
+        const int64_t T = gc::radix_tile_keys();
+        cap = (cap + cap / 20 + 2 * T + T - 1) / T * T;
+        if (cap > 0xFFFFFFF0ll) return bail(fail(ctx, GC_ERR_CAPACITY, "a batch needs more than 2^32 keys"));
+        for (gc_saved *x : G->states) {  // re-bind the states to the fixed capacity
+            gc_saved *fresh = nullptr;
+            if ((st = gc_saved_create(ctx, &fresh)) != GC_OK) return bail(st);
+            gc_saved_destroy(ctx, x);
+            std::replace(G->states.begin(), G->states.end(), x, fresh);
+        }
+    }
+    G->key_capacity = cap;
+    ctx->opt.key_capacity = cap;
+    // 2. eager pass: sizes every buffer, uploads the request tables
+    if ((st = graph_pass(G, g, frames, n_frames, reqs, dL_dimages, grads, s)) != GC_OK) return bail(st);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctx, GC_ERR_CUDA, "eager pass failed"));
+    for (gc_saved *x : G->states)
+        if ((st = batch_check(ctx, *x)) != GC_OK) return bail(st);
+    // 3. capture the same pass
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(ctx, GC_ERR_CUDA, "cannot begin stream capture"));
+    }
+    st = graph_pass(G, g, frames, n_frames, reqs, dL_dimages, grads, s);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    G->graph = graph;
+    if (st != GC_OK) return bail(st);
+    if (ce != cudaSuccess || !graph) {
+        cudaGetLastError();
+        return bail(fail(ctx, GC_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ce)));
+    }
+    size_t n_nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &n_nodes);
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    if (n_nodes) cudaGraphGetNodes(graph, nodes.data(), &n_nodes);
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) G->kernel_nodes++;
+    }
+    if (cudaGraphInstantiate(&G->exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(ctx, GC_ERR_CUDA, "graph instantiation failed"));
+    }
+    ctx->opt = saved_opt;
+    *out = G;
+    return GC_OK;
+}
+
+extern "C" gc_status gc_batch_graph_launch(gc_batch_graph *G, void *stream) {
+    if (!G) return GC_ERR_INVALID_ARG;
+    DeviceGuard dg(G->ctx->device);
+    GC_CUDA(G->ctx, cudaGraphLaunch(G->exec, (cudaStream_t)stream));
+    gc::note_launches((int)G->kernel_nodes);
+    return GC_OK;
+}
+
+extern "C" gc_status gc_batch_graph_info(const gc_batch_graph *G, int64_t *key_capacity, int64_t *kernel_nodes,
+                                         int32_t *n_batches) {
+    if (!G) return GC_ERR_INVALID_ARG;
+    if (key_capacity) *key_capacity = G->key_capacity;
+    if (kernel_nodes) *kernel_nodes = G->kernel_nodes;
+    if (n_batches) *n_batches = (int32_t)G->states.size();
+    return GC_OK;
+}
+
+extern "C" gc_status gc_batch_graph_check(gc_batch_graph *G, void *stream) {
+    if (!G) return GC_ERR_INVALID_ARG;
+    DeviceGuard dg(G->ctx->device);
+    GC_CUDA(G->ctx, cudaStreamSynchronize((cudaStream_t)stream));
+    for (gc_saved *x : G->states) {
+        const gc_status st = batch_check(G->ctx, *x);
+        if (st != GC_OK) return st;
+    }
+    return GC_OK;
+}
+
+extern "C" gc_status gc_batch_graph_destroy(gc_batch_graph *G) {
+    if (!G) return GC_ERR_INVALID_ARG;
+    graph_free(G);
+    return GC_OK;
+}
+
+// --------------------------------------------------------------------------- autotuner
+
+extern "C" gc_status gc_tune_batch(gc_context *ctx, const gc_gaussians *g, const gc_motion *frames,
+                                   int32_t n_frames, const gc_request *reqs, int32_t n_req,
+                                   const float *const *dL_dimages, gc_grads *grads, const int32_t *depths,
+                                   int32_t n_depths, int32_t iters, gc_tune_entry *entries,
+                                   gc_tune_entry *best, void *stream) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    if (!depths || n_depths <= 0 || !entries || !best)
+        return fail(ctx, GC_ERR_INVALID_ARG, "depths, entries and best are required");
+    if (iters <= 0) return fail(ctx, GC_ERR_INVALID_ARG, "iters must be >= 1");
+    static const int shapes[3][2] = {{16, 16}, {8, 32}, {32, 8}};
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStream_t own = nullptr;
+    if (!s) {
+        GC_CUDA(ctx, cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+        s = own;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const gc_options base = ctx->opt;
+    gc_status st = GC_OK;
+    int n_out = 0, ib = -1;
+    for (int sh = 0; sh < 3 && st == GC_OK; ++sh) {
+        for (int d = 0; d < n_depths && st == GC_OK; ++d) {
+            ctx->opt = base;
+            ctx->opt.tile_w = shapes[sh][0];
+            ctx->opt.tile_h = shapes[sh][1];
+            gc_batch_graph *G = nullptr;
+            st = gc_batch_graph_create(ctx, g, frames, n_frames, reqs, n_req, depths[d], dL_dimages, grads, s, &G);
+            if (st != GC_OK) break;
+            float ms = 0.f;
+            if ((st = gc_batch_graph_launch(G, s)) == GC_OK) {  // warm-up
+                cudaEventRecord(e0, s);
+                for (int it = 0; it < iters && st == GC_OK; ++it) st = gc_batch_graph_launch(G, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    cudaGetLastError();
+                    st = fail(ctx, GC_ERR_CUDA, "timing failed");
+                }
+            }
+            if (st == GC_OK) st = gc_batch_graph_check(G, s);
+            gc_tune_entry &E = entries[n_out];
+            E.tile_w = shapes[sh][0];
+            E.tile_h = shapes[sh][1];
+            E.depth = std::min<int>(depths[d], n_req);
+            E.key_capacity = G->key_capacity;
+            E.ms = ms / (float)iters;
+            graph_free(G);
+            if (st != GC_OK) break;
+            if (ib < 0 || E.ms < entries[ib].ms) ib = n_out;
+            ++n_out;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (own) cudaStreamDestroy(own);
+    ctx->opt = base;
+    if (st != GC_OK) return st;
+    *best = entries[ib];
+    ctx->opt.tile_w = best->tile_w;
+    ctx->opt.tile_h = best->tile_h;
+    return GC_OK;
+}

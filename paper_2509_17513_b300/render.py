@@ -229,23 +229,10 @@ class Renderer:
                       outs: list | None = None, stream=None) -> list:
         """Renders every request (camera, frame index or -1, layer mask) of one Gaussian set
         in one batched pass; returns one (3, H, W) image per request."""
-        dev = f"cuda:{self.device}"
-        n = len(requests)
-        reqs = (_abi.Request * n)()
-        if outs is None:
-            outs = []
-            for cam, _, _ in requests:
-                outs.append(torch.empty((3, int(cam.height), int(cam.width)), dtype=torch.float32, device=dev))
-        for q, (cam, frame, mask) in enumerate(requests):
-            reqs[q].camera = camera_struct(cam)
-            reqs[q].frame = int(frame)
-            reqs[q].layer_mask = int(mask) & 0xFFFFFFFF
-            reqs[q].image = outs[q].data_ptr()
-        fr = (_abi.Motion * max(len(frames), 1))()
-        for f, m in enumerate(frames):
-            fr[f] = m.struct
-        st = lib().gc_render_batch_forward(self.ctx, C.byref(gs.struct), fr if frames else None, len(frames),
-                                           reqs, n, saved.handle if saved is not None else None,
+        reqs, outs = self._requests(requests, outs)
+        fr, nf = self._frames(frames)
+        st = lib().gc_render_batch_forward(self.ctx, C.byref(gs.struct), fr, nf,
+                                           reqs, len(requests), saved.handle if saved is not None else None,
                                            _stream(stream))
         check(st, self.ctx)
         return outs
@@ -273,14 +260,58 @@ class Renderer:
         g = self._grads_struct(grads)
         dls = [d.contiguous() for d in dL_dimages]
         ptrs = (C.c_void_p * len(dls))(*[d.data_ptr() for d in dls])
-        fr = (_abi.Motion * max(len(frames), 1))()
-        for f, m in enumerate(frames):
-            fr[f] = m.struct
+        fr, nf = self._frames(frames)
         st = lib().gc_render_batch_backward(self.ctx, saved.handle if saved is not None else None,
-                                            C.byref(gs.struct), fr if frames else None, len(frames), ptrs,
+                                            C.byref(gs.struct), fr, nf, ptrs,
                                             1 if accumulate else 0, C.byref(g), _stream(stream))
         check(st, self.ctx)
         return grads
+
+    def tune_batch(self, gs: GaussianSet, frames: list, requests: list, dL_dimages: list | None = None,
+                   grads: dict | None = None, depths=(16, 32, 64, 128), iters: int = 3, outs: list | None = None,
+                   stream=None) -> dict:
+        """Autotuner over tile shape x batch depth (native, gc_tune_batch).  Sets the best
+        tile shape in this renderer's options and returns every measurement."""
+        reqs, outs = self._requests(requests, outs)
+        fr, nf = self._frames(frames)
+        g, ptrs = None, None
+        if dL_dimages is not None:
+            grads = grads if grads is not None else self.batch_grads(gs, frames)
+            g = self._grads_struct(grads)
+            ptrs = (C.c_void_p * len(dL_dimages))(*[d.data_ptr() for d in dL_dimages])
+        ds = (C.c_int32 * len(depths))(*[int(d) for d in depths])
+        entries = (_abi.TuneEntry * (3 * len(depths)))()
+        best = _abi.TuneEntry()
+        st = lib().gc_tune_batch(self.ctx, C.byref(gs.struct), fr, nf, reqs, len(requests), ptrs,
+                                 C.byref(g) if g is not None else None, ds, len(depths), int(iters), entries,
+                                 C.byref(best), _stream(stream))
+        check(st, self.ctx)
+        self.options.tile_w, self.options.tile_h = best.tile_w, best.tile_h
+
+        def row(e):
+            return {"tile": (e.tile_w, e.tile_h), "depth": e.depth, "key_capacity": e.key_capacity, "ms": e.ms}
+        return {"best": row(best), "entries": [row(e) for e in entries]}
+
+    def _requests(self, requests, outs):
+        dev = f"cuda:{self.device}"
+        n = len(requests)
+        reqs = (_abi.Request * n)()
+        if outs is None:
+            outs = [torch.empty((3, int(c.height), int(c.width)), dtype=torch.float32, device=dev)
+                    for c, _, _ in requests]
+        for q, (cam, frame, mask) in enumerate(requests):
+            reqs[q].camera = camera_struct(cam)
+            reqs[q].frame = int(frame)
+            reqs[q].layer_mask = int(mask) & 0xFFFFFFFF
+            reqs[q].image = outs[q].data_ptr()
+        return reqs, outs
+
+    @staticmethod
+    def _frames(frames):
+        fr = (_abi.Motion * max(len(frames), 1))()
+        for f, m in enumerate(frames):
+            fr[f] = m.struct
+        return (fr if frames else None), len(frames)
 
     @staticmethod
     def _grads_struct(grads: dict) -> _abi.Grads:
@@ -333,6 +364,54 @@ class Renderer:
 
     def check(self, stream=None):
         check(lib().gc_check(self.ctx, _stream(stream)), self.ctx)
+
+
+class BatchGraph:
+    """A whole step over many requests as one CUDA graph (gc_batch_graph): batches of
+    `depth` requests, each a batched forward and, with dL_dimages, a batched backward
+    whose gradients are summed over all requests.  The tensors given here are the ones
+    every launch reads and writes: update them in place."""
+
+    def __init__(self, renderer: Renderer, gs: GaussianSet, frames: list, requests: list, depth: int,
+                 dL_dimages: list | None = None, grads: dict | None = None, outs: list | None = None,
+                 stream=None):
+        self.renderer = renderer
+        self.gs, self.frames = gs, frames
+        self.reqs, self.outs = renderer._requests(requests, outs)
+        self._fr, nf = renderer._frames(frames)
+        self.dL = dL_dimages
+        self.grads = None
+        g, ptrs = None, None
+        if dL_dimages is not None:
+            self.grads = grads if grads is not None else renderer.batch_grads(gs, frames)
+            self._g = g = renderer._grads_struct(self.grads)
+            self._ptrs = ptrs = (C.c_void_p * len(dL_dimages))(*[d.data_ptr() for d in dL_dimages])
+        h = C.c_void_p()
+        st = lib().gc_batch_graph_create(renderer.ctx, C.byref(gs.struct), self._fr, nf, self.reqs, len(requests),
+                                         int(depth), ptrs, C.byref(g) if g is not None else None,
+                                         _stream(stream), C.byref(h))
+        check(st, renderer.ctx)
+        self.handle = h
+        cap, nodes, nb = C.c_int64(), C.c_int64(), C.c_int32()
+        check(lib().gc_batch_graph_info(h, C.byref(cap), C.byref(nodes), C.byref(nb)), renderer.ctx)
+        self.key_capacity, self.kernel_nodes, self.n_batches = cap.value, nodes.value, nb.value
+
+    def launch(self, stream=None):
+        check(lib().gc_batch_graph_launch(self.handle, _stream(stream)), self.renderer.ctx)
+
+    def check(self, stream=None):
+        check(lib().gc_batch_graph_check(self.handle, _stream(stream)), self.renderer.ctx)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().gc_batch_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class _RenderFn(torch.autograd.Function):

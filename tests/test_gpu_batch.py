@@ -256,3 +256,81 @@ def test_batch_workload_at_scale(gc):
     for k in g1:
         assert torch.isfinite(g1[k]).all(), k
         assert torch.equal(g1[k], g2[k]), k
+    del saved, g1, g2
+    # eight requests at full size: batched gradients equal the in-order sum of the
+    # single-request gradients up to float summation order
+    pick = (3, 20, 45, 64, 90, 101, 118, 125)
+    sub = gc.Saved(r)
+    r.batch_forward(gs, frames, [trip[q] for q in pick], sub, outs=[imgs[q] for q in pick])
+    got = r.batch_backward(sub, gs, frames, [dls[q] for q in pick])
+    acc = {k: torch.zeros_like(v) for k, v in got.items()}
+    for q in pick:
+        req = w.requests[q]
+        _, g = _single(gc, r, gs, frames, req, dls[q])
+        for k in NAMES:
+            acc[k] += g[k]
+        acc["group_q"][req.frame] += g["group_q"]
+        acc["group_t"][req.frame] += g["group_t"]
+    torch.cuda.synchronize()
+    for k in acc:
+        a, b = got[k], acc[k]
+        assert torch.allclose(a, b, rtol=0, atol=1e-5 * float(b.abs().max()) + 1e-7), k
+
+
+def test_batch_graph_step(gc, small):
+    """A step of 6 requests in batches of 2 as one native CUDA graph: images equal the
+    single renders bit for bit after a replay; gradients equal one eager batch over all
+    requests up to float summation order."""
+    scene, motion, reqs = small
+    gs = gc.GaussianSet.from_scene(scene)
+    frames = _frames(gc, motion)
+    trip = _batch_triplets(reqs)
+    r = gc.Renderer(0)
+    s_all = gc.Saved(r)
+    ref = r.batch_forward(gs, frames, trip, s_all)
+    dls = [torch.randn_like(x) for x in ref]
+    ref_g = r.batch_backward(s_all, gs, frames, dls)
+    torch.cuda.synchronize()
+    graph = gc.BatchGraph(r, gs, frames, trip, 2, dL_dimages=dls)
+    assert graph.n_batches == 3 and graph.kernel_nodes > 0 and graph.key_capacity % 2048 == 0
+    for o in graph.outs:
+        o.zero_()
+    for v in graph.grads.values():
+        v.fill_(3.0)
+    graph.launch()
+    graph.check()
+    for q in range(len(reqs)):
+        assert torch.equal(graph.outs[q], ref[q]), q
+    for k, b in ref_g.items():
+        a = graph.grads[k]
+        assert torch.allclose(a, b, rtol=0, atol=1e-5 * float(b.abs().max()) + 1e-7), k
+    graph.launch()  # replays are deterministic
+    g1 = {k: v.clone() for k, v in graph.grads.items()}
+    graph.launch()
+    graph.check()
+    for k in g1:
+        assert torch.equal(g1[k], graph.grads[k]), k
+    graph.close()
+
+
+def test_autotuner_picks_a_measured_configuration(gc, small):
+    scene, motion, reqs = small
+    gs = gc.GaussianSet.from_scene(scene)
+    frames = _frames(gc, motion)
+    trip = _batch_triplets(reqs)
+    r = gc.Renderer(0)
+    outs = [torch.empty((3, q.camera.height, q.camera.width), device="cuda") for q in reqs]
+    dls = [torch.randn_like(x) for x in outs]
+    res = r.tune_batch(gs, frames, trip, dL_dimages=dls, depths=(2, 6), iters=2, outs=outs)
+    ents = res["entries"]
+    assert len(ents) == 6
+    assert {e["tile"] for e in ents} == {(16, 16), (8, 32), (32, 8)}
+    assert all(e["ms"] > 0 for e in ents)
+    best = res["best"]
+    assert best["ms"] == min(e["ms"] for e in ents)
+    assert (r.options.tile_w, r.options.tile_h) == best["tile"]
+    # the tuned renderer still renders every request exactly like the single path
+    imgs = r.batch_forward(gs, frames, trip)
+    for q, req in enumerate(reqs):
+        one, _ = _single(gc, r, gs, frames, req)
+        assert torch.equal(imgs[q], one), q
