@@ -5,7 +5,11 @@ Workload (the 300k-Gaussian hierarchical scene at 1920x1080): 300,000 Gaussians 
 6 nested layers of 50k (SH degree 3, 64 motion groups), 30 frames of cumulative
 group motion, every frame rendered at every level L1..L6 on an orbit camera.  One
 step = those 180 renders through the library (motion, projection, depth sort,
-binning, tile sort, blend).  Value = Mpixel/s over all ranks.
+binning, tile sort, blend), as batched requests replayed from one CUDA graph (tile
+shape and batch depth autotuned).  Value = Mpixel/s over all ranks.  The same line
+carries the forward + backward step, the plain FP32 single-view form (one call per
+render), the BF16/FP8 storage form, the 128-request batching workload, the
+end-to-end figure with host buffers, and the oracle timed on the host cores.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -123,11 +127,13 @@ def load_traffic(kernel: str):
 
 # --------------------------------------------------------------------------- GPU arm
 
-def roofline_for(stage, per_launch_ms, work, peaks, peak_kind):
+def roofline_for(stage, per_launch_ms, work, peaks, peak_kind, batched=False):
     """Roofline object of the dominant stage.  `work`: algorithmic FLOPs (ALU stages)
     or bytes (HBM stages) of one launch."""
-    alu = {"blend": ("k_blend_fwd", BLEND_FLOPS_PER_PAIR), "blend_bwd": ("k_blend_bwd", BLEND_BWD_FLOPS_PER_PAIR)}
-    hbm = {"tile_sort": "k_radix_scatter", "emit": "k_emit", "reduce": "k_reduce_entries",
+    pre = "k_batch_" if batched else "k_"
+    alu = {"blend": (pre + "blend_fwd", BLEND_FLOPS_PER_PAIR),
+           "blend_bwd": (pre + "blend_bwd", BLEND_BWD_FLOPS_PER_PAIR)}
+    hbm = {"tile_sort": "k_radix_scatter", "emit": pre + "emit", "reduce": pre + "reduce",
            "depth_sort": "k_radix_scatter"}
     if stage in alu:
         peak = N_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
@@ -147,6 +153,53 @@ def roofline_for(stage, per_launch_ms, work, peaks, peak_kind):
     return None
 
 
+class Timer:
+    """K steps timed with CUDA events on the rendering stream, L2 flushed between steps
+    (outside the events), clocks sampled during the region, max over ranks."""
+
+    def __init__(self, r, stream, local, world, dev):
+        import torch
+        self.r, self.stream, self.local, self.world, self.dev = r, stream, local, world, dev
+        self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def __call__(self, step, steps, profile=False):
+        import torch
+        import torch.distributed as dist
+        clocks = ClockSampler(self.local)
+        self.r.profile(profile)
+        self.r.profile_read()
+        if self.world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        total = 0.0
+        for _ in range(steps):
+            self.flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            step()
+            e1.record(self.stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        prof = self.r.profile_read()
+        self.r.profile(False)
+        if self.world > 1:
+            t = torch.tensor([total], device=self.dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total, prof, clk
+
+
+def stage_summary(prof):
+    st_ms, st_calls = prof["stage_ms"], prof["stage_calls"]
+    tot = max(1e-9, sum(st_ms.values()))
+    return ({k: round(v / max(1, st_calls[k]), 4) for k, v in st_ms.items() if v > 0},
+            {k: round(v / tot, 4) for k, v in st_ms.items() if v > 0})
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -162,132 +215,180 @@ def run_gpu(args):
     dev = f"cuda:{local}"
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
+    peaks, peak_kind = measured_peaks()
 
     w = scenes.hier1080(n_frames=args.frames)
     W, H = 1920, 1080
-    reqs = [(f, lv) for f in range(args.frames) for lv in range(1, 7)]
+    order = [(f, lv) for f in range(args.frames) for lv in range(1, 7)]
+    reqs = [(w.cameras[f], f, scenes.level_mask(lv)) for f, lv in order]
+    n_req = len(reqs)
+    pixels_per_step = n_req * W * H
     r = gc.Renderer(local)
+    timer = Timer(r, stream, local, world, dev)
     gs = gc.GaussianSet.from_scene(w.scene, dev)
-    motions = [gc.MotionFrame.from_motion(w.motion, f, dev) for f in range(args.frames)]
-    ring = [torch.empty((3, H, W), device=dev) for _ in range(4)]
-    saved = gc.Saved(r)
+    gsq = gc.GaussianSet.from_quantized(scenes.quantize_scene(w.scene), w.scene, dev)
+    frames = [gc.MotionFrame.from_motion(w.motion, f, dev) for f in range(args.frames)]
+    outs = [torch.empty((3, H, W), device=dev) for _ in range(n_req)]
     upstream = (torch.randn((3, H, W), generator=torch.Generator().manual_seed(7)) * 1e-3).to(dev)
-    grads = None
+    dls = [upstream] * n_req
 
-    # capacity for the (tile, Gaussian) lists: the largest frame of the workload, plus slack
+    def mpix(total_ms, steps, px=pixels_per_step):
+        return round(px * steps * world / (total_ms / 1e3) / 1e6, 1)
+
+    # ---- plain FP32 single-view form: one gc_render_forward (+ backward) per request
+    saved = gc.Saved(r)
     kmax = 0
-    for (f, lv) in reqs:
-        r.forward(gs, motions[f], scenes.level_mask(lv), w.cameras[f], out=ring[0])
+    for q, (cam, f, mask) in enumerate(reqs):
+        r.forward(gs, frames[f], mask, cam, out=outs[q])
         kmax = max(kmax, r.stats()["n_keys"])
-    cap = int(kmax * 1.05) + 4096
-    r.set_options(key_capacity=cap)
+    r.set_options(key_capacity=int(kmax * 1.05) + 4096)
+    grads1 = None
 
-    def step_fwd():
-        for i, (f, lv) in enumerate(reqs):
-            r.forward(gs, motions[f], scenes.level_mask(lv), w.cameras[f], out=ring[i % 4])
+    def single_fwd():
+        for q, (cam, f, mask) in enumerate(reqs):
+            r.forward(gs, frames[f], mask, cam, out=outs[q])
 
-    def step_fwd_bwd():
-        nonlocal grads
-        for i, (f, lv) in enumerate(reqs):
-            r.forward(gs, motions[f], scenes.level_mask(lv), w.cameras[f], saved, out=ring[i % 4])
-            grads = r.backward(saved, gs, motions[f], upstream, grads)
+    def single_fwd_bwd():
+        nonlocal grads1
+        for q, (cam, f, mask) in enumerate(reqs):
+            r.forward(gs, frames[f], mask, cam, saved, out=outs[q])
+            grads1 = r.backward(saved, gs, frames[f], upstream, grads1)
 
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
-        step_fwd()
-        step_fwd_bwd()
+        single_fwd()
+        single_fwd_bwd()
     r.check()
-    torch.cuda.synchronize()
-
-    # algorithmic work of one step (deterministic; measured outside the timed regions)
+    # algorithmic work of one step (deterministic, outside the timed regions)
     walked_pairs = bwd_pairs = keys_total = 0
-    for (f, lv) in reqs:
-        r.forward(gs, motions[f], scenes.level_mask(lv), w.cameras[f], out=ring[0])
+    for q, (cam, f, mask) in enumerate(reqs):
+        r.forward(gs, frames[f], mask, cam, out=outs[q])
         _, _, walked, contrib = r.pixel_state(with_walked=True)
         walked_pairs += int(walked.sum(dtype=torch.int64).item())
         bwd_pairs += int(contrib.sum(dtype=torch.int64).item())
         keys_total += r.stats()["n_keys"]
-    keys_mean = keys_total / len(reqs)
-    torch.cuda.synchronize()
+    keys_mean = keys_total / n_req
+    s_steps = max(1, min(args.steps, 3))
+    sf_ms, sf_prof, _ = timer(single_fwd, s_steps, profile=True)
+    sfb_ms, sfb_prof, _ = timer(single_fwd_bwd, s_steps, profile=True)
+    r.check()
+    single_view = {"form": "plain FP32, one gc_render_forward (+ gc_render_backward) per request",
+                   "fwd": mpix(sf_ms, s_steps), "fwd_bwd": mpix(sfb_ms, s_steps), "unit": UNIT,
+                   "ms_per_step": {"fwd": round(sf_ms / s_steps, 2), "fwd_bwd": round(sfb_ms / s_steps, 2)},
+                   "stage_ms_per_render": stage_summary(sfb_prof)[0], "steps": s_steps}
+    del saved, grads1
+    r.set_options(key_capacity=0)
 
-    def timed(step):
-        """K steps, CUDA events on the rendering stream, L2 flushed between steps."""
-        clocks = ClockSampler(local)
-        r.profile(True)
-        r.profile_read()
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        clocks.start()
-        total = 0.0
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            e1.synchronize()
-            total += e0.elapsed_time(e1)
-        torch.cuda.synchronize()
-        clk = clocks.stop()
-        prof = r.profile_read()
-        r.profile(False)
-        r.check()
-        if world > 1:
-            t = torch.tensor([total], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
-        return total, prof, clk
+    # ---- batched form: autotuned tile shape x batch depth, CUDA graph of the whole step
+    tune = r.tune_batch(gs, frames, reqs, dL_dimages=dls, depths=(30, 60, 90, n_req), iters=2, outs=outs)
+    best = tune["best"]
+    depth, tile = best["depth"], tuple(best["tile"])
+    grads = r.batch_grads(gs, frames)
+    g_fwd = gc.BatchGraph(r, gs, frames, reqs, depth, outs=outs)
+    g_fb = gc.BatchGraph(r, gs, frames, reqs, depth, dL_dimages=dls, grads=grads, outs=outs)
+    for _ in range(args.warmup):
+        g_fwd.launch()
+        g_fb.launch()
+    g_fwd.check()
+    g_fb.check()
+    fwd_ms, fwd_prof, clk = timer(g_fwd.launch, args.steps)
+    fb_ms, fb_prof, clk_fb = timer(g_fb.launch, args.steps)
+    g_fwd.check()
+    g_fb.check()
+    ref_imgs = [o.clone() for o in outs[:: max(1, n_req // 12)]]
+    cap = g_fwd.key_capacity
+    g_fwd.close()
+    g_fb.close()
 
-    peaks, peak_kind = measured_peaks()
-    pixels_per_step = len(reqs) * W * H
+    # ---- the same batched step, eager with per-stage CUDA events (roofline of the top kernel)
+    sv = [gc.Saved(r) for _ in range((n_req + depth - 1) // depth)]
 
-    def summary(total_ms, prof):
+    def eager(bwd):
+        def step():
+            for b, s in enumerate(sv):
+                r.batch_forward(gs, frames, reqs[b * depth:(b + 1) * depth], s,
+                                outs=outs[b * depth:(b + 1) * depth])
+            if bwd:
+                for b, s in enumerate(sv):
+                    r.batch_backward(s, gs, frames, dls[b * depth:(b + 1) * depth], grads=grads,
+                                     accumulate=b > 0)
+        return step
+
+    r.set_options(key_capacity=cap)
+    eager(True)()
+    r.check()
+    e_steps = max(1, min(args.steps, 3))
+    ef_ms, ef_prof, _ = timer(eager(False), e_steps, profile=True)
+    efb_ms, efb_prof, _ = timer(eager(True), e_steps, profile=True)
+    r.check()
+    del sv
+    r.set_options(key_capacity=0)
+
+    def roof(prof, bwd):
         st_ms, st_calls = prof["stage_ms"], prof["stage_calls"]
         dom = max(st_ms, key=lambda k: st_ms[k])
-        per_launch = st_ms[dom] / max(1, st_calls[dom])
-        work = {"blend": walked_pairs / len(reqs) * BLEND_FLOPS_PER_PAIR,
-                "blend_bwd": bwd_pairs / len(reqs) * BLEND_BWD_FLOPS_PER_PAIR,
-                "tile_sort": 2 * SORT_BYTES_PER_KEY_PASS * keys_mean,
-                "emit": 8 * keys_mean, "reduce": 40 * keys_mean}.get(dom, 0.0)
-        tot = max(1e-9, sum(st_ms.values()))
-        return {"value": round(pixels_per_step * args.steps * world / (total_ms / 1e3) / 1e6, 1),
-                "ms_per_step": round(total_ms / args.steps, 3),
-                "fps": round(len(reqs) * args.steps * world / (total_ms / 1e3), 1),
-                "stage_ms_per_render": {k: round(v / max(1, st_calls[k]), 4) for k, v in st_ms.items() if v > 0},
-                "stage_share": {k: round(v / tot, 4) for k, v in st_ms.items() if v > 0},
-                "gpu_launches": prof["kernel_launches"],
-                "roofline": roofline_for(dom, per_launch, work, peaks, peak_kind)}
+        launches = max(1, st_calls[dom])
+        per_launch = st_ms[dom] / launches
+        steps = e_steps
+        work = {"blend": walked_pairs * steps / launches * BLEND_FLOPS_PER_PAIR,
+                "blend_bwd": bwd_pairs * steps / launches * BLEND_BWD_FLOPS_PER_PAIR,
+                "tile_sort": 2 * SORT_BYTES_PER_KEY_PASS * keys_total * steps / launches,
+                "emit": 8 * keys_total * steps / launches}.get(dom, 0.0)
+        return roofline_for(dom, per_launch, work, peaks, peak_kind, batched=True)
 
-    fwd_ms, fwd_prof, clk = timed(step_fwd)
-    fwd = summary(fwd_ms, fwd_prof)
-    fb_ms, fb_prof, clk_fb = timed(step_fwd_bwd)
-    fb = summary(fb_ms, fb_prof)
+    # ---- reduced-precision storage (BF16 geometry, FP8-E4M3 SH), same batched graph
+    gq = gc.BatchGraph(r, gsq, frames, reqs, depth, dL_dimages=dls, grads=r.batch_grads(gsq, frames), outs=outs)
+    for _ in range(args.warmup):
+        gq.launch()
+    gq.check()
+    q_ms, _, clk_q = timer(gq.launch, args.steps)
+    gq.check()
+    q_imgs = outs[:: max(1, n_req // 12)]
+    mse = sum(float(((a - b) ** 2).mean()) for a, b in zip(q_imgs, ref_imgs)) / len(ref_imgs)
+    q_psnr = round(10 * np.log10(1.0 / mse), 2) if mse > 0 else None
+    gq.close()
 
-    e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(args, r, w, reqs, W, H, dev, stream)
-
-    line = {"metric": METRIC, "value": fwd["value"], "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": fwd["ms_per_step"],
+    line = {"metric": METRIC, "value": mpix(fwd_ms, args.steps), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(fwd_ms / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded scene shaped like the paper's workload; no dataset)",
             "config": {"workload": WORKLOAD, "n_gaussians": w.scene.n, "width": W, "height": H,
-                       "renders_per_step": len(reqs), "tile": "16x16", "key_capacity": cap,
+                       "renders_per_step": n_req, "path": "batched requests, one CUDA graph per step",
+                       "tile": f"{tile[0]}x{tile[1]}", "batch_depth": depth, "key_capacity_per_batch": cap,
                        "l2": "flushed (256 MB write) between steps, outside the timed events",
                        "parallelism": f"replicas x{world}"},
-            "fps": fwd["fps"],
-            "stage_ms_per_render": fwd["stage_ms_per_render"], "stage_share": fwd["stage_share"],
-            "gpu_launches": fwd["gpu_launches"],
-            "roofline": fwd["roofline"], "clocks": clk, "e2e": e2e,
-            "fwd_bwd": {"metric": "Mpixel/s at 1920x1080, forward + backward (upstream dL/dimage given)",
-                        "value": fb["value"], "unit": UNIT, "ms_per_step": fb["ms_per_step"],
-                        "fps": fb["fps"], "stage_ms_per_render": fb["stage_ms_per_render"],
-                        "stage_share": fb["stage_share"], "gpu_launches": fb["gpu_launches"],
-                        "roofline": fb["roofline"], "clocks": clk_fb},
+            "fps": round(n_req * args.steps * world / (fwd_ms / 1e3), 1),
+            "gpu_launches": fwd_prof["kernel_launches"],
+            "roofline": roof(ef_prof, False), "clocks": clk,
+            "fwd_bwd": {"metric": "Mpixel/s at 1920x1080, forward + backward (upstream dL/dimage given), "
+                                  "gradients summed over the step's renders",
+                        "value": mpix(fb_ms, args.steps), "unit": UNIT,
+                        "ms_per_step": round(fb_ms / args.steps, 3),
+                        "fps": round(n_req * args.steps * world / (fb_ms / 1e3), 1),
+                        "gpu_launches": fb_prof["kernel_launches"], "roofline": roof(efb_prof, True),
+                        "clocks": clk_fb},
+            "stage_profile": {"note": "eager batched calls with CUDA events between stages (same kernels "
+                                      "as the graph); ms per batch call",
+                              "fwd_mpix_s": mpix(ef_ms, e_steps), "fwd_bwd_mpix_s": mpix(efb_ms, e_steps),
+                              "stage_ms_per_call": stage_summary(efb_prof)[0],
+                              "stage_share_fwd": stage_summary(ef_prof)[1],
+                              "stage_share_fwd_bwd": stage_summary(efb_prof)[1]},
+            "single_view": single_view,
+            "reduced_precision": {"storage": "BF16 means/log-scales/quats/opacity, FP8-E4M3 SH, FP32 scales; "
+                                             "FP32 arithmetic", "fwd_bwd": mpix(q_ms, args.steps),
+                                  "unit": UNIT, "ms_per_step": round(q_ms / args.steps, 3),
+                                  "psnr_vs_fp32_scene_db": q_psnr, "clocks": clk_q,
+                                  "bytes_per_gaussian": {"fp32": 4 * 59 + 4, "bf16_fp8": 2 * 11 + 48 + 4}},
+            "autotune": tune,
             "work_per_step": {"blend_walked_pairs": walked_pairs, "blend_bwd_pairs": bwd_pairs,
                               "keys_per_render": round(keys_mean)}}
+    del outs, ref_imgs, q_imgs, grads, dls
+    torch.cuda.empty_cache()
+
+    if not args.no_batch128:
+        line["batch128"] = run_batch128(args, r, timer, dev)
+        torch.cuda.empty_cache()
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(args, r, w, reqs, depth, W, H, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
@@ -296,14 +397,70 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, r, w, reqs, W, H, dev, stream):
-    """Same metric through the public API with host buffers: every step copies the
-    scene and motion tables from pinned host memory and reads every image back."""
-    import numpy as np
+def run_batch128(args, r, timer, dev):
+    """The 128-request batching workload: 500k Gaussians, 16 views x 8 frames, each at its
+    own level and resolution; forward + backward, batched graph (autotuned) against the
+    plain FP32 single-view loop, FP32 and BF16/FP8 storage."""
     import torch
 
     import paper_2509_17513_b300 as gc
     from synth import scenes
+
+    w = scenes.batch()
+    gs = gc.GaussianSet.from_scene(w.scene, dev)
+    gsq = gc.GaussianSet.from_quantized(scenes.quantize_scene(w.scene), w.scene, dev)
+    frames = [gc.MotionFrame.from_motion(w.motion, f, dev) for f in range(w.motion.q.shape[0])]
+    reqs = [(q.camera, q.frame, q.layer_mask) for q in w.requests]
+    px = sum(q.camera.width * q.camera.height for q in w.requests)
+    outs = [torch.empty((3, q.camera.height, q.camera.width), device=dev) for q in w.requests]
+    gen = torch.Generator(device=dev).manual_seed(9)
+    dls = [torch.randn(o.shape, generator=gen, device=dev) * 1e-3 for o in outs]
+    steps = max(1, min(args.steps, 5))
+    tune = r.tune_batch(gs, frames, reqs, dL_dimages=dls, depths=(16, 32, 64, 128), iters=2, outs=outs)
+    best = tune["best"]
+    res = {"workload": "500k Gaussians, SH degree 3, 128 motion groups; 16 views x 8 frames = 128 requests, "
+                       "level ~ U{L1..L6}, resolution ~ U{960x540, 1280x720, 1920x1080}; forward + backward",
+           "pixels_per_step": px, "unit": UNIT, "steps": steps,
+           "tile": f"{best['tile'][0]}x{best['tile'][1]}", "batch_depth": best["depth"]}
+    for name, g_set in (("batched_fp32", gs), ("batched_bf16_fp8", gsq)):
+        g = gc.BatchGraph(r, g_set, frames, reqs, best["depth"], dL_dimages=dls,
+                          grads=r.batch_grads(g_set, frames), outs=outs)
+        g.launch()
+        g.check()
+        ms, prof, clk = timer(g.launch, steps)
+        g.check()
+        res[name] = {"value": round(px * steps / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms / steps, 2),
+                     "gpu_launches": prof["kernel_launches"], "clocks": clk}
+        g.close()
+        torch.cuda.empty_cache()
+    rs = gc.Renderer(r.device, tile=best["tile"])
+    sv = gc.Saved(rs)
+    grads = None
+
+    def single():
+        nonlocal grads
+        for q, (cam, f, mask) in enumerate(reqs):
+            rs.forward(gs, frames[f], mask, cam, sv, out=outs[q])
+            grads = rs.backward(sv, gs, frames[f], dls[q], grads)
+
+    single()
+    ms, _, _ = timer(single, max(1, min(steps, 2)))
+    res["single_view_fp32"] = {"value": round(px * max(1, min(steps, 2)) / (ms / 1e3) / 1e6, 1),
+                               "ms_per_step": round(ms / max(1, min(steps, 2)), 2)}
+    del sv, grads
+    rs.close()
+    return res
+
+
+def run_e2e(args, r, w, reqs, depth, W, H, dev, stream):
+    """Same metric through the public API with host buffers: every step copies the
+    scene and motion tables from pinned host memory, replays the batched graphs (one
+    per batch of requests) and reads every image back to pinned host memory; the copy
+    of batch b overlaps the render of batch b + 1."""
+    import numpy as np
+    import torch
+
+    import paper_2509_17513_b300 as gc
 
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(w.scene, k), np.float32)).pin_memory()
             for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
@@ -314,31 +471,36 @@ def run_e2e(args, r, w, reqs, W, H, dev, stream):
     dq = torch.empty_like(hq, device=dev)
     dt = torch.empty_like(ht, device=dev)
     gs = gc.GaussianSet(w.scene.layer_offsets, w.scene.sh_degree, 0, **dev_t)
-    motions = [gc.MotionFrame(dq[f], dt[f]) for f in range(args.frames)]
-    nring = 4
-    ring = [torch.empty((3, H, W), device=dev) for _ in range(nring)]
-    out_host = [torch.empty((3, H, W)).pin_memory() for _ in range(nring)]
+    frames = [gc.MotionFrame(dq[f], dt[f]) for f in range(args.frames)]
+    for k, v in host.items():
+        dev_t[k].copy_(v)
+    dq.copy_(hq)
+    dt.copy_(ht)
+    chunk = min(depth, 30)
+    n_req = len(reqs)
+    outs = [torch.empty((3, H, W), device=dev) for _ in range(n_req)]
+    graphs = [gc.BatchGraph(r, gs, frames, reqs[b:b + chunk], chunk, outs=outs[b:b + chunk], stream=stream)
+              for b in range(0, n_req, chunk)]
+    out_host = [torch.empty((3, H, W)).pin_memory() for _ in range(chunk)]
     copy_stream = torch.cuda.Stream(device=dev)
-    rendered = [torch.cuda.Event() for _ in range(nring)]
-    copied = [torch.cuda.Event() for _ in range(nring)]
+    rendered = [torch.cuda.Event() for _ in graphs]
     h2d = sum(v.numel() * v.element_size() for v in host.values()) + hq.numel() * 4 + ht.numel() * 4
-    d2h = len(reqs) * 3 * H * W * 4
+    d2h = n_req * 3 * H * W * 4
 
     def step():
         for k, v in host.items():
             dev_t[k].copy_(v, non_blocking=True)
         dq.copy_(hq, non_blocking=True)
         dt.copy_(ht, non_blocking=True)
-        for i, (f, lv) in enumerate(reqs):
-            slot = i % nring
-            if i >= nring:
-                stream.wait_event(copied[slot])
-            r.forward(gs, motions[f], scenes.level_mask(lv), w.cameras[f], out=ring[slot])
-            rendered[slot].record(stream)
-            copy_stream.wait_event(rendered[slot])
+        for b, g in enumerate(graphs):
+            g.launch(stream)
+            rendered[b].record(stream)
+            copy_stream.wait_event(rendered[b])
             with torch.cuda.stream(copy_stream):
-                out_host[slot].copy_(ring[slot], non_blocking=True)
-                copied[slot].record(copy_stream)
+                for i in range(chunk):
+                    q = b * chunk + i
+                    if q < n_req:
+                        out_host[i].copy_(outs[q], non_blocking=True)
         stream.wait_stream(copy_stream)
 
     for _ in range(2):
@@ -353,15 +515,16 @@ def run_e2e(args, r, w, reqs, W, H, dev, stream):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = max(e0.elapsed_time(e1), 1e-6)
     wall = (time.perf_counter() - t0) * 1e3
-    r.check()
-    ms = max(ms, 1e-6)
-    return {"value": round(len(reqs) * W * H * steps / (ms / 1e3) / 1e6, 1), "unit": UNIT,
+    for g in graphs:
+        g.check(stream)
+        g.close()
+    return {"value": round(n_req * W * H * steps / (ms / 1e3) / 1e6, 1), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": round(ms / steps, 3), "wall_ms_per_step": round(wall / steps, 3),
-            "note": "pinned host scene + motion in, every image back to pinned host; "
-                    "copies on a second stream overlap rendering"}
+            "note": f"pinned host scene + motion in, every image back to pinned host; batched graphs of "
+                    f"{chunk} requests, image copies on a second stream overlap the next batch"}
 
 
 # --------------------------------------------------------------------------- oracle legs
@@ -440,6 +603,7 @@ def main():
     ap.add_argument("--frames", type=int, default=30, help="frames of the workload (30 = full)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch128", action="store_true", help="skip the 128-request batching workload")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
