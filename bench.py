@@ -162,7 +162,7 @@ class Timer:
         self.r, self.stream, self.local, self.world, self.dev = r, stream, local, world, dev
         self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def __call__(self, step, steps, profile=False):
+    def __call__(self, step, steps, profile=False, name="timed"):
         import torch
         import torch.distributed as dist
         clocks = ClockSampler(self.local)
@@ -173,6 +173,7 @@ class Timer:
         torch.cuda.synchronize()
         clocks.start()
         total = 0.0
+        torch.cuda.nvtx.range_push(name)  # lets a profiler select the kernels of this region
         for _ in range(steps):
             self.flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -182,6 +183,7 @@ class Timer:
             e1.record(self.stream)
             e1.synchronize()
             total += e0.elapsed_time(e1)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         clk = clocks.stop()
         prof = self.r.profile_read()
@@ -268,8 +270,8 @@ def run_gpu(args):
         keys_total += r.stats()["n_keys"]
     keys_mean = keys_total / n_req
     s_steps = max(1, min(args.steps, 3))
-    sf_ms, sf_prof, _ = timer(single_fwd, s_steps, profile=True)
-    sfb_ms, sfb_prof, _ = timer(single_fwd_bwd, s_steps, profile=True)
+    sf_ms, sf_prof, _ = timer(single_fwd, s_steps, profile=True, name="single_fwd")
+    sfb_ms, sfb_prof, _ = timer(single_fwd_bwd, s_steps, profile=True, name="single_fwd_bwd")
     r.check()
     single_view = {"form": "plain FP32, one gc_render_forward (+ gc_render_backward) per request",
                    "fwd": mpix(sf_ms, s_steps), "fwd_bwd": mpix(sfb_ms, s_steps), "unit": UNIT,
@@ -290,8 +292,8 @@ def run_gpu(args):
         g_fb.launch()
     g_fwd.check()
     g_fb.check()
-    fwd_ms, fwd_prof, clk = timer(g_fwd.launch, args.steps)
-    fb_ms, fb_prof, clk_fb = timer(g_fb.launch, args.steps)
+    fwd_ms, fwd_prof, clk = timer(g_fwd.launch, args.steps, name="graph_fwd")
+    fb_ms, fb_prof, clk_fb = timer(g_fb.launch, args.steps, name="graph_fwd_bwd")
     g_fwd.check()
     g_fb.check()
     ref_imgs = [o.clone() for o in outs[:: max(1, n_req // 12)]]
@@ -317,8 +319,8 @@ def run_gpu(args):
     eager(True)()
     r.check()
     e_steps = max(1, min(args.steps, 3))
-    ef_ms, ef_prof, _ = timer(eager(False), e_steps, profile=True)
-    efb_ms, efb_prof, _ = timer(eager(True), e_steps, profile=True)
+    ef_ms, ef_prof, _ = timer(eager(False), e_steps, profile=True, name="eager_fwd")
+    efb_ms, efb_prof, _ = timer(eager(True), e_steps, profile=True, name="eager_fwd_bwd")
     r.check()
     del sv
     r.set_options(key_capacity=0)
@@ -340,7 +342,7 @@ def run_gpu(args):
     for _ in range(args.warmup):
         gq.launch()
     gq.check()
-    q_ms, _, clk_q = timer(gq.launch, args.steps)
+    q_ms, _, clk_q = timer(gq.launch, args.steps, name="graph_bf16_fp8_fwd_bwd")
     gq.check()
     q_imgs = outs[:: max(1, n_req // 12)]
     mse = sum(float(((a - b) ** 2).mean()) for a, b in zip(q_imgs, ref_imgs)) / len(ref_imgs)
@@ -427,7 +429,7 @@ def run_batch128(args, r, timer, dev):
                           grads=r.batch_grads(g_set, frames), outs=outs)
         g.launch()
         g.check()
-        ms, prof, clk = timer(g.launch, steps)
+        ms, prof, clk = timer(g.launch, steps, name="b128_" + name)
         g.check()
         res[name] = {"value": round(px * steps / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms / steps, 2),
                      "gpu_launches": prof["kernel_launches"], "clocks": clk}
@@ -444,7 +446,7 @@ def run_batch128(args, r, timer, dev):
             grads = rs.backward(sv, gs, frames[f], dls[q], grads)
 
     single()
-    ms, _, _ = timer(single, max(1, min(steps, 2)))
+    ms, _, _ = timer(single, max(1, min(steps, 2)), name="b128_single_view")
     res["single_view_fp32"] = {"value": round(px * max(1, min(steps, 2)) / (ms / 1e3) / 1e6, 1),
                                "ms_per_step": round(ms / max(1, min(steps, 2)), 2)}
     del sv, grads

@@ -74,6 +74,11 @@ typedef struct {
     int64_t key_capacity;     /* 0: size the (tile, Gaussian) list per frame, one host sync per
                                  frame; > 0: fixed capacity, no host sync, GC_ERR_CAPACITY is
                                  reported by gc_check() when a frame needs more */
+    int32_t alpha_cull;       /* 1 (default): the footprint is also clipped to the bounding box
+                                 of the region where the Gaussian's alpha can reach 1/255
+                                 (with a safety margin), and Gaussians with opacity <= 1/255
+                                 are dropped; the image and the gradients are unchanged, the
+                                 lists are shorter.  0: 3-sigma footprint only. */
 } gc_options;
 
 /* The Gaussian set, in layer order: layer l is [layer_offsets[l], layer_offsets[l+1]). */

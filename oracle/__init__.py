@@ -60,7 +60,7 @@ class Camera(C.Structure):
 class Options(C.Structure):
     _fields_ = [("near_plane", C.c_float), ("dilation", C.c_float), ("frustum_clamp", C.c_float),
                 ("bg", C.c_float * 3), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
-                ("membership", C.c_int32)]
+                ("membership", C.c_int32), ("alpha_cull", C.c_int32)]
 
 
 class SceneS(C.Structure):
@@ -118,9 +118,9 @@ class _Pack:
 
 
 def default_options(tile=(16, 16), bg=(0.0, 0.0, 0.0), near=0.2, dilation=0.3, clamp=1.3,
-                    membership=0) -> dict:
+                    membership=0, alpha_cull=1) -> dict:
     return {"tile": tuple(tile), "bg": tuple(bg), "near": near, "dilation": dilation,
-            "clamp": clamp, "membership": membership}
+            "clamp": clamp, "membership": membership, "alpha_cull": alpha_cull}
 
 
 def _options(o: dict) -> Options:
@@ -133,6 +133,7 @@ def _options(o: dict) -> Options:
         op.bg[k] = bg[k]
     op.tile_w, op.tile_h = o.get("tile", (16, 16))
     op.membership = o.get("membership", 0)
+    op.alpha_cull = o.get("alpha_cull", 1)
     return op
 
 

@@ -52,6 +52,7 @@ typedef struct {
     float bg[3];
     int32_t tile_w, tile_h;
     int32_t membership;   /* 0: pixel square of half-width r; 1: every pixel of a touched tile */
+    int32_t alpha_cull;   /* 1: footprint also clipped to the alpha >= 1/255 bounding box */
 } gco_options;
 
 typedef struct {
@@ -315,6 +316,26 @@ static void bin_one_f32(const gco_scene *sc, const gco_motion *mo, const gco_cam
     fx0 = fmaxf(fx0, 0.0f); fy0 = fmaxf(fy0, 0.0f);
     fx1 = fminf(fx1, (float)(cam->width - 1)); fy1 = fminf(fy1, (float)(cam->height - 1));
     if (!(fx0 <= fx1) || !(fy0 <= fy1)) return;   /* also rejects NaN */
+    /* 14. alpha footprint (binning spec, not in the paper): alpha = o exp(-Q/2) reaches
+       1/255 only where Q <= tau = 2 ln(255 o).  The ellipse Q <= tau_c, tau_c = tau +
+       0.02 + 1e-6 (ia + 2|ib| + ic)(r + 1)^2 (the second term bounds the rounding of an
+       FP32 evaluation of Q over the 3-sigma square), has the half-extents
+       sqrt(tau_c ic / det_c) and sqrt(tau_c ia / det_c); the rectangle is clipped to
+       them.  Opacity <= 1/255: the Gaussian is never blended and is not binned. */
+    if (op->alpha_cull) {
+        float tau = (float)(2.0 * log(255.0 / (1.0 + exp(-(double)sc->opacity_logits[i]))));
+        if (!(tau > 0.0f)) return;
+        float t1 = rf + 1.0f;
+        float mt = ((ia + 2.0f * fabsf(ib)) + ic) * (t1 * t1);
+        float tc = (tau + 0.02f) + 1e-6f * mt;
+        float detc = ia * ic - ib * ib;
+        if (detc > 0.0f) {
+            float xa = sqrtf((tc * ic) / detc), ya = sqrtf((tc * ia) / detc);
+            fx0 = fmaxf(fx0, ceilf((u - xa) - 0.5f)); fx1 = fminf(fx1, floorf((u + xa) - 0.5f));
+            fy0 = fmaxf(fy0, ceilf((v - ya) - 0.5f)); fy1 = fminf(fy1, floorf((v + ya) - 0.5f));
+            if (!(fx0 <= fx1) || !(fy0 <= fy1)) return;
+        }
+    }
     out->visible = 1;
     out->depth = cz;
     out->rect[0] = (int32_t)fx0; out->rect[1] = (int32_t)fx1;

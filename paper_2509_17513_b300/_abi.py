@@ -35,7 +35,7 @@ GC_MEMBER_TILE = 1
 class Options(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("near_plane", C.c_float),
                 ("dilation", C.c_float), ("frustum_clamp", C.c_float), ("bg", C.c_float * 3),
-                ("membership", C.c_int32), ("key_capacity", C.c_int64)]
+                ("membership", C.c_int32), ("key_capacity", C.c_int64), ("alpha_cull", C.c_int32)]
 
 
 class Gaussians(C.Structure):

@@ -43,6 +43,7 @@ gc_status gc_default_options(gc_options *o) {
     o->frustum_clamp = 1.3f;
     o->membership = GC_MEMBER_PIXEL;
     o->key_capacity = 0;
+    o->alpha_cull = 1;
     return GC_OK;
 }
 
@@ -168,6 +169,7 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
     rp.ntx = (cam->width + o.tile_w - 1) / o.tile_w;
     rp.nty = (cam->height + o.tile_h - 1) / o.tile_h;
     rp.membership = o.membership;
+    rp.alpha_cull = o.alpha_cull;
     const int64_t n_tiles = (int64_t)rp.ntx * rp.nty;
     const int64_t hw = (int64_t)cam->width * cam->height;
 

@@ -609,6 +609,7 @@ gc_status build_table(gc_context *ctx, const gc_gaussians *g, const gc_motion *f
         R.rp.ntx = (cam->width + o.tile_w - 1) / o.tile_w;
         R.rp.nty = (cam->height + o.tile_h - 1) / o.tile_h;
         R.rp.membership = o.membership;
+        R.rp.alpha_cull = o.alpha_cull;
         int64_t n_sel = 0;
         R.sel = make_selection(g, rq.layer_mask, n_sel);
         R.n_sel = n_sel;

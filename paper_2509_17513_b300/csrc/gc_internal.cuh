@@ -39,6 +39,7 @@ struct RenderParams {
     int tile_w, tile_h, tile_w_log2, tile_h_log2;
     int ntx, nty;
     int membership;
+    int alpha_cull;
 };
 
 // Attribute source.  FP32 arrays, or BF16/FP8 planes with per-channel scales.

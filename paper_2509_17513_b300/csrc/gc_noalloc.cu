@@ -224,6 +224,7 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
     rp.tile_w_log2 = log2_exact(o.tile_w); rp.tile_h_log2 = log2_exact(o.tile_h);
     rp.ntx = ntx; rp.nty = nty;
     rp.membership = o.membership;
+    rp.alpha_cull = o.alpha_cull;
 
     cudaStream_t s = (cudaStream_t)stream;
     float4 *rec = reinterpret_cast<float4 *>(base + kOffRec);

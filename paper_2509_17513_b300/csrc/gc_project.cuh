@@ -198,6 +198,26 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
         fx1 = fminf(fx1, (float)(cam.width - 1));
         fy1 = fminf(fy1, (float)(cam.height - 1));
         if (!(fx0 <= fx1) || !(fy0 <= fy1)) break;
+        // 14. alpha footprint: o exp(-Q/2) >= 1/255 needs Q <= tau = 2 ln(255 o); the
+        //     ellipse Q <= tau_c (tau plus a margin that covers the blend's FP32 rounding)
+        //     has half-extents sqrt(tau_c ic / det_c), sqrt(tau_c ia / det_c)
+        if (rp.alpha_cull) {
+            const float tau = (float)(2.0 * log(255.0 / (1.0 + exp(-(double)A.logit))));
+            if (!(tau > 0.f)) break;  // opacity <= 1/255: never blended
+            const float t1 = fadd(rf, 1.f);
+            const float mt = fmul(fadd(fadd(ia, fmul(2.f, fabsf(ib))), ic), fmul(t1, t1));
+            const float tc = fadd(fadd(tau, 0.02f), fmul(1e-6f, mt));
+            const float detc = fsub(fmul(ia, ic), fmul(ib, ib));
+            if (detc > 0.f) {
+                const float xa = __fsqrt_rn(fdiv(fmul(tc, ic), detc));
+                const float ya = __fsqrt_rn(fdiv(fmul(tc, ia), detc));
+                fx0 = fmaxf(fx0, ceilf(fsub(fsub(u, xa), 0.5f)));
+                fx1 = fminf(fx1, floorf(fsub(fadd(u, xa), 0.5f)));
+                fy0 = fmaxf(fy0, ceilf(fsub(fsub(v, ya), 0.5f)));
+                fy1 = fminf(fy1, floorf(fsub(fadd(v, ya), 0.5f)));
+                if (!(fx0 <= fx1) || !(fy0 <= fy1)) break;
+            }
+        }
         const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
         const int tx0 = x0 >> rp.tile_w_log2, tx1 = x1 >> rp.tile_w_log2;
         const int ty0 = y0 >> rp.tile_h_log2, ty1 = y1 >> rp.tile_h_log2;

@@ -144,6 +144,7 @@ inline gc_status check_options(gc_context *ctx, const gc_options *o) {
         return fail(ctx, GC_ERR_INVALID_ARG, "membership must be GC_MEMBER_PIXEL or GC_MEMBER_TILE");
     if (o->key_capacity < 0 || o->key_capacity > 0xFFFFFFF0ll)
         return fail(ctx, GC_ERR_INVALID_ARG, "key_capacity out of range");
+    if (o->alpha_cull != 0 && o->alpha_cull != 1) return fail(ctx, GC_ERR_INVALID_ARG, "alpha_cull must be 0 or 1");
     return GC_OK;
 }
 

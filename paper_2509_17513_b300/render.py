@@ -141,7 +141,7 @@ class Renderer:
 
     def __init__(self, device: int = 0, tile=(16, 16), near=0.2, dilation=0.3, clamp=1.3,
                  bg=(0.0, 0.0, 0.0), membership: int = _abi.GC_MEMBER_PIXEL,
-                 key_capacity: int = 0):
+                 key_capacity: int = 0, alpha_cull: bool = True):
         L = lib()
         o = _abi.Options()
         check(L.gc_default_options(C.byref(o)))
@@ -151,6 +151,7 @@ class Renderer:
             o.bg[k] = float(bg[k])
         o.membership = int(membership)
         o.key_capacity = int(key_capacity)
+        o.alpha_cull = 1 if alpha_cull else 0
         self.options = o
         self.device = int(device)
         h = C.c_void_p()
@@ -179,6 +180,8 @@ class Renderer:
                 o.bg[k] = float(kw["bg"][k])
         if "membership" in kw:
             o.membership = int(kw["membership"])
+        if "alpha_cull" in kw:
+            o.alpha_cull = 1 if kw["alpha_cull"] else 0
         check(lib().gc_set_options(self.ctx, C.byref(o)), self.ctx)
 
     def forward(self, gs: GaussianSet, motion: MotionFrame | None, layer_mask: int, camera,

@@ -187,3 +187,34 @@ def test_hier1080_at_scale(gc, hier1080, frame, level):
     assert ok.mean() > 0.95
     assert err[ok].max() <= PIX_TOL, float(err[ok].max())
     assert np.array_equal(gpu["nb"][pix[:, 1], pix[:, 0]][ok], ref["n_blended"][ok])
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8)])
+def test_alpha_cull_changes_lists_not_results(gc, tile):
+    """The alpha footprint shortens the tile lists; images and per-pixel state are
+    bit-identical to the 3-sigma-only lists (the removed pairs were skipped by the
+    compositing rule anyway) and the gradients agree up to the order of the per-Gaussian
+    sum over tiles (the removed tiles held exact zeros)."""
+    rng = np.random.default_rng(91)
+    scene = scenes.make_hier_scene(rng, 20000, 6, 3, 16)
+    motion = scenes.random_motion(rng, 16, 2)
+    cam = scenes.orbit_camera(0.9, 4.0, 400, 300)
+    gs = gc.GaussianSet.from_scene(scene)
+    mo = gc.MotionFrame.from_motion(motion, 1)
+    up = torch.randn((3, 300, 400), generator=torch.Generator().manual_seed(2)).cuda()
+    out = {}
+    for cull in (False, True):
+        r = gc.Renderer(0, tile=tile, alpha_cull=cull)
+        saved = gc.Saved(r)
+        img = r.forward(gs, mo, 63, cam, saved)
+        T, nb = r.pixel_state(saved)
+        g = r.backward(saved, gs, mo, up)
+        torch.cuda.synchronize()
+        out[cull] = (img, T, nb, {k: v.clone() for k, v in g.items()}, r.stats(saved)["n_keys"])
+    assert torch.equal(out[False][0], out[True][0])
+    assert torch.equal(out[False][1], out[True][1])
+    assert torch.equal(out[False][2], out[True][2])
+    for k in out[False][3]:
+        a, b = out[True][3][k], out[False][3][k]
+        assert float((a - b).abs().max()) <= 1e-5 * float(b.abs().max()), k
+    assert out[True][4] < 0.85 * out[False][4]

@@ -236,10 +236,11 @@ def test_mirror_agrees_with_fp64_geometry(oracle_lib):
 
 
 def test_mirror_rect_is_pixel_square(oracle_lib):
-    """Every pixel of the rectangle has its centre within r of (u, v), and its neighbours do not."""
+    """Without the alpha cull, every pixel of the rectangle has its centre within r of
+    (u, v), and its neighbours do not."""
     w = scenes.tiny()
     cam = w.cameras[0]
-    opts = oracle_lib.default_options()
+    opts = oracle_lib.default_options(alpha_cull=0)
     b = oracle_lib.bin_f32(w.scene, None, 0, cam, opts, 1)
     for j in range(0, w.scene.n, 11):
         if not b["visible"][j]:
