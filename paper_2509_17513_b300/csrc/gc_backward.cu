@@ -27,27 +27,20 @@ namespace gc {
 namespace {
 
 
-#ifndef GC_BWD_PPT
-#define GC_BWD_PPT 1  // pixels per thread in the backward blend (1 measured fastest on B300)
-#endif
-
 // One CTA per tile of a single image.
-template <int TW, int TH, int PPT>
-__global__ void __launch_bounds__(256 / PPT) k_blend_bwd(
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) k_blend_bwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, int ntx,
     int tw_log2, int th_log2, float bg0, float bg1, float bg2, int membership,
     const float *__restrict__ final_T, const uint32_t *__restrict__ n_contrib,
     const float *__restrict__ dimg, float *__restrict__ part, int64_t K,
     int32_t *__restrict__ tile_rmax) {
-    constexpr int NW = 256 / PPT / 32;
-    __shared__ float4 sA[256], sB[256], sC[256], sD[256];
-    __shared__ float wpart[32 * NW * 9];
-    __shared__ uint32_t s_last_max;
+    __shared__ __align__(16) BwdSmem sm;
     const int tile = blockIdx.x;
-    blend_bwd_tile<TW, TH, PPT>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, offsets, 0u, W, H,
-                                tw_log2, th_log2, bg0, bg1, bg2, membership, final_T, n_contrib, dimg, part,
-                                tile_rmax + tile, sA, sB, sC, sD, wpart, &s_last_max);
+    const TileBwd o{final_T, n_contrib, dimg, bg0, bg1, bg2, W, H, membership, tw_log2, th_log2, 0u};
+    blend_bwd_tile<TW, TH>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, offsets, o, part,
+                           tile_rmax + tile, sm);
 }
 
 // One warp per rank: sum of the Gaussian's partials over its tiles (entry-major
@@ -191,13 +184,12 @@ cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
     ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp.ntx, rp.tile_w_log2,       \
         rp.tile_h_log2, rp.bg[0], rp.bg[1], rp.bg[2], rp.membership, final_T, n_contrib,      \
         dL_dimg, part, K, tile_rmax
-    constexpr int kThreads = 256 / GC_BWD_PPT;
     if (rp.tile_w == 16 && rp.tile_h == 16)
-        k_blend_bwd<16, 16, GC_BWD_PPT><<<tiles, kThreads, 0, st>>>(GC_BWD_ARGS);
+        k_blend_bwd<16, 16><<<tiles, 256, 0, st>>>(GC_BWD_ARGS);
     else if (rp.tile_w == 8 && rp.tile_h == 32)
-        k_blend_bwd<8, 32, GC_BWD_PPT><<<tiles, kThreads, 0, st>>>(GC_BWD_ARGS);
+        k_blend_bwd<8, 32><<<tiles, 256, 0, st>>>(GC_BWD_ARGS);
     else if (rp.tile_w == 32 && rp.tile_h == 8)
-        k_blend_bwd<32, 8, GC_BWD_PPT><<<tiles, kThreads, 0, st>>>(GC_BWD_ARGS);
+        k_blend_bwd<32, 8><<<tiles, 256, 0, st>>>(GC_BWD_ARGS);
     else
         return cudaErrorInvalidValue;
 #undef GC_BWD_ARGS

@@ -42,6 +42,23 @@ struct BatchReq {
 
 namespace {
 
+// Grid of a persistent kernel: every CTA (256 threads) that fits on the device at once,
+// queried once per kernel (the device's SM count times resident CTAs per SM).
+template <auto Kernel>
+int64_t persistent_grid() {
+    static int64_t cached = 0;
+    if (!cached) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Kernel, 256, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 4;
+        cudaGetLastError();
+        cached = (int64_t)sms * per_sm;
+    }
+    return cached;
+}
+
 // Last q with base[q] <= x, over q in [0, n).
 __device__ __forceinline__ int find_req(const int64_t *base, int n, int64_t x) {
     int lo = 0, hi = n - 1;
@@ -265,22 +282,30 @@ __global__ void __launch_bounds__(256) k_batch_blend_fwd(const BatchReq *__restr
                                                          float *__restrict__ final_T,
                                                          uint32_t *__restrict__ n_contrib,
                                                          unsigned long long *counter) {
-    __shared__ float4 sA[256], sB[256], sC[256];
-    __shared__ long long s_tile;
+    __shared__ __align__(16) FwdSmem sm;
+    __shared__ TileOut s_out;
+    __shared__ int4 s_tile;  // tx, ty, range start, range end (tx < 0: no tile left)
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(counter, 1ull);
+        if (threadIdx.x == 0) {
+            const long long t = (long long)atomicAdd(counter, 1ull);
+            if (t < n_tiles) {
+                const int q = find_req(tile_base, n_req, t);
+                const BatchReq &R = reqs[q];
+                const int local = (int)(t - R.tile_base);
+                const uint2 rg = ranges[t];
+                s_tile = make_int4(local % R.rp.ntx, local / R.rp.ntx, (int)rg.x, (int)rg.y);
+                s_out = TileOut{R.image, final_T + R.pixel_base, n_contrib + R.pixel_base, nullptr, nullptr,
+                                R.rp.bg[0], R.rp.bg[1], R.rp.bg[2], R.cam.width, R.cam.height, R.rp.membership};
+            } else {
+                s_tile = make_int4(-1, 0, 0, 0);
+            }
+        }
         __syncthreads();
-        const long long t = s_tile;
+        const int4 tl = s_tile;
+        if (tl.x < 0) break;
+        blend_fwd_tile<TW, TH, false>(tl.x, tl.y, make_uint2((uint32_t)tl.z, (uint32_t)tl.w), sorted_vals, ranked,
+                                      s_out, sm);
         __syncthreads();
-        if (t >= n_tiles) break;
-        const int q = find_req(tile_base, n_req, t);
-        const BatchReq &R = reqs[q];
-        const int local = (int)(t - R.tile_base);
-        const int ntx = R.rp.ntx;
-        blend_fwd_tile<TW, TH, 1>(local % ntx, local / ntx, ranges[t], sorted_vals, ranked, R.cam.width,
-                                  R.cam.height, R.rp.bg[0], R.rp.bg[1], R.rp.bg[2], R.rp.membership, R.image,
-                                  final_T + R.pixel_base, n_contrib + R.pixel_base, nullptr, nullptr, sA, sB,
-                                  sC);
     }
 }
 
@@ -297,25 +322,32 @@ __global__ void __launch_bounds__(256) k_batch_blend_bwd(const BatchReq *__restr
                                                          const float *const *__restrict__ dimgs,
                                                          float *__restrict__ part, int32_t *__restrict__ rmax,
                                                          unsigned long long *counter) {
-    __shared__ float4 sA[256], sB[256], sC[256], sD[256];
-    __shared__ float wpart[32 * 8 * 9];
-    __shared__ uint32_t s_last_max;
-    __shared__ long long s_tile;
+    __shared__ __align__(16) BwdSmem sm;
+    __shared__ TileBwd s_in;
+    __shared__ int4 s_tile;    // tx, ty, range start, range end (tx < 0: no tile left)
+    __shared__ long long s_t;  // global tile index
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(counter, 1ull);
+        if (threadIdx.x == 0) {
+            const long long t = (long long)atomicAdd(counter, 1ull);
+            if (t < n_tiles) {
+                const int q = find_req(tile_base, n_req, t);
+                const BatchReq &R = reqs[q];
+                const int local = (int)(t - R.tile_base);
+                const uint2 rg = ranges[t];
+                s_tile = make_int4(local % R.rp.ntx, local / R.rp.ntx, (int)rg.x, (int)rg.y);
+                s_t = t;
+                s_in = TileBwd{final_T + R.pixel_base, n_contrib + R.pixel_base, dimgs[q], R.rp.bg[0], R.rp.bg[1],
+                               R.rp.bg[2], R.cam.width, R.cam.height, R.rp.membership, R.rp.tile_w_log2,
+                               R.rp.tile_h_log2, eshift[q]};
+            } else {
+                s_tile = make_int4(-1, 0, 0, 0);
+            }
+        }
         __syncthreads();
-        const long long t = s_tile;
-        __syncthreads();
-        if (t >= n_tiles) break;
-        const int q = find_req(tile_base, n_req, t);
-        const BatchReq &R = reqs[q];
-        const int local = (int)(t - R.tile_base);
-        const int ntx = R.rp.ntx;
-        blend_bwd_tile<TW, TH, 1>(local % ntx, local / ntx, ranges[t], sorted_vals, ranked, offsets, eshift[q],
-                                  R.cam.width, R.cam.height, R.rp.tile_w_log2, R.rp.tile_h_log2, R.rp.bg[0],
-                                  R.rp.bg[1], R.rp.bg[2], R.rp.membership, final_T + R.pixel_base,
-                                  n_contrib + R.pixel_base, dimgs[q], part, rmax + t, sA, sB, sC, sD, wpart,
-                                  &s_last_max);
+        const int4 tl = s_tile;
+        if (tl.x < 0) break;
+        blend_bwd_tile<TW, TH>(tl.x, tl.y, make_uint2((uint32_t)tl.z, (uint32_t)tl.w), sorted_vals, ranked, offsets,
+                               s_in, part, rmax + s_t, sm);
         __syncthreads();
     }
 }
@@ -858,13 +890,16 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     GC_CUDA(ctx, cudaMemsetAsync(B.counter.p, 0, 8, s));
     {
         const uint32_t *sv = (K > 0 && items > 0) ? B.tvals[B.tile_buf].as<uint32_t>() : nullptr;
-        const unsigned grid = (unsigned)std::min<int64_t>(std::max<int64_t>(tiles, 1), 148 * 6);
         unsigned long long *ctr = B.counter.as<unsigned long long>();
+        auto grid = [&](int64_t g) { return (unsigned)std::min<int64_t>(std::max<int64_t>(tiles, 1), g); };
 #define GC_BB_ARGS rq_dev, tb_dev, n_req, tiles, B.ranges.as<uint2>(), sv, B.ranked.as<float4>(), \
                    B.final_T.as<float>(), B.n_contrib.as<uint32_t>(), ctr
-        if (o.tile_w == 16) gc::k_batch_blend_fwd<16, 16><<<grid, 256, 0, s>>>(GC_BB_ARGS);
-        else if (o.tile_w == 8) gc::k_batch_blend_fwd<8, 32><<<grid, 256, 0, s>>>(GC_BB_ARGS);
-        else gc::k_batch_blend_fwd<32, 8><<<grid, 256, 0, s>>>(GC_BB_ARGS);
+        if (o.tile_w == 16)
+            gc::k_batch_blend_fwd<16, 16><<<grid(gc::persistent_grid<gc::k_batch_blend_fwd<16, 16>>()), 256, 0, s>>>(GC_BB_ARGS);
+        else if (o.tile_w == 8)
+            gc::k_batch_blend_fwd<8, 32><<<grid(gc::persistent_grid<gc::k_batch_blend_fwd<8, 32>>()), 256, 0, s>>>(GC_BB_ARGS);
+        else
+            gc::k_batch_blend_fwd<32, 8><<<grid(gc::persistent_grid<gc::k_batch_blend_fwd<32, 8>>()), 256, 0, s>>>(GC_BB_ARGS);
 #undef GC_BB_ARGS
         gc::note_launches(1);
         GC_CUDA(ctx, cudaGetLastError());
@@ -941,15 +976,18 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
     GC_CUDA(ctx, cudaMemsetAsync(B.counter.p, 0, 8, s));
     {
         const uint32_t *sv = (B.K_cap > 0 && items > 0) ? B.tvals[B.tile_buf].as<uint32_t>() : nullptr;
-        const unsigned grid = (unsigned)std::min<int64_t>(std::max<int64_t>(B.n_tiles, 1), 148 * 4);
         unsigned long long *ctr = B.counter.as<unsigned long long>();
+        auto grid = [&](int64_t g) { return (unsigned)std::min<int64_t>(std::max<int64_t>(B.n_tiles, 1), g); };
 #define GC_BB_ARGS rq_dev, tb_dev, n_req, B.n_tiles, B.ranges.as<uint2>(), sv, B.ranked.as<float4>(),            \
                    B.offsets.as<uint32_t>(), B.eshift.as<uint32_t>(), B.final_T.as<float>(),                     \
                    B.n_contrib.as<uint32_t>(), B.dimg_dev.as<const float *>(), B.part.as<float>(),              \
                    B.rmax.as<int32_t>(), ctr
-        if (B.opt.tile_w == 16) gc::k_batch_blend_bwd<16, 16><<<grid, 256, 0, s>>>(GC_BB_ARGS);
-        else if (B.opt.tile_w == 8) gc::k_batch_blend_bwd<8, 32><<<grid, 256, 0, s>>>(GC_BB_ARGS);
-        else gc::k_batch_blend_bwd<32, 8><<<grid, 256, 0, s>>>(GC_BB_ARGS);
+        if (B.opt.tile_w == 16)
+            gc::k_batch_blend_bwd<16, 16><<<grid(gc::persistent_grid<gc::k_batch_blend_bwd<16, 16>>()), 256, 0, s>>>(GC_BB_ARGS);
+        else if (B.opt.tile_w == 8)
+            gc::k_batch_blend_bwd<8, 32><<<grid(gc::persistent_grid<gc::k_batch_blend_bwd<8, 32>>()), 256, 0, s>>>(GC_BB_ARGS);
+        else
+            gc::k_batch_blend_bwd<32, 8><<<grid(gc::persistent_grid<gc::k_batch_blend_bwd<32, 8>>()), 256, 0, s>>>(GC_BB_ARGS);
 #undef GC_BB_ARGS
         gc::note_launches(1);
         GC_CUDA(ctx, cudaGetLastError());

@@ -81,22 +81,18 @@ __global__ void k_tile_ranges(const uint32_t *__restrict__ keys, const uint32_t 
     }
 }
 
-#ifndef GC_FWD_PPT
-#define GC_FWD_PPT 1  // pixels per thread in the forward blend (1 measured fastest on B300)
-#endif
-
-// One CTA per tile of a single image.
-template <int TW, int TH, int PPT>
-__global__ void __launch_bounds__(256 / PPT) k_blend_fwd(
+// One CTA per tile of a single image (with the per-pixel blended / walked counts).
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) k_blend_fwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, int W, int H, int ntx, float bg0, float bg1, float bg2,
     int membership, float *__restrict__ image, float *__restrict__ final_T,
     uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ n_blended,
     uint32_t *__restrict__ n_walked) {
-    __shared__ float4 sA[256], sB[256], sC[256];
+    __shared__ __align__(16) FwdSmem sm;
     const int tile = blockIdx.x;
-    blend_fwd_tile<TW, TH, PPT>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, W, H, bg0, bg1,
-                                bg2, membership, image, final_T, n_contrib, n_blended, n_walked, sA, sB, sC);
+    const TileOut o{image, final_T, n_contrib, n_blended, n_walked, bg0, bg1, bg2, W, H, membership};
+    blend_fwd_tile<TW, TH, true>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, o, sm);
 }
 
 // Single CTA: 2D inclusive prefix of the tile difference grid (rows, then columns)
@@ -237,13 +233,12 @@ cudaError_t launch_blend_fwd(const uint2 *ranges, const uint32_t *sorted_vals,
 #define GC_BLEND_ARGS                                                                          \
     ranges, sorted_vals, ranked, cam.width, cam.height, rp.ntx, rp.bg[0], rp.bg[1], rp.bg[2], \
         rp.membership, image, final_T, n_contrib, n_blended, n_walked
-    constexpr int kThreads = 256 / GC_FWD_PPT;
     if (rp.tile_w == 16 && rp.tile_h == 16)
-        k_blend_fwd<16, 16, GC_FWD_PPT><<<tiles, kThreads, 0, st>>>(GC_BLEND_ARGS);
+        k_blend_fwd<16, 16><<<tiles, 256, 0, st>>>(GC_BLEND_ARGS);
     else if (rp.tile_w == 8 && rp.tile_h == 32)
-        k_blend_fwd<8, 32, GC_FWD_PPT><<<tiles, kThreads, 0, st>>>(GC_BLEND_ARGS);
+        k_blend_fwd<8, 32><<<tiles, 256, 0, st>>>(GC_BLEND_ARGS);
     else if (rp.tile_w == 32 && rp.tile_h == 8)
-        k_blend_fwd<32, 8, GC_FWD_PPT><<<tiles, kThreads, 0, st>>>(GC_BLEND_ARGS);
+        k_blend_fwd<32, 8><<<tiles, 256, 0, st>>>(GC_BLEND_ARGS);
     else
         return cudaErrorInvalidValue;
     note_launches(1);

@@ -17,251 +17,256 @@ __device__ __forceinline__ void unpack_rect(float4 r2, int &x0, int &x1, int &y0
     y1 = (int)(ry >> 16);
 }
 
-// Per-pixel front-to-back state.
-struct FwdPix {
-    float T, C0, C1, C2;
-    uint32_t last, nb, walked;
-    bool done;
-};
-
-// One compositing step of Eq. 2 for one pixel and the staged Gaussian (a, bb, blue).
-__device__ __forceinline__ void fwd_step(FwdPix &P, float pcx, float pcy, const float4 &a,
-                                         const float4 &bb, float blue, uint32_t idx) {
-    const float dx = pcx - a.x, dy = pcy - a.y;
-    const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
-    if (p2 > 0.f) return;
-    float G;
-    const float alpha = fminf(kAlphaMax, blend_raw_alpha(bb.y, p2, G));
-    if (alpha < kAlphaMin) return;
-    const float Tn = P.T * (1.f - alpha);
-    if (Tn < kTStop) {
-        P.done = true;
-        P.walked = idx + 1;
-        return;
-    }
-    const float w = alpha * P.T;
-    P.C0 = fmaf(bb.z, w, P.C0);
-    P.C1 = fmaf(bb.w, w, P.C1);
-    P.C2 = fmaf(blue, w, P.C2);
-    P.T = Tn;
-    P.last = idx + 1;
-    ++P.nb;
+// Pixel layout of a tile's 256 threads: each warp owns an 8 x 4 block of the tile
+// (blocks row-major, TW / 8 per block row), lane l the pixel (l % 8, l / 8) of its
+// block.  Square warp footprints keep a small Gaussian inside few warps, so most warps
+// skip most list entries with one uniform test.
+template <int TW, int TH>
+__device__ __forceinline__ void pixel_of_thread(int t, int &lx, int &ly) {
+    static_assert(TW % 8 == 0 && TH % 4 == 0 && TW * TH == 256, "tile must be 256 pixels of 8x4 blocks");
+    constexpr int BX = TW / 8;
+    const int w = t >> 5, l = t & 31;
+    lx = (w % BX) * 8 + (l & 7);
+    ly = (w / BX) * 4 + (l >> 3);
 }
 
-// Front-to-back compositing (Eq. 2) of tile (tx, ty) of one image by a CTA of
-// 256 / PPT threads; thread t owns the PPT vertically adjacent pixels
-// (t % TW, PPT * (t / TW) + i), so each staged Gaussian is read from shared memory
-// once per PPT pixels.  Batches of up to 256 list entries are staged in shared
-// memory (sA/sB/sC, 256 float4 each), gathered from the depth-ranked records; a
-// pixel stops when blending the next Gaussian would take its transmittance below
-// 1e-4, the CTA as soon as all its pixels did.  Per-pixel outputs are indexed
-// py * W + px from the given image-local pointers.
-template <int TW, int TH, int PPT>
-__device__ __forceinline__ void blend_fwd_tile(
-    int tx, int ty, uint2 range, const uint32_t *__restrict__ sorted_vals,
-    const float4 *__restrict__ ranked, int W, int H, float bg0, float bg1, float bg2,
-    int membership, float *__restrict__ image, float *__restrict__ final_T,
-    uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ n_blended,
-    uint32_t *__restrict__ n_walked, float4 *sA, float4 *sB, float4 *sC) {
-    static_assert(TW * TH == 256, "tile must hold 256 pixels");
-    constexpr int NT = 256 / PPT;
-    const int lx = threadIdx.x % TW, lyb = PPT * (threadIdx.x / TW);
-    const int px = tx * TW + lx;
-    const float pcx = (float)px + 0.5f;
-    const uint32_t xbit = 1u << lx;
-    const int n = (int)(range.y - range.x);
+// Membership mask of warp w's 32 pixels for an entry whose footprint covers the tile
+// columns in cm and the tile rows in rm (bit i = column / row i).
+template <int TW>
+__device__ __forceinline__ uint32_t warp_mask(uint32_t cm, uint32_t rm, int w) {
+    constexpr int BX = TW / 8;
+    const uint32_t cb = (cm >> ((w % BX) * 8)) & 0xffu;
+    const uint32_t rb = (rm >> ((w / BX) * 4)) & 0xfu;
+    const uint32_t spread = (rb & 1u) | ((rb & 2u) << 7) | ((rb & 4u) << 14) | ((rb & 8u) << 21);
+    return cb * spread;  // bit 8 r + c = column c and row r of the block
+}
 
-    FwdPix P[PPT];
-#pragma unroll
-    for (int i = 0; i < PPT; ++i) P[i] = {1.f, 0.f, 0.f, 0.f, 0u, 0u, 0u, !(px < W && ty * TH + lyb + i < H)};
-    auto all_done = [&]() {
-        bool d = true;
-#pragma unroll
-        for (int i = 0; i < PPT; ++i) d = d && P[i].done;
-        return d;
-    };
+// Column and row masks of an entry's pixel rectangle within tile (tx, ty).
+template <int TW, int TH>
+__device__ __forceinline__ void rect_masks(float4 r2, int tx, int ty, int membership, uint32_t &cm,
+                                           uint32_t &rm) {
+    cm = 0xffffffffu;
+    rm = 0xffffffffu;
+    if (membership == GC_MEMBER_PIXEL) {
+        int x0, x1, y0, y1;
+        unpack_rect(r2, x0, x1, y0, y1);
+        const int lx0 = max(x0 - tx * TW, 0), lx1 = min(x1 - tx * TW, TW - 1);
+        const int ly0 = max(y0 - ty * TH, 0), ly1 = min(y1 - ty * TH, TH - 1);
+        cm = (lx1 >= lx0) ? ((0xffffffffu >> (31 - lx1)) & (0xffffffffu << lx0)) : 0u;
+        rm = (ly1 >= ly0) ? ((0xffffffffu >> (31 - ly1)) & (0xffffffffu << ly0)) : 0u;
+    }
+}
+
+template <int TW>
+__device__ __forceinline__ void store_masks(uint32_t *m8, uint32_t cm, uint32_t rm) {
+    uint4 *mo = reinterpret_cast<uint4 *>(m8);
+    mo[0] = make_uint4(warp_mask<TW>(cm, rm, 0), warp_mask<TW>(cm, rm, 1), warp_mask<TW>(cm, rm, 2),
+                       warp_mask<TW>(cm, rm, 3));
+    mo[1] = make_uint4(warp_mask<TW>(cm, rm, 4), warp_mask<TW>(cm, rm, 5), warp_mask<TW>(cm, rm, 6),
+                       warp_mask<TW>(cm, rm, 7));
+}
+
+// Shared staging of one batch of up to 256 list entries for the forward blend:
+//   a = {u, v, A, B}, b = {C, opacity}  (what every walked pair reads),
+//   c = {r, g, b, -}                    (read only when the pair is blended),
+//   m = per entry and warp, the mask of the warp's pixels the entry may touch.
+struct FwdSmem {
+    float4 a[256];
+    float2 b[256];
+    float4 c[256];
+    uint32_t m[256 * 8];
+};
+
+// Where a tile's pixels go: image planes (3 x H x W), final transmittance, list position
+// after the last blended entry, optional counts, background.  The batched kernels keep it
+// in shared memory so that it holds no registers during the blend.
+struct TileOut {
+    float *image, *final_T;
+    uint32_t *n_contrib, *n_blended, *n_walked;
+    float bg0, bg1, bg2;
+    int W, H, membership;
+};
+
+// Front-to-back compositing (Eq. 2) of tile (tx, ty) of one image by a CTA of 256
+// threads, one pixel each.  Batches of up to 256 list entries are staged in shared
+// memory, gathered from the depth-ranked records.  Per walked entry a lane first tests
+// the entry's membership mask against its own bit (cleared once its pixel is done), then
+// evaluates the Gaussian; the colour is read only for blended pairs.  A pixel stops when
+// blending the next Gaussian would take its transmittance below 1e-4, a warp (checked
+// every 16 entries) when all its pixels did, the CTA when all warps did.  STATS adds
+// the per-pixel blended and walked counts.
+template <int TW, int TH, bool STATS>
+__device__ __forceinline__ void blend_fwd_tile(int tx, int ty, uint2 range,
+                                               const uint32_t *__restrict__ sorted_vals,
+                                               const float4 *__restrict__ ranked, const TileOut &o,
+                                               FwdSmem &sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int lx, ly;
+    pixel_of_thread<TW, TH>((int)threadIdx.x, lx, ly);
+    const int px = tx * TW + lx, py = ty * TH + ly;
+    const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
+    const int n = (int)(range.y - range.x);
+    const bool inside = px < o.W && py < o.H;
+    const int membership = o.membership;
+    uint32_t act = inside ? (1u << lane) : 0u;  // this lane's bit while the pixel is active
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    uint32_t last = 0u, nb = 0u, walked = (uint32_t)n;
 
     for (int b = 0; b < n; b += 256) {
-        if (__syncthreads_count(all_done()) == NT) break;
-#pragma unroll
-        for (int h = 0; h < PPT; ++h) {
-            const int slot = (int)threadIdx.x + NT * h;
-            const int idx = b + slot;
+        if (__syncthreads_count(act != 0u) == 0) break;
+        {
+            const int idx = b + (int)threadIdx.x;
             if (idx < n) {
                 const uint32_t r = sorted_vals[range.x + idx];
                 const float4 a = ranked[3 * (size_t)r];
                 const float4 bb = ranked[3 * (size_t)r + 1];
                 const float4 c = ranked[3 * (size_t)r + 2];
-                uint32_t cm = 0xffffffffu, rm = 0xffffffffu;
-                if (membership == GC_MEMBER_PIXEL) {
-                    int x0, x1, y0, y1;
-                    unpack_rect(c, x0, x1, y0, y1);
-                    const int lx0 = max(x0 - tx * TW, 0), lx1 = min(x1 - tx * TW, TW - 1);
-                    const int ly0r = max(y0 - ty * TH, 0), ly1r = min(y1 - ty * TH, TH - 1);
-                    cm = (lx1 >= lx0) ? ((0xffffffffu >> (31 - lx1)) & (0xffffffffu << lx0)) : 0u;
-                    rm = (ly1r >= ly0r) ? ((0xffffffffu >> (31 - ly1r)) & (0xffffffffu << ly0r)) : 0u;
-                }
-                sA[slot] = a;
-                sB[slot] = bb;
-                sC[slot] = make_float4(c.x, __uint_as_float(cm), __uint_as_float(rm), 0.f);
+                uint32_t cm, rm;
+                rect_masks<TW, TH>(c, tx, ty, membership, cm, rm);
+                sm.a[threadIdx.x] = a;
+                sm.b[threadIdx.x] = make_float2(bb.x, bb.y);
+                sm.c[threadIdx.x] = make_float4(bb.z, bb.w, c.x, 0.f);
+                store_masks<TW>(&sm.m[8 * threadIdx.x], cm, rm);
             }
         }
         __syncthreads();
         const int cnt = min(256, n - b);
-        for (int k = 0; k < cnt; ++k) {
-            if (all_done()) break;
-            const float4 c = sC[k];
-            if (!(__float_as_uint(c.y) & xbit)) continue;
-            const uint32_t rm = __float_as_uint(c.z) >> lyb;  // bit i: row lyb + i of the tile
-            bool any = false;
-#pragma unroll
-            for (int i = 0; i < PPT; ++i) any = any || (!P[i].done && ((rm >> i) & 1u));
-            if (!any) continue;
-            const float4 a = sA[k];
-            const float4 bb = sB[k];
-            const uint32_t idx = (uint32_t)(b + k);
-#pragma unroll
-            for (int i = 0; i < PPT; ++i)
-                if (!P[i].done && ((rm >> i) & 1u))
-                    fwd_step(P[i], pcx, (float)(ty * TH + lyb + i) + 0.5f, a, bb, c.x, idx);
+        for (int k0 = 0; k0 < cnt; k0 += 16) {
+            if (__ballot_sync(0xffffffffu, act != 0u) == 0u) break;  // the whole warp is done
+            const int k1 = min(k0 + 16, cnt);
+#pragma unroll 4
+            for (int k = k0; k < k1; ++k) {
+                const uint32_t wm = sm.m[8 * k + warp];
+                if ((wm & act) == 0u) continue;
+                const float4 a = sm.a[k];
+                const float2 bb = sm.b[k];
+                const float dx = pcx - a.x, dy = pcy - a.y;
+                const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
+                if (p2 > 0.f) continue;
+                float G;
+                const float alpha = fminf(kAlphaMax, blend_raw_alpha(bb.y, p2, G));
+                if (alpha < kAlphaMin) continue;
+                const float Tn = T * (1.f - alpha);
+                if (Tn < kTStop) {
+                    act = 0u;
+                    walked = (uint32_t)(b + k + 1);
+                    continue;
+                }
+                const float4 col = sm.c[k];
+                const float w = alpha * T;
+                C0 = fmaf(col.x, w, C0);
+                C1 = fmaf(col.y, w, C1);
+                C2 = fmaf(col.z, w, C2);
+                T = Tn;
+                last = (uint32_t)(b + k + 1);
+                if (STATS) ++nb;
+            }
         }
     }
-    const size_t hw = (size_t)W * H;
-#pragma unroll
-    for (int i = 0; i < PPT; ++i) {
-        const int py = ty * TH + lyb + i;
-        if (px < W && py < H) {
-            const size_t p = (size_t)py * W + px;
-            image[p] = fmaf(P[i].T, bg0, P[i].C0);
-            image[hw + p] = fmaf(P[i].T, bg1, P[i].C1);
-            image[2 * hw + p] = fmaf(P[i].T, bg2, P[i].C2);
-            final_T[p] = P[i].T;
-            n_contrib[p] = P[i].last;
-            if (n_blended) n_blended[p] = P[i].nb;
-            if (n_walked) n_walked[p] = P[i].done ? P[i].walked : (uint32_t)n;
+    if (inside) {
+        const int W = o.W;
+        const size_t hw = (size_t)W * o.H;
+        const size_t p = (size_t)py * W + px;
+        o.image[p] = fmaf(T, o.bg0, C0);
+        o.image[hw + p] = fmaf(T, o.bg1, C1);
+        o.image[2 * hw + p] = fmaf(T, o.bg2, C2);
+        o.final_T[p] = T;
+        o.n_contrib[p] = last;
+        if (STATS) {
+            if (o.n_blended) o.n_blended[p] = nb;
+            if (o.n_walked) o.n_walked[p] = walked;
         }
     }
 }
 
-// Per-pixel reverse state.
-struct BwdPix {
-    float T, A0, A1, A2, g0, g1, g2;
-    uint32_t last;
+// Shared staging for the reverse blend: a, b as in the forward; c = {r, g, b, a_nat} and
+// d = {b_nat, c_nat} (colour and natural conic, read only for blended pairs); m the warp
+// masks; e the entries' emit positions; wpart the per-warp sums of a group of 32 entries.
+struct BwdSmem {
+    float4 a[256];
+    float2 b[256];
+    float4 c[256];
+    float2 d[256];
+    uint32_t m[256 * 8];
+    uint32_t e[256];
+    float wpart[32][8][9];
+    uint32_t last_max;
 };
 
-// Reverse step of Eq. 2 for one pixel and list entry k; adds the pixel's nine partial
-// derivatives (du, dv, da, db, dc, dopacity, dr, dg, db) to v.  Returns whether the
-// entry was blended into the pixel.
-__device__ __forceinline__ bool bwd_step(BwdPix &P, float pcx, float pcy, const float4 &a,
-                                         const float4 &bb, const float4 &nat, float blue, float *v) {
-    const float dx = pcx - a.x, dy = pcy - a.y;
-    const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
-    if (p2 > 0.f) return false;
-    float G;
-    const float a0 = blend_raw_alpha(bb.y, p2, G);
-    const float alpha = fminf(kAlphaMax, a0);
-    if (alpha < kAlphaMin) return false;
-    P.T = P.T / (1.f - alpha);
-    const float w = alpha * P.T;
-    v[6] += w * P.g0;
-    v[7] += w * P.g1;
-    v[8] += w * P.g2;
-    const float dal = P.T * (P.g0 * (bb.z - P.A0) + P.g1 * (bb.w - P.A1) + P.g2 * (blue - P.A2));
-    P.A0 = fmaf(alpha, bb.z - P.A0, P.A0);
-    P.A1 = fmaf(alpha, bb.w - P.A1, P.A1);
-    P.A2 = fmaf(alpha, blue - P.A2, P.A2);
-    if (!(a0 > kAlphaMax)) {
-        v[5] += G * dal;
-        const float dp = alpha * dal;  // dL/dpower (natural exponent)
-        v[0] += (nat.x * dx + nat.y * dy) * dp;
-        v[1] += (nat.y * dx + nat.z * dy) * dp;
-        v[2] += -0.5f * dx * dx * dp;
-        v[3] += -dx * dy * dp;
-        v[4] += -0.5f * dy * dy * dp;
-    }
-    return true;
-}
+// What the reverse blend of a tile reads besides the lists: saved per-pixel state,
+// dL/dimage, background, image size, membership rule and entry-position parameters.
+struct TileBwd {
+    const float *final_T;
+    const uint32_t *n_contrib;
+    const float *dimg;
+    float bg0, bg1, bg2;
+    int W, H, membership, tw_log2, th_log2;
+    uint32_t entry_shift;
+};
 
-// Reverse compositing of tile (tx, ty) of one image by a CTA of 256 / PPT
-// threads, each owning PPT vertically adjacent pixels.  For every list entry, the
-// nine partials are summed over the thread's pixels, then over the warp with a
-// transposing butterfly (values 0-7 spread over lane groups, 9 shuffles) plus a
-// plain butterfly for value 8, then over the warps in order, and stored at the
-// entry's emit position offsets[r] + entry_shift + (index of the tile in the
-// Gaussian's tile rectangle).  *tile_rmax receives the largest rank that may have
-// contributed (-1: none).  Shared scratch: sA..sD (256 float4 each), wpart_raw
-// (32 x warps x 9 floats), s_last_max.
-template <int TW, int TH, int PPT>
-__device__ __forceinline__ void blend_bwd_tile(
-    int tx, int ty, uint2 range, const uint32_t *__restrict__ sorted_vals,
-    const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, uint32_t entry_shift,
-    int W, int H, int tw_log2, int th_log2, float bg0, float bg1, float bg2, int membership,
-    const float *__restrict__ final_T, const uint32_t *__restrict__ n_contrib,
-    const float *__restrict__ dimg, float *__restrict__ part, int32_t *tile_rmax, float4 *sA,
-    float4 *sB, float4 *sC, float4 *sD, float *wpart_raw, uint32_t *s_last_max) {
-    constexpr int NT = 256 / PPT;
-    constexpr int NW = NT / 32;
-    float (*wpart)[NW][9] = reinterpret_cast<float (*)[NW][9]>(wpart_raw);
-    const int lx = threadIdx.x % TW, lyb = PPT * (threadIdx.x / TW);
-    const int px = tx * TW + lx;
+// Reverse compositing of tile (tx, ty) of one image by a CTA of 256 threads, one pixel
+// each (the pixel layout of the forward).  Each pixel starts from its saved final
+// transmittance T and list position `last` and walks the list back to front, undoing
+// one blend per step (T_before = T_after / (1 - alpha), running colour behind).  For
+// every entry the nine partials (du, dv, da, db, dc, dopacity, dr, dg, db) are summed
+// over the warp's pixels with a transposing butterfly (values 0-7 spread over lane
+// groups) plus a plain butterfly for value 8, skipped when no lane of the warp blended
+// the entry, then over the warps in order, and stored at the entry's emit position
+// offsets[r] + entry_shift + (index of the tile in the Gaussian's tile rectangle).
+// *tile_rmax receives the largest rank that may have contributed (-1: none).
+template <int TW, int TH>
+__device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
+                                               const uint32_t *__restrict__ sorted_vals,
+                                               const float4 *__restrict__ ranked,
+                                               const uint32_t *__restrict__ offsets, const TileBwd &o,
+                                               float *__restrict__ part, int32_t *tile_rmax, BwdSmem &sm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float pcx = (float)px + 0.5f;
-    const uint32_t xbit = 1u << lx;
-    const size_t hw = (size_t)W * H;
-
-    BwdPix P[PPT];
-    uint32_t my_last = 0;
-#pragma unroll
-    for (int i = 0; i < PPT; ++i) {
-        const int py = ty * TH + lyb + i;
-        P[i] = {1.f, bg0, bg1, bg2, 0.f, 0.f, 0.f, 0u};
-        if (px < W && py < H) {
-            const size_t p = (size_t)py * W + px;
-            P[i].T = final_T[p];
-            P[i].last = n_contrib[p];
-            P[i].g0 = dimg[p];
-            P[i].g1 = dimg[hw + p];
-            P[i].g2 = dimg[2 * hw + p];
-        }
-        my_last = max(my_last, P[i].last);
+    int lx, ly;
+    pixel_of_thread<TW, TH>((int)threadIdx.x, lx, ly);
+    const int px = tx * TW + lx, py = ty * TH + ly;
+    const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
+    const int membership = o.membership;
+    float T = 1.f, A0 = o.bg0, A1 = o.bg1, A2 = o.bg2, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    uint32_t last = 0u;
+    const uint32_t bit = 1u << lane;
+    if (px < o.W && py < o.H) {
+        const size_t hw = (size_t)o.W * o.H;
+        const size_t p = (size_t)py * o.W + px;
+        T = o.final_T[p];
+        last = o.n_contrib[p];
+        g0 = o.dimg[p];
+        g1 = o.dimg[hw + p];
+        g2 = o.dimg[2 * hw + p];
     }
-
-    if (threadIdx.x == 0) *s_last_max = 0;
+    if (threadIdx.x == 0) sm.last_max = 0u;
     __syncthreads();
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, my_last);
-    if (lane == 0) atomicMax(s_last_max, wmax);
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, last);
+    if (lane == 0) atomicMax(&sm.last_max, wmax);
     __syncthreads();
-    const int n_active = (int)*s_last_max;
-    if (threadIdx.x == 0)
-        *tile_rmax = n_active > 0 ? (int32_t)sorted_vals[range.x + n_active - 1] : -1;
+    const int n_active = (int)sm.last_max;
+    if (threadIdx.x == 0) *tile_rmax = n_active > 0 ? (int32_t)sorted_vals[range.x + n_active - 1] : -1;
 
     for (int hi = n_active; hi > 0; hi -= 256) {
         const int lo = max(hi - 256, 0);
         __syncthreads();
-#pragma unroll
-        for (int h = 0; h < PPT; ++h) {
-            const int slot = (int)threadIdx.x + NT * h;
-            const int k = lo + slot;
+        {
+            const int k = lo + (int)threadIdx.x;
             if (k < hi) {
                 const uint32_t r = sorted_vals[range.x + k];
                 const float4 a = ranked[3 * (size_t)r];
                 const float4 bb = ranked[3 * (size_t)r + 1];
                 const float4 c = ranked[3 * (size_t)r + 2];
+                uint32_t cm, rm;
+                rect_masks<TW, TH>(c, tx, ty, membership, cm, rm);
                 int x0, x1, y0, y1;
                 unpack_rect(c, x0, x1, y0, y1);
-                uint32_t cm = 0xffffffffu, rm = 0xffffffffu;
-                if (membership == GC_MEMBER_PIXEL) {
-                    const int lx0 = max(x0 - tx * TW, 0), lx1 = min(x1 - tx * TW, TW - 1);
-                    const int ly0r = max(y0 - ty * TH, 0), ly1r = min(y1 - ty * TH, TH - 1);
-                    cm = (lx1 >= lx0) ? ((0xffffffffu >> (31 - lx1)) & (0xffffffffu << lx0)) : 0u;
-                    rm = (ly1r >= ly0r) ? ((0xffffffffu >> (31 - ly1r)) & (0xffffffffu << ly0r)) : 0u;
-                }
-                const int tx0 = x0 >> tw_log2, ty0 = y0 >> th_log2, twid = (x1 >> tw_log2) - tx0 + 1;
-                const uint32_t e = offsets[r] + entry_shift + (uint32_t)((ty - ty0) * twid + (tx - tx0));
-                sA[slot] = a;
-                sB[slot] = bb;
-                sC[slot] = make_float4(c.x, __uint_as_float(cm), __uint_as_float(rm), __uint_as_float(e));
-                sD[slot] = make_float4(a.z * kUnscaleDiag, a.w * kUnscaleOff, bb.x * kUnscaleDiag, 0.f);
+                const int tx0 = x0 >> o.tw_log2, ty0 = y0 >> o.th_log2, twid = (x1 >> o.tw_log2) - tx0 + 1;
+                sm.a[threadIdx.x] = a;
+                sm.b[threadIdx.x] = make_float2(bb.x, bb.y);
+                sm.c[threadIdx.x] = make_float4(bb.z, bb.w, c.x, a.z * kUnscaleDiag);
+                sm.d[threadIdx.x] = make_float2(a.w * kUnscaleOff, bb.x * kUnscaleDiag);
+                store_masks<TW>(&sm.m[8 * threadIdx.x], cm, rm);
+                sm.e[threadIdx.x] = offsets[r] + o.entry_shift + (uint32_t)((ty - ty0) * twid + (tx - tx0));
             }
         }
         __syncthreads();
@@ -272,19 +277,41 @@ __device__ __forceinline__ void blend_bwd_tile(
                 float v[9];
 #pragma unroll
                 for (int c = 0; c < 9; ++c) v[c] = 0.f;
-                const float4 c4 = sC[s];
-                const uint32_t rm = __float_as_uint(c4.z) >> lyb;
-                const bool col = (__float_as_uint(c4.y) & xbit) != 0;
-                bool any = false;
-#pragma unroll
-                for (int i = 0; i < PPT; ++i) any = any || (col && (uint32_t)k < P[i].last && ((rm >> i) & 1u));
                 bool contrib = false;
-                if (any) {
-                    const float4 a = sA[s], bb = sB[s], nat = sD[s];
-#pragma unroll
-                    for (int i = 0; i < PPT; ++i)
-                        if (col && (uint32_t)k < P[i].last && ((rm >> i) & 1u))
-                            contrib |= bwd_step(P[i], pcx, (float)(ty * TH + lyb + i) + 0.5f, a, bb, nat, c4.x, v);
+                const uint32_t wm = sm.m[8 * s + warp];
+                if ((wm & bit) != 0u && (uint32_t)k < last) {
+                    const float4 a = sm.a[s];
+                    const float2 bb = sm.b[s];
+                    const float dx = pcx - a.x, dy = pcy - a.y;
+                    const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
+                    if (p2 <= 0.f) {
+                        float G;
+                        const float a0 = blend_raw_alpha(bb.y, p2, G);
+                        const float alpha = fminf(kAlphaMax, a0);
+                        if (alpha >= kAlphaMin) {
+                            contrib = true;
+                            const float4 col = sm.c[s];
+                            T = T / (1.f - alpha);
+                            const float w = alpha * T;
+                            v[6] = w * g0;
+                            v[7] = w * g1;
+                            v[8] = w * g2;
+                            const float dal = T * (g0 * (col.x - A0) + g1 * (col.y - A1) + g2 * (col.z - A2));
+                            A0 = fmaf(alpha, col.x - A0, A0);
+                            A1 = fmaf(alpha, col.y - A1, A1);
+                            A2 = fmaf(alpha, col.z - A2, A2);
+                            if (!(a0 > kAlphaMax)) {
+                                const float2 nd = sm.d[s];
+                                v[5] = G * dal;
+                                const float dp = alpha * dal;  // dL/dpower (natural exponent)
+                                v[0] = (col.w * dx + nd.x * dy) * dp;
+                                v[1] = (nd.x * dx + nd.y * dy) * dp;
+                                v[2] = -0.5f * dx * dx * dp;
+                                v[3] = -dx * dy * dp;
+                                v[4] = -0.5f * dy * dy * dp;
+                            }
+                        }
+                    }
                 }
                 float out0 = 0.f, out8 = 0.f;
                 if (__any_sync(0xffffffffu, contrib)) {
@@ -318,20 +345,19 @@ __device__ __forceinline__ void blend_bwd_tile(
                     out0 = v[0];
                     float x = v[8];
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
                     out8 = x;
                 }
-                if ((lane & 3) == 0) wpart[k - gbot][warp][lane >> 2] = out0;
-                if (lane == 1) wpart[k - gbot][warp][8] = out8;
+                if ((lane & 3) == 0) sm.wpart[k - gbot][warp][lane >> 2] = out0;
+                if (lane == 1) sm.wpart[k - gbot][warp][8] = out8;
             }
             __syncthreads();
-            for (int idx = threadIdx.x; idx < (gtop - gbot) * 9; idx += NT) {
+            for (int idx = threadIdx.x; idx < (gtop - gbot) * 9; idx += 256) {
                 const int q = idx / 9, c = idx - q * 9;
-                float acc = wpart[q][0][c];
+                float acc = sm.wpart[q][0][c];
 #pragma unroll
-                for (int w2 = 1; w2 < NW; ++w2) acc += wpart[q][w2][c];
-                const uint32_t e = __float_as_uint(sC[gbot + q - lo].w);
-                part[(int64_t)e * 9 + c] = acc;
+                for (int w2 = 1; w2 < 8; ++w2) acc += sm.wpart[q][w2][c];
+                part[(int64_t)sm.e[gbot + q - lo] * 9 + c] = acc;
             }
             __syncthreads();
         }
