@@ -29,7 +29,7 @@ namespace {
 
 // One CTA per tile of a single image.
 template <int TW, int TH>
-__global__ void __launch_bounds__(256) k_blend_bwd(
+__global__ void __launch_bounds__(kBwdThreads) k_blend_bwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, int ntx,
     int tw_log2, int th_log2, float bg0, float bg1, float bg2, int membership,
@@ -185,11 +185,11 @@ cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
         rp.tile_h_log2, rp.bg[0], rp.bg[1], rp.bg[2], rp.membership, final_T, n_contrib,      \
         dL_dimg, part, K, tile_rmax
     if (rp.tile_w == 16 && rp.tile_h == 16)
-        k_blend_bwd<16, 16><<<tiles, 256, 0, st>>>(GC_BWD_ARGS);
+        k_blend_bwd<16, 16><<<tiles, kBwdThreads, 0, st>>>(GC_BWD_ARGS);
     else if (rp.tile_w == 8 && rp.tile_h == 32)
-        k_blend_bwd<8, 32><<<tiles, 256, 0, st>>>(GC_BWD_ARGS);
+        k_blend_bwd<8, 32><<<tiles, kBwdThreads, 0, st>>>(GC_BWD_ARGS);
     else if (rp.tile_w == 32 && rp.tile_h == 8)
-        k_blend_bwd<32, 8><<<tiles, 256, 0, st>>>(GC_BWD_ARGS);
+        k_blend_bwd<32, 8><<<tiles, kBwdThreads, 0, st>>>(GC_BWD_ARGS);
     else
         return cudaErrorInvalidValue;
 #undef GC_BWD_ARGS

@@ -42,16 +42,16 @@ struct BatchReq {
 
 namespace {
 
-// Grid of a persistent kernel: every CTA (256 threads) that fits on the device at once,
+// Grid of a persistent kernel: every CTA (of `threads`) that fits on the device at once,
 // queried once per kernel (the device's SM count times resident CTAs per SM).
-template <auto Kernel>
+template <auto Kernel, int threads>
 int64_t persistent_grid() {
     static int64_t cached = 0;
     if (!cached) {
         int per_sm = 0, dev = 0, sms = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Kernel, 256, 0) != cudaSuccess || per_sm < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Kernel, threads, 0) != cudaSuccess || per_sm < 1)
             per_sm = 4;
         cudaGetLastError();
         cached = (int64_t)sms * per_sm;
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(256) k_batch_blend_fwd(const BatchReq *__restr
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(256) k_batch_blend_bwd(const BatchReq *__restrict__ reqs,
+__global__ void __launch_bounds__(kBwdThreads) k_batch_blend_bwd(const BatchReq *__restrict__ reqs,
                                                          const int64_t *__restrict__ tile_base, int n_req,
                                                          int64_t n_tiles, const uint2 *__restrict__ ranges,
                                                          const uint32_t *__restrict__ sorted_vals,
@@ -895,11 +895,11 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
 #define GC_BB_ARGS rq_dev, tb_dev, n_req, tiles, B.ranges.as<uint2>(), sv, B.ranked.as<float4>(), \
                    B.final_T.as<float>(), B.n_contrib.as<uint32_t>(), ctr
         if (o.tile_w == 16)
-            gc::k_batch_blend_fwd<16, 16><<<grid(gc::persistent_grid<gc::k_batch_blend_fwd<16, 16>>()), 256, 0, s>>>(GC_BB_ARGS);
+            gc::k_batch_blend_fwd<16, 16><<<grid(gc::persistent_grid<gc::k_batch_blend_fwd<16, 16>, 256>()), 256, 0, s>>>(GC_BB_ARGS);
         else if (o.tile_w == 8)
-            gc::k_batch_blend_fwd<8, 32><<<grid(gc::persistent_grid<gc::k_batch_blend_fwd<8, 32>>()), 256, 0, s>>>(GC_BB_ARGS);
+            gc::k_batch_blend_fwd<8, 32><<<grid(gc::persistent_grid<gc::k_batch_blend_fwd<8, 32>, 256>()), 256, 0, s>>>(GC_BB_ARGS);
         else
-            gc::k_batch_blend_fwd<32, 8><<<grid(gc::persistent_grid<gc::k_batch_blend_fwd<32, 8>>()), 256, 0, s>>>(GC_BB_ARGS);
+            gc::k_batch_blend_fwd<32, 8><<<grid(gc::persistent_grid<gc::k_batch_blend_fwd<32, 8>, 256>()), 256, 0, s>>>(GC_BB_ARGS);
 #undef GC_BB_ARGS
         gc::note_launches(1);
         GC_CUDA(ctx, cudaGetLastError());
@@ -983,11 +983,11 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
                    B.n_contrib.as<uint32_t>(), B.dimg_dev.as<const float *>(), B.part.as<float>(),              \
                    B.rmax.as<int32_t>(), ctr
         if (B.opt.tile_w == 16)
-            gc::k_batch_blend_bwd<16, 16><<<grid(gc::persistent_grid<gc::k_batch_blend_bwd<16, 16>>()), 256, 0, s>>>(GC_BB_ARGS);
+            gc::k_batch_blend_bwd<16, 16><<<grid(gc::persistent_grid<gc::k_batch_blend_bwd<16, 16>, gc::kBwdThreads>()), gc::kBwdThreads, 0, s>>>(GC_BB_ARGS);
         else if (B.opt.tile_w == 8)
-            gc::k_batch_blend_bwd<8, 32><<<grid(gc::persistent_grid<gc::k_batch_blend_bwd<8, 32>>()), 256, 0, s>>>(GC_BB_ARGS);
+            gc::k_batch_blend_bwd<8, 32><<<grid(gc::persistent_grid<gc::k_batch_blend_bwd<8, 32>, gc::kBwdThreads>()), gc::kBwdThreads, 0, s>>>(GC_BB_ARGS);
         else
-            gc::k_batch_blend_bwd<32, 8><<<grid(gc::persistent_grid<gc::k_batch_blend_bwd<32, 8>>()), 256, 0, s>>>(GC_BB_ARGS);
+            gc::k_batch_blend_bwd<32, 8><<<grid(gc::persistent_grid<gc::k_batch_blend_bwd<32, 8>, gc::kBwdThreads>()), gc::kBwdThreads, 0, s>>>(GC_BB_ARGS);
 #undef GC_BB_ARGS
         gc::note_launches(1);
         GC_CUDA(ctx, cudaGetLastError());

@@ -179,9 +179,14 @@ __device__ __forceinline__ void blend_fwd_tile(int tx, int ty, uint2 range,
     }
 }
 
+// Threads of a reverse-blend CTA: each thread owns two pixels of the tile.
+constexpr int kBwdThreads = 128;
+
 // Shared staging for the reverse blend: a, b as in the forward; c = {r, g, b, a_nat} and
-// d = {b_nat, c_nat} (colour and natural conic, read only for blended pairs); m the warp
-// masks; e the entries' emit positions; wpart the per-warp sums of a group of 32 entries.
+// d = {b_nat, c_nat} (colour and natural conic, read only for blended pairs); m the
+// membership masks (per entry: two words per warp, the upper and lower 8 x 4 halves of
+// its 8 x 8 block); e the entries' emit positions; wpart the per-warp sums of a group of
+// 32 entries.
 struct BwdSmem {
     float4 a[256];
     float2 b[256];
@@ -189,7 +194,7 @@ struct BwdSmem {
     float2 d[256];
     uint32_t m[256 * 8];
     uint32_t e[256];
-    float wpart[32][8][9];
+    float wpart[32][4][9];
     uint32_t last_max;
 };
 
@@ -204,43 +209,89 @@ struct TileBwd {
     uint32_t entry_shift;
 };
 
-// Reverse compositing of tile (tx, ty) of one image by a CTA of 256 threads, one pixel
-// each (the pixel layout of the forward).  Each pixel starts from its saved final
-// transmittance T and list position `last` and walks the list back to front, undoing
-// one blend per step (T_before = T_after / (1 - alpha), running colour behind).  For
-// every entry the nine partials (du, dv, da, db, dc, dopacity, dr, dg, db) are summed
-// over the warp's pixels with a transposing butterfly (values 0-7 spread over lane
-// groups) plus a plain butterfly for value 8, skipped when no lane of the warp blended
-// the entry, then over the warps in order, and stored at the entry's emit position
-// offsets[r] + entry_shift + (index of the tile in the Gaussian's tile rectangle).
-// *tile_rmax receives the largest rank that may have contributed (-1: none).
+// Mask of the 8 x 4 pixel block at tile column c0 and row r0 (bit 8 r + c = pixel
+// (c0 + c, r0 + r)) for an entry covering tile columns cm and rows rm.
+__device__ __forceinline__ uint32_t block_mask(uint32_t cm, uint32_t rm, int c0, int r0) {
+    const uint32_t cb = (cm >> c0) & 0xffu;
+    const uint32_t rb = (rm >> r0) & 0xfu;
+    const uint32_t spread = (rb & 1u) | ((rb & 2u) << 7) | ((rb & 4u) << 14) | ((rb & 8u) << 21);
+    return cb * spread;
+}
+
+// Reverse state of one pixel: transmittance, colour behind, dL/dcolour, list position.
+struct BwdPix {
+    float T, A0, A1, A2, g0, g1, g2;
+    uint32_t last;
+};
+
+// Reverse step of Eq. 2 for one pixel and a blended entry: undoes the blend
+// (T_before = T_after / (1 - alpha), running colour behind) and adds the pixel's nine
+// partials (du, dv, da, db, dc, dopacity, dr, dg, db) to v.
+__device__ __forceinline__ void bwd_blend(BwdPix &P, float dx, float dy, float alpha, float a0, float G,
+                                          const float4 &col, const float2 &nd, float *v) {
+    P.T = P.T / (1.f - alpha);
+    const float w = alpha * P.T;
+    v[6] += w * P.g0;
+    v[7] += w * P.g1;
+    v[8] += w * P.g2;
+    const float dal = P.T * (P.g0 * (col.x - P.A0) + P.g1 * (col.y - P.A1) + P.g2 * (col.z - P.A2));
+    P.A0 = fmaf(alpha, col.x - P.A0, P.A0);
+    P.A1 = fmaf(alpha, col.y - P.A1, P.A1);
+    P.A2 = fmaf(alpha, col.z - P.A2, P.A2);
+    if (!(a0 > kAlphaMax)) {
+        v[5] += G * dal;
+        const float dp = alpha * dal;  // dL/dpower (natural exponent)
+        v[0] += (col.w * dx + nd.x * dy) * dp;
+        v[1] += (nd.x * dx + nd.y * dy) * dp;
+        v[2] += -0.5f * dx * dx * dp;
+        v[3] += -dx * dy * dp;
+        v[4] += -0.5f * dy * dy * dp;
+    }
+}
+
+// Reverse compositing of tile (tx, ty) of one image by a CTA of 128 threads.  Warp w
+// owns an 8 x 8 block of the tile (blocks row-major, TW / 8 per block row); lane l the
+// pixels (l % 8, l / 8) and (l % 8, l / 8 + 4) of its block.  Each pixel starts from its
+// saved final transmittance T and list position `last` and walks the list back to
+// front, undoing one blend per step.  For every entry the nine partials are summed over
+// the thread's two pixels (first, second), over the warp with a transposing butterfly
+// (values 0-7 spread over lane groups) plus a plain butterfly for value 8 - skipped when
+// no pixel of the warp blended the entry - then over the warps in order, and stored at
+// the entry's emit position offsets[r] + entry_shift + (index of the tile in the
+// Gaussian's tile rectangle).  *tile_rmax receives the largest rank that may have
+// contributed (-1: none).
 template <int TW, int TH>
 __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
                                                const uint32_t *__restrict__ sorted_vals,
                                                const float4 *__restrict__ ranked,
                                                const uint32_t *__restrict__ offsets, const TileBwd &o,
                                                float *__restrict__ part, int32_t *tile_rmax, BwdSmem &sm) {
+    static_assert(TW % 8 == 0 && TH % 8 == 0 && TW * TH == 256, "tile must be 256 pixels of 8x8 blocks");
+    constexpr int BX = TW / 8;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int lx, ly;
-    pixel_of_thread<TW, TH>((int)threadIdx.x, lx, ly);
-    const int px = tx * TW + lx, py = ty * TH + ly;
-    const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
+    const int bx = (warp % BX) * 8, by = (warp / BX) * 8;  // block origin in the tile
+    const int px = tx * TW + bx + (lane & 7), py0 = ty * TH + by + (lane >> 3);
+    const float pcx = (float)px + 0.5f;
     const int membership = o.membership;
-    float T = 1.f, A0 = o.bg0, A1 = o.bg1, A2 = o.bg2, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    uint32_t last = 0u;
     const uint32_t bit = 1u << lane;
-    if (px < o.W && py < o.H) {
-        const size_t hw = (size_t)o.W * o.H;
-        const size_t p = (size_t)py * o.W + px;
-        T = o.final_T[p];
-        last = o.n_contrib[p];
-        g0 = o.dimg[p];
-        g1 = o.dimg[hw + p];
-        g2 = o.dimg[2 * hw + p];
+    BwdPix P[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int py = py0 + 4 * i;
+        P[i] = {1.f, o.bg0, o.bg1, o.bg2, 0.f, 0.f, 0.f, 0u};
+        if (px < o.W && py < o.H) {
+            const size_t hw = (size_t)o.W * o.H;
+            const size_t p = (size_t)py * o.W + px;
+            P[i].T = o.final_T[p];
+            P[i].last = o.n_contrib[p];
+            P[i].g0 = o.dimg[p];
+            P[i].g1 = o.dimg[hw + p];
+            P[i].g2 = o.dimg[2 * hw + p];
+        }
     }
     if (threadIdx.x == 0) sm.last_max = 0u;
     __syncthreads();
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, last);
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(P[0].last, P[1].last));
     if (lane == 0) atomicMax(&sm.last_max, wmax);
     __syncthreads();
     const int n_active = (int)sm.last_max;
@@ -249,8 +300,10 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
     for (int hi = n_active; hi > 0; hi -= 256) {
         const int lo = max(hi - 256, 0);
         __syncthreads();
-        {
-            const int k = lo + (int)threadIdx.x;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int slot = (int)threadIdx.x + kBwdThreads * h;
+            const int k = lo + slot;
             if (k < hi) {
                 const uint32_t r = sorted_vals[range.x + k];
                 const float4 a = ranked[3 * (size_t)r];
@@ -261,12 +314,19 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
                 int x0, x1, y0, y1;
                 unpack_rect(c, x0, x1, y0, y1);
                 const int tx0 = x0 >> o.tw_log2, ty0 = y0 >> o.th_log2, twid = (x1 >> o.tw_log2) - tx0 + 1;
-                sm.a[threadIdx.x] = a;
-                sm.b[threadIdx.x] = make_float2(bb.x, bb.y);
-                sm.c[threadIdx.x] = make_float4(bb.z, bb.w, c.x, a.z * kUnscaleDiag);
-                sm.d[threadIdx.x] = make_float2(a.w * kUnscaleOff, bb.x * kUnscaleDiag);
-                store_masks<TW>(&sm.m[8 * threadIdx.x], cm, rm);
-                sm.e[threadIdx.x] = offsets[r] + o.entry_shift + (uint32_t)((ty - ty0) * twid + (tx - tx0));
+                sm.a[slot] = a;
+                sm.b[slot] = make_float2(bb.x, bb.y);
+                sm.c[slot] = make_float4(bb.z, bb.w, c.x, a.z * kUnscaleDiag);
+                sm.d[slot] = make_float2(a.w * kUnscaleOff, bb.x * kUnscaleDiag);
+                uint4 *mo = reinterpret_cast<uint4 *>(&sm.m[8 * slot]);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int w0 = 2 * q, w1 = 2 * q + 1;
+                    const int c0a = (w0 % BX) * 8, r0a = (w0 / BX) * 8, c0b = (w1 % BX) * 8, r0b = (w1 / BX) * 8;
+                    mo[q] = make_uint4(block_mask(cm, rm, c0a, r0a), block_mask(cm, rm, c0a, r0a + 4),
+                                       block_mask(cm, rm, c0b, r0b), block_mask(cm, rm, c0b, r0b + 4));
+                }
+                sm.e[slot] = offsets[r] + o.entry_shift + (uint32_t)((ty - ty0) * twid + (tx - tx0));
             }
         }
         __syncthreads();
@@ -274,43 +334,28 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
             const int gbot = max(gtop - 32, lo);
             for (int k = gtop - 1; k >= gbot; --k) {
                 const int s = k - lo;
+                const uint2 wm = *reinterpret_cast<const uint2 *>(&sm.m[8 * s + 2 * warp]);
+                const bool m0 = (wm.x & bit) != 0u && (uint32_t)k < P[0].last;
+                const bool m1 = (wm.y & bit) != 0u && (uint32_t)k < P[1].last;
                 float v[9];
 #pragma unroll
                 for (int c = 0; c < 9; ++c) v[c] = 0.f;
                 bool contrib = false;
-                const uint32_t wm = sm.m[8 * s + warp];
-                if ((wm & bit) != 0u && (uint32_t)k < last) {
+                if (m0 || m1) {
                     const float4 a = sm.a[s];
                     const float2 bb = sm.b[s];
-                    const float dx = pcx - a.x, dy = pcy - a.y;
-                    const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
-                    if (p2 <= 0.f) {
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        if (!(i == 0 ? m0 : m1)) continue;
+                        const float dx = pcx - a.x, dy = ((float)(py0 + 4 * i) + 0.5f) - a.y;
+                        const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
+                        if (p2 > 0.f) continue;
                         float G;
                         const float a0 = blend_raw_alpha(bb.y, p2, G);
                         const float alpha = fminf(kAlphaMax, a0);
-                        if (alpha >= kAlphaMin) {
-                            contrib = true;
-                            const float4 col = sm.c[s];
-                            T = T / (1.f - alpha);
-                            const float w = alpha * T;
-                            v[6] = w * g0;
-                            v[7] = w * g1;
-                            v[8] = w * g2;
-                            const float dal = T * (g0 * (col.x - A0) + g1 * (col.y - A1) + g2 * (col.z - A2));
-                            A0 = fmaf(alpha, col.x - A0, A0);
-                            A1 = fmaf(alpha, col.y - A1, A1);
-                            A2 = fmaf(alpha, col.z - A2, A2);
-                            if (!(a0 > kAlphaMax)) {
-                                const float2 nd = sm.d[s];
-                                v[5] = G * dal;
-                                const float dp = alpha * dal;  // dL/dpower (natural exponent)
-                                v[0] = (col.w * dx + nd.x * dy) * dp;
-                                v[1] = (nd.x * dx + nd.y * dy) * dp;
-                                v[2] = -0.5f * dx * dx * dp;
-                                v[3] = -dx * dy * dp;
-                                v[4] = -0.5f * dy * dy * dp;
-                            }
-                        }
+                        if (alpha < kAlphaMin) continue;
+                        contrib = true;
+                        bwd_blend(P[i], dx, dy, alpha, a0, G, sm.c[s], sm.d[s], v);
                     }
                 }
                 float out0 = 0.f, out8 = 0.f;
@@ -352,11 +397,9 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
                 if (lane == 1) sm.wpart[k - gbot][warp][8] = out8;
             }
             __syncthreads();
-            for (int idx = threadIdx.x; idx < (gtop - gbot) * 9; idx += 256) {
+            for (int idx = threadIdx.x; idx < (gtop - gbot) * 9; idx += kBwdThreads) {
                 const int q = idx / 9, c = idx - q * 9;
-                float acc = sm.wpart[q][0][c];
-#pragma unroll
-                for (int w2 = 1; w2 < 8; ++w2) acc += sm.wpart[q][w2][c];
+                const float acc = ((sm.wpart[q][0][c] + sm.wpart[q][1][c]) + sm.wpart[q][2][c]) + sm.wpart[q][3][c];
                 part[(int64_t)sm.e[gbot + q - lo] * 9 + c] = acc;
             }
             __syncthreads();
