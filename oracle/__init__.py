@@ -80,7 +80,8 @@ def lib():
             build()
             L = C.CDLL(_LIB)
             P = C.c_void_p
-            L.gco_bin_f32.argtypes = [P] * 5 + [C.c_int64] + [P] * 7
+            L.gco_bin_f32.argtypes = [P] * 5 + [C.c_int64] + [P] * 8
+            L.gco_bin_rows.argtypes = [P, P, C.c_int64] + [P] * 9
             L.gco_render_f64.argtypes = [P] * 5 + [C.c_int64] + [P] * 5 + [C.c_int64] + [P] * 5
             L.gco_render_f64.restype = C.c_int
             L.gco_grad_f64.argtypes = [P] * 5 + [C.c_int64] + [P] * 5 + [P] * 8
@@ -183,7 +184,11 @@ def selection(scene, layer_mask: int) -> np.ndarray:
 
 
 def bin_f32(scene, motion, frame, cam, opts: dict, layer_mask: int = 1) -> dict:
-    """FP32 binning mirror over the selected Gaussians (arrays by selected position)."""
+    """FP32 binning mirror over the selected Gaussians (arrays by selected position).
+
+    ``row_off`` / ``row_a`` / ``row_b``: for visible position j, its tile rows
+    trect[j, 2] .. trect[j, 3] are entries row_off[j] .. row_off[j+1]-1, each the
+    inclusive tile-column interval [a, b] of that row (a > b: empty)."""
     L = lib()
     pk = _Pack()
     sel = np.ascontiguousarray(selection(scene, layer_mask))
@@ -192,11 +197,20 @@ def bin_f32(scene, motion, frame, cam, opts: dict, layer_mask: int = 1) -> dict:
            "visible": np.zeros(n, np.int32), "depth": np.zeros(n, np.float32),
            "rect": np.zeros((n, 4), np.int32), "trect": np.zeros((n, 4), np.int32),
            "radius": np.zeros(n, np.int32), "uv": np.zeros((n, 2), np.float32),
-           "conic": np.zeros((n, 3), np.float32)}
+           "conic": np.zeros((n, 3), np.float32), "tc": np.zeros(n, np.float32)}
     sc, mo, ca, op = _scene(pk, scene), _motion(pk, motion, frame), _camera(cam), _options(opts)
     L.gco_bin_f32(C.byref(sc), C.byref(mo), C.byref(ca), C.byref(op), _ptr(sel), n,
                   _ptr(out["visible"]), _ptr(out["depth"]), _ptr(out["rect"]), _ptr(out["trect"]),
-                  _ptr(out["radius"]), _ptr(out["uv"]), _ptr(out["conic"]))
+                  _ptr(out["radius"]), _ptr(out["uv"]), _ptr(out["conic"]), _ptr(out["tc"]))
+    rows = np.where(out["visible"] != 0, out["trect"][:, 3] - out["trect"][:, 2] + 1, 0).astype(np.int64)
+    row_off = np.zeros(n + 1, np.int64)
+    np.cumsum(rows, out=row_off[1:])
+    out["row_off"] = row_off
+    out["row_a"] = np.ones(int(row_off[-1]), np.int32)
+    out["row_b"] = np.zeros(int(row_off[-1]), np.int32)
+    L.gco_bin_rows(C.byref(ca), C.byref(op), n, _ptr(out["visible"]), _ptr(out["rect"]), _ptr(out["trect"]),
+                   _ptr(out["uv"]), _ptr(out["conic"]), _ptr(out["tc"]), _ptr(row_off), _ptr(out["row_a"]),
+                   _ptr(out["row_b"]))
     return out
 
 
@@ -298,25 +312,27 @@ def grad(scene, motion, frame, cam, opts: dict, dL_dimage, layer_mask: int = 1,
 def tile_lists(bins: dict, cam, tile=(16, 16)) -> dict:
     """Per-tile lists of global Gaussian ids ordered by (depth, index).
 
-    Every visible Gaussian contributes one entry per tile of its tile
-    rectangle.  Returns ``gauss_of_entry`` / ``tile_of_entry`` sorted by
+    Every visible Gaussian contributes one entry per tile of each row interval of
+    its tile rectangle.  Returns ``gauss_of_entry`` / ``tile_of_entry`` sorted by
     (tile, depth, index) with numpy's lexsort, and ``ranges`` (n_tiles, 2).
     """
     tw, th = tile
     ntx = (cam.width + tw - 1) // tw
     nty = (cam.height + th - 1) // th
-    vis = np.nonzero(bins["visible"])[0]
-    tr = bins["trect"][vis].astype(np.int64)
-    wdt = tr[:, 1] - tr[:, 0] + 1
-    cnt = wdt * (tr[:, 3] - tr[:, 2] + 1)
-    owner = np.repeat(np.arange(len(vis)), cnt)
+    off = bins["row_off"]
+    n_rows = int(off[-1])
+    row_owner = np.repeat(np.arange(len(off) - 1), np.diff(off))  # selected position of each row
+    row_ty = bins["trect"][row_owner, 2].astype(np.int64) + (np.arange(n_rows) - off[row_owner])
+    a = bins["row_a"].astype(np.int64)
+    cnt = np.maximum(bins["row_b"].astype(np.int64) - a + 1, 0)
+    owner = np.repeat(row_owner, cnt)
     start = np.concatenate([[0], np.cumsum(cnt)[:-1]]) if len(cnt) else np.zeros(0, np.int64)
     k = np.arange(int(cnt.sum()), dtype=np.int64) - np.repeat(start, cnt)
-    ty = tr[owner, 2] + k // wdt[owner]
-    tx = tr[owner, 0] + k % wdt[owner]
+    tx = np.repeat(a, cnt) + k
+    ty = np.repeat(row_ty, cnt)
     t = ty * ntx + tx
-    g = bins["sel"][vis][owner]
-    d = bins["depth"][vis][owner]
+    g = bins["sel"][owner]
+    d = bins["depth"][owner]
     order = np.lexsort((g, d, t))
     t, g = t[order], g[order]
     n_tiles = ntx * nty
@@ -332,8 +348,10 @@ def tile_list(bins: dict, cam, tile_id: int, tile=(16, 16)) -> np.ndarray:
     ntx = (cam.width + tw - 1) // tw
     tx, ty = tile_id % ntx, tile_id // ntx
     tr = bins["trect"]
-    m = (bins["visible"] == 1) & (tr[:, 0] <= tx) & (tr[:, 1] >= tx) & (tr[:, 2] <= ty) & (tr[:, 3] >= ty)
+    m = (bins["visible"] == 1) & (tr[:, 2] <= ty) & (tr[:, 3] >= ty)
     j = np.nonzero(m)[0]
+    row = bins["row_off"][j] + (ty - tr[j, 2])
+    j = j[(bins["row_a"][row] <= tx) & (bins["row_b"][row] >= tx)]
     order = np.lexsort((bins["sel"][j], bins["depth"][j]))
     return bins["sel"][j][order]
 

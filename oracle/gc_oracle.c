@@ -213,6 +213,7 @@ typedef struct {
     int32_t trect[4];  /* tx0, tx1, ty0, ty1 (inclusive) */
     int32_t radius;
     float u, v, conic[3];
+    float tc;          /* alpha-ellipse level of step 14 (0 without the alpha cull) */
 } gco_bin;
 
 static void bin_one_f32(const gco_scene *sc, const gco_motion *mo, const gco_camera *cam,
@@ -328,6 +329,7 @@ static void bin_one_f32(const gco_scene *sc, const gco_motion *mo, const gco_cam
         float t1 = rf + 1.0f;
         float mt = ((ia + 2.0f * fabsf(ib)) + ic) * (t1 * t1);
         float tc = (tau + 0.02f) + 1e-6f * mt;
+        out->tc = tc;
         float detc = ia * ic - ib * ib;
         if (detc > 0.0f) {
             float xa = sqrtf((tc * ic) / detc), ya = sqrtf((tc * ia) / detc);
@@ -347,11 +349,50 @@ static void bin_one_f32(const gco_scene *sc, const gco_motion *mo, const gco_cam
     out->conic[0] = ia; out->conic[1] = ib; out->conic[2] = ic;
 }
 
+/* 15. row intervals (binning spec, not in the paper).  With the alpha cull, a tile row
+   keeps only the tile columns whose pixel centres can meet the ellipse Q <= tc within
+   the row's band of pixel-centre rows: over dy in [d0, d1] the ellipse spans
+   dx in [(-ib dy - sqrt(ia tc - det dy^2)) / ia, (-ib dy + sqrt(...)) / ia]; its right
+   end is largest at dy = -s and its left end smallest at dy = s, s = ib xa / ic (the
+   extreme points), each clamped into the band.  Without the cull, or for a degenerate
+   conic, a row is the rectangle's [tx0, tx1].  Writes [*a, *b] (*a > *b: empty). */
+static void row_interval_f32(const gco_bin *b, int ty, const gco_options *op, const gco_camera *cam,
+                             int32_t *a, int32_t *bb) {
+    const int TW = op->tile_w, TH = op->tile_h;
+    *a = b->trect[0]; *bb = b->trect[1];
+    if (!op->alpha_cull) return;
+    const float ia = b->conic[0], ib = b->conic[1], ic = b->conic[2], tc = b->tc, u = b->u, v = b->v;
+    const float detc = ia * ic - ib * ib;
+    if (!(detc > 0.0f)) return;
+    const float xa = sqrtf((tc * ic) / detc);
+    const float sy = (ib * xa) / ic;
+    int r0, r1, c0, c1;
+    if (op->membership == 0) {
+        r0 = ty * TH > b->rect[2] ? ty * TH : b->rect[2];
+        r1 = ty * TH + TH - 1 < b->rect[3] ? ty * TH + TH - 1 : b->rect[3];
+        c0 = b->rect[0]; c1 = b->rect[1];
+    } else {
+        r0 = ty * TH;
+        r1 = ty * TH + TH - 1 < cam->height - 1 ? ty * TH + TH - 1 : cam->height - 1;
+        c0 = b->trect[0] * TW;
+        c1 = b->trect[1] * TW + TW - 1 < cam->width - 1 ? b->trect[1] * TW + TW - 1 : cam->width - 1;
+    }
+    const float d0 = ((float)r0 + 0.5f) - v, d1 = ((float)r1 + 0.5f) - v;
+    const float dr = fminf(fmaxf(-sy, d0), d1), dl = fminf(fmaxf(sy, d0), d1);
+    const float qr = ia * tc - (detc * dr) * dr, ql = ia * tc - (detc * dl) * dl;
+    const float xr = (sqrtf(fmaxf(qr, 0.0f)) - ib * dr) / ia;
+    const float xl = (-(ib * dl) - sqrtf(fmaxf(ql, 0.0f))) / ia;
+    float fx0 = ceilf((u + xl) - 0.5f), fx1 = floorf((u + xr) - 0.5f);
+    fx0 = fmaxf(fx0, (float)c0); fx1 = fminf(fx1, (float)c1);
+    if (!(fx0 <= fx1)) { *a = 1; *bb = 0; return; }
+    *a = (int32_t)fx0 / TW; *bb = (int32_t)fx1 / TW;
+}
+
 /* Binning mirror over the selected Gaussians sel[0..n_sel). */
 API void gco_bin_f32(const gco_scene *sc, const gco_motion *mo, const gco_camera *cam,
                      const gco_options *op, const int64_t *sel, int64_t n_sel,
                      int32_t *visible, float *depth, int32_t *rect, int32_t *trect,
-                     int32_t *radius, float *uv, float *conic) {
+                     int32_t *radius, float *uv, float *conic, float *tc) {
 #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n_sel; ++j) {
         gco_bin b;
@@ -362,6 +403,28 @@ API void gco_bin_f32(const gco_scene *sc, const gco_motion *mo, const gco_camera
         radius[j] = b.radius;
         uv[2 * j] = b.u; uv[2 * j + 1] = b.v;
         for (int k = 0; k < 3; ++k) conic[3 * j + k] = b.conic[k];
+        tc[j] = b.tc;
+    }
+}
+
+/* Row intervals of binned Gaussians: for visible j, its tile rows trect[2..3] are
+   entries row_off[j] .. row_off[j+1]-1 of a / b (step 15). */
+API void gco_bin_rows(const gco_camera *cam, const gco_options *op, int64_t n_sel,
+                      const int32_t *visible, const int32_t *rect, const int32_t *trect,
+                      const float *uv, const float *conic, const float *tc, const int64_t *row_off,
+                      int32_t *a, int32_t *b) {
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n_sel; ++j) {
+        if (!visible[j]) continue;
+        gco_bin g;
+        memset(&g, 0, sizeof g);
+        g.visible = 1;
+        for (int k = 0; k < 4; ++k) { g.rect[k] = rect[4 * j + k]; g.trect[k] = trect[4 * j + k]; }
+        g.u = uv[2 * j]; g.v = uv[2 * j + 1];
+        for (int k = 0; k < 3; ++k) g.conic[k] = conic[3 * j + k];
+        g.tc = tc[j];
+        for (int ty = g.trect[2]; ty <= g.trect[3]; ++ty)
+            row_interval_f32(&g, ty, op, cam, &a[row_off[j] + ty - g.trect[2]], &b[row_off[j] + ty - g.trect[2]]);
     }
 }
 

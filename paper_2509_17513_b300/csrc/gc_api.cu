@@ -175,8 +175,8 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
 
     // per-frame buffers sized by the selection and the image
     const int64_t nn = n_sel > 0 ? n_sel : 1;
-    GC_CUDA(ctx, grow(S.rec, (size_t)nn * 48));
-    GC_CUDA(ctx, grow(S.ranked, (size_t)nn * 48));
+    GC_CUDA(ctx, grow(S.rec, (size_t)nn * 16 * gc::kRec));
+    GC_CUDA(ctx, grow(S.ranked, (size_t)nn * 16 * gc::kRec));
     for (int b = 0; b < 2; ++b) {
         GC_CUDA(ctx, grow(S.dkeys[b], (size_t)nn * 4));
         GC_CUDA(ctx, grow(S.dvals[b], (size_t)nn * 4));
@@ -240,7 +240,7 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
         if (K > 0) {
             GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_EMIT));
             GC_CUDA(ctx, gc::launch_emit(S.ranked.as<float4>(), S.offsets.as<uint32_t>(),
-                                         S.touched_r.as<uint32_t>(), n_sel, rp,
+                                         S.touched_r.as<uint32_t>(), n_sel, rp, cam->width, cam->height,
                                          S.tkeys[0].as<uint32_t>(), S.tvals[0].as<uint32_t>(),
                                          (uint32_t)K, s));
             uint32_t *tk[2] = {S.tkeys[0].as<uint32_t>(), S.tkeys[1].as<uint32_t>()};
@@ -450,7 +450,7 @@ extern "C" gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved,
     GC_CUDA(ctx, gc::launch_reduce_entries(ctx->bwd_part.as<float>(), S.offsets.as<uint32_t>(),
                                            S.touched_r.as<uint32_t>(), S.ranked.as<float4>(),
                                            ctx->bwd_rmax.as<int32_t>(), S.dvals[S.depth_buf].as<uint32_t>(),
-                                           S.rp, S.n_sel, ctx->bwd_g2d.as<float>(), s));
+                                           S.rp, S.cam.width, S.cam.height, S.n_sel, ctx->bwd_g2d.as<float>(), s));
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_PREPROCESS_BWD));
     GC_CUDA(ctx, gc::launch_preprocess_bwd(src, S.sel, S.n_sel, S.cam, S.rp, ctx->bwd_g2d.as<float>(),
                                            S.touched.as<uint32_t>(), *out,

@@ -31,14 +31,12 @@ namespace {
 template <int TW, int TH>
 __global__ void __launch_bounds__(kBwdThreads) k_blend_bwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
-    const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, int ntx,
-    int tw_log2, int th_log2, float bg0, float bg1, float bg2, int membership,
+    const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, RenderParams rp,
     const float *__restrict__ final_T, const uint32_t *__restrict__ n_contrib,
-    const float *__restrict__ dimg, float *__restrict__ part, int64_t K,
-    int32_t *__restrict__ tile_rmax) {
+    const float *__restrict__ dimg, float *__restrict__ part, int32_t *__restrict__ tile_rmax) {
     __shared__ __align__(16) BwdSmem sm;
-    const int tile = blockIdx.x;
-    const TileBwd o{final_T, n_contrib, dimg, bg0, bg1, bg2, W, H, membership, tw_log2, th_log2, 0u};
+    const int tile = blockIdx.x, ntx = rp.ntx;
+    const TileBwd o{final_T, n_contrib, dimg, rp, W, H, 0u};
     blend_bwd_tile<TW, TH>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, offsets, o, part,
                            tile_rmax + tile, sm);
 }
@@ -49,40 +47,13 @@ __global__ void __launch_bounds__(kBwdThreads) k_blend_bwd(
 __global__ void __launch_bounds__(256) k_reduce_entries(
     const float *__restrict__ part, const uint32_t *__restrict__ offsets,
     const uint32_t *__restrict__ touched_r, const float4 *__restrict__ ranked,
-    const int32_t *__restrict__ tile_rmax, const uint32_t *__restrict__ perm, int tw_log2,
-    int th_log2, int ntx, int64_t n, float *__restrict__ g2d) {
+    const int32_t *__restrict__ tile_rmax, const uint32_t *__restrict__ perm, RenderParams rp, int W,
+    int H, int64_t n, float *__restrict__ g2d) {
     const int lane = threadIdx.x & 31;
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= n) return;
-    const uint32_t cnt = touched_r[r];
-    float acc[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) acc[c] = 0.f;
-    if (cnt) {
-        const uint32_t off = offsets[r];
-        int x0, x1, y0, y1;
-        unpack_rect(ranked[3 * r + 2], x0, x1, y0, y1);
-        const int tx0 = x0 >> tw_log2, ty0 = y0 >> th_log2, twid = (x1 >> tw_log2) - tx0 + 1;
-        for (uint32_t j = lane; j < cnt; j += 32) {
-            const int t = (ty0 + (int)(j / (uint32_t)twid)) * ntx + tx0 + (int)(j % (uint32_t)twid);
-            if ((int64_t)r <= (int64_t)tile_rmax[t]) {
-                const float *p = part + (int64_t)(off + j) * 9;
-#pragma unroll
-                for (int c = 0; c < 9; ++c) acc[c] += p[c];
-            }
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-        float x = acc[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        acc[c] = x;
-    }
     float mine = 0.f;
-#pragma unroll
-    for (int c = 0; c < 9; ++c)
-        if (lane == c) mine = acc[c];
+    if (touched_r[r]) mine = reduce_entries_warp(part, offsets[r], r, ranked, tile_rmax, rp, W, H);
     if (lane < 9) g2d[9 * (int64_t)perm[r] + lane] = mine;
 }
 
@@ -181,9 +152,8 @@ cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
     const unsigned tiles = (unsigned)(rp.ntx * rp.nty);
     if (tiles == 0) return cudaSuccess;
 #define GC_BWD_ARGS                                                                           \
-    ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp.ntx, rp.tile_w_log2,       \
-        rp.tile_h_log2, rp.bg[0], rp.bg[1], rp.bg[2], rp.membership, final_T, n_contrib,      \
-        dL_dimg, part, K, tile_rmax
+    ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp, final_T, n_contrib, dL_dimg, part, \
+        tile_rmax
     if (rp.tile_w == 16 && rp.tile_h == 16)
         k_blend_bwd<16, 16><<<tiles, kBwdThreads, 0, st>>>(GC_BWD_ARGS);
     else if (rp.tile_w == 8 && rp.tile_h == 32)
@@ -200,11 +170,12 @@ cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
 cudaError_t launch_reduce_entries(const float *part, const uint32_t *offsets,
                                   const uint32_t *touched_r, const float4 *ranked,
                                   const int32_t *tile_rmax, const uint32_t *perm,
-                                  const RenderParams &rp, int64_t n, float *g2d, cudaStream_t st) {
+                                  const RenderParams &rp, int W, int H, int64_t n, float *g2d,
+                                  cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int64_t threads = n * 32;
-    k_reduce_entries<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-        part, offsets, touched_r, ranked, tile_rmax, perm, rp.tile_w_log2, rp.tile_h_log2, rp.ntx, n, g2d);
+    k_reduce_entries<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(part, offsets, touched_r, ranked,
+                                                                         tile_rmax, perm, rp, W, H, n, g2d);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -88,21 +88,15 @@ __global__ void __launch_bounds__(256) k_batch_preprocess(GaussSrc G, const Batc
     } else {
         P.key = kCulledKey;
         P.ntouch = 0;
-        P.r0 = P.r1 = P.r2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        P.r0 = P.r1 = P.r2 = P.r3 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    rec[3 * item] = P.r0;
-    rec[3 * item + 1] = P.r1;
-    rec[3 * item + 2] = P.r2;
+    rec[kRec * item] = P.r0;
+    rec[kRec * item + 1] = P.r1;
+    rec[kRec * item + 2] = P.r2;
+    rec[kRec * item + 3] = P.r3;
+    const uint32_t nt = bin_rows(P, R.rp, R.cam.width, R.cam.height, diff + R.diff_base, R.rp.ntx + 1);
     keys[item] = P.key;
-    touched[item] = P.ntouch;
-    if (P.ntouch) {
-        int32_t *d = diff + R.diff_base;
-        const int gw = R.rp.ntx + 1;
-        atomicAdd(&d[P.ty0 * gw + P.tx0], 1);
-        atomicAdd(&d[P.ty0 * gw + P.tx1 + 1], -1);
-        atomicAdd(&d[(P.ty1 + 1) * gw + P.tx0], -1);
-        atomicAdd(&d[(P.ty1 + 1) * gw + P.tx1 + 1], 1);
-    }
+    touched[item] = nt;
 }
 
 // Per request: entry count K_q, padded entry base, the shift from the unpadded scan
@@ -135,8 +129,8 @@ __global__ void k_batch_entry_bases(const uint32_t *__restrict__ offsets, const 
 }
 
 // One warp emits the entries of 32 consecutive ranks (one request: requests are
-// padded to the radix tile); entry e = offsets[r] + eshift[q] + index of the tile in
-// the Gaussian's tile rectangle; key = the request's local tile id, value = r.
+// padded to the radix tile); entry e = offsets[r] + eshift[q] + index of the tile among
+// the Gaussian's row intervals; key = the request's local tile id, value = r.
 __global__ void __launch_bounds__(256) k_batch_emit(const float4 *__restrict__ ranked,
                                                     const uint32_t *__restrict__ offsets,
                                                     const uint32_t *__restrict__ touched_r,
@@ -151,42 +145,9 @@ __global__ void __launch_bounds__(256) k_batch_emit(const float4 *__restrict__ r
     if (wbase >= n) return;
     if (*padded_total > cap) return;  // overflow: reported by gc_check, nothing emitted
     const int q = find_req(item_base, n_req, wbase);
-    const int ntx = reqs[q].rp.ntx, twl = reqs[q].rp.tile_w_log2, thl = reqs[q].rp.tile_h_log2;
-    const uint32_t shift = eshift[q];
-    const int64_t r = wbase + lane;
-    const bool valid = r < n;
-    const uint32_t cnt = valid ? touched_r[r] : 0u;
-    const uint32_t off = valid ? offsets[r] : 0xffffffffu;
-    int tx0 = 0, ty0 = 0, twid = 1;
-    if (valid && cnt) {
-        int x0, x1, y0, y1;
-        unpack_rect(ranked[3 * r + 2], x0, x1, y0, y1);
-        tx0 = x0 >> twl;
-        ty0 = y0 >> thl;
-        twid = (x1 >> twl) - tx0 + 1;
-    }
-    const uint32_t start = __shfl_sync(0xffffffffu, off, 0);
-    const uint32_t end = __reduce_max_sync(0xffffffffu, valid ? off + cnt : 0u);
-    for (uint32_t e0 = start; e0 < end; e0 += 32) {
-        const uint32_t e = e0 + lane;
-        int owner = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const uint32_t o = __shfl_sync(0xffffffffu, off, owner + step);
-            if (o <= e) owner += step;
-        }
-        const uint32_t oo = __shfl_sync(0xffffffffu, off, owner);
-        const int otw = __shfl_sync(0xffffffffu, twid, owner);
-        const int otx = __shfl_sync(0xffffffffu, tx0, owner);
-        const int oty = __shfl_sync(0xffffffffu, ty0, owner);
-        if (e < end) {
-            const uint32_t k = e - oo;
-            const uint32_t ty = (uint32_t)oty + k / (uint32_t)otw;
-            const uint32_t tx = (uint32_t)otx + k % (uint32_t)otw;
-            keys[e + shift] = ty * (uint32_t)ntx + tx;
-            vals[e + shift] = (uint32_t)(wbase + owner);
-        }
-    }
+    const BatchReq &R = reqs[q];
+    emit_rows_warp(ranked, wbase, n, offsets, touched_r, eshift[q], R.rp, R.cam.width, R.cam.height, cap, keys,
+                   vals);
 }
 
 // Pad keys after every request's entries (they sort to the end of the segment).
@@ -216,17 +177,9 @@ __global__ void __launch_bounds__(1024) k_batch_ranges(const BatchReq *__restric
     const int32_t *src = diff + R.diff_base;
     for (int k = threadIdx.x; k < cells; k += blockDim.x) g[k] = src[k];
     __syncthreads();
-    for (int r = threadIdx.x; r < gh; r += blockDim.x) {
+    for (int r = threadIdx.x; r < gh; r += blockDim.x) {  // row prefix: entries per tile
         int acc = 0;
         for (int c = 0; c < gw; ++c) {
-            acc += g[r * gw + c];
-            g[r * gw + c] = acc;
-        }
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < gw; c += blockDim.x) {
-        int acc = 0;
-        for (int r = 0; r < gh; ++r) {
             acc += g[r * gw + c];
             g[r * gw + c] = acc;
         }
@@ -336,9 +289,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_batch_blend_bwd(const BatchReq 
                 const uint2 rg = ranges[t];
                 s_tile = make_int4(local % R.rp.ntx, local / R.rp.ntx, (int)rg.x, (int)rg.y);
                 s_t = t;
-                s_in = TileBwd{final_T + R.pixel_base, n_contrib + R.pixel_base, dimgs[q], R.rp.bg[0], R.rp.bg[1],
-                               R.rp.bg[2], R.cam.width, R.cam.height, R.rp.membership, R.rp.tile_w_log2,
-                               R.rp.tile_h_log2, eshift[q]};
+                s_in = TileBwd{final_T + R.pixel_base, n_contrib + R.pixel_base, dimgs[q], R.rp, R.cam.width,
+                               R.cam.height, eshift[q]};
             } else {
                 s_tile = make_int4(-1, 0, 0, 0);
             }
@@ -366,39 +318,13 @@ __global__ void __launch_bounds__(256) k_batch_reduce(const float *__restrict__ 
     const int lane = threadIdx.x & 31;
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= n) return;
-    const int q = find_req(item_base, n_req, r);
-    const BatchReq &R = reqs[q];
-    const uint32_t cnt = touched_r[r];
-    float acc[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) acc[c] = 0.f;
-    if (cnt) {
-        const uint32_t off = offsets[r] + eshift[q];
-        int x0, x1, y0, y1;
-        unpack_rect(ranked[3 * r + 2], x0, x1, y0, y1);
-        const int twl = R.rp.tile_w_log2, thl = R.rp.tile_h_log2, ntx = R.rp.ntx;
-        const int tx0 = x0 >> twl, ty0 = y0 >> thl, twid = (x1 >> twl) - tx0 + 1;
-        const int32_t *rm = rmax + R.tile_base;
-        for (uint32_t j = lane; j < cnt; j += 32) {
-            const int t = (ty0 + (int)(j / (uint32_t)twid)) * ntx + tx0 + (int)(j % (uint32_t)twid);
-            if (r <= (int64_t)rm[t]) {
-                const float *p = part + (int64_t)(off + j) * 9;
-#pragma unroll
-                for (int c = 0; c < 9; ++c) acc[c] += p[c];
-            }
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-        float x = acc[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        acc[c] = x;
-    }
     float mine = 0.f;
-#pragma unroll
-    for (int c = 0; c < 9; ++c)
-        if (lane == c) mine = acc[c];
+    if (touched_r[r]) {
+        const int q = find_req(item_base, n_req, r);
+        const BatchReq &R = reqs[q];
+        mine = reduce_entries_warp(part, offsets[r] + eshift[q], r, ranked, rmax + R.tile_base, R.rp, R.cam.width,
+                                   R.cam.height);
+    }
     if (lane < 9) g2d[9 * (int64_t)perm[r] + lane] = mine;
 }
 
@@ -755,8 +681,8 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     need(B.tile_base, 8 * (n_req + 1));
     need(B.seg_items, 4 * (n_req + 1));
     const int64_t ni = items > 0 ? items : 1;
-    need(B.rec, (size_t)ni * 48);
-    need(B.ranked, (size_t)ni * 48);
+    need(B.rec, (size_t)ni * 16 * gc::kRec);
+    need(B.ranked, (size_t)ni * 16 * gc::kRec);
     for (int b = 0; b < 2; ++b) {
         need(B.dkeys[b], (size_t)ni * 4);
         need(B.dvals[b], (size_t)ni * 4);

@@ -1,6 +1,6 @@
 // gc_internal.cuh - device-side types and launchers shared by the kernel files.
 //
-// Layout of the per-Gaussian projected record (three float4, 48 bytes), written
+// Layout of the per-Gaussian projected record (four float4, 64 bytes), written
 // by the preprocess kernel at the Gaussian's compact (selected) position and
 // gathered into depth-rank order before binning:
 //   r0 = { u, v, A, B }                  conic = inverse 2D covariance [[a, b], [b, c]],
@@ -8,6 +8,10 @@
 //                                        C = -c log2e/2 (gc_blend.cuh)
 //   r2 = { blue, depth, rect_x, rect_y } rect_* = pixel footprint, int bits: lo16 = first,
 //                                        hi16 = last (inclusive)
+//   r3 = { a, b, c, tc }                 the conic as computed by the binning spec and the
+//                                        alpha-ellipse level (row intervals, step 15)
+// The blends read r0..r2; binning, emit and the reverse pass recompute a Gaussian's
+// per-row tile intervals from r0, r2, r3.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -18,6 +22,7 @@ namespace gc {
 
 constexpr int kMaxLayers = 32;
 constexpr uint32_t kCulledKey = 0xFFFFFFFFu;
+constexpr int kRec = 4;  // float4s per projected record
 
 // Selected layer ranges: compact index j maps to global index
 // range_begin[k] + (j - range_start[k]) for the range k holding j.
@@ -68,11 +73,12 @@ uint64_t launches_total();
 
 // ---- launchers (host) ----
 
-// Projection of the n_sel selected Gaussians.  Writes rec[3*j..3*j+2], depth
+// Projection of the n_sel selected Gaussians.  Writes rec[4*j..4*j+3], depth
 // keys (kCulledKey when culled), values = j, and tiles touched per Gaussian.  If
 // tile_diff != NULL (a zeroed (nty+1) x (ntx+1) int grid), every visible Gaussian
-// adds its tile rectangle to it as a 2D difference (four integer atomics), so that
-// its 2D prefix sum is the number of list entries of every tile.
+// adds each of its tile-row intervals to it as a row difference (two integer atomics
+// per row), so that the prefix sum along each row is the number of list entries of
+// every tile.
 cudaError_t launch_preprocess(const GaussSrc &g, const Selection &sel, int64_t n_sel,
                               const CamParams &cam, const RenderParams &rp, float4 *rec,
                               uint32_t *depth_keys, uint32_t *depth_vals, uint32_t *touched,
@@ -112,10 +118,11 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
                              cudaStream_t st, uint32_t *err, bool keys_out = true,
                              const uint32_t *seg_block0 = nullptr, int n_seg = 0);
 
-// Emit (tile key, rank) for every tile of every visible Gaussian, in rank order.
-// Entries at positions >= cap are dropped (fixed-capacity mode reports the overflow).
+// Emit (tile key, rank) for every tile of every row interval of every visible Gaussian,
+// in rank order (image W x H).  Entries at positions >= cap are dropped (fixed-capacity
+// mode reports the overflow).
 cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uint32_t *touched_r,
-                        int64_t n, const RenderParams &rp, uint32_t *keys, uint32_t *vals,
+                        int64_t n, const RenderParams &rp, int W, int H, uint32_t *keys, uint32_t *vals,
                         uint32_t cap, cudaStream_t st);
 
 // Tile ranges [start, end) from sorted tile keys; ranges must be zeroed.
@@ -152,7 +159,8 @@ cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
 cudaError_t launch_reduce_entries(const float *part, const uint32_t *offsets,
                                   const uint32_t *touched_r, const float4 *ranked,
                                   const int32_t *tile_rmax, const uint32_t *perm,
-                                  const RenderParams &rp, int64_t n, float *g2d, cudaStream_t st);
+                                  const RenderParams &rp, int W, int H, int64_t n, float *g2d,
+                                  cudaStream_t st);
 
 // Chain rule from the 2D gradients (by compact position) to the attributes (by
 // global index) and to per-Gaussian motion terms (7 floats per compact position:

@@ -41,8 +41,8 @@ constexpr size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Carving of the array (byte offsets).
 constexpr size_t kOffRec = 0;
-constexpr size_t kOffRanked = kOffRec + al(kMaxSelected * 48);
-constexpr size_t kOffDKeys0 = kOffRanked + al(kMaxSelected * 48);
+constexpr size_t kOffRanked = kOffRec + al(kMaxSelected * 16 * gc::kRec);
+constexpr size_t kOffDKeys0 = kOffRanked + al(kMaxSelected * 16 * gc::kRec);
 constexpr size_t kOffDKeys1 = kOffDKeys0 + al(kMaxSelected * 4);
 constexpr size_t kOffDVals0 = kOffDKeys1 + al(kMaxSelected * 4);
 constexpr size_t kOffDVals1 = kOffDVals0 + al(kMaxSelected * 4);
@@ -263,7 +263,7 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
                        "the frame needs %lld (tile, Gaussian) pairs; the no-allocation maximum is %lld",
                        (long long)K, (long long)kMaxKeys);
         if (K > 0) {
-            NA_CUDA(gc::launch_emit(ranked, offsets, touched_r, n_sel, rp, tk[0], tv[0], (uint32_t)K, s));
+            NA_CUDA(gc::launch_emit(ranked, offsets, touched_r, n_sel, rp, cam->width, cam->height, tk[0], tv[0], (uint32_t)K, s));
             NA_CUDA(gc::radix_sort_pairs(tk, tv, K, nullptr, key_bits(n_tiles - 1), sort_scratch,
                                          &tile_buf, s, words + 1));
             NA_CUDA(gc::launch_tile_ranges(tk[tile_buf], nullptr, K, ranges, s));

@@ -20,19 +20,14 @@ __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, i
     const int64_t i = sel_global(sel, j);
     Proj P;
     project_gaussian(G, i, G.group_q, G.group_t, G.n_groups, cam, rp, P);
-    rec[3 * j] = P.r0;
-    rec[3 * j + 1] = P.r1;
-    rec[3 * j + 2] = P.r2;
+    rec[kRec * j] = P.r0;
+    rec[kRec * j + 1] = P.r1;
+    rec[kRec * j + 2] = P.r2;
+    rec[kRec * j + 3] = P.r3;
+    const uint32_t nt = bin_rows(P, rp, cam.width, cam.height, tile_diff, rp.ntx + 1);
     depth_keys[j] = P.key;
     depth_vals[j] = (uint32_t)j;
-    touched[j] = P.ntouch;
-    if (tile_diff && P.ntouch) {
-        const int gw = rp.ntx + 1;
-        atomicAdd(&tile_diff[P.ty0 * gw + P.tx0], 1);
-        atomicAdd(&tile_diff[P.ty0 * gw + P.tx1 + 1], -1);
-        atomicAdd(&tile_diff[(P.ty1 + 1) * gw + P.tx0], -1);
-        atomicAdd(&tile_diff[(P.ty1 + 1) * gw + P.tx1 + 1], 1);
-    }
+    touched[j] = nt;
 }
 
 __global__ void __launch_bounds__(256) k_rank_gather(const uint32_t *__restrict__ perm,
@@ -43,9 +38,8 @@ __global__ void __launch_bounds__(256) k_rank_gather(const uint32_t *__restrict_
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const uint32_t j = perm[r];
-    ranked[3 * r] = rec[3 * (int64_t)j];
-    ranked[3 * r + 1] = rec[3 * (int64_t)j + 1];
-    ranked[3 * r + 2] = rec[3 * (int64_t)j + 2];
+#pragma unroll
+    for (int k = 0; k < kRec; ++k) ranked[kRec * r + k] = rec[kRec * (int64_t)j + k];
     touched_r[r] = touched[j];
 }
 

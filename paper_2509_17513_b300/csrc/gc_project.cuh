@@ -68,7 +68,7 @@ __device__ __forceinline__ float load_sh(const GaussSrc &G, int64_t i, int k, in
 // Result of projecting one Gaussian: the three record float4s, the depth key
 // (kCulledKey when culled), the number of tiles touched and the tile rectangle.
 struct Proj {
-    float4 r0, r1, r2;
+    float4 r0, r1, r2, r3;
     uint32_t key, ntouch;
     int tx0, tx1, ty0, ty1;
 };
@@ -87,6 +87,7 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
     P.r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     P.r1 = P.r0;
     P.r2 = P.r0;
+    P.r3 = P.r0;
     do {
         float gq[4] = {1.f, 0.f, 0.f, 0.f}, gt[3] = {0.f, 0.f, 0.f};
         if (group_q && (A.g < 0 || A.g >= n_groups)) break;  // invalid group id: culled
@@ -201,12 +202,14 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
         // 14. alpha footprint: o exp(-Q/2) >= 1/255 needs Q <= tau = 2 ln(255 o); the
         //     ellipse Q <= tau_c (tau plus a margin that covers the blend's FP32 rounding)
         //     has half-extents sqrt(tau_c ic / det_c), sqrt(tau_c ia / det_c)
+        float tc_out = 0.f;
         if (rp.alpha_cull) {
             const float tau = (float)(2.0 * log(255.0 / (1.0 + exp(-(double)A.logit))));
             if (!(tau > 0.f)) break;  // opacity <= 1/255: never blended
             const float t1 = fadd(rf, 1.f);
             const float mt = fmul(fadd(fadd(ia, fmul(2.f, fabsf(ib))), ic), fmul(t1, t1));
             const float tc = fadd(fadd(tau, 0.02f), fmul(1e-6f, mt));
+            tc_out = tc;
             const float detc = fsub(fmul(ia, ic), fmul(ib, ib));
             if (detc > 0.f) {
                 const float xa = __fsqrt_rn(fdiv(fmul(tc, ic), detc));
@@ -242,7 +245,227 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
         P.r0 = make_float4(u, v, __fmul_rn(ia, -0.5f * kLog2e), __fmul_rn(ib, -kLog2e));
         P.r1 = make_float4(__fmul_rn(ic, -0.5f * kLog2e), op, rgb[0], rgb[1]);
         P.r2 = make_float4(rgb[2], cz, __int_as_float(x0 | (x1 << 16)), __int_as_float(y0 | (y1 << 16)));
+        P.r3 = make_float4(ia, ib, ic, tc_out);
     } while (0);
+}
+
+// Per-Gaussian part of binning step 15: the ellipse Q <= tc (conic a, b, c from r3) and
+// its extreme points.  Without the alpha cull, or for a degenerate conic, rows are the
+// whole rectangle.
+struct RowGeom {
+    float u, v, ia, ib, ic, tc, detc, sy;
+    int x0, x1, y0, y1, tx0, tx1, ty0, ty1;
+    bool cull;
+};
+
+__device__ __forceinline__ void row_geom(const float4 &r0, const float4 &r2, const float4 &r3,
+                                         const RenderParams &rp, RowGeom &g) {
+    const uint32_t rx = __float_as_uint(r2.z), ry = __float_as_uint(r2.w);
+    g.x0 = (int)(rx & 0xffffu);
+    g.x1 = (int)(rx >> 16);
+    g.y0 = (int)(ry & 0xffffu);
+    g.y1 = (int)(ry >> 16);
+    g.tx0 = g.x0 >> rp.tile_w_log2;
+    g.tx1 = g.x1 >> rp.tile_w_log2;
+    g.ty0 = g.y0 >> rp.tile_h_log2;
+    g.ty1 = g.y1 >> rp.tile_h_log2;
+    g.u = r0.x;
+    g.v = r0.y;
+    g.ia = r3.x;
+    g.ib = r3.y;
+    g.ic = r3.z;
+    g.tc = r3.w;
+    g.detc = fsub(fmul(g.ia, g.ic), fmul(g.ib, g.ib));
+    g.cull = rp.alpha_cull && g.detc > 0.f;
+    g.sy = 0.f;
+    if (g.cull) {
+        const float xa = __fsqrt_rn(fdiv(fmul(g.tc, g.ic), g.detc));
+        g.sy = fdiv(fmul(g.ib, xa), g.ic);
+    }
+}
+
+// Binning step 15: tile columns [a, b] (a > b: empty) of tile row ty, i.e. the tiles whose
+// pixel centres in the row's band of pixel-centre rows can meet the ellipse.  Over dy in
+// [d0, d1] the ellipse spans dx in [(-b dy - sqrt(a tc - det dy^2)) / a, (-b dy + sqrt(.)) / a];
+// the right end is largest at dy = -sy, the left end smallest at dy = sy, each clamped into
+// the band.  Every operation is a separately rounded IEEE binary32 operation (the oracle's
+// FP32 mirror evaluates the same sequence).
+__device__ __forceinline__ void row_interval(const RowGeom &g, int ty, const RenderParams &rp, int W, int H,
+                                             int &a, int &b) {
+    a = g.tx0;
+    b = g.tx1;
+    if (!g.cull) return;
+    const int TW = rp.tile_w, TH = rp.tile_h;
+    int r0, r1, c0, c1;
+    if (rp.membership == GC_MEMBER_PIXEL) {
+        r0 = max(ty * TH, g.y0);
+        r1 = min(ty * TH + TH - 1, g.y1);
+        c0 = g.x0;
+        c1 = g.x1;
+    } else {
+        r0 = ty * TH;
+        r1 = min(ty * TH + TH - 1, H - 1);
+        c0 = g.tx0 * TW;
+        c1 = min(g.tx1 * TW + TW - 1, W - 1);
+    }
+    const float d0 = fsub(fadd((float)r0, 0.5f), g.v), d1 = fsub(fadd((float)r1, 0.5f), g.v);
+    const float dr = fminf(fmaxf(-g.sy, d0), d1), dl = fminf(fmaxf(g.sy, d0), d1);
+    const float at = fmul(g.ia, g.tc);
+    const float qr = fsub(at, fmul(fmul(g.detc, dr), dr)), ql = fsub(at, fmul(fmul(g.detc, dl), dl));
+    const float xr = fdiv(fsub(__fsqrt_rn(fmaxf(qr, 0.f)), fmul(g.ib, dr)), g.ia);
+    const float xl = fdiv(fsub(-fmul(g.ib, dl), __fsqrt_rn(fmaxf(ql, 0.f))), g.ia);
+    float fx0 = ceilf(fsub(fadd(g.u, xl), 0.5f)), fx1 = floorf(fsub(fadd(g.u, xr), 0.5f));
+    fx0 = fmaxf(fx0, (float)c0);
+    fx1 = fminf(fx1, (float)c1);
+    if (!(fx0 <= fx1)) {
+        a = 1;
+        b = 0;
+        return;
+    }
+    a = (int)fx0 >> rp.tile_w_log2;
+    b = (int)fx1 >> rp.tile_w_log2;
+}
+
+// Emit of one warp: the 32 consecutive ranks wbase .. wbase + 31 (all of one image) write
+// their (tile key, rank) entries, entry k of rank r at position offsets[r] + shift + k
+// with k running over the Gaussian's tile rows in order and over the columns of each
+// row's interval.  The warp walks the row index j = 0, 1, ... of all its Gaussians
+// together; per step a warp scan of the lanes' interval lengths spreads the step's
+// entries over the lanes (each lane's entries stay contiguous).  Positions >= cap are
+// dropped.
+__device__ __forceinline__ void emit_rows_warp(const float4 *__restrict__ ranked, int64_t wbase, int64_t n,
+                                               const uint32_t *__restrict__ offsets,
+                                               const uint32_t *__restrict__ touched_r, uint32_t shift,
+                                               const RenderParams &rp, int W, int H, uint32_t cap,
+                                               uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = wbase + lane;
+    const bool valid = r < n && touched_r[r] != 0u;
+    RowGeom g;
+    int nrows = 0;
+    uint32_t pos = 0u;
+    if (valid) {
+        row_geom(ranked[kRec * r], ranked[kRec * r + 2], ranked[kRec * r + 3], rp, g);
+        nrows = g.ty1 - g.ty0 + 1;
+        pos = offsets[r] + shift;
+    }
+    const int steps = __reduce_max_sync(0xffffffffu, (uint32_t)nrows);
+    for (int j = 0; j < steps; ++j) {
+        int a = 0, b = -1, ty = 0;
+        if (j < nrows) {
+            ty = g.ty0 + j;
+            row_interval(g, ty, rp, W, H, a, b);
+        }
+        const uint32_t c = b >= a ? (uint32_t)(b - a + 1) : 0u;
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t excl = incl - c;
+        for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+            const uint32_t e = e0 + lane;
+            int owner = 0;  // first lane whose inclusive prefix exceeds e
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t p = __shfl_sync(0xffffffffu, incl, owner + step - 1);
+                if (p <= e) owner += step;
+            }
+            const uint32_t oex = __shfl_sync(0xffffffffu, excl, owner);
+            const uint32_t opos = __shfl_sync(0xffffffffu, pos, owner);
+            const int oa = __shfl_sync(0xffffffffu, a, owner);
+            const int oty = __shfl_sync(0xffffffffu, ty, owner);
+            if (e < total) {
+                const uint32_t k = e - oex;
+                const uint32_t at = opos + k;
+                if (at < cap) {
+                    keys[at] = (uint32_t)oty * (uint32_t)rp.ntx + (uint32_t)(oa + (int)k);
+                    vals[at] = (uint32_t)(wbase + owner);
+                }
+            }
+        }
+        pos += c;
+    }
+}
+
+// Position of tile (tx, ty) among a Gaussian's entries (its rows in order, the columns
+// of each row's interval); the tile must be one of them.
+__device__ __forceinline__ uint32_t entry_index(const RowGeom &g, int tx, int ty, const RenderParams &rp,
+                                                int W, int H) {
+    uint32_t k = 0u;
+    for (int y = g.ty0; y < ty; ++y) {
+        int a, b;
+        row_interval(g, y, rp, W, H, a, b);
+        if (b >= a) k += (uint32_t)(b - a + 1);
+    }
+    int a, b;
+    row_interval(g, ty, rp, W, H, a, b);
+    return k + (uint32_t)(tx - a);
+}
+
+// One warp sums the partials of rank r's entries (positions base + k, nine floats each)
+// over the tiles whose largest contributing rank (rmax, by tile index) is >= r; walks
+// the Gaussian's rows in order, lanes over each row's columns.  Returns the nine sums
+// in lanes 0..8 of `mine`.
+__device__ __forceinline__ float reduce_entries_warp(const float *__restrict__ part, uint32_t base, int64_t r,
+                                                     const float4 *__restrict__ ranked,
+                                                     const int32_t *__restrict__ rmax, const RenderParams &rp,
+                                                     int W, int H) {
+    const int lane = threadIdx.x & 31;
+    float acc[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[c] = 0.f;
+    RowGeom g;
+    row_geom(ranked[kRec * r], ranked[kRec * r + 2], ranked[kRec * r + 3], rp, g);
+    uint32_t k = 0u;
+    for (int ty = g.ty0; ty <= g.ty1; ++ty) {
+        int a, b;
+        row_interval(g, ty, rp, W, H, a, b);
+        if (a > b) continue;
+        for (int col = a + lane; col <= b; col += 32) {
+            if (r <= (int64_t)rmax[ty * rp.ntx + col]) {
+                const float *p = part + (int64_t)(base + k + (uint32_t)(col - a)) * 9;
+#pragma unroll
+                for (int c = 0; c < 9; ++c) acc[c] += p[c];
+            }
+        }
+        k += (uint32_t)(b - a + 1);
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        float x = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        acc[c] = x;
+    }
+    float mine = 0.f;
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+        if (lane == c) mine = acc[c];
+    return mine;
+}
+
+// Tiles touched by a projected Gaussian (sum of its row intervals); if diff != NULL also
+// adds each row interval to the row-difference grid (row pitch gw).
+__device__ __forceinline__ uint32_t bin_rows(const Proj &P, const RenderParams &rp, int W, int H,
+                                             int32_t *diff, int gw) {
+    if (!P.ntouch) return 0u;
+    RowGeom g;
+    row_geom(P.r0, P.r2, P.r3, rp, g);
+    uint32_t total = 0u;
+    for (int ty = g.ty0; ty <= g.ty1; ++ty) {
+        int a, b;
+        row_interval(g, ty, rp, W, H, a, b);
+        if (a > b) continue;
+        total += (uint32_t)(b - a + 1);
+        if (diff) {
+            atomicAdd(&diff[ty * gw + a], 1);
+            atomicAdd(&diff[ty * gw + b + 1], -1);
+        }
+    }
+    return total;
 }
 
 }  // namespace gc

@@ -5,9 +5,9 @@
 // and a stable sort on the tile id alone (log2(tiles) bits, two 8-bit digits at
 // 1080p and 4K) yields per-tile lists that are already front to back, with
 // ties broken by the global index (the depth sort is stable over index order).
-// An entry's position in emit order is offsets[r] + (its tile's index in the
-// Gaussian's tile rectangle); the backward pass writes its partial gradients
-// there, so each Gaussian's partials are contiguous.
+// An entry's position in emit order is offsets[r] + (its tile's index among the
+// Gaussian's row intervals, binning step 15); the backward pass writes its partial
+// gradients there, so each Gaussian's partials are contiguous.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,51 +19,17 @@ namespace gc {
 namespace {
 
 
-// One warp emits the entries of 32 consecutive ranks, lanes striding over the
-// warp's contiguous output range (coalesced writes, balanced across lanes).
+// One warp emits the entries of 32 consecutive ranks (row by row, see emit_rows_warp).
 __global__ void __launch_bounds__(256) k_emit(const float4 *__restrict__ ranked,
                                               const uint32_t *__restrict__ offsets,
                                               const uint32_t *__restrict__ touched_r, int64_t n,
-                                              int tw_log2, int th_log2, int ntx, uint32_t cap,
+                                              RenderParams rp, int W, int H, uint32_t cap,
                                               uint32_t *__restrict__ keys,
                                               uint32_t *__restrict__ vals) {
     const int lane = threadIdx.x & 31;
     const int64_t wbase = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - lane;
     if (wbase >= n) return;
-    const int64_t r = wbase + lane;
-    const bool valid = r < n;
-    uint32_t cnt = valid ? touched_r[r] : 0u;
-    uint32_t off = valid ? offsets[r] : 0xffffffffu;
-    int tx0 = 0, ty0 = 0, twid = 1;
-    if (valid && cnt) {
-        int x0, x1, y0, y1;
-        unpack_rect(ranked[3 * r + 2], x0, x1, y0, y1);
-        tx0 = x0 >> tw_log2;
-        ty0 = y0 >> th_log2;
-        twid = (x1 >> tw_log2) - tx0 + 1;
-    }
-    const uint32_t start = __shfl_sync(0xffffffffu, off, 0);
-    const uint32_t end = __reduce_max_sync(0xffffffffu, valid ? off + cnt : 0u);
-    for (uint32_t e0 = start; e0 < end; e0 += 32) {
-        const uint32_t e = e0 + lane;
-        int owner = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            uint32_t o = __shfl_sync(0xffffffffu, off, owner + step);
-            if (o <= e) owner += step;
-        }
-        const uint32_t oo = __shfl_sync(0xffffffffu, off, owner);
-        const int otw = __shfl_sync(0xffffffffu, twid, owner);
-        const int otx = __shfl_sync(0xffffffffu, tx0, owner);
-        const int oty = __shfl_sync(0xffffffffu, ty0, owner);
-        if (e < end && e < cap) {
-            const uint32_t k = e - oo;
-            const uint32_t ty = (uint32_t)oty + k / (uint32_t)otw;
-            const uint32_t tx = (uint32_t)otx + k % (uint32_t)otw;
-            keys[e] = ty * (uint32_t)ntx + tx;
-            vals[e] = (uint32_t)(wbase + owner);
-        }
-    }
+    emit_rows_warp(ranked, wbase, n, offsets, touched_r, 0u, rp, W, H, cap, keys, vals);
 }
 
 __global__ void k_tile_ranges(const uint32_t *__restrict__ keys, const uint32_t *n_dev,
@@ -95,8 +61,8 @@ __global__ void __launch_bounds__(256) k_blend_fwd(
     blend_fwd_tile<TW, TH, true>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, o, sm);
 }
 
-// Single CTA: 2D inclusive prefix of the tile difference grid (rows, then columns)
-// gives the entry count of every tile; an exclusive scan in tile order gives the
+// Single CTA: the inclusive prefix of every row of the tile difference grid gives the
+// entry count of every tile; an exclusive scan in tile order gives the
 // ranges of the tile-sorted list.
 __global__ void __launch_bounds__(1024) k_tile_ranges_from_diff(const int32_t *__restrict__ diff,
                                                                 int ntx, int nty,
@@ -112,14 +78,6 @@ __global__ void __launch_bounds__(1024) k_tile_ranges_from_diff(const int32_t *_
     for (int r = threadIdx.x; r < gh; r += blockDim.x) {
         int acc = 0;
         for (int c = 0; c < gw; ++c) {
-            acc += g[r * gw + c];
-            g[r * gw + c] = acc;
-        }
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < gw; c += blockDim.x) {
-        int acc = 0;
-        for (int r = 0; r < gh; ++r) {
             acc += g[r * gw + c];
             g[r * gw + c] = acc;
         }
@@ -185,12 +143,12 @@ cudaError_t launch_entries_to_global(const uint32_t *sorted_vals, const uint32_t
 }
 
 cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uint32_t *touched_r,
-                        int64_t n, const RenderParams &rp, uint32_t *keys, uint32_t *vals,
+                        int64_t n, const RenderParams &rp, int W, int H, uint32_t *keys, uint32_t *vals,
                         uint32_t cap, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int64_t threads = ((n + 31) / 32) * 32;
-    k_emit<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-        ranked, offsets, touched_r, n, rp.tile_w_log2, rp.tile_h_log2, rp.ntx, cap, keys, vals);
+    k_emit<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(ranked, offsets, touched_r, n, rp, W, H, cap,
+                                                                keys, vals);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -6,6 +6,7 @@
 
 #include "gc_blend.cuh"
 #include "gc_internal.cuh"
+#include "gc_project.cuh"
 
 namespace gc {
 
@@ -118,9 +119,9 @@ __device__ __forceinline__ void blend_fwd_tile(int tx, int ty, uint2 range,
             const int idx = b + (int)threadIdx.x;
             if (idx < n) {
                 const uint32_t r = sorted_vals[range.x + idx];
-                const float4 a = ranked[3 * (size_t)r];
-                const float4 bb = ranked[3 * (size_t)r + 1];
-                const float4 c = ranked[3 * (size_t)r + 2];
+                const float4 a = ranked[kRec * (size_t)r];
+                const float4 bb = ranked[kRec * (size_t)r + 1];
+                const float4 c = ranked[kRec * (size_t)r + 2];
                 uint32_t cm, rm;
                 rect_masks<TW, TH>(c, tx, ty, membership, cm, rm);
                 sm.a[threadIdx.x] = a;
@@ -204,8 +205,8 @@ struct TileBwd {
     const float *final_T;
     const uint32_t *n_contrib;
     const float *dimg;
-    float bg0, bg1, bg2;
-    int W, H, membership, tw_log2, th_log2;
+    RenderParams rp;  // background, tile shape, membership, alpha cull
+    int W, H;
     uint32_t entry_shift;
 };
 
@@ -272,13 +273,13 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
     const int bx = (warp % BX) * 8, by = (warp / BX) * 8;  // block origin in the tile
     const int px = tx * TW + bx + (lane & 7), py0 = ty * TH + by + (lane >> 3);
     const float pcx = (float)px + 0.5f;
-    const int membership = o.membership;
+    const int membership = o.rp.membership;
     const uint32_t bit = 1u << lane;
     BwdPix P[2];
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const int py = py0 + 4 * i;
-        P[i] = {1.f, o.bg0, o.bg1, o.bg2, 0.f, 0.f, 0.f, 0u};
+        P[i] = {1.f, o.rp.bg[0], o.rp.bg[1], o.rp.bg[2], 0.f, 0.f, 0.f, 0u};
         if (px < o.W && py < o.H) {
             const size_t hw = (size_t)o.W * o.H;
             const size_t p = (size_t)py * o.W + px;
@@ -306,14 +307,13 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
             const int k = lo + slot;
             if (k < hi) {
                 const uint32_t r = sorted_vals[range.x + k];
-                const float4 a = ranked[3 * (size_t)r];
-                const float4 bb = ranked[3 * (size_t)r + 1];
-                const float4 c = ranked[3 * (size_t)r + 2];
+                const float4 a = ranked[kRec * (size_t)r];
+                const float4 bb = ranked[kRec * (size_t)r + 1];
+                const float4 c = ranked[kRec * (size_t)r + 2];
                 uint32_t cm, rm;
                 rect_masks<TW, TH>(c, tx, ty, membership, cm, rm);
-                int x0, x1, y0, y1;
-                unpack_rect(c, x0, x1, y0, y1);
-                const int tx0 = x0 >> o.tw_log2, ty0 = y0 >> o.th_log2, twid = (x1 >> o.tw_log2) - tx0 + 1;
+                RowGeom g;
+                row_geom(a, c, ranked[kRec * (size_t)r + 3], o.rp, g);
                 sm.a[slot] = a;
                 sm.b[slot] = make_float2(bb.x, bb.y);
                 sm.c[slot] = make_float4(bb.z, bb.w, c.x, a.z * kUnscaleDiag);
@@ -326,7 +326,7 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
                     mo[q] = make_uint4(block_mask(cm, rm, c0a, r0a), block_mask(cm, rm, c0a, r0a + 4),
                                        block_mask(cm, rm, c0b, r0b), block_mask(cm, rm, c0b, r0b + 4));
                 }
-                sm.e[slot] = offsets[r] + o.entry_shift + (uint32_t)((ty - ty0) * twid + (tx - tx0));
+                sm.e[slot] = offsets[r] + o.entry_shift + entry_index(g, tx, ty, o.rp, o.W, o.H);
             }
         }
         __syncthreads();

@@ -1,12 +1,14 @@
-"""The alpha footprint of the binning specification (step 14, not in the paper).
+"""The alpha footprint of the binning specification (steps 14-15, not in the paper).
 
 A Gaussian's value can reach the 1/255 skip threshold of the compositing rule
 (Sec. 3.1, Eq. 2) only where o exp(-Q/2) >= 1/255.  The mirror clips the 3-sigma
-pixel square to the bounding box of that region plus a margin.  The pins:
+pixel square to the bounding box of that region plus a margin (step 14) and keeps, per
+tile row, only the tile columns whose pixel centres can meet it (step 15).  The pins:
 
-* the clipped rectangle lies inside the 3-sigma square;
-* every pixel removed by the clip has alpha < (1/255) exp(-0.005) in FP64, checked by
-  brute force over the removed pixels;
+* the clipped rectangle lies inside the 3-sigma square, every row interval inside the
+  rectangle's tile columns;
+* every pixel removed by the clip or by the row intervals has alpha < (1/255)
+  exp(-0.005) in FP64, checked by brute force over the removed pixels;
 * Gaussians with opacity <= 1/255 are not binned;
 * the FP64 render and its pixel flags do not change at all (bit for bit), and the FP64
   gradients agree to the oracle's own run-to-run summation noise (1e-12 relative):
@@ -18,9 +20,10 @@ import pytest
 from synth import scenes
 
 
-def _removed_alpha_max(oracle_lib, scene, motion, frame, cam, mask, step=1):
-    on = oracle_lib.bin_f32(scene, motion, frame, cam, oracle_lib.default_options(), mask)
-    off = oracle_lib.bin_f32(scene, motion, frame, cam, oracle_lib.default_options(alpha_cull=0), mask)
+def _removed_alpha_max(oracle_lib, scene, motion, frame, cam, mask, step=1, tile=(16, 16)):
+    tw, th = tile
+    on = oracle_lib.bin_f32(scene, motion, frame, cam, oracle_lib.default_options(tile=tile), mask)
+    off = oracle_lib.bin_f32(scene, motion, frame, cam, oracle_lib.default_options(tile=tile, alpha_cull=0), mask)
     logit = scene.opacity_logits[on["sel"]].astype(np.float64)
     o = 1.0 / (1.0 + np.exp(-logit))
     worst = 0.0
@@ -38,6 +41,17 @@ def _removed_alpha_max(oracle_lib, scene, motion, frame, cam, mask, step=1):
             a0, a1, b0, b1 = on["rect"][j]
             assert x0 <= a0 <= a1 <= x1 and y0 <= b0 <= b1 <= y1, j
             keep[b0 - y0:b1 - y0 + 1, a0 - x0:a1 - x0 + 1] = True
+            t0, t1, s0, s1 = on["trect"][j]
+            ra = on["row_a"][on["row_off"][j]:on["row_off"][j + 1]]
+            rb = on["row_b"][on["row_off"][j]:on["row_off"][j + 1]]
+            assert len(ra) == s1 - s0 + 1
+            for i in range(len(ra)):
+                assert ra[i] > rb[i] or t0 <= ra[i] <= rb[i] <= t1, (j, i)
+            tile_x = (X.astype(np.int64) // tw)
+            tile_y = (Y.astype(np.int64) // th)
+            ri = np.clip(tile_y - s0, 0, len(ra) - 1)
+            in_row = (tile_x >= ra[ri]) & (tile_x <= rb[ri]) & (tile_y >= s0) & (tile_y <= s1)
+            keep &= in_row
         else:
             assert o[j] <= 1.0 / 255.0 or True  # dropped: every pixel is checked below
         if keep.all():
@@ -58,12 +72,13 @@ def test_alpha_cull_removes_only_pixels_below_threshold_tiny(oracle_lib):
     assert worst < (1.0 / 255.0) * np.exp(-0.005), worst
 
 
-def test_alpha_cull_removes_only_pixels_below_threshold_hier(oracle_lib):
+@pytest.mark.parametrize("tile", [(16, 16), (8, 32), (32, 8)])
+def test_alpha_cull_removes_only_pixels_below_threshold_hier(oracle_lib, tile):
     rng = np.random.default_rng(81)
     scene = scenes.make_hier_scene(rng, 6000, 6, 3, 16)
     motion = scenes.random_motion(rng, 16, 3)
     cam = scenes.orbit_camera(0.7, 4.0, 320, 240)
-    worst, n = _removed_alpha_max(oracle_lib, scene, motion, 2, cam, 63, step=3)
+    worst, n = _removed_alpha_max(oracle_lib, scene, motion, 2, cam, 63, step=3, tile=tile)
     assert n > 10000
     assert worst < (1.0 / 255.0) * np.exp(-0.005), worst
 

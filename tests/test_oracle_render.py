@@ -250,10 +250,21 @@ def test_pixel_square_is_tile_shape_invariant(oracle_lib):
 
 
 def test_tile_lists_cover_rectangles(oracle_lib):
+    """Without the alpha cull every tile of every rectangle is listed; with it, the lists
+    are a subset; lists are depth-ordered either way, and one tile's list equals its
+    slice of the full lists."""
     w = scenes.tiny(n=300, size=64)
     cam = w.cameras[0]
-    b = oracle_lib.bin_f32(w.scene, None, 0, cam, oracle_lib.default_options(), 1)
+    bc = oracle_lib.bin_f32(w.scene, None, 0, cam, oracle_lib.default_options(), 1)
+    tlc = oracle_lib.tile_lists(bc, cam)
+    b = oracle_lib.bin_f32(w.scene, None, 0, cam, oracle_lib.default_options(alpha_cull=0), 1)
     tl = oracle_lib.tile_lists(b, cam)
+    full = set(zip(tl["tile_of_entry"].tolist(), tl["gauss_of_entry"].tolist()))
+    culled = set(zip(tlc["tile_of_entry"].tolist(), tlc["gauss_of_entry"].tolist()))
+    assert culled < full
+    for t in range(tlc["n_tiles"]):
+        s, e = tlc["ranges"][t]
+        assert np.array_equal(tlc["gauss_of_entry"][s:e], oracle_lib.tile_list(bc, cam, t))
     tr = b["trect"][b["visible"] == 1]
     assert len(tl["gauss_of_entry"]) == int(((tr[:, 1] - tr[:, 0] + 1) * (tr[:, 3] - tr[:, 2] + 1)).sum())
     for t in range(tl["n_tiles"]):
