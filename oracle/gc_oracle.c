@@ -352,9 +352,9 @@ static void bin_one_f32(const gco_scene *sc, const gco_motion *mo, const gco_cam
 /* 15. row intervals (binning spec, not in the paper).  With the alpha cull, a tile row
    keeps only the tile columns whose pixel centres can meet the ellipse Q <= tc within
    the row's band of pixel-centre rows: over dy in [d0, d1] the ellipse spans
-   dx in [(-ib dy - sqrt(ia tc - det dy^2)) / ia, (-ib dy + sqrt(...)) / ia]; its right
-   end is largest at dy = -s and its left end smallest at dy = s, s = ib xa / ic (the
-   extreme points), each clamped into the band.  Without the cull, or for a degenerate
+   dx in [(-ib dy - sqrt(ia tc - det dy^2)) / ia, (-ib dy + sqrt(...)) / ia] (evaluated as
+   a product with ria = 1 / ia); its right end is largest at dy = -s and its left end
+   smallest at dy = s, s = ib xa / ic (the extreme points), each clamped into the band.  Without the cull, or for a degenerate
    conic, a row is the rectangle's [tx0, tx1].  Writes [*a, *b] (*a > *b: empty). */
 static void row_interval_f32(const gco_bin *b, int ty, const gco_options *op, const gco_camera *cam,
                              int32_t *a, int32_t *bb) {
@@ -366,6 +366,7 @@ static void row_interval_f32(const gco_bin *b, int ty, const gco_options *op, co
     if (!(detc > 0.0f)) return;
     const float xa = sqrtf((tc * ic) / detc);
     const float sy = (ib * xa) / ic;
+    const float ria = 1.0f / ia;
     int r0, r1, c0, c1;
     if (op->membership == 0) {
         r0 = ty * TH > b->rect[2] ? ty * TH : b->rect[2];
@@ -380,8 +381,8 @@ static void row_interval_f32(const gco_bin *b, int ty, const gco_options *op, co
     const float d0 = ((float)r0 + 0.5f) - v, d1 = ((float)r1 + 0.5f) - v;
     const float dr = fminf(fmaxf(-sy, d0), d1), dl = fminf(fmaxf(sy, d0), d1);
     const float qr = ia * tc - (detc * dr) * dr, ql = ia * tc - (detc * dl) * dl;
-    const float xr = (sqrtf(fmaxf(qr, 0.0f)) - ib * dr) / ia;
-    const float xl = (-(ib * dl) - sqrtf(fmaxf(ql, 0.0f))) / ia;
+    const float xr = (sqrtf(fmaxf(qr, 0.0f)) - ib * dr) * ria;
+    const float xl = (-(ib * dl) - sqrtf(fmaxf(ql, 0.0f))) * ria;
     float fx0 = ceilf((u + xl) - 0.5f), fx1 = floorf((u + xr) - 0.5f);
     fx0 = fmaxf(fx0, (float)c0); fx1 = fminf(fx1, (float)c1);
     if (!(fx0 <= fx1)) { *a = 1; *bb = 0; return; }

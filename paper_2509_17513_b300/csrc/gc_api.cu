@@ -94,7 +94,7 @@ gc_status gc_destroy(gc_context *ctx) {
         saved_release(ctx, &ctx->internal);
         ctx->internal.batch.reset();
         DevBuf *bufs[] = {&ctx->scratch, &ctx->bwd_part, &ctx->bwd_g2d, &ctx->bwd_motion,
-                          &ctx->bwd_rmax, &ctx->bwd_group};
+                          &ctx->bwd_group};
         for (DevBuf *b : bufs) release(*b);
         if (ctx->host_word) cudaFreeHost(ctx->host_word);
         for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
@@ -433,24 +433,28 @@ extern "C" gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved,
         return GC_OK;
     }
     const int64_t K = S.K > 0 ? S.K : 1;
-    const int64_t n_tiles = (int64_t)S.rp.ntx * S.rp.nty;
-    GC_CUDA(ctx, grow(ctx->bwd_part, (size_t)K * 9 * 4));
+    {
+        void *before = ctx->bwd_part.p;
+        GC_CUDA(ctx, grow(ctx->bwd_part, (size_t)K * 9 * 4));
+        if (ctx->bwd_part.p != before) ctx->bwd_part_clean = false;
+    }
+    if (!ctx->bwd_part_clean) GC_CUDA(ctx, cudaMemsetAsync(ctx->bwd_part.p, 0, ctx->bwd_part.cap, s));
     GC_CUDA(ctx, grow(ctx->bwd_g2d, (size_t)S.n_sel * 9 * 4));
     GC_CUDA(ctx, grow(ctx->bwd_motion, (size_t)S.n_sel * 7 * 4));
-    GC_CUDA(ctx, grow(ctx->bwd_rmax, (size_t)n_tiles * 4));
     if (G) GC_CUDA(ctx, grow(ctx->bwd_group, gc::group_partial_floats(S.n_sel, G) * 4));
     const uint32_t *sorted_vals = S.K > 0 ? S.tvals[S.tile_buf].as<uint32_t>() : nullptr;
 
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_BLEND_BWD));
+    ctx->bwd_part_clean = false;
     GC_CUDA(ctx, gc::launch_blend_bwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(),
                                       S.offsets.as<uint32_t>(), S.cam, S.rp, S.final_T.as<float>(),
-                                      S.n_contrib.as<uint32_t>(), dL_dimage, ctx->bwd_part.as<float>(),
-                                      K, ctx->bwd_rmax.as<int32_t>(), s));
+                                      S.n_contrib.as<uint32_t>(), dL_dimage, ctx->bwd_part.as<float>(), s));
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_REDUCE));
     GC_CUDA(ctx, gc::launch_reduce_entries(ctx->bwd_part.as<float>(), S.offsets.as<uint32_t>(),
-                                           S.touched_r.as<uint32_t>(), S.ranked.as<float4>(),
-                                           ctx->bwd_rmax.as<int32_t>(), S.dvals[S.depth_buf].as<uint32_t>(),
-                                           S.rp, S.cam.width, S.cam.height, S.n_sel, ctx->bwd_g2d.as<float>(), s));
+                                           S.touched_r.as<uint32_t>(), S.dvals[S.depth_buf].as<uint32_t>(),
+                                           S.n_sel, (uint32_t)std::min<int64_t>(K, 0xFFFFFFFFll),
+                                           ctx->bwd_g2d.as<float>(), s));
+    ctx->bwd_part_clean = true;
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_PREPROCESS_BWD));
     GC_CUDA(ctx, gc::launch_preprocess_bwd(src, S.sel, S.n_sel, S.cam, S.rp, ctx->bwd_g2d.as<float>(),
                                            S.touched.as<uint32_t>(), *out,

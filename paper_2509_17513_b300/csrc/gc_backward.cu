@@ -33,28 +33,26 @@ __global__ void __launch_bounds__(kBwdThreads) k_blend_bwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, RenderParams rp,
     const float *__restrict__ final_T, const uint32_t *__restrict__ n_contrib,
-    const float *__restrict__ dimg, float *__restrict__ part, int32_t *__restrict__ tile_rmax) {
+    const float *__restrict__ dimg, float *__restrict__ part) {
     __shared__ __align__(16) BwdSmem sm;
     const int tile = blockIdx.x, ntx = rp.ntx;
     const TileBwd o{final_T, n_contrib, dimg, rp, W, H, 0u};
-    blend_bwd_tile<TW, TH>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, offsets, o, part,
-                           tile_rmax + tile, sm);
+    blend_bwd_tile<TW, TH>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, offsets, o, part, sm);
 }
 
 // One warp per rank: sum of the Gaussian's partials over its tiles (entry-major
 // partials, nine floats per entry); the result goes to the Gaussian's compact
 // position j = perm[r].
-__global__ void __launch_bounds__(256) k_reduce_entries(
-    const float *__restrict__ part, const uint32_t *__restrict__ offsets,
-    const uint32_t *__restrict__ touched_r, const float4 *__restrict__ ranked,
-    const int32_t *__restrict__ tile_rmax, const uint32_t *__restrict__ perm, RenderParams rp, int W,
-    int H, int64_t n, float *__restrict__ g2d) {
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256) k_reduce_entries(float *__restrict__ part,
+                                                        const uint32_t *__restrict__ offsets,
+                                                        const uint32_t *__restrict__ touched_r,
+                                                        const uint32_t *__restrict__ perm, int64_t n,
+                                                        uint32_t cap, float *__restrict__ g2d) {
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= n) return;
-    float mine = 0.f;
-    if (touched_r[r]) mine = reduce_entries_warp(part, offsets[r], r, ranked, tile_rmax, rp, W, H);
-    if (lane < 9) g2d[9 * (int64_t)perm[r] + lane] = mine;
+    float out0, out8;
+    reduce_entries_warp(part, offsets[r], touched_r[r], cap, out0, out8);
+    store_reduced(g2d + 9 * (int64_t)perm[r], out0, out8);
 }
 
 // Thread per selected Gaussian in index order (coalesced attribute reads and
@@ -148,12 +146,11 @@ cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
                              const float4 *ranked, const uint32_t *offsets, const CamParams &cam,
                              const RenderParams &rp, const float *final_T,
                              const uint32_t *n_contrib, const float *dL_dimg, float *part,
-                             int64_t K, int32_t *tile_rmax, cudaStream_t st) {
+                             cudaStream_t st) {
     const unsigned tiles = (unsigned)(rp.ntx * rp.nty);
     if (tiles == 0) return cudaSuccess;
 #define GC_BWD_ARGS                                                                           \
-    ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp, final_T, n_contrib, dL_dimg, part, \
-        tile_rmax
+    ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp, final_T, n_contrib, dL_dimg, part
     if (rp.tile_w == 16 && rp.tile_h == 16)
         k_blend_bwd<16, 16><<<tiles, kBwdThreads, 0, st>>>(GC_BWD_ARGS);
     else if (rp.tile_w == 8 && rp.tile_h == 32)
@@ -167,15 +164,12 @@ cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_entries(const float *part, const uint32_t *offsets,
-                                  const uint32_t *touched_r, const float4 *ranked,
-                                  const int32_t *tile_rmax, const uint32_t *perm,
-                                  const RenderParams &rp, int W, int H, int64_t n, float *g2d,
-                                  cudaStream_t st) {
+cudaError_t launch_reduce_entries(float *part, const uint32_t *offsets, const uint32_t *touched_r,
+                                  const uint32_t *perm, int64_t n, uint32_t cap, float *g2d, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int64_t threads = n * 32;
-    k_reduce_entries<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(part, offsets, touched_r, ranked,
-                                                                         tile_rmax, perm, rp, W, H, n, g2d);
+    k_reduce_entries<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(part, offsets, touched_r, perm, n, cap,
+                                                                         g2d);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -273,12 +273,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_batch_blend_bwd(const BatchReq 
                                                          const float *__restrict__ final_T,
                                                          const uint32_t *__restrict__ n_contrib,
                                                          const float *const *__restrict__ dimgs,
-                                                         float *__restrict__ part, int32_t *__restrict__ rmax,
-                                                         unsigned long long *counter) {
+                                                         float *__restrict__ part, unsigned long long *counter) {
     __shared__ __align__(16) BwdSmem sm;
     __shared__ TileBwd s_in;
     __shared__ int4 s_tile;    // tx, ty, range start, range end (tx < 0: no tile left)
-    __shared__ long long s_t;  // global tile index
     for (;;) {
         if (threadIdx.x == 0) {
             const long long t = (long long)atomicAdd(counter, 1ull);
@@ -288,7 +286,6 @@ __global__ void __launch_bounds__(kBwdThreads) k_batch_blend_bwd(const BatchReq 
                 const int local = (int)(t - R.tile_base);
                 const uint2 rg = ranges[t];
                 s_tile = make_int4(local % R.rp.ntx, local / R.rp.ntx, (int)rg.x, (int)rg.y);
-                s_t = t;
                 s_in = TileBwd{final_T + R.pixel_base, n_contrib + R.pixel_base, dimgs[q], R.rp, R.cam.width,
                                R.cam.height, eshift[q]};
             } else {
@@ -299,33 +296,26 @@ __global__ void __launch_bounds__(kBwdThreads) k_batch_blend_bwd(const BatchReq 
         const int4 tl = s_tile;
         if (tl.x < 0) break;
         blend_bwd_tile<TW, TH>(tl.x, tl.y, make_uint2((uint32_t)tl.z, (uint32_t)tl.w), sorted_vals, ranked, offsets,
-                               s_in, part, rmax + s_t, sm);
+                               s_in, part, sm);
         __syncthreads();
     }
 }
 
 // One warp per rank: the Gaussian's partials over its tiles -> g2d at its item.
-__global__ void __launch_bounds__(256) k_batch_reduce(const float *__restrict__ part,
+__global__ void __launch_bounds__(256) k_batch_reduce(float *__restrict__ part,
                                                       const uint32_t *__restrict__ offsets,
                                                       const uint32_t *__restrict__ touched_r,
-                                                      const float4 *__restrict__ ranked,
-                                                      const int32_t *__restrict__ rmax,
                                                       const uint32_t *__restrict__ perm,
-                                                      const BatchReq *__restrict__ reqs,
                                                       const int64_t *__restrict__ item_base, int n_req,
-                                                      const uint32_t *__restrict__ eshift, int64_t n,
+                                                      const uint32_t *__restrict__ eshift, int64_t n, uint32_t cap,
                                                       float *__restrict__ g2d) {
-    const int lane = threadIdx.x & 31;
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= n) return;
-    float mine = 0.f;
-    if (touched_r[r]) {
-        const int q = find_req(item_base, n_req, r);
-        const BatchReq &R = reqs[q];
-        mine = reduce_entries_warp(part, offsets[r] + eshift[q], r, ranked, rmax + R.tile_base, R.rp, R.cam.width,
-                                   R.cam.height);
-    }
-    if (lane < 9) g2d[9 * (int64_t)perm[r] + lane] = mine;
+    const uint32_t cnt = touched_r[r];
+    const uint32_t base = cnt ? offsets[r] + eshift[find_req(item_base, n_req, r)] : 0u;
+    float out0, out8;
+    reduce_entries_warp(part, base, cnt, cap, out0, out8);
+    store_reduced(g2d + 9 * (int64_t)perm[r], out0, out8);
 }
 
 // Compact position of global Gaussian i in a selection, or -1.
@@ -462,14 +452,15 @@ struct BatchState {
     DevBuf reqs_dev, item_base, tile_base, seg_items, ebase, eshift, ecount, seg_entries, dimg_dev;
     DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
         final_T, n_contrib, diff, words, counter, scratch;
-    DevBuf part, g2d, mcontrib, rmax, gpartial;
+    DevBuf part, g2d, mcontrib, gpartial;
+    bool part_clean = false;  // part holds only zeros (see the reduce)
 
     ~BatchState() {
         DevBuf *bufs[] = {&reqs_dev, &item_base, &tile_base, &seg_items, &ebase, &eshift, &ecount,
                           &seg_entries, &dimg_dev, &rec, &ranked, &dkeys[0], &dkeys[1], &dvals[0],
                           &dvals[1], &touched, &touched_r, &offsets, &tkeys[0], &tkeys[1], &tvals[0],
                           &tvals[1], &ranges, &final_T, &n_contrib, &diff, &words, &counter, &scratch,
-                          &part, &g2d, &mcontrib, &rmax, &gpartial};
+                          &part, &g2d, &mcontrib, &gpartial};
         for (DevBuf *b : bufs) release(*b);
         if (staging) cudaFreeHost(staging);
         if (staging_base) cudaFreeHost(staging_base);
@@ -877,10 +868,13 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
     const int64_t chunks = items / gc::kBatchChunk;
     Sizer need{ctx, fixed};
     need(B.dimg_dev, sizeof(float *) * n_req);
-    need(B.part, (size_t)K * 9 * 4 + 64);
+    {
+        void *before = B.part.p;
+        need(B.part, (size_t)K * 9 * 4 + 64);
+        if (B.part.p != before) B.part_clean = false;
+    }
     need(B.g2d, (size_t)ni * 9 * 4);
     need(B.mcontrib, (size_t)ni * 7 * 4);
-    need(B.rmax, (size_t)std::max<int64_t>(B.n_tiles, 1) * 4);
     if (G) need(B.gpartial, (size_t)std::max<int64_t>(chunks, 1) * G * 7 * 4);
     if (need.st != GC_OK) return need.st;
     if (!same_dimg) {
@@ -897,7 +891,12 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
     const gc::BatchReq *rq_dev = B.reqs_dev.as<gc::BatchReq>();
     const int64_t *ib_dev = B.item_base.as<int64_t>(), *tb_dev = B.tile_base.as<int64_t>();
 
+    if (!B.part_clean) {
+        if (capturing) return fail(ctx, GC_ERR_STATE, "the partials buffer is not clean; run the backward eagerly first");
+        GC_CUDA(ctx, cudaMemsetAsync(B.part.p, 0, B.part.cap, s));
+    }
     GC_CUDA(ctx, mark(GC_STAGE_BLEND_BWD));
+    B.part_clean = false;
     if (G) GC_CUDA(ctx, cudaMemsetAsync(B.mcontrib.p, 0, (size_t)ni * 7 * 4, s));
     GC_CUDA(ctx, cudaMemsetAsync(B.counter.p, 0, 8, s));
     {
@@ -906,8 +905,7 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
         auto grid = [&](int64_t g) { return (unsigned)std::min<int64_t>(std::max<int64_t>(B.n_tiles, 1), g); };
 #define GC_BB_ARGS rq_dev, tb_dev, n_req, B.n_tiles, B.ranges.as<uint2>(), sv, B.ranked.as<float4>(),            \
                    B.offsets.as<uint32_t>(), B.eshift.as<uint32_t>(), B.final_T.as<float>(),                     \
-                   B.n_contrib.as<uint32_t>(), B.dimg_dev.as<const float *>(), B.part.as<float>(),              \
-                   B.rmax.as<int32_t>(), ctr
+                   B.n_contrib.as<uint32_t>(), B.dimg_dev.as<const float *>(), B.part.as<float>(), ctr
         if (B.opt.tile_w == 16)
             gc::k_batch_blend_bwd<16, 16><<<grid(gc::persistent_grid<gc::k_batch_blend_bwd<16, 16>, gc::kBwdThreads>()), gc::kBwdThreads, 0, s>>>(GC_BB_ARGS);
         else if (B.opt.tile_w == 8)
@@ -921,12 +919,13 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
     if (items > 0) {
         GC_CUDA(ctx, mark(GC_STAGE_REDUCE));
         gc::k_batch_reduce<<<(unsigned)((items * 32 + 255) / 256), 256, 0, s>>>(
-            B.part.as<float>(), B.offsets.as<uint32_t>(), B.touched_r.as<uint32_t>(), B.ranked.as<float4>(),
-            B.rmax.as<int32_t>(), B.dvals[B.depth_buf].as<uint32_t>(), rq_dev, ib_dev, n_req,
-            B.eshift.as<uint32_t>(), items, B.g2d.as<float>());
+            B.part.as<float>(), B.offsets.as<uint32_t>(), B.touched_r.as<uint32_t>(),
+            B.dvals[B.depth_buf].as<uint32_t>(), ib_dev, n_req, B.eshift.as<uint32_t>(), items,
+            (uint32_t)std::min<int64_t>(B.K_cap, 0xFFFFFFFFll), B.g2d.as<float>());
         gc::note_launches(1);
         GC_CUDA(ctx, cudaGetLastError());
     }
+    B.part_clean = true;
     GC_CUDA(ctx, mark(GC_STAGE_PREPROCESS_BWD));
     if (g->n > 0) {
         gc::k_batch_preprocess_bwd<<<(unsigned)((g->n + 127) / 128), 128, 0, s>>>(

@@ -144,23 +144,22 @@ cudaError_t launch_entries_to_global(const uint32_t *sorted_vals, const uint32_t
 // ---- backward ----
 
 // Reverse compositing per tile; writes 9 partial gradients per (tile, Gaussian)
-// entry at the entry's emit position e = offsets[r] + (index of the tile in the
-// Gaussian's tile rectangle): part[9 * e + c], c = du, dv, da, db, dc, dopacity,
-// dr, dg, db.  Entries behind every pixel's last blended one are not written;
-// tile_rmax[t] = largest rank that may have contributed to tile t (-1: none).
+// entry at the entry's emit position e = offsets[r] + (index of the tile among the
+// Gaussian's row intervals): part[9 * e + c], c = du, dv, da, db, dc, dopacity,
+// dr, dg, db.  Entries behind every pixel's last blended one are not written: the
+// buffer must hold zeros there (the reduce leaves it all zero).
 cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
                              const float4 *ranked, const uint32_t *offsets, const CamParams &cam,
                              const RenderParams &rp, const float *final_T,
                              const uint32_t *n_contrib, const float *dL_dimg, float *part,
-                             int64_t K, int32_t *tile_rmax, cudaStream_t st);
+                             cudaStream_t st);
 
 // Per-rank sum of the partials over the Gaussian's entries -> g2d[9 * j + c] at the
-// Gaussian's compact position j = perm[r].
-cudaError_t launch_reduce_entries(const float *part, const uint32_t *offsets,
-                                  const uint32_t *touched_r, const float4 *ranked,
-                                  const int32_t *tile_rmax, const uint32_t *perm,
-                                  const RenderParams &rp, int W, int H, int64_t n, float *g2d,
-                                  cudaStream_t st);
+// Gaussian's compact position j = perm[r]; zeroes the partials it read (all of them
+// nonzero are reset, so the buffer is all zero afterwards).  cap: buffer capacity in
+// entries (Gaussians whose entries pass it contribute zero).
+cudaError_t launch_reduce_entries(float *part, const uint32_t *offsets, const uint32_t *touched_r,
+                                  const uint32_t *perm, int64_t n, uint32_t cap, float *g2d, cudaStream_t st);
 
 // Chain rule from the 2D gradients (by compact position) to the attributes (by
 // global index) and to per-Gaussian motion terms (7 floats per compact position:

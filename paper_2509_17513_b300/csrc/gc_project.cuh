@@ -253,7 +253,7 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
 // its extreme points.  Without the alpha cull, or for a degenerate conic, rows are the
 // whole rectangle.
 struct RowGeom {
-    float u, v, ia, ib, ic, tc, detc, sy;
+    float u, v, ia, ib, ic, tc, detc, sy, ria, at;
     int x0, x1, y0, y1, tx0, tx1, ty0, ty1;
     bool cull;
 };
@@ -278,17 +278,21 @@ __device__ __forceinline__ void row_geom(const float4 &r0, const float4 &r2, con
     g.detc = fsub(fmul(g.ia, g.ic), fmul(g.ib, g.ib));
     g.cull = rp.alpha_cull && g.detc > 0.f;
     g.sy = 0.f;
+    g.ria = 0.f;
+    g.at = 0.f;
     if (g.cull) {
         const float xa = __fsqrt_rn(fdiv(fmul(g.tc, g.ic), g.detc));
         g.sy = fdiv(fmul(g.ib, xa), g.ic);
+        g.ria = fdiv(1.f, g.ia);
+        g.at = fmul(g.ia, g.tc);
     }
 }
 
 // Binning step 15: tile columns [a, b] (a > b: empty) of tile row ty, i.e. the tiles whose
 // pixel centres in the row's band of pixel-centre rows can meet the ellipse.  Over dy in
-// [d0, d1] the ellipse spans dx in [(-b dy - sqrt(a tc - det dy^2)) / a, (-b dy + sqrt(.)) / a];
-// the right end is largest at dy = -sy, the left end smallest at dy = sy, each clamped into
-// the band.  Every operation is a separately rounded IEEE binary32 operation (the oracle's
+// [d0, d1] the ellipse spans dx in [(-b dy - sqrt(a tc - det dy^2)) / a, (-b dy + sqrt(.)) / a]
+// (evaluated as products with ria = 1 / a); the right end is largest at dy = -sy, the left
+// end smallest at dy = sy, each clamped into the band.  Every operation is a separately rounded IEEE binary32 operation (the oracle's
 // FP32 mirror evaluates the same sequence).
 __device__ __forceinline__ void row_interval(const RowGeom &g, int ty, const RenderParams &rp, int W, int H,
                                              int &a, int &b) {
@@ -310,10 +314,9 @@ __device__ __forceinline__ void row_interval(const RowGeom &g, int ty, const Ren
     }
     const float d0 = fsub(fadd((float)r0, 0.5f), g.v), d1 = fsub(fadd((float)r1, 0.5f), g.v);
     const float dr = fminf(fmaxf(-g.sy, d0), d1), dl = fminf(fmaxf(g.sy, d0), d1);
-    const float at = fmul(g.ia, g.tc);
-    const float qr = fsub(at, fmul(fmul(g.detc, dr), dr)), ql = fsub(at, fmul(fmul(g.detc, dl), dl));
-    const float xr = fdiv(fsub(__fsqrt_rn(fmaxf(qr, 0.f)), fmul(g.ib, dr)), g.ia);
-    const float xl = fdiv(fsub(-fmul(g.ib, dl), __fsqrt_rn(fmaxf(ql, 0.f))), g.ia);
+    const float qr = fsub(g.at, fmul(fmul(g.detc, dr), dr)), ql = fsub(g.at, fmul(fmul(g.detc, dl), dl));
+    const float xr = fmul(fsub(__fsqrt_rn(fmaxf(qr, 0.f)), fmul(g.ib, dr)), g.ria);
+    const float xl = fmul(fsub(-fmul(g.ib, dl), __fsqrt_rn(fmaxf(ql, 0.f))), g.ria);
     float fx0 = ceilf(fsub(fadd(g.u, xl), 0.5f)), fx1 = floorf(fsub(fadd(g.u, xr), 0.5f));
     fx0 = fmaxf(fx0, (float)c0);
     fx1 = fminf(fx1, (float)c1);
@@ -405,46 +408,74 @@ __device__ __forceinline__ uint32_t entry_index(const RowGeom &g, int tx, int ty
     return k + (uint32_t)(tx - a);
 }
 
-// One warp sums the partials of rank r's entries (positions base + k, nine floats each)
-// over the tiles whose largest contributing rank (rmax, by tile index) is >= r; walks
-// the Gaussian's rows in order, lanes over each row's columns.  Returns the nine sums
-// in lanes 0..8 of `mine`.
-__device__ __forceinline__ float reduce_entries_warp(const float *__restrict__ part, uint32_t base, int64_t r,
-                                                     const float4 *__restrict__ ranked,
-                                                     const int32_t *__restrict__ rmax, const RenderParams &rp,
-                                                     int W, int H) {
+// One warp sums the partials of one Gaussian's entries (positions base .. base + cnt - 1,
+// nine floats each, contiguous) and sets every nonzero one back to zero, so that the
+// partials buffer is all zeros again for the next reverse pass (entries the reverse
+// blend does not reach are never written and must read as zero).  Entries past `cap`
+// (an overflowed fixed capacity) are skipped.  Lanes stride over the entries; the warp
+// sum is a transposing butterfly: afterwards lane 4 c holds value c (c < 8) and every
+// lane holds value 8.
+__device__ __forceinline__ void reduce_entries_warp(float *__restrict__ part, uint32_t base, uint32_t cnt,
+                                                    uint32_t cap, float &out0, float &out8) {
     const int lane = threadIdx.x & 31;
-    float acc[9];
+    float v[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) acc[c] = 0.f;
-    RowGeom g;
-    row_geom(ranked[kRec * r], ranked[kRec * r + 2], ranked[kRec * r + 3], rp, g);
-    uint32_t k = 0u;
-    for (int ty = g.ty0; ty <= g.ty1; ++ty) {
-        int a, b;
-        row_interval(g, ty, rp, W, H, a, b);
-        if (a > b) continue;
-        for (int col = a + lane; col <= b; col += 32) {
-            if (r <= (int64_t)rmax[ty * rp.ntx + col]) {
-                const float *p = part + (int64_t)(base + k + (uint32_t)(col - a)) * 9;
+    for (int c = 0; c < 9; ++c) v[c] = 0.f;
+    if ((uint64_t)base + cnt <= cap) {
+        for (uint32_t k = lane; k < cnt; k += 32) {
+            float *p = part + (int64_t)(base + k) * 9;
+            float x[9];
+            bool nz = false;
 #pragma unroll
-                for (int c = 0; c < 9; ++c) acc[c] += p[c];
+            for (int c = 0; c < 9; ++c) {
+                x[c] = p[c];
+                nz |= x[c] != 0.f;
+                v[c] += x[c];
+            }
+            if (nz) {
+#pragma unroll
+                for (int c = 0; c < 9; ++c) p[c] = 0.f;
             }
         }
-        k += (uint32_t)(b - a + 1);
     }
+    {
+        const bool up = lane & 16;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-        float x = acc[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        acc[c] = x;
+        for (int i = 0; i < 4; ++i) {
+            const float send = up ? v[i] : v[i + 4];
+            const float keep = up ? v[i + 4] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
     }
-    float mine = 0.f;
+    {
+        const bool up = lane & 8;
 #pragma unroll
-    for (int c = 0; c < 9; ++c)
-        if (lane == c) mine = acc[c];
-    return mine;
+        for (int i = 0; i < 2; ++i) {
+            const float send = up ? v[i] : v[i + 2];
+            const float keep = up ? v[i + 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+    }
+    {
+        const bool up = lane & 4;
+        const float send = up ? v[0] : v[1];
+        const float keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    out0 = v[0];
+    float x8 = v[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x8 += __shfl_xor_sync(0xffffffffu, x8, o);
+    out8 = x8;
+}
+
+// Writes the nine sums of reduce_entries_warp to g[0..8].
+__device__ __forceinline__ void store_reduced(float *g, float out0, float out8) {
+    const int lane = threadIdx.x & 31;
+    if ((lane & 3) == 0) g[lane >> 2] = out0;
+    if (lane == 1) g[8] = out8;
 }
 
 // Tiles touched by a projected Gaussian (sum of its row intervals); if diff != NULL also

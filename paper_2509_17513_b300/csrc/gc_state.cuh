@@ -93,7 +93,8 @@ struct gc_context {
     uint64_t launch_base = 0;
     gc_options opt{};
     gc_saved internal;
-    DevBuf scratch, bwd_part, bwd_g2d, bwd_motion, bwd_rmax, bwd_group;
+    DevBuf scratch, bwd_part, bwd_g2d, bwd_motion, bwd_group;
+    bool bwd_part_clean = false;  // bwd_part holds only zeros (see the reduce)
     uint32_t *host_word = nullptr;  // pinned
     const gc_saved *last = nullptr; // state written by the most recent forward
     std::string err;

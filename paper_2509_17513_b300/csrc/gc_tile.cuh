@@ -259,14 +259,13 @@ __device__ __forceinline__ void bwd_blend(BwdPix &P, float dx, float dy, float a
 // (values 0-7 spread over lane groups) plus a plain butterfly for value 8 - skipped when
 // no pixel of the warp blended the entry - then over the warps in order, and stored at
 // the entry's emit position offsets[r] + entry_shift + (index of the tile in the
-// Gaussian's tile rectangle).  *tile_rmax receives the largest rank that may have
-// contributed (-1: none).
+// Gaussian's row intervals).
 template <int TW, int TH>
 __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
                                                const uint32_t *__restrict__ sorted_vals,
                                                const float4 *__restrict__ ranked,
                                                const uint32_t *__restrict__ offsets, const TileBwd &o,
-                                               float *__restrict__ part, int32_t *tile_rmax, BwdSmem &sm) {
+                                               float *__restrict__ part, BwdSmem &sm) {
     static_assert(TW % 8 == 0 && TH % 8 == 0 && TW * TH == 256, "tile must be 256 pixels of 8x8 blocks");
     constexpr int BX = TW / 8;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -296,7 +295,6 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
     if (lane == 0) atomicMax(&sm.last_max, wmax);
     __syncthreads();
     const int n_active = (int)sm.last_max;
-    if (threadIdx.x == 0) *tile_rmax = n_active > 0 ? (int32_t)sorted_vals[range.x + n_active - 1] : -1;
 
     for (int hi = n_active; hi > 0; hi -= 256) {
         const int lo = max(hi - 256, 0);
