@@ -187,7 +187,7 @@ constexpr int kBwdThreads = 128;
 // d = {b_nat, c_nat} (colour and natural conic, read only for blended pairs); m the
 // membership masks (per entry: two words per warp, the upper and lower 8 x 4 halves of
 // its 8 x 8 block); e the entries' emit positions; wpart the per-warp sums of a group of
-// 32 entries.
+// 64 entries.
 struct BwdSmem {
     float4 a[256];
     float2 b[256];
@@ -195,7 +195,7 @@ struct BwdSmem {
     float2 d[256];
     uint32_t m[256 * 8];
     uint32_t e[256];
-    float wpart[32][4][9];
+    float wpart[64][4][9];
     uint32_t last_max;
 };
 
@@ -226,11 +226,12 @@ struct BwdPix {
 };
 
 // Reverse step of Eq. 2 for one pixel and a blended entry: undoes the blend
-// (T_before = T_after / (1 - alpha), running colour behind) and adds the pixel's nine
+// (T_before = T_after / (1 - alpha) by a fast divide, 1 - alpha >= 0.01; running colour
+// behind) and adds the pixel's nine
 // partials (du, dv, da, db, dc, dopacity, dr, dg, db) to v.
 __device__ __forceinline__ void bwd_blend(BwdPix &P, float dx, float dy, float alpha, float a0, float G,
                                           const float4 &col, const float2 &nd, float *v) {
-    P.T = P.T / (1.f - alpha);
+    P.T = __fdividef(P.T, 1.f - alpha);
     const float w = alpha * P.T;
     v[6] += w * P.g0;
     v[7] += w * P.g1;
@@ -328,8 +329,8 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
             }
         }
         __syncthreads();
-        for (int gtop = hi; gtop > lo; gtop -= 32) {
-            const int gbot = max(gtop - 32, lo);
+        for (int gtop = hi; gtop > lo; gtop -= 64) {
+            const int gbot = max(gtop - 64, lo);
             for (int k = gtop - 1; k >= gbot; --k) {
                 const int s = k - lo;
                 const uint2 wm = *reinterpret_cast<const uint2 *>(&sm.m[8 * s + 2 * warp]);
