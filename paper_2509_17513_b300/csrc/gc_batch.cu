@@ -69,13 +69,20 @@ __device__ __forceinline__ int find_req(const int64_t *base, int n, int64_t x) {
     return lo;
 }
 
-__global__ void __launch_bounds__(256) k_batch_preprocess(GaussSrc G, const BatchReq *__restrict__ reqs,
+// The request-independent activations of every Gaussian (scales, alpha level), once per batch.
+__global__ void __launch_bounds__(256) k_batch_activate(GaussSrc G, int64_t n, float4 *__restrict__ act) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) act[i] = gaussian_activation(G, i);
+}
+
+__global__ void __launch_bounds__(256, 5) k_batch_preprocess(GaussSrc G, const BatchReq *__restrict__ reqs,
                                                           const int64_t *__restrict__ item_base, int n_req,
                                                           int64_t n_items, float4 *__restrict__ rec,
                                                           uint32_t *__restrict__ keys,
                                                           uint32_t *__restrict__ vals,
                                                           uint32_t *__restrict__ touched,
-                                                          int32_t *__restrict__ diff) {
+                                                          int32_t *__restrict__ diff,
+                                                          const float4 *__restrict__ act) {
     const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= n_items) return;
     const int q = find_req(item_base, n_req, item);
@@ -84,17 +91,18 @@ __global__ void __launch_bounds__(256) k_batch_preprocess(GaussSrc G, const Batc
     vals[item] = (uint32_t)item;
     Proj P;
     if (j < R.n_sel) {
-        project_gaussian(G, sel_global(R.sel, j), R.group_q, R.group_t, R.n_groups, R.cam, R.rp, P);
+        project_gaussian(G, sel_global(R.sel, j), R.group_q, R.group_t, R.n_groups, R.cam, R.rp, P, act);
     } else {
         P.key = kCulledKey;
         P.ntouch = 0;
-        P.r0 = P.r1 = P.r2 = P.r3 = make_float4(0.f, 0.f, 0.f, 0.f);
+        P.r0 = P.r1 = P.r2 = P.r3 = P.r4 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     rec[kRec * item] = P.r0;
     rec[kRec * item + 1] = P.r1;
     rec[kRec * item + 2] = P.r2;
-    rec[kRec * item + 3] = P.r3;
     const uint32_t nt = bin_rows(P, R.rp, R.cam.width, R.cam.height, diff + R.diff_base, R.rp.ntx + 1);
+    rec[kRec * item + 3] = P.r3;
+    rec[kRec * item + 4] = P.r4;
     keys[item] = P.key;
     touched[item] = nt;
 }
@@ -451,7 +459,7 @@ struct BatchState {
     gc_options opt{};
     DevBuf reqs_dev, item_base, tile_base, seg_items, ebase, eshift, ecount, seg_entries, dimg_dev;
     DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
-        final_T, n_contrib, diff, words, counter, scratch;
+        final_T, n_contrib, diff, words, counter, scratch, act;
     DevBuf part, g2d, mcontrib, gpartial;
     bool part_clean = false;  // part holds only zeros (see the reduce)
 
@@ -459,7 +467,7 @@ struct BatchState {
         DevBuf *bufs[] = {&reqs_dev, &item_base, &tile_base, &seg_items, &ebase, &eshift, &ecount,
                           &seg_entries, &dimg_dev, &rec, &ranked, &dkeys[0], &dkeys[1], &dvals[0],
                           &dvals[1], &touched, &touched_r, &offsets, &tkeys[0], &tkeys[1], &tvals[0],
-                          &tvals[1], &ranges, &final_T, &n_contrib, &diff, &words, &counter, &scratch,
+                          &tvals[1], &ranges, &final_T, &n_contrib, &diff, &words, &counter, &scratch, &act,
                           &part, &g2d, &mcontrib, &gpartial};
         for (DevBuf *b : bufs) release(*b);
         if (staging) cudaFreeHost(staging);
@@ -690,6 +698,7 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     need(B.n_contrib, (size_t)pixels * 4);
     need(B.diff, (size_t)cells * 4);
     need(B.counter, 16);
+    need(B.act, (size_t)std::max<int64_t>(g->n, 1) * 16);
     const bool fresh_words = !B.words.p;
     need(B.words, 64);
     need(B.scratch, 4 * std::max(gc::radix_scratch_words(ni), gc::scan_partials_size(ni)));
@@ -730,10 +739,11 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     const int64_t *ib_dev = B.item_base.as<int64_t>(), *tb_dev = B.tile_base.as<int64_t>();
     uint32_t *scratch = B.scratch.as<uint32_t>();
     if (items > 0) {
+        gc::k_batch_activate<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(src, g->n, B.act.as<float4>());
         gc::k_batch_preprocess<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(
             src, rq_dev, ib_dev, n_req, items, B.rec.as<float4>(), B.dkeys[0].as<uint32_t>(),
-            B.dvals[0].as<uint32_t>(), B.touched.as<uint32_t>(), B.diff.as<int32_t>());
-        gc::note_launches(1);
+            B.dvals[0].as<uint32_t>(), B.touched.as<uint32_t>(), B.diff.as<int32_t>(), B.act.as<float4>());
+        gc::note_launches(2);
         GC_CUDA(ctx, cudaGetLastError());
         GC_CUDA(ctx, mark(GC_STAGE_DEPTH_SORT));
         uint32_t *dk[2] = {B.dkeys[0].as<uint32_t>(), B.dkeys[1].as<uint32_t>()};

@@ -1,6 +1,6 @@
 // gc_internal.cuh - device-side types and launchers shared by the kernel files.
 //
-// Layout of the per-Gaussian projected record (four float4, 64 bytes), written
+// Layout of the per-Gaussian projected record (five float4, 80 bytes), written
 // by the preprocess kernel at the Gaussian's compact (selected) position and
 // gathered into depth-rank order before binning:
 //   r0 = { u, v, A, B }                  conic = inverse 2D covariance [[a, b], [b, c]],
@@ -10,8 +10,12 @@
 //                                        hi16 = last (inclusive)
 //   r3 = { a, b, c, tc }                 the conic as computed by the binning spec and the
 //                                        alpha-ellipse level (row intervals, step 15)
-// The blends read r0..r2; binning, emit and the reverse pass recompute a Gaussian's
-// per-row tile intervals from r0, r2, r3.
+//   r4 = 16 bytes                        the row intervals packed (row i: start column
+//                                        - tx0 in byte 2i, length in byte 2i + 1) when
+//                                        the Gaussian has at most 8 tile rows and every
+//                                        start offset is below 255; byte 0 = 255 otherwise
+// The blends read r0..r2; emit and the reverse pass read a Gaussian's per-row tile
+// intervals from r4, or recompute them from r0, r2, r3 when they are not packed.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -22,7 +26,7 @@ namespace gc {
 
 constexpr int kMaxLayers = 32;
 constexpr uint32_t kCulledKey = 0xFFFFFFFFu;
-constexpr int kRec = 4;  // float4s per projected record
+constexpr int kRec = 5;  // float4s per projected record
 
 // Selected layer ranges: compact index j maps to global index
 // range_begin[k] + (j - range_start[k]) for the range k holding j.

@@ -23,8 +23,9 @@ __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, i
     rec[kRec * j] = P.r0;
     rec[kRec * j + 1] = P.r1;
     rec[kRec * j + 2] = P.r2;
-    rec[kRec * j + 3] = P.r3;
     const uint32_t nt = bin_rows(P, rp, cam.width, cam.height, tile_diff, rp.ntx + 1);
+    rec[kRec * j + 3] = P.r3;
+    rec[kRec * j + 4] = P.r4;
     depth_keys[j] = P.key;
     depth_vals[j] = (uint32_t)j;
     touched[j] = nt;

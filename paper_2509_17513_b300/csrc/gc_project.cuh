@@ -68,17 +68,28 @@ __device__ __forceinline__ float load_sh(const GaussSrc &G, int64_t i, int k, in
 // Result of projecting one Gaussian: the three record float4s, the depth key
 // (kCulledKey when culled), the number of tiles touched and the tile rectangle.
 struct Proj {
-    float4 r0, r1, r2, r3;
+    float4 r0, r1, r2, r3, r4;
     uint32_t key, ntouch;
     int tx0, tx1, ty0, ty1;
 };
 
 // Projects global Gaussian i under group motion (group_q == NULL: identity) into
 // camera `cam` with options `rp`.
+// Per-Gaussian values that depend on no camera or motion: the scales
+// s = (float)exp((double)log_s) (step 5) and tau = (float)(2 ln(255 / (1 + exp(-logit))))
+// (step 14).  A batch computes them once per Gaussian instead of once per request.
+__device__ __forceinline__ float4 gaussian_activation(const GaussSrc &G, int64_t i) {
+    Attr A;
+    load_attr(G, i, A);
+    return make_float4((float)exp((double)A.ls[0]), (float)exp((double)A.ls[1]), (float)exp((double)A.ls[2]),
+                       (float)(2.0 * log(255.0 / (1.0 + exp(-(double)A.logit)))));
+}
+
+// act: NULL, or the cached gaussian_activation of every Gaussian (bit-identical results).
 __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, const float *group_q,
                                                 const float *group_t, int n_groups,
                                                 const CamParams &cam, const RenderParams &rp,
-                                                Proj &P) {
+                                                Proj &P, const float4 *act = nullptr) {
     Attr A;
     load_attr(G, i, A);
     P.key = kCulledKey;
@@ -88,6 +99,7 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
     P.r1 = P.r0;
     P.r2 = P.r0;
     P.r3 = P.r0;
+    P.r4 = P.r0;
     do {
         float gq[4] = {1.f, 0.f, 0.f, 0.f}, gt[3] = {0.f, 0.f, 0.f};
         if (group_q && (A.g < 0 || A.g >= n_groups)) break;  // invalid group id: culled
@@ -121,8 +133,16 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
         R[6] = fmul(2.f, fsub(xz, wy)); R[7] = fmul(2.f, fadd(yz, wx)); R[8] = fsub(1.f, fmul(2.f, fadd(xx, yy)));
         // 5. scales, correctly rounded to FP32 through FP64
         float s[3];
+        float4 av;
+        if (act) {
+            av = act[i];
+            s[0] = av.x;
+            s[1] = av.y;
+            s[2] = av.z;
+        } else {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) s[k] = (float)exp((double)A.ls[k]);
+            for (int k = 0; k < 3; ++k) s[k] = (float)exp((double)A.ls[k]);
+        }
         // 6-7. M = R diag(s), Sigma = M M^T
         float M[9];
 #pragma unroll
@@ -204,7 +224,7 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
         //     has half-extents sqrt(tau_c ic / det_c), sqrt(tau_c ia / det_c)
         float tc_out = 0.f;
         if (rp.alpha_cull) {
-            const float tau = (float)(2.0 * log(255.0 / (1.0 + exp(-(double)A.logit))));
+            const float tau = act ? av.w : (float)(2.0 * log(255.0 / (1.0 + exp(-(double)A.logit))));
             if (!(tau > 0.f)) break;  // opacity <= 1/255: never blended
             const float t1 = fadd(rf, 1.f);
             const float mt = fmul(fadd(fadd(ia, fmul(2.f, fabsf(ib))), ic), fmul(t1, t1));
@@ -232,12 +252,16 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
         float dxv = m0 - cam.campos[0], dyv = m1 - cam.campos[1], dzv = m2 - cam.campos[2];
         float inv = 1.0f / sqrtf(dxv * dxv + dyv * dyv + dzv * dzv);
         float Y[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) Y[k] = 0.f;
         sh_basis(G.sh_degree, dxv * inv, dyv * inv, dzv * inv, Y);
         float rgb[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float acc = 0.f;
-            for (int k = 0; k < G.K; ++k) acc = fmaf(Y[k], load_sh(G, i, k, c), acc);
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (k < G.K) acc = fmaf(Y[k], load_sh(G, i, k, c), acc);
             rgb[c] = fmaxf(acc + 0.5f, 0.f);
         }
         const float op = 1.0f / (1.0f + expf(-A.logit));
@@ -329,13 +353,35 @@ __device__ __forceinline__ void row_interval(const RowGeom &g, int ty, const Ren
     b = (int)fx1 >> rp.tile_w_log2;
 }
 
+// Packed row intervals (r4): row i of a Gaussian with tile columns from tx0 has start
+// tx0 + byte(2i) and length byte(2i + 1); byte 0 = 255 means "not packed".
+__device__ __forceinline__ bool rows_packed(const float4 &r4) {
+    return (__float_as_uint(r4.x) & 0xffu) != 0xffu;
+}
+
+__device__ __forceinline__ void packed_row(const float4 &r4, int i, int tx0, int &a, int &b) {
+    const uint32_t w = __float_as_uint(i < 2 ? r4.x : i < 4 ? r4.y : i < 6 ? r4.z : r4.w);
+    const uint32_t h = (w >> (16 * (i & 1))) & 0xffffu;
+    a = tx0 + (int)(h & 0xffu);
+    b = a + (int)(h >> 8) - 1;
+}
+
+// Row interval of row ty: from the packed bytes when present, else recomputed.
+__device__ __forceinline__ void row_interval_rec(const RowGeom &g, const float4 &r4, int ty,
+                                                 const RenderParams &rp, int W, int H, int &a, int &b) {
+    if (rows_packed(r4)) packed_row(r4, ty - g.ty0, g.tx0, a, b);
+    else row_interval(g, ty, rp, W, H, a, b);
+}
+
 // Emit of one warp: the 32 consecutive ranks wbase .. wbase + 31 (all of one image) write
 // their (tile key, rank) entries, entry k of rank r at position offsets[r] + shift + k
 // with k running over the Gaussian's tile rows in order and over the columns of each
-// row's interval.  The warp walks the row index j = 0, 1, ... of all its Gaussians
-// together; per step a warp scan of the lanes' interval lengths spreads the step's
-// entries over the lanes (each lane's entries stay contiguous).  Positions >= cap are
-// dropped.
+// row's interval.  Gaussians with packed row intervals (nearly all): the lanes stride
+// over the warp's contiguous output range, each finding its entry's Gaussian by a
+// search over the lanes' offsets and its row by a scan of the packed lengths (coalesced
+// writes).  The others: the warp walks their row index j = 0, 1, ... together; per step
+// a warp scan of the lanes' interval lengths spreads the step's entries over the lanes.
+// Positions >= cap are dropped.
 __device__ __forceinline__ void emit_rows_warp(const float4 *__restrict__ ranked, int64_t wbase, int64_t n,
                                                const uint32_t *__restrict__ offsets,
                                                const uint32_t *__restrict__ touched_r, uint32_t shift,
@@ -343,16 +389,71 @@ __device__ __forceinline__ void emit_rows_warp(const float4 *__restrict__ ranked
                                                uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     const int lane = threadIdx.x & 31;
     const int64_t r = wbase + lane;
-    const bool valid = r < n && touched_r[r] != 0u;
+    const bool in = r < n;
+    const uint32_t cnt = in ? touched_r[r] : 0u;
+    const uint32_t off = in ? offsets[r] + shift : 0xffffffffu;
     RowGeom g;
-    int nrows = 0;
-    uint32_t pos = 0u;
-    if (valid) {
-        row_geom(ranked[kRec * r], ranked[kRec * r + 2], ranked[kRec * r + 3], rp, g);
-        nrows = g.ty1 - g.ty0 + 1;
-        pos = offsets[r] + shift;
+    float4 r4 = make_float4(__uint_as_float(0xffu), 0.f, 0.f, 0.f);
+    bool packed = false;
+    if (cnt) {
+        r4 = ranked[kRec * r + 4];
+        packed = rows_packed(r4);
+        if (packed) {  // only the tile rectangle's origin is needed
+            const float4 r2 = ranked[kRec * r + 2];
+            g.tx0 = (int)(__float_as_uint(r2.z) & 0xffffu) >> rp.tile_w_log2;
+            g.ty0 = (int)(__float_as_uint(r2.w) & 0xffffu) >> rp.tile_h_log2;
+            g.ty1 = g.ty0;
+        } else {
+            row_geom(ranked[kRec * r], ranked[kRec * r + 2], ranked[kRec * r + 3], rp, g);
+        }
+    } else {
+        g.tx0 = g.ty0 = 0;
+        g.ty1 = -1;
     }
+    // packed Gaussians: contiguous output range of the warp
+    const uint32_t start = __shfl_sync(0xffffffffu, off, 0);
+    const uint32_t end = __reduce_max_sync(0xffffffffu, in ? off + cnt : 0u);
+    for (uint32_t e0 = start; e0 < end; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t o = __shfl_sync(0xffffffffu, off, owner + step);
+            if (o <= e) owner += step;
+        }
+        const uint32_t oo = __shfl_sync(0xffffffffu, off, owner);
+        const bool opk = __shfl_sync(0xffffffffu, (int)packed, owner) != 0;
+        const int otx = __shfl_sync(0xffffffffu, g.tx0, owner);
+        const int oty = __shfl_sync(0xffffffffu, g.ty0, owner);
+        const uint32_t w0 = __shfl_sync(0xffffffffu, __float_as_uint(r4.x), owner);
+        const uint32_t w1 = __shfl_sync(0xffffffffu, __float_as_uint(r4.y), owner);
+        const uint32_t w2 = __shfl_sync(0xffffffffu, __float_as_uint(r4.z), owner);
+        const uint32_t w3 = __shfl_sync(0xffffffffu, __float_as_uint(r4.w), owner);
+        if (e < end && opk && e < cap) {
+            uint32_t k = e - oo;
+            int row = 0, a = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint32_t w = i < 2 ? w0 : i < 4 ? w1 : i < 6 ? w2 : w3;
+                const uint32_t h = (w >> (16 * (i & 1))) & 0xffffu, len = h >> 8;
+                if (row == i) {
+                    if (k < len) {
+                        a = otx + (int)(h & 0xffu) + (int)k;
+                        row = i + 100;  // found
+                    } else {
+                        k -= len;
+                        row = i + 1;
+                    }
+                }
+            }
+            keys[e] = (uint32_t)(oty + row - 100) * (uint32_t)rp.ntx + (uint32_t)a;
+            vals[e] = (uint32_t)(wbase + owner);
+        }
+    }
+    // Gaussians whose rows are not packed: row by row
+    const int nrows = (cnt && !packed) ? g.ty1 - g.ty0 + 1 : 0;
     const int steps = __reduce_max_sync(0xffffffffu, (uint32_t)nrows);
+    uint32_t pos = off;
     for (int j = 0; j < steps; ++j) {
         int a = 0, b = -1, ty = 0;
         if (j < nrows) {
@@ -395,16 +496,16 @@ __device__ __forceinline__ void emit_rows_warp(const float4 *__restrict__ ranked
 
 // Position of tile (tx, ty) among a Gaussian's entries (its rows in order, the columns
 // of each row's interval); the tile must be one of them.
-__device__ __forceinline__ uint32_t entry_index(const RowGeom &g, int tx, int ty, const RenderParams &rp,
-                                                int W, int H) {
+__device__ __forceinline__ uint32_t entry_index(const RowGeom &g, const float4 &r4, int tx, int ty,
+                                                const RenderParams &rp, int W, int H) {
     uint32_t k = 0u;
     for (int y = g.ty0; y < ty; ++y) {
         int a, b;
-        row_interval(g, y, rp, W, H, a, b);
+        row_interval_rec(g, r4, y, rp, W, H, a, b);
         if (b >= a) k += (uint32_t)(b - a + 1);
     }
     int a, b;
-    row_interval(g, ty, rp, W, H, a, b);
+    row_interval_rec(g, r4, ty, rp, W, H, a, b);
     return k + (uint32_t)(tx - a);
 }
 
@@ -478,24 +579,40 @@ __device__ __forceinline__ void store_reduced(float *g, float out0, float out8) 
     if (lane == 1) g[8] = out8;
 }
 
-// Tiles touched by a projected Gaussian (sum of its row intervals); if diff != NULL also
-// adds each row interval to the row-difference grid (row pitch gw).
-__device__ __forceinline__ uint32_t bin_rows(const Proj &P, const RenderParams &rp, int W, int H,
-                                             int32_t *diff, int gw) {
+// Tiles touched by a projected Gaussian (sum of its row intervals); packs the intervals
+// into P.r4 when they fit; if diff != NULL also adds each row interval to the
+// row-difference grid (row pitch gw).
+__device__ __forceinline__ uint32_t bin_rows(Proj &P, const RenderParams &rp, int W, int H, int32_t *diff,
+                                             int gw) {
+    P.r4 = make_float4(__uint_as_float(0xffu), 0.f, 0.f, 0.f);
     if (!P.ntouch) return 0u;
     RowGeom g;
     row_geom(P.r0, P.r2, P.r3, rp, g);
-    uint32_t total = 0u;
+    uint32_t total = 0u, pk0 = 0u, pk1 = 0u, pk2 = 0u, pk3 = 0u;
+    bool fits = g.ty1 - g.ty0 < 8;
     for (int ty = g.ty0; ty <= g.ty1; ++ty) {
         int a, b;
         row_interval(g, ty, rp, W, H, a, b);
+        const int i = ty - g.ty0, len = b >= a ? b - a + 1 : 0;
+        const int off = b >= a ? a - g.tx0 : 0;
+        if (off > 254 || len > 255) fits = false;
+        if (fits) {
+            const uint32_t h = ((uint32_t)off | ((uint32_t)len << 8)) << (16 * (i & 1));
+            const int w = i >> 1;
+            pk0 |= w == 0 ? h : 0u;
+            pk1 |= w == 1 ? h : 0u;
+            pk2 |= w == 2 ? h : 0u;
+            pk3 |= w == 3 ? h : 0u;
+        }
         if (a > b) continue;
-        total += (uint32_t)(b - a + 1);
+        total += (uint32_t)len;
         if (diff) {
             atomicAdd(&diff[ty * gw + a], 1);
             atomicAdd(&diff[ty * gw + b + 1], -1);
         }
     }
+    if (fits)
+        P.r4 = make_float4(__uint_as_float(pk0), __uint_as_float(pk1), __uint_as_float(pk2), __uint_as_float(pk3));
     return total;
 }
 

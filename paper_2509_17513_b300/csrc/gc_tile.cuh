@@ -313,6 +313,7 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
                 rect_masks<TW, TH>(c, tx, ty, membership, cm, rm);
                 RowGeom g;
                 row_geom(a, c, ranked[kRec * (size_t)r + 3], o.rp, g);
+                const float4 r4 = ranked[kRec * (size_t)r + 4];
                 sm.a[slot] = a;
                 sm.b[slot] = make_float2(bb.x, bb.y);
                 sm.c[slot] = make_float4(bb.z, bb.w, c.x, a.z * kUnscaleDiag);
@@ -325,7 +326,7 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
                     mo[q] = make_uint4(block_mask(cm, rm, c0a, r0a), block_mask(cm, rm, c0a, r0a + 4),
                                        block_mask(cm, rm, c0b, r0b), block_mask(cm, rm, c0b, r0b + 4));
                 }
-                sm.e[slot] = offsets[r] + o.entry_shift + entry_index(g, tx, ty, o.rp, o.W, o.H);
+                sm.e[slot] = offsets[r] + o.entry_shift + entry_index(g, r4, tx, ty, o.rp, o.W, o.H);
             }
         }
         __syncthreads();
