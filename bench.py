@@ -39,8 +39,11 @@ WORKLOAD = ("hier1080: 300k Gaussians in 6 layers of 50k, SH degree 3, 64 motion
             "30 frames x levels L1..L6 = 180 renders of 1920x1080 per step")
 FP32_LANES_PER_SM = 128
 N_SMS = 148
-BLEND_FLOPS_PER_PAIR = 26  # FP32 ops of one compositing step (Eq. 2), see the design doc
-BLEND_BWD_FLOPS_PER_PAIR = 48  # FP32 ops of one reverse compositing step incl. its share of the reduction
+# FP32 FLOPs (FMA = 2) of the compositing rule (Eq. 2): evaluating one (pixel, entry) pair up to
+# the 1/255 test, and the extra work of a pair that is blended (forward / reverse step)
+EVAL_FLOPS_PER_PAIR = 14
+FWD_BLEND_FLOPS_PER_PAIR = 10
+BWD_BLEND_FLOPS_PER_PAIR = 51
 SORT_BYTES_PER_KEY_PASS = 20  # histogram read 4 B + scatter read 8 B + write 8 B
 
 
@@ -112,42 +115,45 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if current."""
+def load_traffic(kernel: str, renders_per_launch: int):
+    """DRAM bytes of one launch of `kernel` covering `renders_per_launch` renders, from the
+    committed ncu summary (profiles/traffic.json, bytes per render of a small capture
+    scaled by renders), or None when the kernels changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    e = d.get(kernel)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if d.get("source_hash") != kernel_source_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    e = d.get("kernels", {}).get(kernel)
+    if not e:
+        return None
+    return int(e["dram_bytes_per_render"] * renders_per_launch)
 
 
 # --------------------------------------------------------------------------- GPU arm
 
-def roofline_for(stage, per_launch_ms, work, peaks, peak_kind, batched=False):
+def roofline_for(stage, per_launch_ms, work, peaks, peak_kind, batched=False, renders_per_launch=1):
     """Roofline object of the dominant stage.  `work`: algorithmic FLOPs (ALU stages)
     or bytes (HBM stages) of one launch."""
     pre = "k_batch_" if batched else "k_"
-    alu = {"blend": (pre + "blend_fwd", BLEND_FLOPS_PER_PAIR),
-           "blend_bwd": (pre + "blend_bwd", BLEND_BWD_FLOPS_PER_PAIR)}
+    alu = {"blend": pre + "blend_fwd", "blend_bwd": pre + "blend_bwd"}
     hbm = {"tile_sort": "k_radix_scatter", "emit": pre + "emit", "reduce": pre + "reduce",
            "depth_sort": "k_radix_scatter"}
     if stage in alu:
         peak = N_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
         achieved = work / (per_launch_ms / 1e3) / 1e12
-        kern = alu[stage][0]
+        kern = alu[stage]
         return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": load_traffic(kern), "kernel": kern,
+                "frac": round(achieved / peak, 4), "traffic": load_traffic(kern, renders_per_launch), "kernel": kern,
                 "launch_ms": round(per_launch_ms, 4),
                 "peak_source": f"derived, not measured: {N_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
                                f"x {peaks.get('sm_max_mhz', 2032.0)} MHz max SM clock ({peak_kind} file)"}
     if stage in hbm:
         achieved = work / (per_launch_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": load_traffic(hbm[stage]),
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": load_traffic(hbm[stage], renders_per_launch),
                 "kernel": hbm[stage], "launch_ms": round(per_launch_ms, 4),
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     return None
@@ -260,15 +266,6 @@ def run_gpu(args):
         single_fwd()
         single_fwd_bwd()
     r.check()
-    # algorithmic work of one step (deterministic, outside the timed regions)
-    walked_pairs = bwd_pairs = keys_total = 0
-    for q, (cam, f, mask) in enumerate(reqs):
-        r.forward(gs, frames[f], mask, cam, out=outs[q])
-        _, _, walked, contrib = r.pixel_state(with_walked=True)
-        walked_pairs += int(walked.sum(dtype=torch.int64).item())
-        bwd_pairs += int(contrib.sum(dtype=torch.int64).item())
-        keys_total += r.stats()["n_keys"]
-    keys_mean = keys_total / n_req
     s_steps = max(1, min(args.steps, 3))
     sf_ms, sf_prof, _ = timer(single_fwd, s_steps, profile=True, name="single_fwd")
     sfb_ms, sfb_prof, _ = timer(single_fwd_bwd, s_steps, profile=True, name="single_fwd_bwd")
@@ -284,6 +281,16 @@ def run_gpu(args):
     tune = r.tune_batch(gs, frames, reqs, dL_dimages=dls, depths=(30, 60, 90, n_req), iters=2, outs=outs)
     best = tune["best"]
     depth, tile = best["depth"], tuple(best["tile"])
+    # algorithmic work of one step at the tuned tile shape (deterministic, outside the timed regions)
+    walked_pairs = blended_pairs = bwd_pairs = keys_total = 0
+    for q, (cam, f, mask) in enumerate(reqs):
+        r.forward(gs, frames[f], mask, cam, out=outs[q])
+        _, blended, walked, contrib = r.pixel_state(with_walked=True)
+        walked_pairs += int(walked.sum(dtype=torch.int64).item())
+        blended_pairs += int(blended.sum(dtype=torch.int64).item())
+        bwd_pairs += int(contrib.sum(dtype=torch.int64).item())
+        keys_total += r.stats()["n_keys"]
+    keys_mean = keys_total / n_req
     grads = r.batch_grads(gs, frames)
     g_fwd = gc.BatchGraph(r, gs, frames, reqs, depth, outs=outs)
     g_fb = gc.BatchGraph(r, gs, frames, reqs, depth, dL_dimages=dls, grads=grads, outs=outs)
@@ -331,11 +338,14 @@ def run_gpu(args):
         launches = max(1, st_calls[dom])
         per_launch = st_ms[dom] / launches
         steps = e_steps
-        work = {"blend": walked_pairs * steps / launches * BLEND_FLOPS_PER_PAIR,
-                "blend_bwd": bwd_pairs * steps / launches * BLEND_BWD_FLOPS_PER_PAIR,
+        fwd_flops = EVAL_FLOPS_PER_PAIR * walked_pairs + FWD_BLEND_FLOPS_PER_PAIR * blended_pairs
+        bwd_flops = EVAL_FLOPS_PER_PAIR * bwd_pairs + BWD_BLEND_FLOPS_PER_PAIR * blended_pairs
+        work = {"blend": fwd_flops * steps / launches,
+                "blend_bwd": bwd_flops * steps / launches,
                 "tile_sort": 2 * SORT_BYTES_PER_KEY_PASS * keys_total * steps / launches,
                 "emit": 8 * keys_total * steps / launches}.get(dom, 0.0)
-        return roofline_for(dom, per_launch, work, peaks, peak_kind, batched=True)
+        return roofline_for(dom, per_launch, work, peaks, peak_kind, batched=True,
+                            renders_per_launch=n_req * e_steps // launches)
 
     # ---- reduced-precision storage (BF16 geometry, FP8-E4M3 SH), same batched graph
     gq = gc.BatchGraph(r, gsq, frames, reqs, depth, dL_dimages=dls, grads=r.batch_grads(gsq, frames), outs=outs)
@@ -381,8 +391,11 @@ def run_gpu(args):
                                   "psnr_vs_fp32_scene_db": q_psnr, "clocks": clk_q,
                                   "bytes_per_gaussian": {"fp32": 4 * 59 + 4, "bf16_fp8": 2 * 11 + 48 + 4}},
             "autotune": tune,
-            "work_per_step": {"blend_walked_pairs": walked_pairs, "blend_bwd_pairs": bwd_pairs,
-                              "keys_per_render": round(keys_mean)}}
+            "work_per_step": {"blend_walked_pairs": walked_pairs, "blended_pairs": blended_pairs,
+                              "blend_bwd_walked_pairs": bwd_pairs, "keys_per_render": round(keys_mean),
+                              "flops_per_pair": {"evaluate": EVAL_FLOPS_PER_PAIR,
+                                                 "blend_fwd": FWD_BLEND_FLOPS_PER_PAIR,
+                                                 "blend_bwd": BWD_BLEND_FLOPS_PER_PAIR}}}
     del outs, ref_imgs, q_imgs, grads, dls
     torch.cuda.empty_cache()
 

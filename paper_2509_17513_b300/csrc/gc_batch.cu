@@ -25,7 +25,7 @@
 
 namespace gc {
 
-struct BatchReq {
+struct __align__(16) BatchReq {
     CamParams cam;
     RenderParams rp;
     Selection sel;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) k_batch_activate(GaussSrc G, int64_t n, f
     if (i < n) act[i] = gaussian_activation(G, i);
 }
 
-__global__ void __launch_bounds__(256, 5) k_batch_preprocess(GaussSrc G, const BatchReq *__restrict__ reqs,
+__global__ void __launch_bounds__(256, 4) k_batch_preprocess(GaussSrc G, const BatchReq *__restrict__ reqs,
                                                           const int64_t *__restrict__ item_base, int n_req,
                                                           int64_t n_items, float4 *__restrict__ rec,
                                                           uint32_t *__restrict__ keys,
@@ -83,10 +83,19 @@ __global__ void __launch_bounds__(256, 5) k_batch_preprocess(GaussSrc G, const B
                                                           uint32_t *__restrict__ touched,
                                                           int32_t *__restrict__ diff,
                                                           const float4 *__restrict__ act) {
+    // a block's 256 items belong to one request (requests are padded to the radix tile):
+    // its table entry is staged in shared memory once
+    __shared__ __align__(16) BatchReq R;
+    {
+        const int64_t first = (int64_t)blockIdx.x * blockDim.x;
+        const int q = find_req(item_base, n_req, first);
+        const int4 *src = reinterpret_cast<const int4 *>(&reqs[q]);
+        int4 *dst = reinterpret_cast<int4 *>(&R);
+        for (int k = threadIdx.x; k < (int)(sizeof(BatchReq) / 16); k += blockDim.x) dst[k] = src[k];
+        __syncthreads();
+    }
     const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= n_items) return;
-    const int q = find_req(item_base, n_req, item);
-    const BatchReq &R = reqs[q];
     const int64_t j = item - R.item_base;
     vals[item] = (uint32_t)item;
     Proj P;

@@ -256,13 +256,45 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
         for (int k = 0; k < 16; ++k) Y[k] = 0.f;
         sh_basis(G.sh_degree, dxv * inv, dyv * inv, dzv * inv, Y);
         float rgb[3];
+        if (G.K == 16) {  // degree 3: the 48 coefficients as 16-byte loads, used as they arrive
+            float acc[3] = {0.f, 0.f, 0.f};
+            if (G.precision == GC_PREC_FP32) {
+                const float4 *p = reinterpret_cast<const float4 *>(G.sh + i * 48);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float acc = 0.f;
+                for (int q = 0; q < 12; ++q) {
+                    const float4 x = p[q];
+                    const float v4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if (k < G.K) acc = fmaf(Y[k], load_sh(G, i, k, c), acc);
-            rgb[c] = fmaxf(acc + 0.5f, 0.f);
+                    for (int t = 0; t < 4; ++t) {
+                        const int idx = 4 * q + t;  // coefficient k = idx / 3, channel idx % 3
+                        acc[idx % 3] = fmaf(Y[idx / 3], v4[t], acc[idx % 3]);
+                    }
+                }
+            } else {
+                const uint4 *p = reinterpret_cast<const uint4 *>(G.sh_q + i * 48);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const uint4 x = p[q];
+                    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                    for (int b = 0; b < 16; ++b) {
+                        const int idx = 16 * q + b;
+                        const float v = fmul(e4m3_to_f32((uint8_t)(w[b >> 2] >> (8 * (b & 3)))), G.scales[11 + idx]);
+                        acc[idx % 3] = fmaf(Y[idx / 3], v, acc[idx % 3]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) rgb[c] = fmaxf(acc[c] + 0.5f, 0.f);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k < G.K) acc = fmaf(Y[k], load_sh(G, i, k, c), acc);
+                rgb[c] = fmaxf(acc + 0.5f, 0.f);
+            }
         }
         const float op = 1.0f / (1.0f + expf(-A.logit));
         // conic stored pre-scaled for the blend's base-2 exponent (see gc_blend.cuh)
