@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
             val[r] = valid ? sv[stage][li] : 0u;
             const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
             const uint32_t d = (key[r] >> shift) & mask;
-            const uint32_t peers = digit_peers(d, bits, vmask);
+            // narrow digits: one match instruction; 8-bit digits: ballots per digit bit
+            const uint32_t peers = bits < 8 ? __match_any_sync(0xffffffffu, d) & vmask : digit_peers(d, bits, vmask);
             const uint32_t before = valid ? wcnt[warp][d] : 0u;
             __syncwarp();
             if (valid && (peers & lt) == 0) wcnt[warp][d] = before + (uint32_t)__popc(peers);
