@@ -214,6 +214,30 @@ GC_API gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved, cons
                              const gc_motion *motion, const float *dL_dimage, gc_grads *out,
                              void *stream);
 
+/*
+ * Multi-level render: all quality levels l = 1..levels of one view (level l = layers
+ * 1..l, the paper's progressive render, Eq. 4) in one pass.  The layers are nested, so
+ * the tile lists of the top level hold everything; every pixel keeps one transmittance
+ * and colour per level and an entry of layer m is blended into the levels >= m.
+ * level_images: host array of `levels` device pointers (3 x height x width each);
+ * image l - 1 equals gc_render_forward with layer mask 1..l bit for bit.  levels <=
+ * min(8, n_layers).  The paper's rate-distortion step renders every level per iteration
+ * (Sec. 3.3); this replaces those renders by one.  `saved` then holds a multi-level
+ * state for gc_render_levels_backward.
+ */
+GC_API gc_status gc_render_levels_forward(gc_context *ctx, const gc_gaussians *g, const gc_motion *motion,
+                                          int32_t levels, const gc_camera *cam, float *const *level_images,
+                                          gc_saved *saved, void *stream);
+
+/*
+ * Backward of a multi-level forward: dL_dimages is a host array of `levels` device
+ * pointers (3 x height x width); the gradients of L = sum_l <dL_dimages[l], image_l>
+ * (one pass; the per-level reverse steps share each entry's evaluation and reduction).
+ */
+GC_API gc_status gc_render_levels_backward(gc_context *ctx, const gc_saved *saved, const gc_gaussians *g,
+                                           const gc_motion *motion, const float *const *dL_dimages,
+                                           gc_grads *out, void *stream);
+
 /* One render of a batch (host struct). */
 typedef struct {
     gc_camera camera;     /* its own pose, intrinsics and resolution */

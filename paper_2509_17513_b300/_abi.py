@@ -90,6 +90,8 @@ SIGNATURES = {
     "gc_render_forward": (C.c_int, [P, P, P, C.c_uint32, P, P, P, P]),
     "gc_render_backward": (C.c_int, [P, P, P, P, P, P, P]),
     "gc_render_forward_noalloc": (C.c_int, [P, P, P, C.c_uint32, P, P, P, C.c_char_p, C.c_size_t]),
+    "gc_render_levels_forward": (C.c_int, [P, P, P, C.c_int32, P, P, P, P]),
+    "gc_render_levels_backward": (C.c_int, [P, P, P, P, P, P, P]),
     "gc_render_batch_forward": (C.c_int, [P, P, P, C.c_int32, P, C.c_int32, P, P]),
     "gc_render_batch_backward": (C.c_int, [P, P, P, P, C.c_int32, P, C.c_int32, P, P]),
     "gc_batch_graph_create": (C.c_int, [P, P, P, C.c_int32, P, C.c_int32, C.c_int32, P, P, P, P]),

@@ -127,11 +127,15 @@ gc_status gc_saved_destroy(gc_context *ctx, gc_saved *saved) {
 
 const char *gc_last_error(gc_context *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
-gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_motion *motion,
-                            uint32_t layer_mask, const gc_camera *cam, float *image,
-                            gc_saved *saved, void *stream) {
+}  // extern "C"
+
+// One view: layer_mask selects the layers (levels = 0) or, for levels L > 0, the layers
+// 1..L rendered as L images at once (level_images[0..L-1]).
+static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, const gc_motion *motion,
+                                     uint32_t layer_mask, const gc_camera *cam, float *image, gc_saved *saved,
+                                     void *stream, int levels, float *const *level_images) {
     if (!ctx) return GC_ERR_INVALID_ARG;
-    if (!cam || !image) return fail(ctx, GC_ERR_INVALID_ARG, "camera or image is NULL");
+    if (!cam || (!image && !levels)) return fail(ctx, GC_ERR_INVALID_ARG, "camera or image is NULL");
     if (cam->width <= 0 || cam->height <= 0 || cam->width > 32768 || cam->height > 32768)
         return fail(ctx, GC_ERR_INVALID_ARG, "image size %dx%d out of range (1..32768)", cam->width, cam->height);
     if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(ctx, GC_ERR_INVALID_ARG, "fx, fy must be > 0");
@@ -143,6 +147,14 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
     gc_saved &S = saved ? *saved : ctx->internal;
     S.valid = false;
     if (S.batch) batch_invalidate(S);
+    if (levels) {
+        if (levels < 1 || levels > gc::kMaxLevels || levels > g->n_layers)
+            return fail(ctx, GC_ERR_INVALID_ARG, "levels must be 1..min(8, n_layers)");
+        for (int l = 0; l < levels; ++l)
+            if (!level_images[l]) return fail(ctx, GC_ERR_INVALID_ARG, "level image %d is NULL", l);
+        layer_mask = (1u << levels) - 1u;
+    }
+    S.levels = levels;
 
     const gc_options &o = ctx->opt;
     int64_t n_sel = 0;
@@ -262,13 +274,39 @@ gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_mot
     S.K = K;
     uint32_t *sorted_vals = (n_sel > 0 && K > 0) ? S.tvals[S.tile_buf].as<uint32_t>() : nullptr;
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_BLEND));
-    GC_CUDA(ctx, gc::launch_blend_fwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(), cp, rp,
-                                      image, S.final_T.as<float>(), S.n_contrib.as<uint32_t>(),
-                                      S.n_blended.as<uint32_t>(), S.n_walked.as<uint32_t>(), s));
+    if (levels) {
+        GC_CUDA(ctx, grow(S.lv_T, (size_t)levels * hw * 4));
+        GC_CUDA(ctx, grow(S.lv_last, (size_t)levels * hw * 4));
+        gc::LevelPtrs lp{};
+        for (int l = 0; l < levels; ++l) lp.img[l] = level_images[l];
+        GC_CUDA(ctx, gc::launch_blend_levels_fwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(), cp, rp,
+                                                 levels, lp, S.lv_T.as<float>(), S.lv_last.as<uint32_t>(), s));
+    } else {
+        GC_CUDA(ctx, gc::launch_blend_fwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(), cp, rp,
+                                          image, S.final_T.as<float>(), S.n_contrib.as<uint32_t>(),
+                                          S.n_blended.as<uint32_t>(), S.n_walked.as<uint32_t>(), s));
+    }
     GC_CUDA(ctx, prof_mark(ctx, s, -1));
     S.valid = true;
     ctx->last = &S;
     return GC_OK;
+}
+
+extern "C" {
+
+gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const gc_motion *motion,
+                            uint32_t layer_mask, const gc_camera *cam, float *image,
+                            gc_saved *saved, void *stream) {
+    return render_forward_impl(ctx, g, motion, layer_mask, cam, image, saved, stream, 0, nullptr);
+}
+
+gc_status gc_render_levels_forward(gc_context *ctx, const gc_gaussians *g, const gc_motion *motion,
+                                   int32_t levels, const gc_camera *cam, float *const *level_images,
+                                   gc_saved *saved, void *stream) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    if (!level_images) return fail(ctx, GC_ERR_INVALID_ARG, "level_images is NULL");
+    if (levels < 1) return fail(ctx, GC_ERR_INVALID_ARG, "levels must be >= 1");
+    return render_forward_impl(ctx, g, motion, 0u, cam, nullptr, saved, stream, levels, level_images);
 }
 
 gc_status gc_saved_stats(gc_context *ctx, const gc_saved *saved, gc_stats *out, void *stream) {
@@ -330,6 +368,7 @@ gc_status gc_saved_pixel_state(gc_context *ctx, const gc_saved *saved, float *fi
     if (!ctx) return GC_ERR_INVALID_ARG;
     const gc_saved &S = saved ? *saved : ctx->internal;
     if (!S.valid) return fail(ctx, GC_ERR_STATE, "no forward recorded");
+    if (S.levels) return fail(ctx, GC_ERR_STATE, "per-pixel state of a multi-level forward is not kept here");
     DeviceGuard dg(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     size_t hw = (size_t)S.cam.width * S.cam.height;
@@ -397,13 +436,19 @@ gc_status gc_check(gc_context *ctx, void *stream) {
 
 }  // extern "C"
 
-extern "C" gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved,
-                                        const gc_gaussians *g, const gc_motion *motion,
-                                        const float *dL_dimage, gc_grads *out, void *stream) {
+static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, const gc_gaussians *g,
+                                      const gc_motion *motion, const float *dL_dimage,
+                                      const float *const *dL_levels, gc_grads *out, void *stream) {
     if (!ctx) return GC_ERR_INVALID_ARG;
-    if (!dL_dimage || !out) return fail(ctx, GC_ERR_INVALID_ARG, "dL_dimage or grads is NULL");
+    if ((!dL_dimage && !dL_levels) || !out) return fail(ctx, GC_ERR_INVALID_ARG, "dL_dimage or grads is NULL");
     const gc_saved &S = saved ? *saved : ctx->internal;
     if (!S.valid) return fail(ctx, GC_ERR_STATE, "no forward recorded in this saved state");
+    if ((S.levels > 0) != (dL_levels != nullptr))
+        return fail(ctx, GC_ERR_STATE, S.levels ? "the saved forward is multi-level: use gc_render_levels_backward"
+                                                : "the saved forward is single-level: use gc_render_backward");
+    if (dL_levels)
+        for (int l = 0; l < S.levels; ++l)
+            if (!dL_levels[l]) return fail(ctx, GC_ERR_INVALID_ARG, "dL_dimages[%d] is NULL", l);
     gc::GaussSrc src;
     gc_status st = make_source(ctx, g, motion, src);
     if (st != GC_OK) return st;
@@ -446,9 +491,17 @@ extern "C" gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved,
 
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_BLEND_BWD));
     ctx->bwd_part_clean = false;
-    GC_CUDA(ctx, gc::launch_blend_bwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(),
-                                      S.offsets.as<uint32_t>(), S.cam, S.rp, S.final_T.as<float>(),
-                                      S.n_contrib.as<uint32_t>(), dL_dimage, ctx->bwd_part.as<float>(), s));
+    if (dL_levels) {
+        gc::LevelGrads lg{};
+        for (int l = 0; l < S.levels; ++l) lg.g[l] = dL_levels[l];
+        GC_CUDA(ctx, gc::launch_blend_levels_bwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(),
+                                                 S.offsets.as<uint32_t>(), S.cam, S.rp, S.levels, S.lv_T.as<float>(),
+                                                 S.lv_last.as<uint32_t>(), lg, ctx->bwd_part.as<float>(), s));
+    } else {
+        GC_CUDA(ctx, gc::launch_blend_bwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(),
+                                          S.offsets.as<uint32_t>(), S.cam, S.rp, S.final_T.as<float>(),
+                                          S.n_contrib.as<uint32_t>(), dL_dimage, ctx->bwd_part.as<float>(), s));
+    }
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_REDUCE));
     GC_CUDA(ctx, gc::launch_reduce_entries(ctx->bwd_part.as<float>(), S.offsets.as<uint32_t>(),
                                            S.touched_r.as<uint32_t>(), S.dvals[S.depth_buf].as<uint32_t>(),
@@ -466,4 +519,20 @@ extern "C" gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved,
     }
     GC_CUDA(ctx, prof_mark(ctx, s, -1));
     return GC_OK;
+}
+
+extern "C" gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved, const gc_gaussians *g,
+                                        const gc_motion *motion, const float *dL_dimage, gc_grads *out,
+                                        void *stream) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    if (!dL_dimage) return fail(ctx, GC_ERR_INVALID_ARG, "dL_dimage or grads is NULL");
+    return render_backward_impl(ctx, saved, g, motion, dL_dimage, nullptr, out, stream);
+}
+
+extern "C" gc_status gc_render_levels_backward(gc_context *ctx, const gc_saved *saved, const gc_gaussians *g,
+                                               const gc_motion *motion, const float *const *dL_dimages,
+                                               gc_grads *out, void *stream) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    if (!dL_dimages) return fail(ctx, GC_ERR_INVALID_ARG, "dL_dimages is NULL");
+    return render_backward_impl(ctx, saved, g, motion, nullptr, dL_dimages, out, stream);
 }

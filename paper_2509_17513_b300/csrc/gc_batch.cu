@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(256, 4) k_batch_preprocess(GaussSrc G, const B
     }
     rec[kRec * item] = P.r0;
     rec[kRec * item + 1] = P.r1;
+    if (j < R.n_sel) P.r2.y = __int_as_float(layer_of(R.sel, sel_global(R.sel, j)));
     rec[kRec * item + 2] = P.r2;
     const uint32_t nt = bin_rows(P, R.rp, R.cam.width, R.cam.height, diff + R.diff_base, R.rp.ntx + 1);
     rec[kRec * item + 3] = P.r3;

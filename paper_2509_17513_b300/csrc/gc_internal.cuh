@@ -6,7 +6,8 @@
 //   r0 = { u, v, A, B }                  conic = inverse 2D covariance [[a, b], [b, c]],
 //   r1 = { C, opacity, red, green }      stored pre-scaled: A = -a log2e/2, B = -b log2e,
 //                                        C = -c log2e/2 (gc_blend.cuh)
-//   r2 = { blue, depth, rect_x, rect_y } rect_* = pixel footprint, int bits: lo16 = first,
+//   r2 = { blue, layer, rect_x, rect_y } layer = the Gaussian's layer (int bits);
+//                                        rect_* = pixel footprint, int bits: lo16 = first,
 //                                        hi16 = last (inclusive)
 //   r3 = { a, b, c, tc }                 the conic as computed by the binning spec and the
 //                                        alpha-ellipse level (row intervals, step 15)
@@ -27,6 +28,15 @@ namespace gc {
 constexpr int kMaxLayers = 32;
 constexpr uint32_t kCulledKey = 0xFFFFFFFFu;
 constexpr int kRec = 5;  // float4s per projected record
+constexpr int kMaxLevels = 8;  // levels of one multi-level render
+
+// Output images (3 x H x W each) and dL/dimage of the levels of a multi-level render.
+struct LevelPtrs {
+    float *img[kMaxLevels];
+};
+struct LevelGrads {
+    const float *g[kMaxLevels];
+};
 
 // Selected layer ranges: compact index j maps to global index
 // range_begin[k] + (j - range_start[k]) for the range k holding j.
@@ -34,7 +44,16 @@ struct Selection {
     int n_ranges;
     int64_t range_begin[kMaxLayers];
     int64_t range_start[kMaxLayers + 1];  // prefix sums of range lengths
+    int n_layers;
+    int64_t layer_off[kMaxLayers + 1];    // the set's layer offsets (layer l = [off[l], off[l+1]))
 };
+
+// Layer (0-based) of global Gaussian i.
+__host__ __device__ inline int layer_of(const Selection &s, int64_t i) {
+    int l = 0;
+    while (l + 1 < s.n_layers && i >= s.layer_off[l + 1]) ++l;
+    return l;
+}
 
 struct CamParams {
     int width, height;
@@ -139,6 +158,17 @@ cudaError_t launch_blend_fwd(const uint2 *ranges, const uint32_t *sorted_vals,
                              const float4 *ranked, const CamParams &cam, const RenderParams &rp,
                              float *image, float *final_T, uint32_t *n_contrib,
                              uint32_t *n_blended, uint32_t *n_walked, cudaStream_t st);
+
+// Multi-level blends (levels 1..L of one view from one list): per-level images, final
+// transmittances lv_T[l * H * W + p] and list positions lv_last; the reverse pass writes
+// the partials of every entry summed over the levels (layout of launch_blend_bwd).
+cudaError_t launch_blend_levels_fwd(const uint2 *ranges, const uint32_t *sorted_vals, const float4 *ranked,
+                                    const CamParams &cam, const RenderParams &rp, int L, const LevelPtrs &out,
+                                    float *lv_T, uint32_t *lv_last, cudaStream_t st);
+cudaError_t launch_blend_levels_bwd(const uint2 *ranges, const uint32_t *sorted_vals, const float4 *ranked,
+                                    const uint32_t *offsets, const CamParams &cam, const RenderParams &rp, int L,
+                                    const float *lv_T, const uint32_t *lv_last, const LevelGrads &dimg,
+                                    float *part, cudaStream_t st);
 
 // sorted list entry (rank) -> global Gaussian index, int64
 cudaError_t launch_entries_to_global(const uint32_t *sorted_vals, const uint32_t *perm,

@@ -1,0 +1,346 @@
+// gc_levels.cu - single-pass multi-level render: every quality level l = 1..L of one view
+// (level l = layers 1..l, Eq. 4) from one sorted list.
+//
+// The layers are nested prefixes of the significance-sorted set (Sec. 3.1), so the tile
+// lists of level L hold every Gaussian that any level needs, in the same (depth, index)
+// order.  Each pixel keeps one transmittance and colour per level; an entry of layer m
+// is evaluated once (its alpha is the same for every level) and blended into every
+// level l >= m that has not stopped.  The image of level l is therefore exactly the
+// single-level render of mask 1..l.  The paper's rate-distortion step renders every
+// level per iteration (Sec. 3.3); this replaces L renders by one pass.
+//
+// The reverse pass keeps the per-level state too: per entry, each level that blended it
+// is undone in turn, the colour and opacity partials summed over the levels, and the
+// power derivative dL/dpower summed over the levels before it is turned into the mean
+// and conic partials (they are linear in it).  One warp reduction per entry serves all
+// levels.
+#include <cuda_runtime.h>
+
+#include "gc_tile.cuh"
+
+namespace gc {
+
+namespace {
+
+// Forward: one CTA of 256 threads per tile, one pixel per thread (the forward layout).
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) k_blend_levels_fwd(
+    const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
+    const float4 *__restrict__ ranked, int W, int H, int ntx, float bg0, float bg1, float bg2, int membership,
+    int L, LevelPtrs out, float *__restrict__ lv_T, uint32_t *__restrict__ lv_last) {
+    __shared__ __align__(16) FwdSmem sm;
+    __shared__ uint8_t lay[256];
+    const int tile = blockIdx.x, tx = tile % ntx, ty = tile / ntx;
+    const uint2 range = ranges[tile];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int lx, ly;
+    pixel_of_thread<TW, TH>((int)threadIdx.x, lx, ly);
+    const int px = tx * TW + lx, py = ty * TH + ly;
+    const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
+    const int n = (int)(range.y - range.x);
+    const bool inside = px < W && py < H;
+    uint32_t lv = inside ? ((1u << L) - 1u) : 0u;  // levels still blending
+    uint32_t act = lv ? (1u << lane) : 0u;
+    float T[kMaxLevels], C0[kMaxLevels], C1[kMaxLevels], C2[kMaxLevels];
+    uint32_t last[kMaxLevels];
+#pragma unroll
+    for (int l = 0; l < kMaxLevels; ++l) {
+        T[l] = 1.f;
+        C0[l] = C1[l] = C2[l] = 0.f;
+        last[l] = 0u;
+    }
+    for (int b = 0; b < n; b += 256) {
+        if (__syncthreads_count(act != 0u) == 0) break;
+        {
+            const int idx = b + (int)threadIdx.x;
+            if (idx < n) {
+                const uint32_t r = sorted_vals[range.x + idx];
+                const float4 a = ranked[kRec * (size_t)r];
+                const float4 bb = ranked[kRec * (size_t)r + 1];
+                const float4 c = ranked[kRec * (size_t)r + 2];
+                uint32_t cm, rm;
+                rect_masks<TW, TH>(c, tx, ty, membership, cm, rm);
+                sm.a[threadIdx.x] = a;
+                sm.b[threadIdx.x] = make_float2(bb.x, bb.y);
+                sm.c[threadIdx.x] = make_float4(bb.z, bb.w, c.x, 0.f);
+                store_masks<TW>(&sm.m[8 * threadIdx.x], cm, rm);
+                lay[threadIdx.x] = (uint8_t)min(__float_as_int(c.y), 31);
+            }
+        }
+        __syncthreads();
+        const int cnt = min(256, n - b);
+        for (int k0 = 0; k0 < cnt; k0 += 16) {
+            if (__ballot_sync(0xffffffffu, act != 0u) == 0u) break;
+            const int k1 = min(k0 + 16, cnt);
+            for (int k = k0; k < k1; ++k) {
+                const uint32_t wm = sm.m[8 * k + warp];
+                if ((wm & act) == 0u) continue;
+                const uint32_t lm = lv & (0xffffffffu << lay[k]);  // active levels >= the entry's layer
+                if (!lm) continue;
+                const float4 a = sm.a[k];
+                const float2 bb = sm.b[k];
+                const float dx = pcx - a.x, dy = pcy - a.y;
+                const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
+                if (p2 > 0.f) continue;
+                float G;
+                const float alpha = fminf(kAlphaMax, blend_raw_alpha(bb.y, p2, G));
+                if (alpha < kAlphaMin) continue;
+                const float4 col = sm.c[k];
+#pragma unroll
+                for (int l = 0; l < kMaxLevels; ++l) {
+                    if (!((lm >> l) & 1u)) continue;
+                    const float Tn = T[l] * (1.f - alpha);
+                    if (Tn < kTStop) {
+                        lv &= ~(1u << l);
+                        continue;
+                    }
+                    const float w = alpha * T[l];
+                    C0[l] = fmaf(col.x, w, C0[l]);
+                    C1[l] = fmaf(col.y, w, C1[l]);
+                    C2[l] = fmaf(col.z, w, C2[l]);
+                    T[l] = Tn;
+                    last[l] = (uint32_t)(b + k + 1);
+                }
+                if (!lv) act = 0u;
+            }
+        }
+    }
+    if (inside) {
+        const size_t hw = (size_t)W * H;
+        const size_t p = (size_t)py * W + px;
+#pragma unroll
+        for (int l = 0; l < kMaxLevels; ++l) {
+            if (l >= L) break;
+            float *img = out.img[l];
+            img[p] = fmaf(T[l], bg0, C0[l]);
+            img[hw + p] = fmaf(T[l], bg1, C1[l]);
+            img[2 * hw + p] = fmaf(T[l], bg2, C2[l]);
+            lv_T[l * hw + p] = T[l];
+            lv_last[l * hw + p] = last[l];
+        }
+    }
+}
+
+// Reverse: one CTA of 256 threads per tile, one pixel per thread.
+template <int TW, int TH>
+__global__ void __launch_bounds__(256) k_blend_levels_bwd(
+    const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
+    const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, RenderParams rp,
+    int L, const float *__restrict__ lv_T, const uint32_t *__restrict__ lv_last, LevelGrads dimg,
+    float *__restrict__ part) {
+    struct Smem {
+        float4 a[256];
+        float2 b[256];
+        float4 c[256];
+        float2 d[256];
+        uint32_t m[256 * 8];
+        uint32_t e[256];
+        uint8_t lay[256];
+        float wpart[32][8][9];
+        uint32_t last_max;
+    };
+    __shared__ __align__(16) Smem sm;
+    const int tile = blockIdx.x, ntx = rp.ntx, tx = tile % ntx, ty = tile / ntx;
+    const uint2 range = ranges[tile];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int lx, ly;
+    pixel_of_thread<TW, TH>((int)threadIdx.x, lx, ly);
+    const int px = tx * TW + lx, py = ty * TH + ly;
+    const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
+    const uint32_t bit = 1u << lane;
+    float T[kMaxLevels], A0[kMaxLevels], A1[kMaxLevels], A2[kMaxLevels], g0[kMaxLevels], g1[kMaxLevels],
+        g2[kMaxLevels];
+    uint32_t last[kMaxLevels];
+    uint32_t my_last = 0u;
+    const size_t hw = (size_t)W * H;
+    const bool inside = px < W && py < H;
+    const size_t p = inside ? (size_t)py * W + px : 0;
+#pragma unroll
+    for (int l = 0; l < kMaxLevels; ++l) {
+        T[l] = 1.f;
+        A0[l] = rp.bg[0];
+        A1[l] = rp.bg[1];
+        A2[l] = rp.bg[2];
+        g0[l] = g1[l] = g2[l] = 0.f;
+        last[l] = 0u;
+        if (inside && l < L) {
+            T[l] = lv_T[l * hw + p];
+            last[l] = lv_last[l * hw + p];
+            const float *gl = dimg.g[l];
+            g0[l] = gl[p];
+            g1[l] = gl[hw + p];
+            g2[l] = gl[2 * hw + p];
+            my_last = max(my_last, last[l]);
+        }
+    }
+    if (threadIdx.x == 0) sm.last_max = 0u;
+    __syncthreads();
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, my_last);
+    if (lane == 0) atomicMax(&sm.last_max, wmax);
+    __syncthreads();
+    const int n_active = (int)sm.last_max;
+    for (int hi = n_active; hi > 0; hi -= 256) {
+        const int lo = max(hi - 256, 0);
+        __syncthreads();
+        {
+            const int k = lo + (int)threadIdx.x;
+            if (k < hi) {
+                const uint32_t r = sorted_vals[range.x + k];
+                const float4 a = ranked[kRec * (size_t)r];
+                const float4 bb = ranked[kRec * (size_t)r + 1];
+                const float4 c = ranked[kRec * (size_t)r + 2];
+                uint32_t cm, rm;
+                rect_masks<TW, TH>(c, tx, ty, rp.membership, cm, rm);
+                RowGeom g;
+                row_geom(a, c, ranked[kRec * (size_t)r + 3], rp, g);
+                const float4 r4 = ranked[kRec * (size_t)r + 4];
+                sm.a[threadIdx.x] = a;
+                sm.b[threadIdx.x] = make_float2(bb.x, bb.y);
+                sm.c[threadIdx.x] = make_float4(bb.z, bb.w, c.x, a.z * kUnscaleDiag);
+                sm.d[threadIdx.x] = make_float2(a.w * kUnscaleOff, bb.x * kUnscaleDiag);
+                store_masks<TW>(&sm.m[8 * threadIdx.x], cm, rm);
+                sm.e[threadIdx.x] = offsets[r] + entry_index(g, r4, tx, ty, rp, W, H);
+                sm.lay[threadIdx.x] = (uint8_t)min(__float_as_int(c.y), 31);
+            }
+        }
+        __syncthreads();
+        for (int gtop = hi; gtop > lo; gtop -= 32) {
+            const int gbot = max(gtop - 32, lo);
+            for (int k = gtop - 1; k >= gbot; --k) {
+                const int s = k - lo;
+                float v[9];
+#pragma unroll
+                for (int c = 0; c < 9; ++c) v[c] = 0.f;
+                bool contrib = false;
+                const uint32_t wm = sm.m[8 * s + warp];
+                uint32_t lm = 0u;  // levels of this pixel that blended entry k
+#pragma unroll
+                for (int l = 0; l < kMaxLevels; ++l)
+                    if (l < L && l >= (int)sm.lay[s] && (uint32_t)k < last[l]) lm |= 1u << l;
+                if ((wm & bit) != 0u && lm) {
+                    const float4 a = sm.a[s];
+                    const float2 bb = sm.b[s];
+                    const float dx = pcx - a.x, dy = pcy - a.y;
+                    const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
+                    float G = 0.f, a0 = 0.f, alpha = 0.f;
+                    bool blended = p2 <= 0.f;
+                    if (blended) {
+                        a0 = blend_raw_alpha(bb.y, p2, G);
+                        alpha = fminf(kAlphaMax, a0);
+                        blended = !(alpha < kAlphaMin);
+                    }
+                    if (blended) {
+                        contrib = true;
+                        const float4 col = sm.c[s];
+                        float dp = 0.f;
+#pragma unroll
+                        for (int l = 0; l < kMaxLevels; ++l) {
+                            if (!((lm >> l) & 1u)) continue;
+                            T[l] = __fdividef(T[l], 1.f - alpha);
+                            const float w = alpha * T[l];
+                            v[6] += w * g0[l];
+                            v[7] += w * g1[l];
+                            v[8] += w * g2[l];
+                            const float dal = T[l] * (g0[l] * (col.x - A0[l]) + g1[l] * (col.y - A1[l]) +
+                                                      g2[l] * (col.z - A2[l]));
+                            A0[l] = fmaf(alpha, col.x - A0[l], A0[l]);
+                            A1[l] = fmaf(alpha, col.y - A1[l], A1[l]);
+                            A2[l] = fmaf(alpha, col.z - A2[l], A2[l]);
+                            if (!(a0 > kAlphaMax)) {
+                                v[5] += G * dal;
+                                dp += alpha * dal;  // dL/dpower (natural exponent), summed over levels
+                            }
+                        }
+                        const float2 nd = sm.d[s];
+                        v[0] = (col.w * dx + nd.x * dy) * dp;
+                        v[1] = (nd.x * dx + nd.y * dy) * dp;
+                        v[2] = -0.5f * dx * dx * dp;
+                        v[3] = -dx * dy * dp;
+                        v[4] = -0.5f * dy * dy * dp;
+                    }
+                }
+                float out0 = 0.f, out8 = 0.f;
+                if (__any_sync(0xffffffffu, contrib)) {
+                    {
+                        const bool up = lane & 16;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float send = up ? v[i] : v[i + 4];
+                            const float keep = up ? v[i + 4] : v[i];
+                            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                        }
+                    }
+                    {
+                        const bool up = lane & 8;
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const float send = up ? v[i] : v[i + 2];
+                            const float keep = up ? v[i + 2] : v[i];
+                            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                        }
+                    }
+                    {
+                        const bool up = lane & 4;
+                        const float send = up ? v[0] : v[1];
+                        const float keep = up ? v[1] : v[0];
+                        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                    }
+                    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+                    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+                    out0 = v[0];
+                    float x = v[8];
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+                    out8 = x;
+                }
+                if ((lane & 3) == 0) sm.wpart[k - gbot][warp][lane >> 2] = out0;
+                if (lane == 1) sm.wpart[k - gbot][warp][8] = out8;
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < (gtop - gbot) * 9; idx += 256) {
+                const int q = idx / 9, c = idx - q * 9;
+                float acc = sm.wpart[q][0][c];
+#pragma unroll
+                for (int w2 = 1; w2 < 8; ++w2) acc += sm.wpart[q][w2][c];
+                part[(int64_t)sm.e[gbot + q - lo] * 9 + c] = acc;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_blend_levels_fwd(const uint2 *ranges, const uint32_t *sorted_vals, const float4 *ranked,
+                                    const CamParams &cam, const RenderParams &rp, int L, const LevelPtrs &out,
+                                    float *lv_T, uint32_t *lv_last, cudaStream_t st) {
+    const unsigned tiles = (unsigned)(rp.ntx * rp.nty);
+    if (tiles == 0) return cudaSuccess;
+#define GC_LV_ARGS ranges, sorted_vals, ranked, cam.width, cam.height, rp.ntx, rp.bg[0], rp.bg[1], rp.bg[2], \
+                   rp.membership, L, out, lv_T, lv_last
+    if (rp.tile_w == 16 && rp.tile_h == 16) k_blend_levels_fwd<16, 16><<<tiles, 256, 0, st>>>(GC_LV_ARGS);
+    else if (rp.tile_w == 8 && rp.tile_h == 32) k_blend_levels_fwd<8, 32><<<tiles, 256, 0, st>>>(GC_LV_ARGS);
+    else if (rp.tile_w == 32 && rp.tile_h == 8) k_blend_levels_fwd<32, 8><<<tiles, 256, 0, st>>>(GC_LV_ARGS);
+    else return cudaErrorInvalidValue;
+#undef GC_LV_ARGS
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_levels_bwd(const uint2 *ranges, const uint32_t *sorted_vals, const float4 *ranked,
+                                    const uint32_t *offsets, const CamParams &cam, const RenderParams &rp, int L,
+                                    const float *lv_T, const uint32_t *lv_last, const LevelGrads &dimg,
+                                    float *part, cudaStream_t st) {
+    const unsigned tiles = (unsigned)(rp.ntx * rp.nty);
+    if (tiles == 0) return cudaSuccess;
+#define GC_LV_ARGS ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp, L, lv_T, lv_last, dimg, part
+    if (rp.tile_w == 16 && rp.tile_h == 16) k_blend_levels_bwd<16, 16><<<tiles, 256, 0, st>>>(GC_LV_ARGS);
+    else if (rp.tile_w == 8 && rp.tile_h == 32) k_blend_levels_bwd<8, 32><<<tiles, 256, 0, st>>>(GC_LV_ARGS);
+    else if (rp.tile_w == 32 && rp.tile_h == 8) k_blend_levels_bwd<32, 8><<<tiles, 256, 0, st>>>(GC_LV_ARGS);
+    else return cudaErrorInvalidValue;
+#undef GC_LV_ARGS
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace gc

@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, i
     project_gaussian(G, i, G.group_q, G.group_t, G.n_groups, cam, rp, P);
     rec[kRec * j] = P.r0;
     rec[kRec * j + 1] = P.r1;
+    P.r2.y = __int_as_float(layer_of(sel, i));
     rec[kRec * j + 2] = P.r2;
     const uint32_t nt = bin_rows(P, rp, cam.width, cam.height, tile_diff, rp.ntx + 1);
     rec[kRec * j + 3] = P.r3;

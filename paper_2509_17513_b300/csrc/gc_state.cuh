@@ -77,6 +77,8 @@ struct gc_saved {
     int depth_buf = 0, tile_buf = 0;
     DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
         final_T, n_contrib, n_blended, n_walked, words, tile_diff;
+    int levels = 0;         // > 0: a multi-level forward of levels 1..levels
+    DevBuf lv_T, lv_last;   // its per-level final transmittance and list position
 };
 
 
@@ -212,6 +214,8 @@ inline gc_status make_source(gc_context *ctx, const gc_gaussians *g, const gc_mo
 inline gc::Selection make_selection(const gc_gaussians *g, uint32_t mask, int64_t &n_sel) {
     gc::Selection s{};
     n_sel = 0;
+    s.n_layers = g->n_layers;
+    for (int l = 0; l <= g->n_layers; ++l) s.layer_off[l] = g->layer_offsets[l];
     s.range_start[0] = 0;
     for (int l = 0; l < g->n_layers; ++l) {
         if (!((mask >> l) & 1u)) continue;

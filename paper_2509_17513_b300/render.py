@@ -226,6 +226,50 @@ class Renderer:
         check(st, self.ctx)
         return grads
 
+    # ---- multi-level render -----------------------------------------------------------
+
+    def levels_forward(self, gs: GaussianSet, motion: MotionFrame | None, levels: int, camera,
+                       saved: Saved | None = None, outs: list | None = None, stream=None) -> list:
+        """Levels 1..levels of one view in one pass; returns one (3, H, W) image per level."""
+        cam = camera_struct(camera)
+        if outs is None:
+            outs = [torch.empty((3, cam.height, cam.width), dtype=torch.float32, device=f"cuda:{self.device}")
+                    for _ in range(levels)]
+        ptrs = (C.c_void_p * levels)(*[o.data_ptr() for o in outs])
+        st = lib().gc_render_levels_forward(self.ctx, C.byref(gs.struct),
+                                            C.byref(motion.struct) if motion is not None else None, int(levels),
+                                            C.byref(cam), ptrs, saved.handle if saved is not None else None,
+                                            _stream(stream))
+        check(st, self.ctx)
+        return outs
+
+    def levels_backward(self, saved: Saved | None, gs: GaussianSet, motion: MotionFrame | None,
+                        dL_dimages: list, grads: dict | None = None, stream=None) -> dict:
+        """Gradients of sum_l <dL_dimages[l], image_l> of a multi-level forward."""
+        if grads is None:
+            grads = self._single_grads(gs, motion)
+        g = self._grads_struct(grads)
+        dls = [d.contiguous() for d in dL_dimages]
+        ptrs = (C.c_void_p * len(dls))(*[d.data_ptr() for d in dls])
+        st = lib().gc_render_levels_backward(self.ctx, saved.handle if saved is not None else None,
+                                             C.byref(gs.struct), C.byref(motion.struct) if motion is not None else None,
+                                             ptrs, C.byref(g), _stream(stream))
+        check(st, self.ctx)
+        return grads
+
+    def _single_grads(self, gs: GaussianSet, motion: MotionFrame | None) -> dict:
+        dev = f"cuda:{self.device}"
+        K = (gs.sh_degree + 1) ** 2
+        n = gs.n
+        grads = {"means": torch.empty((n, 3), device=dev), "log_scales": torch.empty((n, 3), device=dev),
+                 "quats": torch.empty((n, 4), device=dev), "opacity_logits": torch.empty(n, device=dev),
+                 "sh": torch.empty((n, K, 3), device=dev)}
+        if motion is not None:
+            G = motion.q.shape[0]
+            grads["group_q"] = torch.empty((G, 4), device=dev)
+            grads["group_t"] = torch.empty((G, 3), device=dev)
+        return grads
+
     # ---- batched requests -------------------------------------------------------------
 
     def batch_forward(self, gs: GaussianSet, frames: list, requests: list, saved: Saved | None = None,

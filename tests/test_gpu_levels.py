@@ -1,0 +1,111 @@
+"""Single-pass multi-level render (levels 1..L of one view from one list, Eq. 4 nested
+layers): every level image equals the single-level render of its layer mask bit for
+bit; the one-pass backward equals the sum of the single-level backwards up to float
+summation order, and the FP64 oracle's gradients summed over the levels."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import scenes
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ("means", "log_scales", "quats", "opacity_logits", "sh", "group_q", "group_t")
+
+
+@pytest.fixture(scope="module")
+def gc():
+    import paper_2509_17513_b300 as gc
+    return gc
+
+
+@pytest.fixture(scope="module")
+def small():
+    rng = np.random.default_rng(101)
+    scene = scenes.make_hier_scene(rng, 8000, 6, 3, 16)
+    motion = scenes.random_motion(rng, 16, 3)
+    return scene, motion
+
+
+@pytest.mark.parametrize("tile,L", [((16, 16), 6), ((8, 32), 6), ((32, 8), 4), ((16, 16), 1)])
+def test_levels_equal_single_level_renders(gc, small, tile, L):
+    scene, motion = small
+    cam = scenes.orbit_camera(1.3, 4.0, 230, 170)
+    r = gc.Renderer(0, tile=tile, bg=(0.2, 0.1, 0.05))
+    gs = gc.GaussianSet.from_scene(scene)
+    mo = gc.MotionFrame.from_motion(motion, 2)
+    imgs = r.levels_forward(gs, mo, L, cam)
+    for l in range(1, L + 1):
+        one = r.forward(gs, mo, scenes.level_mask(l), cam)
+        torch.cuda.synchronize()
+        assert torch.equal(imgs[l - 1], one), (tile, l)
+
+
+def test_levels_backward_matches_single_sum_and_oracle(gc, small):
+    scene, motion = small
+    cam = scenes.orbit_camera(0.4, 4.0, 128, 96)
+    L = 6
+    opts = oracle.default_options()
+    refs = [oracle.render(scene, motion, 1, cam, opts, scenes.level_mask(l)) for l in range(1, L + 1)]
+    rng = np.random.default_rng(3)
+    ups = [(rng.normal(0, 1, (3, 96, 128)) * (~ref["ambiguous"])[None]).astype(np.float32) for ref in refs]
+    r = gc.Renderer(0)
+    gs = gc.GaussianSet.from_scene(scene)
+    mo = gc.MotionFrame.from_motion(motion, 1)
+    saved = gc.Saved(r)
+    r.levels_forward(gs, mo, L, cam, saved)
+    dls = [torch.from_numpy(u).cuda() for u in ups]
+    got = r.levels_backward(saved, gs, mo, dls)
+    torch.cuda.synchronize()
+    got = {k: v.clone() for k, v in got.items()}
+    # against the in-order sum of single-level GPU backwards
+    acc = {k: torch.zeros_like(v) for k, v in got.items()}
+    for l in range(1, L + 1):
+        s1 = gc.Saved(r)
+        r.forward(gs, mo, scenes.level_mask(l), cam, s1)
+        g1 = r.backward(s1, gs, mo, dls[l - 1])
+        for k in acc:
+            acc[k] += g1[k]
+    torch.cuda.synchronize()
+    for k in acc:
+        a, b = got[k], acc[k]
+        assert float((a - b).abs().max()) <= 1e-5 * float(b.abs().max()) + 1e-7, k
+    # against the FP64 oracle, summed over the levels
+    want = None
+    for l in range(1, L + 1):
+        og = oracle.grad(scene, motion, 1, cam, opts, ups[l - 1].astype(np.float64), scenes.level_mask(l),
+                         bins=refs[l - 1]["bins"])
+        want = {k: og[k] for k in NAMES} if want is None else {k: want[k] + og[k] for k in NAMES}
+    for k in NAMES:
+        a = got[k].cpu().numpy().astype(np.float64)
+        b = np.asarray(want[k]).reshape(a.shape)
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 1e-4, k
+        assert np.abs(a - b).max() <= 1e-3 * np.abs(b).max() + 1e-6, k
+
+
+def test_levels_argument_errors(gc, small):
+    scene, motion = small
+    cam = scenes.orbit_camera(0.4, 4.0, 64, 48)
+    r = gc.Renderer(0)
+    gs = gc.GaussianSet.from_scene(scene)
+    with pytest.raises(gc.GCError):
+        r.levels_forward(gs, None, 7, cam)  # the set has 6 layers
+    saved = gc.Saved(r)
+    imgs = r.levels_forward(gs, None, 3, cam, saved)
+    with pytest.raises(gc.GCError, match="multi-level"):
+        r.backward(saved, gs, None, torch.zeros_like(imgs[0]))
+
+
+def test_levels_at_1080p(gc):
+    """hier1080 frame 7: the six level images of one pass equal the six single renders."""
+    w = scenes.hier1080(n_frames=8)
+    cam = w.cameras[7]
+    r = gc.Renderer(0)
+    gs = gc.GaussianSet.from_scene(w.scene)
+    mo = gc.MotionFrame.from_motion(w.motion, 7)
+    imgs = r.levels_forward(gs, mo, 6, cam)
+    for l in range(1, 7):
+        one = r.forward(gs, mo, scenes.level_mask(l), cam)
+        torch.cuda.synchronize()
+        assert torch.equal(imgs[l - 1], one), l
