@@ -22,12 +22,14 @@ namespace gc {
 
 namespace {
 
-// Forward: one CTA of 256 threads per tile, one pixel per thread (the forward layout).
-template <int TW, int TH>
+// Forward: one CTA of 256 threads per tile, one pixel per thread (the forward layout);
+// NL = number of levels (compile time, so that the per-level state fits in registers).
+template <int TW, int TH, int NL>
 __global__ void __launch_bounds__(256) k_blend_levels_fwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, int W, int H, int ntx, float bg0, float bg1, float bg2, int membership,
-    int L, LevelPtrs out, float *__restrict__ lv_T, uint32_t *__restrict__ lv_last) {
+    LevelPtrs out, float *__restrict__ lv_T, uint32_t *__restrict__ lv_last) {
+    constexpr int L = NL;
     __shared__ __align__(16) FwdSmem sm;
     __shared__ uint8_t lay[256];
     const int tile = blockIdx.x, tx = tile % ntx, ty = tile / ntx;
@@ -41,10 +43,10 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
     const bool inside = px < W && py < H;
     uint32_t lv = inside ? ((1u << L) - 1u) : 0u;  // levels still blending
     uint32_t act = lv ? (1u << lane) : 0u;
-    float T[kMaxLevels], C0[kMaxLevels], C1[kMaxLevels], C2[kMaxLevels];
-    uint32_t last[kMaxLevels];
+    float T[NL], C0[NL], C1[NL], C2[NL];
+    uint32_t last[NL];
 #pragma unroll
-    for (int l = 0; l < kMaxLevels; ++l) {
+    for (int l = 0; l < NL; ++l) {
         T[l] = 1.f;
         C0[l] = C1[l] = C2[l] = 0.f;
         last[l] = 0u;
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
                 if (alpha < kAlphaMin) continue;
                 const float4 col = sm.c[k];
 #pragma unroll
-                for (int l = 0; l < kMaxLevels; ++l) {
+                for (int l = 0; l < NL; ++l) {
                     if (!((lm >> l) & 1u)) continue;
                     const float Tn = T[l] * (1.f - alpha);
                     if (Tn < kTStop) {
@@ -109,8 +111,7 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
         const size_t hw = (size_t)W * H;
         const size_t p = (size_t)py * W + px;
 #pragma unroll
-        for (int l = 0; l < kMaxLevels; ++l) {
-            if (l >= L) break;
+        for (int l = 0; l < NL; ++l) {
             float *img = out.img[l];
             img[p] = fmaf(T[l], bg0, C0[l]);
             img[hw + p] = fmaf(T[l], bg1, C1[l]);
@@ -121,13 +122,14 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
     }
 }
 
-// Reverse: one CTA of 256 threads per tile, one pixel per thread.
-template <int TW, int TH>
+// Reverse: one CTA of 256 threads per tile, one pixel per thread; NL levels.
+template <int TW, int TH, int NL>
 __global__ void __launch_bounds__(256) k_blend_levels_bwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, RenderParams rp,
-    int L, const float *__restrict__ lv_T, const uint32_t *__restrict__ lv_last, LevelGrads dimg,
+    const float *__restrict__ lv_T, const uint32_t *__restrict__ lv_last, LevelGrads dimg,
     float *__restrict__ part) {
+    constexpr int L = NL;
     struct Smem {
         float4 a[256];
         float2 b[256];
@@ -148,15 +150,14 @@ __global__ void __launch_bounds__(256) k_blend_levels_bwd(
     const int px = tx * TW + lx, py = ty * TH + ly;
     const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
     const uint32_t bit = 1u << lane;
-    float T[kMaxLevels], A0[kMaxLevels], A1[kMaxLevels], A2[kMaxLevels], g0[kMaxLevels], g1[kMaxLevels],
-        g2[kMaxLevels];
-    uint32_t last[kMaxLevels];
+    float T[NL], A0[NL], A1[NL], A2[NL], g0[NL], g1[NL], g2[NL];
+    uint32_t last[NL];
     uint32_t my_last = 0u;
     const size_t hw = (size_t)W * H;
     const bool inside = px < W && py < H;
     const size_t p = inside ? (size_t)py * W + px : 0;
 #pragma unroll
-    for (int l = 0; l < kMaxLevels; ++l) {
+    for (int l = 0; l < NL; ++l) {
         T[l] = 1.f;
         A0[l] = rp.bg[0];
         A1[l] = rp.bg[1];
@@ -215,8 +216,8 @@ __global__ void __launch_bounds__(256) k_blend_levels_bwd(
                 const uint32_t wm = sm.m[8 * s + warp];
                 uint32_t lm = 0u;  // levels of this pixel that blended entry k
 #pragma unroll
-                for (int l = 0; l < kMaxLevels; ++l)
-                    if (l < L && l >= (int)sm.lay[s] && (uint32_t)k < last[l]) lm |= 1u << l;
+                for (int l = 0; l < NL; ++l)
+                    if (l >= (int)sm.lay[s] && (uint32_t)k < last[l]) lm |= 1u << l;
                 if ((wm & bit) != 0u && lm) {
                     const float4 a = sm.a[s];
                     const float2 bb = sm.b[s];
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(256) k_blend_levels_bwd(
                         const float4 col = sm.c[s];
                         float dp = 0.f;
 #pragma unroll
-                        for (int l = 0; l < kMaxLevels; ++l) {
+                        for (int l = 0; l < NL; ++l) {
                             if (!((lm >> l) & 1u)) continue;
                             T[l] = __fdividef(T[l], 1.f - alpha);
                             const float w = alpha * T[l];
@@ -317,11 +318,19 @@ cudaError_t launch_blend_levels_fwd(const uint2 *ranges, const uint32_t *sorted_
     const unsigned tiles = (unsigned)(rp.ntx * rp.nty);
     if (tiles == 0) return cudaSuccess;
 #define GC_LV_ARGS ranges, sorted_vals, ranked, cam.width, cam.height, rp.ntx, rp.bg[0], rp.bg[1], rp.bg[2], \
-                   rp.membership, L, out, lv_T, lv_last
-    if (rp.tile_w == 16 && rp.tile_h == 16) k_blend_levels_fwd<16, 16><<<tiles, 256, 0, st>>>(GC_LV_ARGS);
-    else if (rp.tile_w == 8 && rp.tile_h == 32) k_blend_levels_fwd<8, 32><<<tiles, 256, 0, st>>>(GC_LV_ARGS);
-    else if (rp.tile_w == 32 && rp.tile_h == 8) k_blend_levels_fwd<32, 8><<<tiles, 256, 0, st>>>(GC_LV_ARGS);
-    else return cudaErrorInvalidValue;
+                   rp.membership, out, lv_T, lv_last
+#define GC_LV_CASE(NLV)                                                                                       \
+    case NLV:                                                                                                 \
+        if (rp.tile_w == 16) k_blend_levels_fwd<16, 16, NLV><<<tiles, 256, 0, st>>>(GC_LV_ARGS);             \
+        else if (rp.tile_w == 8) k_blend_levels_fwd<8, 32, NLV><<<tiles, 256, 0, st>>>(GC_LV_ARGS);          \
+        else k_blend_levels_fwd<32, 8, NLV><<<tiles, 256, 0, st>>>(GC_LV_ARGS);                               \
+        break;
+    switch (L) {
+        GC_LV_CASE(1) GC_LV_CASE(2) GC_LV_CASE(3) GC_LV_CASE(4) GC_LV_CASE(5) GC_LV_CASE(6) GC_LV_CASE(7)
+        GC_LV_CASE(8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef GC_LV_CASE
 #undef GC_LV_ARGS
     note_launches(1);
     return cudaGetLastError();
@@ -333,11 +342,19 @@ cudaError_t launch_blend_levels_bwd(const uint2 *ranges, const uint32_t *sorted_
                                     float *part, cudaStream_t st) {
     const unsigned tiles = (unsigned)(rp.ntx * rp.nty);
     if (tiles == 0) return cudaSuccess;
-#define GC_LV_ARGS ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp, L, lv_T, lv_last, dimg, part
-    if (rp.tile_w == 16 && rp.tile_h == 16) k_blend_levels_bwd<16, 16><<<tiles, 256, 0, st>>>(GC_LV_ARGS);
-    else if (rp.tile_w == 8 && rp.tile_h == 32) k_blend_levels_bwd<8, 32><<<tiles, 256, 0, st>>>(GC_LV_ARGS);
-    else if (rp.tile_w == 32 && rp.tile_h == 8) k_blend_levels_bwd<32, 8><<<tiles, 256, 0, st>>>(GC_LV_ARGS);
-    else return cudaErrorInvalidValue;
+#define GC_LV_ARGS ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp, lv_T, lv_last, dimg, part
+#define GC_LV_CASE(NLV)                                                                                       \
+    case NLV:                                                                                                 \
+        if (rp.tile_w == 16) k_blend_levels_bwd<16, 16, NLV><<<tiles, 256, 0, st>>>(GC_LV_ARGS);             \
+        else if (rp.tile_w == 8) k_blend_levels_bwd<8, 32, NLV><<<tiles, 256, 0, st>>>(GC_LV_ARGS);          \
+        else k_blend_levels_bwd<32, 8, NLV><<<tiles, 256, 0, st>>>(GC_LV_ARGS);                               \
+        break;
+    switch (L) {
+        GC_LV_CASE(1) GC_LV_CASE(2) GC_LV_CASE(3) GC_LV_CASE(4) GC_LV_CASE(5) GC_LV_CASE(6) GC_LV_CASE(7)
+        GC_LV_CASE(8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef GC_LV_CASE
 #undef GC_LV_ARGS
     note_launches(1);
     return cudaGetLastError();
