@@ -227,6 +227,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     peaks, peak_kind = measured_peaks()
+    skip = {x.strip() for x in args.skip_forms.split(",") if x.strip()}
 
     w = scenes.hier1080(n_frames=args.frames)
     W, H = 1920, 1080
@@ -247,44 +248,51 @@ def run_gpu(args):
         return round(px * steps * world / (total_ms / 1e3) / 1e6, 1)
 
     # ---- plain FP32 single-view form: one gc_render_forward (+ backward) per request
-    saved = gc.Saved(r)
-    kmax = 0
-    for q, (cam, f, mask) in enumerate(reqs):
-        r.forward(gs, frames[f], mask, cam, out=outs[q])
-        kmax = max(kmax, r.stats()["n_keys"])
-    cap_single = int(kmax * 1.05) + 4096
-    r.set_options(key_capacity=cap_single)
-    grads1 = None
-
-    def single_fwd():
+    single_view = None
+    s_steps = max(1, min(args.steps, 3))
+    if "single" not in skip:
+        saved = gc.Saved(r)
+        kmax = 0
         for q, (cam, f, mask) in enumerate(reqs):
             r.forward(gs, frames[f], mask, cam, out=outs[q])
+            kmax = max(kmax, r.stats()["n_keys"])
+        cap_single = int(kmax * 1.05) + 4096
+        r.set_options(key_capacity=cap_single)
+        grads1 = None
 
-    def single_fwd_bwd():
-        nonlocal grads1
-        for q, (cam, f, mask) in enumerate(reqs):
-            r.forward(gs, frames[f], mask, cam, saved, out=outs[q])
-            grads1 = r.backward(saved, gs, frames[f], upstream, grads1)
+        def single_fwd():
+            for q, (cam, f, mask) in enumerate(reqs):
+                r.forward(gs, frames[f], mask, cam, out=outs[q])
 
-    for _ in range(args.warmup):
-        single_fwd()
-        single_fwd_bwd()
-    r.check()
-    s_steps = max(1, min(args.steps, 3))
-    sf_ms, sf_prof, _ = timer(single_fwd, s_steps, profile=True, name="single_fwd")
-    sfb_ms, sfb_prof, _ = timer(single_fwd_bwd, s_steps, profile=True, name="single_fwd_bwd")
-    r.check()
-    single_view = {"form": "plain FP32, one gc_render_forward (+ gc_render_backward) per request",
-                   "fwd": mpix(sf_ms, s_steps), "fwd_bwd": mpix(sfb_ms, s_steps), "unit": UNIT,
-                   "ms_per_step": {"fwd": round(sf_ms / s_steps, 2), "fwd_bwd": round(sfb_ms / s_steps, 2)},
-                   "stage_ms_per_render": stage_summary(sfb_prof)[0], "steps": s_steps}
-    del saved, grads1
-    r.set_options(key_capacity=0)
+        def single_fwd_bwd():
+            nonlocal grads1
+            for q, (cam, f, mask) in enumerate(reqs):
+                r.forward(gs, frames[f], mask, cam, saved, out=outs[q])
+                grads1 = r.backward(saved, gs, frames[f], upstream, grads1)
+
+        for _ in range(args.warmup):
+            single_fwd()
+            single_fwd_bwd()
+        r.check()
+        s_steps = max(1, min(args.steps, 3))
+        sf_ms, sf_prof, _ = timer(single_fwd, s_steps, profile=True, name="single_fwd")
+        sfb_ms, sfb_prof, _ = timer(single_fwd_bwd, s_steps, profile=True, name="single_fwd_bwd")
+        r.check()
+        single_view = {"form": "plain FP32, one gc_render_forward (+ gc_render_backward) per request",
+                       "fwd": mpix(sf_ms, s_steps), "fwd_bwd": mpix(sfb_ms, s_steps), "unit": UNIT,
+                       "ms_per_step": {"fwd": round(sf_ms / s_steps, 2), "fwd_bwd": round(sfb_ms / s_steps, 2)},
+                       "stage_ms_per_render": stage_summary(sfb_prof)[0], "steps": s_steps}
+        del saved, grads1
+        r.set_options(key_capacity=0)
 
     # ---- batched form: autotuned tile shape x batch depth, CUDA graph of the whole step
-    tune = r.tune_batch(gs, frames, reqs, dL_dimages=dls, depths=(30, 60, 90, n_req), iters=2, outs=outs)
-    best = tune["best"]
-    depth, tile = best["depth"], tuple(best["tile"])
+    tune = None
+    if "batched" not in skip:
+        tune = r.tune_batch(gs, frames, reqs, dL_dimages=dls, depths=(30, 60, 90, n_req), iters=2, outs=outs)
+        depth, tile = tune["best"]["depth"], tuple(tune["best"]["tile"])
+    else:
+        depth, tile = n_req, (8, 32)
+        r.set_options(tile=tile)
     # algorithmic work of one step at the tuned tile shape (deterministic, outside the timed regions):
     # walked / blended pairs per render, and of the top level alone (what a multi-level pass walks)
     walked_pairs = blended_pairs = bwd_pairs = keys_total = walked_top = bwd_top = kmax_tuned = 0
@@ -304,47 +312,6 @@ def run_gpu(args):
         kmax_tuned = max(kmax_tuned, nk)
     keys_mean = keys_total / n_req
     cap_levels = int(kmax_tuned * 1.05) + 4096  # the multi-level lists are the top level's
-    grads = r.batch_grads(gs, frames)
-    g_fwd = gc.BatchGraph(r, gs, frames, reqs, depth, outs=outs)
-    g_fb = gc.BatchGraph(r, gs, frames, reqs, depth, dL_dimages=dls, grads=grads, outs=outs)
-    for _ in range(args.warmup):
-        g_fwd.launch()
-        g_fb.launch()
-    g_fwd.check()
-    g_fb.check()
-    bf_ms, _, clk_bf = timer(g_fwd.launch, args.steps, name="graph_fwd")
-    bfb_ms, _, clk_bfb = timer(g_fb.launch, args.steps, name="graph_fwd_bwd")
-    g_fwd.check()
-    g_fb.check()
-    ref_imgs = [o.clone() for o in outs[:: max(1, n_req // 12)]]
-    cap = g_fwd.key_capacity
-    g_fwd.close()
-    g_fb.close()
-
-    # the same batched step, eager with per-stage CUDA events
-    sv = [gc.Saved(r) for _ in range((n_req + depth - 1) // depth)]
-
-    def eager(bwd):
-        def step():
-            for b, s in enumerate(sv):
-                r.batch_forward(gs, frames, reqs[b * depth:(b + 1) * depth], s,
-                                outs=outs[b * depth:(b + 1) * depth])
-            if bwd:
-                for b, s in enumerate(sv):
-                    r.batch_backward(s, gs, frames, dls[b * depth:(b + 1) * depth], grads=grads,
-                                     accumulate=b > 0)
-        return step
-
-    r.set_options(key_capacity=cap)
-    eager(True)()
-    r.check()
-    e_steps = max(1, min(args.steps, 3))
-    ef_ms, ef_prof, _ = timer(eager(False), e_steps, profile=True, name="eager_fwd")
-    efb_ms, efb_prof, _ = timer(eager(True), e_steps, profile=True, name="eager_fwd_bwd")
-    r.check()
-    del sv
-    r.set_options(key_capacity=0)
-
     def roof(prof, steps, batched, eval_pairs, bwd_eval_pairs, renders_per_step):
         st_ms, st_calls = prof["stage_ms"], prof["stage_calls"]
         dom = max(st_ms, key=lambda k: st_ms[k])
@@ -358,17 +325,78 @@ def run_gpu(args):
         return roofline_for(dom, per_launch, work, peaks, peak_kind, batched=batched,
                             renders_per_launch=renders_per_step * steps // launches)
 
-    # ---- reduced-precision storage (BF16 geometry, FP8-E4M3 SH), same batched graph
-    gq = gc.BatchGraph(r, gsq, frames, reqs, depth, dL_dimages=dls, grads=r.batch_grads(gsq, frames), outs=outs)
-    for _ in range(args.warmup):
-        gq.launch()
-    gq.check()
-    q_ms, _, clk_q = timer(gq.launch, args.steps, name="graph_bf16_fp8_fwd_bwd")
-    gq.check()
-    q_imgs = outs[:: max(1, n_req // 12)]
-    mse = sum(float(((a - b) ** 2).mean()) for a, b in zip(q_imgs, ref_imgs)) / len(ref_imgs)
-    q_psnr = round(10 * np.log10(1.0 / mse), 2) if mse > 0 else None
-    gq.close()
+    batched_obj = precision_obj = None
+    if "batched" not in skip:
+        grads = r.batch_grads(gs, frames)
+        g_fwd = gc.BatchGraph(r, gs, frames, reqs, depth, outs=outs)
+        g_fb = gc.BatchGraph(r, gs, frames, reqs, depth, dL_dimages=dls, grads=grads, outs=outs)
+        for _ in range(args.warmup):
+            g_fwd.launch()
+            g_fb.launch()
+        g_fwd.check()
+        g_fb.check()
+        bf_ms, _, clk_bf = timer(g_fwd.launch, args.steps, name="graph_fwd")
+        bfb_ms, _, clk_bfb = timer(g_fb.launch, args.steps, name="graph_fwd_bwd")
+        g_fwd.check()
+        g_fb.check()
+        ref_imgs = [o.clone() for o in outs[:: max(1, n_req // 12)]]
+        cap = g_fwd.key_capacity
+        g_fwd.close()
+        g_fb.close()
+
+        # the same batched step, eager with per-stage CUDA events
+        sv = [gc.Saved(r) for _ in range((n_req + depth - 1) // depth)]
+
+        def eager(bwd):
+            def step():
+                for b, s in enumerate(sv):
+                    r.batch_forward(gs, frames, reqs[b * depth:(b + 1) * depth], s,
+                                    outs=outs[b * depth:(b + 1) * depth])
+                if bwd:
+                    for b, s in enumerate(sv):
+                        r.batch_backward(s, gs, frames, dls[b * depth:(b + 1) * depth], grads=grads,
+                                         accumulate=b > 0)
+            return step
+
+        r.set_options(key_capacity=cap)
+        eager(True)()
+        r.check()
+        e_steps = max(1, min(args.steps, 3))
+        ef_ms, ef_prof, _ = timer(eager(False), e_steps, profile=True, name="eager_fwd")
+        efb_ms, efb_prof, _ = timer(eager(True), e_steps, profile=True, name="eager_fwd_bwd")
+        r.check()
+        del sv
+        r.set_options(key_capacity=0)
+
+        # ---- reduced-precision storage (BF16 geometry, FP8-E4M3 SH), same batched graph
+        gq = gc.BatchGraph(r, gsq, frames, reqs, depth, dL_dimages=dls, grads=r.batch_grads(gsq, frames), outs=outs)
+        for _ in range(args.warmup):
+            gq.launch()
+        gq.check()
+        q_ms, _, clk_q = timer(gq.launch, args.steps, name="graph_bf16_fp8_fwd_bwd")
+        gq.check()
+        q_imgs = outs[:: max(1, n_req // 12)]
+        mse = sum(float(((a - b) ** 2).mean()) for a, b in zip(q_imgs, ref_imgs)) / len(ref_imgs)
+        q_psnr = round(10 * np.log10(1.0 / mse), 2) if mse > 0 else None
+        gq.close()
+        batched_obj = {"form": "the 180 renders as batched requests replayed from one CUDA graph "
+                               "(autotuned tile shape and batch depth)",
+                       "fwd": mpix(bf_ms, args.steps), "fwd_bwd": mpix(bfb_ms, args.steps), "unit": UNIT,
+                       "ms_per_step": {"fwd": round(bf_ms / args.steps, 3), "fwd_bwd": round(bfb_ms / args.steps, 3)},
+                       "tile": f"{tile[0]}x{tile[1]}", "batch_depth": depth, "key_capacity_per_batch": cap,
+                       "clocks": {"fwd": clk_bf, "fwd_bwd": clk_bfb},
+                       "roofline": {"fwd": roof(ef_prof, e_steps, True, walked_pairs, bwd_pairs, n_req),
+                                    "fwd_bwd": roof(efb_prof, e_steps, True, walked_pairs, bwd_pairs, n_req)},
+                       "stage_ms_per_call": stage_summary(efb_prof)[0],
+                       "stage_share_fwd": stage_summary(ef_prof)[1],
+                       "stage_share_fwd_bwd": stage_summary(efb_prof)[1],
+                       "eager_fwd": mpix(ef_ms, e_steps), "eager_fwd_bwd": mpix(efb_ms, e_steps)}
+        precision_obj = {"storage": "BF16 means/log-scales/quats/opacity, FP8-E4M3 SH, FP32 scales; "
+                                    "FP32 arithmetic; batched graph", "fwd_bwd": mpix(q_ms, args.steps),
+                         "unit": UNIT, "ms_per_step": round(q_ms / args.steps, 3),
+                         "psnr_vs_fp32_scene_db": q_psnr, "clocks": clk_q,
+                         "bytes_per_gaussian": {"fp32": 4 * 59 + 4, "bf16_fp8": 2 * 11 + 48 + 4}}
+        del ref_imgs, grads
 
     # ---- headline: single-pass multi-level form, per frame levels 1..6 from one list (the
     # same 180 images, bit for bit), fixed key capacity, per-stage CUDA events
@@ -424,24 +452,9 @@ def run_gpu(args):
                               "stage_ms_per_call_fwd_bwd": stage_summary(fb_prof)[0],
                               "stage_share_fwd": stage_summary(fwd_prof)[1],
                               "stage_share_fwd_bwd": stage_summary(fb_prof)[1]},
-            "batched": {"form": "the 180 renders as batched requests replayed from one CUDA graph "
-                                "(autotuned tile shape and batch depth)",
-                        "fwd": mpix(bf_ms, args.steps), "fwd_bwd": mpix(bfb_ms, args.steps), "unit": UNIT,
-                        "ms_per_step": {"fwd": round(bf_ms / args.steps, 3), "fwd_bwd": round(bfb_ms / args.steps, 3)},
-                        "tile": f"{tile[0]}x{tile[1]}", "batch_depth": depth, "key_capacity_per_batch": cap,
-                        "clocks": {"fwd": clk_bf, "fwd_bwd": clk_bfb},
-                        "roofline": {"fwd": roof(ef_prof, e_steps, True, walked_pairs, bwd_pairs, n_req),
-                                     "fwd_bwd": roof(efb_prof, e_steps, True, walked_pairs, bwd_pairs, n_req)},
-                        "stage_ms_per_call": stage_summary(efb_prof)[0],
-                        "stage_share_fwd": stage_summary(ef_prof)[1],
-                        "stage_share_fwd_bwd": stage_summary(efb_prof)[1],
-                        "eager_fwd": mpix(ef_ms, e_steps), "eager_fwd_bwd": mpix(efb_ms, e_steps)},
+            "batched": batched_obj,
             "single_view": single_view,
-            "reduced_precision": {"storage": "BF16 means/log-scales/quats/opacity, FP8-E4M3 SH, FP32 scales; "
-                                             "FP32 arithmetic; batched graph", "fwd_bwd": mpix(q_ms, args.steps),
-                                  "unit": UNIT, "ms_per_step": round(q_ms / args.steps, 3),
-                                  "psnr_vs_fp32_scene_db": q_psnr, "clocks": clk_q,
-                                  "bytes_per_gaussian": {"fp32": 4 * 59 + 4, "bf16_fp8": 2 * 11 + 48 + 4}},
+            "reduced_precision": precision_obj,
             "autotune": tune,
             "work_per_step": {"blend_walked_pairs": walked_pairs, "blended_pairs": blended_pairs,
                               "blend_bwd_walked_pairs": bwd_pairs, "top_level_walked_pairs": walked_top,
@@ -449,7 +462,8 @@ def run_gpu(args):
                               "flops_per_pair": {"evaluate": EVAL_FLOPS_PER_PAIR,
                                                  "blend_fwd": FWD_BLEND_FLOPS_PER_PAIR,
                                                  "blend_bwd": BWD_BLEND_FLOPS_PER_PAIR}}}
-    del outs, ref_imgs, q_imgs, grads, dls
+    line = {k: v for k, v in line.items() if v is not None}
+    del outs, dls
     torch.cuda.empty_cache()
 
     if not args.no_batch128:
@@ -668,6 +682,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch128", action="store_true", help="skip the 128-request batching workload")
+    ap.add_argument("--skip-forms", default="", help="comma list of side forms to leave out: single, batched "
+                    "(then 8x32 tiles are used and the BF16/FP8 form is left out too)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
