@@ -117,10 +117,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel: str, renders_per_launch: int):
-    """DRAM bytes of one launch of `kernel` covering `renders_per_launch` renders, from the
-    committed ncu summary (profiles/traffic.json, bytes per render of a small capture
-    scaled by renders), or None when the kernels changed since it was taken."""
+def load_traffic(kernel: str, units_per_launch: int):
+    """DRAM bytes of one launch of `kernel` covering `units_per_launch` units (renders, or
+    frames of a multi-level pass), from the committed ncu summary profiles/traffic.json
+    (bytes per unit of a small capture), or None when the kernels changed since it was
+    taken or the kernel was not captured."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -131,7 +132,7 @@ def load_traffic(kernel: str, renders_per_launch: int):
     e = d.get("kernels", {}).get(kernel)
     if not e:
         return None
-    return int(e["dram_bytes_per_render"] * renders_per_launch)
+    return int(e["dram_bytes_per_unit"] * units_per_launch)
 
 
 # --------------------------------------------------------------------------- GPU arm
