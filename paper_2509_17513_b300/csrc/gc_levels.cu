@@ -65,17 +65,25 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
                 sm.a[threadIdx.x] = a;
                 sm.b[threadIdx.x] = make_float2(bb.x, bb.y);
                 sm.c[threadIdx.x] = make_float4(bb.z, bb.w, c.x, 0.f);
-                store_masks<TW>(&sm.m[8 * threadIdx.x], cm, rm);
+                store_masks_by_warp<TW>(sm.m, (int)threadIdx.x, cm, rm);
                 lay[threadIdx.x] = (uint8_t)min(__float_as_int(c.y), 31);
             }
         }
         __syncthreads();
         const int cnt = min(256, n - b);
-        for (int k0 = 0; k0 < cnt; k0 += 16) {
-            if (__ballot_sync(0xffffffffu, act != 0u) == 0u) break;
-            const int k1 = min(k0 + 16, cnt);
-            for (int k = k0; k < k1; ++k) {
-                const uint32_t wm = sm.m[8 * k + warp];
+        for (int k0 = 0; k0 < cnt; k0 += 32) {
+            // the entries of this group that can change a pixel of the warp: footprint
+            // over one of its active pixels, layer at most the highest level still blending
+            const uint32_t wact = __reduce_or_sync(0xffffffffu, act);
+            if (wact == 0u) break;  // the whole warp is done
+            const uint32_t wlv = __reduce_or_sync(0xffffffffu, lv);
+            const int kq = k0 + lane;
+            const bool rel = kq < cnt && (sm.m[warp * 256 + kq] & wact) != 0u && (wlv >> lay[kq]) != 0u;
+            uint32_t todo = __ballot_sync(0xffffffffu, rel);
+            while (todo) {
+                const int k = k0 + __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const uint32_t wm = sm.m[warp * 256 + k];
                 if ((wm & act) == 0u) continue;
                 const uint32_t lm = lv & (0xffffffffu << lay[k]);  // active levels >= the entry's layer
                 if (!lm) continue;
@@ -139,6 +147,7 @@ __global__ void __launch_bounds__(256) k_blend_levels_bwd(
         uint32_t e[256];
         uint8_t lay[256];
         float wpart[32][8][9];
+        uint32_t wsuf[8][16];  // per warp: max over its pixels and levels l >= m of last[l]
         uint32_t last_max;
     };
     __shared__ __align__(16) Smem sm;
@@ -175,9 +184,18 @@ __global__ void __launch_bounds__(256) k_blend_levels_bwd(
         }
     }
     if (threadIdx.x == 0) sm.last_max = 0u;
+    {
+        uint32_t suf = 0u;
+#pragma unroll
+        for (int l = 15; l >= 0; --l) {
+            if (l < NL) suf = max(suf, __reduce_max_sync(0xffffffffu, last[l < NL ? l : 0]));
+            if (lane == 0) sm.wsuf[warp][l] = suf;
+        }
+    }
     __syncthreads();
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, my_last);
     if (lane == 0) atomicMax(&sm.last_max, wmax);
+    const uint32_t wpix = __ballot_sync(0xffffffffu, my_last != 0u);  // pixels of the warp with work
     __syncthreads();
     const int n_active = (int)sm.last_max;
     for (int hi = n_active; hi > 0; hi -= 256) {
@@ -199,21 +217,37 @@ __global__ void __launch_bounds__(256) k_blend_levels_bwd(
                 sm.b[threadIdx.x] = make_float2(bb.x, bb.y);
                 sm.c[threadIdx.x] = make_float4(bb.z, bb.w, c.x, a.z * kUnscaleDiag);
                 sm.d[threadIdx.x] = make_float2(a.w * kUnscaleOff, bb.x * kUnscaleDiag);
-                store_masks<TW>(&sm.m[8 * threadIdx.x], cm, rm);
+                store_masks_by_warp<TW>(sm.m, (int)threadIdx.x, cm, rm);
                 sm.e[threadIdx.x] = offsets[r] + entry_index(g, r4, tx, ty, rp, W, H);
-                sm.lay[threadIdx.x] = (uint8_t)min(__float_as_int(c.y), 31);
+                sm.lay[threadIdx.x] = (uint8_t)min(__float_as_int(c.y), 15);
             }
         }
         __syncthreads();
         for (int gtop = hi; gtop > lo; gtop -= 32) {
             const int gbot = max(gtop - 32, lo);
-            for (int k = gtop - 1; k >= gbot; --k) {
+            // entries of the group that a pixel of the warp blended at some level: footprint
+            // over a pixel with work, and a level >= the entry's layer still past it
+            const int kq = gbot + lane;
+            bool rel = false;
+            if (kq < gtop) {
+                const int sq = kq - lo;
+                rel = (sm.m[warp * 256 + sq] & wpix) != 0u && (uint32_t)kq < sm.wsuf[warp][sm.lay[sq]];
+                if (!rel) {
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) sm.wpart[lane][warp][c] = 0.f;
+                }
+            }
+            uint32_t todo = __ballot_sync(0xffffffffu, rel);
+            while (todo) {
+                const int j = 31 - __clz(todo);
+                todo &= ~(1u << j);
+                const int k = gbot + j;
                 const int s = k - lo;
                 float v[9];
 #pragma unroll
                 for (int c = 0; c < 9; ++c) v[c] = 0.f;
                 bool contrib = false;
-                const uint32_t wm = sm.m[8 * s + warp];
+                const uint32_t wm = sm.m[warp * 256 + s];
                 uint32_t lm = 0u;  // levels of this pixel that blended entry k
 #pragma unroll
                 for (int l = 0; l < NL; ++l)

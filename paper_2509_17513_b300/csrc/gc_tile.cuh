@@ -67,6 +67,14 @@ __device__ __forceinline__ void store_masks(uint32_t *m8, uint32_t cm, uint32_t 
                        warp_mask<TW>(cm, rm, 7));
 }
 
+// The same masks stored warp-major (m[w * 256 + t] for entry t), so that a warp reads
+// the masks of 32 consecutive entries with one conflict-free load.
+template <int TW>
+__device__ __forceinline__ void store_masks_by_warp(uint32_t *m, int t, uint32_t cm, uint32_t rm) {
+#pragma unroll
+    for (int w = 0; w < 8; ++w) m[w * 256 + t] = warp_mask<TW>(cm, rm, w);
+}
+
 // Shared staging of one batch of up to 256 list entries for the forward blend:
 //   a = {u, v, A, B}, b = {C, opacity}  (what every walked pair reads),
 //   c = {r, g, b, -}                    (read only when the pair is blended),
