@@ -59,7 +59,7 @@ constexpr size_t kOffNContrib = kOffFinalT + al(kMaxPixels * 4);
 constexpr size_t kOffWords = kOffNContrib + al(kMaxPixels * 4);
 constexpr size_t kOffSortScratch = kOffWords + 256;
 // radix histograms (256 per block of at least 2048 keys) + their scan partials, with slack
-constexpr size_t kSortScratchBytes = al((256 * ((kMaxKeys + 2047) / 2048) + 1024) * 4);
+constexpr size_t kSortScratchBytes = al((4 * (257 + 256 * ((kMaxKeys + 2047) / 2048)) + 1024) * 4);  // one-sweep layout
 constexpr size_t kScratchBytes = kOffSortScratch + kSortScratchBytes;
 
 }  // namespace

@@ -1,14 +1,24 @@
 // gc_sort.cu - exclusive scan and stable LSD radix sort of (uint32 key, uint32 value)
 // pairs, written for sm_103a.
 //
-// Neither routine waits on another CTA: the scan is reduce-then-scan (three
-// launches) and each radix digit is histogram -> scan -> scatter.  So no kernel
-// can hang on a missing predecessor, and every result is deterministic.
+// Two radix sorts share the tile ranking:
+//  * one-sweep (unsegmented sorts of up to 2^21 keys): one histogram kernel counts the digits of every pass
+//    in one read of the keys, then each pass is a single scatter launch in which a CTA
+//    takes the next tile from a ticket counter, publishes its digit counts and finds its
+//    global offsets by decoupled look-back over the tiles before it.  A CTA waits only on
+//    tiles with smaller tickets, which were taken by CTAs already running and which
+//    publish their counts before they wait themselves, so the waits always end; each is
+//    still bounded, and a wait that runs out sets the error word.
+//  * histogram -> scan -> scatter per digit (longer sorts, and the segmented sorts of the
+//    batched path, whose segments need per-segment offsets), where no CTA waits on another.
+// The scan is reduce-then-scan (three launches, or one CTA for short inputs).
 //
 // Scatter stability: each warp owns a contiguous segment of its CTA's tile
 // (kSortItems rows of 32 keys) and ranks its keys row by row (ballot multisplit),
-// so the global order of equal digits is (CTA, warp, row, lane) = input order.
+// so the global order of equal digits is (tile, warp, row, lane) = input order.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "gc_async.cuh"
 #include "gc_internal.cuh"
@@ -380,6 +390,212 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     }
 }
 
+
+// ---------------------------------------------------------------- one-sweep sort
+
+constexpr int kMaxPasses = 4;
+constexpr uint32_t kFlagAgg = 1u << 30;   // status word: tile's own digit count published
+constexpr uint32_t kFlagInc = 2u << 30;   // status word: inclusive prefix over tiles <= t
+constexpr uint32_t kValueMask = (1u << 30) - 1u;
+constexpr uint32_t kLookbackLimit = 1u << 22;  // polls per status word
+// One-sweep pays a look-back per tile; beyond this many keys the per-digit histogram
+// path is faster (its scatter is bound by shared-memory traffic either way).
+constexpr int64_t kOnesweepMaxKeys = int64_t(1) << 21;
+#ifndef GC_LOOK_WINDOW
+#define GC_LOOK_WINDOW 4
+#endif
+constexpr int kLookWindow = GC_LOOK_WINDOW;  // status words read per look-back round trip
+
+struct DigitPlan {
+    int passes;
+    int shift[kMaxPasses];
+    uint32_t mask[kMaxPasses];
+};
+
+// The status words carry their own payload (flag and count in one 32-bit word), so the
+// look-back needs no ordering beyond the word's own coherence: relaxed accesses suffice.
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Digit counts of every pass over all keys: ghist[pass * 256 + digit].  Per-warp shared
+// histograms, grid-stride over 16-byte groups of keys.
+__global__ void __launch_bounds__(kSortThreads) k_onesweep_hist(const uint32_t *__restrict__ keys,
+                                                                const uint32_t *n_dev, int64_t n_max,
+                                                                DigitPlan plan, uint32_t *__restrict__ ghist) {
+    __shared__ uint32_t wh[kWarps][kMaxPasses][256];
+    const int warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < kWarps * kMaxPasses * 256; k += kSortThreads) (&wh[0][0][0])[k] = 0;
+    __syncthreads();
+    const int64_t n = device_count(n_dev, n_max);
+    const int64_t n4 = n >> 2;
+    const uint4 *k4 = reinterpret_cast<const uint4 *>(keys);
+    auto count = [&](uint32_t key) {
+#pragma unroll
+        for (int p = 0; p < kMaxPasses; ++p)
+            if (p < plan.passes) atomicAdd(&wh[warp][p][(key >> plan.shift[p]) & plan.mask[p]], 1u);
+    };
+    for (int64_t i = (int64_t)blockIdx.x * kSortThreads + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * kSortThreads) {
+        const uint4 q = k4[i];
+        count(q.x);
+        count(q.y);
+        count(q.z);
+        count(q.w);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) count(keys[(n4 << 2) + threadIdx.x]);
+    __syncthreads();
+    for (int p = 0; p < plan.passes; ++p) {
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) tot += wh[w][p][threadIdx.x];
+        if (tot) atomicAdd(&ghist[p * 256 + threadIdx.x], tot);
+    }
+}
+
+// One pass: a CTA per tile of kSortTile keys, tiles taken in ticket order.  status holds
+// one word per (tile, digit), zero before the pass.
+__global__ void __launch_bounds__(kSortThreads) k_onesweep_scatter(
+    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+    uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *n_dev,
+    int64_t n_max, int shift, uint32_t mask, const uint32_t *__restrict__ ghist, uint32_t *status,
+    uint32_t *ticket, uint32_t *err) {
+    __shared__ __align__(128) uint32_t sk[kSortTile];
+    __shared__ __align__(128) uint32_t sv[kSortTile];
+    __shared__ uint32_t wcnt[kWarps][256];
+    __shared__ uint32_t dstart[256];
+    __shared__ uint32_t gbase[256];
+    __shared__ uint32_t ws[33];
+    __shared__ int s_tile;
+    __shared__ __align__(8) uint64_t bar;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n = device_count(n_dev, n_max);
+    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    const int bits = __popc(mask);
+    const uint32_t lt = lanemask_lt();
+    if (threadIdx.x == 0) {
+        s_tile = (int)atomicAdd(ticket, 1u);
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) return;
+    const int64_t base = (int64_t)t * kSortTile;
+    const int nvalid = (int)((n - base) < kSortTile ? (n - base) : kSortTile);
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)((nvalid * 4 + 15) & ~15);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&bar, 2 * bytes);
+        bulk_copy_g2s(sk, keys_in + base, bytes, &bar);
+        bulk_copy_g2s(sv, vals_in + base, bytes, &bar);
+    }
+    for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wcnt[0][0])[k] = 0;
+    // global start of every digit (exclusive scan of the pass histogram), while the tile lands
+    uint32_t gtot;
+    const uint32_t gstart = block_exclusive_scan<kSortThreads>(ghist[threadIdx.x], ws, &gtot);
+    const bool ok = mbar_wait_bounded(&bar, 0u);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, kErrTimeout);
+            mbar_wait_bounded(&bar, 0u);
+        }
+        // publish an (empty) inclusive prefix so that no later tile waits on this one
+        status[(size_t)t * 256 + threadIdx.x] = kFlagInc;
+        return;
+    }
+    uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
+    const int wseg = warp * (32 * kSortItems);
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int li = wseg + r * 32 + lane;
+        const bool valid = li < nvalid;
+        key[r] = valid ? sk[li] : 0xffffffffu;
+        val[r] = valid ? sv[li] : 0u;
+        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        const uint32_t d = (key[r] >> shift) & mask;
+        const uint32_t peers = bits < 8 ? __match_any_sync(0xffffffffu, d) & vmask : digit_peers(d, bits, vmask);
+        const uint32_t before = valid ? wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) wcnt[warp][d] = before + (uint32_t)__popc(peers);
+        __syncwarp();
+        loc[r] = before + (uint32_t)__popc(peers & lt);
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t x = wcnt[w][d];
+            wcnt[w][d] = c;
+            c += x;
+        }
+        // publish this tile's count of digit d, then look back for the tiles before it
+        uint32_t *my = status + (size_t)t * 256 + d;
+        uint32_t excl = 0;
+        if (t == 0) {
+            st_relaxed(my, kFlagInc | c);
+        } else {
+            st_relaxed(my, kFlagAgg | c);
+            // kLookWindow predecessors per round trip, nearest first; before tile 0 the
+            // sentinel (inclusive, count 0) ends the walk
+            bool done = false;
+            for (int q = t - 1; !done; q -= kLookWindow) {
+                uint32_t v[kLookWindow];
+#pragma unroll
+                for (int i = 0; i < kLookWindow; ++i)
+                    v[i] = q - i >= 0 ? ld_relaxed(status + (size_t)(q - i) * 256 + d) : kFlagInc;
+#pragma unroll
+                for (int i = 0; i < kLookWindow; ++i) {
+                    if (done) break;
+                    uint32_t x = v[i];
+                    for (uint32_t it = 0; (x & ~kValueMask) == 0u; ++it) {
+                        if (it >= kLookbackLimit) {
+                            atomicOr(err, kErrTimeout);
+                            x = kFlagInc;
+                            break;
+                        }
+                        x = ld_relaxed(status + (size_t)(q - i) * 256 + d);
+                    }
+                    excl += x & kValueMask;
+                    done = (x & kFlagInc) != 0u;
+                }
+            }
+            st_relaxed(my, kFlagInc | (excl + c));
+        }
+        uint32_t tot;
+        dstart[d] = block_exclusive_scan<kSortThreads>(c, ws, &tot);
+        gbase[d] = gstart + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int li = wseg + r * 32 + lane;
+        if (li < nvalid) {
+            const uint32_t d = (key[r] >> shift) & mask;
+            const uint32_t pos = dstart[d] + wcnt[warp][d] + loc[r];
+            sk[pos] = key[r];
+            sv[pos] = val[r];
+        }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < nvalid; p += kSortThreads) {
+        const uint32_t k = sk[p];
+        const uint32_t d = (k >> shift) & mask;
+        const uint32_t o = gbase[d] + (uint32_t)p - dstart[d];
+        if (keys_out) keys_out[o] = k;
+        vals_out[o] = sv[p];
+    }
+}
+
 }  // namespace
 
 size_t scan_partials_size(int64_t n) { return (size_t)((n + kScanChunk - 1) / kScanChunk) + 1; }
@@ -408,10 +624,17 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
 
 int radix_tile_keys() { return kSortTile; }
 
+// Classic layout: per-block digit counts + scan partials.  One-sweep layout: per pass
+// 256 digit counts, a ticket and 256 status words per tile.
+static size_t onesweep_words(int64_t nb, int passes) {
+    return (size_t)passes * (256 + 1 + (size_t)256 * nb);
+}
+
 size_t radix_scratch_words(int64_t n_max) {
     int64_t nb = (n_max + kSortTile - 1) / kSortTile;
     if (nb < 1) nb = 1;
-    return (size_t)(256 * nb) + scan_partials_size(256 * nb);
+    const size_t classic = (size_t)(256 * nb) + scan_partials_size(256 * nb);
+    return n_max <= kOnesweepMaxKeys ? std::max(classic, onesweep_words(nb, kMaxPasses)) : classic;
 }
 
 cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
@@ -424,11 +647,44 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
         return cudaSuccess;
     }
     const int nblocks = (int)((n_max + kSortTile - 1) / kSortTile);
+    const int passes = (end_bit + 7) / 8;
+    if (!seg_block0 && n_max <= kOnesweepMaxKeys && passes <= kMaxPasses) {
+        // one-sweep: zero the counts, tickets and status words; one histogram kernel;
+        // one scatter launch per pass
+        DigitPlan plan;
+        plan.passes = passes;
+        int sh = 0;
+        for (int p = 0; p < kMaxPasses; ++p) {
+            const int bits = p < passes ? (end_bit - sh + (passes - p) - 1) / (passes - p) : 0;
+            plan.shift[p] = sh;
+            plan.mask[p] = bits ? (1u << bits) - 1u : 0u;
+            sh += bits;
+        }
+        uint32_t *ghist = scratch;
+        uint32_t *tickets = ghist + 256 * passes;
+        uint32_t *status = tickets + passes;
+        cudaError_t e = cudaMemsetAsync(scratch, 0, 4 * onesweep_words(nblocks, passes), st);
+        if (e != cudaSuccess) return e;
+        const int64_t groups = (n_max + 3) / 4;
+        int hgrid = (int)std::min<int64_t>((groups + kSortThreads * 4 - 1) / (kSortThreads * 4), 148 * 4);
+        if (hgrid < 1) hgrid = 1;
+        k_onesweep_hist<<<hgrid, kSortThreads, 0, st>>>(keys[cur], n_dev, n_max, plan, ghist);
+        note_launches(1);
+        for (int p = 0; p < passes; ++p) {
+            const bool last = p == passes - 1;
+            k_onesweep_scatter<<<nblocks, kSortThreads, 0, st>>>(
+                keys[cur], vals[cur], (last && !keys_out) ? nullptr : keys[cur ^ 1], vals[cur ^ 1], n_dev, n_max,
+                plan.shift[p], plan.mask[p], ghist + 256 * p, status + (size_t)256 * nblocks * p, tickets + p, err);
+            note_launches(1);
+            cur ^= 1;
+        }
+        *out_buf = cur;
+        return cudaGetLastError();
+    }
     const int grid = nblocks < 148 * 4 ? nblocks : 148 * 4;
     uint32_t *counts = scratch;
     uint32_t *partials = scratch + (size_t)256 * nblocks;
     // balanced digit widths: ceil(end_bit / 8) passes of nearly equal width
-    const int passes = (end_bit + 7) / 8;
     int shift = 0;
     for (int pass = 0; pass < passes; ++pass) {
         const int bits = (end_bit - shift + (passes - pass) - 1) / (passes - pass);
