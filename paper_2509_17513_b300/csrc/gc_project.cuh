@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "gc_blend.cuh"
+#include "gc_exact.cuh"
 #include "gc_internal.cuh"
 #include "gc_sh.cuh"
 
@@ -81,8 +82,8 @@ struct Proj {
 __device__ __forceinline__ float4 gaussian_activation(const GaussSrc &G, int64_t i) {
     Attr A;
     load_attr(G, i, A);
-    return make_float4((float)exp((double)A.ls[0]), (float)exp((double)A.ls[1]), (float)exp((double)A.ls[2]),
-                       (float)(2.0 * log(255.0 / (1.0 + exp(-(double)A.logit)))));
+    return make_float4(exp_f32_of_f64(A.ls[0]), exp_f32_of_f64(A.ls[1]), exp_f32_of_f64(A.ls[2]),
+                       tau_f32_of_f64(A.logit));
 }
 
 // act: NULL, or the cached gaussian_activation of every Gaussian (bit-identical results).
@@ -131,7 +132,7 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
         R[0] = fsub(1.f, fmul(2.f, fadd(yy, zz))); R[1] = fmul(2.f, fsub(xy, wz)); R[2] = fmul(2.f, fadd(xz, wy));
         R[3] = fmul(2.f, fadd(xy, wz)); R[4] = fsub(1.f, fmul(2.f, fadd(xx, zz))); R[5] = fmul(2.f, fsub(yz, wx));
         R[6] = fmul(2.f, fsub(xz, wy)); R[7] = fmul(2.f, fadd(yz, wx)); R[8] = fsub(1.f, fmul(2.f, fadd(xx, yy)));
-        // 5. scales, correctly rounded to FP32 through FP64
+        // 5. scales: the FP32 rounding of the FP64 exponential
         float s[3];
         float4 av;
         if (act) {
@@ -141,7 +142,7 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
             s[2] = av.z;
         } else {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) s[k] = (float)exp((double)A.ls[k]);
+            for (int k = 0; k < 3; ++k) s[k] = exp_f32_of_f64(A.ls[k]);
         }
         // 6-7. M = R diag(s), Sigma = M M^T
         float M[9];
@@ -224,7 +225,7 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
         //     has half-extents sqrt(tau_c ic / det_c), sqrt(tau_c ia / det_c)
         float tc_out = 0.f;
         if (rp.alpha_cull) {
-            const float tau = act ? av.w : (float)(2.0 * log(255.0 / (1.0 + exp(-(double)A.logit))));
+            const float tau = act ? av.w : tau_f32_of_f64(A.logit);
             if (!(tau > 0.f)) break;  // opacity <= 1/255: never blended
             const float t1 = fadd(rf, 1.f);
             const float mt = fmul(fadd(fadd(ia, fmul(2.f, fabsf(ib))), ic), fmul(t1, t1));
