@@ -70,7 +70,8 @@ class SceneS(C.Structure):
 
 
 class MotionS(C.Structure):
-    _fields_ = [("n_groups", C.c_int32), ("q", C.c_void_p), ("t", C.c_void_p)]
+    _fields_ = [("n_groups", C.c_int32), ("q", C.c_void_p), ("t", C.c_void_p),
+                ("res_ls", C.c_void_p), ("res_logit", C.c_void_p), ("res_sh", C.c_void_p)]
 
 
 def lib():
@@ -164,7 +165,10 @@ def _scene(pk: _Pack, scene) -> SceneS:
     return s
 
 
-def _motion(pk: _Pack, motion, frame: int):
+def _motion(pk: _Pack, motion, frame: int, residual=None):
+    """Frame `frame` of the group motion (None: keyframe, identity) and, optionally, that
+    frame's residual deformation (an object with ls (n,3), logit (n,) and sh (n,K,3)
+    arrays, any of them None; Sec. 3.2, Eq. 7)."""
     m = MotionS()
     if motion is None:
         m.n_groups = 1
@@ -174,6 +178,10 @@ def _motion(pk: _Pack, motion, frame: int):
         m.n_groups = motion.q.shape[1]
         m.q = _ptr(pk.f32(motion.q[frame]))
         m.t = _ptr(pk.f32(motion.t[frame]))
+    if residual is not None:
+        m.res_ls = _ptr(pk.f32(residual.ls)) if residual.ls is not None else None
+        m.res_logit = _ptr(pk.f32(residual.logit)) if residual.logit is not None else None
+        m.res_sh = _ptr(pk.f32(residual.sh)) if residual.sh is not None else None
     return m
 
 
@@ -183,8 +191,9 @@ def selection(scene, layer_mask: int) -> np.ndarray:
     return np.concatenate(parts) if parts else np.zeros(0, np.int64)
 
 
-def bin_f32(scene, motion, frame, cam, opts: dict, layer_mask: int = 1) -> dict:
+def bin_f32(scene, motion, frame, cam, opts: dict, layer_mask: int = 1, residual=None) -> dict:
     """FP32 binning mirror over the selected Gaussians (arrays by selected position).
+    ``residual``: the frame's residual deformation (see ``_motion``), or None.
 
     ``row_off`` / ``row_a`` / ``row_b``: for visible position j, its tile rows
     trect[j, 2] .. trect[j, 3] are entries row_off[j] .. row_off[j+1]-1, each the
@@ -198,7 +207,7 @@ def bin_f32(scene, motion, frame, cam, opts: dict, layer_mask: int = 1) -> dict:
            "rect": np.zeros((n, 4), np.int32), "trect": np.zeros((n, 4), np.int32),
            "radius": np.zeros(n, np.int32), "uv": np.zeros((n, 2), np.float32),
            "conic": np.zeros((n, 3), np.float32), "tc": np.zeros(n, np.float32)}
-    sc, mo, ca, op = _scene(pk, scene), _motion(pk, motion, frame), _camera(cam), _options(opts)
+    sc, mo, ca, op = _scene(pk, scene), _motion(pk, motion, frame, residual), _camera(cam), _options(opts)
     L.gco_bin_f32(C.byref(sc), C.byref(mo), C.byref(ca), C.byref(op), _ptr(sel), n,
                   _ptr(out["visible"]), _ptr(out["depth"]), _ptr(out["rect"]), _ptr(out["trect"]),
                   _ptr(out["radius"]), _ptr(out["uv"]), _ptr(out["conic"]), _ptr(out["tc"]))
@@ -215,20 +224,21 @@ def bin_f32(scene, motion, frame, cam, opts: dict, layer_mask: int = 1) -> dict:
 
 
 def render(scene, motion, frame, cam, opts: dict, layer_mask: int = 1, pixels=None,
-           bins: dict | None = None) -> dict:
+           bins: dict | None = None, residual=None) -> dict:
     """FP64 render.  ``pixels``: optional (n, 2) int (x, y) sample list.
 
     Returns ``image`` (3, H, W) or (n, 3) for samples, ``T`` (final
     transmittance), ``n_blended``, ``ambiguous`` (a decision within the FP32
     margin), ``signature`` and the binning mirror output ``bins``.
-    ``bins`` may be given to freeze the discrete decisions.
+    ``bins`` may be given to freeze the discrete decisions.  ``residual``: the frame's
+    residual deformation (Sec. 3.2, Eq. 7), or None.
     """
     L = lib()
     pk = _Pack()
     if bins is None:
-        bins = bin_f32(scene, motion, frame, cam, opts, layer_mask)
+        bins = bin_f32(scene, motion, frame, cam, opts, layer_mask, residual)
     sel = bins["sel"]
-    sc, mo, ca, op = _scene(pk, scene), _motion(pk, motion, frame), _camera(cam), _options(opts)
+    sc, mo, ca, op = _scene(pk, scene), _motion(pk, motion, frame, residual), _camera(cam), _options(opts)
     W, H = int(cam.width), int(cam.height)
     if pixels is None:
         npx = 0
@@ -263,21 +273,23 @@ def render(scene, motion, frame, cam, opts: dict, layer_mask: int = 1, pixels=No
 
 
 def grad(scene, motion, frame, cam, opts: dict, dL_dimage, layer_mask: int = 1,
-         bins: dict | None = None) -> dict:
+         bins: dict | None = None, residual=None) -> dict:
     """FP64 gradient of L = sum(dL_dimage * image) w.r.t. every input.
 
     Gradients are returned for the full scene arrays (zero outside the
     selection and for culled Gaussians) plus the group motion table of the
     frame, and the per-Gaussian 2D gradient ``d2d`` (du, dv, dconic a/b/c,
-    dopacity, drgb) by selected position.
+    dopacity, drgb) by selected position.  With a ``residual`` (Sec. 3.2, Eq. 7) the
+    log-scale, logit and SH gradients are those of the deformed attributes, which are
+    also the gradients of the residuals (they enter additively).
     """
     L = lib()
     pk = _Pack()
     if bins is None:
-        bins = bin_f32(scene, motion, frame, cam, opts, layer_mask)
+        bins = bin_f32(scene, motion, frame, cam, opts, layer_mask, residual)
     sel = bins["sel"]
     n_sel = sel.shape[0]
-    sc, mo, ca, op = _scene(pk, scene), _motion(pk, motion, frame), _camera(cam), _options(opts)
+    sc, mo, ca, op = _scene(pk, scene), _motion(pk, motion, frame, residual), _camera(cam), _options(opts)
     K = (scene.sh_degree + 1) ** 2
     G = motion.q.shape[1] if motion is not None else 1
     g = np.ascontiguousarray(dL_dimage, np.float64).reshape(3, cam.height, cam.width)
@@ -380,9 +392,9 @@ def sh_eval(deg: int, dirs, with_grad: bool = False):
     return (Y, dY) if with_grad else Y
 
 
-def geom(scene, motion, frame, cam, opts: dict, i: int) -> dict:
+def geom(scene, motion, frame, cam, opts: dict, i: int, residual=None) -> dict:
     pk = _Pack()
-    sc, mo, ca, op = _scene(pk, scene), _motion(pk, motion, frame), _camera(cam), _options(opts)
+    sc, mo, ca, op = _scene(pk, scene), _motion(pk, motion, frame, residual), _camera(cam), _options(opts)
     out = np.zeros(28)
     lib().gco_geom_f64(C.byref(sc), C.byref(mo), C.byref(ca), C.byref(op), int(i), _ptr(out))
     return {"u": out[0], "v": out[1], "sigma2": np.array([[out[2], out[3]], [out[3], out[4]]]),

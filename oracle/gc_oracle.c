@@ -70,7 +70,43 @@ typedef struct {
     int32_t n_groups;
     const float *q;  /* G x 4 unit (w, x, y, z), or NULL: identity motion */
     const float *t;  /* G x 3 */
+    /* Residual deformation of this frame (Sec. 3.2, Eq. 7: s_t = s_{t-1} + ds_t,
+       alpha_t = alpha_{t-1} + dalpha_t, f_t = f_{t-1} + df_t), cumulative from the
+       keyframe and indexed by global Gaussian; each may be NULL (no residual).  Read as
+       additive in log-scale, opacity-logit and SH-coefficient space. */
+    const float *res_ls;     /* n x 3 */
+    const float *res_logit;  /* n */
+    const float *res_sh;     /* n x K x 3 */
 } gco_motion;
+
+/* Deformed log-scale k, opacity logit and SH coefficient e (= 3 k + channel) of global
+   Gaussian i: exact FP64 sums for the FP64 renderer ... */
+static double ls_d(const gco_scene *sc, const gco_motion *mo, int64_t i, int k) {
+    double v = sc->log_scales[3 * i + k];
+    if (mo && mo->res_ls) v += (double)mo->res_ls[3 * i + k];
+    return v;
+}
+static double logit_d(const gco_scene *sc, const gco_motion *mo, int64_t i) {
+    double v = sc->opacity_logits[i];
+    if (mo && mo->res_logit) v += (double)mo->res_logit[i];
+    return v;
+}
+static double sh_d(const gco_scene *sc, const gco_motion *mo, int64_t i, int K, int e) {
+    double v = sc->sh[i * K * 3 + e];
+    if (mo && mo->res_sh) v += (double)mo->res_sh[i * K * 3 + e];
+    return v;
+}
+/* ... and single FP32 additions for the binning mirror (binning specification). */
+static float ls_f(const gco_scene *sc, const gco_motion *mo, int64_t i, int k) {
+    float v = sc->log_scales[3 * i + k];
+    if (mo && mo->res_ls) v = v + mo->res_ls[3 * i + k];
+    return v;
+}
+static float logit_f(const gco_scene *sc, const gco_motion *mo, int64_t i) {
+    float v = sc->opacity_logits[i];
+    if (mo && mo->res_logit) v = v + mo->res_logit[i];
+    return v;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Quaternions and rotations (FP64)                                          */
@@ -219,7 +255,7 @@ typedef struct {
 static void bin_one_f32(const gco_scene *sc, const gco_motion *mo, const gco_camera *cam,
                         const gco_options *op, int64_t i, gco_bin *out) {
     memset(out, 0, sizeof *out);
-    const float *mu = sc->means + 3 * i, *ls = sc->log_scales + 3 * i, *qq = sc->quats + 4 * i;
+    const float *mu = sc->means + 3 * i, *qq = sc->quats + 4 * i;
     int g = sc->group_id ? sc->group_id[i] : 0;
     float gq[4] = {1.0f, 0.0f, 0.0f, 0.0f}, gt[3] = {0.0f, 0.0f, 0.0f};
     if (mo && mo->q) {
@@ -249,7 +285,7 @@ static void bin_one_f32(const gco_scene *sc, const gco_motion *mo, const gco_cam
     R[6] = 2.0f * (xz - wy); R[7] = 2.0f * (yz + wx); R[8] = 1.0f - 2.0f * (xx + yy);
     /* 5. scales */
     float s[3];
-    for (int k = 0; k < 3; ++k) s[k] = (float)exp((double)ls[k]);
+    for (int k = 0; k < 3; ++k) s[k] = (float)exp((double)ls_f(sc, mo, i, k));
     /* 6. M = R diag(s) */
     float M[9];
     for (int r = 0; r < 3; ++r)
@@ -324,7 +360,7 @@ static void bin_one_f32(const gco_scene *sc, const gco_motion *mo, const gco_cam
        sqrt(tau_c ic / det_c) and sqrt(tau_c ia / det_c); the rectangle is clipped to
        them.  Opacity <= 1/255: the Gaussian is never blended and is not binned. */
     if (op->alpha_cull) {
-        float tau = (float)(2.0 * log(255.0 / (1.0 + exp(-(double)sc->opacity_logits[i]))));
+        float tau = (float)(2.0 * log(255.0 / (1.0 + exp(-(double)logit_f(sc, mo, i)))));
         if (!(tau > 0.0f)) return;
         float t1 = rf + 1.0f;
         float mt = ((ia + 2.0f * fabsf(ib)) + ic) * (t1 * t1);
@@ -456,7 +492,7 @@ typedef struct {
 
 static void geom_d(const gco_scene *sc, const gco_motion *mo, const gco_camera *cam,
                    const gco_options *op, int64_t i, gc_geom *G) {
-    const float *mu = sc->means + 3 * i, *ls = sc->log_scales + 3 * i, *qq = sc->quats + 4 * i;
+    const float *mu = sc->means + 3 * i, *qq = sc->quats + 4 * i;
     int g = sc->group_id ? sc->group_id[i] : 0;
     double gq[4] = {1, 0, 0, 0}, gt[3] = {0, 0, 0};
     if (mo && mo->q) {
@@ -469,7 +505,7 @@ static void geom_d(const gco_scene *sc, const gco_motion *mo, const gco_camera *
     G->pn = sqrt(G->p[0] * G->p[0] + G->p[1] * G->p[1] + G->p[2] * G->p[2] + G->p[3] * G->p[3]);
     for (int k = 0; k < 4; ++k) G->qn[k] = G->p[k] / G->pn;
     quat_to_rot_d(G->qn, G->R);
-    for (int k = 0; k < 3; ++k) G->s[k] = exp((double)ls[k]);
+    for (int k = 0; k < 3; ++k) G->s[k] = exp(ls_d(sc, mo, i, k));
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) G->M[3 * r + c] = G->R[3 * r + c] * G->s[c];
     for (int r = 0; r < 3; ++r)
@@ -509,17 +545,16 @@ static void geom_d(const gco_scene *sc, const gco_motion *mo, const gco_camera *
     G->conic[0] = G->C / G->det; G->conic[1] = -G->B / G->det; G->conic[2] = G->A / G->det;
     G->u = fx * G->xoz + cam->cx;
     G->v = fy * G->yoz + cam->cy;
-    G->o = 1.0 / (1.0 + exp(-(double)sc->opacity_logits[i]));
+    G->o = 1.0 / (1.0 + exp(-logit_d(sc, mo, i)));
     double dv[3];
     for (int k = 0; k < 3; ++k) dv[k] = G->mup[k] - (double)cam->campos[k];
     G->dnorm = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
     for (int k = 0; k < 3; ++k) G->dir[k] = dv[k] / G->dnorm;
     G->K = (sc->sh_degree + 1) * (sc->sh_degree + 1);
     sh_eval_d(sc->sh_degree, G->dir, G->Y, NULL);
-    const float *f = sc->sh + (int64_t)i * G->K * 3;
     for (int ch = 0; ch < 3; ++ch) {
         double acc = 0;
-        for (int k = 0; k < G->K; ++k) acc += G->Y[k] * (double)f[3 * k + ch];
+        for (int k = 0; k < G->K; ++k) acc += G->Y[k] * sh_d(sc, mo, i, G->K, 3 * k + ch);
         G->raw[ch] = acc + 0.5;
         G->rgb[ch] = G->raw[ch] > 0 ? G->raw[ch] : 0.0;
     }
@@ -823,13 +858,12 @@ API int gco_grad_f64(const gco_scene *sc, const gco_motion *mo, const gco_camera
         for (int ch = 0; ch < 3; ++ch) draw[ch] = G->raw[ch] > 0 ? d[6 + ch] : 0.0;
         double Y[16], dY[48];
         sh_eval_d(sc->sh_degree, G->dir, Y, dY);
-        const float *f = sc->sh + sel[j] * K * 3;
         double ddir[3] = {0, 0, 0};
         for (int k = 0; k < K; ++k) {
             double s_k = 0;
             for (int ch = 0; ch < 3; ++ch) {
                 d_sh[(j * K + k) * 3 + ch] = Y[k] * draw[ch];
-                s_k += (double)f[3 * k + ch] * draw[ch];
+                s_k += sh_d(sc, mo, sel[j], K, 3 * k + ch) * draw[ch];
             }
             for (int a = 0; a < 3; ++a) ddir[a] += s_k * dY[3 * k + a];
         }

@@ -88,6 +88,43 @@ class Motion:
 
 
 @dataclass
+class Residual:
+    """Residual deformation of one frame (Sec. 3.2, Eq. 7), cumulative from the keyframe:
+    offsets added to the log-scales, opacity logits and SH coefficients before activation.
+    Any field may be None (no residual for that attribute)."""
+
+    ls: np.ndarray | None      # (n, 3) float32
+    logit: np.ndarray | None   # (n,) float32
+    sh: np.ndarray | None      # (n, K, 3) float32
+
+
+def random_residual(seed: int, n: int, sh_degree: int, frame: int, ls_sigma=0.01, logit_sigma=0.05,
+                    sh_sigma=0.01) -> Residual:
+    """Residuals of frame `frame` of a random walk with independent N(0, sigma^2) steps per
+    frame (the paper observes Gaussian-distributed residual attributes, Sec. 3.3): the
+    cumulative offset is N(0, frame sigma^2) per attribute; the keyframe (frame 0) has none."""
+    rng = np.random.default_rng([seed, frame])
+    k = _sh_count(sh_degree)
+    sd = np.sqrt(max(frame, 0))
+    return Residual(ls=(rng.normal(0.0, ls_sigma * sd, (n, 3))).astype(np.float32),
+                    logit=(rng.normal(0.0, logit_sigma * sd, n)).astype(np.float32),
+                    sh=(rng.normal(0.0, sh_sigma * sd, (n, k, 3))).astype(np.float32))
+
+
+def apply_residual(scene: "Scene", res: Residual) -> "Scene":
+    """The scene with the residuals added in FP32 (one rounding per attribute)."""
+    import dataclasses
+    out = dataclasses.replace(scene)
+    if res.ls is not None:
+        out.log_scales = (scene.log_scales + res.ls).astype(np.float32)
+    if res.logit is not None:
+        out.opacity_logits = (scene.opacity_logits + res.logit).astype(np.float32)
+    if res.sh is not None:
+        out.sh = (scene.sh + res.sh).astype(np.float32)
+    return out
+
+
+@dataclass
 class Camera:
     """Pinhole camera, OpenCV axes (x right, y down, z forward).
 
