@@ -105,11 +105,21 @@ typedef struct {
                                         order means, log_scales, quats, opacity, sh (k-major, rgb) */
 } gc_gaussians;
 
-/* Cumulative per-group rigid motion of one frame (device arrays). */
+/* One frame (device arrays): the cumulative per-group rigid motion (Sec. 3.2, rigid
+ * transformation) and, optionally, the frame's residual deformation (Sec. 3.2, Eq. 7:
+ * s_t = s_{t-1} + ds_t, alpha_t = alpha_{t-1} + dalpha_t, f_t = f_{t-1} + df_t), cumulative
+ * from the keyframe.  The residuals are added, one FP32 addition each, to the log-scales,
+ * the opacity logits and the SH coefficients before activation; each array may be NULL
+ * (no residual for that attribute), and q, t may both be NULL (no group motion).  A
+ * backward with residuals returns the gradients of the deformed attributes, which are
+ * also the gradients of the residuals (they enter additively). */
 typedef struct {
     int32_t n_groups;   /* G >= 1 */
     const float *q;     /* G x 4 unit quaternions; q' = q_g (x) q */
     const float *t;     /* G x 3 translations; mu' = mu + t_g */
+    const float *res_log_scales;     /* n x 3 FP32, or NULL */
+    const float *res_opacity_logits; /* n FP32, or NULL */
+    const float *res_sh;             /* n x K x 3 FP32 (the set's K), or NULL */
 } gc_motion;
 
 /* Pinhole camera (host, by value). X_cam = R X_world + t. */

@@ -49,7 +49,8 @@ class Gaussians(C.Structure):
 
 
 class Motion(C.Structure):
-    _fields_ = [("n_groups", C.c_int32), ("q", C.c_void_p), ("t", C.c_void_p)]
+    _fields_ = [("n_groups", C.c_int32), ("q", C.c_void_p), ("t", C.c_void_p),
+                ("res_log_scales", C.c_void_p), ("res_opacity_logits", C.c_void_p), ("res_sh", C.c_void_p)]
 
 
 class Camera(C.Structure):

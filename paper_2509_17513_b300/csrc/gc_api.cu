@@ -163,7 +163,8 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
     S.n_sel = n_sel;
     S.sh_degree = g->sh_degree;
     S.n_groups = src.n_groups;
-    S.has_motion = motion != nullptr;
+    S.has_motion = src.group_q != nullptr;
+    S.res = src.res;
     S.n_layers = g->n_layers;
     for (int l = 0; l <= g->n_layers; ++l) S.layer_offsets[l] = g->layer_offsets[l];
     S.layer_mask = layer_mask;
@@ -454,8 +455,10 @@ static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, co
     if (st != GC_OK) return st;
     if (g->n != S.n || g->sh_degree != S.sh_degree || g->n_layers != S.n_layers)
         return fail(ctx, GC_ERR_STATE, "the Gaussian set differs from the one of the saved forward");
-    if ((motion != nullptr) != S.has_motion || (motion && motion->n_groups != S.n_groups))
+    if ((src.group_q != nullptr) != S.has_motion || (S.has_motion && src.n_groups != S.n_groups))
         return fail(ctx, GC_ERR_STATE, "the motion differs from the one of the saved forward");
+    if (src.res.ls != S.res.ls || src.res.logit != S.res.logit || src.res.sh != S.res.sh)
+        return fail(ctx, GC_ERR_STATE, "the residual deformation differs from the one of the saved forward");
     DeviceGuard dg(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int K3 = 3 * (g->sh_degree + 1) * (g->sh_degree + 1);

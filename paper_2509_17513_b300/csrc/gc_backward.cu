@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(GaussSrc G, Selection se
     float m7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (touched[j] != 0) {
         const int g = (G.group_q && G.group_id) ? G.group_id[i] : 0;
-        chain_rule(G, i, G.group_q, G.group_t, g, cam, rp, g2d + 9 * j, acc, m7);
+        chain_rule(G, i, G.group_q, G.group_t, g, cam, rp, g2d + 9 * j, acc, m7, G.res);
     }
     if (out.d_means) for (int k = 0; k < 3; ++k) out.d_means[3 * i + k] = acc.dmu[k];
     if (out.d_log_scales) for (int k = 0; k < 3; ++k) out.d_log_scales[3 * i + k] = acc.dls[k];

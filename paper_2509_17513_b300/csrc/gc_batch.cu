@@ -38,6 +38,7 @@ struct __align__(16) BatchReq {
     int n_groups;
     int frame;
     float *image;
+    Residual res;  // the frame's residual deformation
 };
 
 namespace {
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(256, 4) k_batch_preprocess(GaussSrc G, const B
     vals[item] = (uint32_t)item;
     Proj P;
     if (j < R.n_sel) {
-        project_gaussian(G, sel_global(R.sel, j), R.group_q, R.group_t, R.n_groups, R.cam, R.rp, P, act);
+        project_gaussian(G, sel_global(R.sel, j), R.group_q, R.group_t, R.n_groups, R.cam, R.rp, P, act, R.res);
     } else {
         P.key = kCulledKey;
         P.ntouch = 0;
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(128) k_batch_preprocess_bwd(GaussSrc G, const 
         if (j < 0) continue;
         const int64_t item = R.item_base + j;
         float m7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (touched[item] != 0) chain_rule(G, i, R.group_q, R.group_t, g, R.cam, R.rp, g2d + 9 * item, acc, m7);
+        if (touched[item] != 0) chain_rule(G, i, R.group_q, R.group_t, g, R.cam, R.rp, g2d + 9 * item, acc, m7, R.res);
         if (mcontrib)
             for (int k = 0; k < 7; ++k) mcontrib[7 * item + k] = m7[k];
     }
@@ -597,6 +598,8 @@ gc_status build_table(gc_context *ctx, const gc_gaussians *g, const gc_motion *f
             R.group_q = frames[rq.frame].q;
             R.group_t = frames[rq.frame].t;
             R.n_groups = n_groups;
+            R.res = gc::Residual{frames[rq.frame].res_log_scales, frames[rq.frame].res_opacity_logits,
+                                 frames[rq.frame].res_sh};
         }
         R.image = rq.image;
     }
@@ -749,11 +752,18 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     const int64_t *ib_dev = B.item_base.as<int64_t>(), *tb_dev = B.tile_base.as<int64_t>();
     uint32_t *scratch = B.scratch.as<uint32_t>();
     if (items > 0) {
-        gc::k_batch_activate<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(src, g->n, B.act.as<float4>());
+        // the per-Gaussian activation cache holds keyframe values: not with scale or opacity residuals
+        bool deformed = false;
+        for (const auto &R : tab) deformed = deformed || R.res.ls || R.res.logit;
+        if (!deformed) {
+            gc::k_batch_activate<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(src, g->n, B.act.as<float4>());
+            gc::note_launches(1);
+        }
         gc::k_batch_preprocess<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(
             src, rq_dev, ib_dev, n_req, items, B.rec.as<float4>(), B.dkeys[0].as<uint32_t>(),
-            B.dvals[0].as<uint32_t>(), B.touched.as<uint32_t>(), B.diff.as<int32_t>(), B.act.as<float4>());
-        gc::note_launches(2);
+            B.dvals[0].as<uint32_t>(), B.touched.as<uint32_t>(), B.diff.as<int32_t>(),
+            deformed ? nullptr : B.act.as<float4>());
+        gc::note_launches(1);
         GC_CUDA(ctx, cudaGetLastError());
         GC_CUDA(ctx, mark(GC_STAGE_DEPTH_SORT));
         uint32_t *dk[2] = {B.dkeys[0].as<uint32_t>(), B.dkeys[1].as<uint32_t>()};
@@ -872,7 +882,9 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
         if (!dL_dimages[q]) return fail(ctx, GC_ERR_INVALID_ARG, "dL_dimages[%d] is NULL", q);
     for (int q = 0; q < n_req; ++q) {
         const int f = B.reqs[q].frame;
-        if (f >= 0 && (B.reqs[q].group_q != frames[f].q || B.reqs[q].group_t != frames[f].t))
+        if (f >= 0 && (B.reqs[q].group_q != frames[f].q || B.reqs[q].group_t != frames[f].t ||
+                       B.reqs[q].res.ls != frames[f].res_log_scales ||
+                       B.reqs[q].res.logit != frames[f].res_opacity_logits || B.reqs[q].res.sh != frames[f].res_sh))
             return fail(ctx, GC_ERR_STATE, "the motion frames differ from the forward's");
     }
     DeviceGuard dg(ctx->device);

@@ -13,12 +13,18 @@ namespace gc {
 
 __device__ __forceinline__ float bf16f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
-// SH coefficient k, channel c of global Gaussian i (dequantised for BF16/FP8 storage).
-__device__ __forceinline__ float sh_coeff(const GaussSrc &G, int64_t i, int k, int c) {
+// SH coefficient k, channel c of global Gaussian i (dequantised for BF16/FP8 storage),
+// plus the frame's residual (Eq. 7).
+__device__ __forceinline__ float sh_coeff(const GaussSrc &G, int64_t i, int k, int c, const Residual &res) {
     const int64_t idx = (i * G.K + k) * 3 + c;
-    if (G.precision == GC_PREC_FP32) return G.sh[idx];
-    __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)G.sh_q[idx], __NV_E4M3);
-    return __fmul_rn(__half2float(__half(hr)), G.scales[11 + 3 * k + c]);
+    float f;
+    if (G.precision == GC_PREC_FP32) {
+        f = G.sh[idx];
+    } else {
+        __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)G.sh_q[idx], __NV_E4M3);
+        f = __fmul_rn(__half2float(__half(hr)), G.scales[11 + 3 * k + c]);
+    }
+    return res.sh ? __fadd_rn(f, res.sh[idx]) : f;
 }
 
 // Gradient accumulators of one Gaussian (added to, never overwritten).
@@ -27,13 +33,14 @@ struct GradAcc {
 };
 
 // Adds the gradient of global Gaussian i, seen by camera `cam` under group motion
-// (group_q == NULL: identity), given its 2D gradient d[9], to `acc`; writes the
-// Gaussian's motion terms (d q_g[4], d t_g[3]) to motion7.  The Gaussian must be
-// visible in that view.
+// (group_q == NULL: identity) and residual deformation `res`, given its 2D gradient d[9],
+// to `acc`; writes the Gaussian's motion terms (d q_g[4], d t_g[3]) to motion7.  The
+// Gaussian must be visible in that view.  The log-scale, logit and SH gradients are those
+// of the deformed attributes (= those of the residuals).
 __device__ __forceinline__ void chain_rule(const GaussSrc &G, int64_t i, const float *group_q,
                                            const float *group_t, int g, const CamParams &cam,
                                            const RenderParams &rp, const float *d, GradAcc &acc,
-                                           float *motion7) {
+                                           float *motion7, const Residual &res) {
     const int K = G.K;
     float mu[3], ls[3], q[4], logit;
     if (G.precision == GC_PREC_FP32) {
@@ -48,6 +55,9 @@ __device__ __forceinline__ void chain_rule(const GaussSrc &G, int64_t i, const f
         for (int k = 0; k < 4; ++k) q[k] = __fmul_rn(bf16f(G.quats_h[4 * i + k]), G.scales[6 + k]);
         logit = __fmul_rn(bf16f(G.opacity_h[i]), G.scales[10]);
     }
+    if (res.ls)
+        for (int k = 0; k < 3; ++k) ls[k] = __fadd_rn(ls[k], res.ls[3 * i + k]);
+    if (res.logit) logit = __fadd_rn(logit, res.logit[i]);
     {
         float gq[4] = {1.f, 0.f, 0.f, 0.f}, gt[3] = {0.f, 0.f, 0.f};
         if (group_q) {
@@ -109,14 +119,14 @@ __device__ __forceinline__ void chain_rule(const GaussSrc &G, int64_t i, const f
         float raw[3] = {0.5f, 0.5f, 0.5f};
         float wsh[16];
         for (int k = 0; k < K; ++k) {
-            raw[0] += Y[k] * sh_coeff(G, i, k, 0);
-            raw[1] += Y[k] * sh_coeff(G, i, k, 1);
-            raw[2] += Y[k] * sh_coeff(G, i, k, 2);
+            raw[0] += Y[k] * sh_coeff(G, i, k, 0, res);
+            raw[1] += Y[k] * sh_coeff(G, i, k, 1, res);
+            raw[2] += Y[k] * sh_coeff(G, i, k, 2, res);
         }
         const float draw[3] = {raw[0] > 0.f ? d[6] : 0.f, raw[1] > 0.f ? d[7] : 0.f, raw[2] > 0.f ? d[8] : 0.f};
         for (int k = 0; k < K; ++k) {
-            wsh[k] = sh_coeff(G, i, k, 0) * draw[0] + sh_coeff(G, i, k, 1) * draw[1] +
-                     sh_coeff(G, i, k, 2) * draw[2];
+            wsh[k] = sh_coeff(G, i, k, 0, res) * draw[0] + sh_coeff(G, i, k, 1, res) * draw[1] +
+                     sh_coeff(G, i, k, 2, res) * draw[2];
             acc.dsh[3 * k] += Y[k] * draw[0];
             acc.dsh[3 * k + 1] += Y[k] * draw[1];
             acc.dsh[3 * k + 2] += Y[k] * draw[2];

@@ -71,6 +71,12 @@ struct RenderParams {
 };
 
 // Attribute source.  FP32 arrays, or BF16/FP8 planes with per-channel scales.
+// Per-Gaussian additive residuals of one frame (Sec. 3.2, Eq. 7): log-scale, opacity logit
+// and SH coefficient offsets, FP32 device arrays by global index, NULL = none.
+struct Residual {
+    const float *ls, *logit, *sh;
+};
+
 struct GaussSrc {
     int64_t n;
     int sh_degree, K;
@@ -82,6 +88,7 @@ struct GaussSrc {
     const float *scales;
     const float *group_q, *group_t;  // NULL = identity motion
     int n_groups;
+    Residual res;                    // the frame's residual deformation
 };
 
 __host__ __device__ inline int64_t sel_global(const Selection &s, int64_t j) {

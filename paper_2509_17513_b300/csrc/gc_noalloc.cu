@@ -157,8 +157,10 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
         (!g->means_bf16 || !g->log_scales_bf16 || !g->quats_bf16 || !g->opacity_bf16 ||
          !g->sh_e4m3 || !g->scales))
         return say(err, err_len, GC_ERR_INVALID_ARG, "a reduced-precision plane is NULL");
-    if (motion && (motion->n_groups < 1 || !motion->q || !motion->t))
+    if (motion && (motion->q || motion->t) && (motion->n_groups < 1 || !motion->q || !motion->t))
         return say(err, err_len, GC_ERR_INVALID_ARG, "invalid motion");
+    if (motion && motion->res_sh && g->sh_degree == 3 && (reinterpret_cast<uintptr_t>(motion->res_sh) & 15))
+        return say(err, err_len, GC_ERR_INVALID_ARG, "res_sh must be 16-byte aligned");
 
     // selection (host, no allocation)
     gc::Selection sel{};
@@ -205,7 +207,8 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
     src.means_h = g->means_bf16; src.log_scales_h = g->log_scales_bf16; src.quats_h = g->quats_bf16;
     src.opacity_h = g->opacity_bf16; src.sh_q = g->sh_e4m3; src.scales = g->scales;
     src.n_groups = 1;
-    if (motion) {
+    if (motion) src.res = gc::Residual{motion->res_log_scales, motion->res_opacity_logits, motion->res_sh};
+    if (motion && motion->q) {
         src.group_id = g->group_id;
         src.group_q = motion->q;
         src.group_t = motion->t;

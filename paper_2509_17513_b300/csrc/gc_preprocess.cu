@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, i
     if (j >= n_sel) return;
     const int64_t i = sel_global(sel, j);
     Proj P;
-    project_gaussian(G, i, G.group_q, G.group_t, G.n_groups, cam, rp, P);
+    project_gaussian(G, i, G.group_q, G.group_t, G.n_groups, cam, rp, P, nullptr, G.res);
     rec[kRec * j] = P.r0;
     rec[kRec * j + 1] = P.r1;
     P.r2.y = __int_as_float(layer_of(sel, i));

@@ -36,7 +36,7 @@ struct Attr {
     int g;
 };
 
-__device__ __forceinline__ void load_attr(const GaussSrc &G, int64_t i, Attr &a) {
+__device__ __forceinline__ void load_attr(const GaussSrc &G, int64_t i, Attr &a, const Residual &res) {
     if (G.precision == GC_PREC_FP32) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -56,13 +56,19 @@ __device__ __forceinline__ void load_attr(const GaussSrc &G, int64_t i, Attr &a)
         for (int k = 0; k < 4; ++k) a.q[k] = fmul(bf16_to_f32(G.quats_h[4 * i + k]), G.scales[6 + k]);
         a.logit = fmul(bf16_to_f32(G.opacity_h[i]), G.scales[10]);
     }
+    // residual deformation (Eq. 7): one FP32 addition per attribute, before activation
+    if (res.ls) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a.ls[k] = fadd(a.ls[k], res.ls[3 * i + k]);
+    }
+    if (res.logit) a.logit = fadd(a.logit, res.logit[i]);
     a.g = G.group_id ? G.group_id[i] : 0;
 }
 
-__device__ __forceinline__ float load_sh(const GaussSrc &G, int64_t i, int k, int c) {
+__device__ __forceinline__ float load_sh(const GaussSrc &G, int64_t i, int k, int c, const Residual &res) {
     int64_t idx = (i * G.K + k) * 3 + c;
-    if (G.precision == GC_PREC_FP32) return G.sh[idx];
-    return fmul(e4m3_to_f32(G.sh_q[idx]), G.scales[11 + 3 * k + c]);
+    const float f = G.precision == GC_PREC_FP32 ? G.sh[idx] : fmul(e4m3_to_f32(G.sh_q[idx]), G.scales[11 + 3 * k + c]);
+    return res.sh ? fadd(f, res.sh[idx]) : f;
 }
 
 
@@ -81,18 +87,19 @@ struct Proj {
 // (step 14).  A batch computes them once per Gaussian instead of once per request.
 __device__ __forceinline__ float4 gaussian_activation(const GaussSrc &G, int64_t i) {
     Attr A;
-    load_attr(G, i, A);
+    load_attr(G, i, A, Residual{nullptr, nullptr, nullptr});
     return make_float4(exp_f32_of_f64(A.ls[0]), exp_f32_of_f64(A.ls[1]), exp_f32_of_f64(A.ls[2]),
                        tau_f32_of_f64(A.logit));
 }
 
-// act: NULL, or the cached gaussian_activation of every Gaussian (bit-identical results).
+// act: NULL, or the cached gaussian_activation of every Gaussian (bit-identical results;
+// only without residuals).  res: the frame's residual deformation.
 __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, const float *group_q,
                                                 const float *group_t, int n_groups,
                                                 const CamParams &cam, const RenderParams &rp,
-                                                Proj &P, const float4 *act = nullptr) {
+                                                Proj &P, const float4 *act, const Residual &res) {
     Attr A;
-    load_attr(G, i, A);
+    load_attr(G, i, A, res);
     P.key = kCulledKey;
     P.ntouch = 0;
     P.tx0 = P.tx1 = P.ty0 = P.ty1 = 0;
@@ -263,7 +270,11 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
                 const float4 *p = reinterpret_cast<const float4 *>(G.sh + i * 48);
 #pragma unroll
                 for (int q = 0; q < 12; ++q) {
-                    const float4 x = p[q];
+                    float4 x = p[q];
+                    if (res.sh) {
+                        const float4 d = reinterpret_cast<const float4 *>(res.sh + i * 48)[q];
+                        x = make_float4(fadd(x.x, d.x), fadd(x.y, d.y), fadd(x.z, d.z), fadd(x.w, d.w));
+                    }
                     const float v4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
@@ -280,7 +291,8 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
 #pragma unroll
                     for (int b = 0; b < 16; ++b) {
                         const int idx = 16 * q + b;
-                        const float v = fmul(e4m3_to_f32((uint8_t)(w[b >> 2] >> (8 * (b & 3)))), G.scales[11 + idx]);
+                        float v = fmul(e4m3_to_f32((uint8_t)(w[b >> 2] >> (8 * (b & 3)))), G.scales[11 + idx]);
+                        if (res.sh) v = fadd(v, res.sh[i * 48 + idx]);
                         acc[idx % 3] = fmaf(Y[idx / 3], v, acc[idx % 3]);
                     }
                 }
@@ -293,7 +305,7 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
                 float acc = 0.f;
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    if (k < G.K) acc = fmaf(Y[k], load_sh(G, i, k, c), acc);
+                    if (k < G.K) acc = fmaf(Y[k], load_sh(G, i, k, c, res), acc);
                 rgb[c] = fmaxf(acc + 0.5f, 0.f);
             }
         }

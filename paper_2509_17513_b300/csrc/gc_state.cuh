@@ -66,6 +66,7 @@ struct gc_saved {
     int64_t n = 0, n_sel = 0;
     int sh_degree = 0, n_groups = 1;
     bool has_motion = false;
+    gc::Residual res{nullptr, nullptr, nullptr};  // residual arrays of the forward
     int n_layers = 0;
     int64_t layer_offsets[gc::kMaxLayers + 1] = {};
     uint32_t layer_mask = 0;
@@ -199,14 +200,19 @@ inline gc_status make_source(gc_context *ctx, const gc_gaussians *g, const gc_mo
     s.means_h = g->means_bf16; s.log_scales_h = g->log_scales_bf16; s.quats_h = g->quats_bf16;
     s.opacity_h = g->opacity_bf16; s.sh_q = g->sh_e4m3; s.scales = g->scales;
     s.n_groups = 1;
-    if (m) {
+    if (m && (m->q || m->t)) {
         if (m->n_groups < 1 || !m->q || !m->t)
-            return fail(ctx, GC_ERR_INVALID_ARG, "motion needs n_groups >= 1 and q, t arrays");
+            return fail(ctx, GC_ERR_INVALID_ARG, "motion needs n_groups >= 1 and both q and t arrays");
         s.group_q = m->q;
         s.group_t = m->t;
         s.n_groups = m->n_groups;
     } else if (g->group_id) {
         s.group_id = nullptr;  // keyframe: groups are irrelevant
+    }
+    if (m) {
+        if (m->res_sh && s.K == 16 && (reinterpret_cast<uintptr_t>(m->res_sh) & 15))
+            return fail(ctx, GC_ERR_INVALID_ARG, "res_sh must be 16-byte aligned");
+        s.res = gc::Residual{m->res_log_scales, m->res_opacity_logits, m->res_sh};
     }
     return GC_OK;
 }

@@ -101,21 +101,34 @@ class GaussianSet:
 
 
 class MotionFrame:
-    """One frame of cumulative group motion: q (G,4), t (G,3) CUDA float32."""
+    """One frame: cumulative group motion q (G,4), t (G,3) (both None: no group motion) and,
+    optionally, the frame's residual deformation (Sec. 3.2, Eq. 7) as CUDA float32 tensors
+    res_log_scales (n,3), res_opacity_logits (n,), res_sh (n,K,3), each None for none."""
 
-    def __init__(self, q: torch.Tensor, t: torch.Tensor):
-        self.q = q.contiguous()
-        self.t = t.contiguous()
+    def __init__(self, q: torch.Tensor | None, t: torch.Tensor | None, res_log_scales=None,
+                 res_opacity_logits=None, res_sh=None):
+        self.q = q.contiguous() if q is not None else None
+        self.t = t.contiguous() if t is not None else None
+        self.res = [x.contiguous() if x is not None else None
+                    for x in (res_log_scales, res_opacity_logits, res_sh)]
         s = _abi.Motion()
-        s.n_groups = int(q.shape[0])
-        s.q = self.q.data_ptr()
-        s.t = self.t.data_ptr()
+        s.n_groups = int(q.shape[0]) if q is not None else 1
+        s.q = self.q.data_ptr() if q is not None else None
+        s.t = self.t.data_ptr() if t is not None else None
+        s.res_log_scales, s.res_opacity_logits, s.res_sh = [x.data_ptr() if x is not None else None
+                                                            for x in self.res]
         self.struct = s
 
     @staticmethod
-    def from_motion(motion, frame: int, device="cuda") -> "MotionFrame":
-        return MotionFrame(torch.from_numpy(np.ascontiguousarray(motion.q[frame])).to(device),
-                           torch.from_numpy(np.ascontiguousarray(motion.t[frame])).to(device))
+    def from_motion(motion, frame: int, device="cuda", residual=None) -> "MotionFrame":
+        """Frame `frame` of a synthetic motion (None: no group motion), with an optional
+        residual (an object with ls, logit, sh arrays, any None)."""
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device) if a is not None else None
+        q = dev(motion.q[frame]) if motion is not None else None
+        t = dev(motion.t[frame]) if motion is not None else None
+        if residual is None:
+            return MotionFrame(q, t)
+        return MotionFrame(q, t, dev(residual.ls), dev(residual.logit), dev(residual.sh))
 
 
 class Saved:
@@ -206,7 +219,7 @@ class Renderer:
             grads = {"means": torch.empty((n, 3), device=dev), "log_scales": torch.empty((n, 3), device=dev),
                      "quats": torch.empty((n, 4), device=dev), "opacity_logits": torch.empty(n, device=dev),
                      "sh": torch.empty((n, K, 3), device=dev)}
-            if motion is not None:
+            if motion is not None and motion.q is not None:
                 G = motion.q.shape[0]
                 grads["group_q"] = torch.empty((G, 4), device=dev)
                 grads["group_t"] = torch.empty((G, 3), device=dev)
@@ -264,7 +277,7 @@ class Renderer:
         grads = {"means": torch.empty((n, 3), device=dev), "log_scales": torch.empty((n, 3), device=dev),
                  "quats": torch.empty((n, 4), device=dev), "opacity_logits": torch.empty(n, device=dev),
                  "sh": torch.empty((n, K, 3), device=dev)}
-        if motion is not None:
+        if motion is not None and motion.q is not None:
             G = motion.q.shape[0]
             grads["group_q"] = torch.empty((G, 4), device=dev)
             grads["group_t"] = torch.empty((G, 3), device=dev)
