@@ -437,5 +437,33 @@ def dequantize(q: dict, scene_template):
     return s
 
 
+def dequantize_planes(planes: dict, scene_template):
+    """Scene whose attributes are the FP32 values of the paper's decoded planes (Sec. 3.4; the
+    layout of ``synth.scenes.quantize_planes``): Gaussian j of layer l is read at row
+    j // plane_width, column j % plane_width of each of its layer's channel planes, and
+    value = fl32(fl32(float(code) * step) + lo) with the channel's (lo, step) - the min / max
+    affine map, one FP32 multiply and one FP32 add.  Group ids come from the template."""
+    import copy
+    s = copy.copy(scene_template)
+    W = int(planes["plane_width"])
+    dq = np.asarray(planes["dequant"], np.float32)
+    n_ch = dq.shape[1]
+    out = np.zeros((scene_template.n, n_ch), np.float32)
+    for l in range(len(scene_template.layer_offsets) - 1):
+        a, b = int(scene_template.layer_offsets[l]), int(scene_template.layer_offsets[l + 1])
+        row, col = np.divmod(np.arange(b - a), W)   # Gaussian j of the layer
+        for ch in range(n_ch):
+            code = planes["pos"][l][ch, row, col] if ch < 3 else planes["u8"][l][ch - 3, row, col]
+            lo, step = dq[l, ch]
+            out[a:b, ch] = (code.astype(np.float32) * step).astype(np.float32) + lo
+    K3 = n_ch - 11
+    s.means = out[:, 0:3].copy()
+    s.quats = out[:, 3:7].copy()
+    s.log_scales = out[:, 7:10].copy()
+    s.opacity_logits = out[:, 10].copy()
+    s.sh = out[:, 11:].reshape(-1, K3 // 3, 3).copy()
+    return s
+
+
 def num_threads() -> int:
     return int(lib().gco_num_threads())

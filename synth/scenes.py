@@ -432,3 +432,62 @@ def quantize_scene(scene: Scene):
     q["opacity_logits"] = q["opacity_logits"].reshape(-1)
     q["sh"], q["sh_scale"] = e4m3_plane(scene.sh)
     return q
+
+
+PLANE_CHANNELS_FIXED = 11  # x, y, z | quaternion w, x, y, z | log-scales 3 | opacity logit
+
+
+def quantize_planes(scene: Scene, plane_width: int = 512, pos_bits: int = 16, pitch_align: int = 256) -> dict:
+    """The paper's decoded attribute format (Sec. 3.4): per layer, each attribute channel is
+    quantised with its own min / max affine map - positions to uint16 (or uint32), every other
+    channel to uint8 - and laid out as a 2D single-channel plane in which Gaussian j of the
+    layer sits at row j // plane_width, column j % plane_width.  A layer's channel planes are
+    stacked in one buffer (channel c in rows [c * rows, (c + 1) * rows), rows = ceil(n_l /
+    plane_width)) whose rows are `pitch` bytes apart (the row size rounded up to `pitch_align`,
+    like a video decoder's frame pitch); padding is zero.  This is the encoder side: it only
+    produces inputs.  Channel order: x, y, z | quaternion w, x, y, z | log-scales 3 | opacity
+    logit | SH (coefficient-major, then r, g, b).
+
+    Returns plane_width, pos_bits, pitch (bytes of the uint8 planes), pos_pitch (bytes of the
+    position planes), u8 (per layer a uint8 array (C - 3, rows, pitch)), pos (per layer a
+    uint16/uint32 array (3, rows, pos_pitch / (pos_bits / 8))) and dequant, float32 (L, C, 2)
+    = (lo, step) per layer and channel, step = (hi - lo) / (2^bits - 1)."""
+    assert pos_bits in (16, 32)
+    n_ch = PLANE_CHANNELS_FIXED + 3 * _sh_count(scene.sh_degree)
+    attrs = np.concatenate([scene.means, scene.quats, scene.log_scales, scene.opacity_logits[:, None],
+                            scene.sh.reshape(scene.n, -1)], axis=1).astype(np.float32)
+    assert attrs.shape[1] == n_ch
+    L = scene.n_layers
+    pb = pos_bits // 8
+    pitch = -(-plane_width // pitch_align) * pitch_align
+    pos_pitch = -(-(plane_width * pb) // pitch_align) * pitch_align
+    pos_dtype = np.uint16 if pos_bits == 16 else np.uint32
+    dequant = np.zeros((L, n_ch, 2), np.float32)
+    u8, pos = [], []
+    for l in range(L):
+        a, b = int(scene.layer_offsets[l]), int(scene.layer_offsets[l + 1])
+        n_l = b - a
+        rows = -(-n_l // plane_width)
+        pl8 = np.zeros((n_ch - 3, rows, pitch), np.uint8)
+        plp = np.zeros((3, rows, pos_pitch // pb), pos_dtype)
+        j = np.arange(n_l)
+        r, c = j // plane_width, j % plane_width
+        for ch in range(n_ch):
+            x = attrs[a:b, ch].astype(np.float64)
+            bits = pos_bits if ch < 3 else 8
+            top = float(2 ** bits - 1)
+            lo = np.float32(x.min()) if n_l else np.float32(0.0)
+            hi = np.float32(x.max()) if n_l else np.float32(0.0)
+            step = np.float32((float(hi) - float(lo)) / top)
+            dequant[l, ch] = (lo, step)
+            if n_l == 0:
+                continue
+            code = np.zeros(n_l) if step == 0 else np.clip(np.rint((x - float(lo)) / float(step)), 0, top)
+            if ch < 3:
+                plp[ch, r, c] = code.astype(pos_dtype)
+            else:
+                pl8[ch - 3, r, c] = code.astype(np.uint8)
+        u8.append(pl8)
+        pos.append(plp)
+    return {"plane_width": plane_width, "pos_bits": pos_bits, "pitch": pitch, "pos_pitch": pos_pitch,
+            "u8": u8, "pos": pos, "dequant": dequant}
