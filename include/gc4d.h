@@ -52,7 +52,7 @@ typedef enum {
     GC_ERR_UNSUPPORTED = 7   /* a valid request this build does not support */
 } gc_status;
 
-enum { GC_PREC_FP32 = 0, GC_PREC_BF16_FP8 = 1 };
+enum { GC_PREC_FP32 = 0, GC_PREC_BF16_FP8 = 1, GC_PREC_PLANES = 2 };
 enum { GC_MEMBER_PIXEL = 0, GC_MEMBER_TILE = 1 };
 
 typedef struct gc_context gc_context;
@@ -87,7 +87,7 @@ typedef struct {
     int32_t n_layers;             /* L, at most 32 */
     const int64_t *layer_offsets; /* HOST array of L+1 nondecreasing offsets, [0] = 0, [L] = n */
     int32_t sh_degree;            /* 0..3; K = (sh_degree+1)^2 coefficients per colour channel */
-    int32_t precision;            /* GC_PREC_FP32 or GC_PREC_BF16_FP8 */
+    int32_t precision;            /* GC_PREC_FP32, GC_PREC_BF16_FP8 or GC_PREC_PLANES */
     /* GC_PREC_FP32 attributes (device) */
     const float *means;           /* n x 3 */
     const float *log_scales;      /* n x 3, s = exp(log_scales) */
@@ -103,6 +103,22 @@ typedef struct {
     const uint8_t *sh_e4m3;          /* n x K x 3 float8 e4m3 ("fn") bit patterns */
     const float *scales;             /* device, 3 + 3 + 4 + 1 + 3K per-channel FP32 scales in the
                                         order means, log_scales, quats, opacity, sh (k-major, rgb) */
+    /* GC_PREC_PLANES: the paper's decoded attribute planes (Sec. 3.4).  C = 11 + 3K channels in
+     * the order x, y, z | quaternion w, x, y, z | log-scales 3 | opacity logit | SH (k-major,
+     * rgb).  Per layer l (n_l Gaussians, rows_l = ceil(n_l / plane_width)) one device buffer of
+     * uint8 codes for channels 3..C-1, channel c occupying rows [(c-3) rows_l, (c-2) rows_l) of
+     * plane_pitch bytes each, and one buffer of pos_bits-bit codes (uint16 or uint32, native
+     * byte order) for channels 0..2, rows of pos_pitch bytes; Gaussian j of the layer is at row
+     * j / plane_width, column j % plane_width of its channel's plane.  value = lo + code * step
+     * in FP32 (the product and the sum each rounded once), (lo, step) = dequant[(l C + c) 2 + 0/1]. */
+    int32_t plane_width;             /* Gaussians per plane row, >= 1 */
+    int32_t pos_bits;                /* 16 or 32 */
+    int64_t plane_pitch;             /* bytes per row of the uint8 planes, >= plane_width */
+    int64_t pos_pitch;               /* bytes per row of the position planes, >= plane_width * pos_bits / 8,
+                                        a multiple of pos_bits / 8 */
+    const uint8_t *const *planes_u8; /* HOST array of n_layers device pointers (may be NULL for empty layers) */
+    const void *const *planes_pos;   /* HOST array of n_layers device pointers (aligned to pos_bits / 8) */
+    const float *dequant;            /* device, n_layers x C x 2 FP32 */
 } gc_gaussians;
 
 /* One frame (device arrays): the cumulative per-group rigid motion (Sec. 3.2, rigid

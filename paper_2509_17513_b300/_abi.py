@@ -28,6 +28,7 @@ STAGES = ("preprocess", "depth_sort", "scan", "emit", "tile_sort", "ranges", "bl
 
 GC_PREC_FP32 = 0
 GC_PREC_BF16_FP8 = 1
+GC_PREC_PLANES = 2
 GC_MEMBER_PIXEL = 0
 GC_MEMBER_TILE = 1
 
@@ -45,7 +46,10 @@ class Gaussians(C.Structure):
                 ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("group_id", C.c_void_p),
                 ("means_bf16", C.c_void_p), ("log_scales_bf16", C.c_void_p),
                 ("quats_bf16", C.c_void_p), ("opacity_bf16", C.c_void_p), ("sh_e4m3", C.c_void_p),
-                ("scales", C.c_void_p)]
+                ("scales", C.c_void_p),
+                ("plane_width", C.c_int32), ("pos_bits", C.c_int32), ("plane_pitch", C.c_int64),
+                ("pos_pitch", C.c_int64), ("planes_u8", C.c_void_p), ("planes_pos", C.c_void_p),
+                ("dequant", C.c_void_p)]
 
 
 class Motion(C.Structure):

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(256) k_reduce_entries(float *__restrict__ part
 
 // Thread per selected Gaussian in index order (coalesced attribute reads and
 // gradient writes); g2d and touched are by compact position.
+template <int PREC>
 __global__ void __launch_bounds__(128) k_preprocess_bwd(GaussSrc G, Selection sel, int64_t n_sel,
                                                         CamParams cam, RenderParams rp,
                                                         const float *__restrict__ g2d,
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(GaussSrc G, Selection se
     float m7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (touched[j] != 0) {
         const int g = (G.group_q && G.group_id) ? G.group_id[i] : 0;
-        chain_rule(G, i, G.group_q, G.group_t, g, cam, rp, g2d + 9 * j, acc, m7, G.res);
+        chain_rule<PREC>(G, i, G.group_q, G.group_t, g, cam, rp, g2d + 9 * j, acc, m7, G.res);
     }
     if (out.d_means) for (int k = 0; k < 3; ++k) out.d_means[3 * i + k] = acc.dmu[k];
     if (out.d_log_scales) for (int k = 0; k < 3; ++k) out.d_log_scales[3 * i + k] = acc.dls[k];
@@ -179,8 +180,8 @@ cudaError_t launch_preprocess_bwd(const GaussSrc &g, const Selection &sel, int64
                                   const uint32_t *touched, gc_grads out, float *motion_contrib,
                                   cudaStream_t st) {
     if (n_sel <= 0) return cudaSuccess;
-    k_preprocess_bwd<<<(unsigned)((n_sel + 127) / 128), 128, 0, st>>>(g, sel, n_sel, cam, rp, g2d, touched,
-                                                                       out, motion_contrib);
+    GC_DISPATCH_PREC(g.precision, k_preprocess_bwd<PREC_><<<(unsigned)((n_sel + 127) / 128), 128, 0, st>>>(
+                                      g, sel, n_sel, cam, rp, g2d, touched, out, motion_contrib))
     note_launches(1);
     return cudaGetLastError();
 }

@@ -71,11 +71,13 @@ __device__ __forceinline__ int find_req(const int64_t *base, int n, int64_t x) {
 }
 
 // The request-independent activations of every Gaussian (scales, alpha level), once per batch.
+template <int PREC>
 __global__ void __launch_bounds__(256) k_batch_activate(GaussSrc G, int64_t n, float4 *__restrict__ act) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) act[i] = gaussian_activation(G, i);
+    if (i < n) act[i] = gaussian_activation<PREC>(G, i);
 }
 
+template <int PREC>
 __global__ void __launch_bounds__(256, 4) k_batch_preprocess(GaussSrc G, const BatchReq *__restrict__ reqs,
                                                           const int64_t *__restrict__ item_base, int n_req,
                                                           int64_t n_items, float4 *__restrict__ rec,
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(256, 4) k_batch_preprocess(GaussSrc G, const B
     vals[item] = (uint32_t)item;
     Proj P;
     if (j < R.n_sel) {
-        project_gaussian(G, sel_global(R.sel, j), R.group_q, R.group_t, R.n_groups, R.cam, R.rp, P, act, R.res);
+        project_gaussian<PREC>(G, sel_global(R.sel, j), R.group_q, R.group_t, R.n_groups, R.cam, R.rp, P, act, R.res);
     } else {
         P.key = kCulledKey;
         P.ntouch = 0;
@@ -348,6 +350,7 @@ __device__ __forceinline__ int64_t sel_local(const Selection &s, int64_t i) {
 
 // Thread per Gaussian: the chain rule for every request that sees it, summed in
 // request order; per-item motion terms for the group sums.
+template <int PREC>
 __global__ void __launch_bounds__(128) k_batch_preprocess_bwd(GaussSrc G, const BatchReq *__restrict__ reqs,
                                                               int n_req, int64_t n,
                                                               const float *__restrict__ g2d,
@@ -370,7 +373,8 @@ __global__ void __launch_bounds__(128) k_batch_preprocess_bwd(GaussSrc G, const 
         if (j < 0) continue;
         const int64_t item = R.item_base + j;
         float m7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (touched[item] != 0) chain_rule(G, i, R.group_q, R.group_t, g, R.cam, R.rp, g2d + 9 * item, acc, m7, R.res);
+        if (touched[item] != 0)
+            chain_rule<PREC>(G, i, R.group_q, R.group_t, g, R.cam, R.rp, g2d + 9 * item, acc, m7, R.res);
         if (mcontrib)
             for (int k = 0; k < 7; ++k) mcontrib[7 * item + k] = m7[k];
     }
@@ -756,13 +760,14 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
         bool deformed = false;
         for (const auto &R : tab) deformed = deformed || R.res.ls || R.res.logit;
         if (!deformed) {
-            gc::k_batch_activate<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(src, g->n, B.act.as<float4>());
+            GC_DISPATCH_PREC(src.precision, gc::k_batch_activate<PREC_><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(
+                                                src, g->n, B.act.as<float4>()))
             gc::note_launches(1);
         }
-        gc::k_batch_preprocess<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(
+        GC_DISPATCH_PREC(src.precision, gc::k_batch_preprocess<PREC_><<<(unsigned)((items + 255) / 256), 256, 0, s>>>(
             src, rq_dev, ib_dev, n_req, items, B.rec.as<float4>(), B.dkeys[0].as<uint32_t>(),
             B.dvals[0].as<uint32_t>(), B.touched.as<uint32_t>(), B.diff.as<int32_t>(),
-            deformed ? nullptr : B.act.as<float4>());
+            deformed ? nullptr : B.act.as<float4>()))
         gc::note_launches(1);
         GC_CUDA(ctx, cudaGetLastError());
         GC_CUDA(ctx, mark(GC_STAGE_DEPTH_SORT));
@@ -960,9 +965,9 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
     B.part_clean = true;
     GC_CUDA(ctx, mark(GC_STAGE_PREPROCESS_BWD));
     if (g->n > 0) {
-        gc::k_batch_preprocess_bwd<<<(unsigned)((g->n + 127) / 128), 128, 0, s>>>(
+        GC_DISPATCH_PREC(src.precision, gc::k_batch_preprocess_bwd<PREC_><<<(unsigned)((g->n + 127) / 128), 128, 0, s>>>(
             src, rq_dev, n_req, g->n, B.g2d.as<float>(), B.touched.as<uint32_t>(), *out, accumulate,
-            G ? B.mcontrib.as<float>() : nullptr);
+            G ? B.mcontrib.as<float>() : nullptr))
         gc::note_launches(1);
         GC_CUDA(ctx, cudaGetLastError());
     }

@@ -13,13 +13,17 @@ namespace gc {
 
 __device__ __forceinline__ float bf16f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
-// SH coefficient k, channel c of global Gaussian i (dequantised for BF16/FP8 storage),
-// plus the frame's residual (Eq. 7).
-__device__ __forceinline__ float sh_coeff(const GaussSrc &G, int64_t i, int k, int c, const Residual &res) {
+// SH coefficient k, channel c of global Gaussian i (dequantised for BF16/FP8 storage or
+// from the decoded planes at `pl`), plus the frame's residual (Eq. 7).
+template <int PREC>
+__device__ __forceinline__ float sh_coeff(const GaussSrc &G, int64_t i, int k, int c, const Residual &res,
+                                          const PlaneLoc &pl) {
     const int64_t idx = (i * G.K + k) * 3 + c;
     float f;
-    if (G.precision == GC_PREC_FP32) {
+    if constexpr (PREC == GC_PREC_FP32) {
         f = G.sh[idx];
+    } else if constexpr (PREC == GC_PREC_PLANES) {
+        f = plane_value(G, pl, 11 + 3 * k + c);
     } else {
         __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)G.sh_q[idx], __NV_E4M3);
         f = __fmul_rn(__half2float(__half(hr)), G.scales[11 + 3 * k + c]);
@@ -37,13 +41,20 @@ struct GradAcc {
 // to `acc`; writes the Gaussian's motion terms (d q_g[4], d t_g[3]) to motion7.  The
 // Gaussian must be visible in that view.  The log-scale, logit and SH gradients are those
 // of the deformed attributes (= those of the residuals).
+template <int PREC>
 __device__ __forceinline__ void chain_rule(const GaussSrc &G, int64_t i, const float *group_q,
                                            const float *group_t, int g, const CamParams &cam,
                                            const RenderParams &rp, const float *d, GradAcc &acc,
                                            float *motion7, const Residual &res) {
     const int K = G.K;
     float mu[3], ls[3], q[4], logit;
-    if (G.precision == GC_PREC_FP32) {
+    PlaneLoc pl{0, 0, 0, 0};
+    if constexpr (PREC == GC_PREC_PLANES) {
+        pl = plane_loc(G, i);
+        for (int k = 0; k < 3; ++k) { mu[k] = plane_value(G, pl, k); ls[k] = plane_value(G, pl, 7 + k); }
+        for (int k = 0; k < 4; ++k) q[k] = plane_value(G, pl, 3 + k);
+        logit = plane_value(G, pl, 10);
+    } else if constexpr (PREC == GC_PREC_FP32) {
         for (int k = 0; k < 3; ++k) { mu[k] = G.means[3 * i + k]; ls[k] = G.log_scales[3 * i + k]; }
         for (int k = 0; k < 4; ++k) q[k] = G.quats[4 * i + k];
         logit = G.opacity_logits[i];
@@ -119,14 +130,14 @@ __device__ __forceinline__ void chain_rule(const GaussSrc &G, int64_t i, const f
         float raw[3] = {0.5f, 0.5f, 0.5f};
         float wsh[16];
         for (int k = 0; k < K; ++k) {
-            raw[0] += Y[k] * sh_coeff(G, i, k, 0, res);
-            raw[1] += Y[k] * sh_coeff(G, i, k, 1, res);
-            raw[2] += Y[k] * sh_coeff(G, i, k, 2, res);
+            raw[0] += Y[k] * sh_coeff<PREC>(G, i, k, 0, res, pl);
+            raw[1] += Y[k] * sh_coeff<PREC>(G, i, k, 1, res, pl);
+            raw[2] += Y[k] * sh_coeff<PREC>(G, i, k, 2, res, pl);
         }
         const float draw[3] = {raw[0] > 0.f ? d[6] : 0.f, raw[1] > 0.f ? d[7] : 0.f, raw[2] > 0.f ? d[8] : 0.f};
         for (int k = 0; k < K; ++k) {
-            wsh[k] = sh_coeff(G, i, k, 0, res) * draw[0] + sh_coeff(G, i, k, 1, res) * draw[1] +
-                     sh_coeff(G, i, k, 2, res) * draw[2];
+            wsh[k] = sh_coeff<PREC>(G, i, k, 0, res, pl) * draw[0] + sh_coeff<PREC>(G, i, k, 1, res, pl) * draw[1] +
+                     sh_coeff<PREC>(G, i, k, 2, res, pl) * draw[2];
             acc.dsh[3 * k] += Y[k] * draw[0];
             acc.dsh[3 * k + 1] += Y[k] * draw[1];
             acc.dsh[3 * k + 2] += Y[k] * draw[2];

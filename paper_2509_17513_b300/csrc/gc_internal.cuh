@@ -89,7 +89,57 @@ struct GaussSrc {
     const float *group_q, *group_t;  // NULL = identity motion
     int n_groups;
     Residual res;                    // the frame's residual deformation
+    // GC_PREC_PLANES (the decoded attribute planes): per-layer plane buffers and offsets
+    int n_layers, plane_width, pos_bits, n_channels;
+    int64_t plane_pitch, pos_pitch;
+    const uint8_t *plane_u8[kMaxLayers];
+    const uint8_t *plane_pos[kMaxLayers];
+    int64_t layer_off[kMaxLayers + 1];
+    const float *dequant;
 };
+
+// Runs the statements with the compile-time constant PREC_ equal to the storage format
+// `prec` (the preprocess and chain-rule kernels are instantiated per format).
+#define GC_DISPATCH_PREC(prec, ...)                                                        \
+    switch (prec) {                                                                        \
+        case GC_PREC_FP32: { constexpr int PREC_ = GC_PREC_FP32; __VA_ARGS__; } break;           \
+        case GC_PREC_BF16_FP8: { constexpr int PREC_ = GC_PREC_BF16_FP8; __VA_ARGS__; } break;   \
+        default: { constexpr int PREC_ = GC_PREC_PLANES; __VA_ARGS__; } break;                   \
+    }
+
+// Where global Gaussian i sits in the decoded planes: its layer, the layer's row count and
+// its row and column.
+struct PlaneLoc {
+    int l, row, col, rows;
+};
+
+__device__ __forceinline__ PlaneLoc plane_loc(const GaussSrc &G, int64_t i) {
+    int l = 0;
+    while (l + 1 < G.n_layers && i >= G.layer_off[l + 1]) ++l;
+    const int j = (int)(i - G.layer_off[l]);
+    const int n_l = (int)(G.layer_off[l + 1] - G.layer_off[l]);
+    PlaneLoc p;
+    p.l = l;
+    p.rows = (n_l + G.plane_width - 1) / G.plane_width;
+    p.row = j / G.plane_width;
+    p.col = j - p.row * G.plane_width;
+    return p;
+}
+
+// Channel ch (0..2 positions, 3..C-1 the uint8 channels) of the Gaussian at `p`:
+// lo + code * step, the product and the sum each rounded once in FP32.
+__device__ __forceinline__ float plane_value(const GaussSrc &G, const PlaneLoc &p, int ch) {
+    uint32_t code;
+    if (ch < 3) {
+        const uint8_t *row = G.plane_pos[p.l] + ((int64_t)ch * p.rows + p.row) * G.pos_pitch;
+        code = G.pos_bits == 16 ? (uint32_t)reinterpret_cast<const uint16_t *>(row)[p.col]
+                                : reinterpret_cast<const uint32_t *>(row)[p.col];
+    } else {
+        code = G.plane_u8[p.l][((int64_t)(ch - 3) * p.rows + p.row) * G.plane_pitch + p.col];
+    }
+    const float2 d = reinterpret_cast<const float2 *>(G.dequant)[(int64_t)p.l * G.n_channels + ch];
+    return __fadd_rn(__fmul_rn(__uint2float_rn(code), d.y), d.x);
+}
 
 __host__ __device__ inline int64_t sel_global(const Selection &s, int64_t j) {
     int k = 0;

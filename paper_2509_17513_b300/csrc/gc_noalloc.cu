@@ -148,6 +148,8 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
     for (int l = 0; l < g->n_layers; ++l)
         if (g->layer_offsets[l + 1] < g->layer_offsets[l])
             return say(err, err_len, GC_ERR_INVALID_ARG, "layer_offsets must be nondecreasing");
+    if (g->precision == GC_PREC_PLANES)
+        return say(err, err_len, GC_ERR_UNSUPPORTED, "the allocation-free path takes FP32 or BF16/FP8 sets, not decoded planes");
     if (g->precision != GC_PREC_FP32 && g->precision != GC_PREC_BF16_FP8)
         return say(err, err_len, GC_ERR_INVALID_ARG, "unknown precision");
     if (g->n > 0 && g->precision == GC_PREC_FP32 &&

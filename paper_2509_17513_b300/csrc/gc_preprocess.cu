@@ -8,6 +8,7 @@ namespace gc {
 
 namespace {
 
+template <int PREC>
 __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, int64_t n_sel,
                                                     CamParams cam, RenderParams rp,
                                                     float4 *__restrict__ rec,
@@ -19,7 +20,7 @@ __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, i
     if (j >= n_sel) return;
     const int64_t i = sel_global(sel, j);
     Proj P;
-    project_gaussian(G, i, G.group_q, G.group_t, G.n_groups, cam, rp, P, nullptr, G.res);
+    project_gaussian<PREC>(G, i, G.group_q, G.group_t, G.n_groups, cam, rp, P, nullptr, G.res);
     rec[kRec * j] = P.r0;
     rec[kRec * j + 1] = P.r1;
     P.r2.y = __int_as_float(layer_of(sel, i));
@@ -53,8 +54,8 @@ cudaError_t launch_preprocess(const GaussSrc &g, const Selection &sel, int64_t n
                               int32_t *tile_diff, cudaStream_t st) {
     if (n_sel <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((n_sel + 255) / 256);
-    k_preprocess<<<blocks, 256, 0, st>>>(g, sel, n_sel, cam, rp, rec, depth_keys, depth_vals,
-                                         touched, tile_diff);
+    GC_DISPATCH_PREC(g.precision, k_preprocess<PREC_><<<blocks, 256, 0, st>>>(
+                                      g, sel, n_sel, cam, rp, rec, depth_keys, depth_vals, touched, tile_diff))
     note_launches(1);
     return cudaGetLastError();
 }

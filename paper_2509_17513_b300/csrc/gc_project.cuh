@@ -36,8 +36,9 @@ struct Attr {
     int g;
 };
 
+template <int PREC>
 __device__ __forceinline__ void load_attr(const GaussSrc &G, int64_t i, Attr &a, const Residual &res) {
-    if (G.precision == GC_PREC_FP32) {
+    if constexpr (PREC == GC_PREC_FP32) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             a.mu[k] = G.means[3 * i + k];
@@ -46,6 +47,15 @@ __device__ __forceinline__ void load_attr(const GaussSrc &G, int64_t i, Attr &a,
 #pragma unroll
         for (int k = 0; k < 4; ++k) a.q[k] = G.quats[4 * i + k];
         a.logit = G.opacity_logits[i];
+    } else if constexpr (PREC == GC_PREC_PLANES) {
+        const PlaneLoc p = plane_loc(G, i);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a.mu[k] = plane_value(G, p, k);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.q[k] = plane_value(G, p, 3 + k);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a.ls[k] = plane_value(G, p, 7 + k);
+        a.logit = plane_value(G, p, 10);
     } else {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -65,10 +75,19 @@ __device__ __forceinline__ void load_attr(const GaussSrc &G, int64_t i, Attr &a,
     a.g = G.group_id ? G.group_id[i] : 0;
 }
 
+// SH coefficient k, channel c (FP32 or FP8 storage; decoded planes go through sh_plane).
+template <int PREC>
 __device__ __forceinline__ float load_sh(const GaussSrc &G, int64_t i, int k, int c, const Residual &res) {
     int64_t idx = (i * G.K + k) * 3 + c;
-    const float f = G.precision == GC_PREC_FP32 ? G.sh[idx] : fmul(e4m3_to_f32(G.sh_q[idx]), G.scales[11 + 3 * k + c]);
+    const float f = PREC == GC_PREC_FP32 ? G.sh[idx] : fmul(e4m3_to_f32(G.sh_q[idx]), G.scales[11 + 3 * k + c]);
     return res.sh ? fadd(f, res.sh[idx]) : f;
+}
+
+template <int PREC>
+__device__ __forceinline__ float sh_plane(const GaussSrc &G, const PlaneLoc &p, int64_t i, int k, int c,
+                                          const Residual &res) {
+    const float f = plane_value(G, p, 11 + 3 * k + c);
+    return res.sh ? fadd(f, res.sh[(i * G.K + k) * 3 + c]) : f;
 }
 
 
@@ -85,21 +104,23 @@ struct Proj {
 // Per-Gaussian values that depend on no camera or motion: the scales
 // s = (float)exp((double)log_s) (step 5) and tau = (float)(2 ln(255 / (1 + exp(-logit))))
 // (step 14).  A batch computes them once per Gaussian instead of once per request.
+template <int PREC>
 __device__ __forceinline__ float4 gaussian_activation(const GaussSrc &G, int64_t i) {
     Attr A;
-    load_attr(G, i, A, Residual{nullptr, nullptr, nullptr});
+    load_attr<PREC>(G, i, A, Residual{nullptr, nullptr, nullptr});
     return make_float4(exp_f32_of_f64(A.ls[0]), exp_f32_of_f64(A.ls[1]), exp_f32_of_f64(A.ls[2]),
                        tau_f32_of_f64(A.logit));
 }
 
 // act: NULL, or the cached gaussian_activation of every Gaussian (bit-identical results;
 // only without residuals).  res: the frame's residual deformation.
+template <int PREC>
 __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, const float *group_q,
                                                 const float *group_t, int n_groups,
                                                 const CamParams &cam, const RenderParams &rp,
                                                 Proj &P, const float4 *act, const Residual &res) {
     Attr A;
-    load_attr(G, i, A, res);
+    load_attr<PREC>(G, i, A, res);
     P.key = kCulledKey;
     P.ntouch = 0;
     P.tx0 = P.tx1 = P.ty0 = P.ty1 = 0;
@@ -264,9 +285,9 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
         for (int k = 0; k < 16; ++k) Y[k] = 0.f;
         sh_basis(G.sh_degree, dxv * inv, dyv * inv, dzv * inv, Y);
         float rgb[3];
-        if (G.K == 16) {  // degree 3: the 48 coefficients as 16-byte loads, used as they arrive
+        if (PREC != GC_PREC_PLANES && G.K == 16) {  // degree 3: 16-byte loads, used as they arrive
             float acc[3] = {0.f, 0.f, 0.f};
-            if (G.precision == GC_PREC_FP32) {
+            if constexpr (PREC == GC_PREC_FP32) {
                 const float4 *p = reinterpret_cast<const float4 *>(G.sh + i * 48);
 #pragma unroll
                 for (int q = 0; q < 12; ++q) {
@@ -299,13 +320,23 @@ __device__ __forceinline__ void project_gaussian(const GaussSrc &G, int64_t i, c
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) rgb[c] = fmaxf(acc[c] + 0.5f, 0.f);
+        } else if constexpr (PREC == GC_PREC_PLANES) {
+            const PlaneLoc pl = plane_loc(G, i);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k < G.K) acc = fmaf(Y[k], sh_plane<PREC>(G, pl, i, k, c, res), acc);
+                rgb[c] = fmaxf(acc + 0.5f, 0.f);
+            }
         } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float acc = 0.f;
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    if (k < G.K) acc = fmaf(Y[k], load_sh(G, i, k, c, res), acc);
+                    if (k < G.K) acc = fmaf(Y[k], load_sh<PREC>(G, i, k, c, res), acc);
                 rgb[c] = fmaxf(acc + 0.5f, 0.f);
             }
         }

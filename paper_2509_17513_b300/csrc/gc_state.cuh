@@ -192,6 +192,23 @@ inline gc_status make_source(gc_context *ctx, const gc_gaussians *g, const gc_mo
         if (g->n > 0 && (!g->means_bf16 || !g->log_scales_bf16 || !g->quats_bf16 ||
                          !g->opacity_bf16 || !g->sh_e4m3 || !g->scales))
             return fail(ctx, GC_ERR_INVALID_ARG, "a reduced-precision plane or the scales are NULL");
+    } else if (g->precision == GC_PREC_PLANES) {
+        if (g->plane_width < 1) return fail(ctx, GC_ERR_INVALID_ARG, "plane_width must be >= 1");
+        if (g->pos_bits != 16 && g->pos_bits != 32) return fail(ctx, GC_ERR_INVALID_ARG, "pos_bits must be 16 or 32");
+        const int pb = g->pos_bits / 8;
+        if (g->plane_pitch < g->plane_width || g->pos_pitch < (int64_t)g->plane_width * pb || g->pos_pitch % pb)
+            return fail(ctx, GC_ERR_INVALID_ARG, "plane pitches too small or misaligned");
+        if (g->n > 0 && (!g->planes_u8 || !g->planes_pos || !g->dequant))
+            return fail(ctx, GC_ERR_INVALID_ARG, "the decoded planes or the dequantisation table are NULL");
+        for (int l = 0; l < g->n_layers; ++l) {
+            if (g->layer_offsets[l + 1] == g->layer_offsets[l]) continue;
+            if (g->layer_offsets[l + 1] - g->layer_offsets[l] > 0x7FFFFFFFll)
+                return fail(ctx, GC_ERR_INVALID_ARG, "a layer holds more than 2^31 - 1 Gaussians");
+            if (!g->planes_u8[l] || !g->planes_pos[l])
+                return fail(ctx, GC_ERR_INVALID_ARG, "the planes of layer %d are NULL", l);
+            if (reinterpret_cast<uintptr_t>(g->planes_pos[l]) % pb)
+                return fail(ctx, GC_ERR_INVALID_ARG, "the position planes of layer %d are misaligned", l);
+        }
     } else {
         return fail(ctx, GC_ERR_INVALID_ARG, "unknown precision %d", g->precision);
     }
@@ -199,6 +216,20 @@ inline gc_status make_source(gc_context *ctx, const gc_gaussians *g, const gc_mo
     s.opacity_logits = g->opacity_logits; s.sh = g->sh; s.group_id = g->group_id;
     s.means_h = g->means_bf16; s.log_scales_h = g->log_scales_bf16; s.quats_h = g->quats_bf16;
     s.opacity_h = g->opacity_bf16; s.sh_q = g->sh_e4m3; s.scales = g->scales;
+    s.n_layers = g->n_layers;
+    for (int l = 0; l <= g->n_layers; ++l) s.layer_off[l] = g->layer_offsets[l];
+    if (g->precision == GC_PREC_PLANES) {
+        s.plane_width = g->plane_width;
+        s.pos_bits = g->pos_bits;
+        s.n_channels = 11 + 3 * s.K;
+        s.plane_pitch = g->plane_pitch;
+        s.pos_pitch = g->pos_pitch;
+        s.dequant = g->dequant;
+        for (int l = 0; l < g->n_layers; ++l) {
+            s.plane_u8[l] = g->planes_u8 ? g->planes_u8[l] : nullptr;
+            s.plane_pos[l] = g->planes_pos ? static_cast<const uint8_t *>(g->planes_pos[l]) : nullptr;
+        }
+    }
     s.n_groups = 1;
     if (m && (m->q || m->t)) {
         if (m->n_groups < 1 || !m->q || !m->t)

@@ -86,6 +86,36 @@ class GaussianSet:
                            group_id=torch.from_numpy(np.ascontiguousarray(scene.group_id, np.int32)).to(device))
 
     @staticmethod
+    def from_planes(planes: dict, scene, device="cuda") -> "GaussianSet":
+        """Set in the paper's decoded attribute format (Sec. 3.4) from
+        ``synth.scenes.quantize_planes`` output: per layer a uint8 plane buffer and a
+        uint16/uint32 position plane buffer, plus the (lo, step) dequantisation table."""
+        gs = GaussianSet(scene.layer_offsets, scene.sh_degree, _abi.GC_PREC_PLANES,
+                         dequant=torch.from_numpy(np.ascontiguousarray(planes["dequant"], np.float32)).to(device),
+                         group_id=torch.from_numpy(np.ascontiguousarray(scene.group_id, np.int32)).to(device))
+        L = len(planes["u8"])
+        gs.plane_tensors = []
+        u8p = (C.c_void_p * L)()
+        posp = (C.c_void_p * L)()
+        for l in range(L):
+            a = torch.from_numpy(np.ascontiguousarray(planes["u8"][l])).to(device)
+            pos = np.ascontiguousarray(planes["pos"][l])
+            p = torch.from_numpy(pos.view(np.int16) if pos.dtype == np.uint16 else pos.view(np.int32)).to(device)
+            gs.plane_tensors += [a, p]
+            u8p[l] = a.data_ptr() if a.numel() else None
+            posp[l] = p.data_ptr() if p.numel() else None
+        gs.plane_ptrs = (u8p, posp)
+        s = gs.struct
+        s.plane_width = int(planes["plane_width"])
+        s.pos_bits = int(planes["pos_bits"])
+        s.plane_pitch = int(planes["pitch"])
+        s.pos_pitch = int(planes["pos_pitch"])
+        s.planes_u8 = C.cast(u8p, C.c_void_p).value
+        s.planes_pos = C.cast(posp, C.c_void_p).value
+        s.dequant = gs.tensors["dequant"].data_ptr()
+        return gs
+
+    @staticmethod
     def from_quantized(q: dict, scene, device="cuda") -> "GaussianSet":
         """Reduced-precision set from ``synth.scenes.quantize_scene`` output."""
         def u16(a):
