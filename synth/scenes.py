@@ -491,3 +491,28 @@ def quantize_planes(scene: Scene, plane_width: int = 512, pos_bits: int = 16, pi
         pos.append(plp)
     return {"plane_width": plane_width, "pos_bits": pos_bits, "pitch": pitch, "pos_pitch": pos_pitch,
             "u8": u8, "pos": pos, "dequant": dequant}
+
+
+def motion_field_params(rng, n_levels=16, log2_T=15, n_min=16, n_max=512, lo=(-1.5,) * 3, hi=(1.5,) * 3,
+                        table_sigma=1e-2, w_sigma=None, hidden=64) -> dict:
+    """Seeded parameters of a per-Gaussian motion source (Sec. 3.2: a multi-resolution hash grid
+    of n_levels levels, 2 features each, 2^log2_T entries per level, resolutions
+    floor(n_min b^l) growing geometrically to n_max, and two MLPs of one hidden layer):
+    table ~ U(-table_sigma, table_sigma), first-layer weights ~ N(0, 1/fan_in), output weights
+    scaled by 0.05 so that the motion is small."""
+    growth = float(np.exp((np.log(n_max) - np.log(n_min)) / max(n_levels - 1, 1)))
+    T = 1 << log2_T
+    d_in = n_levels * 2
+    HIDDEN, FEAT = hidden, 2
+
+    def w(o, i):
+        s = (1.0 / np.sqrt(i)) if w_sigma is None else w_sigma
+        return rng.normal(0, s, (o, i)).astype(np.float32)
+
+    return {"table": rng.uniform(-table_sigma, table_sigma, (n_levels, T, FEAT)).astype(np.float32),
+            "lo": np.asarray(lo, np.float32), "hi": np.asarray(hi, np.float32),
+            "res": np.array([int(np.floor(n_min * growth ** l)) for l in range(n_levels)], np.int32),
+            "w1t": w(HIDDEN, d_in), "b1t": rng.normal(0, 0.01, HIDDEN).astype(np.float32),
+            "w2t": (w(3, HIDDEN) * 0.05).astype(np.float32), "b2t": np.zeros(3, np.float32),
+            "w1r": w(HIDDEN, d_in), "b1r": rng.normal(0, 0.01, HIDDEN).astype(np.float32),
+            "w2r": (w(4, HIDDEN) * 0.05).astype(np.float32), "b2r": np.zeros(4, np.float32)}
