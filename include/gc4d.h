@@ -136,6 +136,11 @@ typedef struct {
     const float *res_log_scales;     /* n x 3 FP32, or NULL */
     const float *res_opacity_logits; /* n FP32, or NULL */
     const float *res_sh;             /* n x K x 3 FP32 (the set's K), or NULL */
+    int32_t per_gaussian;            /* 1: one rigid motion per Gaussian (Sec. 3.2: dmu and dR from
+                                        the motion source, e.g. gc_motion_field_forward): q is n x 4,
+                                        t is n x 3, indexed by global Gaussian index; group ids and
+                                        n_groups are ignored and the backward's d_group_q / d_group_t
+                                        are n x 4 / n x 3.  Single-frame and multi-level calls only. */
 } gc_motion;
 
 /* Pinhole camera (host, by value). X_cam = R X_world + t. */
@@ -159,6 +164,33 @@ typedef struct {
     float *d_group_q;        /* G x 4 */
     float *d_group_t;        /* G x 3 */
 } gc_grads;
+
+/* Per-Gaussian motion source (Sec. 3.2, rigid transformation): the positions of frame t-1
+ * are encoded by a multi-resolution hash grid and two small MLPs give each Gaussian's
+ * translation dmu and rotation dR.  Sizes the paper leaves open are fixed as: 2 features per
+ * level, MLPs of one hidden layer of 64 ReLU units, translation = W2t relu(W1t h + b1t) + b2t,
+ * rotation quaternion = W2r relu(W1r h + b1r) + b2r + (1, 0, 0, 0) (not normalised; the
+ * renderer normalises q_g (x) q).  Level l: x = (mu - lo) / (hi - lo) clamped to [0, 1] per
+ * axis, p = x N_l, cell = floor(p) clamped to [0, N_l - 1], w = p - cell (FP32, each
+ * operation rounded once); vertex (i, j, k) is table entry i + (N_l + 1)(j + (N_l + 1) k) when
+ * (N_l + 1)^3 <= T, else (i xor 2654435761 j xor 805459861 k) mod 2^32 mod T; h = per level the
+ * trilinear blend of the cell's 8 vertex features. */
+typedef struct {
+    int32_t n_levels;          /* L_h, 1..16; the MLP input width is 2 L_h */
+    int32_t log2_table;        /* T = 2^log2_table entries per level, 4..26 */
+    int32_t resolution[16];    /* N_l >= 1 per level (first n_levels used) */
+    float lo[3], hi[3];        /* box mapped to [0, 1]^3, hi > lo per axis */
+    const float *table;        /* device, n_levels x T x 2 */
+    const float *w1t, *b1t, *w2t, *b2t; /* device, row-major (out x in): 64 x 2L_h, 64, 3 x 64, 3 */
+    const float *w1r, *b1r, *w2r, *b2r; /* device: 64 x 2L_h, 64, 4 x 64, 4 */
+} gc_motion_field;
+
+/* Gradients of a motion source (device, overwritten; any NULL is skipped).  The table
+ * gradient is accumulated with atomic additions (its summation order is not fixed); the
+ * weight gradients are summed per block and then over blocks in a fixed order. */
+typedef struct {
+    float *table, *w1t, *b1t, *w2t, *b2t, *w1r, *b1r, *w2r, *b2r;
+} gc_motion_field_grads;
 
 /* Per-frame statistics of a saved forward. */
 typedef struct {
@@ -364,6 +396,18 @@ GC_API gc_status gc_tune_batch(gc_context *ctx, const gc_gaussians *g, const gc_
                                const float *const *dL_dimages, gc_grads *grads, const int32_t *depths,
                                int32_t n_depths, int32_t iters, gc_tune_entry *entries,
                                gc_tune_entry *best, void *stream);
+
+/* Motion source forward: for the n Gaussians at means (device, n x 3, the frame t-1
+ * positions) writes q (device, n x 4, dR) and t (device, n x 3, dmu), which a gc_motion with
+ * per_gaussian = 1 applies to the frame t-1 Gaussians (mu_t = mu + dmu, R_t = dR R). */
+GC_API gc_status gc_motion_field_forward(gc_context *ctx, const gc_motion_field *field, const float *means,
+                                         int64_t n, float *q, float *t, void *stream);
+
+/* Motion source backward: given dL/dq (n x 4) and dL/dt (n x 3) - the d_group_q / d_group_t of
+ * a per-Gaussian render backward - writes the gradients of the table and the MLP weights. */
+GC_API gc_status gc_motion_field_backward(gc_context *ctx, const gc_motion_field *field, const float *means,
+                                          int64_t n, const float *d_q, const float *d_t,
+                                          gc_motion_field_grads *out, void *stream);
 
 /* Statistics of the last forward recorded in `saved` (synchronises `stream`). */
 GC_API gc_status gc_saved_stats(gc_context *ctx, const gc_saved *saved, gc_stats *out, void *stream);

@@ -54,7 +54,19 @@ class Gaussians(C.Structure):
 
 class Motion(C.Structure):
     _fields_ = [("n_groups", C.c_int32), ("q", C.c_void_p), ("t", C.c_void_p),
-                ("res_log_scales", C.c_void_p), ("res_opacity_logits", C.c_void_p), ("res_sh", C.c_void_p)]
+                ("res_log_scales", C.c_void_p), ("res_opacity_logits", C.c_void_p), ("res_sh", C.c_void_p),
+                ("per_gaussian", C.c_int32)]
+
+
+class MotionField(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("log2_table", C.c_int32), ("resolution", C.c_int32 * 16),
+                ("lo", C.c_float * 3), ("hi", C.c_float * 3), ("table", C.c_void_p),
+                ("w1t", C.c_void_p), ("b1t", C.c_void_p), ("w2t", C.c_void_p), ("b2t", C.c_void_p),
+                ("w1r", C.c_void_p), ("b1r", C.c_void_p), ("w2r", C.c_void_p), ("b2r", C.c_void_p)]
+
+
+class MotionFieldGrads(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("table", "w1t", "b1t", "w2t", "b2t", "w1r", "b1r", "w2r", "b2r")]
 
 
 class Camera(C.Structure):
@@ -97,6 +109,8 @@ SIGNATURES = {
     "gc_render_forward_noalloc": (C.c_int, [P, P, P, C.c_uint32, P, P, P, C.c_char_p, C.c_size_t]),
     "gc_render_levels_forward": (C.c_int, [P, P, P, C.c_int32, P, P, P, P]),
     "gc_render_levels_backward": (C.c_int, [P, P, P, P, P, P, P]),
+    "gc_motion_field_forward": (C.c_int, [P, P, P, C.c_int64, P, P, P]),
+    "gc_motion_field_backward": (C.c_int, [P, P, P, C.c_int64, P, P, P, P]),
     "gc_render_batch_forward": (C.c_int, [P, P, P, C.c_int32, P, C.c_int32, P, P]),
     "gc_render_batch_backward": (C.c_int, [P, P, P, P, C.c_int32, P, C.c_int32, P, P]),
     "gc_batch_graph_create": (C.c_int, [P, P, P, C.c_int32, P, C.c_int32, C.c_int32, P, P, P, P]),

@@ -94,7 +94,7 @@ gc_status gc_destroy(gc_context *ctx) {
         saved_release(ctx, &ctx->internal);
         ctx->internal.batch.reset();
         DevBuf *bufs[] = {&ctx->scratch, &ctx->bwd_part, &ctx->bwd_g2d, &ctx->bwd_motion,
-                          &ctx->bwd_group};
+                          &ctx->bwd_group, &ctx->field_part};
         for (DevBuf *b : bufs) release(*b);
         if (ctx->host_word) cudaFreeHost(ctx->host_word);
         for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
@@ -164,6 +164,7 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
     S.sh_degree = g->sh_degree;
     S.n_groups = src.n_groups;
     S.has_motion = src.group_q != nullptr;
+    S.per_gaussian = src.per_gaussian;
     S.res = src.res;
     S.n_layers = g->n_layers;
     for (int l = 0; l <= g->n_layers; ++l) S.layer_offsets[l] = g->layer_offsets[l];
@@ -455,7 +456,8 @@ static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, co
     if (st != GC_OK) return st;
     if (g->n != S.n || g->sh_degree != S.sh_degree || g->n_layers != S.n_layers)
         return fail(ctx, GC_ERR_STATE, "the Gaussian set differs from the one of the saved forward");
-    if ((src.group_q != nullptr) != S.has_motion || (S.has_motion && src.n_groups != S.n_groups))
+    if ((src.group_q != nullptr) != S.has_motion || (S.has_motion && src.n_groups != S.n_groups) ||
+        src.per_gaussian != S.per_gaussian)
         return fail(ctx, GC_ERR_STATE, "the motion differs from the one of the saved forward");
     if (src.res.ls != S.res.ls || src.res.logit != S.res.logit || src.res.sh != S.res.sh)
         return fail(ctx, GC_ERR_STATE, "the residual deformation differs from the one of the saved forward");
@@ -489,7 +491,7 @@ static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, co
     if (!ctx->bwd_part_clean) GC_CUDA(ctx, cudaMemsetAsync(ctx->bwd_part.p, 0, ctx->bwd_part.cap, s));
     GC_CUDA(ctx, grow(ctx->bwd_g2d, (size_t)S.n_sel * 9 * 4));
     GC_CUDA(ctx, grow(ctx->bwd_motion, (size_t)S.n_sel * 7 * 4));
-    if (G) GC_CUDA(ctx, grow(ctx->bwd_group, gc::group_partial_floats(S.n_sel, G) * 4));
+    if (G && !S.per_gaussian) GC_CUDA(ctx, grow(ctx->bwd_group, gc::group_partial_floats(S.n_sel, G) * 4));
     const uint32_t *sorted_vals = S.K > 0 ? S.tvals[S.tile_buf].as<uint32_t>() : nullptr;
 
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_BLEND_BWD));
@@ -515,7 +517,14 @@ static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, co
     GC_CUDA(ctx, gc::launch_preprocess_bwd(src, S.sel, S.n_sel, S.cam, S.rp, ctx->bwd_g2d.as<float>(),
                                            S.touched.as<uint32_t>(), *out,
                                            G ? ctx->bwd_motion.as<float>() : nullptr, s));
-    if (G) {
+    if (G && S.per_gaussian) {
+        // one motion per Gaussian: its motion terms are its gradient (zero when not selected)
+        GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_GROUP_REDUCE));
+        if (out->d_group_q) GC_CUDA(ctx, cudaMemsetAsync(out->d_group_q, 0, (size_t)G * 16, s));
+        if (out->d_group_t) GC_CUDA(ctx, cudaMemsetAsync(out->d_group_t, 0, (size_t)G * 12, s));
+        GC_CUDA(ctx, gc::launch_motion_scatter(ctx->bwd_motion.as<float>(), S.sel, S.n_sel, out->d_group_q,
+                                               out->d_group_t, s));
+    } else if (G) {
         GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_GROUP_REDUCE));
         GC_CUDA(ctx, gc::launch_group_reduce(ctx->bwd_motion.as<float>(), src.group_id, S.sel, S.n_sel, G,
                                              ctx->bwd_group.as<float>(), out->d_group_q, out->d_group_t, s));

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(GaussSrc G, Selection se
     for (int k = 0; k < K3; ++k) acc.dsh[k] = 0.f;
     float m7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (touched[j] != 0) {
-        const int g = (G.group_q && G.group_id) ? G.group_id[i] : 0;
+        const int g = G.per_gaussian ? (int)i : ((G.group_q && G.group_id) ? G.group_id[i] : 0);
         chain_rule<PREC>(G, i, G.group_q, G.group_t, g, cam, rp, g2d + 9 * j, acc, m7, G.res);
     }
     if (out.d_means) for (int k = 0; k < 3; ++k) out.d_means[3 * i + k] = acc.dmu[k];
@@ -83,6 +83,18 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(GaussSrc G, Selection se
     if (out.d_opacity_logits) out.d_opacity_logits[i] = acc.dlogit;
     if (out.d_sh) for (int k = 0; k < K3; ++k) out.d_sh[i * K3 + k] = acc.dsh[k];
     if (mcontrib) for (int k = 0; k < 7; ++k) mcontrib[7 * j + k] = m7[k];
+}
+
+// Per-Gaussian motion: scatter each selected Gaussian's motion terms to its own rows.
+__global__ void k_motion_scatter(const float *__restrict__ mcontrib, Selection sel, int64_t n_sel,
+                                 float *__restrict__ d_q, float *__restrict__ d_t) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_sel) return;
+    const int64_t i = sel_global(sel, j);
+    if (d_q)
+        for (int k = 0; k < 4; ++k) d_q[4 * i + k] = mcontrib[7 * j + k];
+    if (d_t)
+        for (int k = 0; k < 3; ++k) d_t[3 * i + k] = mcontrib[7 * j + 4 + k];
 }
 
 constexpr int kGroupChunk = 256;
@@ -189,6 +201,14 @@ cudaError_t launch_preprocess_bwd(const GaussSrc &g, const Selection &sel, int64
 size_t group_partial_floats(int64_t n_sel, int n_groups) {
     const int64_t chunks = (n_sel + kGroupChunk - 1) / kGroupChunk;
     return (size_t)std::max<int64_t>(chunks, 1) * n_groups * 7;
+}
+
+cudaError_t launch_motion_scatter(const float *motion_contrib, const Selection &sel, int64_t n_sel, float *d_q,
+                                  float *d_t, cudaStream_t st) {
+    if (n_sel <= 0) return cudaSuccess;
+    k_motion_scatter<<<(unsigned)((n_sel + 255) / 256), 256, 0, st>>>(motion_contrib, sel, n_sel, d_q, d_t);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_group_reduce(const float *motion_contrib, const int32_t *group_id,

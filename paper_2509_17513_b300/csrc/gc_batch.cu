@@ -645,9 +645,12 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     if (st != GC_OK) return st;
     src.group_id = g->group_id;  // motion applies per request
     const int n_groups = n_frames > 0 ? frames[0].n_groups : 1;
-    for (int f = 0; f < n_frames; ++f)
+    for (int f = 0; f < n_frames; ++f) {
+        if (frames[f].per_gaussian)
+            return fail(ctx, GC_ERR_UNSUPPORTED, "per-Gaussian motion is taken by the single-frame and multi-level calls");
         if (frames[f].n_groups != n_groups || !frames[f].q || !frames[f].t)
             return fail(ctx, GC_ERR_INVALID_ARG, "motion frames must share n_groups and have q, t");
+    }
     const gc_options &o = ctx->opt;
     DeviceGuard dg(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;

@@ -88,6 +88,7 @@ struct GaussSrc {
     const float *scales;
     const float *group_q, *group_t;  // NULL = identity motion
     int n_groups;
+    int per_gaussian;                // 1: group index = global Gaussian index (n_groups = n)
     Residual res;                    // the frame's residual deformation
     // GC_PREC_PLANES (the decoded attribute planes): per-layer plane buffers and offsets
     int n_layers, plane_width, pos_bits, n_channels;
@@ -263,6 +264,8 @@ cudaError_t launch_preprocess_bwd(const GaussSrc &g, const Selection &sel, int64
 // Deterministic per-group sums of the motion terms.  `partial` needs
 // group_partial_floats(n_sel, n_groups) floats.
 size_t group_partial_floats(int64_t n_sel, int n_groups);
+cudaError_t launch_motion_scatter(const float *motion_contrib, const Selection &sel, int64_t n_sel, float *d_q,
+                                  float *d_t, cudaStream_t st);
 cudaError_t launch_group_reduce(const float *motion_contrib, const int32_t *group_id,
                                 const Selection &sel, int64_t n_sel, int n_groups, float *partial,
                                 float *d_group_q, float *d_group_t, cudaStream_t st);

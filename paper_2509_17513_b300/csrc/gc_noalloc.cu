@@ -159,7 +159,8 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
         (!g->means_bf16 || !g->log_scales_bf16 || !g->quats_bf16 || !g->opacity_bf16 ||
          !g->sh_e4m3 || !g->scales))
         return say(err, err_len, GC_ERR_INVALID_ARG, "a reduced-precision plane is NULL");
-    if (motion && (motion->q || motion->t) && (motion->n_groups < 1 || !motion->q || !motion->t))
+    if (motion && (motion->q || motion->t || motion->per_gaussian) &&
+        ((!motion->per_gaussian && motion->n_groups < 1) || !motion->q || !motion->t))
         return say(err, err_len, GC_ERR_INVALID_ARG, "invalid motion");
     if (motion && motion->res_sh && g->sh_degree == 3 && (reinterpret_cast<uintptr_t>(motion->res_sh) & 15))
         return say(err, err_len, GC_ERR_INVALID_ARG, "res_sh must be 16-byte aligned");
@@ -211,10 +212,11 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
     src.n_groups = 1;
     if (motion) src.res = gc::Residual{motion->res_log_scales, motion->res_opacity_logits, motion->res_sh};
     if (motion && motion->q) {
-        src.group_id = g->group_id;
+        src.group_id = motion->per_gaussian ? nullptr : g->group_id;
         src.group_q = motion->q;
         src.group_t = motion->t;
-        src.n_groups = motion->n_groups;
+        src.n_groups = motion->per_gaussian ? (int)(g->n > 0 ? g->n : 1) : motion->n_groups;
+        src.per_gaussian = motion->per_gaussian ? 1 : 0;
     }
     gc::CamParams cp;
     cp.width = cam->width; cp.height = cam->height;

@@ -72,7 +72,7 @@ __device__ __forceinline__ void load_attr(const GaussSrc &G, int64_t i, Attr &a,
         for (int k = 0; k < 3; ++k) a.ls[k] = fadd(a.ls[k], res.ls[3 * i + k]);
     }
     if (res.logit) a.logit = fadd(a.logit, res.logit[i]);
-    a.g = G.group_id ? G.group_id[i] : 0;
+    a.g = G.per_gaussian ? (int)i : (G.group_id ? G.group_id[i] : 0);
 }
 
 // SH coefficient k, channel c (FP32 or FP8 storage; decoded planes go through sh_plane).

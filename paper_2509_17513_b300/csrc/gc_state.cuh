@@ -66,6 +66,7 @@ struct gc_saved {
     int64_t n = 0, n_sel = 0;
     int sh_degree = 0, n_groups = 1;
     bool has_motion = false;
+    int per_gaussian = 0;
     gc::Residual res{nullptr, nullptr, nullptr};  // residual arrays of the forward
     int n_layers = 0;
     int64_t layer_offsets[gc::kMaxLayers + 1] = {};
@@ -97,6 +98,7 @@ struct gc_context {
     gc_options opt{};
     gc_saved internal;
     DevBuf scratch, bwd_part, bwd_g2d, bwd_motion, bwd_group;
+    DevBuf field_part;              // per-block partial gradients of the motion source
     bool bwd_part_clean = false;  // bwd_part holds only zeros (see the reduce)
     uint32_t *host_word = nullptr;  // pinned
     const gc_saved *last = nullptr; // state written by the most recent forward
@@ -231,7 +233,14 @@ inline gc_status make_source(gc_context *ctx, const gc_gaussians *g, const gc_mo
         }
     }
     s.n_groups = 1;
-    if (m && (m->q || m->t)) {
+    if (m && m->per_gaussian) {
+        if (!m->q || !m->t) return fail(ctx, GC_ERR_INVALID_ARG, "per-Gaussian motion needs q and t arrays");
+        s.group_q = m->q;
+        s.group_t = m->t;
+        s.n_groups = (int)std::max<int64_t>(g->n, 1);
+        s.per_gaussian = 1;
+        s.group_id = nullptr;
+    } else if (m && (m->q || m->t)) {
         if (m->n_groups < 1 || !m->q || !m->t)
             return fail(ctx, GC_ERR_INVALID_ARG, "motion needs n_groups >= 1 and both q and t arrays");
         s.group_q = m->q;

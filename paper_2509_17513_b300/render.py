@@ -136,7 +136,7 @@ class MotionFrame:
     res_log_scales (n,3), res_opacity_logits (n,), res_sh (n,K,3), each None for none."""
 
     def __init__(self, q: torch.Tensor | None, t: torch.Tensor | None, res_log_scales=None,
-                 res_opacity_logits=None, res_sh=None):
+                 res_opacity_logits=None, res_sh=None, per_gaussian: bool = False):
         self.q = q.contiguous() if q is not None else None
         self.t = t.contiguous() if t is not None else None
         self.res = [x.contiguous() if x is not None else None
@@ -147,6 +147,7 @@ class MotionFrame:
         s.t = self.t.data_ptr() if t is not None else None
         s.res_log_scales, s.res_opacity_logits, s.res_sh = [x.data_ptr() if x is not None else None
                                                             for x in self.res]
+        s.per_gaussian = 1 if per_gaussian else 0
         self.struct = s
 
     @staticmethod
@@ -159,6 +160,30 @@ class MotionFrame:
         if residual is None:
             return MotionFrame(q, t)
         return MotionFrame(q, t, dev(residual.ls), dev(residual.logit), dev(residual.sh))
+
+
+class MotionField:
+    """Parameters of a per-Gaussian motion source (Sec. 3.2): hash-grid table (L, T, 2) and the
+    translation / rotation MLPs, as CUDA float32 tensors (``synth.scenes.motion_field_params``
+    layout), plus the level resolutions and the box of the positions."""
+
+    NAMES = ("table", "w1t", "b1t", "w2t", "b2t", "w1r", "b1r", "w2r", "b2r")
+
+    def __init__(self, params: dict, device="cuda"):
+        self.t = {k: torch.as_tensor(np.ascontiguousarray(params[k], np.float32)).to(device).contiguous()
+                  for k in self.NAMES}
+        L, T, _ = self.t["table"].shape
+        s = _abi.MotionField()
+        s.n_levels = int(L)
+        s.log2_table = int(T).bit_length() - 1
+        for l, r in enumerate(np.asarray(params["res"]).tolist()):
+            s.resolution[l] = int(r)
+        for a in range(3):
+            s.lo[a] = float(params["lo"][a])
+            s.hi[a] = float(params["hi"][a])
+        for k in self.NAMES:
+            setattr(s, k, self.t[k].data_ptr())
+        self.struct = s
 
 
 class Saved:
@@ -312,6 +337,31 @@ class Renderer:
             grads["group_q"] = torch.empty((G, 4), device=dev)
             grads["group_t"] = torch.empty((G, 3), device=dev)
         return grads
+
+    # ---- per-Gaussian motion source ---------------------------------------------------
+
+    def motion_field_forward(self, field: "MotionField", means: torch.Tensor, stream=None):
+        """(q (n,4), t (n,3)): each Gaussian's rotation and translation from the motion source
+        at the frame t-1 positions ``means``; use as MotionFrame(q, t, per_gaussian=True)."""
+        n = int(means.shape[0])
+        dev = means.device
+        q = torch.empty((n, 4), device=dev)
+        t = torch.empty((n, 3), device=dev)
+        check(lib().gc_motion_field_forward(self.ctx, C.byref(field.struct), means.contiguous().data_ptr(), n,
+                                            q.data_ptr(), t.data_ptr(), _stream(stream)), self.ctx)
+        return q, t
+
+    def motion_field_backward(self, field: "MotionField", means: torch.Tensor, d_q: torch.Tensor,
+                              d_t: torch.Tensor, stream=None) -> dict:
+        """Gradients of the motion source's table and weights given dL/dq, dL/dt."""
+        g = {k: torch.empty_like(v) for k, v in field.t.items()}
+        s = _abi.MotionFieldGrads()
+        for k in MotionField.NAMES:
+            setattr(s, k, g[k].data_ptr())
+        check(lib().gc_motion_field_backward(self.ctx, C.byref(field.struct), means.contiguous().data_ptr(),
+                                             int(means.shape[0]), d_q.contiguous().data_ptr(),
+                                             d_t.contiguous().data_ptr(), C.byref(s), _stream(stream)), self.ctx)
+        return g
 
     # ---- batched requests -------------------------------------------------------------
 
