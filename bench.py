@@ -462,6 +462,60 @@ def run_gpu(args):
         r.set_options(key_capacity=0)
         torch.cuda.empty_cache()
 
+    # ---- per-Gaussian motion source (Sec. 3.2): per frame the hash-grid + MLP motion of all
+    # 300k Gaussians, then the multi-level render with one rigid motion per Gaussian
+    field_obj = None
+    if "field" not in skip:
+        fp = scenes.motion_field_params(np.random.default_rng(12), n_levels=16, log2_T=19, n_min=16, n_max=2048)
+        field = gc.MotionField(fp, dev)
+        means_d = gs.tensors["means"]
+        fq, ft = r.motion_field_forward(field, means_d)
+        r.set_options(key_capacity=0, tile=tile)
+        r.levels_forward(gs, gc.MotionFrame(fq, ft, per_gaussian=True), 6, w.cameras[0], outs=outs[0:6])
+        fcap = int(r.stats()["n_keys"] * 1.3) + 4096
+        r.set_options(key_capacity=fcap, tile=tile)
+        gq_up = torch.randn((w.scene.n, 4), generator=torch.Generator(device=dev).manual_seed(3), device=dev)
+        gt_up = torch.randn((w.scene.n, 3), generator=torch.Generator(device=dev).manual_seed(4), device=dev)
+
+        def field_fwd():
+            for _ in range(args.frames):
+                r.motion_field_forward(field, means_d)
+
+        def field_bwd():
+            for _ in range(args.frames):
+                r.motion_field_backward(field, means_d, gq_up, gt_up)
+
+        def field_step():
+            for f in range(args.frames):
+                q_, t_ = r.motion_field_forward(field, means_d)
+                r.levels_forward(gs, gc.MotionFrame(q_, t_, per_gaussian=True), 6, w.cameras[f],
+                                 outs=outs[6 * f:6 * f + 6])
+
+        for _ in range(args.warmup):
+            field_fwd()
+            field_bwd()
+            field_step()
+        r.check()
+        mff_ms, _, _ = timer(field_fwd, args.steps, name="field_fwd")
+        mfb_ms, _, _ = timer(field_bwd, args.steps, name="field_bwd")
+        mfs_ms, _, clk_fs = timer(field_step, args.steps, name="field_step")
+        r.check()
+        n_g = w.scene.n
+        per_ms_f = mff_ms / args.steps / args.frames
+        field_obj = {"form": "per-Gaussian motion source (Sec. 3.2): 16-level hash grid (2^19 entries x 2 features "
+                             "per level, resolutions 16..2048) + translation and rotation MLPs (32-64-3, 32-64-4) "
+                             "for the 300k Gaussians of every frame, then the multi-level render with one rigid "
+                             "motion per Gaussian",
+                     "field_fwd_ms_per_frame": round(per_ms_f, 4),
+                     "field_bwd_ms_per_frame": round(mfb_ms / args.steps / args.frames, 4),
+                     "field_fwd_gaussians_per_s": round(n_g / (per_ms_f / 1e3), 1),
+                     "field_fwd_tflops": round(n_g * 2 * (2 * 64 * 32 + 7 * 64) / (per_ms_f / 1e3) / 1e12, 3),
+                     "step_fwd": mpix(mfs_ms, args.steps), "unit": UNIT, "key_capacity": fcap,
+                     "clocks": clk_fs}
+        del field, fq, ft, gq_up, gt_up
+        r.set_options(key_capacity=0)
+        torch.cuda.empty_cache()
+
     # ---- residual deformation (Eq. 7): the same multi-level step with per-frame log-scale,
     # logit and SH residuals fused into the preprocess (device-generated, N(0, f sigma^2))
     residual_obj = None
@@ -541,6 +595,7 @@ def run_gpu(args):
             "batched": batched_obj,
             "residual_deformation": residual_obj,
             "decoded_planes": planes_obj,
+            "motion_field": field_obj,
             "single_view": single_view,
             "reduced_precision": precision_obj,
             "autotune": tune,
@@ -770,7 +825,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch128", action="store_true", help="skip the 128-request batching workload")
-    ap.add_argument("--skip-forms", default="", help="comma list of side forms to leave out: single, batched, residual, planes "
+    ap.add_argument("--skip-forms", default="", help="comma list of side forms to leave out: single, batched, residual, planes, field "
                     "(then 8x32 tiles are used and the BF16/FP8 form is left out too)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -240,13 +240,12 @@ __global__ void __launch_bounds__(kFT) k_field_bwd(Field F, const float *__restr
             float w[3];
             level_cell(F, l, x, c, w);
             const bool dense = level_dense(F.res[l], F.log2T);
-            float *tab = d_table + (size_t)l * T * 2;
+            float2 *tab = reinterpret_cast<float2 *>(d_table) + (size_t)l * T;
             for (int corner = 0; corner < 8; ++corner) {
                 const int o0 = corner & 1, o1 = (corner >> 1) & 1, o2 = (corner >> 2) & 1;
                 const float wt = (o0 ? w[0] : 1.f - w[0]) * (o1 ? w[1] : 1.f - w[1]) * (o2 ? w[2] : 1.f - w[2]);
                 const uint32_t idx = vertex_index(c[0] + o0, c[1] + o1, c[2] + o2, F.res[l], dense, T);
-                atomicAdd(tab + 2 * idx, wt * dh[2 * l]);
-                atomicAdd(tab + 2 * idx + 1, wt * dh[2 * l + 1]);
+                atomicAdd(tab + idx, make_float2(wt * dh[2 * l], wt * dh[2 * l + 1]));  // one vector atomic
             }
         }
     }
@@ -336,6 +335,7 @@ extern "C" gc_status gc_motion_field_backward(gc_context *ctx, const gc_motion_f
     gc_status st = gc::make_field(ctx, field, F);
     if (st != GC_OK) return st;
     if (!out) return fail(ctx, GC_ERR_INVALID_ARG, "grads is NULL");
+    if (reinterpret_cast<uintptr_t>(out->table) & 7) return fail(ctx, GC_ERR_INVALID_ARG, "the table gradient must be 8-byte aligned");
     if (n < 0) return fail(ctx, GC_ERR_INVALID_ARG, "n < 0");
     if (n > 0 && (!means || !d_q || !d_t)) return fail(ctx, GC_ERR_INVALID_ARG, "means, d_q or d_t is NULL");
     DeviceGuard dg(ctx->device);
