@@ -130,9 +130,10 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
     }
 }
 
-// Reverse: one CTA of 256 threads per tile, one pixel per thread; NL levels.
+// Reverse: one CTA of 256 threads per tile, one pixel per thread; NL levels.  Three CTAs per
+// SM (at most 85 registers; a few spill) measured faster than two without spills.
 template <int TW, int TH, int NL>
-__global__ void __launch_bounds__(256) k_blend_levels_bwd(
+__global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, RenderParams rp,
     const float *__restrict__ lv_T, const uint32_t *__restrict__ lv_last, LevelGrads dimg,
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(256) k_blend_levels_bwd(
         uint32_t m[256 * 8];
         uint32_t e[256];
         uint8_t lay[256];
-        float wpart[32][8][9];
+        float wpart[64][8][9];
         uint32_t wsuf[8][16];  // per warp: max over its pixels and levels l >= m of last[l]
         uint32_t last_max;
     };
@@ -223,113 +224,116 @@ __global__ void __launch_bounds__(256) k_blend_levels_bwd(
             }
         }
         __syncthreads();
-        for (int gtop = hi; gtop > lo; gtop -= 32) {
-            const int gbot = max(gtop - 32, lo);
-            // entries of the group that a pixel of the warp blended at some level: footprint
-            // over a pixel with work, and a level >= the entry's layer still past it
-            const int kq = gbot + lane;
-            bool rel = false;
-            if (kq < gtop) {
-                const int sq = kq - lo;
-                rel = (sm.m[warp * 256 + sq] & wpix) != 0u && (uint32_t)kq < sm.wsuf[warp][sm.lay[sq]];
-                if (!rel) {
+        for (int gtop = hi; gtop > lo; gtop -= 64) {
+            const int gbot = max(gtop - 64, lo);
+            for (int stop = gtop; stop > gbot; stop -= 32) {   // two halves of 32, upper first
+                const int sbot = max(stop - 32, gbot);
+                // entries of the half that a pixel of the warp blended at some level: footprint
+                // over a pixel with work, and a level >= the entry's layer still past it
+                const int kq = sbot + lane;
+                bool rel = false;
+                if (kq < stop) {
+                    const int sq = kq - lo;
+                    rel = (sm.m[warp * 256 + sq] & wpix) != 0u && (uint32_t)kq < sm.wsuf[warp][sm.lay[sq]];
+                    if (!rel) {
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) sm.wpart[lane][warp][c] = 0.f;
-                }
-            }
-            uint32_t todo = __ballot_sync(0xffffffffu, rel);
-            while (todo) {
-                const int j = 31 - __clz(todo);
-                todo &= ~(1u << j);
-                const int k = gbot + j;
-                const int s = k - lo;
-                float v[9];
-#pragma unroll
-                for (int c = 0; c < 9; ++c) v[c] = 0.f;
-                bool contrib = false;
-                const uint32_t wm = sm.m[warp * 256 + s];
-                uint32_t lm = 0u;  // levels of this pixel that blended entry k
-#pragma unroll
-                for (int l = 0; l < NL; ++l)
-                    if (l >= (int)sm.lay[s] && (uint32_t)k < last[l]) lm |= 1u << l;
-                if ((wm & bit) != 0u && lm) {
-                    const float4 a = sm.a[s];
-                    const float2 bb = sm.b[s];
-                    const float dx = pcx - a.x, dy = pcy - a.y;
-                    const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
-                    float G = 0.f, a0 = 0.f, alpha = 0.f;
-                    bool blended = p2 <= 0.f;
-                    if (blended) {
-                        a0 = blend_raw_alpha(bb.y, p2, G);
-                        alpha = fminf(kAlphaMax, a0);
-                        blended = !(alpha < kAlphaMin);
+                        for (int c = 0; c < 9; ++c) sm.wpart[kq - gbot][warp][c] = 0.f;
                     }
-                    if (blended) {
-                        contrib = true;
-                        const float4 col = sm.c[s];
-                        float dp = 0.f;
+                }
+                uint32_t todo = __ballot_sync(0xffffffffu, rel);
+                while (todo) {
+                    const int j = 31 - __clz(todo);
+                    todo &= ~(1u << j);
+                    const int k = sbot + j;
+                    const int s = k - lo;
+                    float v[9];
 #pragma unroll
-                        for (int l = 0; l < NL; ++l) {
-                            if (!((lm >> l) & 1u)) continue;
-                            T[l] = __fdividef(T[l], 1.f - alpha);
-                            const float w = alpha * T[l];
-                            v[6] += w * g0[l];
-                            v[7] += w * g1[l];
-                            v[8] += w * g2[l];
-                            const float dal = T[l] * (g0[l] * (col.x - A0[l]) + g1[l] * (col.y - A1[l]) +
-                                                      g2[l] * (col.z - A2[l]));
-                            A0[l] = fmaf(alpha, col.x - A0[l], A0[l]);
-                            A1[l] = fmaf(alpha, col.y - A1[l], A1[l]);
-                            A2[l] = fmaf(alpha, col.z - A2[l], A2[l]);
-                            if (!(a0 > kAlphaMax)) {
-                                v[5] += G * dal;
-                                dp += alpha * dal;  // dL/dpower (natural exponent), summed over levels
+                    for (int c = 0; c < 9; ++c) v[c] = 0.f;
+                    bool contrib = false;
+                    const uint32_t wm = sm.m[warp * 256 + s];
+                    uint32_t lm = 0u;  // levels of this pixel that blended entry k
+#pragma unroll
+                    for (int l = 0; l < NL; ++l)
+                        if (l >= (int)sm.lay[s] && (uint32_t)k < last[l]) lm |= 1u << l;
+                    if ((wm & bit) != 0u && lm) {
+                        const float4 a = sm.a[s];
+                        const float2 bb = sm.b[s];
+                        const float dx = pcx - a.x, dy = pcy - a.y;
+                        const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
+                        float G = 0.f, a0 = 0.f, alpha = 0.f;
+                        bool blended = p2 <= 0.f;
+                        if (blended) {
+                            a0 = blend_raw_alpha(bb.y, p2, G);
+                            alpha = fminf(kAlphaMax, a0);
+                            blended = !(alpha < kAlphaMin);
+                        }
+                        if (blended) {
+                            contrib = true;
+                            const float4 col = sm.c[s];
+                            float dp = 0.f;
+#pragma unroll
+                            for (int l = 0; l < NL; ++l) {
+                                if (!((lm >> l) & 1u)) continue;
+                                T[l] = __fdividef(T[l], 1.f - alpha);
+                                const float w = alpha * T[l];
+                                v[6] += w * g0[l];
+                                v[7] += w * g1[l];
+                                v[8] += w * g2[l];
+                                const float dal = T[l] * (g0[l] * (col.x - A0[l]) + g1[l] * (col.y - A1[l]) +
+                                                          g2[l] * (col.z - A2[l]));
+                                A0[l] = fmaf(alpha, col.x - A0[l], A0[l]);
+                                A1[l] = fmaf(alpha, col.y - A1[l], A1[l]);
+                                A2[l] = fmaf(alpha, col.z - A2[l], A2[l]);
+                                if (!(a0 > kAlphaMax)) {
+                                    v[5] += G * dal;
+                                    dp += alpha * dal;  // dL/dpower (natural exponent), summed over levels
+                                }
+                            }
+                            const float2 nd = sm.d[s];
+                            v[0] = (col.w * dx + nd.x * dy) * dp;
+                            v[1] = (nd.x * dx + nd.y * dy) * dp;
+                            v[2] = -0.5f * dx * dx * dp;
+                            v[3] = -dx * dy * dp;
+                            v[4] = -0.5f * dy * dy * dp;
+                        }
+                    }
+                    float out0 = 0.f, out8 = 0.f;
+                    if (__any_sync(0xffffffffu, contrib)) {
+                        {
+                            const bool up = lane & 16;
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const float send = up ? v[i] : v[i + 4];
+                                const float keep = up ? v[i + 4] : v[i];
+                                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
                             }
                         }
-                        const float2 nd = sm.d[s];
-                        v[0] = (col.w * dx + nd.x * dy) * dp;
-                        v[1] = (nd.x * dx + nd.y * dy) * dp;
-                        v[2] = -0.5f * dx * dx * dp;
-                        v[3] = -dx * dy * dp;
-                        v[4] = -0.5f * dy * dy * dp;
-                    }
-                }
-                float out0 = 0.f, out8 = 0.f;
-                if (__any_sync(0xffffffffu, contrib)) {
-                    {
-                        const bool up = lane & 16;
+                        {
+                            const bool up = lane & 8;
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float send = up ? v[i] : v[i + 4];
-                            const float keep = up ? v[i + 4] : v[i];
-                            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                            for (int i = 0; i < 2; ++i) {
+                                const float send = up ? v[i] : v[i + 2];
+                                const float keep = up ? v[i + 2] : v[i];
+                                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                            }
                         }
-                    }
-                    {
-                        const bool up = lane & 8;
-#pragma unroll
-                        for (int i = 0; i < 2; ++i) {
-                            const float send = up ? v[i] : v[i + 2];
-                            const float keep = up ? v[i + 2] : v[i];
-                            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                        {
+                            const bool up = lane & 4;
+                            const float send = up ? v[0] : v[1];
+                            const float keep = up ? v[1] : v[0];
+                            v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
                         }
-                    }
-                    {
-                        const bool up = lane & 4;
-                        const float send = up ? v[0] : v[1];
-                        const float keep = up ? v[1] : v[0];
-                        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-                    }
-                    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
-                    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-                    out0 = v[0];
-                    float x = v[8];
+                        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+                        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+                        out0 = v[0];
+                        float x = v[8];
 #pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-                    out8 = x;
+                        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+                        out8 = x;
+                    }
+                    if ((lane & 3) == 0) sm.wpart[k - gbot][warp][lane >> 2] = out0;
+                    if (lane == 1) sm.wpart[k - gbot][warp][8] = out8;
                 }
-                if ((lane & 3) == 0) sm.wpart[k - gbot][warp][lane >> 2] = out0;
-                if (lane == 1) sm.wpart[k - gbot][warp][8] = out8;
             }
             __syncthreads();
             for (int idx = threadIdx.x; idx < (gtop - gbot) * 9; idx += 256) {
