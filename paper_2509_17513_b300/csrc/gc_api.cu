@@ -82,7 +82,7 @@ static void saved_release(gc_context *ctx, gc_saved *s) {
     DevBuf *bufs[] = {&s->rec, &s->ranked, &s->dkeys[0], &s->dkeys[1], &s->dvals[0], &s->dvals[1],
                       &s->touched, &s->touched_r, &s->offsets, &s->tkeys[0], &s->tkeys[1],
                       &s->tvals[0], &s->tvals[1], &s->ranges, &s->final_T, &s->n_contrib,
-                      &s->n_blended, &s->n_walked, &s->words, &s->tile_diff};
+                      &s->n_blended, &s->n_walked, &s->words};
     for (DevBuf *b : bufs) release(*b);
     s->valid = false;
 }
@@ -207,9 +207,10 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
         GC_CUDA(ctx, grow(S.words, 64));
         GC_CUDA(ctx, cudaMemsetAsync(S.words.p, 0, 64, s));
     }
-    const bool diff_ranges = gc::tile_diff_fits(rp.ntx, rp.nty);
-    const size_t diff_bytes = (size_t)(rp.ntx + 1) * (rp.nty + 1) * 4;
-    if (diff_ranges) GC_CUDA(ctx, grow(S.tile_diff, diff_bytes));
+    // Tile ranges come from the sorted keys (the last sort pass keeps them): counting entries
+    // per tile with a difference grid filled by the preprocess costs ~2.4M contended integer
+    // atomics on a few thousand cells per 1080p frame, measured slower than one pass over the
+    // sorted keys.
     const int64_t cap_fixed = o.key_capacity;
     const size_t scan_words = gc::scan_partials_size(nn);
 
@@ -220,11 +221,9 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
         GC_CUDA(ctx, grow(ctx->scratch, 4 * std::max(gc::radix_scratch_words(nn), scan_words)));
         uint32_t *scratch = ctx->scratch.as<uint32_t>();
         GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_PREPROCESS));
-        if (diff_ranges) GC_CUDA(ctx, cudaMemsetAsync(S.tile_diff.p, 0, diff_bytes, s));
         GC_CUDA(ctx, gc::launch_preprocess(src, S.sel, n_sel, cp, rp, S.rec.as<float4>(),
                                            S.dkeys[0].as<uint32_t>(), S.dvals[0].as<uint32_t>(),
-                                           S.touched.as<uint32_t>(),
-                                           diff_ranges ? S.tile_diff.as<int32_t>() : nullptr, s));
+                                           S.touched.as<uint32_t>(), nullptr, s));
         uint32_t *dk[2] = {S.dkeys[0].as<uint32_t>(), S.dkeys[1].as<uint32_t>()};
         uint32_t *dv[2] = {S.dvals[0].as<uint32_t>(), S.dvals[1].as<uint32_t>()};
         GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_DEPTH_SORT));
@@ -262,13 +261,9 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
             const uint32_t *ndev = S.k_exact ? nullptr : words;
             GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_TILE_SORT));
             GC_CUDA(ctx, gc::radix_sort_pairs(tk, tv, K, ndev, bits_for(n_tiles - 1), scratch,
-                                              &S.tile_buf, s, words + 1, /*keys_out=*/!diff_ranges));
+                                              &S.tile_buf, s, words + 1, /*keys_out=*/true));
             GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_RANGES));
-            if (diff_ranges)
-                GC_CUDA(ctx, gc::launch_tile_ranges_from_diff(S.tile_diff.as<int32_t>(), rp.ntx, rp.nty,
-                                                              words, (uint32_t)K, S.ranges.as<uint2>(), s));
-            else
-                GC_CUDA(ctx, gc::launch_tile_ranges(tk[S.tile_buf], ndev, K, S.ranges.as<uint2>(), s));
+            GC_CUDA(ctx, gc::launch_tile_ranges(tk[S.tile_buf], ndev, K, S.ranges.as<uint2>(), s));
         }
     } else {
         GC_CUDA(ctx, cudaMemsetAsync(words, 0, 4, s));

@@ -154,7 +154,7 @@ uint64_t launches_total();
 
 // ---- launchers (host) ----
 
-// Projection of the n_sel selected Gaussians.  Writes rec[4*j..4*j+3], depth
+// Projection of the n_sel selected Gaussians.  Writes the records rec[kRec*j ..], depth
 // keys (kCulledKey when culled), values = j, and tiles touched per Gaussian.  If
 // tile_diff != NULL (a zeroed (nty+1) x (ntx+1) int grid), every visible Gaussian
 // adds each of its tile-row intervals to it as a row difference (two integer atomics
@@ -164,15 +164,6 @@ cudaError_t launch_preprocess(const GaussSrc &g, const Selection &sel, int64_t n
                               const CamParams &cam, const RenderParams &rp, float4 *rec,
                               uint32_t *depth_keys, uint32_t *depth_vals, uint32_t *touched,
                               int32_t *tile_diff, cudaStream_t st);
-
-// Tile ranges from the difference grid: 2D prefix sum -> per-tile counts ->
-// exclusive scan in tile order.  If the device key count exceeds `cap`, every
-// range is left empty (the overflow is reported separately).  Returns
-// cudaErrorNotSupported when the grid does not fit in shared memory.
-cudaError_t launch_tile_ranges_from_diff(const int32_t *tile_diff, int ntx, int nty,
-                                         const uint32_t *total_dev, uint32_t cap, uint2 *ranges,
-                                         cudaStream_t st);
-bool tile_diff_fits(int ntx, int nty);
 
 // rank r -> compact j = perm[r]: ranked[r] = rec[j], touched_r[r] = touched[j]
 cudaError_t launch_rank_gather(const uint32_t *perm, const float4 *rec, const uint32_t *touched,

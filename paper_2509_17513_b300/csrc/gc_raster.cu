@@ -61,67 +61,6 @@ __global__ void __launch_bounds__(256) k_blend_fwd(
     blend_fwd_tile<TW, TH, true>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, o, sm);
 }
 
-// Single CTA: the inclusive prefix of every row of the tile difference grid gives the
-// entry count of every tile; an exclusive scan in tile order gives the
-// ranges of the tile-sorted list.
-__global__ void __launch_bounds__(1024) k_tile_ranges_from_diff(const int32_t *__restrict__ diff,
-                                                                int ntx, int nty,
-                                                                const uint32_t *total_dev,
-                                                                uint32_t cap,
-                                                                uint2 *__restrict__ ranges) {
-    extern __shared__ int32_t g[];
-    __shared__ uint32_t ws[33];
-    const int gw = ntx + 1, gh = nty + 1;
-    const int cells = gw * gh;
-    for (int k = threadIdx.x; k < cells; k += blockDim.x) g[k] = diff[k];
-    __syncthreads();
-    for (int r = threadIdx.x; r < gh; r += blockDim.x) {
-        int acc = 0;
-        for (int c = 0; c < gw; ++c) {
-            acc += g[r * gw + c];
-            g[r * gw + c] = acc;
-        }
-    }
-    __syncthreads();
-    const bool overflow = total_dev && (*total_dev > cap);
-    const int T = ntx * nty;
-    const int per = (T + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int start = (int)threadIdx.x * per;
-    uint32_t s = 0;
-    for (int q = 0; q < per; ++q) {
-        const int t = start + q;
-        if (t < T) s += (uint32_t)g[(t / ntx) * gw + (t % ntx)];
-    }
-    // block exclusive scan of the per-thread sums
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t inc = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) ws[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = ws[lane];
-        uint32_t wi = w;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += y;
-        }
-        ws[lane] = wi - w;
-    }
-    __syncthreads();
-    uint32_t run = ws[warp] + inc - s;
-    for (int q = 0; q < per; ++q) {
-        const int t = start + q;
-        if (t < T) {
-            const uint32_t c = (uint32_t)g[(t / ntx) * gw + (t % ntx)];
-            ranges[t] = overflow ? make_uint2(0u, 0u) : make_uint2(run, run + c);
-            run += c;
-        }
-    }
-}
-
 __global__ void k_entries_to_global(const uint32_t *__restrict__ sorted_vals,
                                     const uint32_t *__restrict__ perm, Selection sel, int64_t K,
                                     int64_t *__restrict__ out) {
@@ -149,25 +88,6 @@ cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uin
     const int64_t threads = ((n + 31) / 32) * 32;
     k_emit<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(ranked, offsets, touched_r, n, rp, W, H, cap,
                                                                 keys, vals);
-    note_launches(1);
-    return cudaGetLastError();
-}
-
-bool tile_diff_fits(int ntx, int nty) {
-    return (size_t)(ntx + 1) * (size_t)(nty + 1) * 4 <= 200 * 1024;
-}
-
-cudaError_t launch_tile_ranges_from_diff(const int32_t *tile_diff, int ntx, int nty,
-                                         const uint32_t *total_dev, uint32_t cap, uint2 *ranges,
-                                         cudaStream_t st) {
-    if (!tile_diff_fits(ntx, nty)) return cudaErrorNotSupported;
-    const size_t smem = (size_t)(ntx + 1) * (nty + 1) * 4;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_ranges_from_diff,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_tile_ranges_from_diff<<<1, 1024, smem, st>>>(tile_diff, ntx, nty, total_dev, cap, ranges);
     note_launches(1);
     return cudaGetLastError();
 }

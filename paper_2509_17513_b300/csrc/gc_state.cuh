@@ -78,7 +78,7 @@ struct gc_saved {
     bool k_exact = false;
     int depth_buf = 0, tile_buf = 0;
     DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
-        final_T, n_contrib, n_blended, n_walked, words, tile_diff;
+        final_T, n_contrib, n_blended, n_walked, words;
     int levels = 0;         // > 0: a multi-level forward of levels 1..levels
     DevBuf lv_T, lv_last;   // its per-level final transmittance and list position
 };
