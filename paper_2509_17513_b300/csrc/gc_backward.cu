@@ -13,7 +13,8 @@
 //  k_preprocess_bwd   chain rule from (u, v, conic, opacity, rgb) to mean, log-scale,
 //                     quaternion, opacity logit, SH and the group motion (Sec. 3.2).
 //  k_group_partial /  per-group sums of the motion terms: each thread owns a group and
-//  k_group_final      adds its members of a chunk in index order; chunks in order.
+//  k_group_final      adds its members of a chunk in index order; then one warp per
+//                     (group, component) adds the chunks in a fixed order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -129,27 +130,31 @@ __global__ void __launch_bounds__(128) k_group_partial(const float *__restrict__
     }
 }
 
-// One thread per (group, component): the chunk partials summed in chunk order.
-__global__ void k_group_final(const float *__restrict__ partial, int n_chunks, int n_groups,
-                              float *__restrict__ d_gq, float *__restrict__ d_gt) {
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= n_groups * 7) return;
+// One warp per (group, component): lane l sums chunks l, l + 32, ... in order, then a fixed
+// butterfly adds the lanes (a fixed summation order: deterministic).
+__global__ void __launch_bounds__(256) k_group_final(const float *__restrict__ partial, int n_chunks,
+                                                     int n_groups, float *__restrict__ d_gq,
+                                                     float *__restrict__ d_gt) {
+    const int lane = threadIdx.x & 31;
+    const int id = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (id >= n_groups * 7) return;  // the whole warp
     const int g = id / 7, c = id - g * 7;
-    float acc = 0.f;
     const int64_t stride = (int64_t)n_groups * 7;
-    int b = 0;
-    for (; b + 8 <= n_chunks; b += 8) {
-        float v[8];
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    int b = lane;
+    for (; b + 96 < n_chunks; b += 128) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = partial[(int64_t)(b + u) * stride + id];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc += v[u];
+        for (int u = 0; u < 4; ++u) acc[u] += partial[(int64_t)(b + 32 * u) * stride + id];
     }
-    for (; b < n_chunks; ++b) acc += partial[(int64_t)b * stride + id];
+    for (; b < n_chunks; b += 32) acc[0] += partial[(int64_t)b * stride + id];
+    float v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane != 0) return;
     if (c < 4) {
-        if (d_gq) d_gq[4 * g + c] = acc;
+        if (d_gq) d_gq[4 * g + c] = v;
     } else if (d_gt) {
-        d_gt[3 * g + (c - 4)] = acc;
+        d_gt[3 * g + (c - 4)] = v;
     }
 }
 
@@ -219,7 +224,7 @@ cudaError_t launch_group_reduce(const float *motion_contrib, const int32_t *grou
         k_group_partial<<<chunks, 128, 0, st>>>(motion_contrib, group_id, sel, n_sel, n_groups, partial);
         note_launches(1);
     }
-    k_group_final<<<(n_groups * 7 + 127) / 128, 128, 0, st>>>(partial, chunks, n_groups, d_group_q, d_group_t);
+    k_group_final<<<(n_groups * 7 + 7) / 8, 256, 0, st>>>(partial, chunks, n_groups, d_group_q, d_group_t);
     note_launches(1);
     return cudaGetLastError();
 }
