@@ -1,0 +1,53 @@
+"""Oracle of the KDE rate estimate of the keyframe RD loss (Sec. 3.3, Eq. of P_PMF): the
+bits an entropy coder spends on the quantised symbols of one attribute channel, estimated
+from a Gaussian kernel density of the channel's own symbols.  TEST INFRASTRUCTURE ONLY.
+
+Readings (the paper names the ingredients - Silverman-rule bandwidth, the CDF of the kernel
+density, PMF(y) = CDF(y + 1/2) - CDF(y - 1/2), rate = -mean log2 PMF - and computes the CDF
+by FFT convolution on a grid):
+
+* symbols s_i = round(y_i) (round half to even), i = 1..N, of one channel;
+* bandwidth h = sigma (3 N / 4)^(-1/5), sigma the sample standard deviation of the symbols
+  (ddof 1) - the normal-reference (Silverman) rule; h = 1 when sigma = 0;
+* CDF(x) = (1/N) sum_i Phi((x - s_i) / h), Phi the standard normal CDF;
+* PMF(k) = CDF(k + 1/2) - CDF(k - 1/2) for every integer k (exactly a convolution of the
+  symbol histogram with the kernel w(d) = Phi((d + 1/2) / h) - Phi((d - 1/2) / h), which the
+  paper evaluates with an FFT);
+* rate = -(1/N) sum_i log2 max(PMF(s_i), 2^-40) bits per symbol.
+
+Here everything is evaluated from that definition in FP64 (sums over the samples).
+"""
+import numpy as np
+from scipy.special import ndtr
+
+PMF_FLOOR = 2.0 ** -40
+
+
+def symbols(y) -> np.ndarray:
+    return np.rint(np.asarray(y, np.float64)).astype(np.int64)
+
+
+def bandwidth(s) -> float:
+    s = np.asarray(s, np.float64)
+    n = s.shape[0]
+    sd = float(np.std(s, ddof=1)) if n > 1 else 0.0
+    return sd * (0.75 * n) ** (-0.2) if sd > 0 else 1.0
+
+
+def pmf(s, k, h=None) -> np.ndarray:
+    """PMF at the integers k from the symbols s (sums over every sample)."""
+    s = np.asarray(s, np.float64)
+    h = bandwidth(s) if h is None else h
+    k = np.asarray(k, np.float64)
+    out = np.zeros(k.shape)
+    for j, kj in enumerate(k.reshape(-1)):
+        out.reshape(-1)[j] = np.mean(ndtr((kj + 0.5 - s) / h) - ndtr((kj - 0.5 - s) / h))
+    return out
+
+
+def rate(y) -> float:
+    """Bits per symbol of one channel."""
+    s = symbols(y)
+    vals, counts = np.unique(s, return_counts=True)
+    p = pmf(s, vals)
+    return float(-(counts * np.log2(np.maximum(p, PMF_FLOOR))).sum() / s.shape[0])
