@@ -409,6 +409,17 @@ GC_API gc_status gc_motion_field_backward(gc_context *ctx, const gc_motion_field
                                           int64_t n, const float *d_q, const float *d_t,
                                           gc_motion_field_grads *out, void *stream);
 
+/* KDE rate estimate of the keyframe RD loss (Sec. 3.3, the PMF equation): for each of
+ * n_channels channels of n FP32 values (channel c at y + c * stride, device), the bits per
+ * symbol of its quantised symbols s_i = round(y_i) (half to even) under the Gaussian kernel
+ * density of those symbols with the Silverman-rule bandwidth h = sigma (3n/4)^(-1/5) (sigma
+ * the symbols' sample standard deviation, h = 1 when it is 0):
+ *   PMF(k) = CDF(k + 1/2) - CDF(k - 1/2),  rate = -(1/n) sum_i log2 max(PMF(s_i), 2^-40).
+ * Writes rate[c] (device).  A channel whose symbols span more than 8192 consecutive integers,
+ * or that holds a value that is not finite or beyond 2^24 in magnitude, gets NaN. */
+GC_API gc_status gc_kde_rate(gc_context *ctx, const float *y, int32_t n_channels, int64_t n, int64_t stride,
+                             float *rate, void *stream);
+
 /* Statistics of the last forward recorded in `saved` (synchronises `stream`). */
 GC_API gc_status gc_saved_stats(gc_context *ctx, const gc_saved *saved, gc_stats *out, void *stream);
 

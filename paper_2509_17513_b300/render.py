@@ -363,6 +363,17 @@ class Renderer:
                                              d_t.contiguous().data_ptr(), C.byref(s), _stream(stream)), self.ctx)
         return g
 
+    # ---- KDE rate estimate --------------------------------------------------------------
+
+    def kde_rate(self, y: torch.Tensor, stream=None) -> torch.Tensor:
+        """Bits per symbol of every row of ``y`` (C, N) under the Silverman-bandwidth kernel
+        density of its rounded values (Sec. 3.3); NaN for an unsupported row."""
+        y = y.contiguous()
+        C_, N = int(y.shape[0]), int(y.shape[1])
+        out = torch.empty(C_, device=y.device)
+        check(lib().gc_kde_rate(self.ctx, y.data_ptr(), C_, N, N, out.data_ptr(), _stream(stream)), self.ctx)
+        return out
+
     # ---- batched requests -------------------------------------------------------------
 
     def batch_forward(self, gs: GaussianSet, frames: list, requests: list, saved: Saved | None = None,
