@@ -516,6 +516,35 @@ def run_gpu(args):
         r.set_options(key_capacity=0)
         torch.cuda.empty_cache()
 
+    # ---- KDE rate estimate (Sec. 3.3): bits per symbol of every uint8 attribute channel of every
+    # layer of the quantised scene (the rate term of the layer-wise RD loss)
+    kde_obj = None
+    if "kde" not in skip:
+        pq = scenes.quantize_planes(w.scene, plane_width=1024)
+        W_p = 1024
+        ys = []
+        for l in range(w.scene.n_layers):
+            n_l = int(w.scene.layer_offsets[l + 1] - w.scene.layer_offsets[l])
+            u8 = pq["u8"][l]
+            ys.append(torch.from_numpy(np.ascontiguousarray(
+                u8[:, :, :W_p].reshape(u8.shape[0], -1)[:, :n_l].astype(np.float32))).to(dev))
+
+        def kde_step():
+            return [r.kde_rate(yl) for yl in ys]
+
+        for _ in range(args.warmup):
+            rates = kde_step()
+        k_ms, _, _ = timer(kde_step, args.steps, name="kde_rate")
+        rates = torch.stack(kde_step()).cpu().numpy()
+        n_sym = sum(int(yl.numel()) for yl in ys)
+        kde_obj = {"form": "KDE rate estimate of the keyframe RD loss (Sec. 3.3): Silverman-bandwidth kernel "
+                           "density PMF of the quantised symbols of each uint8 attribute channel of each layer "
+                           "(56 channels x 6 layers of hier1080, 300k Gaussians)",
+                   "ms_per_step": round(k_ms / args.steps, 4), "channels": int(rates.size),
+                   "symbols_per_s": round(n_sym / (k_ms / args.steps / 1e3), 1),
+                   "mean_bits_per_symbol": round(float(np.nanmean(rates)), 4)}
+        del ys
+
     # ---- residual deformation (Eq. 7): the same multi-level step with per-frame log-scale,
     # logit and SH residuals fused into the preprocess (device-generated, N(0, f sigma^2))
     residual_obj = None
@@ -596,6 +625,7 @@ def run_gpu(args):
             "residual_deformation": residual_obj,
             "decoded_planes": planes_obj,
             "motion_field": field_obj,
+            "kde_rate": kde_obj,
             "single_view": single_view,
             "reduced_precision": precision_obj,
             "autotune": tune,
@@ -825,7 +855,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch128", action="store_true", help="skip the 128-request batching workload")
-    ap.add_argument("--skip-forms", default="", help="comma list of side forms to leave out: single, batched, residual, planes, field "
+    ap.add_argument("--skip-forms", default="", help="comma list of side forms to leave out: single, batched, residual, planes, field, kde "
                     "(then 8x32 tiles are used and the BF16/FP8 form is left out too)")
     args = ap.parse_args()
     if args.impl == "reference":
