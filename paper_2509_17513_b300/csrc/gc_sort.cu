@@ -275,18 +275,17 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
 // A tile's keys and values arrive in shared memory by two bulk asynchronous copies
 // (cp.async.bulk, completed on an mbarrier), double-buffered so the next tile streams
 // in while this one is ranked.  Every warp ranks its contiguous 256-key segment row by
-// row (ballot multisplit), the CTA turns warp counts into offsets, places keys and
-// values digit-sorted back into the tile's buffer and writes them out in contiguous
-// runs.  keys_out may be NULL (last pass of a sort whose keys are not kept).
+// row (match.any or ballot multisplit), the CTA turns warp counts into each warp's tile
+// positions per digit, places the (key, value) pairs digit-sorted back into the tile's
+// buffer as 8-byte pairs and writes them out in contiguous runs.  keys_out may be NULL
+// (last pass of a sort whose keys are not kept).
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *n_dev,
     int64_t n_max, int shift, uint32_t mask, const uint32_t *__restrict__ scanned, int nblocks,
     uint32_t *err, const uint32_t *seg_block0, int n_seg) {
-    __shared__ __align__(128) uint32_t sk[2][kSortTile];
-    __shared__ __align__(128) uint32_t sv[2][kSortTile];
+    __shared__ __align__(128) uint32_t skv[2][2][kSortTile];  // per stage: keys, values (then key-value pairs)
     __shared__ uint32_t wcnt[kWarps][256];
-    __shared__ uint32_t dstart[256];
     __shared__ uint32_t gbase[256];
     __shared__ uint32_t ws[33];
     __shared__ __align__(8) uint64_t bar[2];
@@ -310,8 +309,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         const uint32_t bytes = (uint32_t)((nv * 4 + 15) & ~15);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&bar[stage], 2 * bytes);
-        bulk_copy_g2s(sk[stage], keys_in + base, bytes, &bar[stage]);
-        bulk_copy_g2s(sv[stage], vals_in + base, bytes, &bar[stage]);
+        bulk_copy_g2s(skv[stage][0], keys_in + base, bytes, &bar[stage]);
+        bulk_copy_g2s(skv[stage][1], vals_in + base, bytes, &bar[stage]);
     };
     if (threadIdx.x == 0) issue(blockIdx.x, 0);
 
@@ -340,8 +339,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         for (int r = 0; r < kSortItems; ++r) {
             const int li = wseg + r * 32 + lane;
             const bool valid = li < nvalid;
-            key[r] = valid ? sk[stage][li] : 0xffffffffu;
-            val[r] = valid ? sv[stage][li] : 0u;
+            key[r] = valid ? skv[stage][0][li] : 0xffffffffu;
+            val[r] = valid ? skv[stage][1][li] : 0u;
             const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
             const uint32_t d = (key[r] >> shift) & mask;
             // narrow digits: one match instruction; 8-bit digits: ballots per digit bit
@@ -364,8 +363,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
             }
             uint32_t tot;
             const uint32_t st = block_exclusive_scan<kSortThreads>(s, ws, &tot);
-            dstart[d] = st;
-            gbase[d] = scanned[count_index(d, t, nblocks, seg_block0, n_seg)];
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) wcnt[w][d] += st;   // tile position of warp w's first digit d
+            gbase[d] = scanned[count_index(d, t, nblocks, seg_block0, n_seg)] - st;  // output = gbase + tile position
         }
         __syncthreads();
 #pragma unroll
@@ -373,18 +373,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
             const int li = wseg + r * 32 + lane;
             if (li < nvalid) {
                 const uint32_t d = (key[r] >> shift) & mask;
-                const uint32_t pos = dstart[d] + wcnt[warp][d] + loc[r];
-                sk[stage][pos] = key[r];
-                sv[stage][pos] = val[r];
+                const uint32_t pos = wcnt[warp][d] + loc[r];
+                reinterpret_cast<uint2 *>(&skv[stage][0][0])[pos] = make_uint2(key[r], val[r]);
             }
         }
         __syncthreads();
         for (int p = threadIdx.x; p < nvalid; p += kSortThreads) {
-            const uint32_t k = sk[stage][p];
-            const uint32_t d = (k >> shift) & mask;
-            const uint32_t o = gbase[d] + (uint32_t)p - dstart[d];
-            if (keys_out) keys_out[o] = k;
-            vals_out[o] = sv[stage][p];
+            const uint2 kv = reinterpret_cast<const uint2 *>(&skv[stage][0][0])[p];
+            const uint32_t o = gbase[(kv.x >> shift) & mask] + (uint32_t)p;
+            if (keys_out) keys_out[o] = kv.x;
+            vals_out[o] = kv.y;
         }
         __syncthreads();
     }
