@@ -32,15 +32,42 @@ __global__ void __launch_bounds__(256) k_emit(const float4 *__restrict__ ranked,
     emit_rows_warp(ranked, wbase, n, offsets, touched_r, 0u, rp, W, H, cap, keys, vals);
 }
 
-__global__ void k_tile_ranges(const uint32_t *__restrict__ keys, const uint32_t *n_dev,
-                              int64_t n_max, uint2 *__restrict__ ranges) {
+// Range of every key of a key-sorted array: where a key differs from its predecessor its
+// range starts, where it differs from its successor it ends.  Each thread takes four
+// consecutive keys (one 16-byte load); the neighbours across threads come by shuffles,
+// across warps by a load.  keys must be 16-byte aligned.
+__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t *__restrict__ keys, const uint32_t *n_dev,
+                                                     int64_t n_max, uint2 *__restrict__ ranges) {
     int64_t n = n_max;
     if (n_dev) {
         int64_t d = (int64_t)*n_dev;
         if (d < n) n = d;
     }
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n4 = n >> 2;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q - lane < n4;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const bool in = q < n4;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (in) v = reinterpret_cast<const uint4 *>(keys)[q];
+        uint32_t prev = __shfl_up_sync(0xffffffffu, v.w, 1);
+        uint32_t next = __shfl_down_sync(0xffffffffu, v.x, 1);
+        if (!in) continue;
+        const int64_t p = 4 * q;
+        if (lane == 0 && p > 0) prev = keys[p - 1];
+        if ((lane == 31 || q + 1 >= n4) && p + 4 < n) next = keys[p + 4];
+        const uint32_t k[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t before = i == 0 ? prev : k[i - 1];
+            const uint32_t after = i == 3 ? next : k[i + 1];
+            if (p + i == 0 || before != k[i]) ranges[k[i]].x = (uint32_t)(p + i);
+            if (p + i == n - 1 || after != k[i]) ranges[k[i]].y = (uint32_t)(p + i + 1);
+        }
+    }
+    // the last n mod 4 keys
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+        const int64_t p = 4 * n4 + threadIdx.x;
         const uint32_t k = keys[p];
         if (p == 0 || keys[p - 1] != k) ranges[k].x = (uint32_t)p;
         if (p == n - 1 || keys[p + 1] != k) ranges[k].y = (uint32_t)(p + 1);
@@ -95,8 +122,9 @@ cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uin
 cudaError_t launch_tile_ranges(const uint32_t *keys, const uint32_t *n_dev, int64_t n_max,
                                uint2 *ranges, cudaStream_t st) {
     if (n_max <= 0) return cudaSuccess;
-    int64_t blocks = (n_max + 255) / 256;
-    if (blocks > 148 * 32) blocks = 148 * 32;
+    int64_t blocks = (n_max / 4 + 255) / 256;   // four keys per thread
+    if (blocks < 1) blocks = 1;
+    if (blocks > 148 * 16) blocks = 148 * 16;
     k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(keys, n_dev, n_max, ranges);
     note_launches(1);
     return cudaGetLastError();
