@@ -109,3 +109,19 @@ def test_levels_at_1080p(gc):
         one = r.forward(gs, mo, scenes.level_mask(l), cam)
         torch.cuda.synchronize()
         assert torch.equal(imgs[l - 1], one), l
+
+
+def test_levels_at_4k_with_a_wider_tile_grid(gc, small):
+    """3840x2160 (32,400 16x16 tiles, 15-bit tile keys): the six level images of one pass
+    equal the single renders, and the lists of the top level equal its single render's."""
+    scene, motion = small
+    cam = scenes.orbit_camera(2.9, 3.2, 3840, 2160)
+    r = gc.Renderer(0)
+    gs = gc.GaussianSet.from_scene(scene)
+    mo = gc.MotionFrame.from_motion(motion, 1)
+    saved = gc.Saved(r)
+    imgs = r.levels_forward(gs, mo, 6, cam, saved)
+    for l in (1, 4, 6):
+        one = r.forward(gs, mo, scenes.level_mask(l), cam)
+        torch.cuda.synchronize()
+        assert torch.equal(imgs[l - 1], one), l
