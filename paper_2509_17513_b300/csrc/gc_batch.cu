@@ -11,9 +11,9 @@
 // Steps (all on one stream, no host sync with a fixed key capacity):
 //   preprocess over all items -> segmented depth sort (each request on its own) ->
 //   rank gather -> scan of tiles touched -> per-request entry bases -> emit -> pad fill
-//   -> segmented tile sort (local tile ids) -> per-request tile ranges from the
-//   difference grids -> persistent blend: CTAs take tiles of all images from a work
-//   counter (an atomic ticket, no waiting on other CTAs).
+//   -> segmented tile sort (local tile ids) -> per-request tile ranges from the sorted
+//   keys -> persistent blend: CTAs take tiles of all images from a work counter (an
+//   atomic ticket, no waiting on other CTAs).
 // Every image equals the single-request render bit for bit: the same projection, the
 // same stable orders and the same per-tile blend run on the same data.
 #include <cuda_runtime.h>
@@ -33,7 +33,6 @@ struct __align__(16) BatchReq {
     int64_t item_base;
     int64_t tile_base;
     int64_t pixel_base;
-    int64_t diff_base;
     const float *group_q, *group_t;
     int n_groups;
     int frame;
@@ -84,7 +83,6 @@ __global__ void __launch_bounds__(256, 4) k_batch_preprocess(GaussSrc G, const B
                                                           uint32_t *__restrict__ keys,
                                                           uint32_t *__restrict__ vals,
                                                           uint32_t *__restrict__ touched,
-                                                          int32_t *__restrict__ diff,
                                                           const float4 *__restrict__ act) {
     // a block's 256 items belong to one request (requests are padded to the radix tile):
     // its table entry is staged in shared memory once
@@ -113,7 +111,7 @@ __global__ void __launch_bounds__(256, 4) k_batch_preprocess(GaussSrc G, const B
     rec[kRec * item + 1] = P.r1;
     if (j < R.n_sel) P.r2.y = __int_as_float(layer_of(R.sel, sel_global(R.sel, j)));
     rec[kRec * item + 2] = P.r2;
-    const uint32_t nt = bin_rows(P, R.rp, R.cam.width, R.cam.height, diff + R.diff_base, R.rp.ntx + 1);
+    const uint32_t nt = bin_rows(P, R.rp, R.cam.width, R.cam.height, nullptr, R.rp.ntx + 1);
     rec[kRec * item + 3] = P.r3;
     rec[kRec * item + 4] = P.r4;
     keys[item] = P.key;
@@ -184,63 +182,55 @@ __global__ void k_batch_pad_fill(const uint32_t *__restrict__ ebase, const uint3
     }
 }
 
-// One CTA per request: the request's tile ranges from its difference grid.
-__global__ void __launch_bounds__(1024) k_batch_ranges(const BatchReq *__restrict__ reqs,
-                                                       const int32_t *__restrict__ diff,
-                                                       const uint32_t *__restrict__ ebase,
-                                                       const uint32_t *padded_total, uint32_t cap,
-                                                       uint2 *__restrict__ ranges) {
-    extern __shared__ int32_t g[];
-    __shared__ uint32_t ws[33];
-    const BatchReq &R = reqs[blockIdx.x];
-    const int ntx = R.rp.ntx, nty = R.rp.nty;
-    const int gw = ntx + 1, gh = nty + 1, cells = gw * gh;
-    const int32_t *src = diff + R.diff_base;
-    for (int k = threadIdx.x; k < cells; k += blockDim.x) g[k] = src[k];
-    __syncthreads();
-    for (int r = threadIdx.x; r < gh; r += blockDim.x) {  // row prefix: entries per tile
-        int acc = 0;
-        for (int c = 0; c < gw; ++c) {
-            acc += g[r * gw + c];
-            g[r * gw + c] = acc;
+// Tile ranges from the segment-sorted keys (each request's keys sorted within its segment
+// [ebase[q], ebase[q] + ecount[q]), pad keys after it): a key that differs from its
+// predecessor in the segment starts its tile's range, one that differs from its successor
+// ends it.  Ranges of tiles without entries stay as zeroed.  Nothing when the padded total
+// overflowed the capacity.  Each thread takes four consecutive keys (one 16-byte load); a
+// warp's 128 keys lie in one segment (segments are 2048-aligned), whose request lane 0
+// looks up once.
+__global__ void __launch_bounds__(256) k_batch_key_ranges(const uint32_t *__restrict__ keys,
+                                                          const uint32_t *__restrict__ ebase,
+                                                          const uint32_t *__restrict__ ecount,
+                                                          const int64_t *__restrict__ tile_base, int n_req,
+                                                          const uint32_t *padded_total, uint32_t cap,
+                                                          uint2 *__restrict__ ranges) {
+    const uint32_t total = *padded_total;
+    if (total > cap) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t n4 = (int64_t)total >> 2;  // the padded total is a multiple of 2048
+    for (int64_t qd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; qd - lane < n4;
+         qd += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = 4 * qd;
+        int req = 0;
+        if (lane == 0) {  // the last request whose segment starts at or before the warp's first key
+            int lo = 0, hi = n_req - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if ((int64_t)ebase[mid] <= p) lo = mid; else hi = mid - 1;
+            }
+            req = lo;
         }
-    }
-    __syncthreads();
-    const bool overflow = *padded_total > cap;
-    const int T = ntx * nty;
-    const int per = (T + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int start = (int)threadIdx.x * per;
-    uint32_t s = 0;
-    for (int q = 0; q < per; ++q) {
-        const int t = start + q;
-        if (t < T) s += (uint32_t)g[(t / ntx) * gw + (t % ntx)];
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t inc = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) ws[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = ws[lane];
-        uint32_t wi = w;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += y;
-        }
-        ws[lane] = wi - w;
-    }
-    __syncthreads();
-    uint32_t run = ebase[blockIdx.x] + ws[warp] + inc - s;
-    uint2 *out = ranges + R.tile_base;
-    for (int q = 0; q < per; ++q) {
-        const int t = start + q;
-        if (t < T) {
-            const uint32_t c = (uint32_t)g[(t / ntx) * gw + (t % ntx)];
-            out[t] = overflow ? make_uint2(0u, 0u) : make_uint2(run, run + c);
-            run += c;
+        req = __shfl_sync(0xffffffffu, req, 0);
+        const bool in = qd < n4;
+        uint4 v = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+        if (in) v = reinterpret_cast<const uint4 *>(keys)[qd];
+        uint32_t prev = __shfl_up_sync(0xffffffffu, v.w, 1);
+        uint32_t next = __shfl_down_sync(0xffffffffu, v.x, 1);
+        if (!in) continue;
+        const int64_t a = ebase[req], e = a + ecount[req];
+        if (lane == 0 && p > a) prev = keys[p - 1];
+        if ((lane == 31 || qd + 1 >= n4) && p + 4 < e) next = keys[p + 4];
+        uint2 *out = ranges + tile_base[req];
+        const uint32_t k[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int64_t pt = p + t;
+            if (pt >= e) break;  // padding
+            const uint32_t before = t == 0 ? prev : k[t - 1];
+            const uint32_t after = t == 3 ? next : k[t + 1];
+            if (pt == a || before != k[t]) out[k[t]].x = (uint32_t)pt;
+            if (pt + 1 == e || after != k[t]) out[k[t]].y = (uint32_t)(pt + 1);
         }
     }
 }
@@ -468,13 +458,13 @@ struct BatchState {
     const float **staging_dimg = nullptr;
     size_t staging_dimg_cap = 0;
     cudaEvent_t staged = nullptr;      // last upload from the pinned buffers
-    int64_t n_items = 0, n_tiles = 0, n_pixels = 0, diff_cells = 0, K_cap = 0;
-    int max_cells = 0, key_bits = 1, depth_buf = 0, tile_buf = 0;
+    int64_t n_items = 0, n_tiles = 0, n_pixels = 0, K_cap = 0;
+    int key_bits = 1, depth_buf = 0, tile_buf = 0;
     bool k_exact = false;
     gc_options opt{};
     DevBuf reqs_dev, item_base, tile_base, seg_items, ebase, eshift, ecount, seg_entries, dimg_dev;
     DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
-        final_T, n_contrib, diff, words, counter, scratch, act;
+        final_T, n_contrib, words, counter, scratch, act;
     DevBuf part, g2d, mcontrib, gpartial;
     bool part_clean = false;  // part holds only zeros (see the reduce)
 
@@ -482,7 +472,7 @@ struct BatchState {
         DevBuf *bufs[] = {&reqs_dev, &item_base, &tile_base, &seg_items, &ebase, &eshift, &ecount,
                           &seg_entries, &dimg_dev, &rec, &ranked, &dkeys[0], &dkeys[1], &dvals[0],
                           &dvals[1], &touched, &touched_r, &offsets, &tkeys[0], &tkeys[1], &tvals[0],
-                          &tvals[1], &ranges, &final_T, &n_contrib, &diff, &words, &counter, &scratch, &act,
+                          &tvals[1], &ranges, &final_T, &n_contrib, &words, &counter, &scratch, &act,
                           &part, &g2d, &mcontrib, &gpartial};
         for (DevBuf *b : bufs) release(*b);
         if (staging) cudaFreeHost(staging);
@@ -544,11 +534,10 @@ struct Sizer {
 gc_status build_table(gc_context *ctx, const gc_gaussians *g, const gc_motion *frames, int n_frames,
                       int n_groups, const gc_request *reqs, int n_req, const gc_options &o,
                       std::vector<gc::BatchReq> &tab, int64_t &items, int64_t &tiles, int64_t &pixels,
-                      int64_t &cells, int &max_cells, int &kbits) {
+                      int &kbits) {
     const int64_t T = gc::radix_tile_keys();
     tab.assign(n_req, gc::BatchReq{});
-    items = tiles = pixels = cells = 0;
-    max_cells = 0;
+    items = tiles = pixels = 0;
     kbits = 1;
     for (int q = 0; q < n_req; ++q) {
         const gc_request &rq = reqs[q];
@@ -591,10 +580,6 @@ gc_status build_table(gc_context *ctx, const gc_gaussians *g, const gc_motion *f
         tiles += (int64_t)R.rp.ntx * R.rp.nty;
         R.pixel_base = pixels;
         pixels += (int64_t)cam->width * cam->height;
-        R.diff_base = cells;
-        const int c = (R.rp.ntx + 1) * (R.rp.nty + 1);
-        cells += c;
-        max_cells = std::max(max_cells, c);
         kbits = std::max(kbits, bits_for((int64_t)R.rp.ntx * R.rp.nty - 1));
         R.frame = rq.frame;
         R.n_groups = 1;
@@ -607,8 +592,6 @@ gc_status build_table(gc_context *ctx, const gc_gaussians *g, const gc_motion *f
         }
         R.image = rq.image;
     }
-    if ((size_t)max_cells * 4 > 200 * 1024)
-        return fail(ctx, GC_ERR_UNSUPPORTED, "image too large for the batched tile-range kernel");
     if (items > 0x7FFFFFFFll) return fail(ctx, GC_ERR_INVALID_ARG, "more than 2^31 - 1 (request, Gaussian) pairs");
     return GC_OK;
 }
@@ -663,10 +646,10 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     const int64_t T = gc::radix_tile_keys();
 
     std::vector<gc::BatchReq> tab;
-    int64_t items, tiles, pixels, cells;
-    int max_cells, kbits;
-    if ((st = build_table(ctx, g, frames, n_frames, n_groups, reqs, n_req, o, tab, items, tiles, pixels, cells,
-                          max_cells, kbits)) != GC_OK)
+    int64_t items, tiles, pixels;
+    int kbits;
+    if ((st = build_table(ctx, g, frames, n_frames, n_groups, reqs, n_req, o, tab, items, tiles, pixels,
+                          kbits)) != GC_OK)
         return st;
     const bool same_table = B.reqs_dev.p && (int)B.reqs.size() == n_req &&
                             memcmp(B.reqs.data(), tab.data(), sizeof(gc::BatchReq) * n_req) == 0;
@@ -689,8 +672,6 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     B.n_items = items;
     B.n_tiles = tiles;
     B.n_pixels = pixels;
-    B.diff_cells = cells;
-    B.max_cells = max_cells;
     B.key_bits = kbits;
     B.opt = o;
 
@@ -716,7 +697,6 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     need(B.ranges, (size_t)tiles * 8);
     need(B.final_T, (size_t)pixels * 4);
     need(B.n_contrib, (size_t)pixels * 4);
-    need(B.diff, (size_t)cells * 4);
     need(B.counter, 16);
     need(B.act, (size_t)std::max<int64_t>(g->n, 1) * 16);
     const bool fresh_words = !B.words.p;
@@ -754,7 +734,6 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     auto mark = [&](int stage) -> cudaError_t { return prof ? prof_mark(ctx, s, stage) : cudaSuccess; };
 
     GC_CUDA(ctx, mark(GC_STAGE_PREPROCESS));
-    GC_CUDA(ctx, cudaMemsetAsync(B.diff.p, 0, (size_t)cells * 4, s));
     const gc::BatchReq *rq_dev = B.reqs_dev.as<gc::BatchReq>();
     const int64_t *ib_dev = B.item_base.as<int64_t>(), *tb_dev = B.tile_base.as<int64_t>();
     uint32_t *scratch = B.scratch.as<uint32_t>();
@@ -769,8 +748,7 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
         }
         GC_DISPATCH_PREC(src.precision, gc::k_batch_preprocess<PREC_><<<(unsigned)((items + 255) / 256), 256, 0, s>>>(
             src, rq_dev, ib_dev, n_req, items, B.rec.as<float4>(), B.dkeys[0].as<uint32_t>(),
-            B.dvals[0].as<uint32_t>(), B.touched.as<uint32_t>(), B.diff.as<int32_t>(),
-            deformed ? nullptr : B.act.as<float4>()))
+            B.dvals[0].as<uint32_t>(), B.touched.as<uint32_t>(), deformed ? nullptr : B.act.as<float4>()))
         gc::note_launches(1);
         GC_CUDA(ctx, cudaGetLastError());
         GC_CUDA(ctx, mark(GC_STAGE_DEPTH_SORT));
@@ -827,17 +805,19 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
         GC_CUDA(ctx, mark(GC_STAGE_TILE_SORT));
         uint32_t *tk[2] = {B.tkeys[0].as<uint32_t>(), B.tkeys[1].as<uint32_t>()};
         uint32_t *tv[2] = {B.tvals[0].as<uint32_t>(), B.tvals[1].as<uint32_t>()};
-        GC_CUDA(ctx, gc::radix_sort_pairs(tk, tv, K, words + 2, kbits, scratch, &B.tile_buf, s, words + 1, false,
-                                          B.seg_entries.as<uint32_t>(), n_req));
+        GC_CUDA(ctx, gc::radix_sort_pairs(tk, tv, K, words + 2, kbits, scratch, &B.tile_buf, s, words + 1,
+                                          /*keys_out=*/true, B.seg_entries.as<uint32_t>(), n_req));
     }
     GC_CUDA(ctx, mark(GC_STAGE_RANGES));
-    {
-        const size_t smem = (size_t)max_cells * 4;
-        if (smem > 48 * 1024 && !capturing)
-            GC_CUDA(ctx, cudaFuncSetAttribute(gc::k_batch_ranges, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem));
-        gc::k_batch_ranges<<<n_req, 1024, smem, s>>>(rq_dev, B.diff.as<int32_t>(), B.ebase.as<uint32_t>(), words + 2,
-                                                     (uint32_t)K, B.ranges.as<uint2>());
+    if (tiles > 0) GC_CUDA(ctx, cudaMemsetAsync(B.ranges.p, 0, (size_t)tiles * 8, s));
+    if (K > 0 && items > 0) {
+        // ranges from the sorted keys: a difference grid filled by the preprocess costs
+        // contended integer atomics, measured slower
+        const int64_t blocks = std::max<int64_t>(std::min<int64_t>((K / 4 + 255) / 256, 148 * 16), 1);
+        gc::k_batch_key_ranges<<<(unsigned)blocks, 256, 0, s>>>(B.tkeys[B.tile_buf].as<uint32_t>(),
+                                                                B.ebase.as<uint32_t>(), B.ecount.as<uint32_t>(),
+                                                                tb_dev, n_req, words + 2, (uint32_t)K,
+                                                                B.ranges.as<uint2>());
         gc::note_launches(1);
         GC_CUDA(ctx, cudaGetLastError());
     }
