@@ -223,7 +223,7 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
         GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_PREPROCESS));
         GC_CUDA(ctx, gc::launch_preprocess(src, S.sel, n_sel, cp, rp, S.rec.as<float4>(),
                                            S.dkeys[0].as<uint32_t>(), S.dvals[0].as<uint32_t>(),
-                                           S.touched.as<uint32_t>(), nullptr, s));
+                                           S.touched.as<uint32_t>(), s));
         uint32_t *dk[2] = {S.dkeys[0].as<uint32_t>(), S.dkeys[1].as<uint32_t>()};
         uint32_t *dv[2] = {S.dvals[0].as<uint32_t>(), S.dvals[1].as<uint32_t>()};
         GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_DEPTH_SORT));

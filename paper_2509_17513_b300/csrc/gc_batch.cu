@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256, 4) k_batch_preprocess(GaussSrc G, const B
     rec[kRec * item + 1] = P.r1;
     if (j < R.n_sel) P.r2.y = __int_as_float(layer_of(R.sel, sel_global(R.sel, j)));
     rec[kRec * item + 2] = P.r2;
-    const uint32_t nt = bin_rows(P, R.rp, R.cam.width, R.cam.height, nullptr, R.rp.ntx + 1);
+    const uint32_t nt = bin_rows(P, R.rp, R.cam.width, R.cam.height);
     rec[kRec * item + 3] = P.r3;
     rec[kRec * item + 4] = P.r4;
     keys[item] = P.key;

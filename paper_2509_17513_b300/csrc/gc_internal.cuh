@@ -155,15 +155,11 @@ uint64_t launches_total();
 // ---- launchers (host) ----
 
 // Projection of the n_sel selected Gaussians.  Writes the records rec[kRec*j ..], depth
-// keys (kCulledKey when culled), values = j, and tiles touched per Gaussian.  If
-// tile_diff != NULL (a zeroed (nty+1) x (ntx+1) int grid), every visible Gaussian
-// adds each of its tile-row intervals to it as a row difference (two integer atomics
-// per row), so that the prefix sum along each row is the number of list entries of
-// every tile.
+// keys (kCulledKey when culled), values = j, and tiles touched per Gaussian.
 cudaError_t launch_preprocess(const GaussSrc &g, const Selection &sel, int64_t n_sel,
                               const CamParams &cam, const RenderParams &rp, float4 *rec,
                               uint32_t *depth_keys, uint32_t *depth_vals, uint32_t *touched,
-                              int32_t *tile_diff, cudaStream_t st);
+                              cudaStream_t st);
 
 // rank r -> compact j = perm[r]: ranked[r] = rec[j], touched_r[r] = touched[j]
 cudaError_t launch_rank_gather(const uint32_t *perm, const float4 *rec, const uint32_t *touched,

@@ -257,7 +257,7 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
     int tile_buf = 0;
     if (n_sel > 0) {
         int depth_buf = 0;
-        NA_CUDA(gc::launch_preprocess(src, sel, n_sel, cp, rp, rec, dk[0], dv[0], touched, nullptr, s));
+        NA_CUDA(gc::launch_preprocess(src, sel, n_sel, cp, rp, rec, dk[0], dv[0], touched, s));
         NA_CUDA(gc::radix_sort_pairs(dk, dv, n_sel, nullptr, 32, sort_scratch, &depth_buf, s, words + 1));
         NA_CUDA(gc::launch_rank_gather(dv[depth_buf], rec, touched, n_sel, ranked, touched_r, s));
         NA_CUDA(gc::launch_exclusive_scan(touched_r, offsets, n_sel, words, sort_scratch, s));

@@ -14,8 +14,7 @@ __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, i
                                                     float4 *__restrict__ rec,
                                                     uint32_t *__restrict__ depth_keys,
                                                     uint32_t *__restrict__ depth_vals,
-                                                    uint32_t *__restrict__ touched,
-                                                    int32_t *__restrict__ tile_diff) {
+                                                    uint32_t *__restrict__ touched) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_sel) return;
     const int64_t i = sel_global(sel, j);
@@ -25,7 +24,7 @@ __global__ void __launch_bounds__(256) k_preprocess(GaussSrc G, Selection sel, i
     rec[kRec * j + 1] = P.r1;
     P.r2.y = __int_as_float(layer_of(sel, i));
     rec[kRec * j + 2] = P.r2;
-    const uint32_t nt = bin_rows(P, rp, cam.width, cam.height, tile_diff, rp.ntx + 1);
+    const uint32_t nt = bin_rows(P, rp, cam.width, cam.height);
     rec[kRec * j + 3] = P.r3;
     rec[kRec * j + 4] = P.r4;
     depth_keys[j] = P.key;
@@ -51,11 +50,11 @@ __global__ void __launch_bounds__(256) k_rank_gather(const uint32_t *__restrict_
 cudaError_t launch_preprocess(const GaussSrc &g, const Selection &sel, int64_t n_sel,
                               const CamParams &cam, const RenderParams &rp, float4 *rec,
                               uint32_t *depth_keys, uint32_t *depth_vals, uint32_t *touched,
-                              int32_t *tile_diff, cudaStream_t st) {
+                              cudaStream_t st) {
     if (n_sel <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((n_sel + 255) / 256);
     GC_DISPATCH_PREC(g.precision, k_preprocess<PREC_><<<blocks, 256, 0, st>>>(
-                                      g, sel, n_sel, cam, rp, rec, depth_keys, depth_vals, touched, tile_diff))
+                                      g, sel, n_sel, cam, rp, rec, depth_keys, depth_vals, touched))
     note_launches(1);
     return cudaGetLastError();
 }

@@ -656,10 +656,8 @@ __device__ __forceinline__ void store_reduced(float *g, float out0, float out8) 
 }
 
 // Tiles touched by a projected Gaussian (sum of its row intervals); packs the intervals
-// into P.r4 when they fit; if diff != NULL also adds each row interval to the
-// row-difference grid (row pitch gw).
-__device__ __forceinline__ uint32_t bin_rows(Proj &P, const RenderParams &rp, int W, int H, int32_t *diff,
-                                             int gw) {
+// into P.r4 when they fit.
+__device__ __forceinline__ uint32_t bin_rows(Proj &P, const RenderParams &rp, int W, int H) {
     P.r4 = make_float4(__uint_as_float(0xffu), 0.f, 0.f, 0.f);
     if (!P.ntouch) return 0u;
     RowGeom g;
@@ -682,10 +680,6 @@ __device__ __forceinline__ uint32_t bin_rows(Proj &P, const RenderParams &rp, in
         }
         if (a > b) continue;
         total += (uint32_t)len;
-        if (diff) {
-            atomicAdd(&diff[ty * gw + a], 1);
-            atomicAdd(&diff[ty * gw + b + 1], -1);
-        }
     }
     if (fits)
         P.r4 = make_float4(__uint_as_float(pk0), __uint_as_float(pk1), __uint_as_float(pk2), __uint_as_float(pk3));
