@@ -72,17 +72,20 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(GaussSrc G, Selection se
     for (int k = 0; k < 3; ++k) { acc.dmu[k] = 0.f; acc.dls[k] = 0.f; }
     for (int k = 0; k < 4; ++k) acc.dq[k] = 0.f;
     acc.dlogit = 0.f;
-    for (int k = 0; k < K3; ++k) acc.dsh[k] = 0.f;
     float m7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // the SH gradient goes straight to its output (one chain rule per Gaussian here)
+    float sh_scratch[48];
+    float *dsh = out.d_sh ? out.d_sh + i * K3 : sh_scratch;
     if (touched[j] != 0) {
         const int g = G.per_gaussian ? (int)i : ((G.group_q && G.group_id) ? G.group_id[i] : 0);
-        chain_rule<PREC>(G, i, G.group_q, G.group_t, g, cam, rp, g2d + 9 * j, acc, m7, G.res);
+        chain_rule<PREC>(G, i, G.group_q, G.group_t, g, cam, rp, g2d + 9 * j, acc, m7, G.res, dsh);
+    } else if (out.d_sh) {
+        for (int k = 0; k < K3; ++k) dsh[k] = 0.f;
     }
     if (out.d_means) for (int k = 0; k < 3; ++k) out.d_means[3 * i + k] = acc.dmu[k];
     if (out.d_log_scales) for (int k = 0; k < 3; ++k) out.d_log_scales[3 * i + k] = acc.dls[k];
     if (out.d_quats) for (int k = 0; k < 4; ++k) out.d_quats[4 * i + k] = acc.dq[k];
     if (out.d_opacity_logits) out.d_opacity_logits[i] = acc.dlogit;
-    if (out.d_sh) for (int k = 0; k < K3; ++k) out.d_sh[i * K3 + k] = acc.dsh[k];
     if (mcontrib) for (int k = 0; k < 7; ++k) mcontrib[7 * j + k] = m7[k];
 }
 

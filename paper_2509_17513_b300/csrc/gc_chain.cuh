@@ -45,7 +45,7 @@ template <int PREC>
 __device__ __forceinline__ void chain_rule(const GaussSrc &G, int64_t i, const float *group_q,
                                            const float *group_t, int g, const CamParams &cam,
                                            const RenderParams &rp, const float *d, GradAcc &acc,
-                                           float *motion7, const Residual &res) {
+                                           float *motion7, const Residual &res, float *dsh_direct = nullptr) {
     const int K = G.K;
     float mu[3], ls[3], q[4], logit;
     PlaneLoc pl{0, 0, 0, 0};
@@ -127,20 +127,35 @@ __device__ __forceinline__ void chain_rule(const GaussSrc &G, int64_t i, const f
         const float dir[3] = {dv[0] / dn, dv[1] / dn, dv[2] / dn};
         float Y[16];
         sh_basis(G.sh_degree, dir[0], dir[1], dir[2], Y);
+        // fully unrolled over the 16 coefficients (guarded by K) so that Y, wsh and the SH
+        // gradient stay in registers; dsh_direct: the SH gradient is stored, not accumulated
         float raw[3] = {0.5f, 0.5f, 0.5f};
         float wsh[16];
-        for (int k = 0; k < K; ++k) {
-            raw[0] += Y[k] * sh_coeff<PREC>(G, i, k, 0, res, pl);
-            raw[1] += Y[k] * sh_coeff<PREC>(G, i, k, 1, res, pl);
-            raw[2] += Y[k] * sh_coeff<PREC>(G, i, k, 2, res, pl);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (k < K) {
+                raw[0] += Y[k] * sh_coeff<PREC>(G, i, k, 0, res, pl);
+                raw[1] += Y[k] * sh_coeff<PREC>(G, i, k, 1, res, pl);
+                raw[2] += Y[k] * sh_coeff<PREC>(G, i, k, 2, res, pl);
+            }
         }
         const float draw[3] = {raw[0] > 0.f ? d[6] : 0.f, raw[1] > 0.f ? d[7] : 0.f, raw[2] > 0.f ? d[8] : 0.f};
-        for (int k = 0; k < K; ++k) {
-            wsh[k] = sh_coeff<PREC>(G, i, k, 0, res, pl) * draw[0] + sh_coeff<PREC>(G, i, k, 1, res, pl) * draw[1] +
-                     sh_coeff<PREC>(G, i, k, 2, res, pl) * draw[2];
-            acc.dsh[3 * k] += Y[k] * draw[0];
-            acc.dsh[3 * k + 1] += Y[k] * draw[1];
-            acc.dsh[3 * k + 2] += Y[k] * draw[2];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            wsh[k] = 0.f;
+            if (k < K) {
+                wsh[k] = sh_coeff<PREC>(G, i, k, 0, res, pl) * draw[0] + sh_coeff<PREC>(G, i, k, 1, res, pl) * draw[1] +
+                         sh_coeff<PREC>(G, i, k, 2, res, pl) * draw[2];
+                if (dsh_direct) {
+                    dsh_direct[3 * k] = Y[k] * draw[0];
+                    dsh_direct[3 * k + 1] = Y[k] * draw[1];
+                    dsh_direct[3 * k + 2] = Y[k] * draw[2];
+                } else {
+                    acc.dsh[3 * k] += Y[k] * draw[0];
+                    acc.dsh[3 * k + 1] += Y[k] * draw[1];
+                    acc.dsh[3 * k + 2] += Y[k] * draw[2];
+                }
+            }
         }
         float ddx, ddy, ddz;
         sh_basis_vjp(G.sh_degree, dir[0], dir[1], dir[2], wsh, ddx, ddy, ddz);
