@@ -196,6 +196,22 @@ def roofline_for(stage, per_launch_ms, work, peaks, peak_kind, batched=False, re
     return None
 
 
+def max_over_ranks(total: float, world: int, device) -> float:
+    """The largest of every rank's value (the slowest replica decides the job's time)."""
+    if world <= 1:
+        return total
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: float, steps: int, world: int, total_ms: float) -> float:
+    """Units processed by all ranks per second (weak scaling: every rank does a full step)."""
+    return units_per_rank_step * steps * world / (total_ms / 1e3)
+
+
 class Timer:
     """K steps timed with CUDA events on the rendering stream, L2 flushed between steps
     (outside the events), clocks sampled during the region, max over ranks."""
@@ -231,10 +247,7 @@ class Timer:
         clk = clocks.stop()
         prof = self.r.profile_read()
         self.r.profile(False)
-        if self.world > 1:
-            t = torch.tensor([total], device=self.dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(total, self.world, self.dev)
         return total, prof, clk
 
 
@@ -281,7 +294,7 @@ def run_gpu(args):
     dls = [upstream] * n_req
 
     def mpix(total_ms, steps, px=pixels_per_step):
-        return round(px * steps * world / (total_ms / 1e3) / 1e6, 1)
+        return round(whole_job_rate(px, steps, world, total_ms) / 1e6, 1)
 
     # ---- plain FP32 single-view form: one gc_render_forward (+ backward) per request
     single_view = None
