@@ -8,10 +8,11 @@
 // FP32 SIMT: their contraction (per Gaussian 2 x 64 x 32 + 7 x 64 multiply-adds) is small,
 // and FP32 keeps the forward within FP32 rounding of the FP64 oracle.
 //
-// Backward: per block of 128 Gaussians the hidden activations and their gradients are
-// staged in shared memory and the weight gradients summed over the block; the per-block sums
-// are added over the blocks in block order by a second kernel (deterministic).  The table
-// gradient is scattered with atomic additions.
+// Backward: persistent blocks; per chunk of 128 Gaussians the encodings, hidden activations
+// and their gradients are staged in shared memory, the weight gradients accumulated in
+// registers over the block's chunks and the per-block sums added over the blocks in block
+// order by a second kernel (deterministic).  The table gradient is scattered with atomic
+// additions.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -150,104 +151,201 @@ __global__ void __launch_bounds__(kFT) k_field_fwd(Field F, const float *__restr
     for (int c = 1; c < 4; ++c) q[4 * i + c] = o[3 + c];
 }
 
-// Backward.  Dynamic shared memory: H[kIn][kFT], A[kHidden][kFT], DZ[kHidden][kFT], DO[7][kFT].
-constexpr size_t kBwdDyn = (size_t)(kIn + 2 * kHidden + 7) * kFT * 4;
+// Backward, first pass: the hash-grid encoding of every Gaussian, kIn floats per row (levels
+// beyond F.L zero).  Its table gathers are latency-bound; this kernel keeps many warps per SM
+// to hide them, which the backward proper (large shared rows) cannot.
+__global__ void __launch_bounds__(kFT) k_field_encode(Field F, const float *__restrict__ means, int64_t n,
+                                                      float4 *__restrict__ hrows) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+    float h[kIn];
+    encode(F, mu, h);
+    float4 *row = hrows + (size_t)i * (kIn / 4);
+#pragma unroll
+    for (int q4 = 0; q4 < kIn / 4; ++q4) row[q4] = make_float4(h[4 * q4], h[4 * q4 + 1], h[4 * q4 + 2], h[4 * q4 + 3]);
+}
 
-__global__ void __launch_bounds__(kFT) k_field_bwd(Field F, const float *__restrict__ means, int64_t n,
-                                                   const float *__restrict__ d_q, const float *__restrict__ d_t,
-                                                   float *__restrict__ partial, float *__restrict__ d_table) {
+// Backward, persistent: block b takes the chunks of kFT Gaussians c = b, b + grid, ... in
+// order.  Per chunk the block copies the chunk's encodings (from k_field_encode) into padded
+// shared rows, each thread recomputes its Gaussian's hidden layers and stages one padded row
+// per Gaussian in shared memory (encoding, output gradient, hidden
+// activation, hidden pre-activation gradient; row pitches chosen so that 16-byte row accesses
+// of eight consecutive threads fall on distinct banks).  The weight gradients are sums over
+// the Gaussians of outer products; each thread accumulates, in registers and over all of its
+// block's chunks, a 4 x 4 tile of dW1 per net and one column of dW2 / db1 (and one entry of
+// db2).  Each block writes one partial vector at the end, summed over the blocks in block
+// order by k_field_reduce, so the weight gradients are reproducible bit for bit for a given n.
+// The table gradient is scattered with atomic additions.
+constexpr int kHP = kIn + 4;       // 36 floats: row pitch of the encodings
+constexpr int kOP = 8;             // row pitch of the output gradients (7 used)
+constexpr int kAP = kHidden + 4;   // 68 floats: row pitch of the hidden rows
+constexpr size_t kBwdDyn = (size_t)kFT * (kHP + kOP + 2 * kAP) * 4;
+constexpr int kBwdBlocksPerSm = 2;
+constexpr int kBwdGrid = 148 * kBwdBlocksPerSm;
+
+__global__ void __launch_bounds__(kFT, kBwdBlocksPerSm) k_field_bwd(
+    Field F, const float *__restrict__ means, const float4 *__restrict__ hrows, int64_t n,
+    const float *__restrict__ d_q, const float *__restrict__ d_t, float *__restrict__ partial,
+    float *__restrict__ d_table) {
     __shared__ __align__(16) FieldSmem s;
     extern __shared__ __align__(16) float dyn[];
-    float *H = dyn, *A = H + kIn * kFT, *DZ = A + kHidden * kFT, *DO = DZ + kHidden * kFT;
+    float *HT = dyn, *DOT = HT + kFT * kHP, *AT = DOT + kFT * kOP, *DZT = AT + kFT * kAP;
     stage_weights(F, s);
     const int tid = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * kFT + tid;
-    const bool valid = i < n;
-    float mu[3] = {0.f, 0.f, 0.f};
-    float h[kIn], dout[7];
+    const int tj = tid >> 3, tk = tid & 7;    // dW1 tile: rows 4 tj .. 4 tj + 3, columns 4 tk .. 4 tk + 3
+    const int cj = tid & 63, ch = tid >> 6;  // dW2 column j = cj, outputs 2 ch and 2 ch + 1; db1 (ch = 0)
+    float g1[2][4][4], g2[2][2], gb1[2], gb2 = 0.f;
 #pragma unroll
-    for (int k = 0; k < kIn; ++k) h[k] = 0.f;
-#pragma unroll
-    for (int c = 0; c < 7; ++c) dout[c] = 0.f;
-    if (valid) {
-        for (int a = 0; a < 3; ++a) mu[a] = means[3 * i + a];
-        encode(F, mu, h);
-        for (int c = 0; c < 3; ++c) dout[c] = d_t[3 * i + c];
-        for (int c = 0; c < 4; ++c) dout[3 + c] = d_q[4 * i + c];
-    }
-#pragma unroll
-    for (int k = 0; k < kIn; ++k) H[k * kFT + tid] = h[k];
-#pragma unroll
-    for (int c = 0; c < 7; ++c) DO[c * kFT + tid] = dout[c];
-    __syncthreads();
-    float dh[kIn];
-#pragma unroll
-    for (int k = 0; k < kIn; ++k) dh[k] = 0.f;
-    float *blk = partial + (size_t)blockIdx.x * kPartials;
     for (int net = 0; net < 2; ++net) {
-        const int o0 = net ? 3 : 0, no = net ? 4 : 3;
-        for (int j = 0; j < kHidden; ++j) {
-            float z = s.b1[net][j];
 #pragma unroll
-            for (int k = 0; k < kIn; ++k) z = fmaf(s.w1[net][j][k], h[k], z);
-            float da = 0.f;
-            for (int c = 0; c < no; ++c) da = fmaf(s.w2[o0 + c][j], dout[o0 + c], da);
-            const float dz = z > 0.f ? da : 0.f;
-            A[j * kFT + tid] = z > 0.f ? z : 0.f;
-            DZ[j * kFT + tid] = dz;
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int k = 0; k < kIn; ++k) dh[k] = fmaf(s.w1[net][j][k], dz, dh[k]);
-        }
-        __syncthreads();
-        // this block's weight gradients of the net (rows of invalid threads are zero)
-        float *P = blk + (net ? kNetOff1 : 0);
-        for (int e = tid; e < kHidden * kIn; e += kFT) {
-            const int j = e / kIn, k = e % kIn;
-            const float4 *a4 = reinterpret_cast<const float4 *>(DZ + j * kFT);
-            const float4 *b4 = reinterpret_cast<const float4 *>(H + k * kFT);
-            float acc = 0.f;
-            for (int r = 0; r < kFT / 4; ++r) {
-                const float4 a = a4[r], b = b4[r];
-                acc = fmaf(a.x, b.x, acc); acc = fmaf(a.y, b.y, acc); acc = fmaf(a.z, b.z, acc); acc = fmaf(a.w, b.w, acc);
-            }
-            P[e] = acc;
-        }
-        for (int j = tid; j < kHidden; j += kFT) {
-            float acc = 0.f;
-            for (int r = 0; r < kFT; ++r) acc += DZ[j * kFT + r];
-            P[kHidden * kIn + j] = acc;
-        }
-        for (int e = tid; e < no * kHidden; e += kFT) {
-            const int c = e / kHidden, j = e % kHidden;
-            float acc = 0.f;
-            for (int r = 0; r < kFT; ++r) acc = fmaf(DO[(o0 + c) * kFT + r], A[j * kFT + r], acc);
-            P[kHidden * kIn + kHidden + e] = acc;
-        }
-        for (int c = tid; c < no; c += kFT) {
-            float acc = 0.f;
-            for (int r = 0; r < kFT; ++r) acc += DO[(o0 + c) * kFT + r];
-            P[kHidden * kIn + kHidden + no * kHidden + c] = acc;
-        }
-        __syncthreads();
+            for (int b = 0; b < 4; ++b) g1[net][a][b] = 0.f;
+        g2[net][0] = g2[net][1] = gb1[net] = 0.f;
     }
-    // table gradient: each corner's weight times the feature gradient
-    if (valid && d_table) {
-        float x[3];
-        unit_pos(F, mu, x);
-        const uint32_t T = 1u << F.log2T;
-        for (int l = 0; l < F.L; ++l) {
-            int c[3];
-            float w[3];
-            level_cell(F, l, x, c, w);
-            const bool dense = level_dense(F.res[l], F.log2T);
-            float2 *tab = reinterpret_cast<float2 *>(d_table) + (size_t)l * T;
-            for (int corner = 0; corner < 8; ++corner) {
-                const int o0 = corner & 1, o1 = (corner >> 1) & 1, o2 = (corner >> 2) & 1;
-                const float wt = (o0 ? w[0] : 1.f - w[0]) * (o1 ? w[1] : 1.f - w[1]) * (o2 ? w[2] : 1.f - w[2]);
-                const uint32_t idx = vertex_index(c[0] + o0, c[1] + o1, c[2] + o2, F.res[l], dense, T);
-                atomicAdd(tab + idx, make_float2(wt * dh[2 * l], wt * dh[2 * l + 1]));  // one vector atomic
+    const int64_t nchunks = (n + kFT - 1) / kFT;
+    for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        const int64_t i = chunk * kFT + tid;
+        const bool valid = i < n;
+        float mu[3] = {0.f, 0.f, 0.f};
+        float h[kIn], dout[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) dout[c] = 0.f;
+        if (valid) {
+            for (int a = 0; a < 3; ++a) mu[a] = means[3 * i + a];
+            for (int c = 0; c < 3; ++c) dout[c] = d_t[3 * i + c];
+            for (int c = 0; c < 4; ++c) dout[3 + c] = d_q[4 * i + c];
+        }
+        __syncthreads();  // the previous chunk's readers of the rows are done
+        {
+            // the chunk's encodings: contiguous in global memory, one padded shared row each
+            const int64_t row0 = chunk * kFT;
+#pragma unroll
+            for (int e = tid; e < kFT * (kIn / 4); e += kFT) {
+                const int r = e / (kIn / 4), q4 = e % (kIn / 4);
+                const float4 v = row0 + r < n ? hrows[(size_t)(row0 + r) * (kIn / 4) + q4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                *reinterpret_cast<float4 *>(HT + r * kHP + 4 * q4) = v;
+            }
+            float4 *orow = reinterpret_cast<float4 *>(DOT + tid * kOP);
+            orow[0] = make_float4(dout[0], dout[1], dout[2], dout[3]);
+            orow[1] = make_float4(dout[4], dout[5], dout[6], 0.f);
+        }
+        __syncthreads();
+        {
+            const float4 *hr = reinterpret_cast<const float4 *>(HT + tid * kHP);
+#pragma unroll
+            for (int q4 = 0; q4 < kIn / 4; ++q4) {
+                const float4 v = hr[q4];
+                h[4 * q4] = v.x;
+                h[4 * q4 + 1] = v.y;
+                h[4 * q4 + 2] = v.z;
+                h[4 * q4 + 3] = v.w;
             }
         }
+        float dh[kIn];
+#pragma unroll
+        for (int k = 0; k < kIn; ++k) dh[k] = 0.f;
+#pragma unroll
+        for (int net = 0; net < 2; ++net) {
+            const int o0 = net ? 3 : 0, no = net ? 4 : 3;
+            if (net) __syncthreads();  // net 0's readers of the hidden rows are done
+            for (int j0 = 0; j0 < kHidden; j0 += 4) {
+                float av[4], dz[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u;
+                    float z = s.b1[net][j];
+#pragma unroll
+                    for (int k = 0; k < kIn; ++k) z = fmaf(s.w1[net][j][k], h[k], z);
+                    float da = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (c < no) da = fmaf(s.w2[o0 + c][j], dout[o0 + c], da);
+                    dz[u] = z > 0.f ? da : 0.f;
+                    av[u] = z > 0.f ? z : 0.f;
+                }
+                *reinterpret_cast<float4 *>(AT + tid * kAP + j0) = make_float4(av[0], av[1], av[2], av[3]);
+                *reinterpret_cast<float4 *>(DZT + tid * kAP + j0) = make_float4(dz[0], dz[1], dz[2], dz[3]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int k = 0; k < kIn; ++k) dh[k] = fmaf(s.w1[net][j0 + u][k], dz[u], dh[k]);
+            }
+            __syncthreads();
+            // dW1[j][k] += sum over the chunk's Gaussians r of DZ[r][j] H[r][k]
+#pragma unroll 4
+            for (int r = 0; r < kFT; ++r) {
+                const float4 d4 = *reinterpret_cast<const float4 *>(DZT + r * kAP + 4 * tj);
+                const float4 h4 = *reinterpret_cast<const float4 *>(HT + r * kHP + 4 * tk);
+                const float dv[4] = {d4.x, d4.y, d4.z, d4.w}, hv[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) g1[net][a][b] = fmaf(dv[a], hv[b], g1[net][a][b]);
+            }
+            // dW2[c][j] += DO[r][c] A[r][j]; db1[j] += DZ[r][j]; db2[c] += DO[r][c]
+            if (ch == 0) {
+#pragma unroll 4
+                for (int r = 0; r < kFT; ++r) {
+                    const float a = AT[r * kAP + cj];
+                    g2[net][0] = fmaf(DOT[r * kOP + o0], a, g2[net][0]);
+                    g2[net][1] = fmaf(DOT[r * kOP + o0 + 1], a, g2[net][1]);
+                    gb1[net] += DZT[r * kAP + cj];
+                }
+            } else {
+#pragma unroll 4
+                for (int r = 0; r < kFT; ++r) {
+                    const float a = AT[r * kAP + cj];
+                    g2[net][0] = fmaf(DOT[r * kOP + o0 + 2], a, g2[net][0]);
+                    if (no == 4) g2[net][1] = fmaf(DOT[r * kOP + o0 + 3], a, g2[net][1]);
+                }
+            }
+            if (net == 0 && tid < 7)
+                for (int r = 0; r < kFT; ++r) gb2 += DOT[r * kOP + tid];
+        }
+        // table gradient: each corner's weight times the feature gradient
+        if (valid && d_table) {
+            float x[3];
+            unit_pos(F, mu, x);
+            const uint32_t T = 1u << F.log2T;
+#pragma unroll
+            for (int l = 0; l < kMaxLv; ++l) {
+                if (l >= F.L) break;
+                int c[3];
+                float w[3];
+                level_cell(F, l, x, c, w);
+                const bool dense = level_dense(F.res[l], F.log2T);
+                float2 *tab = reinterpret_cast<float2 *>(d_table) + (size_t)l * T;
+                for (int corner = 0; corner < 8; ++corner) {
+                    const int o0 = corner & 1, o1 = (corner >> 1) & 1, o2 = (corner >> 2) & 1;
+                    const float wt = (o0 ? w[0] : 1.f - w[0]) * (o1 ? w[1] : 1.f - w[1]) * (o2 ? w[2] : 1.f - w[2]);
+                    const uint32_t idx = vertex_index(c[0] + o0, c[1] + o1, c[2] + o2, F.res[l], dense, T);
+                    atomicAdd(tab + idx, make_float2(wt * dh[2 * l], wt * dh[2 * l + 1]));  // one vector atomic
+                }
+            }
+        }
+    }
+    // this block's partial: per net w1 (kHidden x kIn), b1, w2 (no x kHidden), b2
+    float *blk = partial + (size_t)blockIdx.x * kPartials;
+#pragma unroll
+    for (int net = 0; net < 2; ++net) {
+        const int no = net ? 4 : 3;
+        float *P = blk + (net ? kNetOff1 : 0);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) P[(4 * tj + a) * kIn + 4 * tk + b] = g1[net][a][b];
+        if (ch == 0) P[kHidden * kIn + cj] = gb1[net];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int c = 2 * ch + u;
+            if (c < no) P[kHidden * kIn + kHidden + c * kHidden + cj] = g2[net][u];
+        }
+    }
+    if (tid < 7) {
+        const int net = tid < 3 ? 0 : 1, c = tid < 3 ? tid : tid - 3, no = net ? 4 : 3;
+        blk[(net ? kNetOff1 : 0) + kHidden * kIn + kHidden + no * kHidden + c] = gb2;
     }
 }
 
@@ -350,15 +448,19 @@ extern "C" gc_status gc_motion_field_backward(gc_context *ctx, const gc_motion_f
             if (zero[k]) GC_CUDA(ctx, cudaMemsetAsync(zero[k], 0, sizes[k] * 4, s));
         return GC_OK;
     }
-    const int nblocks = (int)((n + gc::kFT - 1) / gc::kFT);
+    const int64_t nchunks = (n + gc::kFT - 1) / gc::kFT;
+    const int nblocks = (int)std::min<int64_t>(nchunks, gc::kBwdGrid);
     GC_CUDA(ctx, grow(ctx->field_part, (size_t)nblocks * gc::kPartials * 4));
+    GC_CUDA(ctx, grow(ctx->field_h, (size_t)n * gc::kIn * 4));
     GC_CUDA(ctx, cudaFuncSetAttribute(gc::k_field_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)gc::kBwdDyn));
-    gc::k_field_bwd<<<nblocks, gc::kFT, gc::kBwdDyn, s>>>(F, means, n, d_q, d_t, ctx->field_part.as<float>(),
-                                                          out->table);
+    float4 *hrows = ctx->field_h.as<float4>();
+    gc::k_field_encode<<<(unsigned)nchunks, gc::kFT, 0, s>>>(F, means, n, hrows);
+    gc::k_field_bwd<<<nblocks, gc::kFT, gc::kBwdDyn, s>>>(F, means, hrows, n, d_q, d_t,
+                                                          ctx->field_part.as<float>(), out->table);
     gc::FieldGrads g{{out->w1t, out->w1r}, {out->b1t, out->b1r}, {out->w2t, out->w2r}, {out->b2t, out->b2r}};
     gc::k_field_reduce<<<(gc::kPartials + 255) / 256, 256, 0, s>>>(ctx->field_part.as<float>(), nblocks, din, g);
-    gc::note_launches(2);
+    gc::note_launches(3);
     GC_CUDA(ctx, cudaGetLastError());
     return GC_OK;
 }

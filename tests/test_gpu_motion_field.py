@@ -24,11 +24,13 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("levels,log2_T", [(16, 15), (5, 12), (1, 4)])
-def test_field_forward_backward_matches_oracle(gc, levels, log2_T):
+@pytest.mark.parametrize("levels,log2_T,n", [(16, 15, 20_077), (5, 12, 20_077), (1, 4, 20_077),
+                                             (16, 19, 296 * 128 * 2 + 77)])
+def test_field_forward_backward_matches_oracle(gc, levels, log2_T, n):
+    """n = 20,077: one chunk of 128 Gaussians per block, ragged last chunk; the last case gives
+    every block of the persistent backward two or three chunks."""
     rng = np.random.default_rng(7 + levels)
     p = scenes.motion_field_params(rng, n_levels=levels, log2_T=log2_T, n_min=4 if levels == 1 else 16)
-    n = 20_000 + 77   # ragged last block
     mu = rng.uniform(-1.6, 1.6, (n, 3)).astype(np.float32)    # some outside the box: clamped
     t_ref, q_ref = mn.forward(mu, p)
     r = gc.Renderer(0)
