@@ -467,9 +467,28 @@ def run_gpu(args):
         levels_fwd()
         levels_fwd_bwd()
     r.check()
-    fwd_ms, fwd_prof, clk = timer(levels_fwd, args.steps, profile=True, name="levels_fwd")
-    fb_ms, fb_prof, clk_fb = timer(levels_fwd_bwd, args.steps, profile=True, name="levels_fwd_bwd")
+    ef_lv_ms, fwd_prof, clk_e = timer(levels_fwd, args.steps, profile=True, name="levels_fwd")
+    efb_lv_ms, fb_prof, clk_efb = timer(levels_fwd_bwd, args.steps, profile=True, name="levels_fwd_bwd")
     r.check()
+    # the headline value: the same steps replayed from one CUDA graph each (gc_levels_graph:
+    # no host work, no launch gaps between the kernels of a frame, identical images); the
+    # eager runs above give the per-stage split and the blend kernels' launch times
+    cams_step = w.cameras[:args.frames]
+    lg_fwd = gc.LevelsGraph(r, gs, frames, cams_step, 6, outs=outs[:6 * args.frames])
+    lg_fb = gc.LevelsGraph(r, gs, frames, cams_step, 6, outs=outs[:6 * args.frames],
+                           dL_dimages=dls[:6 * args.frames], grads=[lgrads] * args.frames)
+    for _ in range(args.warmup):
+        lg_fwd.launch()
+        lg_fb.launch()
+    lg_fwd.check()
+    lg_fb.check()
+    fwd_ms, gfwd_prof, clk = timer(lg_fwd.launch, args.steps, name="levels_graph_fwd")
+    fb_ms, gfb_prof, clk_fb = timer(lg_fb.launch, args.steps, name="levels_graph_fwd_bwd")
+    lg_fwd.check()
+    lg_fb.check()
+    graph_nodes = {"fwd": lg_fwd.kernel_nodes, "fwd_bwd": lg_fb.kernel_nodes}
+    lg_fwd.close()
+    lg_fb.close()
     del lsaved, lgrads
     r.set_options(key_capacity=0)
     frames_per_step = args.frames
@@ -649,20 +668,26 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "n_gaussians": w.scene.n, "width": W, "height": H,
                        "renders_per_step": n_req,
                        "path": "single-pass multi-level render: per frame one gc_render_levels_forward "
-                               "(+ gc_render_levels_backward) renders levels L1..L6",
+                               "(+ gc_render_levels_backward) renders levels L1..L6; the step's frames "
+                               "replayed from one CUDA graph (gc_levels_graph)",
                        "tile": f"{tile[0]}x{tile[1]}", "key_capacity": cap_levels,
                        "l2": "flushed (256 MB write) between steps, outside the timed events",
                        "parallelism": f"replicas x{world}"},
             "fps": round(n_req * args.steps * world / (fwd_ms / 1e3), 1),
-            "gpu_launches": fwd_prof["kernel_launches"],
+            "gpu_launches": gfwd_prof["kernel_launches"],
             "roofline": roof(fwd_prof, args.steps, False, walked_top, bwd_top, frames_per_step),
             "clocks": clk,
+            "eager": {"note": "the same steps as eager calls (one library call per frame, per-stage CUDA "
+                              "events on); their events give stage_profile and the roofline launch times",
+                      "fwd": mpix(ef_lv_ms, args.steps), "fwd_bwd": mpix(efb_lv_ms, args.steps), "unit": UNIT,
+                      "gpu_launches": {"fwd": fwd_prof["kernel_launches"], "fwd_bwd": fb_prof["kernel_launches"]},
+                      "graph_kernel_nodes": graph_nodes, "clocks": {"fwd": clk_e, "fwd_bwd": clk_efb}},
             "fwd_bwd": {"metric": "Mpixel/s at 1920x1080, forward + backward (upstream dL/dimage given), "
                                   "gradients summed over the step's renders",
                         "value": mpix(fb_ms, args.steps), "unit": UNIT,
                         "ms_per_step": round(fb_ms / args.steps, 3),
                         "fps": round(n_req * args.steps * world / (fb_ms / 1e3), 1),
-                        "gpu_launches": fb_prof["kernel_launches"],
+                        "gpu_launches": gfb_prof["kernel_launches"],
                         "roofline": roof(fb_prof, args.steps, False, walked_top, bwd_top, frames_per_step),
                         "clocks": clk_fb},
             "stage_profile": {"note": "ms per call of the headline path (one frame, six levels)",

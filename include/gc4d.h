@@ -376,6 +376,44 @@ GC_API gc_status gc_batch_graph_info(const gc_batch_graph *graph, int64_t *key_c
 GC_API gc_status gc_batch_graph_check(gc_batch_graph *graph, void *stream);
 GC_API gc_status gc_batch_graph_destroy(gc_batch_graph *graph);
 
+/*
+ * Multi-level graphs: a multi-frame step of the single-pass multi-level render (every
+ * quality level of each frame, Eq. 4; the paper's per-level rate-distortion renders,
+ * Sec. 3.3) as one CUDA graph.  Per frame f = 0..n_frames-1, in order, the graph holds
+ * gc_render_levels_forward(motions[f] (or no motion when motions is NULL), cameras[f],
+ * levels, level_images + f * levels) and, when dL_dimages is not NULL,
+ * gc_render_levels_backward(dL_dimages + f * levels, &grads[f]) - so a training step
+ * renders and differentiates every frame; grads is a host array of n_frames gradient
+ * sets (entries may name the same buffers; each frame overwrites what it names).
+ * cameras: host array of n_frames; level_images and dL_dimages: host arrays of
+ * n_frames * levels device pointers (3 x height x width each).  Creation fixes the key
+ * capacity (the context's option, or with 0 the largest frame's exact need plus 5 %,
+ * measured by one eager forward pass), runs the step eagerly once at that capacity
+ * (sizing every buffer), then captures it; launching replays every kernel with no host
+ * work, images identical to the eager calls.  The graph reads and writes the same
+ * device arrays as at creation: update their contents in place.  It owns its saved
+ * state and must be destroyed before the context.  An overflow of any frame and
+ * bounded-wait timeouts are reported by gc_levels_graph_check.  The context's options
+ * are read at creation and restored afterwards; profiling is off inside the graph.
+ * Errors: GC_ERR_INVALID_ARG (missing arrays, n_frames or levels < 1), any error of the
+ * captured calls, GC_ERR_CUDA if capture or instantiation fails; nothing is created
+ * then.
+ */
+typedef struct gc_levels_graph gc_levels_graph;
+
+GC_API gc_status gc_levels_graph_create(gc_context *ctx, const gc_gaussians *g, const gc_motion *motions,
+                                        int32_t n_frames, const gc_camera *cameras, int32_t levels,
+                                        float *const *level_images, const float *const *dL_dimages,
+                                        gc_grads *grads, void *stream, gc_levels_graph **out);
+GC_API gc_status gc_levels_graph_launch(gc_levels_graph *graph, void *stream);
+/* Key capacity per frame and kernel nodes in the graph; either may be NULL. */
+GC_API gc_status gc_levels_graph_info(const gc_levels_graph *graph, int64_t *key_capacity,
+                                      int64_t *kernel_nodes);
+/* Synchronises `stream`; GC_ERR_CAPACITY if a frame of a replay since the last check
+ * needed more keys than the capacity, GC_ERR_TIMEOUT if a bounded wait ran out. */
+GC_API gc_status gc_levels_graph_check(gc_levels_graph *graph, void *stream);
+GC_API gc_status gc_levels_graph_destroy(gc_levels_graph *graph);
+
 /* One measured configuration of the autotuner. */
 typedef struct {
     int32_t tile_w, tile_h;  /* tile shape */

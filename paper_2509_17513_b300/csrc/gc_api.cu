@@ -255,7 +255,7 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
             GC_CUDA(ctx, gc::launch_emit(S.ranked.as<float4>(), S.offsets.as<uint32_t>(),
                                          S.touched_r.as<uint32_t>(), n_sel, rp, cam->width, cam->height,
                                          S.tkeys[0].as<uint32_t>(), S.tvals[0].as<uint32_t>(),
-                                         (uint32_t)K, s));
+                                         (uint32_t)K, s, words, S.k_exact ? nullptr : words + 2));
             uint32_t *tk[2] = {S.tkeys[0].as<uint32_t>(), S.tkeys[1].as<uint32_t>()};
             uint32_t *tv[2] = {S.tvals[0].as<uint32_t>(), S.tvals[1].as<uint32_t>()};
             const uint32_t *ndev = S.k_exact ? nullptr : words;
@@ -286,6 +286,18 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
     GC_CUDA(ctx, prof_mark(ctx, s, -1));
     S.valid = true;
     ctx->last = &S;
+    return GC_OK;
+}
+
+// Fixed key capacity: the largest count that any forward on this state needed since the last
+// check (word 2, kept by the emit kernel) against the capacity; the record is then cleared.
+gc_status capacity_check(gc_context *ctx, const gc_saved &S) {
+    uint32_t w[3];
+    GC_CUDA(ctx, cudaMemcpy(w, S.words.p, 12, cudaMemcpyDeviceToHost));
+    GC_CUDA(ctx, cudaMemset(static_cast<uint32_t *>(S.words.p) + 2, 0, 4));
+    const uint32_t need = std::max(w[0], w[2]);
+    if ((int64_t)need > S.K)
+        return fail(ctx, GC_ERR_CAPACITY, "a frame needs %u keys, capacity %lld", need, (long long)S.K);
     return GC_OK;
 }
 
@@ -422,12 +434,7 @@ gc_status gc_check(gc_context *ctx, void *stream) {
         }
     }
     if (S.batch && S.batch.get() && !S.valid) return batch_check(ctx, S);
-    if (S.valid && !S.k_exact && S.n_sel > 0) {
-        GC_CUDA(ctx, cudaMemcpy(ctx->host_word, S.words.p, 4, cudaMemcpyDeviceToHost));
-        if ((int64_t)ctx->host_word[0] > S.K)
-            return fail(ctx, GC_ERR_CAPACITY, "frame needs %u keys, capacity %lld",
-                        ctx->host_word[0], (long long)S.K);
-    }
+    if (S.valid && !S.k_exact && S.n_sel > 0) return capacity_check(ctx, S);
     return GC_OK;
 }
 

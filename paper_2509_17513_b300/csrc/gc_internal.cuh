@@ -191,7 +191,8 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
 // mode reports the overflow).
 cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uint32_t *touched_r,
                         int64_t n, const RenderParams &rp, int W, int H, uint32_t *keys, uint32_t *vals,
-                        uint32_t cap, cudaStream_t st);
+                        uint32_t cap, cudaStream_t st, const uint32_t *total = nullptr,
+                        uint32_t *peak = nullptr);
 
 // Tile ranges [start, end) from sorted tile keys; ranges must be zeroed.
 cudaError_t launch_tile_ranges(const uint32_t *keys, const uint32_t *n_dev, int64_t n_max,

@@ -1,0 +1,184 @@
+// gc_levels_graph.cu - a multi-frame step of the single-pass multi-level render (every
+// quality level of each frame from one sorted list, Eq. 4 / Sec. 3.3) as one CUDA graph.
+//
+// Per frame, in order: gc_render_levels_forward and, for a training step,
+// gc_render_levels_backward, on one saved state that the graph owns.  With a fixed key
+// capacity neither call synchronises, allocates or copies to the host once the buffers are
+// sized, so the whole step is captured after one eager pass and replayed with no host work:
+// the launch gaps between the ~15 kernels of every frame disappear.  The emit kernel keeps
+// the largest key count of any frame on the state, which gc_levels_graph_check compares
+// with the capacity.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "gc_state.cuh"
+
+struct gc_levels_graph {
+    gc_context *ctx = nullptr;
+    gc_saved *state = nullptr;
+    int64_t key_capacity = 0;
+    int64_t kernel_nodes = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void levels_graph_free(gc_levels_graph *G) {
+    if (!G) return;
+    DeviceGuard dg(G->ctx->device);
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    if (G->state) gc_saved_destroy(G->ctx, G->state);
+    if (G->own_stream) cudaStreamDestroy(G->own_stream);
+    delete G;
+}
+
+struct LevelsStep {
+    const gc_gaussians *g;
+    const gc_motion *motions;
+    int n_frames;
+    const gc_camera *cams;
+    int levels;
+    float *const *images;
+    const float *const *dL;
+    gc_grads *grads;
+};
+
+gc_status levels_pass(gc_levels_graph *G, const LevelsStep &P, cudaStream_t s, int64_t *max_keys) {
+    for (int f = 0; f < P.n_frames; ++f) {
+        const gc_motion *m = P.motions ? &P.motions[f] : nullptr;
+        gc_status st = gc_render_levels_forward(G->ctx, P.g, m, P.levels, &P.cams[f], P.images + (size_t)f * P.levels,
+                                                G->state, s);
+        if (st != GC_OK) return st;
+        if (max_keys) *max_keys = std::max<int64_t>(*max_keys, G->state->K);
+        if (P.dL) {
+            st = gc_render_levels_backward(G->ctx, G->state, P.g, m, P.dL + (size_t)f * P.levels, &P.grads[f], s);
+            if (st != GC_OK) return st;
+        }
+    }
+    return GC_OK;
+}
+
+}  // namespace
+
+extern "C" gc_status gc_levels_graph_create(gc_context *ctx, const gc_gaussians *g, const gc_motion *motions,
+                                            int32_t n_frames, const gc_camera *cameras, int32_t levels,
+                                            float *const *level_images, const float *const *dL_dimages,
+                                            gc_grads *grads, void *stream, gc_levels_graph **out) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    if (!out) return fail(ctx, GC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_frames < 1 || !cameras || !level_images || levels < 1)
+        return fail(ctx, GC_ERR_INVALID_ARG, "need n_frames >= 1, cameras, levels >= 1 and level_images");
+    if (dL_dimages && !grads) return fail(ctx, GC_ERR_INVALID_ARG, "dL_dimages without grads");
+    DeviceGuard dg(ctx->device);
+    gc_levels_graph *G = new gc_levels_graph;
+    G->ctx = ctx;
+    const gc_options saved_opt = ctx->opt;
+    const bool saved_prof = ctx->prof_on;
+    auto bail = [&](gc_status e) {
+        ctx->opt = saved_opt;
+        ctx->prof_on = saved_prof;
+        levels_graph_free(G);
+        return e;
+    };
+    gc_status st = gc_saved_create(ctx, &G->state);
+    if (st != GC_OK) return bail(st);
+    ctx->prof_on = false;  // no profiling events inside a graph
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!s) {  // capture needs a stream other than the legacy default one
+        if (cudaStreamCreateWithFlags(&G->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(ctx, GC_ERR_CUDA, "stream creation failed"));
+        }
+        s = G->own_stream;
+    }
+    const LevelsStep P{g, motions, n_frames, cameras, levels, level_images, dL_dimages, grads};
+    // 1. key capacity: the caller's, or the largest frame's exact need plus 5 %
+    int64_t cap = saved_opt.key_capacity;
+    if (cap <= 0) {
+        ctx->opt.key_capacity = 0;
+        int64_t kmax = 0;
+        const LevelsStep fwd{g, motions, n_frames, cameras, levels, level_images, nullptr, nullptr};
+        if ((st = levels_pass(G, fwd, s, &kmax)) != GC_OK) return bail(st);
+        const int64_t T = gc::radix_tile_keys();
+        cap = (kmax + kmax / 20 + 2 * T + T - 1) / T * T;
+        if (cap > 0xFFFFFFF0ll) return bail(fail(ctx, GC_ERR_CAPACITY, "a frame needs more than 2^32 keys"));
+    }
+    G->key_capacity = cap;
+    ctx->opt.key_capacity = cap;
+    // 2. eager pass at the fixed capacity: sizes every buffer
+    if ((st = levels_pass(G, P, s, nullptr)) != GC_OK) return bail(st);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctx, GC_ERR_CUDA, "eager pass failed"));
+    if ((st = capacity_check(ctx, *G->state)) != GC_OK) return bail(st);
+    // 3. capture the same pass
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(ctx, GC_ERR_CUDA, "cannot begin stream capture"));
+    }
+    st = levels_pass(G, P, s, nullptr);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    G->graph = graph;
+    if (st != GC_OK) return bail(st);
+    if (ce != cudaSuccess || !graph) {
+        cudaGetLastError();
+        return bail(fail(ctx, GC_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ce)));
+    }
+    size_t n_nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &n_nodes);
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    if (n_nodes) cudaGraphGetNodes(graph, nodes.data(), &n_nodes);
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) G->kernel_nodes++;
+    }
+    if (cudaGraphInstantiate(&G->exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(ctx, GC_ERR_CUDA, "graph instantiation failed"));
+    }
+    ctx->opt = saved_opt;
+    ctx->prof_on = saved_prof;
+    *out = G;
+    return GC_OK;
+}
+
+extern "C" gc_status gc_levels_graph_launch(gc_levels_graph *G, void *stream) {
+    if (!G) return GC_ERR_INVALID_ARG;
+    DeviceGuard dg(G->ctx->device);
+    GC_CUDA(G->ctx, cudaGraphLaunch(G->exec, (cudaStream_t)stream));
+    gc::note_launches((int)G->kernel_nodes);
+    return GC_OK;
+}
+
+extern "C" gc_status gc_levels_graph_info(const gc_levels_graph *G, int64_t *key_capacity, int64_t *kernel_nodes) {
+    if (!G) return GC_ERR_INVALID_ARG;
+    if (key_capacity) *key_capacity = G->key_capacity;
+    if (kernel_nodes) *kernel_nodes = G->kernel_nodes;
+    return GC_OK;
+}
+
+extern "C" gc_status gc_levels_graph_check(gc_levels_graph *G, void *stream) {
+    if (!G) return GC_ERR_INVALID_ARG;
+    gc_context *ctx = G->ctx;
+    DeviceGuard dg(ctx->device);
+    GC_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+    const gc_saved &S = *G->state;
+    uint32_t err = 0;
+    GC_CUDA(ctx, cudaMemcpy(&err, static_cast<uint32_t *>(S.words.p) + 1, 4, cudaMemcpyDeviceToHost));
+    if (err) {
+        GC_CUDA(ctx, cudaMemset(static_cast<uint32_t *>(S.words.p) + 1, 0, 4));
+        return fail(ctx, GC_ERR_TIMEOUT, "a bounded device wait ran out (error word %#x)", err);
+    }
+    return capacity_check(ctx, S);
+}
+
+extern "C" gc_status gc_levels_graph_destroy(gc_levels_graph *G) {
+    if (!G) return GC_ERR_INVALID_ARG;
+    levels_graph_free(G);
+    return GC_OK;
+}

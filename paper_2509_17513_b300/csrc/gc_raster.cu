@@ -25,7 +25,11 @@ __global__ void __launch_bounds__(256) k_emit(const float4 *__restrict__ ranked,
                                               const uint32_t *__restrict__ touched_r, int64_t n,
                                               RenderParams rp, int W, int H, uint32_t cap,
                                               uint32_t *__restrict__ keys,
-                                              uint32_t *__restrict__ vals) {
+                                              uint32_t *__restrict__ vals, const uint32_t *total,
+                                              uint32_t *peak) {
+    // the largest key count any forward needed since the host last looked (a fixed capacity
+    // is checked against it, so that an overflow of any frame of a multi-frame step shows)
+    if (peak && blockIdx.x == 0 && threadIdx.x == 0) atomicMax(peak, *total);
     const int lane = threadIdx.x & 31;
     const int64_t wbase = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - lane;
     if (wbase >= n) return;
@@ -110,11 +114,12 @@ cudaError_t launch_entries_to_global(const uint32_t *sorted_vals, const uint32_t
 
 cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uint32_t *touched_r,
                         int64_t n, const RenderParams &rp, int W, int H, uint32_t *keys, uint32_t *vals,
-                        uint32_t cap, cudaStream_t st) {
+                        uint32_t cap, cudaStream_t st, const uint32_t *total, uint32_t *peak) {
     if (n <= 0) return cudaSuccess;
+    if (peak && !total) return cudaErrorInvalidValue;
     const int64_t threads = ((n + 31) / 32) * 32;
     k_emit<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(ranked, offsets, touched_r, n, rp, W, H, cap,
-                                                                keys, vals);
+                                                                keys, vals, total, peak);
     note_launches(1);
     return cudaGetLastError();
 }

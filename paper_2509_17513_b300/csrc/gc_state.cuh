@@ -127,6 +127,10 @@ inline gc_status fail(gc_context *ctx, gc_status s, const char *fmt, ...) {
     } while (0)
 
 // Records a stage boundary on the stream when profiling is on.
+// GC_ERR_CAPACITY if a forward on S since the last check needed more keys than its fixed
+// capacity (synchronous; S must have a fixed capacity).
+gc_status capacity_check(gc_context *ctx, const gc_saved &S);
+
 inline cudaError_t prof_mark(gc_context *ctx, cudaStream_t s, int stage) {
     if (!ctx->prof_on) return cudaSuccess;
     const size_t idx = ctx->prof_marks.size();

@@ -517,6 +517,75 @@ class Renderer:
         check(lib().gc_check(self.ctx, _stream(stream)), self.ctx)
 
 
+class LevelsGraph:
+    """A multi-frame step of the single-pass multi-level render as one CUDA graph
+    (gc_levels_graph): per frame the images of levels 1..levels and, with dL_dimages, their
+    backward into that frame's gradient set.  frames: one MotionFrame (or None) per frame;
+    outs / dL_dimages: n_frames * levels tensors (3, H, W), frame-major; grads: one dict per
+    frame (the same dict may repeat).  The tensors given here are the ones every launch
+    reads and writes: update them in place."""
+
+    def __init__(self, renderer: Renderer, gs: GaussianSet, frames: list, cameras: list, levels: int,
+                 outs: list | None = None, dL_dimages: list | None = None, grads: list | None = None,
+                 stream=None):
+        nf = len(cameras)
+        if len(frames) != nf:
+            raise ValueError("one motion frame (or None) per camera")
+        self.renderer, self.gs, self.frames, self.levels = renderer, gs, frames, int(levels)
+        self._cams = (_abi.Camera * nf)(*[camera_struct(c) for c in cameras])
+        if outs is None:
+            outs = [torch.empty((3, c.height, c.width), dtype=torch.float32, device=f"cuda:{renderer.device}")
+                    for c in cameras for _ in range(levels)]
+        if len(outs) != nf * levels:
+            raise ValueError("outs needs n_frames * levels images")
+        self.outs = outs
+        self._imgs = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+        motions = None
+        if any(f is not None for f in frames):
+            if not all(f is not None for f in frames):
+                raise ValueError("either every frame has a motion or none has")
+            motions = (_abi.Motion * nf)(*[f.struct for f in frames])
+        self._motions = motions
+        self.dL, self.grads, dls, gstructs = dL_dimages, None, None, None
+        if dL_dimages is not None:
+            if len(dL_dimages) != nf * levels:
+                raise ValueError("dL_dimages needs n_frames * levels tensors")
+            dls = (C.c_void_p * len(dL_dimages))(*[d.data_ptr() for d in dL_dimages])
+            if grads is None:
+                g0 = renderer._single_grads(gs, frames[0])
+                grads = [g0] * nf
+            if len(grads) != nf:
+                raise ValueError("grads needs one dict per frame")
+            self.grads = grads
+            gstructs = (_abi.Grads * nf)(*[renderer._grads_struct(g) for g in grads])
+        self._dls, self._gstructs = dls, gstructs
+        h = C.c_void_p()
+        st = lib().gc_levels_graph_create(renderer.ctx, C.byref(gs.struct), motions, nf, self._cams, self.levels,
+                                          self._imgs, dls, gstructs, _stream(stream), C.byref(h))
+        check(st, renderer.ctx)
+        self.handle = h
+        cap, nodes = C.c_int64(), C.c_int64()
+        check(lib().gc_levels_graph_info(h, C.byref(cap), C.byref(nodes)), renderer.ctx)
+        self.key_capacity, self.kernel_nodes = cap.value, nodes.value
+
+    def launch(self, stream=None):
+        check(lib().gc_levels_graph_launch(self.handle, _stream(stream)), self.renderer.ctx)
+
+    def check(self, stream=None):
+        check(lib().gc_levels_graph_check(self.handle, _stream(stream)), self.renderer.ctx)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().gc_levels_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class BatchGraph:
     """A whole step over many requests as one CUDA graph (gc_batch_graph): batches of
     `depth` requests, each a batched forward and, with dL_dimages, a batched backward
