@@ -135,10 +135,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash() -> str:
+# the source file that defines each profiled kernel (every kernel also depends on the shared
+# .cuh headers); a kernel not listed depends on every source file
+KERNEL_SOURCES = {"k_blend_levels_fwd": "gc_levels.cu", "k_blend_levels_bwd": "gc_levels.cu",
+                  "k_blend_fwd": "gc_raster.cu", "k_emit": "gc_raster.cu", "k_radix_scatter": "gc_sort.cu",
+                  "k_batch_blend_fwd": "gc_batch.cu", "k_batch_blend_bwd": "gc_batch.cu",
+                  "k_batch_emit": "gc_batch.cu", "k_field_bwd": "gc_motion_field.cu",
+                  "k_field_encode": "gc_motion_field.cu"}
+
+
+def kernel_source_hash(kernel: str | None = None) -> str:
+    """First 16 hex digits of the sha256 over the sources that make up `kernel`: the file that
+    defines it and the shared headers (every csrc file when the kernel is not listed)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2509_17513_b300", "csrc")
+    own = KERNEL_SOURCES.get(kernel)
     for name in sorted(os.listdir(d)):
+        if own is not None and not (name.endswith(".cuh") or name == own):
+            continue
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -147,17 +161,15 @@ def kernel_source_hash() -> str:
 def load_traffic(kernel: str, units_per_launch: int):
     """DRAM bytes of one launch of `kernel` covering `units_per_launch` units (renders, or
     frames of a multi-level pass), from the committed ncu summary profiles/traffic.json
-    (bytes per unit of a small capture), or None when the kernels changed since it was
-    taken or the kernel was not captured."""
+    (bytes per unit of a small capture), or None when the kernel's sources changed since it
+    was taken or the kernel was not captured."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("source_hash") != kernel_source_hash():
-        return None
     e = d.get("kernels", {}).get(kernel)
-    if not e:
+    if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return int(e["dram_bytes_per_unit"] * units_per_launch)
 
