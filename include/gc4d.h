@@ -458,6 +458,22 @@ GC_API gc_status gc_motion_field_backward(gc_context *ctx, const gc_motion_field
 GC_API gc_status gc_kde_rate(gc_context *ctx, const float *y, int32_t n_channels, int64_t n, int64_t stride,
                              float *rate, void *stream);
 
+/* Training form of the KDE rate (Sec. 3.3: differentiable quantisation by injected uniform
+ * noise).  y holds the noise-injected values y~_i = y_i + u_i in units of the quantisation
+ * step (the caller draws u), n per channel at y + c * stride.  The density is the one of
+ * gc_kde_rate, built from the symbols s_i = round(y~_i) and held fixed; the rate is taken at
+ * the continuous values and differentiated through them:
+ *   P(x) = CDF(x + 1/2) - CDF(x - 1/2),  R_c = -(1/n) sum_i log2 max(P(y~_i), 2^-40),
+ *   dR_c/dy~_i = -(pdf(y~_i + 1/2) - pdf(y~_i - 1/2)) / (n ln 2 P(y~_i))  (0 at the floor),
+ *   pdf(x) = (1/(n h)) sum_j phi((x - s_j) / h).
+ * For integer inputs R_c equals gc_kde_rate.  d_rate: device array of n_channels upstream
+ * gradients dL/dR_c, or NULL for ones.  Writes rate[c] (device) and, when d_y is not NULL,
+ * d_y[c * stride + i] = dL/dR_c * dR_c/dy~_i (device, the layout of y).  Unsupported channels
+ * (as in gc_kde_rate) get NaN in rate and in their d_y row.  Symbols farther than 12 h + 1
+ * from a value are left out of its sums (their share is below 1e-32). */
+GC_API gc_status gc_kde_rate_grad(gc_context *ctx, const float *y, int32_t n_channels, int64_t n,
+                                  int64_t stride, const float *d_rate, float *rate, float *d_y, void *stream);
+
 /* Statistics of the last forward recorded in `saved` (synchronises `stream`). */
 GC_API gc_status gc_saved_stats(gc_context *ctx, const gc_saved *saved, gc_stats *out, void *stream);
 

@@ -94,7 +94,7 @@ gc_status gc_destroy(gc_context *ctx) {
         saved_release(ctx, &ctx->internal);
         ctx->internal.batch.reset();
         DevBuf *bufs[] = {&ctx->scratch, &ctx->bwd_part, &ctx->bwd_g2d, &ctx->bwd_motion,
-                          &ctx->bwd_group, &ctx->field_part, &ctx->field_h};
+                          &ctx->bwd_group, &ctx->field_part, &ctx->field_h, &ctx->kde_scratch};
         for (DevBuf *b : bufs) release(*b);
         if (ctx->host_word) cudaFreeHost(ctx->host_word);
         for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);

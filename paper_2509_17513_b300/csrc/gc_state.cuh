@@ -100,6 +100,7 @@ struct gc_context {
     DevBuf scratch, bwd_part, bwd_g2d, bwd_motion, bwd_group;
     DevBuf field_part;              // per-block partial gradients of the motion source
     DevBuf field_h;                 // hash-grid encodings of the motion source (backward)
+    DevBuf kde_scratch;             // KDE training form: histograms, bandwidths, partial sums
     bool bwd_part_clean = false;  // bwd_part holds only zeros (see the reduce)
     uint32_t *host_word = nullptr;  // pinned
     const gc_saved *last = nullptr; // state written by the most recent forward

@@ -374,6 +374,22 @@ class Renderer:
         check(lib().gc_kde_rate(self.ctx, y.data_ptr(), C_, N, N, out.data_ptr(), _stream(stream)), self.ctx)
         return out
 
+    def kde_rate_grad(self, y: torch.Tensor, d_rate: torch.Tensor | None = None, grad: bool = True,
+                      stream=None):
+        """Training form of the rate (Sec. 3.3): ``y`` (C, N) holds noise-injected values; the
+        density of their rounded values is held fixed and the rate is taken at the values
+        themselves.  Returns (rate (C,), dL/dy (C, N) or None), dL/dy = d_rate[c] dR_c/dy
+        (d_rate None = ones)."""
+        y = y.contiguous()
+        C_, N = int(y.shape[0]), int(y.shape[1])
+        out = torch.empty(C_, device=y.device)
+        dy = torch.empty_like(y) if grad else None
+        dr = d_rate.contiguous() if d_rate is not None else None
+        check(lib().gc_kde_rate_grad(self.ctx, y.data_ptr(), C_, N, N, dr.data_ptr() if dr is not None else None,
+                                     out.data_ptr(), dy.data_ptr() if dy is not None else None, _stream(stream)),
+              self.ctx)
+        return out, dy
+
     # ---- batched requests -------------------------------------------------------------
 
     def batch_forward(self, gs: GaussianSet, frames: list, requests: list, saved: Saved | None = None,
