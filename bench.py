@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -135,8 +136,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# the source file that defines each profiled kernel (every kernel also depends on the shared
-# .cuh headers); a kernel not listed depends on every source file
+# the source file that defines each profiled kernel; its hash covers that file and the kernel
+# sources it includes (transitively).  A kernel not listed depends on every source file.
+HEADLINE_TILE = (8, 32)  # tile shape (width x height) of the multi-level headline
+HOST_AHEAD_CYCLES = 200_000_000  # GPU spin before a stage-profiled step (about 0.1 s at 2 GHz)
+
 KERNEL_SOURCES = {"k_blend_levels_fwd": "gc_levels.cu", "k_blend_levels_bwd": "gc_levels.cu",
                   "k_blend_fwd": "gc_raster.cu", "k_emit": "gc_raster.cu", "k_radix_scatter": "gc_sort.cu",
                   "k_batch_blend_fwd": "gc_batch.cu", "k_batch_blend_bwd": "gc_batch.cu",
@@ -144,25 +148,43 @@ KERNEL_SOURCES = {"k_blend_levels_fwd": "gc_levels.cu", "k_blend_levels_bwd": "g
                   "k_field_encode": "gc_motion_field.cu"}
 
 
+def _include_closure(path: str) -> list:
+    """`path` and every kernel source (same directory) reached through its #include "..."
+    lines, sorted; the public C-ABI header (declarations) is not followed."""
+    root = os.path.dirname(os.path.normpath(path))
+    seen, todo = set(), [os.path.normpath(path)]
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(f) or os.path.dirname(f) != root:
+            continue
+        seen.add(f)
+        with open(f, encoding="utf-8", errors="replace") as fh:
+            for line in fh:
+                m = re.match(r'\s*#\s*include\s+"([^"]+)"', line)
+                if m:
+                    todo.append(os.path.normpath(os.path.join(os.path.dirname(f), m.group(1))))
+    return sorted(seen)
+
+
 def kernel_source_hash(kernel: str | None = None) -> str:
     """First 16 hex digits of the sha256 over the sources that make up `kernel`: the file that
-    defines it and the shared headers (every csrc file when the kernel is not listed)."""
+    defines it and its include closure (every csrc file when the kernel is not listed)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2509_17513_b300", "csrc")
     own = KERNEL_SOURCES.get(kernel)
-    for name in sorted(os.listdir(d)):
-        if own is not None and not (name.endswith(".cuh") or name == own):
-            continue
-        with open(os.path.join(d, name), "rb") as f:
-            h.update(name.encode() + f.read())
+    files = (_include_closure(os.path.join(d, own)) if own is not None
+             else [os.path.join(d, n) for n in sorted(os.listdir(d))])
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(os.path.relpath(f, ROOT).encode() + fh.read())
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel: str, units_per_launch: int):
+def load_traffic(kernel: str, units_per_launch: int, tile: str | None = None):
     """DRAM bytes of one launch of `kernel` covering `units_per_launch` units (renders, or
     frames of a multi-level pass), from the committed ncu summary profiles/traffic.json
     (bytes per unit of a small capture), or None when the kernel's sources changed since it
-    was taken or the kernel was not captured."""
+    was taken, the capture used another tile shape, or the kernel was not captured."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -171,12 +193,14 @@ def load_traffic(kernel: str, units_per_launch: int):
     e = d.get("kernels", {}).get(kernel)
     if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
+    if e.get("tile") and tile and e["tile"] != tile:  # another template instance
+        return None
     return int(e["dram_bytes_per_unit"] * units_per_launch)
 
 
 # --------------------------------------------------------------------------- GPU arm
 
-def roofline_for(stage, per_launch_ms, work, peaks, peak_kind, batched=False, renders_per_launch=1):
+def roofline_for(stage, per_launch_ms, work, peaks, peak_kind, batched=False, renders_per_launch=1, tile=None):
     """Roofline object of the dominant stage.  `work`: algorithmic FLOPs (ALU stages)
     or bytes (HBM stages) of one launch."""
     pre = "k_batch_" if batched else "k_"
@@ -197,12 +221,12 @@ def roofline_for(stage, per_launch_ms, work, peaks, peak_kind, batched=False, re
                f"x {peaks.get('sm_max_mhz', 2032.0)} MHz max SM clock ({peak_kind} file)")
         return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "frac_of_derived": round(achieved / derived, 4),
-                "traffic": load_traffic(kern, renders_per_launch), "kernel": kern,
+                "traffic": load_traffic(kern, renders_per_launch, tile), "kernel": kern,
                 "launch_ms": round(per_launch_ms, 4), "peak_source": src}
     if stage in hbm:
         achieved = work / (per_launch_ms / 1e3) / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": load_traffic(hbm[stage], renders_per_launch),
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": load_traffic(hbm[stage], renders_per_launch, tile),
                 "kernel": hbm[stage], "launch_ms": round(per_launch_ms, 4),
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     return None
@@ -233,7 +257,10 @@ class Timer:
         self.r, self.stream, self.local, self.world, self.dev = r, stream, local, world, dev
         self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def __call__(self, step, steps, profile=False, name="timed"):
+    def __call__(self, step, steps, profile=False, name="timed", host_ahead=False):
+        """host_ahead: before each step the GPU spins for a bounded time (outside the events),
+        so that the host queues the whole step before the GPU reaches it and the stage events
+        measure the kernels rather than the host's launch rate."""
         import torch
         import torch.distributed as dist
         clocks = ClockSampler(self.local)
@@ -247,6 +274,8 @@ class Timer:
         torch.cuda.nvtx.range_push(name)  # lets a profiler select the kernels of this region
         for _ in range(steps):
             self.flush.fill_(1.0)
+            if host_ahead:
+                torch.cuda._sleep(HOST_AHEAD_CYCLES)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(self.stream)
@@ -350,41 +379,47 @@ def run_gpu(args):
     tune = None
     if "batched" not in skip:
         tune = r.tune_batch(gs, frames, reqs, dL_dimages=dls, depths=(30, 60, 90, n_req), iters=2, outs=outs)
-        depth, tile = tune["best"]["depth"], tuple(tune["best"]["tile"])
+        depth, tile_b = tune["best"]["depth"], tuple(tune["best"]["tile"])
     else:
-        depth, tile = n_req, (8, 32)
-        r.set_options(tile=tile)
-    # algorithmic work of one step at the tuned tile shape (deterministic, outside the timed regions):
+        depth, tile_b = n_req, HEADLINE_TILE
+
+    # algorithmic work of one step at a tile shape (deterministic, outside the timed regions):
     # walked / blended pairs per render, and of the top level alone (what a multi-level pass walks)
-    walked_pairs = blended_pairs = bwd_pairs = keys_total = walked_top = bwd_top = kmax_tuned = 0
-    for q, (cam, f, mask) in enumerate(reqs):
-        r.forward(gs, frames[f], mask, cam, out=outs[q])
-        _, blended, walked, contrib = r.pixel_state(with_walked=True)
-        wq = int(walked.sum(dtype=torch.int64).item())
-        cq = int(contrib.sum(dtype=torch.int64).item())
-        walked_pairs += wq
-        blended_pairs += int(blended.sum(dtype=torch.int64).item())
-        bwd_pairs += cq
-        if mask == scenes.level_mask(6):
-            walked_top += wq
-            bwd_top += cq
-        nk = r.stats()["n_keys"]
-        keys_total += nk
-        kmax_tuned = max(kmax_tuned, nk)
-    keys_mean = keys_total / n_req
-    cap_levels = int(kmax_tuned * 1.05) + 4096  # the multi-level lists are the top level's
-    def roof(prof, steps, batched, eval_pairs, bwd_eval_pairs, renders_per_step):
+    def count_work(tl):
+        r.set_options(tile=tl, key_capacity=0)
+        c = {"walked": 0, "blended": 0, "bwd": 0, "keys": 0, "walked_top": 0, "bwd_top": 0, "kmax": 0}
+        for q, (cam, f, mask) in enumerate(reqs):
+            r.forward(gs, frames[f], mask, cam, out=outs[q])
+            _, blended, walked, contrib = r.pixel_state(with_walked=True)
+            wq = int(walked.sum(dtype=torch.int64).item())
+            cq = int(contrib.sum(dtype=torch.int64).item())
+            c["walked"] += wq
+            c["blended"] += int(blended.sum(dtype=torch.int64).item())
+            c["bwd"] += cq
+            if mask == scenes.level_mask(6):
+                c["walked_top"] += wq
+                c["bwd_top"] += cq
+            nk = r.stats()["n_keys"]
+            c["keys"] += nk
+            c["kmax"] = max(c["kmax"], nk)
+        return c
+
+    work_b = count_work(tile_b)
+    r.set_options(tile=tile_b)
+
+    def roof(prof, steps, batched, eval_pairs, bwd_eval_pairs, renders_per_step, work):
         st_ms, st_calls = prof["stage_ms"], prof["stage_calls"]
         dom = max(st_ms, key=lambda k: st_ms[k])
         launches = max(1, st_calls[dom])
         per_launch = st_ms[dom] / launches
-        fwd_flops = EVAL_FLOPS_PER_PAIR * eval_pairs + FWD_BLEND_FLOPS_PER_PAIR * blended_pairs
-        bwd_flops = EVAL_FLOPS_PER_PAIR * bwd_eval_pairs + BWD_BLEND_FLOPS_PER_PAIR * blended_pairs
-        work = {"blend": fwd_flops * steps / launches, "blend_bwd": bwd_flops * steps / launches,
-                "tile_sort": 2 * SORT_BYTES_PER_KEY_PASS * keys_total * steps / launches,
-                "emit": 8 * keys_total * steps / launches}.get(dom, 0.0)
-        return roofline_for(dom, per_launch, work, peaks, peak_kind, batched=batched,
-                            renders_per_launch=renders_per_step * steps // launches)
+        fwd_flops = EVAL_FLOPS_PER_PAIR * eval_pairs + FWD_BLEND_FLOPS_PER_PAIR * work["blended"]
+        bwd_flops = EVAL_FLOPS_PER_PAIR * bwd_eval_pairs + BWD_BLEND_FLOPS_PER_PAIR * work["blended"]
+        amount = {"blend": fwd_flops * steps / launches, "blend_bwd": bwd_flops * steps / launches,
+                  "tile_sort": 2 * SORT_BYTES_PER_KEY_PASS * work["keys"] * steps / launches,
+                  "emit": 8 * work["keys"] * steps / launches}.get(dom, 0.0)
+        return roofline_for(dom, per_launch, amount, peaks, peak_kind, batched=batched,
+                            renders_per_launch=renders_per_step * steps // launches,
+                            tile=f"{r.options.tile_w}x{r.options.tile_h}")
 
     batched_obj = precision_obj = None
     if "batched" not in skip:
@@ -444,10 +479,11 @@ def run_gpu(args):
                                "(autotuned tile shape and batch depth)",
                        "fwd": mpix(bf_ms, args.steps), "fwd_bwd": mpix(bfb_ms, args.steps), "unit": UNIT,
                        "ms_per_step": {"fwd": round(bf_ms / args.steps, 3), "fwd_bwd": round(bfb_ms / args.steps, 3)},
-                       "tile": f"{tile[0]}x{tile[1]}", "batch_depth": depth, "key_capacity_per_batch": cap,
+                       "tile": f"{tile_b[0]}x{tile_b[1]}", "batch_depth": depth, "key_capacity_per_batch": cap,
                        "clocks": {"fwd": clk_bf, "fwd_bwd": clk_bfb},
-                       "roofline": {"fwd": roof(ef_prof, e_steps, True, walked_pairs, bwd_pairs, n_req),
-                                    "fwd_bwd": roof(efb_prof, e_steps, True, walked_pairs, bwd_pairs, n_req)},
+                       "roofline": {"fwd": roof(ef_prof, e_steps, True, work_b["walked"], work_b["bwd"], n_req, work_b),
+                                    "fwd_bwd": roof(efb_prof, e_steps, True, work_b["walked"], work_b["bwd"], n_req,
+                                                    work_b)},
                        "stage_ms_per_call": stage_summary(efb_prof)[0],
                        "stage_share_fwd": stage_summary(ef_prof)[1],
                        "stage_share_fwd_bwd": stage_summary(efb_prof)[1],
@@ -461,6 +497,12 @@ def run_gpu(args):
 
     # ---- headline: single-pass multi-level form, per frame levels 1..6 from one list (the
     # same 180 images, bit for bit), fixed key capacity, per-stage CUDA events
+    # the headline and the forms after it use 8x32 tiles, the shape the multi-level blend kernels
+    # are profiled with; on this workload the batched autotuner finds 16x16 and 8x32 within a
+    # fraction of a percent of each other
+    tile = HEADLINE_TILE
+    work = work_b if tuple(tile) == tuple(tile_b) else count_work(tile)
+    cap_levels = int(work["kmax"] * 1.05) + 4096  # the multi-level lists are the top level's
     r.set_options(key_capacity=cap_levels, tile=tile)
     lsaved = gc.Saved(r)
     lgrads = None
@@ -479,8 +521,11 @@ def run_gpu(args):
         levels_fwd()
         levels_fwd_bwd()
     r.check()
-    ef_lv_ms, fwd_prof, clk_e = timer(levels_fwd, args.steps, profile=True, name="levels_fwd")
-    efb_lv_ms, fb_prof, clk_efb = timer(levels_fwd_bwd, args.steps, profile=True, name="levels_fwd_bwd")
+    ef_lv_ms, efwd_prof, clk_e = timer(levels_fwd, args.steps, name="levels_fwd")
+    efb_lv_ms, efb_lv_prof, clk_efb = timer(levels_fwd_bwd, args.steps, name="levels_fwd_bwd")
+    # per-stage CUDA events with the host queued ahead of the GPU: kernel times, not launch gaps
+    _, fwd_prof, _ = timer(levels_fwd, args.steps, profile=True, name="levels_fwd_stages", host_ahead=True)
+    _, fb_prof, _ = timer(levels_fwd_bwd, args.steps, profile=True, name="levels_fwd_bwd_stages", host_ahead=True)
     r.check()
     # the headline value: the same steps replayed from one CUDA graph each (gc_levels_graph:
     # no host work, no launch gaps between the kernels of a frame, identical images); the
@@ -702,12 +747,13 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}"},
             "fps": round(n_req * args.steps * world / (fwd_ms / 1e3), 1),
             "gpu_launches": gfwd_prof["kernel_launches"],
-            "roofline": roof(fwd_prof, args.steps, False, walked_top, bwd_top, frames_per_step),
+            "roofline": roof(fwd_prof, args.steps, False, work["walked_top"], work["bwd_top"], frames_per_step, work),
             "clocks": clk,
-            "eager": {"note": "the same steps as eager calls (one library call per frame, per-stage CUDA "
-                              "events on); their events give stage_profile and the roofline launch times",
+            "eager": {"note": "the same steps as eager calls (one library call per frame); stage_profile and "
+                              "the roofline launch times come from per-stage CUDA events of further eager "
+                              "steps, each queued whole by the host before the GPU starts it",
                       "fwd": mpix(ef_lv_ms, args.steps), "fwd_bwd": mpix(efb_lv_ms, args.steps), "unit": UNIT,
-                      "gpu_launches": {"fwd": fwd_prof["kernel_launches"], "fwd_bwd": fb_prof["kernel_launches"]},
+                      "gpu_launches": {"fwd": efwd_prof["kernel_launches"], "fwd_bwd": efb_lv_prof["kernel_launches"]},
                       "graph_kernel_nodes": graph_nodes, "clocks": {"fwd": clk_e, "fwd_bwd": clk_efb}},
             "fwd_bwd": {"metric": "Mpixel/s at 1920x1080, forward + backward (upstream dL/dimage given), "
                                   "gradients summed over the step's renders",
@@ -715,7 +761,8 @@ def run_gpu(args):
                         "ms_per_step": round(fb_ms / args.steps, 3),
                         "fps": round(n_req * args.steps * world / (fb_ms / 1e3), 1),
                         "gpu_launches": gfb_prof["kernel_launches"],
-                        "roofline": roof(fb_prof, args.steps, False, walked_top, bwd_top, frames_per_step),
+                        "roofline": roof(fb_prof, args.steps, False, work["walked_top"], work["bwd_top"],
+                                         frames_per_step, work),
                         "clocks": clk_fb},
             "stage_profile": {"note": "ms per call of the headline path (one frame, six levels)",
                               "stage_ms_per_call_fwd_bwd": stage_summary(fb_prof)[0],
@@ -729,9 +776,10 @@ def run_gpu(args):
             "single_view": single_view,
             "reduced_precision": precision_obj,
             "autotune": tune,
-            "work_per_step": {"blend_walked_pairs": walked_pairs, "blended_pairs": blended_pairs,
-                              "blend_bwd_walked_pairs": bwd_pairs, "top_level_walked_pairs": walked_top,
-                              "top_level_bwd_walked_pairs": bwd_top, "keys_per_render": round(keys_mean),
+            "work_per_step": {"blend_walked_pairs": work["walked"], "blended_pairs": work["blended"],
+                              "blend_bwd_walked_pairs": work["bwd"], "top_level_walked_pairs": work["walked_top"],
+                              "top_level_bwd_walked_pairs": work["bwd_top"],
+                              "keys_per_render": round(work["keys"] / n_req),
                               "flops_per_pair": {"evaluate": EVAL_FLOPS_PER_PAIR,
                                                  "blend_fwd": FWD_BLEND_FLOPS_PER_PAIR,
                                                  "blend_bwd": BWD_BLEND_FLOPS_PER_PAIR}}}
