@@ -290,11 +290,13 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
 }
 
 // Fixed key capacity: the largest count that any forward on this state needed since the last
-// check (word 2, kept by the emit kernel) against the capacity; the record is then cleared.
-gc_status capacity_check(gc_context *ctx, const gc_saved &S) {
+// check (word 2, kept by the emit kernel) against the capacity; the record is then cleared on
+// `stream`, ordered before the stream's next forwards.
+gc_status capacity_check(gc_context *ctx, const gc_saved &S, cudaStream_t stream) {
     uint32_t w[3];
-    GC_CUDA(ctx, cudaMemcpy(w, S.words.p, 12, cudaMemcpyDeviceToHost));
-    GC_CUDA(ctx, cudaMemset(static_cast<uint32_t *>(S.words.p) + 2, 0, 4));
+    GC_CUDA(ctx, cudaMemcpyAsync(w, S.words.p, 12, cudaMemcpyDeviceToHost, stream));
+    GC_CUDA(ctx, cudaStreamSynchronize(stream));
+    GC_CUDA(ctx, cudaMemsetAsync(static_cast<uint32_t *>(S.words.p) + 2, 0, 4, stream));
     const uint32_t need = std::max(w[0], w[2]);
     if ((int64_t)need > S.K)
         return fail(ctx, GC_ERR_CAPACITY, "a frame needs %u keys, capacity %lld", need, (long long)S.K);
@@ -427,14 +429,15 @@ gc_status gc_check(gc_context *ctx, void *stream) {
     const gc_saved &S = *ctx->last;
     if (S.words.p) {
         uint32_t w[2];
-        GC_CUDA(ctx, cudaMemcpy(w, S.words.p, 8, cudaMemcpyDeviceToHost));
+        GC_CUDA(ctx, cudaMemcpyAsync(w, S.words.p, 8, cudaMemcpyDeviceToHost, s));
+        GC_CUDA(ctx, cudaStreamSynchronize(s));
         if (w[1]) {
-            GC_CUDA(ctx, cudaMemset(static_cast<uint32_t *>(S.words.p) + 1, 0, 4));
+            GC_CUDA(ctx, cudaMemsetAsync(static_cast<uint32_t *>(S.words.p) + 1, 0, 4, s));
             return fail(ctx, GC_ERR_TIMEOUT, "a bounded device wait ran out (error word %#x)", w[1]);
         }
     }
-    if (S.batch && S.batch.get() && !S.valid) return batch_check(ctx, S);
-    if (S.valid && !S.k_exact && S.n_sel > 0) return capacity_check(ctx, S);
+    if (S.batch && S.batch.get() && !S.valid) return batch_check(ctx, S, s);
+    if (S.valid && !S.k_exact && S.n_sel > 0) return capacity_check(ctx, S, s);
     return GC_OK;
 }
 

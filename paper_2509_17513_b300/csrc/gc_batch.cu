@@ -602,13 +602,14 @@ void batch_invalidate(gc_saved &S) {
     if (S.batch) S.batch->valid = false;
 }
 
-gc_status batch_check(gc_context *ctx, const gc_saved &S) {
+gc_status batch_check(gc_context *ctx, const gc_saved &S, cudaStream_t stream) {
     if (!S.batch || !S.batch->valid || !S.batch->words.p) return GC_OK;
     const BatchState &B = *S.batch;
     uint32_t w[3];
-    GC_CUDA(ctx, cudaMemcpy(w, B.words.p, 12, cudaMemcpyDeviceToHost));
+    GC_CUDA(ctx, cudaMemcpyAsync(w, B.words.p, 12, cudaMemcpyDeviceToHost, stream));
+    GC_CUDA(ctx, cudaStreamSynchronize(stream));
     if (w[1]) {
-        GC_CUDA(ctx, cudaMemset(static_cast<uint32_t *>(B.words.p) + 1, 0, 4));
+        GC_CUDA(ctx, cudaMemsetAsync(static_cast<uint32_t *>(B.words.p) + 1, 0, 4, stream));
         return fail(ctx, GC_ERR_TIMEOUT, "a bounded device wait ran out (error word %#x)", w[1]);
     }
     if (!B.k_exact && (int64_t)w[2] > B.K_cap)
@@ -1086,7 +1087,7 @@ extern "C" gc_status gc_batch_graph_create(gc_context *ctx, const gc_gaussians *
     if ((st = graph_pass(G, g, frames, n_frames, reqs, dL_dimages, grads, s)) != GC_OK) return bail(st);
     if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctx, GC_ERR_CUDA, "eager pass failed"));
     for (gc_saved *x : G->states)
-        if ((st = batch_check(ctx, *x)) != GC_OK) return bail(st);
+        if ((st = batch_check(ctx, *x, s)) != GC_OK) return bail(st);
     // 3. capture the same pass
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
@@ -1140,7 +1141,7 @@ extern "C" gc_status gc_batch_graph_check(gc_batch_graph *G, void *stream) {
     DeviceGuard dg(G->ctx->device);
     GC_CUDA(G->ctx, cudaStreamSynchronize((cudaStream_t)stream));
     for (gc_saved *x : G->states) {
-        const gc_status st = batch_check(G->ctx, *x);
+        const gc_status st = batch_check(G->ctx, *x, (cudaStream_t)stream);
         if (st != GC_OK) return st;
     }
     return GC_OK;

@@ -114,7 +114,7 @@ extern "C" gc_status gc_levels_graph_create(gc_context *ctx, const gc_gaussians 
     // 2. eager pass at the fixed capacity: sizes every buffer
     if ((st = levels_pass(G, P, s, nullptr)) != GC_OK) return bail(st);
     if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctx, GC_ERR_CUDA, "eager pass failed"));
-    if ((st = capacity_check(ctx, *G->state)) != GC_OK) return bail(st);
+    if ((st = capacity_check(ctx, *G->state, s)) != GC_OK) return bail(st);
     // 3. capture the same pass
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
@@ -166,15 +166,16 @@ extern "C" gc_status gc_levels_graph_check(gc_levels_graph *G, void *stream) {
     if (!G) return GC_ERR_INVALID_ARG;
     gc_context *ctx = G->ctx;
     DeviceGuard dg(ctx->device);
-    GC_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
     const gc_saved &S = *G->state;
     uint32_t err = 0;
-    GC_CUDA(ctx, cudaMemcpy(&err, static_cast<uint32_t *>(S.words.p) + 1, 4, cudaMemcpyDeviceToHost));
+    GC_CUDA(ctx, cudaMemcpyAsync(&err, static_cast<uint32_t *>(S.words.p) + 1, 4, cudaMemcpyDeviceToHost, s));
+    GC_CUDA(ctx, cudaStreamSynchronize(s));
     if (err) {
-        GC_CUDA(ctx, cudaMemset(static_cast<uint32_t *>(S.words.p) + 1, 0, 4));
+        GC_CUDA(ctx, cudaMemsetAsync(static_cast<uint32_t *>(S.words.p) + 1, 0, 4, s));
         return fail(ctx, GC_ERR_TIMEOUT, "a bounded device wait ran out (error word %#x)", err);
     }
-    return capacity_check(ctx, S);
+    return capacity_check(ctx, S, s);
 }
 
 extern "C" gc_status gc_levels_graph_destroy(gc_levels_graph *G) {

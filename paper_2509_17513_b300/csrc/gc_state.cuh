@@ -16,7 +16,7 @@
 
 struct BatchState;  // gc_batch.cu
 struct gc_saved;
-gc_status batch_check(gc_context *ctx, const gc_saved &S);  // gc_batch.cu: errors of a batched forward
+gc_status batch_check(gc_context *ctx, const gc_saved &S, cudaStream_t stream);  // gc_batch.cu: errors of a batched forward (synchronises stream)
 void batch_invalidate(gc_saved &S);                        // gc_batch.cu: a single-frame forward replaced it
 
 struct DevBuf {
@@ -129,8 +129,8 @@ inline gc_status fail(gc_context *ctx, gc_status s, const char *fmt, ...) {
 
 // Records a stage boundary on the stream when profiling is on.
 // GC_ERR_CAPACITY if a forward on S since the last check needed more keys than its fixed
-// capacity (synchronous; S must have a fixed capacity).
-gc_status capacity_check(gc_context *ctx, const gc_saved &S);
+// capacity (synchronises `stream`, the stream of those forwards; S must have a fixed capacity).
+gc_status capacity_check(gc_context *ctx, const gc_saved &S, cudaStream_t stream);
 
 inline cudaError_t prof_mark(gc_context *ctx, cudaStream_t s, int stage) {
     if (!ctx->prof_on) return cudaSuccess;
