@@ -127,3 +127,19 @@ def test_kde_rate_grad_of_noisy_attribute_planes(gc):
         assert abs(rate[c] - kr.rate_continuous(yc)) <= 2e-5 * max(kr.rate_continuous(yc), 1.0)
         want = kr.rate_continuous_grad(yc)
         assert np.abs(dy[c] - want).max() <= 1e-4 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n", [1, 2, 2049])
+def test_kde_rate_grad_edge_lengths(gc, n):
+    """One value (h = 1), two values, and one value past a chunk of 2048."""
+    rng = np.random.default_rng(100 + n)
+    y = (np.rint(rng.normal(3.0, 4.0, (2, n))) + rng.uniform(-0.5, 0.5, (2, n))).astype(np.float32)
+    r = gc.Renderer(0)
+    rate, dy = r.kde_rate_grad(torch.from_numpy(y).cuda())
+    rate, dy = rate.cpu().numpy().astype(np.float64), dy.cpu().numpy().astype(np.float64)
+    for c in range(2):
+        yc = y[c].astype(np.float64)
+        want_r = kr.rate_continuous(yc)
+        assert abs(rate[c] - want_r) <= 2e-5 * max(abs(want_r), 1.0), (n, c, rate[c], want_r)
+        want_g = kr.rate_continuous_grad(yc)
+        assert np.abs(dy[c] - want_g).max() <= 1e-4 * max(np.abs(want_g).max(), 1e-30), (n, c)
