@@ -367,10 +367,25 @@ def run_gpu(args):
         s_steps = max(1, min(args.steps, 3))
         sf_ms, sf_prof, _ = timer(single_fwd, s_steps, profile=True, name="single_fwd")
         sfb_ms, sfb_prof, _ = timer(single_fwd_bwd, s_steps, profile=True, name="single_fwd_bwd")
+        # per level: the frames of the step rendered at that level alone (forward), FPS and Mpixel/s
+        per_level = {}
+        for lv in range(1, 7):
+            lv_reqs = [(cam, f, mask) for (cam, f, mask) in reqs if mask == scenes.level_mask(lv)]
+
+            def level_fwd(lv_reqs=lv_reqs):
+                for q, (cam, f, mask) in enumerate(lv_reqs):
+                    r.forward(gs, frames[f], mask, cam, out=outs[q])
+
+            lv_ms, _, _ = timer(level_fwd, s_steps, name=f"single_level_{lv}")
+            n_lv = len(lv_reqs) * s_steps
+            per_level[f"L{lv}"] = {"fps": round(n_lv * world / (lv_ms / 1e3), 1),
+                                   "mpix_s": round(n_lv * W * H * world / (lv_ms / 1e3) / 1e6, 1),
+                                   "ms_per_render": round(lv_ms / n_lv, 4)}
         r.check()
         single_view = {"form": "plain FP32, one gc_render_forward (+ gc_render_backward) per request",
                        "fwd": mpix(sf_ms, s_steps), "fwd_bwd": mpix(sfb_ms, s_steps), "unit": UNIT,
                        "ms_per_step": {"fwd": round(sf_ms / s_steps, 2), "fwd_bwd": round(sfb_ms / s_steps, 2)},
+                       "per_level_fwd": per_level,
                        "stage_ms_per_render": stage_summary(sfb_prof)[0], "steps": s_steps}
         del saved, grads1
         r.set_options(key_capacity=0)
