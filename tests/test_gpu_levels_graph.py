@@ -135,3 +135,33 @@ def test_graph_argument_errors(gc, small):
         gc.LevelsGraph(r, gs, [frames[0], None, frames[2]], cams, 6)
     with pytest.raises(gc.GCError):
         gc.LevelsGraph(r, gs, frames, cams, 0)
+
+
+def test_graph_shared_gradient_set_and_static_scene(gc, small):
+    """One gradient set named by every frame holds the last frame's gradients; a step without
+    motion tables (static scene) replays like its eager calls."""
+    r, gs, frames, cams = _setup(gc, small, tile=(16, 16))
+    L = 3
+    gen = torch.Generator(device="cuda").manual_seed(19)
+    dls = [torch.randn((3, c.height, c.width), generator=gen, device="cuda") for c in cams for _ in range(L)]
+    saved = gc.Saved(r)
+    r.levels_forward(gs, frames[2], L, cams[2], saved)
+    want = {k: v.clone() for k, v in r.levels_backward(saved, gs, frames[2], dls[2 * L:3 * L]).items()}
+    shared = r._single_grads(gs, frames[0])
+    g = gc.LevelsGraph(r, gs, frames, cams, L, dL_dimages=dls, grads=[shared] * 3)
+    g.launch()
+    g.check()
+    torch.cuda.synchronize()
+    for k in NAMES:
+        rel = float((shared[k] - want[k]).norm() / max(float(want[k].norm()), 1e-30))
+        assert rel <= 1e-6, (k, rel)
+    g.close()
+    static = [None, None, None]
+    eager = [img.clone() for f in range(3) for img in r.levels_forward(gs, None, L, cams[f])]
+    gs_static = gc.LevelsGraph(r, gs, static, cams, L)
+    gs_static.launch()
+    gs_static.check()
+    torch.cuda.synchronize()
+    for a, b in zip(eager, gs_static.outs):
+        assert torch.equal(a, b)
+    gs_static.close()
