@@ -469,8 +469,9 @@ GC_API gc_status gc_kde_rate(gc_context *ctx, const float *y, int32_t n_channels
  * For integer inputs R_c equals gc_kde_rate.  d_rate: device array of n_channels upstream
  * gradients dL/dR_c, or NULL for ones.  Writes rate[c] (device) and, when d_y is not NULL,
  * d_y[c * stride + i] = dL/dR_c * dR_c/dy~_i (device, the layout of y).  Unsupported channels
- * (as in gc_kde_rate) get NaN in rate and in their d_y row.  Symbols farther than 12 h + 1
- * from a value are left out of its sums (their share is below 1e-32). */
+ * (as in gc_kde_rate) get NaN in rate and in their d_y row.  Symbols farther than 8 h + 1
+ * from a value are left out of its sums: their mass is below Phi(-8) = 6e-16 of their count,
+ * while P of a value is at least about 1 / (n h) from its own symbol (relative error < 1e-9). */
 GC_API gc_status gc_kde_rate_grad(gc_context *ctx, const float *y, int32_t n_channels, int64_t n,
                                   int64_t stride, const float *d_rate, float *rate, float *d_y, void *stream);
 
