@@ -270,24 +270,29 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
                         if (blended) {
                             contrib = true;
                             const float4 col = sm.c[s];
-                            float dp = 0.f;
+                            // sums over the levels that blended the entry; the per-entry factors
+                            // alpha and G multiply them once
+                            float s0 = 0.f, s1 = 0.f, s2 = 0.f, sal = 0.f;
 #pragma unroll
                             for (int l = 0; l < NL; ++l) {
                                 if (!((lm >> l) & 1u)) continue;
                                 T[l] = __fdividef(T[l], 1.f - alpha);
-                                const float w = alpha * T[l];
-                                v[6] += w * g0[l];
-                                v[7] += w * g1[l];
-                                v[8] += w * g2[l];
-                                const float dal = T[l] * (g0[l] * (col.x - A0[l]) + g1[l] * (col.y - A1[l]) +
-                                                          g2[l] * (col.z - A2[l]));
-                                A0[l] = fmaf(alpha, col.x - A0[l], A0[l]);
-                                A1[l] = fmaf(alpha, col.y - A1[l], A1[l]);
-                                A2[l] = fmaf(alpha, col.z - A2[l], A2[l]);
-                                if (!(a0 > kAlphaMax)) {
-                                    v[5] += G * dal;
-                                    dp += alpha * dal;  // dL/dpower (natural exponent), summed over levels
-                                }
+                                s0 = fmaf(T[l], g0[l], s0);
+                                s1 = fmaf(T[l], g1[l], s1);
+                                s2 = fmaf(T[l], g2[l], s2);
+                                const float d0 = col.x - A0[l], d1 = col.y - A1[l], d2 = col.z - A2[l];
+                                sal = fmaf(T[l], fmaf(g0[l], d0, fmaf(g1[l], d1, g2[l] * d2)), sal);
+                                A0[l] = fmaf(alpha, d0, A0[l]);
+                                A1[l] = fmaf(alpha, d1, A1[l]);
+                                A2[l] = fmaf(alpha, d2, A2[l]);
+                            }
+                            v[6] = alpha * s0;
+                            v[7] = alpha * s1;
+                            v[8] = alpha * s2;
+                            float dp = 0.f;  // dL/dpower (natural exponent), summed over levels
+                            if (!(a0 > kAlphaMax)) {
+                                v[5] = G * sal;
+                                dp = alpha * sal;
                             }
                             const float2 nd = sm.d[s];
                             v[0] = (col.w * dx + nd.x * dy) * dp;
