@@ -273,10 +273,11 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
                             // sums over the levels that blended the entry; the per-entry factors
                             // alpha and G multiply them once
                             float s0 = 0.f, s1 = 0.f, s2 = 0.f, sal = 0.f;
+                            const float inv_oma = __fdividef(1.f, 1.f - alpha);
 #pragma unroll
                             for (int l = 0; l < NL; ++l) {
                                 if (!((lm >> l) & 1u)) continue;
-                                T[l] = __fdividef(T[l], 1.f - alpha);
+                                T[l] = T[l] * inv_oma;
                                 s0 = fmaf(T[l], g0[l], s0);
                                 s1 = fmaf(T[l], g1[l], s1);
                                 s2 = fmaf(T[l], g2[l], s2);
