@@ -197,6 +197,10 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, my_last);
     if (lane == 0) atomicMax(&sm.last_max, wmax);
     const uint32_t wpix = __ballot_sync(0xffffffffu, my_last != 0u);  // pixels of the warp with work
+    // levels whose last blended position lies beyond the current entry: entries are visited in
+    // decreasing position, so the set only grows; it is refreshed when the position drops below
+    // the largest last position of a level not yet in it (at most once per level)
+    uint32_t alive = 0u, next_last = my_last;
     __syncthreads();
     const int n_active = (int)sm.last_max;
     for (int hi = n_active; hi > 0; hi -= 256) {
@@ -251,10 +255,17 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
                     for (int c = 0; c < 9; ++c) v[c] = 0.f;
                     bool contrib = false;
                     const uint32_t wm = sm.m[warp * 256 + s];
-                    uint32_t lm = 0u;  // levels of this pixel that blended entry k
+                    if ((uint32_t)k < next_last) {
+                        alive = 0u;
+                        next_last = 0u;
 #pragma unroll
-                    for (int l = 0; l < NL; ++l)
-                        if (l >= (int)sm.lay[s] && (uint32_t)k < last[l]) lm |= 1u << l;
+                        for (int l = 0; l < NL; ++l) {
+                            if ((uint32_t)k < last[l]) alive |= 1u << l;
+                            else next_last = max(next_last, last[l]);
+                        }
+                    }
+                    // levels of this pixel that blended entry k: alive ones at or above its layer
+                    const uint32_t lm = alive & (0xffffffffu << sm.lay[s]);
                     if ((wm & bit) != 0u && lm) {
                         const float4 a = sm.a[s];
                         const float2 bb = sm.b[s];
