@@ -253,7 +253,6 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
                     float v[9];
 #pragma unroll
                     for (int c = 0; c < 9; ++c) v[c] = 0.f;
-                    bool contrib = false;
                     const uint32_t wm = sm.m[warp * 256 + s];
                     if ((uint32_t)k < next_last) {
                         alive = 0u;
@@ -279,7 +278,6 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
                             blended = !(alpha < kAlphaMin);
                         }
                         if (blended) {
-                            contrib = true;
                             const float4 col = sm.c[s];
                             // sums over the levels that blended the entry; the per-entry factors
                             // alpha and G multiply them once
@@ -314,8 +312,10 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
                             v[4] = -0.5f * dy * dy * dp;
                         }
                     }
+                    // the entry passed the warp's relevance ballot: some pixel nearly always
+                    // blended it, so the reduction runs without a vote
                     float out0 = 0.f, out8 = 0.f;
-                    if (__any_sync(0xffffffffu, contrib)) {
+                    {
                         {
                             const bool up = lane & 16;
 #pragma unroll
