@@ -236,24 +236,27 @@ GC_API gc_status gc_render_forward(gc_context *ctx, const gc_gaussians *g, const
  * Forward render that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they
  * render - a playback thread with a hard per-frame deadline (an allocation can
- * block or fail with out-of-memory mid-stream), code capturing its stream into
- * a CUDA graph (cudaMalloc is not allowed during the capture), and plugins
- * running in another application's CUDA context under a fixed memory budget
- * that cannot hold a gc_context.
+ * block or fail with out-of-memory mid-stream), and plugins running in another
+ * application's CUDA context under a fixed memory budget that cannot hold a
+ * gc_context.
  *
- * Same result as gc_render_forward with the same options (opt may be NULL for
- * the defaults; key_capacity is ignored), no saved state.  All scratch lives in
+ * Same image as gc_render_forward with the same options, bit for bit (opt may
+ * be NULL for exactly the gc_default_options values; key_capacity is ignored),
+ * no saved state.  All scratch lives in
  * one static device array of about 22.5 MiB inside the library, which every GPU
  * that loads the library holds until the process exits.  Limits: at most
  * 32,768 selected Gaussians, 1,048,576 (tile, Gaussian) pairs, 262,144 pixels
  * and 4,096 tiles; larger requests return GC_ERR_CAPACITY with a message in
  * err (a caller buffer of err_len bytes, may be NULL) and write nothing.
- * The first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.  Each call synchronises `stream` once (to read
- * the pair count into a stack variable).  Calls share the array: calls whose
- * work overlaps on the GPU (other streams, other threads) race and corrupt
- * each other's images; serialise them on one stream.
+ * The pair limit is checked after the depth sort and scan have run on the
+ * GPU; the image is still left untouched.  The first call on each device
+ * looks up the array's device address with cudaGetSymbolAddress (with that
+ * device current).  Each call synchronises `stream`: once to read the pair
+ * count and the error word into stack variables, and, when the frame has any
+ * pairs, once more after the blend, so the call returns with the image
+ * complete.  GC_ERR_TIMEOUT if a bounded wait of either sort ran out.  Calls
+ * share the array: calls whose work overlaps on the GPU (other streams, other
+ * threads) race and corrupt each other's images; serialise them on one stream.
  */
 GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, const gc_gaussians *g,
                                            const gc_motion *motion, uint32_t layer_mask,

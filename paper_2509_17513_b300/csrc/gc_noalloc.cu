@@ -3,12 +3,11 @@
 //
 // Who needs it: callers that cannot allocate device memory at render time.  A
 // decode-and-render playback thread with a hard per-frame deadline must not block
-// in the allocator or fail with out-of-memory halfway through a stream; code that
-// is capturing its stream into a CUDA graph may not call cudaMalloc during the
-// capture; and host applications or plugins that run inside someone else's CUDA
-// context under a fixed memory budget may neither create a gc_context (which owns
-// grow-only scratch) nor allocate after start-up.  This entry point serves them
-// with a fixed, stated maximum problem size.
+// in the allocator or fail with out-of-memory halfway through a stream; and host
+// applications or plugins that run inside someone else's CUDA context under a
+// fixed memory budget may neither create a gc_context (which owns grow-only
+// scratch) nor allocate after start-up.  This entry point serves them with a
+// fixed, stated maximum problem size.
 //
 // The scratch is g_noalloc_scratch below (kScratchBytes, about 22.5 MiB).  Every GPU
 // that loads this module holds it until the process exits.  In host code the
@@ -127,12 +126,8 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
                                                       void *stream, char *err, size_t err_len) {
     if (err && err_len) err[0] = '\0';
     gc_options o;
-    if (opt) {
-        o = *opt;
-    } else {
-        memset(&o, 0, sizeof o);
-        o.tile_w = 16; o.tile_h = 16; o.near_plane = 0.2f; o.dilation = 0.3f; o.frustum_clamp = 1.3f;
-    }
+    if (opt) o = *opt;
+    else gc_default_options(&o);  // exactly the library defaults (alpha footprint on)
     const bool shape_ok = (o.tile_w == 16 && o.tile_h == 16) || (o.tile_w == 8 && o.tile_h == 32) ||
                           (o.tile_w == 32 && o.tile_h == 8);
     if (!shape_ok || !(o.near_plane > 0.f) || !(o.dilation >= 0.f) || !(o.frustum_clamp > 0.f) ||
@@ -261,10 +256,12 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
         NA_CUDA(gc::radix_sort_pairs(dk, dv, n_sel, nullptr, 32, sort_scratch, &depth_buf, s, words + 1));
         NA_CUDA(gc::launch_rank_gather(dv[depth_buf], rec, touched, n_sel, ranked, touched_r, s));
         NA_CUDA(gc::launch_exclusive_scan(touched_r, offsets, n_sel, words, sort_scratch, s));
-        uint32_t k_host = 0;  // stack variable: no host allocation
-        NA_CUDA(cudaMemcpyAsync(&k_host, words, 4, cudaMemcpyDeviceToHost, s));
+        uint32_t w_host[2] = {0u, 0u};  // pair count and error word; stack: no host allocation
+        NA_CUDA(cudaMemcpyAsync(w_host, words, 8, cudaMemcpyDeviceToHost, s));
         NA_CUDA(cudaStreamSynchronize(s));
-        K = k_host;
+        if (w_host[1] != 0u)
+            return say(err, err_len, GC_ERR_TIMEOUT, "a bounded wait of the depth sort ran out");
+        K = w_host[0];
         if (K > kMaxKeys)
             return say(err, err_len, GC_ERR_CAPACITY,
                        "the frame needs %lld (tile, Gaussian) pairs; the no-allocation maximum is %lld",
@@ -278,5 +275,13 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
     }
     NA_CUDA(gc::launch_blend_fwd(ranges, K > 0 ? tv[tile_buf] : nullptr, ranked, cp, rp, image,
                                  final_T, n_contrib, nullptr, nullptr, s));
+    if (K > 0) {
+        // the tile sort's bounded waits report through the same error word
+        uint32_t e_host = 0u;
+        NA_CUDA(cudaMemcpyAsync(&e_host, words + 1, 4, cudaMemcpyDeviceToHost, s));
+        NA_CUDA(cudaStreamSynchronize(s));
+        if (e_host != 0u)
+            return say(err, err_len, GC_ERR_TIMEOUT, "a bounded wait of the tile sort ran out");
+    }
     return GC_OK;
 }
