@@ -500,6 +500,20 @@ GC_API gc_status gc_saved_pixel_state(gc_context *ctx, const gc_saved *saved, fl
                                       int32_t *n_blended, int32_t *n_walked, int32_t *n_contrib,
                                       void *stream);
 
+/*
+ * L1 photometric distortion of a rendered image against a target (the distortion term of
+ * the rate-distortion training loss, Sec. 3.3, in its plain L1 form):
+ *   loss = scale * sum_i |image_i - target_i|,  dL_dimage_i = scale * sign(image_i - target_i),
+ * sign(0) = 0; scale = 1 / n gives the mean.  image, target, dL_dimage: device, n floats
+ * each (any layout, the same for all three); loss: device, one float.  Either output may be
+ * NULL (both NULL: nothing runs).  The sum is deterministic (one FP64 partial per CTA of a
+ * fixed grid, added in CTA order).  The first call grows a small context-owned buffer of
+ * partial sums; later calls allocate nothing, so a training step that calls it can be
+ * captured into a graph after one eager step.
+ */
+GC_API gc_status gc_l1_loss(gc_context *ctx, const float *image, const float *target, int64_t n, float scale,
+                            float *dL_dimage, float *loss, void *stream);
+
 /* Stages timed by the profiler (CUDA events recorded on the call's stream
  * between stages). */
 enum {
@@ -517,7 +531,10 @@ enum {
     GC_N_STAGES = 11
 };
 
-/* Enables (1) or disables (0) per-stage event timing on this context. */
+/* Per-stage event timing on this context: 0 off, 1 on, 2 on with L2 flushed before
+ * every stage (a 256 MB context-owned buffer is written between the event that closes
+ * one stage and the event that opens the next, so each stage reads its inputs from
+ * HBM and its time excludes the flush). */
 GC_API gc_status gc_profile_enable(gc_context *ctx, int enable);
 
 /* Reads and resets the profile: per stage the summed milliseconds and the

@@ -113,6 +113,7 @@ SIGNATURES = {
     "gc_motion_field_backward": (C.c_int, [P, P, P, C.c_int64, P, P, P, P]),
     "gc_kde_rate": (C.c_int, [P, P, C.c_int32, C.c_int64, C.c_int64, P, P]),
     "gc_kde_rate_grad": (C.c_int, [P, P, C.c_int32, C.c_int64, C.c_int64, P, P, P, P]),
+    "gc_l1_loss": (C.c_int, [P, P, P, C.c_int64, C.c_float, P, P, P]),
     "gc_render_batch_forward": (C.c_int, [P, P, P, C.c_int32, P, C.c_int32, P, P]),
     "gc_render_batch_backward": (C.c_int, [P, P, P, P, C.c_int32, P, C.c_int32, P, P]),
     "gc_batch_graph_create": (C.c_int, [P, P, P, C.c_int32, P, C.c_int32, C.c_int32, P, P, P, P]),

@@ -94,7 +94,8 @@ gc_status gc_destroy(gc_context *ctx) {
         saved_release(ctx, &ctx->internal);
         ctx->internal.batch.reset();
         DevBuf *bufs[] = {&ctx->scratch, &ctx->bwd_part, &ctx->bwd_g2d, &ctx->bwd_motion,
-                          &ctx->bwd_group, &ctx->field_part, &ctx->field_h, &ctx->kde_scratch};
+                          &ctx->bwd_group, &ctx->field_part, &ctx->field_h, &ctx->kde_scratch,
+                          &ctx->prof_flush, &ctx->loss_part};
         for (DevBuf *b : bufs) release(*b);
         if (ctx->host_word) cudaFreeHost(ctx->host_word);
         for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
@@ -392,7 +393,13 @@ gc_status gc_saved_pixel_state(gc_context *ctx, const gc_saved *saved, float *fi
 
 gc_status gc_profile_enable(gc_context *ctx, int enable) {
     if (!ctx) return GC_ERR_INVALID_ARG;
+    if (enable < 0 || enable > 2) return fail(ctx, GC_ERR_INVALID_ARG, "profile mode must be 0, 1 or 2");
+    if (enable == 2) {
+        DeviceGuard dg(ctx->device);
+        GC_CUDA(ctx, grow(ctx->prof_flush, (size_t)256 << 20));  // twice the 126 MB L2
+    }
     ctx->prof_on = enable != 0;
+    ctx->prof_flush_on = enable == 2;
     return GC_OK;
 }
 
@@ -403,17 +410,18 @@ gc_status gc_profile_read(gc_context *ctx, double *stage_ms, int64_t *stage_call
     if (stage_ms) for (int k = 0; k < GC_N_STAGES; ++k) stage_ms[k] = 0.0;
     if (stage_calls) for (int k = 0; k < GC_N_STAGES; ++k) stage_calls[k] = 0;
     if (!ctx->prof_marks.empty()) {
-        GC_CUDA(ctx, cudaEventSynchronize(ctx->prof_pool[ctx->prof_marks.back().event]));
+        GC_CUDA(ctx, cudaEventSynchronize(ctx->prof_pool[ctx->prof_marks.back().ev_start]));
         for (size_t i = 0; i + 1 < ctx->prof_marks.size(); ++i) {
             const ProfMark &a = ctx->prof_marks[i], &b = ctx->prof_marks[i + 1];
             if (a.stage < 0) continue;
             float ms = 0.f;
-            GC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->prof_pool[a.event], ctx->prof_pool[b.event]));
+            GC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->prof_pool[a.ev_start], ctx->prof_pool[b.ev_end]));
             if (stage_ms) stage_ms[a.stage] += ms;
             if (stage_calls) stage_calls[a.stage] += 1;
         }
     }
     ctx->prof_marks.clear();
+    ctx->prof_used = 0;
     const uint64_t now = gc::launches_total();
     if (kernel_launches) *kernel_launches = now - ctx->launch_base;
     ctx->launch_base = now;

@@ -85,15 +85,19 @@ struct gc_saved {
 
 
 struct ProfMark {
-    int stage;  // -1: end of a call
-    int event;  // index into the event pool
+    int stage;     // -1: end of a call
+    int ev_end;    // event closing the previous stage (index into the event pool)
+    int ev_start;  // event opening this stage: ev_end, or the event after the L2 flush
 };
 
 struct gc_context {
     int device = 0;
     bool prof_on = false;
+    bool prof_flush_on = false;     // flush L2 before each stage (outside its events)
+    DevBuf prof_flush;              // the buffer written to flush L2
     std::vector<cudaEvent_t> prof_pool;
     std::vector<ProfMark> prof_marks;
+    int prof_used = 0;              // events of the pool recorded since the last read
     uint64_t launch_base = 0;
     gc_options opt{};
     gc_saved internal;
@@ -101,6 +105,7 @@ struct gc_context {
     DevBuf field_part;              // per-block partial gradients of the motion source
     DevBuf field_h;                 // hash-grid encodings of the motion source (backward)
     DevBuf kde_scratch;             // KDE training form: histograms, bandwidths, partial sums
+    DevBuf loss_part;               // L1 loss: one FP64 partial sum per CTA
     bool bwd_part_clean = false;  // bwd_part holds only zeros (see the reduce)
     uint32_t *host_word = nullptr;  // pinned
     const gc_saved *last = nullptr; // state written by the most recent forward
@@ -132,17 +137,35 @@ inline gc_status fail(gc_context *ctx, gc_status s, const char *fmt, ...) {
 // capacity (synchronises `stream`, the stream of those forwards; S must have a fixed capacity).
 gc_status capacity_check(gc_context *ctx, const gc_saved &S, cudaStream_t stream);
 
-inline cudaError_t prof_mark(gc_context *ctx, cudaStream_t s, int stage) {
-    if (!ctx->prof_on) return cudaSuccess;
-    const size_t idx = ctx->prof_marks.size();
-    if (idx >= ctx->prof_pool.size()) {
+inline cudaError_t prof_event(gc_context *ctx, cudaStream_t s, int &idx) {
+    idx = ctx->prof_used;
+    if ((size_t)idx >= ctx->prof_pool.size()) {
         cudaEvent_t e;
         cudaError_t err = cudaEventCreate(&e);
         if (err != cudaSuccess) return err;
         ctx->prof_pool.push_back(e);
     }
-    ctx->prof_marks.push_back({stage, (int)idx});
+    ctx->prof_used++;
     return cudaEventRecord(ctx->prof_pool[idx], s);
+}
+
+// With the flush on, a stage boundary records the end of the previous stage, writes the
+// flush buffer (larger than L2) and records the start of the next stage after it, so that
+// each stage starts with its inputs in HBM and its time excludes the flush.
+inline cudaError_t prof_mark(gc_context *ctx, cudaStream_t s, int stage) {
+    if (!ctx->prof_on) return cudaSuccess;
+    int e0 = 0, e1 = 0;
+    cudaError_t err = prof_event(ctx, s, e0);
+    if (err != cudaSuccess) return err;
+    e1 = e0;
+    if (ctx->prof_flush_on && stage >= 0 && ctx->prof_flush.p) {
+        err = cudaMemsetAsync(ctx->prof_flush.p, (int)(ctx->prof_marks.size() & 0x7f), ctx->prof_flush.cap, s);
+        if (err != cudaSuccess) return err;
+        err = prof_event(ctx, s, e1);
+        if (err != cudaSuccess) return err;
+    }
+    ctx->prof_marks.push_back({stage, e0, e1});
+    return cudaSuccess;
 }
 
 inline gc_status check_options(gc_context *ctx, const gc_options *o) {

@@ -390,6 +390,23 @@ class Renderer:
               self.ctx)
         return out, dy
 
+    # ---- L1 photometric loss ------------------------------------------------------------
+
+    def l1_loss(self, image: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | None = None,
+                loss: torch.Tensor | None = None, scale: float | None = None, stream=None):
+        """Mean (or ``scale``-weighted) L1 distance of ``image`` to ``target`` and its gradient
+        scale * sign(image - target), written into ``grad`` (allocated when None) and ``loss``
+        (a one-element device tensor, allocated when None).  Returns (loss, grad)."""
+        if image.shape != target.shape or not image.is_contiguous() or not target.is_contiguous():
+            raise ValueError("image and target must be contiguous and of the same shape")
+        n = image.numel()
+        grad = torch.empty_like(image) if grad is None else grad
+        loss = torch.empty(1, device=image.device) if loss is None else loss
+        s = (1.0 / n if n else 1.0) if scale is None else float(scale)
+        check(lib().gc_l1_loss(self.ctx, image.data_ptr(), target.data_ptr(), n, s, grad.data_ptr(),
+                               loss.data_ptr(), _stream(stream)), self.ctx)
+        return loss, grad
+
     # ---- batched requests -------------------------------------------------------------
 
     def batch_forward(self, gs: GaussianSet, frames: list, requests: list, saved: Saved | None = None,
@@ -516,8 +533,10 @@ class Renderer:
                                          _ptr(nw), _ptr(nc), _stream(stream)), self.ctx)
         return (T, nb, nw, nc) if with_walked else (T, nb)
 
-    def profile(self, enable: bool = True):
-        check(lib().gc_profile_enable(self.ctx, 1 if enable else 0), self.ctx)
+    def profile(self, enable: bool = True, flush_l2: bool = False):
+        """Per-stage CUDA-event timing; flush_l2 writes a 256 MB buffer before every stage
+        (outside the stage's events)."""
+        check(lib().gc_profile_enable(self.ctx, (2 if flush_l2 else 1) if enable else 0), self.ctx)
 
     def profile_read(self) -> dict:
         """Per-stage summed ms and call counts since the last read, and kernel launches."""

@@ -1,4 +1,4 @@
-// exact_probe.cu - checks the library's float-float evaluations of the binning
+// exact_check.cu - checks the library's float-float evaluations of the binning
 // specification's FP64 quantities (step 5: (float)exp((double)x); step 14: tau) against
 // the FP64 expressions themselves, over a uniform grid and over scattered float bit
 // patterns of [-60, 60].  Prints one line per (quantity, sampling): sample count,
