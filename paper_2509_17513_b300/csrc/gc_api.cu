@@ -290,17 +290,20 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
     return GC_OK;
 }
 
-// Fixed key capacity: the largest count that any forward on this state needed since the last
-// check (word 2, kept by the emit kernel) against the capacity; the record is then cleared on
-// `stream`, ordered before the stream's next forwards.
+// Fixed key capacity: word 2 holds the largest count of any forward on this state that
+// overflowed the capacity it ran with since the last check (kept by the emit kernel), word 0
+// the last forward's count; the record is then cleared on `stream`, ordered before the
+// stream's next forwards.
 gc_status capacity_check(gc_context *ctx, const gc_saved &S, cudaStream_t stream) {
     uint32_t w[3];
     GC_CUDA(ctx, cudaMemcpyAsync(w, S.words.p, 12, cudaMemcpyDeviceToHost, stream));
     GC_CUDA(ctx, cudaStreamSynchronize(stream));
     GC_CUDA(ctx, cudaMemsetAsync(static_cast<uint32_t *>(S.words.p) + 2, 0, 4, stream));
-    const uint32_t need = std::max(w[0], w[2]);
-    if ((int64_t)need > S.K)
-        return fail(ctx, GC_ERR_CAPACITY, "a frame needs %u keys, capacity %lld", need, (long long)S.K);
+    if (w[2] != 0u)
+        return fail(ctx, GC_ERR_CAPACITY, "a frame needed %u keys, more than its fixed capacity (now %lld)",
+                    w[2], (long long)S.K);
+    if ((int64_t)w[0] > S.K)
+        return fail(ctx, GC_ERR_CAPACITY, "a frame needs %u keys, capacity %lld", w[0], (long long)S.K);
     return GC_OK;
 }
 

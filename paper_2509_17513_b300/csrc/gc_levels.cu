@@ -130,15 +130,23 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
     }
 }
 
-// Reverse: one CTA of 256 threads per tile, one pixel per thread; NL levels.  Three CTAs per
-// SM (at most 85 registers; a few spill) measured faster than two without spills.
+// Reverse: one CTA of 256 threads per tile, one pixel per thread; NL levels.
+//
+// Per pixel and level the reverse step of Eq. 2 needs the transmittance T_l before the entry
+// and g_l . (c - A_l), with A_l the colour accumulated behind the entry; only the scalar
+// B_l = g_l . A_l is kept (B_l <- B_l + alpha (g_l . c - B_l) when the level blends the
+// entry, B_l = g_l . bg at the start), so a pixel's state is T_l, B_l and g_l per level.  The
+// list positions after each level's last blended entry stay in shared memory (read only when
+// the walk passes one of them).  A warp writes its 9 partials of an entry only when the entry
+// passed its relevance ballot and records that in one byte per (entry, warp); the cross-warp
+// sum adds the written ones in warp order, which gives the same bits as adding every warp
+// with zeros for the others.
 template <int TW, int TH, int NL>
-__global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
+__global__ void __launch_bounds__(256, 4) k_blend_levels_bwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, RenderParams rp,
     const float *__restrict__ lv_T, const uint32_t *__restrict__ lv_last, LevelGrads dimg,
     float *__restrict__ part) {
-    constexpr int L = NL;
     struct Smem {
         float4 a[256];
         float2 b[256];
@@ -148,7 +156,9 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
         uint32_t e[256];
         uint8_t lay[256];
         float wpart[64][8][9];
-        uint32_t wsuf[8][16];  // per warp: max over its pixels and levels l >= m of last[l]
+        uint8_t wrote[64][8];      // per entry of the group and warp: partial written
+        uint32_t last[NL][256];    // per level and pixel: list position after the last blend
+        uint32_t wsuf[8][16];      // per warp: max over its pixels and levels l >= m of last[l]
         uint32_t last_max;
     };
     __shared__ __align__(16) Smem sm;
@@ -160,36 +170,35 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
     const int px = tx * TW + lx, py = ty * TH + ly;
     const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
     const uint32_t bit = 1u << lane;
-    float T[NL], A0[NL], A1[NL], A2[NL], g0[NL], g1[NL], g2[NL];
-    uint32_t last[NL];
+    float T[NL], B[NL], g0[NL], g1[NL], g2[NL];
     uint32_t my_last = 0u;
     const size_t hw = (size_t)W * H;
     const bool inside = px < W && py < H;
     const size_t p = inside ? (size_t)py * W + px : 0;
-#pragma unroll
-    for (int l = 0; l < NL; ++l) {
-        T[l] = 1.f;
-        A0[l] = rp.bg[0];
-        A1[l] = rp.bg[1];
-        A2[l] = rp.bg[2];
-        g0[l] = g1[l] = g2[l] = 0.f;
-        last[l] = 0u;
-        if (inside && l < L) {
-            T[l] = lv_T[l * hw + p];
-            last[l] = lv_last[l * hw + p];
-            const float *gl = dimg.g[l];
-            g0[l] = gl[p];
-            g1[l] = gl[hw + p];
-            g2[l] = gl[2 * hw + p];
-            my_last = max(my_last, last[l]);
-        }
-    }
     if (threadIdx.x == 0) sm.last_max = 0u;
     {
+        uint32_t lastv[NL];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            T[l] = 1.f;
+            g0[l] = g1[l] = g2[l] = 0.f;
+            lastv[l] = 0u;
+            if (inside) {
+                T[l] = lv_T[l * hw + p];
+                lastv[l] = lv_last[l * hw + p];
+                const float *gl = dimg.g[l];
+                g0[l] = gl[p];
+                g1[l] = gl[hw + p];
+                g2[l] = gl[2 * hw + p];
+                my_last = max(my_last, lastv[l]);
+            }
+            B[l] = fmaf(g2[l], rp.bg[2], fmaf(g1[l], rp.bg[1], g0[l] * rp.bg[0]));
+            sm.last[l][threadIdx.x] = lastv[l];
+        }
         uint32_t suf = 0u;
 #pragma unroll
         for (int l = 15; l >= 0; --l) {
-            if (l < NL) suf = max(suf, __reduce_max_sync(0xffffffffu, last[l < NL ? l : 0]));
+            if (l < NL) suf = max(suf, __reduce_max_sync(0xffffffffu, lastv[l < NL ? l : 0]));
             if (lane == 0) sm.wsuf[warp][l] = suf;
         }
     }
@@ -239,10 +248,7 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
                 if (kq < stop) {
                     const int sq = kq - lo;
                     rel = (sm.m[warp * 256 + sq] & wpix) != 0u && (uint32_t)kq < sm.wsuf[warp][sm.lay[sq]];
-                    if (!rel) {
-#pragma unroll
-                        for (int c = 0; c < 9; ++c) sm.wpart[kq - gbot][warp][c] = 0.f;
-                    }
+                    sm.wrote[kq - gbot][warp] = rel ? 1 : 0;
                 }
                 uint32_t todo = __ballot_sync(0xffffffffu, rel);
                 while (todo) {
@@ -259,8 +265,9 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
                         next_last = 0u;
 #pragma unroll
                         for (int l = 0; l < NL; ++l) {
-                            if ((uint32_t)k < last[l]) alive |= 1u << l;
-                            else next_last = max(next_last, last[l]);
+                            const uint32_t ll = sm.last[l][threadIdx.x];
+                            if ((uint32_t)k < ll) alive |= 1u << l;
+                            else next_last = max(next_last, ll);
                         }
                     }
                     // levels of this pixel that blended entry k: alive ones at or above its layer
@@ -290,11 +297,10 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
                                 s0 = fmaf(T[l], g0[l], s0);
                                 s1 = fmaf(T[l], g1[l], s1);
                                 s2 = fmaf(T[l], g2[l], s2);
-                                const float d0 = col.x - A0[l], d1 = col.y - A1[l], d2 = col.z - A2[l];
-                                sal = fmaf(T[l], fmaf(g0[l], d0, fmaf(g1[l], d1, g2[l] * d2)), sal);
-                                A0[l] = fmaf(alpha, d0, A0[l]);
-                                A1[l] = fmaf(alpha, d1, A1[l]);
-                                A2[l] = fmaf(alpha, d2, A2[l]);
+                                const float gc = fmaf(g2[l], col.z, fmaf(g1[l], col.y, g0[l] * col.x));
+                                const float dl = gc - B[l];
+                                sal = fmaf(T[l], dl, sal);
+                                B[l] = fmaf(alpha, dl, B[l]);
                             }
                             v[6] = alpha * s0;
                             v[7] = alpha * s1;
@@ -314,7 +320,7 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
                     }
                     // the entry passed the warp's relevance ballot: some pixel nearly always
                     // blended it, so the reduction runs without a vote
-                    float out0 = 0.f, out8 = 0.f;
+                    float out0, out8;
                     {
                         {
                             const bool up = lane & 16;
@@ -355,9 +361,13 @@ __global__ void __launch_bounds__(256, 3) k_blend_levels_bwd(
             __syncthreads();
             for (int idx = threadIdx.x; idx < (gtop - gbot) * 9; idx += 256) {
                 const int q = idx / 9, c = idx - q * 9;
-                float acc = sm.wpart[q][0][c];
+                const uint2 wr = *reinterpret_cast<const uint2 *>(&sm.wrote[q][0]);
+                float acc = 0.f;
 #pragma unroll
-                for (int w2 = 1; w2 < 8; ++w2) acc += sm.wpart[q][w2][c];
+                for (int w2 = 0; w2 < 8; ++w2) {
+                    const uint32_t byte = ((w2 < 4 ? wr.x : wr.y) >> (8 * (w2 & 3))) & 0xffu;
+                    if (byte) acc += sm.wpart[q][w2][c];
+                }
                 part[(int64_t)sm.e[gbot + q - lo] * 9 + c] = acc;
             }
             __syncthreads();

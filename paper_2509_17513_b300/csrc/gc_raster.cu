@@ -27,9 +27,10 @@ __global__ void __launch_bounds__(256) k_emit(const float4 *__restrict__ ranked,
                                               uint32_t *__restrict__ keys,
                                               uint32_t *__restrict__ vals, const uint32_t *total,
                                               uint32_t *peak) {
-    // the largest key count any forward needed since the host last looked (a fixed capacity
-    // is checked against it, so that an overflow of any frame of a multi-frame step shows)
-    if (peak && blockIdx.x == 0 && threadIdx.x == 0) atomicMax(peak, *total);
+    // the largest key count of a forward that overflowed the capacity it ran with, since the
+    // host last looked (so that an overflow in any frame of a multi-frame step shows, and a
+    // count that fitted an earlier, larger capacity is not taken for one)
+    if (peak && blockIdx.x == 0 && threadIdx.x == 0 && *total > cap) atomicMax(peak, *total);
     const int lane = threadIdx.x & 31;
     const int64_t wbase = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - lane;
     if (wbase >= n) return;

@@ -127,6 +127,31 @@ def test_overflow_in_any_frame_is_reported(gc, small):
     g.close()
 
 
+def test_capacity_change_keeps_the_overflow_record_exact(gc, small):
+    """Only overflows are recorded: counts that fitted an earlier, larger capacity do not fail
+    a check after the capacity shrinks, and an overflow under a small capacity is still
+    reported after the capacity grows."""
+    r0, gs, frames, cams = _setup(gc, small)
+    need = []
+    for f in range(3):
+        r0.levels_forward(gs, frames[f], 6, cams[f])
+        need.append(r0.stats()["n_keys"])
+    small_cap = (need[0] + max(need[1], need[2])) // 2   # fits frames 1 and 2, not frame 0
+    r, gs, frames, cams = _setup(gc, small, key_capacity=need[0] + 4096)
+    r.levels_forward(gs, frames[0], 6, cams[0])           # fits the large capacity
+    r.set_options(key_capacity=small_cap)
+    for f in (1, 2):
+        r.levels_forward(gs, frames[f], 6, cams[f])
+    r.check()                                             # no frame overflowed
+    r.levels_forward(gs, frames[0], 6, cams[0])           # overflows the small capacity
+    r.set_options(key_capacity=need[0] + 4096)
+    r.levels_forward(gs, frames[1], 6, cams[1])
+    with pytest.raises(gc.GCError, match="capacity"):
+        r.check()
+    r.levels_forward(gs, frames[2], 6, cams[2])
+    r.check()                                             # the record was cleared by the check
+
+
 def test_graph_argument_errors(gc, small):
     r, gs, frames, cams = _setup(gc, small)
     with pytest.raises(ValueError):
