@@ -82,7 +82,7 @@ static void saved_release(gc_context *ctx, gc_saved *s) {
     DevBuf *bufs[] = {&s->rec, &s->ranked, &s->dkeys[0], &s->dkeys[1], &s->dvals[0], &s->dvals[1],
                       &s->touched, &s->touched_r, &s->offsets, &s->tkeys[0], &s->tkeys[1],
                       &s->tvals[0], &s->tvals[1], &s->ranges, &s->final_T, &s->n_contrib,
-                      &s->n_blended, &s->n_walked, &s->words};
+                      &s->n_blended, &s->n_walked, &s->words, &s->lv_T, &s->lv_last, &s->row_shift};
     for (DevBuf *b : bufs) release(*b);
     s->valid = false;
 }
@@ -245,26 +245,48 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
             S.k_exact = true;
         }
         const int64_t kk = K > 0 ? K : 1;
+        // binning by tile row pads every row's segment to whole radix tiles: room for that
+        // beyond the entries (the capacity counts entries only)
+        const int64_t kpad = (kk + (int64_t)rp.nty * gc::radix_tile_keys() + 3) & ~int64_t(3);
+        const bool rows = gc::bucket_binning_fits(rp) && kpad <= 0xFFFFFFF0ll;
+        const int64_t kalloc = rows ? kpad : kk;
         for (int b = 0; b < 2; ++b) {
-            GC_CUDA(ctx, grow(S.tkeys[b], (size_t)kk * 4));
-            GC_CUDA(ctx, grow(S.tvals[b], (size_t)kk * 4));
+            GC_CUDA(ctx, grow(S.tkeys[b], (size_t)kalloc * 4));
+            GC_CUDA(ctx, grow(S.tvals[b], (size_t)kalloc * 4));
         }
-        GC_CUDA(ctx, grow(ctx->scratch, 4 * std::max(gc::radix_scratch_words(kk), scan_words)));
+        const size_t bucket_words = rows ? ((gc::bucket_scratch_words(n_sel, rp.nty) + 63) & ~size_t(63)) : 0;
+        GC_CUDA(ctx, grow(ctx->scratch, 4 * (bucket_words + std::max(gc::radix_scratch_words(kalloc), scan_words))));
         scratch = ctx->scratch.as<uint32_t>();
+        S.row_binned = false;
         if (K > 0) {
-            GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_EMIT));
-            GC_CUDA(ctx, gc::launch_emit(S.ranked.as<float4>(), S.offsets.as<uint32_t>(),
-                                         S.touched_r.as<uint32_t>(), n_sel, rp, cam->width, cam->height,
-                                         S.tkeys[0].as<uint32_t>(), S.tvals[0].as<uint32_t>(),
-                                         (uint32_t)K, s, words, S.k_exact ? nullptr : words + 2));
             uint32_t *tk[2] = {S.tkeys[0].as<uint32_t>(), S.tkeys[1].as<uint32_t>()};
             uint32_t *tv[2] = {S.tvals[0].as<uint32_t>(), S.tvals[1].as<uint32_t>()};
-            const uint32_t *ndev = S.k_exact ? nullptr : words;
-            GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_TILE_SORT));
-            GC_CUDA(ctx, gc::radix_sort_pairs(tk, tv, K, ndev, bits_for(n_tiles - 1), scratch,
-                                              &S.tile_buf, s, words + 1, /*keys_out=*/true));
-            GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_RANGES));
-            GC_CUDA(ctx, gc::launch_tile_ranges(tk[S.tile_buf], ndev, K, S.ranges.as<uint2>(), s));
+            uint32_t *peak = S.k_exact ? nullptr : words + 2;
+            GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_EMIT));
+            if (rows) {
+                GC_CUDA(ctx, grow(S.row_shift, (size_t)(rp.nty + 1) * 4));
+                GC_CUDA(ctx, gc::launch_bucket_place(S.ranked.as<float4>(), words, S.touched_r.as<uint32_t>(), n_sel,
+                                                     rp, cam->width, cam->height, tk[0], tv[0],
+                                                     (uint32_t)std::min<int64_t>(K, 0xFFFFFFFFll), (uint32_t)kalloc,
+                                                     words, S.row_shift.as<uint32_t>(), scratch, peak, s));
+                GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_TILE_SORT));
+                GC_CUDA(ctx, gc::launch_bucket_sort(tk, tv, (uint32_t)kalloc, words, n_sel, rp.nty, scratch,
+                                                    scratch + bucket_words, &S.tile_buf, s));
+                GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_RANGES));
+                GC_CUDA(ctx, gc::launch_row_key_ranges(tk[S.tile_buf], words, (uint32_t)kalloc, rp,
+                                                       S.ranges.as<uint2>(), s));
+                S.row_binned = true;
+            } else {
+                GC_CUDA(ctx, gc::launch_emit(S.ranked.as<float4>(), S.offsets.as<uint32_t>(),
+                                             S.touched_r.as<uint32_t>(), n_sel, rp, cam->width, cam->height,
+                                             tk[0], tv[0], (uint32_t)K, s, words, peak));
+                const uint32_t *ndev = S.k_exact ? nullptr : words;
+                GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_TILE_SORT));
+                GC_CUDA(ctx, gc::radix_sort_pairs(tk, tv, K, ndev, bits_for(n_tiles - 1), scratch,
+                                                  &S.tile_buf, s, words + 1, /*keys_out=*/true));
+                GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_RANGES));
+                GC_CUDA(ctx, gc::launch_tile_ranges(tk[S.tile_buf], ndev, K, S.ranges.as<uint2>(), s));
+            }
         }
     } else {
         GC_CUDA(ctx, cudaMemsetAsync(words, 0, 4, s));
@@ -368,11 +390,17 @@ gc_status gc_saved_tile_lists(gc_context *ctx, const gc_saved *saved, int32_t *r
     }
     if (capacity < K) return fail(ctx, GC_ERR_CAPACITY, "tile lists need %lld entries", (long long)K);
     const int64_t n_tiles = (int64_t)S.rp.ntx * S.rp.nty;
-    GC_CUDA(ctx, cudaMemcpyAsync(ranges, S.ranges.p, (size_t)n_tiles * 8, cudaMemcpyDeviceToDevice, s));
-    if (K > 0)
-        GC_CUDA(ctx, gc::launch_entries_to_global(S.tvals[S.tile_buf].as<uint32_t>(),
-                                                  S.dvals[S.depth_buf].as<uint32_t>(), S.sel, K,
-                                                  gauss_ids, s));
+    if (S.row_binned && K > 0) {  // row segments carry padding: export the lists without it
+        GC_CUDA(ctx, gc::launch_row_lists_export(S.ranges.as<uint2>(), S.tvals[S.tile_buf].as<uint32_t>(),
+                                                 S.row_shift.as<uint32_t>(), S.rp, S.dvals[S.depth_buf].as<uint32_t>(),
+                                                 S.sel, ranges, gauss_ids, s));
+    } else {
+        GC_CUDA(ctx, cudaMemcpyAsync(ranges, S.ranges.p, (size_t)n_tiles * 8, cudaMemcpyDeviceToDevice, s));
+        if (K > 0)
+            GC_CUDA(ctx, gc::launch_entries_to_global(S.tvals[S.tile_buf].as<uint32_t>(),
+                                                      S.dvals[S.depth_buf].as<uint32_t>(), S.sel, K,
+                                                      gauss_ids, s));
+    }
     GC_CUDA(ctx, cudaStreamSynchronize(s));
     return GC_OK;
 }

@@ -194,6 +194,28 @@ cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uin
                         uint32_t cap, cudaStream_t st, const uint32_t *total = nullptr,
                         uint32_t *peak = nullptr);
 
+// Binning by tile row (gc_bucket.cu), for images of at most 256 tile columns
+// (bucket_binning_fits): the entries placed straight into per-row segments padded to whole
+// radix tiles, key (row << 8) | column, value = rank (launch_bucket_place: words[3] = padded
+// total, shift[row] = padded minus unpadded start of the row, more than `cap` entries
+// recorded in *peak); one segmented stable pass on the column (launch_bucket_sort); tile
+// ranges from those keys (launch_row_key_ranges; ranges must be zeroed).  Buffers hold
+// `alloc` >= entries + rows x radix_tile_keys() keys; `scratch` needs bucket_scratch_words.
+bool bucket_binning_fits(const RenderParams &rp);
+size_t bucket_scratch_words(int64_t n, int n_rows);
+cudaError_t launch_bucket_place(const float4 *ranked, const uint32_t *total, const uint32_t *touched_r, int64_t n,
+                                const RenderParams &rp, int W, int H, uint32_t *keys, uint32_t *vals, uint32_t cap,
+                                uint32_t alloc, uint32_t *words, uint32_t *shift, uint32_t *scratch, uint32_t *peak,
+                                cudaStream_t st);
+cudaError_t launch_bucket_sort(uint32_t *keys[2], uint32_t *vals[2], uint32_t alloc, uint32_t *words, int64_t n,
+                               int n_rows, uint32_t *scratch, uint32_t *sort_scratch, int *out_buf, cudaStream_t st);
+cudaError_t launch_row_key_ranges(const uint32_t *keys, const uint32_t *words, uint32_t alloc, const RenderParams &rp,
+                                  uint2 *ranges, cudaStream_t st);
+// Unpadded tile lists of a row-binned state: ranges (int32 pairs) and global indices.
+cudaError_t launch_row_lists_export(const uint2 *ranges, const uint32_t *sorted_vals, const uint32_t *shift,
+                                    const RenderParams &rp, const uint32_t *perm, const Selection &sel,
+                                    int32_t *out_ranges, int64_t *out_ids, cudaStream_t st);
+
 // Tile ranges [start, end) from sorted tile keys; ranges must be zeroed.
 cudaError_t launch_tile_ranges(const uint32_t *keys, const uint32_t *n_dev, int64_t n_max,
                                uint2 *ranges, cudaStream_t st);

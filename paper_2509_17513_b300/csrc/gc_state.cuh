@@ -81,6 +81,8 @@ struct gc_saved {
         final_T, n_contrib, n_blended, n_walked, words;
     int levels = 0;         // > 0: a multi-level forward of levels 1..levels
     DevBuf lv_T, lv_last;   // its per-level final transmittance and list position
+    bool row_binned = false;  // lists binned by tile row: row segments padded to radix tiles
+    DevBuf row_shift;         // per tile row: padded minus unpadded start of its segment
 };
 
 
