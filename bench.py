@@ -88,8 +88,8 @@ def stage_work(stage: str, w: dict):
         return n * (REC_BYTES + 8) + k * 8, "bytes", None
     if stage == "tile_sort":           # one read + one write of 8 B pairs; 2 passes x 20 B
         return k * 16, "bytes", k * 40
-    if stage == "ranges":
-        return k * 4 + w["tiles"] * 8, "bytes", None
+    if stage == "ranges":  # row-binned lists: two scanned digit counts read, one range written per tile
+        return w["tiles"] * 16, "bytes", None
     if stage == "reduce":              # 36 B of partials per entry in, 36 B per Gaussian out
         return k * 36 + n * 44, "bytes", None
     if stage == "preprocess_bwd":      # attributes, 2D gradient and count in; gradients and

@@ -234,7 +234,7 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
                                             S.touched.as<uint32_t>(), n_sel, S.ranked.as<float4>(),
                                             S.touched_r.as<uint32_t>(), s));
         GC_CUDA(ctx, gc::launch_exclusive_scan(S.touched_r.as<uint32_t>(), S.offsets.as<uint32_t>(),
-                                               n_sel, words, scratch, s));
+                                               n_sel, words, scratch, s, words + 1));
         if (cap_fixed > 0) {
             K = cap_fixed;
             S.k_exact = false;
@@ -273,8 +273,8 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
                 GC_CUDA(ctx, gc::launch_bucket_sort(tk, tv, (uint32_t)kalloc, words, n_sel, rp.nty, scratch,
                                                     scratch + bucket_words, &S.tile_buf, s));
                 GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_RANGES));
-                GC_CUDA(ctx, gc::launch_row_key_ranges(tk[S.tile_buf], words, (uint32_t)kalloc, rp,
-                                                       S.ranges.as<uint2>(), s));
+                GC_CUDA(ctx, gc::launch_bucket_ranges(n_sel, scratch, scratch + bucket_words, rp,
+                                                      S.ranges.as<uint2>(), s));
                 S.row_binned = true;
             } else {
                 GC_CUDA(ctx, gc::launch_emit(S.ranked.as<float4>(), S.offsets.as<uint32_t>(),

@@ -761,7 +761,7 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
         GC_CUDA(ctx, gc::launch_rank_gather(dv[B.depth_buf], B.rec.as<float4>(), B.touched.as<uint32_t>(), items,
                                             B.ranked.as<float4>(), B.touched_r.as<uint32_t>(), s));
         GC_CUDA(ctx, gc::launch_exclusive_scan(B.touched_r.as<uint32_t>(), B.offsets.as<uint32_t>(), items, words,
-                                               scratch, s));
+                                               scratch, s, words + 1));
     } else {
         GC_CUDA(ctx, cudaMemsetAsync(words, 0, 4, s));
     }

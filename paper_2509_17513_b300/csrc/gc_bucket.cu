@@ -16,14 +16,15 @@
 //   k_bucket_segments  each row's segment padded to whole radix tiles (a radix block never
 //                   straddles two rows): the shift from the scanned offsets to the padded
 //                   positions, the segments in radix-block units, the padded total;
-//   k_bucket_pads   pad slots get the key 0xFFFFFFFF (column 255: sorted behind the row's
-//                   entries; skipped by the ranges);
+//   k_bucket_pads   pad slots get the key 0xFFFFFFFF (column 255, which no tile uses: sorted
+//                   behind the row's entries);
 //   k_bucket_place  the chunk's entries of each row written at their positions, key =
 //                   (row << 8) | column, value = rank.
 // Within a chunk the lanes' entries of a row are laid out lane by lane (rank order); each
 // warp computes the per-row lane prefix in a 32-row window of shared memory (column =
 // lane, padded to 33 words so that both the lane writes and the row scans hit distinct
-// banks).  Tile columns must fit 8 bits (at most 256 tiles per row).
+// banks).  After the pass, tile (row, column)'s range is the column's digit range in the
+// row's segment, read from the pass's scanned digit counts.  At most 255 tile columns.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -270,39 +271,6 @@ __global__ void __launch_bounds__(kBucketWarps * 32) k_bucket_place(const float4
     }
 }
 
-// Tile ranges from keys (row << 8) | column sorted by tile; pad keys (row >= n_rows) are
-// skipped.  Four keys per thread (16-byte loads; keys 16-byte aligned), neighbours across
-// threads by shuffles, across warps by a load.
-__global__ void __launch_bounds__(256) k_row_key_ranges(const uint32_t *__restrict__ keys, const uint32_t *words,
-                                                        int ntx, int n_rows, uint2 *__restrict__ ranges) {
-    const int64_t n = (int64_t)words[3];
-    const int lane = threadIdx.x & 31;
-    const int64_t n4 = n >> 2;  // the padded total is a multiple of the radix tile
-    auto tile_of = [&](uint32_t k) { return (int64_t)(k >> 8) * ntx + (k & 0xffu); };
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q - lane < n4;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const bool in = q < n4;
-        uint4 v = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-        if (in) v = reinterpret_cast<const uint4 *>(keys)[q];
-        uint32_t prev = __shfl_up_sync(0xffffffffu, v.w, 1);
-        uint32_t next = __shfl_down_sync(0xffffffffu, v.x, 1);
-        if (!in) continue;
-        const int64_t p = 4 * q;
-        if (lane == 0 && p > 0) prev = keys[p - 1];
-        if ((lane == 31 || q + 1 >= n4) && p + 4 < n) next = keys[p + 4];
-        const uint32_t k[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if ((int)(k[i] >> 8) >= n_rows || (int)(k[i] & 0xffu) >= ntx) continue;  // pad
-            const uint32_t before = i == 0 ? prev : k[i - 1];
-            const uint32_t after = i == 3 ? next : k[i + 1];
-            const int64_t t = tile_of(k[i]);
-            if (p + i == 0 || before != k[i]) ranges[t].x = (uint32_t)(p + i);
-            if (p + i == n - 1 || after != k[i]) ranges[t].y = (uint32_t)(p + i + 1);
-        }
-    }
-}
-
 // Tile lists without the row padding (diagnostics): per tile its range shifted back by the
 // row's pad shift, and the global index of each of its entries at the unpadded position.
 __global__ void k_row_lists_export(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
@@ -322,12 +290,13 @@ __global__ void k_row_lists_export(const uint2 *__restrict__ ranges, const uint3
 
 }  // namespace
 
-bool bucket_binning_fits(const RenderParams &rp) { return rp.ntx >= 1 && rp.ntx <= 256 && rp.nty <= 1 << 16; }
+// Column 255 is left to the pad keys, so that a tile's range is a digit range of its row.
+bool bucket_binning_fits(const RenderParams &rp) { return rp.ntx >= 1 && rp.ntx <= 255 && rp.nty <= 1 << 16; }
 
 size_t bucket_scratch_words(int64_t n, int n_rows) {
     const int64_t chunks = (n + 31) / 32;
     const int64_t cells = (int64_t)n_rows * (chunks > 0 ? chunks : 1);
-    // counts, scanned counts, scan partials, segments, pads (uint2, 8-byte aligned)
+    // counts, scanned counts, scan state (8-byte aligned), segments, pads (uint2, 8-byte aligned)
     return (size_t)(2 * cells + scan_partials_size(cells) + (n_rows + 1) + 2 * (n_rows + 1) + 64);
 }
 
@@ -342,7 +311,7 @@ BucketScratch carve(uint32_t *scratch, int64_t n, int n_rows) {
     BucketScratch b;
     b.counts = scratch;
     b.scanned = b.counts + cells;
-    b.partials = b.scanned + cells;
+    b.partials = b.counts + 2 * cells;  // an even word offset: the scan's 64-bit status words are 8-byte aligned
     b.segs = b.partials + scan_partials_size(cells);
     size_t off = (size_t)(b.segs - scratch) + (size_t)(n_rows + 1);
     off = (off + 1) & ~(size_t)1;
@@ -359,10 +328,12 @@ cudaError_t launch_bucket_place(const float4 *ranked, const uint32_t *total, con
     const int64_t chunks = (n + 31) / 32;
     const int64_t cells = (int64_t)n_rows * chunks;
     const BucketScratch b = carve(scratch, n, n_rows);
+    if ((reinterpret_cast<uintptr_t>(b.pads) | reinterpret_cast<uintptr_t>(b.partials)) & 7)
+        return cudaErrorMisalignedAddress;  // 8-byte words must be 8-byte aligned (never launched)
     const unsigned grid = (unsigned)((chunks + kBucketWarps - 1) / kBucketWarps);
     k_bucket_count<<<grid, kBucketWarps * 32, 0, st>>>(ranked, touched_r, n, rp, W, H, n_rows, chunks, b.counts);
     note_launches(1);
-    cudaError_t e = launch_exclusive_scan(b.counts, b.scanned, cells, nullptr, b.partials, st);
+    cudaError_t e = launch_exclusive_scan(b.counts, b.scanned, cells, nullptr, b.partials, st, words + 1);
     if (e != cudaSuccess) return e;
     k_bucket_segments<<<1, 1024, 0, st>>>(b.scanned, total, n_rows, chunks, (uint32_t)radix_tile_keys(), cap, alloc,
                                           shift, b.segs, b.pads, words, peak);
@@ -378,18 +349,15 @@ cudaError_t launch_bucket_place(const float4 *ranked, const uint32_t *total, con
 cudaError_t launch_bucket_sort(uint32_t *keys[2], uint32_t *vals[2], uint32_t alloc, uint32_t *words, int64_t n,
                                int n_rows, uint32_t *scratch, uint32_t *sort_scratch, int *out_buf, cudaStream_t st) {
     const BucketScratch b = carve(scratch, n, n_rows);
-    return radix_sort_pairs(keys, vals, alloc, words + 3, 8, sort_scratch, out_buf, st, words + 1, true, b.segs,
+    // the sorted keys are not kept: the ranges come from the pass's digit counts
+    return radix_sort_pairs(keys, vals, alloc, words + 3, 8, sort_scratch, out_buf, st, words + 1, false, b.segs,
                             n_rows);
 }
 
-cudaError_t launch_row_key_ranges(const uint32_t *keys, const uint32_t *words, uint32_t alloc, const RenderParams &rp,
-                                  uint2 *ranges, cudaStream_t st) {
-    int64_t blocks = ((int64_t)alloc / 4 + 255) / 256;
-    if (blocks < 1) blocks = 1;
-    if (blocks > 148 * 16) blocks = 148 * 16;
-    k_row_key_ranges<<<(unsigned)blocks, 256, 0, st>>>(keys, words, rp.ntx, rp.nty, ranges);
-    note_launches(1);
-    return cudaGetLastError();
+cudaError_t launch_bucket_ranges(int64_t n, uint32_t *scratch, uint32_t *sort_scratch, const RenderParams &rp,
+                                 uint2 *ranges, cudaStream_t st) {
+    const BucketScratch b = carve(scratch, n, rp.nty);
+    return launch_segment_digit_ranges(sort_scratch, b.segs, rp.nty, rp.ntx, ranges, st);
 }
 
 cudaError_t launch_row_lists_export(const uint2 *ranges, const uint32_t *sorted_vals, const uint32_t *shift,

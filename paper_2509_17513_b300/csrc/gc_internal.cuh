@@ -166,10 +166,12 @@ cudaError_t launch_rank_gather(const uint32_t *perm, const float4 *rec, const ui
                                int64_t n, float4 *ranked, uint32_t *touched_r, cudaStream_t st);
 
 // Exclusive scan of n uint32 values; writes out[0..n) and, if total != NULL,
-// the sum to *total (device).  `partials` needs scan_partials_size(n) words.
+// the sum to *total (device).  `partials` needs scan_partials_size(n) words (8-byte
+// aligned).  Longer inputs are scanned in one chained pass whose bounded waits set
+// kErrTimeout in *err (device word; NULL: a word of `partials`).
 size_t scan_partials_size(int64_t n);
 cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
-                                  uint32_t *partials, cudaStream_t st);
+                                  uint32_t *partials, cudaStream_t st, uint32_t *err = nullptr);
 
 // Stable LSD radix sort of (key, value) pairs on key bits [0, end_bit).
 // keys[0]/vals[0] hold the input; the sorted output ends in buffer *out_buf.
@@ -186,6 +188,12 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
                              cudaStream_t st, uint32_t *err, bool keys_out = true,
                              const uint32_t *seg_block0 = nullptr, int n_seg = 0);
 
+// After a one-pass segmented radix_sort_pairs (8-bit digit) with scratch `sort_scratch`:
+// ranges[s * n_digits + d] = [start, end) of digit d < n_digits <= 255 in segment s (written
+// only when nonempty; ranges must be zeroed).
+cudaError_t launch_segment_digit_ranges(const uint32_t *sort_scratch, const uint32_t *seg_block0, int n_seg,
+                                        int n_digits, uint2 *ranges, cudaStream_t st);
+
 // Emit (tile key, rank) for every tile of every row interval of every visible Gaussian,
 // in rank order (image W x H).  Entries at positions >= cap are dropped (fixed-capacity
 // mode reports the overflow).
@@ -199,7 +207,7 @@ cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uin
 // radix tiles, key (row << 8) | column, value = rank (launch_bucket_place: words[3] = padded
 // total, shift[row] = padded minus unpadded start of the row, more than `cap` entries
 // recorded in *peak); one segmented stable pass on the column (launch_bucket_sort); tile
-// ranges from those keys (launch_row_key_ranges; ranges must be zeroed).  Buffers hold
+// ranges from its digit counts (launch_bucket_ranges; ranges must be zeroed).  Buffers hold
 // `alloc` >= entries + rows x radix_tile_keys() keys; `scratch` needs bucket_scratch_words.
 bool bucket_binning_fits(const RenderParams &rp);
 size_t bucket_scratch_words(int64_t n, int n_rows);
@@ -209,8 +217,8 @@ cudaError_t launch_bucket_place(const float4 *ranked, const uint32_t *total, con
                                 cudaStream_t st);
 cudaError_t launch_bucket_sort(uint32_t *keys[2], uint32_t *vals[2], uint32_t alloc, uint32_t *words, int64_t n,
                                int n_rows, uint32_t *scratch, uint32_t *sort_scratch, int *out_buf, cudaStream_t st);
-cudaError_t launch_row_key_ranges(const uint32_t *keys, const uint32_t *words, uint32_t alloc, const RenderParams &rp,
-                                  uint2 *ranges, cudaStream_t st);
+cudaError_t launch_bucket_ranges(int64_t n, uint32_t *scratch, uint32_t *sort_scratch, const RenderParams &rp,
+                                 uint2 *ranges, cudaStream_t st);
 // Unpadded tile lists of a row-binned state: ranges (int32 pairs) and global indices.
 cudaError_t launch_row_lists_export(const uint2 *ranges, const uint32_t *sorted_vals, const uint32_t *shift,
                                     const RenderParams &rp, const uint32_t *perm, const Selection &sel,

@@ -255,7 +255,7 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
         NA_CUDA(gc::launch_preprocess(src, sel, n_sel, cp, rp, rec, dk[0], dv[0], touched, s));
         NA_CUDA(gc::radix_sort_pairs(dk, dv, n_sel, nullptr, 32, sort_scratch, &depth_buf, s, words + 1));
         NA_CUDA(gc::launch_rank_gather(dv[depth_buf], rec, touched, n_sel, ranked, touched_r, s));
-        NA_CUDA(gc::launch_exclusive_scan(touched_r, offsets, n_sel, words, sort_scratch, s));
+        NA_CUDA(gc::launch_exclusive_scan(touched_r, offsets, n_sel, words, sort_scratch, s, words + 1));
         uint32_t w_host[2] = {0u, 0u};  // pair count and error word; stack: no host allocation
         NA_CUDA(cudaMemcpyAsync(w_host, words, 8, cudaMemcpyDeviceToHost, s));
         NA_CUDA(cudaStreamSynchronize(s));

@@ -106,64 +106,6 @@ __device__ __forceinline__ void store16(uint32_t *out, int64_t start, int64_t n,
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ in,
-                                                              int64_t n, bool vec,
-                                                              uint32_t *__restrict__ partials) {
-    __shared__ uint32_t red[kScanThreads / 32];
-    const int64_t start = (int64_t)blockIdx.x * kScanChunk + 16 * (int64_t)threadIdx.x;
-    uint32_t x[16];
-    load16(in, start, n, vec, x);
-    uint32_t s = 0;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) s += x[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
-        partials[blockIdx.x] = t;
-    }
-}
-
-// One CTA scans the partials in chunks of 1024 with a running carry.
-__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *partials, int64_t nb,
-                                                        uint32_t *total) {
-    __shared__ uint32_t ws[33];
-    uint32_t carry = 0;
-    for (int64_t b = 0; b < nb; b += 1024) {
-        int64_t i = b + threadIdx.x;
-        uint32_t x = (i < nb) ? partials[i] : 0u;
-        uint32_t tot;
-        uint32_t ex = block_exclusive_scan<1024>(x, ws, &tot);
-        if (i < nb) partials[i] = carry + ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0 && total) *total = carry;
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *in, uint32_t *out,
-                                                            int64_t n, bool vec,
-                                                            const uint32_t *__restrict__ partials) {
-    __shared__ uint32_t ws[33];
-    const int64_t start = (int64_t)blockIdx.x * kScanChunk + 16 * (int64_t)threadIdx.x;
-    uint32_t x[16];
-    load16(in, start, n, vec, x);
-    uint32_t s = 0;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const uint32_t v = x[q];
-        x[q] = s;
-        s += v;
-    }
-    uint32_t tot;
-    const uint32_t ex = block_exclusive_scan<kScanThreads>(s, ws, &tot) + partials[blockIdx.x];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) x[q] += ex;
-    store16(out, start, n, vec, x);
-}
-
 // Whole scan in one CTA of 1024 threads for n <= kSmallScan: chunks of 16384
 // elements, 16 contiguous per thread (16-byte loads), one block scan per chunk.
 constexpr int64_t kSmallScan = 1024 * 16 * 8;
@@ -191,6 +133,90 @@ __global__ void __launch_bounds__(1024) k_scan_single(const uint32_t *in, uint32
         carry += tot;
     }
     if (threadIdx.x == 0 && total) *total = carry;
+}
+
+// Single-pass chained scan for n > kSmallScan: CTAs take chunks of kScanChunk by ticket,
+// scan them, publish the chunk's sum (flag 1) and, once the sum of every chunk before it is
+// known, the inclusive prefix (flag 2): one warp looks back over 32 predecessors per round
+// trip, adding sums until it meets an inclusive prefix.  A chunk waits only on chunks with
+// smaller tickets, taken by CTAs already running, so every wait ends; each is still bounded
+// and a wait that runs out sets the error word.  status (one 64-bit word per chunk, flag in
+// the high half) and the ticket must be zero before the launch.
+constexpr uint32_t kScanWaitLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const uint32_t *in, uint32_t *out, int64_t n,
+                                                               bool vec, uint32_t *ticket,
+                                                               unsigned long long *status, uint32_t *total,
+                                                               uint32_t *err) {
+    __shared__ uint32_t ws[33];
+    __shared__ uint32_t s_chunk, s_excl;
+    if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t c = (int64_t)s_chunk;
+    const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    if (c >= nb) return;  // CTA-uniform
+    const int64_t start = c * kScanChunk + 16 * (int64_t)threadIdx.x;
+    uint32_t x[16];
+    load16(in, start, n, vec, x);
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const uint32_t v = x[q];
+        x[q] = s;
+        s += v;
+    }
+    uint32_t agg;
+    const uint32_t ex = block_exclusive_scan<kScanThreads>(s, ws, &agg);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        uint32_t excl = 0u;
+        if (c == 0) {
+            if (lane == 0) st_relaxed64(&status[0], (2ull << 32) | agg);
+        } else {
+            if (lane == 0) st_relaxed64(&status[c], (1ull << 32) | agg);
+            int64_t q = c - 1;
+            for (;;) {
+                const int64_t idx = q - lane;
+                unsigned long long v = idx >= 0 ? ld_relaxed64(&status[idx]) : (2ull << 32);
+                for (uint32_t it = 0; (v >> 32) == 0ull; ++it) {
+                    if (it >= kScanWaitLimit) {
+                        atomicOr(err, kErrTimeout);
+                        v = 2ull << 32;
+                        break;
+                    }
+                    v = ld_relaxed64(&status[idx]);
+                }
+                const uint32_t inc = __ballot_sync(0xffffffffu, (v >> 32) == 2ull);
+                const uint32_t upto = inc ? (2u << (__ffs(inc) - 1)) - 1u : 0xffffffffu;  // lanes 0..first inclusive
+                uint32_t part = ((upto >> lane) & 1u) ? (uint32_t)v : 0u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                excl += part;
+                if (inc) break;
+                q -= 32;
+            }
+            if (lane == 0) st_relaxed64(&status[c], (2ull << 32) | (excl + agg));
+        }
+        if (lane == 0) {
+            s_excl = excl;
+            if (c == nb - 1 && total) *total = excl + agg;
+        }
+    }
+    __syncthreads();
+    const uint32_t base = s_excl + ex;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] += base;
+    store16(out, start, n, vec, x);
 }
 
 __device__ __forceinline__ int64_t device_count(const uint32_t *n_dev, int64_t n_max) {
@@ -594,12 +620,40 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep_scatter(
     }
 }
 
+// Ranges of the digits of every segment after a one-pass segmented sort, from the scanned
+// per-block digit counts it leaves in `counts` (segment-major, digit-major within a segment):
+// digit d of segment s starts at counts[256 b0 + d nb] (b0, nb: the segment's first block and
+// block count) and ends where digit d + 1 starts.  Thread per (segment, digit < n_digits),
+// digits < 255; empty ranges are not written.
+__global__ void k_segment_digit_ranges(const uint32_t *__restrict__ counts, const uint32_t *__restrict__ seg_block0,
+                                       int n_seg, int n_digits, uint2 *__restrict__ ranges) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_seg * n_digits) return;
+    const int sg = (int)(i / n_digits), d = (int)(i - (int64_t)sg * n_digits);
+    const uint32_t b0 = seg_block0[sg], nb = seg_block0[sg + 1] - b0;
+    if (nb == 0u) return;
+    const uint32_t a = counts[(int64_t)256 * b0 + (int64_t)d * nb];
+    const uint32_t b = counts[(int64_t)256 * b0 + (int64_t)(d + 1) * nb];
+    if (b > a) ranges[i] = make_uint2(a, b);
+}
+
 }  // namespace
 
-size_t scan_partials_size(int64_t n) { return (size_t)((n + kScanChunk - 1) / kScanChunk) + 1; }
+cudaError_t launch_segment_digit_ranges(const uint32_t *sort_scratch, const uint32_t *seg_block0, int n_seg,
+                                        int n_digits, uint2 *ranges, cudaStream_t st) {
+    if (n_seg <= 0 || n_digits <= 0 || n_digits > 255) return n_digits > 255 ? cudaErrorInvalidValue : cudaSuccess;
+    const int64_t n = (int64_t)n_seg * n_digits;
+    k_segment_digit_ranges<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sort_scratch, seg_block0, n_seg, n_digits,
+                                                                        ranges);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// Chained scan state: ticket, pad word, one 64-bit status word per chunk, error word.
+size_t scan_partials_size(int64_t n) { return (size_t)2 * ((n + kScanChunk - 1) / kScanChunk) + 4; }
 
 cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
-                                  uint32_t *partials, cudaStream_t st) {
+                                  uint32_t *partials, cudaStream_t st, uint32_t *err) {
     if (n <= 0) {
         if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
         return cudaSuccess;
@@ -610,12 +664,15 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
         note_launches(1);
         return cudaGetLastError();
     }
-    int64_t nb = (n + kScanChunk - 1) / kScanChunk;
-    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, vec, partials);
-    note_launches(1);
-    k_scan_partials<<<1, 1024, 0, st>>>(partials, nb, total);
-    note_launches(1);
-    k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, vec, partials);
+    const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    if (reinterpret_cast<uintptr_t>(partials) & 7) return cudaErrorMisalignedAddress;  // 64-bit status words
+    uint32_t *ticket = partials;
+    unsigned long long *status = reinterpret_cast<unsigned long long *>(partials + 2);
+    uint32_t *own_err = partials + 2 + 2 * nb;
+    cudaError_t e = cudaMemsetAsync(partials, 0, 4 * scan_partials_size(n), st);
+    if (e != cudaSuccess) return e;
+    k_scan_onepass<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, vec, ticket, status, total,
+                                                          err ? err : own_err);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -691,7 +748,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
                                                        nblocks, seg_block0, n_seg);
         note_launches(1);
         cudaError_t e = launch_exclusive_scan(counts, counts, (int64_t)256 * nblocks, nullptr,
-                                              partials, st);
+                                              partials, st, err);
         if (e != cudaSuccess) return e;
         const bool last = pass == passes - 1;
         k_radix_scatter<<<grid, kSortThreads, 0, st>>>(keys[cur], vals[cur],
