@@ -501,8 +501,8 @@ GC_API gc_status gc_saved_pixel_state(gc_context *ctx, const gc_saved *saved, fl
                                       void *stream);
 
 /*
- * L1 photometric distortion of a rendered image against a target (the distortion term of
- * the rate-distortion training loss, Sec. 3.3, in its plain L1 form):
+ * L1 photometric distortion of a rendered image against a target (the L1 part of the colour
+ * loss of the rate-distortion training, Sec. 3.3; its D-SSIM part is not built):
  *   loss = scale * sum_i |image_i - target_i|,  dL_dimage_i = scale * sign(image_i - target_i),
  * sign(0) = 0; scale = 1 / n gives the mean.  image, target, dL_dimage: device, n floats
  * each (any layout, the same for all three); loss: device, one float.  Either output may be

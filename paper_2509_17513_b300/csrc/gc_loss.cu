@@ -1,5 +1,6 @@
-// gc_loss.cu - the L1 photometric distortion of a rendered image against a target image,
-// the distortion term of the rate-distortion training loss (Sec. 3.3) in the plain L1 form:
+// gc_loss.cu - the L1 photometric distortion of a rendered image against a target image: the
+// L1 part of the colour loss of the rate-distortion training (Sec. 3.3, weighted there by
+// 1 - lambda_ssim beside a D-SSIM term, which is not built here):
 //   loss = scale * sum_i |image_i - target_i|,   dL/dimage_i = scale * sign(image_i - target_i)
 // with sign(0) = 0 (scale = 1 / n gives the mean).  One pass reads both images and writes the
 // gradient; the loss is summed deterministically: a fixed grid writes one FP64 partial per
