@@ -27,9 +27,11 @@ namespace {
 template <int TW, int TH, int NL>
 __global__ void __launch_bounds__(256) k_blend_levels_fwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
-    const float4 *__restrict__ ranked, int W, int H, int ntx, float bg0, float bg1, float bg2, int membership,
-    LevelPtrs out, float *__restrict__ lv_T, uint32_t *__restrict__ lv_last) {
+    const float4 *__restrict__ ranked, int W, int H, RenderParams rp, LevelPtrs out, float *__restrict__ lv_T,
+    uint32_t *__restrict__ lv_last) {
     constexpr int L = NL;
+    const int ntx = rp.ntx;
+    const float bg0 = rp.bg[0], bg1 = rp.bg[1], bg2 = rp.bg[2];
     __shared__ __align__(16) FwdSmem sm;
     __shared__ uint8_t lay[256];
     const int tile = blockIdx.x, tx = tile % ntx, ty = tile / ntx;
@@ -60,12 +62,10 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
                 const float4 a = ranked[kRec * (size_t)r];
                 const float4 bb = ranked[kRec * (size_t)r + 1];
                 const float4 c = ranked[kRec * (size_t)r + 2];
-                uint32_t cm, rm;
-                rect_masks<TW, TH>(c, tx, ty, membership, cm, rm);
                 sm.a[threadIdx.x] = a;
                 sm.b[threadIdx.x] = make_float2(bb.x, bb.y);
                 sm.c[threadIdx.x] = make_float4(bb.z, bb.w, c.x, 0.f);
-                store_masks_by_warp<TW>(sm.m, (int)threadIdx.x, cm, rm);
+                store_entry_masks<TW, TH>(sm.m, (int)threadIdx.x, a, c, ranked[kRec * (size_t)r + 3], tx, ty, rp);
                 lay[threadIdx.x] = (uint8_t)min(__float_as_int(c.y), 31);
             }
         }
@@ -222,8 +222,6 @@ __global__ void __launch_bounds__(256, 4) k_blend_levels_bwd(
                 const float4 a = ranked[kRec * (size_t)r];
                 const float4 bb = ranked[kRec * (size_t)r + 1];
                 const float4 c = ranked[kRec * (size_t)r + 2];
-                uint32_t cm, rm;
-                rect_masks<TW, TH>(c, tx, ty, rp.membership, cm, rm);
                 RowGeom g;
                 row_geom(a, c, ranked[kRec * (size_t)r + 3], rp, g);
                 const float4 r4 = ranked[kRec * (size_t)r + 4];
@@ -231,7 +229,15 @@ __global__ void __launch_bounds__(256, 4) k_blend_levels_bwd(
                 sm.b[threadIdx.x] = make_float2(bb.x, bb.y);
                 sm.c[threadIdx.x] = make_float4(bb.z, bb.w, c.x, a.z * kUnscaleDiag);
                 sm.d[threadIdx.x] = make_float2(a.w * kUnscaleOff, bb.x * kUnscaleDiag);
-                store_masks_by_warp<TW>(sm.m, (int)threadIdx.x, cm, rm);
+                if (rp.membership == GC_MEMBER_PIXEL && g.cull) {  // alpha-footprint block masks
+#pragma unroll
+                    for (int w = 0; w < 8; ++w)
+                        sm.m[w * 256 + threadIdx.x] = block_alpha_mask<TW, TH>(g, tx, ty, w);
+                } else {
+                    uint32_t cm, rm;
+                    rect_masks<TW, TH>(c, tx, ty, rp.membership, cm, rm);
+                    store_masks_by_warp<TW>(sm.m, (int)threadIdx.x, cm, rm);
+                }
                 sm.e[threadIdx.x] = offsets[r] + entry_index(g, r4, tx, ty, rp, W, H);
                 sm.lay[threadIdx.x] = (uint8_t)min(__float_as_int(c.y), 15);
             }
@@ -382,8 +388,7 @@ cudaError_t launch_blend_levels_fwd(const uint2 *ranges, const uint32_t *sorted_
                                     float *lv_T, uint32_t *lv_last, cudaStream_t st) {
     const unsigned tiles = (unsigned)(rp.ntx * rp.nty);
     if (tiles == 0) return cudaSuccess;
-#define GC_LV_ARGS ranges, sorted_vals, ranked, cam.width, cam.height, rp.ntx, rp.bg[0], rp.bg[1], rp.bg[2], \
-                   rp.membership, out, lv_T, lv_last
+#define GC_LV_ARGS ranges, sorted_vals, ranked, cam.width, cam.height, rp, out, lv_T, lv_last
 #define GC_LV_CASE(NLV)                                                                                       \
     case NLV:                                                                                                 \
         if (rp.tile_w == 16) k_blend_levels_fwd<16, 16, NLV><<<tiles, 256, 0, st>>>(GC_LV_ARGS);             \

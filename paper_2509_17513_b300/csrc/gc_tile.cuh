@@ -67,12 +67,59 @@ __device__ __forceinline__ void store_masks(uint32_t *m8, uint32_t cm, uint32_t 
                        warp_mask<TW>(cm, rm, 7));
 }
 
+// Mask of warp w's 8 x 4 block (bit 8 r + c = pixel (c, r) of the block) that an entry's alpha
+// footprint can reach: binning step 15 evaluated on the block's band of four pixel rows
+// instead of the tile row (the same FP32 operation sequence; a pixel left out has alpha below
+// 1/255, so the blends skip nothing they would have blended), clipped to the pixel rectangle.
+// Needs the alpha footprint (g.cull) and pixel-square membership.
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t block_alpha_mask(const RowGeom &g, int tx, int ty, int w) {
+    constexpr int BX = TW / 8;
+    const int bx0 = tx * TW + (w % BX) * 8, by0 = ty * TH + (w / BX) * 4;
+    const int r0 = max(by0, g.y0), r1 = min(by0 + 3, g.y1);
+    if (r0 > r1) return 0u;
+    const float d0 = fsub(fadd((float)r0, 0.5f), g.v), d1 = fsub(fadd((float)r1, 0.5f), g.v);
+    const float dr = fminf(fmaxf(-g.sy, d0), d1), dl = fminf(fmaxf(g.sy, d0), d1);
+    const float qr = fsub(g.at, fmul(fmul(g.detc, dr), dr)), ql = fsub(g.at, fmul(fmul(g.detc, dl), dl));
+    const float xr = fmul(fsub(__fsqrt_rn(fmaxf(qr, 0.f)), fmul(g.ib, dr)), g.ria);
+    const float xl = fmul(fsub(-fmul(g.ib, dl), __fsqrt_rn(fmaxf(ql, 0.f))), g.ria);
+    float fx0 = ceilf(fsub(fadd(g.u, xl), 0.5f)), fx1 = floorf(fsub(fadd(g.u, xr), 0.5f));
+    fx0 = fmaxf(fx0, (float)max(g.x0, bx0));
+    fx1 = fminf(fx1, (float)min(g.x1, bx0 + 7));
+    if (!(fx0 <= fx1)) return 0u;
+    const int c0 = (int)fx0 - bx0, c1 = (int)fx1 - bx0;
+    const uint32_t cb = (0xffu >> (7 - c1)) & (0xffu << c0);
+    const uint32_t rb = (0xfu >> (3 - (r1 - by0))) & (0xfu << (r0 - by0));
+    const uint32_t spread = (rb & 1u) | ((rb & 2u) << 7) | ((rb & 4u) << 14) | ((rb & 8u) << 21);
+    return cb * spread;
+}
+
 // The same masks stored warp-major (m[w * 256 + t] for entry t), so that a warp reads
 // the masks of 32 consecutive entries with one conflict-free load.
 template <int TW>
 __device__ __forceinline__ void store_masks_by_warp(uint32_t *m, int t, uint32_t cm, uint32_t rm) {
 #pragma unroll
     for (int w = 0; w < 8; ++w) m[w * 256 + t] = warp_mask<TW>(cm, rm, w);
+}
+
+// Warp-major masks of an entry (record words a, c, r3): the alpha-footprint block masks when
+// the footprint applies (alpha cull on, pixel-square membership, a proper conic), else the
+// pixel rectangle's masks.
+template <int TW, int TH>
+__device__ __forceinline__ void store_entry_masks(uint32_t *m, int t, const float4 &a, const float4 &c,
+                                                  const float4 &r3, int tx, int ty, const RenderParams &rp) {
+    uint32_t cm, rm;
+    rect_masks<TW, TH>(c, tx, ty, rp.membership, cm, rm);
+    if (rp.membership == GC_MEMBER_PIXEL && rp.alpha_cull) {
+        RowGeom g;
+        row_geom(a, c, r3, rp, g);
+        if (g.cull) {
+#pragma unroll
+            for (int w = 0; w < 8; ++w) m[w * 256 + t] = block_alpha_mask<TW, TH>(g, tx, ty, w);
+            return;
+        }
+    }
+    store_masks_by_warp<TW>(m, t, cm, rm);
 }
 
 // Shared staging of one batch of up to 256 list entries for the forward blend:
