@@ -18,6 +18,7 @@
 // same stable orders and the same per-tile blend run on the same data.
 #include <cuda_runtime.h>
 
+#include "gc_bucket.cuh"
 #include "gc_chain.cuh"
 #include "gc_project.cuh"
 #include "gc_state.cuh"
@@ -33,6 +34,9 @@ struct __align__(16) BatchReq {
     int64_t item_base;
     int64_t tile_base;
     int64_t pixel_base;
+    int64_t row_base;   // row binning: global tile row of the request's row 0
+    int64_t cell_base;  // row binning: first (row, chunk) cell of the request
+    int64_t n_chunks;   // row binning: chunks of 32 items (the request's padded items / 32)
     const float *group_q, *group_t;
     int n_groups;
     int frame;
@@ -68,6 +72,37 @@ __device__ __forceinline__ int find_req(const int64_t *base, int n, int64_t x) {
     }
     return lo;
 }
+
+// Row binning over a batch (gc_bucket.cuh): chunk c = items 32 c .. 32 c + 31 (requests are
+// padded to radix tiles, so a chunk never straddles two), cells and global rows request by
+// request, tiles at the request's tile base.
+struct BatchBucketMap {
+    const BatchReq *reqs;
+    const int64_t *item_base, *row_base;
+    int n_req;
+    __device__ __forceinline__ void chunk(int64_t c, BucketChunk &ci) const {
+        const int64_t item = c * 32;
+        const BatchReq &R = reqs[find_req(item_base, n_req, item)];
+        ci.rp = R.rp;
+        ci.W = R.cam.width;
+        ci.H = R.cam.height;
+        ci.n_rows = R.rp.nty;
+        ci.cell0 = R.cell_base + (item - R.item_base) / 32;
+        ci.stride = R.n_chunks;
+        ci.row0 = R.row_base;
+        ci.r0 = item;
+        const int64_t left = R.n_sel - (item - R.item_base);
+        ci.n_valid = left <= 0 ? 0 : (left < 32 ? (int)left : 32);
+    }
+    __device__ __forceinline__ void row(int64_t gr, BucketRow &ri) const {
+        const BatchReq &R = reqs[find_req(row_base, n_req, gr)];
+        const int64_t y = gr - R.row_base;
+        ri.cell = R.cell_base + y * R.n_chunks;
+        ri.n_cells = R.n_chunks;
+        ri.tile0 = R.tile_base + y * R.rp.ntx;
+        ri.ntx = R.rp.ntx;
+    }
+};
 
 // The request-independent activations of every Gaussian (scales, alpha level), once per batch.
 template <int PREC>
@@ -463,6 +498,7 @@ struct BatchState {
     bool k_exact = false;
     gc_options opt{};
     DevBuf reqs_dev, item_base, tile_base, seg_items, ebase, eshift, ecount, seg_entries, dimg_dev;
+    DevBuf row_base, row_shift;  // row binning: per request its first global tile row; per row the pad shift
     DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
         final_T, n_contrib, words, counter, scratch, act;
     DevBuf part, g2d, mcontrib, gpartial;
@@ -470,7 +506,7 @@ struct BatchState {
 
     ~BatchState() {
         DevBuf *bufs[] = {&reqs_dev, &item_base, &tile_base, &seg_items, &ebase, &eshift, &ecount,
-                          &seg_entries, &dimg_dev, &rec, &ranked, &dkeys[0], &dkeys[1], &dvals[0],
+                          &seg_entries, &dimg_dev, &row_base, &row_shift, &rec, &ranked, &dkeys[0], &dkeys[1], &dvals[0],
                           &dvals[1], &touched, &touched_r, &offsets, &tkeys[0], &tkeys[1], &tvals[0],
                           &tvals[1], &ranges, &final_T, &n_contrib, &words, &counter, &scratch, &act,
                           &part, &g2d, &mcontrib, &gpartial};
@@ -534,11 +570,12 @@ struct Sizer {
 gc_status build_table(gc_context *ctx, const gc_gaussians *g, const gc_motion *frames, int n_frames,
                       int n_groups, const gc_request *reqs, int n_req, const gc_options &o,
                       std::vector<gc::BatchReq> &tab, int64_t &items, int64_t &tiles, int64_t &pixels,
-                      int &kbits) {
+                      int &kbits, int64_t &rows, int64_t &cells, bool &rows_fit) {
     const int64_t T = gc::radix_tile_keys();
     tab.assign(n_req, gc::BatchReq{});
-    items = tiles = pixels = 0;
+    items = tiles = pixels = rows = cells = 0;
     kbits = 1;
+    rows_fit = true;
     for (int q = 0; q < n_req; ++q) {
         const gc_request &rq = reqs[q];
         const gc_camera *cam = &rq.camera;
@@ -575,7 +612,14 @@ gc_status build_table(gc_context *ctx, const gc_gaussians *g, const gc_motion *f
         R.sel = make_selection(g, rq.layer_mask, n_sel);
         R.n_sel = n_sel;
         R.item_base = items;
-        items += (n_sel + T - 1) / T * T;
+        const int64_t padded_items = (n_sel + T - 1) / T * T;
+        items += padded_items;
+        R.row_base = rows;
+        rows += R.rp.nty;
+        R.n_chunks = padded_items / 32;
+        R.cell_base = cells;
+        cells += (int64_t)R.rp.nty * R.n_chunks;
+        rows_fit = rows_fit && gc::bucket_binning_fits(R.rp);
         R.tile_base = tiles;
         tiles += (int64_t)R.rp.ntx * R.rp.nty;
         R.pixel_base = pixels;
@@ -649,8 +693,10 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     std::vector<gc::BatchReq> tab;
     int64_t items, tiles, pixels;
     int kbits;
+    int64_t rows, cells;
+    bool rows_fit;
     if ((st = build_table(ctx, g, frames, n_frames, n_groups, reqs, n_req, o, tab, items, tiles, pixels,
-                          kbits)) != GC_OK)
+                          kbits, rows, cells, rows_fit)) != GC_OK)
         return st;
     const bool same_table = B.reqs_dev.p && (int)B.reqs.size() == n_req &&
                             memcmp(B.reqs.data(), tab.data(), sizeof(gc::BatchReq) * n_req) == 0;
@@ -681,6 +727,8 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     need(B.item_base, 8 * (n_req + 1));
     need(B.tile_base, 8 * (n_req + 1));
     need(B.seg_items, 4 * (n_req + 1));
+    need(B.row_base, 8 * (n_req + 1));
+    need(B.row_shift, 4 * (size_t)(rows + 1));
     const int64_t ni = items > 0 ? items : 1;
     need(B.rec, (size_t)ni * 16 * gc::kRec);
     need(B.ranked, (size_t)ni * 16 * gc::kRec);
@@ -711,23 +759,27 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
         if (B.staged) GC_CUDA(ctx, cudaEventSynchronize(B.staged));
         else GC_CUDA(ctx, cudaEventCreateWithFlags(&B.staged, cudaEventDisableTiming));
         if ((st = grow_pinned(ctx, B.staging, B.staging_cap, (size_t)n_req)) != GC_OK) return st;
-        if ((st = grow_pinned(ctx, B.staging_base, B.staging_base_cap, (size_t)3 * (n_req + 1))) != GC_OK) return st;
+        if ((st = grow_pinned(ctx, B.staging_base, B.staging_base_cap, (size_t)4 * (n_req + 1))) != GC_OK) return st;
         memcpy(B.staging, tab.data(), sizeof(gc::BatchReq) * n_req);
         int64_t *ib = B.staging_base, *tb = B.staging_base + (n_req + 1);
         uint32_t *si = reinterpret_cast<uint32_t *>(B.staging_base + 2 * (n_req + 1));
+        int64_t *rb = B.staging_base + 3 * (n_req + 1);
         for (int q = 0; q < n_req; ++q) {
             ib[q] = tab[q].item_base;
             tb[q] = tab[q].tile_base;
             si[q] = (uint32_t)(tab[q].item_base / T);
+            rb[q] = tab[q].row_base;
         }
         ib[n_req] = items;
         tb[n_req] = tiles;
         si[n_req] = (uint32_t)(items / T);
+        rb[n_req] = rows;
         GC_CUDA(ctx, cudaMemcpyAsync(B.reqs_dev.p, B.staging, sizeof(gc::BatchReq) * n_req,
                                      cudaMemcpyHostToDevice, s));
         GC_CUDA(ctx, cudaMemcpyAsync(B.item_base.p, ib, 8 * (n_req + 1), cudaMemcpyHostToDevice, s));
         GC_CUDA(ctx, cudaMemcpyAsync(B.tile_base.p, tb, 8 * (n_req + 1), cudaMemcpyHostToDevice, s));
         GC_CUDA(ctx, cudaMemcpyAsync(B.seg_items.p, si, 4 * (n_req + 1), cudaMemcpyHostToDevice, s));
+        GC_CUDA(ctx, cudaMemcpyAsync(B.row_base.p, rb, 8 * (n_req + 1), cudaMemcpyHostToDevice, s));
         GC_CUDA(ctx, cudaEventRecord(B.staged, s));
         B.reqs = tab;
     }
@@ -783,44 +835,66 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
         B.k_exact = true;
     }
     const int64_t kk = K > 0 ? K : 1;
+    // row binning (every request within 255 tile columns): the lists in per-(request, tile row)
+    // segments padded to whole radix tiles, one segmented pass on the column; room for the
+    // padding beyond the capacity K (which counts the entries, padded per request)
+    const int64_t kpad = (kk + rows * T + 3) & ~int64_t(3);
+    const bool by_rows = rows_fit && rows > 0 && kpad <= 0xFFFFFFF0ll;
+    const int64_t kalloc = by_rows ? kpad : kk;
     for (int b = 0; b < 2; ++b) {
-        need(B.tkeys[b], (size_t)kk * 4 + 16);
-        need(B.tvals[b], (size_t)kk * 4 + 16);
+        need(B.tkeys[b], (size_t)kalloc * 4 + 16);
+        need(B.tvals[b], (size_t)kalloc * 4 + 16);
     }
-    need(B.scratch, 4 * std::max(gc::radix_scratch_words(kk), gc::scan_partials_size(ni)));
+    const size_t bwords = by_rows ? ((gc::bucket_words(cells, (int)rows) + 63) & ~size_t(63)) : 0;
+    need(B.scratch, 4 * (bwords + std::max(gc::radix_scratch_words(kalloc), gc::scan_partials_size(ni))));
     if (need.st != GC_OK) return need.st;
     scratch = B.scratch.as<uint32_t>();
     B.K_cap = K;
-    if (K > 0 && items > 0) {
+    uint32_t *tk[2] = {B.tkeys[0].as<uint32_t>(), B.tkeys[1].as<uint32_t>()};
+    uint32_t *tv[2] = {B.tvals[0].as<uint32_t>(), B.tvals[1].as<uint32_t>()};
+    if (by_rows) {
+        const gc::BatchBucketMap map{rq_dev, ib_dev, B.row_base.as<int64_t>(), n_req};
         GC_CUDA(ctx, mark(GC_STAGE_EMIT));
-        const int64_t threads = ((items + 31) / 32) * 32;
-        gc::k_batch_emit<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-            B.ranked.as<float4>(), B.offsets.as<uint32_t>(), B.touched_r.as<uint32_t>(), rq_dev, ib_dev, n_req,
-            B.eshift.as<uint32_t>(), items, (uint32_t)K, words + 2, B.tkeys[0].as<uint32_t>(),
-            B.tvals[0].as<uint32_t>());
-        gc::note_launches(1);
-        gc::k_batch_pad_fill<<<n_req, 256, 0, s>>>(B.ebase.as<uint32_t>(), B.ecount.as<uint32_t>(), (uint32_t)K,
-                                                   words + 2, B.tkeys[0].as<uint32_t>(), B.tvals[0].as<uint32_t>());
-        gc::note_launches(1);
-        GC_CUDA(ctx, cudaGetLastError());
+        if (K > 0 && items > 0)
+            GC_CUDA(ctx, gc::bucket_place(B.ranked.as<float4>(), words, words + 2, B.touched_r.as<uint32_t>(), map, items / 32,
+                                          (int)rows, cells, tk[0], tv[0], (uint32_t)kk, (uint32_t)kalloc, words,
+                                          B.row_shift.as<uint32_t>(), scratch, nullptr, s));
         GC_CUDA(ctx, mark(GC_STAGE_TILE_SORT));
-        uint32_t *tk[2] = {B.tkeys[0].as<uint32_t>(), B.tkeys[1].as<uint32_t>()};
-        uint32_t *tv[2] = {B.tvals[0].as<uint32_t>(), B.tvals[1].as<uint32_t>()};
-        GC_CUDA(ctx, gc::radix_sort_pairs(tk, tv, K, words + 2, kbits, scratch, &B.tile_buf, s, words + 1,
-                                          /*keys_out=*/true, B.seg_entries.as<uint32_t>(), n_req));
-    }
-    GC_CUDA(ctx, mark(GC_STAGE_RANGES));
-    if (tiles > 0) GC_CUDA(ctx, cudaMemsetAsync(B.ranges.p, 0, (size_t)tiles * 8, s));
-    if (K > 0 && items > 0) {
-        // ranges from the sorted keys: a difference grid filled by the preprocess costs
-        // contended integer atomics, measured slower
-        const int64_t blocks = std::max<int64_t>(std::min<int64_t>((K / 4 + 255) / 256, 148 * 16), 1);
-        gc::k_batch_key_ranges<<<(unsigned)blocks, 256, 0, s>>>(B.tkeys[B.tile_buf].as<uint32_t>(),
-                                                                B.ebase.as<uint32_t>(), B.ecount.as<uint32_t>(),
-                                                                tb_dev, n_req, words + 2, (uint32_t)K,
-                                                                B.ranges.as<uint2>());
-        gc::note_launches(1);
-        GC_CUDA(ctx, cudaGetLastError());
+        if (K > 0 && items > 0)
+            GC_CUDA(ctx, gc::bucket_sort(tk, tv, (uint32_t)kalloc, words, (int)rows, cells, scratch, scratch + bwords,
+                                         &B.tile_buf, s));
+        GC_CUDA(ctx, mark(GC_STAGE_RANGES));
+        if (tiles > 0) GC_CUDA(ctx, cudaMemsetAsync(B.ranges.p, 0, (size_t)tiles * 8, s));
+        if (K > 0 && items > 0)
+            GC_CUDA(ctx, gc::bucket_ranges(map, (int)rows, cells, scratch, scratch + bwords, B.ranges.as<uint2>(), s));
+    } else {
+        if (K > 0 && items > 0) {
+            GC_CUDA(ctx, mark(GC_STAGE_EMIT));
+            const int64_t threads = ((items + 31) / 32) * 32;
+            gc::k_batch_emit<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+                B.ranked.as<float4>(), B.offsets.as<uint32_t>(), B.touched_r.as<uint32_t>(), rq_dev, ib_dev, n_req,
+                B.eshift.as<uint32_t>(), items, (uint32_t)K, words + 2, tk[0], tv[0]);
+            gc::note_launches(1);
+            gc::k_batch_pad_fill<<<n_req, 256, 0, s>>>(B.ebase.as<uint32_t>(), B.ecount.as<uint32_t>(), (uint32_t)K,
+                                                       words + 2, tk[0], tv[0]);
+            gc::note_launches(1);
+            GC_CUDA(ctx, cudaGetLastError());
+            GC_CUDA(ctx, mark(GC_STAGE_TILE_SORT));
+            GC_CUDA(ctx, gc::radix_sort_pairs(tk, tv, K, words + 2, kbits, scratch, &B.tile_buf, s, words + 1,
+                                              /*keys_out=*/true, B.seg_entries.as<uint32_t>(), n_req));
+        }
+        GC_CUDA(ctx, mark(GC_STAGE_RANGES));
+        if (tiles > 0) GC_CUDA(ctx, cudaMemsetAsync(B.ranges.p, 0, (size_t)tiles * 8, s));
+        if (K > 0 && items > 0) {
+            // ranges from the sorted keys: a difference grid filled by the preprocess costs
+            // contended integer atomics, measured slower
+            const int64_t blocks = std::max<int64_t>(std::min<int64_t>((K / 4 + 255) / 256, 148 * 16), 1);
+            gc::k_batch_key_ranges<<<(unsigned)blocks, 256, 0, s>>>(tk[B.tile_buf], B.ebase.as<uint32_t>(),
+                                                                    B.ecount.as<uint32_t>(), tb_dev, n_req, words + 2,
+                                                                    (uint32_t)K, B.ranges.as<uint2>());
+            gc::note_launches(1);
+            GC_CUDA(ctx, cudaGetLastError());
+        }
     }
     GC_CUDA(ctx, mark(GC_STAGE_BLEND));
     GC_CUDA(ctx, cudaMemsetAsync(B.counter.p, 0, 8, s));

@@ -180,19 +180,16 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
 // Buffers must hold n_max rounded up to 4 elements (tiles are copied in 16-byte units).
 // A bounded wait that runs out sets kErrTimeout in *err (device word).
 // Segmented mode (seg_block0 != NULL, device array of n_seg + 1 block indices in units
-// of radix_tile_keys()): every segment is sorted on its own and stays in place.
+// of radix_tile_keys()): every segment is sorted on its own and stays in place; the last
+// pass leaves its scanned per-block digit counts at the start of `scratch`, segment-major
+// and digit-major within a segment (digit d of the segment with first block b0 and nb
+// blocks starts at scratch[256 b0 + d nb]; gc_bucket.cuh reads tile ranges from them).
 size_t radix_scratch_words(int64_t n_max);
 int radix_tile_keys();
 cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
                              const uint32_t *n_dev, int end_bit, uint32_t *scratch, int *out_buf,
                              cudaStream_t st, uint32_t *err, bool keys_out = true,
                              const uint32_t *seg_block0 = nullptr, int n_seg = 0);
-
-// After a one-pass segmented radix_sort_pairs (8-bit digit) with scratch `sort_scratch`:
-// ranges[s * n_digits + d] = [start, end) of digit d < n_digits <= 255 in segment s (written
-// only when nonempty; ranges must be zeroed).
-cudaError_t launch_segment_digit_ranges(const uint32_t *sort_scratch, const uint32_t *seg_block0, int n_seg,
-                                        int n_digits, uint2 *ranges, cudaStream_t st);
 
 // Emit (tile key, rank) for every tile of every row interval of every visible Gaussian,
 // in rank order (image W x H).  Entries at positions >= cap are dropped (fixed-capacity

@@ -203,10 +203,17 @@ def test_batch_graph_replay_and_capacity(gc, small):
         r.batch_forward(gs, frames, trip[:3], saved)
     del graph
 
-    # too small a capacity: nothing emitted, reported by gc_check
+    # too small a capacity: nothing placed (the images are the background, the backward
+    # writes no partial and gives zero gradients), reported by gc_check
     rs = gc.Renderer(0, key_capacity=2048)
     ss = gc.Saved(rs)
-    rs.batch_forward(gs, frames, trip, ss)
+    imgs = rs.batch_forward(gs, frames, trip, ss)
+    gz = rs.batch_backward(ss, gs, frames, dls)
+    torch.cuda.synchronize()
+    for x in imgs:
+        assert not x.any()
+    for k, v in gz.items():
+        assert not v.any(), k
     with pytest.raises(gc.GCError, match="capacity"):
         rs.check()
 
@@ -334,3 +341,36 @@ def test_autotuner_picks_a_measured_configuration(gc, small):
     for q, req in enumerate(reqs):
         one, _ = _single(gc, r, gs, frames, req)
         assert torch.equal(imgs[q], one), q
+
+
+def test_batch_with_a_request_over_255_tile_columns(gc, small):
+    """A 4,200 x 1,050 px request (263 columns of 16 px tiles) is past binning by tile row, so the
+    batch takes the per-request key sort instead: every image still equals its single render
+    (the wide one takes the single path's key sort too), and the gradients the in-order sum of
+    the single-request gradients (up to the order of the float additions of the chain rule)."""
+    scene, motion, reqs = small
+    wide = scenes.Request(scenes.orbit_camera(0.8, 4.0, 4200, 1050), 1, 0b001111)
+    reqs = list(reqs[:3]) + [wide] + list(reqs[3:])
+    r = gc.Renderer(0)
+    gs = gc.GaussianSet.from_scene(scene)
+    frames = _frames(gc, motion)
+    saved = gc.Saved(r)
+    imgs = r.batch_forward(gs, frames, _batch_triplets(reqs), saved)
+    gen = torch.Generator(device="cuda").manual_seed(9)
+    dls = [torch.randn(x.shape, generator=gen, device="cuda") for x in imgs]
+    got = {k: v.clone() for k, v in r.batch_backward(saved, gs, frames, dls).items()}
+    r.check()
+    acc = {k: torch.zeros_like(v) for k, v in got.items()}
+    for q, req in enumerate(reqs):
+        one, g = _single(gc, r, gs, frames, req, dls[q])
+        assert torch.equal(imgs[q], one), q
+        for k in NAMES:
+            acc[k] += g[k]
+        if req.frame >= 0:
+            acc["group_q"][req.frame] += g["group_q"]
+            acc["group_t"][req.frame] += g["group_t"]
+    torch.cuda.synchronize()
+    assert imgs[3].any()
+    for k in acc:
+        a, b = got[k].double(), acc[k].double()
+        assert (a - b).abs().max() <= 1e-5 * b.abs().max() + 1e-7, k

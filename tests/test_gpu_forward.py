@@ -154,7 +154,17 @@ def test_fixed_capacity(gc, hier_small):
     assert np.array_equal(a["image"], b["image"])
     r = gc.Renderer(0, key_capacity=k // 2)
     gs = gc.GaussianSet.from_scene(scene)
-    r.forward(gs, gc.MotionFrame.from_motion(motion, 1), 63, cam)
+    mo = gc.MotionFrame.from_motion(motion, 1)
+    saved = gc.Saved(r)
+    img = r.forward(gs, mo, 63, cam, saved)
+    # over its capacity a frame places no entry (8 tile columns: binning by tile row), so the
+    # image is the background and the backward, whose partials buffer the capacity sizes,
+    # writes no partial
+    g = r.backward(saved, gs, mo, torch.ones_like(img))
+    torch.cuda.synchronize()
+    assert not img.any()
+    for name, v in g.items():
+        assert not v.any(), name
     with pytest.raises(gc.GCError) as e:
         r.check()
     assert "GC_ERR_CAPACITY" in str(e.value)
@@ -218,3 +228,24 @@ def test_alpha_cull_changes_lists_not_results(gc, tile):
         a, b = out[True][3][k], out[False][3][k]
         assert float((a - b).abs().max()) <= 1e-5 * float(b.abs().max()), k
     assert out[True][4] < 0.85 * out[False][4]
+
+
+def test_frame_over_255_tile_columns(gc, hier_small):
+    """4,160 x 1,040 px (260 columns of 16 px tiles): past binning by tile row, the frame takes the
+    full-key tile sort; its lists are bit-exact against the oracle's FP32 binning mirror and
+    its pixels within the bar on 4,096 seeded samples."""
+    scene, motion = hier_small
+    cam = scenes.orbit_camera(0.9, 4.0, 4160, 1040)
+    gpu = _render_gpu(gc, scene, motion, 1, cam, 63)
+    opts = oracle.default_options()
+    bins = oracle.bin_f32(scene, motion, 1, cam, opts, 63)
+    tiles = oracle.tile_lists(bins, cam)
+    assert len(tiles["gauss_of_entry"]) > 0
+    assert np.array_equal(gpu["ids"], tiles["gauss_of_entry"])
+    assert np.array_equal(gpu["ranges"][:, 1] - gpu["ranges"][:, 0], tiles["ranges"][:, 1] - tiles["ranges"][:, 0])
+    pix = scenes.sample_pixels(41, cam.width, cam.height, 4096)
+    ref = oracle.render(scene, motion, 1, cam, opts, 63, pixels=pix, bins=bins)
+    ok = ~ref["ambiguous"]
+    g = gpu["image"][:, pix[:, 1], pix[:, 0]].T
+    assert ok.mean() > 0.95
+    assert np.abs(g - ref["image"]).max(axis=1)[ok].max() <= PIX_TOL
