@@ -11,7 +11,7 @@
 //    still bounded, and a wait that runs out sets the error word.
 //  * histogram -> scan -> scatter per digit (longer sorts, and the segmented sorts of the
 //    batched path, whose segments need per-segment offsets), where no CTA waits on another.
-// The scan is reduce-then-scan (three launches, or one CTA for short inputs).
+// The scan is one chained pass (decoupled look-back), or one CTA for short inputs.
 //
 // Scatter stability: each warp owns a contiguous segment of its CTA's tile
 // (kSortItems rows of 32 keys) and ranks its keys row by row (ballot multisplit),
@@ -225,24 +225,34 @@ __device__ __forceinline__ int64_t device_count(const uint32_t *n_dev, int64_t n
     return n < n_max ? n : n_max;
 }
 
-// Index of (digit d, block b) in the histogram array.  Without segments the layout
-// is digit-major over all blocks.  With segments (seg_block0: S+1 nondecreasing block
-// indices, segment s = blocks [seg_block0[s], seg_block0[s+1])), each segment owns a
-// contiguous digit-major region in segment order, so one exclusive scan over the
-// array yields offsets that keep every segment within its own range; blocks past the
-// last segment hold zero counts after all segments.
-__device__ __forceinline__ int64_t count_index(uint32_t d, int b, int nblocks, const uint32_t *seg_block0,
-                                               int n_seg) {
-    if (!seg_block0) return (int64_t)d * nblocks + b;
-    const int total = (int)seg_block0[n_seg];
-    if (b >= total) return (int64_t)256 * b + d;
-    int lo = 0, hi = n_seg - 1;  // last segment with seg_block0[s] <= b
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if ((int)seg_block0[mid] <= b) lo = mid; else hi = mid - 1;
-    }
-    const int b0 = (int)seg_block0[lo], nb = (int)seg_block0[lo + 1] - b0;
-    return (int64_t)256 * b0 + (int64_t)d * nb + (b - b0);
+// Index of (digit d, block b) in the histogram array: base + d * stride.  Without segments
+// the layout is digit-major over all blocks (base b, stride nblocks).  With segments
+// (seg_block0: S+1 nondecreasing block indices, segment s = blocks [seg_block0[s],
+// seg_block0[s+1])), each segment owns a contiguous digit-major region in segment order, so
+// one exclusive scan over the array yields offsets that keep every segment within its own
+// range: block b of the segment starting at b0 with nb blocks has base 256 b0 + (b - b0) and
+// stride nb, read from the per-block table blk (k_block_segments); blocks past the last
+// segment hold zero counts after all segments (base 256 b, stride 1).  Both loads are
+// independent, so a block pays one memory round trip for its index.
+struct SegIndex {
+    const uint32_t *seg_block0;  // NULL: unsegmented
+    const uint2 *blk;
+    int n_seg;
+};
+
+__device__ __forceinline__ uint2 count_index(int b, int nblocks, const SegIndex &sg) {
+    if (!sg.seg_block0) return make_uint2((uint32_t)b, (uint32_t)nblocks);
+    const int total = (int)sg.seg_block0[sg.n_seg];
+    const uint2 e = sg.blk[b];  // the table has a word pair for every block (unset past the last segment)
+    return b < total ? e : make_uint2(256u * (uint32_t)b, 1u);
+}
+
+// The per-block table of a segmented sort: CTA s writes (base, stride) of every block of
+// segment s.
+__global__ void __launch_bounds__(128) k_block_segments(const uint32_t *__restrict__ seg_block0,
+                                                        uint2 *__restrict__ blk) {
+    const uint32_t b0 = seg_block0[blockIdx.x], nb = seg_block0[blockIdx.x + 1] - b0;
+    for (uint32_t i = threadIdx.x; i < nb; i += 128) blk[b0 + i] = make_uint2(256u * b0 + i, nb);
 }
 
 // Peers of this lane: the lanes of the warp whose digit equals this lane's, among the
@@ -260,16 +270,28 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, int bits, uint32_t v
     return peers;
 }
 
+// The same for 8-bit digits (the bit count known at compile time).
+__device__ __forceinline__ uint32_t digit_peers8(uint32_t d, uint32_t valid) {
+    uint32_t peers = valid;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t t = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? t : ~t;
+    }
+    return peers;
+}
+
 // Per-CTA digit histogram, digit-major: counts[d * nblocks + b].  Keys are read with
 // 16-byte loads when the tile is full; each warp counts into its own shared row.
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__restrict__ keys,
                                                              const uint32_t *n_dev, int64_t n_max,
                                                              int shift, uint32_t mask,
                                                              uint32_t *__restrict__ counts,
-                                                             int nblocks, const uint32_t *seg_block0,
-                                                             int n_seg) {
+                                                             int nblocks, SegIndex sg) {
     __shared__ uint32_t wh[kWarps][256];
     const int warp = threadIdx.x >> 5;
+    const uint2 ci = count_index((int)blockIdx.x, nblocks, sg);  // in flight while the keys load
     for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0;
     __syncthreads();
     const int64_t n = device_count(n_dev, n_max);
@@ -294,7 +316,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
     uint32_t tot = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) tot += wh[w][threadIdx.x];
-    counts[count_index(threadIdx.x, blockIdx.x, nblocks, seg_block0, n_seg)] = tot;
+    counts[ci.x + threadIdx.x * ci.y] = tot;
 }
 
 // Stable scatter, persistent: each CTA walks tiles t = blockIdx.x, + gridDim.x, ...
@@ -309,7 +331,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *n_dev,
     int64_t n_max, int shift, uint32_t mask, const uint32_t *__restrict__ scanned, int nblocks,
-    uint32_t *err, const uint32_t *seg_block0, int n_seg) {
+    uint32_t *err, SegIndex sg) {
     __shared__ __align__(128) uint32_t skv[2][2][kSortTile];  // per stage: keys, values (then key-value pairs)
     __shared__ uint32_t wcnt[kWarps][256];
     __shared__ uint32_t gbase[256];
@@ -347,6 +369,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         const int nvalid = (int)((n - base) < kSortTile ? (n - base) : kSortTile);
         const bool has_next = t + (int)gridDim.x < ntiles;
         if (threadIdx.x == 0 && has_next) issue(t + gridDim.x, stage ^ 1);
+        const uint2 ci = count_index(t, nblocks, sg);  // in flight while the tile is ranked
         for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wcnt[0][0])[k] = 0;
         const bool ok = mbar_wait_bounded(&bar[stage], (uint32_t)(it >> 1) & 1u);
         if (__syncthreads_or(!ok)) {
@@ -361,21 +384,39 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         }
         uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
         const int wseg = warp * (32 * kSortItems);
+        if (nvalid == kSortTile && bits == 8) {
+            // full tile of 8-bit digits (every key valid, the bit count fixed): the common case
 #pragma unroll
-        for (int r = 0; r < kSortItems; ++r) {
-            const int li = wseg + r * 32 + lane;
-            const bool valid = li < nvalid;
-            key[r] = valid ? skv[stage][0][li] : 0xffffffffu;
-            val[r] = valid ? skv[stage][1][li] : 0u;
-            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-            const uint32_t d = (key[r] >> shift) & mask;
-            // narrow digits: one match instruction; 8-bit digits: ballots per digit bit
-            const uint32_t peers = bits < 8 ? __match_any_sync(0xffffffffu, d) & vmask : digit_peers(d, bits, vmask);
-            const uint32_t before = valid ? wcnt[warp][d] : 0u;
-            __syncwarp();
-            if (valid && (peers & lt) == 0) wcnt[warp][d] = before + (uint32_t)__popc(peers);
-            __syncwarp();
-            loc[r] = before + (uint32_t)__popc(peers & lt);
+            for (int r = 0; r < kSortItems; ++r) {
+                const int li = wseg + r * 32 + lane;
+                key[r] = skv[stage][0][li];
+                val[r] = skv[stage][1][li];
+                const uint32_t d = (key[r] >> shift) & 0xffu;
+                const uint32_t peers = digit_peers8(d, 0xffffffffu);
+                const uint32_t before = wcnt[warp][d];
+                __syncwarp();
+                if ((peers & lt) == 0) wcnt[warp][d] = before + (uint32_t)__popc(peers);
+                __syncwarp();
+                loc[r] = before + (uint32_t)__popc(peers & lt);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < kSortItems; ++r) {
+                const int li = wseg + r * 32 + lane;
+                const bool valid = li < nvalid;
+                key[r] = valid ? skv[stage][0][li] : 0xffffffffu;
+                val[r] = valid ? skv[stage][1][li] : 0u;
+                const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+                const uint32_t d = (key[r] >> shift) & mask;
+                // narrow digits: one match instruction; 8-bit digits: ballots per digit bit
+                const uint32_t peers =
+                    bits < 8 ? __match_any_sync(0xffffffffu, d) & vmask : digit_peers(d, bits, vmask);
+                const uint32_t before = valid ? wcnt[warp][d] : 0u;
+                __syncwarp();
+                if (valid && (peers & lt) == 0) wcnt[warp][d] = before + (uint32_t)__popc(peers);
+                __syncwarp();
+                loc[r] = before + (uint32_t)__popc(peers & lt);
+            }
         }
         __syncthreads();
         {
@@ -391,7 +432,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
             const uint32_t st = block_exclusive_scan<kSortThreads>(s, ws, &tot);
 #pragma unroll
             for (int w = 0; w < kWarps; ++w) wcnt[w][d] += st;   // tile position of warp w's first digit d
-            gbase[d] = scanned[count_index(d, t, nblocks, seg_block0, n_seg)] - st;  // output = gbase + tile position
+            gbase[d] = scanned[ci.x + (uint32_t)d * ci.y] - st;  // output = gbase + tile position
         }
         __syncthreads();
 #pragma unroll
@@ -620,34 +661,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep_scatter(
     }
 }
 
-// Ranges of the digits of every segment after a one-pass segmented sort, from the scanned
-// per-block digit counts it leaves in `counts` (segment-major, digit-major within a segment):
-// digit d of segment s starts at counts[256 b0 + d nb] (b0, nb: the segment's first block and
-// block count) and ends where digit d + 1 starts.  Thread per (segment, digit < n_digits),
-// digits < 255; empty ranges are not written.
-__global__ void k_segment_digit_ranges(const uint32_t *__restrict__ counts, const uint32_t *__restrict__ seg_block0,
-                                       int n_seg, int n_digits, uint2 *__restrict__ ranges) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n_seg * n_digits) return;
-    const int sg = (int)(i / n_digits), d = (int)(i - (int64_t)sg * n_digits);
-    const uint32_t b0 = seg_block0[sg], nb = seg_block0[sg + 1] - b0;
-    if (nb == 0u) return;
-    const uint32_t a = counts[(int64_t)256 * b0 + (int64_t)d * nb];
-    const uint32_t b = counts[(int64_t)256 * b0 + (int64_t)(d + 1) * nb];
-    if (b > a) ranges[i] = make_uint2(a, b);
-}
-
 }  // namespace
-
-cudaError_t launch_segment_digit_ranges(const uint32_t *sort_scratch, const uint32_t *seg_block0, int n_seg,
-                                        int n_digits, uint2 *ranges, cudaStream_t st) {
-    if (n_seg <= 0 || n_digits <= 0 || n_digits > 255) return n_digits > 255 ? cudaErrorInvalidValue : cudaSuccess;
-    const int64_t n = (int64_t)n_seg * n_digits;
-    k_segment_digit_ranges<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sort_scratch, seg_block0, n_seg, n_digits,
-                                                                        ranges);
-    note_launches(1);
-    return cudaGetLastError();
-}
 
 // Chained scan state: ticket, pad word, one 64-bit status word per chunk, error word.
 size_t scan_partials_size(int64_t n) { return (size_t)2 * ((n + kScanChunk - 1) / kScanChunk) + 4; }
@@ -679,6 +693,25 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
 
 int radix_tile_keys() { return kSortTile; }
 
+// Grid of the persistent scatter: every CTA that fits at once with the shared-memory carveout
+// at its maximum (at 48 registers and 42 KB of shared memory, five CTAs per SM), queried once.
+static int scatter_grid() {
+    static int cached = 0;
+    if (!cached) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+        cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radix_scatter, kSortThreads, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 4;
+        cudaGetLastError();
+        cached = sms * per_sm;
+    }
+    return cached;
+}
+
 // Classic layout: per-block digit counts + scan partials.  One-sweep layout: per pass
 // 256 digit counts, a ticket and 256 status words per tile.
 static size_t onesweep_words(int64_t nb, int passes) {
@@ -688,7 +721,8 @@ static size_t onesweep_words(int64_t nb, int passes) {
 size_t radix_scratch_words(int64_t n_max) {
     int64_t nb = (n_max + kSortTile - 1) / kSortTile;
     if (nb < 1) nb = 1;
-    const size_t classic = (size_t)(256 * nb) + scan_partials_size(256 * nb);
+    // counts, scan state, per-block segment table (two words per block, 8-byte aligned)
+    const size_t classic = (size_t)(256 * nb) + scan_partials_size(256 * nb) + 2 * (size_t)nb + 2;
     return n_max <= kOnesweepMaxKeys ? std::max(classic, onesweep_words(nb, kMaxPasses)) : classic;
 }
 
@@ -736,16 +770,28 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
         *out_buf = cur;
         return cudaGetLastError();
     }
-    const int grid = nblocks < 148 * 4 ? nblocks : 148 * 4;
+    const int grid = std::min(nblocks, scatter_grid());
     uint32_t *counts = scratch;
     uint32_t *partials = scratch + (size_t)256 * nblocks;
+    SegIndex sg{seg_block0, nullptr, n_seg};
+    if (seg_block0) {
+        size_t off = (size_t)256 * nblocks + scan_partials_size((int64_t)256 * nblocks);
+        off = (off + 1) & ~(size_t)1;
+        uint2 *blk = reinterpret_cast<uint2 *>(scratch + off);
+        if (reinterpret_cast<uintptr_t>(blk) & 7) return cudaErrorMisalignedAddress;
+        if (n_seg > 0) {
+            k_block_segments<<<(unsigned)n_seg, 128, 0, st>>>(seg_block0, blk);
+            note_launches(1);
+        }
+        sg.blk = blk;
+    }
     // balanced digit widths: ceil(end_bit / 8) passes of nearly equal width
     int shift = 0;
     for (int pass = 0; pass < passes; ++pass) {
         const int bits = (end_bit - shift + (passes - pass) - 1) / (passes - pass);
         const uint32_t mask = (1u << bits) - 1u;
         k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(keys[cur], n_dev, n_max, shift, mask, counts,
-                                                       nblocks, seg_block0, n_seg);
+                                                       nblocks, sg);
         note_launches(1);
         cudaError_t e = launch_exclusive_scan(counts, counts, (int64_t)256 * nblocks, nullptr,
                                               partials, st, err);
@@ -754,7 +800,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
         k_radix_scatter<<<grid, kSortThreads, 0, st>>>(keys[cur], vals[cur],
                                                        (last && !keys_out) ? nullptr : keys[cur ^ 1],
                                                        vals[cur ^ 1], n_dev, n_max, shift, mask,
-                                                       counts, nblocks, err, seg_block0, n_seg);
+                                                       counts, nblocks, err, sg);
         note_launches(1);
         cur ^= 1;
         shift += bits;
