@@ -185,6 +185,7 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
     rp.nty = (cam->height + o.tile_h - 1) / o.tile_h;
     rp.membership = o.membership;
     rp.alpha_cull = o.alpha_cull;
+    rp.list_packed = 0;  // set below when the lists are binned by tile row
     const int64_t n_tiles = (int64_t)rp.ntx * rp.nty;
     const int64_t hw = (int64_t)cam->width * cam->height;
 
@@ -248,11 +249,11 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
         // binning by tile row pads every row's segment to whole radix tiles: room for that
         // beyond the entries (the capacity counts entries only)
         const int64_t kpad = (kk + (int64_t)rp.nty * gc::radix_tile_keys() + 3) & ~int64_t(3);
-        const bool rows = gc::bucket_binning_fits(rp) && kpad <= 0xFFFFFFF0ll;
+        const bool rows = gc::bucket_binning_fits(rp, n_sel) && kpad <= 0xFFFFFFF0ll;
         const int64_t kalloc = rows ? kpad : kk;
         for (int b = 0; b < 2; ++b) {
             GC_CUDA(ctx, grow(S.tkeys[b], (size_t)kalloc * 4));
-            GC_CUDA(ctx, grow(S.tvals[b], (size_t)kalloc * 4));
+            if (!rows) GC_CUDA(ctx, grow(S.tvals[b], (size_t)kalloc * 4));  // row-binned lists: one word per entry
         }
         const size_t bucket_words = rows ? ((gc::bucket_scratch_words(n_sel, rp.nty) + 63) & ~size_t(63)) : 0;
         GC_CUDA(ctx, grow(ctx->scratch, 4 * (bucket_words + std::max(gc::radix_scratch_words(kalloc), scan_words))));
@@ -266,16 +267,17 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
             if (rows) {
                 GC_CUDA(ctx, grow(S.row_shift, (size_t)(rp.nty + 1) * 4));
                 GC_CUDA(ctx, gc::launch_bucket_place(S.ranked.as<float4>(), words, S.touched_r.as<uint32_t>(), n_sel,
-                                                     rp, cam->width, cam->height, tk[0], tv[0],
+                                                     rp, cam->width, cam->height, tk[0],
                                                      (uint32_t)std::min<int64_t>(K, 0xFFFFFFFFll), (uint32_t)kalloc,
                                                      words, S.row_shift.as<uint32_t>(), scratch, peak, s));
                 GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_TILE_SORT));
-                GC_CUDA(ctx, gc::launch_bucket_sort(tk, tv, (uint32_t)kalloc, words, n_sel, rp.nty, scratch,
+                GC_CUDA(ctx, gc::launch_bucket_sort(tk, (uint32_t)kalloc, words, n_sel, rp.nty, scratch,
                                                     scratch + bucket_words, &S.tile_buf, s));
                 GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_RANGES));
                 GC_CUDA(ctx, gc::launch_bucket_ranges(n_sel, scratch, scratch + bucket_words, rp,
                                                       S.ranges.as<uint2>(), s));
                 S.row_binned = true;
+                rp.list_packed = 1;
             } else {
                 GC_CUDA(ctx, gc::launch_emit(S.ranked.as<float4>(), S.offsets.as<uint32_t>(),
                                              S.touched_r.as<uint32_t>(), n_sel, rp, cam->width, cam->height,
@@ -292,7 +294,7 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
         GC_CUDA(ctx, cudaMemsetAsync(words, 0, 4, s));
     }
     S.K = K;
-    uint32_t *sorted_vals = (n_sel > 0 && K > 0) ? S.tvals[S.tile_buf].as<uint32_t>() : nullptr;
+    uint32_t *sorted_vals = (n_sel > 0 && K > 0) ? S.lists() : nullptr;
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_BLEND));
     if (levels) {
         GC_CUDA(ctx, grow(S.lv_T, (size_t)levels * hw * 4));
@@ -391,13 +393,13 @@ gc_status gc_saved_tile_lists(gc_context *ctx, const gc_saved *saved, int32_t *r
     if (capacity < K) return fail(ctx, GC_ERR_CAPACITY, "tile lists need %lld entries", (long long)K);
     const int64_t n_tiles = (int64_t)S.rp.ntx * S.rp.nty;
     if (S.row_binned && K > 0) {  // row segments carry padding: export the lists without it
-        GC_CUDA(ctx, gc::launch_row_lists_export(S.ranges.as<uint2>(), S.tvals[S.tile_buf].as<uint32_t>(),
+        GC_CUDA(ctx, gc::launch_row_lists_export(S.ranges.as<uint2>(), S.lists(),
                                                  S.row_shift.as<uint32_t>(), S.rp, S.dvals[S.depth_buf].as<uint32_t>(),
                                                  S.sel, ranges, gauss_ids, s));
     } else {
         GC_CUDA(ctx, cudaMemcpyAsync(ranges, S.ranges.p, (size_t)n_tiles * 8, cudaMemcpyDeviceToDevice, s));
         if (K > 0)
-            GC_CUDA(ctx, gc::launch_entries_to_global(S.tvals[S.tile_buf].as<uint32_t>(),
+            GC_CUDA(ctx, gc::launch_entries_to_global(S.lists(),
                                                       S.dvals[S.depth_buf].as<uint32_t>(), S.sel, K,
                                                       gauss_ids, s));
     }
@@ -536,7 +538,7 @@ static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, co
     GC_CUDA(ctx, grow(ctx->bwd_g2d, (size_t)S.n_sel * 9 * 4));
     GC_CUDA(ctx, grow(ctx->bwd_motion, (size_t)S.n_sel * 7 * 4));
     if (G && !S.per_gaussian) GC_CUDA(ctx, grow(ctx->bwd_group, gc::group_partial_floats(S.n_sel, G) * 4));
-    const uint32_t *sorted_vals = S.K > 0 ? S.tvals[S.tile_buf].as<uint32_t>() : nullptr;
+    const uint32_t *sorted_vals = S.K > 0 ? S.lists() : nullptr;
 
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_BLEND_BWD));
     ctx->bwd_part_clean = false;

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_blend_bwd(
     const float *__restrict__ dimg, float *__restrict__ part) {
     __shared__ __align__(16) BwdSmem sm;
     const int tile = blockIdx.x, ntx = rp.ntx;
-    const TileBwd o{final_T, n_contrib, dimg, rp, W, H, 0u};
+    const TileBwd o{final_T, n_contrib, dimg, rp, W, H, 0u, 0u};
     blend_bwd_tile<TW, TH>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, offsets, o, part, sm);
 }
 

@@ -91,6 +91,7 @@ struct BatchBucketMap {
         ci.stride = R.n_chunks;
         ci.row0 = R.row_base;
         ci.r0 = item;
+        ci.v0 = item - R.item_base;  // list words hold the rank within the request
         const int64_t left = R.n_sel - (item - R.item_base);
         ci.n_valid = left <= 0 ? 0 : (left < 32 ? (int)left : 32);
     }
@@ -294,7 +295,8 @@ __global__ void __launch_bounds__(256) k_batch_blend_fwd(const BatchReq *__restr
                 const uint2 rg = ranges[t];
                 s_tile = make_int4(local % R.rp.ntx, local / R.rp.ntx, (int)rg.x, (int)rg.y);
                 s_out = TileOut{R.image, final_T + R.pixel_base, n_contrib + R.pixel_base, nullptr, nullptr,
-                                R.rp.bg[0], R.rp.bg[1], R.rp.bg[2], R.cam.width, R.cam.height, R.rp.membership};
+                                R.rp.bg[0], R.rp.bg[1], R.rp.bg[2], R.cam.width, R.cam.height, R.rp.membership,
+                                list_rank_mask(R.rp), R.rp.list_packed ? (uint32_t)R.item_base : 0u};
             } else {
                 s_tile = make_int4(-1, 0, 0, 0);
             }
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(256) k_batch_blend_fwd(const BatchReq *__restr
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(kBwdThreads) k_batch_blend_bwd(const BatchReq *__restrict__ reqs,
+__global__ void __launch_bounds__(kBwdThreads, 6) k_batch_blend_bwd(const BatchReq *__restrict__ reqs,
                                                          const int64_t *__restrict__ tile_base, int n_req,
                                                          int64_t n_tiles, const uint2 *__restrict__ ranges,
                                                          const uint32_t *__restrict__ sorted_vals,
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_batch_blend_bwd(const BatchReq 
                 const uint2 rg = ranges[t];
                 s_tile = make_int4(local % R.rp.ntx, local / R.rp.ntx, (int)rg.x, (int)rg.y);
                 s_in = TileBwd{final_T + R.pixel_base, n_contrib + R.pixel_base, dimgs[q], R.rp, R.cam.width,
-                               R.cam.height, eshift[q]};
+                               R.cam.height, eshift[q], R.rp.list_packed ? (uint32_t)R.item_base : 0u};
             } else {
                 s_tile = make_int4(-1, 0, 0, 0);
             }
@@ -496,9 +498,15 @@ struct BatchState {
     int64_t n_items = 0, n_tiles = 0, n_pixels = 0, K_cap = 0;
     int key_bits = 1, depth_buf = 0, tile_buf = 0;
     bool k_exact = false;
+    bool row_binned = false;  // lists binned by tile row (one word per entry, in tkeys)
     gc_options opt{};
     DevBuf reqs_dev, item_base, tile_base, seg_items, ebase, eshift, ecount, seg_entries, dimg_dev;
     DevBuf row_base, row_shift;  // row binning: per request its first global tile row; per row the pad shift
+    // The sorted tile lists: one word per entry (column << 24 | rank within the request) in the
+    // last pass's keys when binned by tile row, else the values of the key sort.
+    uint32_t *lists() const {
+        return row_binned ? tkeys[tile_buf].as<uint32_t>() : tvals[tile_buf].as<uint32_t>();
+    }
     DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
         final_T, n_contrib, words, counter, scratch, act;
     DevBuf part, g2d, mcontrib, gpartial;
@@ -619,7 +627,7 @@ gc_status build_table(gc_context *ctx, const gc_gaussians *g, const gc_motion *f
         R.n_chunks = padded_items / 32;
         R.cell_base = cells;
         cells += (int64_t)R.rp.nty * R.n_chunks;
-        rows_fit = rows_fit && gc::bucket_binning_fits(R.rp);
+        rows_fit = rows_fit && gc::bucket_binning_fits(R.rp, n_sel);
         R.tile_base = tiles;
         tiles += (int64_t)R.rp.ntx * R.rp.nty;
         R.pixel_base = pixels;
@@ -637,6 +645,8 @@ gc_status build_table(gc_context *ctx, const gc_gaussians *g, const gc_motion *f
         R.image = rq.image;
     }
     if (items > 0x7FFFFFFFll) return fail(ctx, GC_ERR_INVALID_ARG, "more than 2^31 - 1 (request, Gaussian) pairs");
+    if (rows_fit)  // the lists of every request are binned by tile row (rank within the request)
+        for (auto &R : tab) R.rp.list_packed = 1;
     return GC_OK;
 }
 
@@ -839,17 +849,20 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     // segments padded to whole radix tiles, one segmented pass on the column; room for the
     // padding beyond the capacity K (which counts the entries, padded per request)
     const int64_t kpad = (kk + rows * T + 3) & ~int64_t(3);
-    const bool by_rows = rows_fit && rows > 0 && kpad <= 0xFFFFFFF0ll;
+    const bool by_rows = rows_fit;
+    if (by_rows && kpad > 0xFFFFFFF0ll)
+        return fail(ctx, GC_ERR_CAPACITY, "batch needs more than 2^32 - 16 list words with its row padding");
     const int64_t kalloc = by_rows ? kpad : kk;
     for (int b = 0; b < 2; ++b) {
         need(B.tkeys[b], (size_t)kalloc * 4 + 16);
-        need(B.tvals[b], (size_t)kalloc * 4 + 16);
+        if (!by_rows) need(B.tvals[b], (size_t)kalloc * 4 + 16);  // row-binned lists: one word per entry
     }
     const size_t bwords = by_rows ? ((gc::bucket_words(cells, (int)rows) + 63) & ~size_t(63)) : 0;
     need(B.scratch, 4 * (bwords + std::max(gc::radix_scratch_words(kalloc), gc::scan_partials_size(ni))));
     if (need.st != GC_OK) return need.st;
     scratch = B.scratch.as<uint32_t>();
     B.K_cap = K;
+    B.row_binned = by_rows;
     uint32_t *tk[2] = {B.tkeys[0].as<uint32_t>(), B.tkeys[1].as<uint32_t>()};
     uint32_t *tv[2] = {B.tvals[0].as<uint32_t>(), B.tvals[1].as<uint32_t>()};
     if (by_rows) {
@@ -857,11 +870,11 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
         GC_CUDA(ctx, mark(GC_STAGE_EMIT));
         if (K > 0 && items > 0)
             GC_CUDA(ctx, gc::bucket_place(B.ranked.as<float4>(), words, words + 2, B.touched_r.as<uint32_t>(), map, items / 32,
-                                          (int)rows, cells, tk[0], tv[0], (uint32_t)kk, (uint32_t)kalloc, words,
+                                          (int)rows, cells, tk[0], (uint32_t)kk, (uint32_t)kalloc, words,
                                           B.row_shift.as<uint32_t>(), scratch, nullptr, s));
         GC_CUDA(ctx, mark(GC_STAGE_TILE_SORT));
         if (K > 0 && items > 0)
-            GC_CUDA(ctx, gc::bucket_sort(tk, tv, (uint32_t)kalloc, words, (int)rows, cells, scratch, scratch + bwords,
+            GC_CUDA(ctx, gc::bucket_sort(tk, (uint32_t)kalloc, words, (int)rows, cells, scratch, scratch + bwords,
                                          &B.tile_buf, s));
         GC_CUDA(ctx, mark(GC_STAGE_RANGES));
         if (tiles > 0) GC_CUDA(ctx, cudaMemsetAsync(B.ranges.p, 0, (size_t)tiles * 8, s));
@@ -899,7 +912,7 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     GC_CUDA(ctx, mark(GC_STAGE_BLEND));
     GC_CUDA(ctx, cudaMemsetAsync(B.counter.p, 0, 8, s));
     {
-        const uint32_t *sv = (K > 0 && items > 0) ? B.tvals[B.tile_buf].as<uint32_t>() : nullptr;
+        const uint32_t *sv = (K > 0 && items > 0) ? B.lists() : nullptr;
         unsigned long long *ctr = B.counter.as<unsigned long long>();
         auto grid = [&](int64_t g) { return (unsigned)std::min<int64_t>(std::max<int64_t>(tiles, 1), g); };
 #define GC_BB_ARGS rq_dev, tb_dev, n_req, tiles, B.ranges.as<uint2>(), sv, B.ranked.as<float4>(), \
@@ -995,7 +1008,7 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
     if (G) GC_CUDA(ctx, cudaMemsetAsync(B.mcontrib.p, 0, (size_t)ni * 7 * 4, s));
     GC_CUDA(ctx, cudaMemsetAsync(B.counter.p, 0, 8, s));
     {
-        const uint32_t *sv = (B.K_cap > 0 && items > 0) ? B.tvals[B.tile_buf].as<uint32_t>() : nullptr;
+        const uint32_t *sv = (B.K_cap > 0 && items > 0) ? B.lists() : nullptr;
         unsigned long long *ctr = B.counter.as<unsigned long long>();
         auto grid = [&](int64_t g) { return (unsigned)std::min<int64_t>(std::max<int64_t>(B.n_tiles, 1), g); };
 #define GC_BB_ARGS rq_dev, tb_dev, n_req, B.n_tiles, B.ranges.as<uint2>(), sv, B.ranked.as<float4>(),            \

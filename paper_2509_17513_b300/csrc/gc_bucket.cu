@@ -25,6 +25,7 @@ struct SingleMap {
         ci.stride = n_chunks;
         ci.row0 = 0;
         ci.r0 = c * 32;
+        ci.v0 = c * 32;
         ci.n_valid = n - c * 32 < 32 ? (int)(n - c * 32) : 32;
     }
     __device__ __forceinline__ void row(int64_t gr, BucketRow &ri) const {
@@ -40,7 +41,8 @@ SingleMap single_map(int64_t n, const RenderParams &rp, int W, int H) {
 }
 
 // Tile lists without the row padding (diagnostics): per tile its range shifted back by the
-// row's pad shift, and the global index of each of its entries at the unpadded position.
+// row's pad shift, and the global index of each of its entries (the rank of its list word)
+// at the unpadded position.
 __global__ void k_row_lists_export(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
                                    const uint32_t *__restrict__ shift, int ntx, int64_t n_tiles,
                                    const uint32_t *__restrict__ perm, Selection sel, int32_t *__restrict__ out_ranges,
@@ -52,30 +54,33 @@ __global__ void k_row_lists_export(const uint2 *__restrict__ ranges, const uint3
         const bool any = r.y > r.x;
         out_ranges[2 * t] = any ? (int32_t)(r.x - sh) : 0;
         out_ranges[2 * t + 1] = any ? (int32_t)(r.y - sh) : 0;
-        for (uint32_t p = r.x; p < r.y; ++p) out_ids[p - sh] = sel_global(sel, perm[sorted_vals[p]]);
+        for (uint32_t p = r.x; p < r.y; ++p) out_ids[p - sh] = sel_global(sel, perm[sorted_vals[p] & kListRankMask]);
     }
 }
 
 }  // namespace
 
-// Column 255 is left to the pad keys, so that a tile's range is a digit range of its row.
-bool bucket_binning_fits(const RenderParams &rp) { return rp.ntx >= 1 && rp.ntx <= 255 && rp.nty <= 1 << 16; }
+// Column 255 is left to the pad words, so that a tile's range is a digit range of its row;
+// ranks take the low 24 bits of a word.
+bool bucket_binning_fits(const RenderParams &rp, int64_t n_sel) {
+    return rp.ntx >= 1 && rp.ntx <= 255 && rp.nty <= 1 << 16 && n_sel <= (int64_t)kListRankMask + 1;
+}
 
 size_t bucket_scratch_words(int64_t n, int n_rows) { return bucket_words((int64_t)n_rows * ((n + 31) / 32), n_rows); }
 
 cudaError_t launch_bucket_place(const float4 *ranked, const uint32_t *total, const uint32_t *touched_r, int64_t n,
-                                const RenderParams &rp, int W, int H, uint32_t *keys, uint32_t *vals, uint32_t cap,
+                                const RenderParams &rp, int W, int H, uint32_t *keys, uint32_t cap,
                                 uint32_t alloc, uint32_t *words, uint32_t *shift, uint32_t *scratch, uint32_t *peak,
                                 cudaStream_t st) {
     const SingleMap map = single_map(n, rp, W, H);
     return bucket_place(ranked, total, total, touched_r, map, map.n_chunks, rp.nty, (int64_t)rp.nty * map.n_chunks, keys,
-                        vals, cap, alloc, words, shift, scratch, peak, st);
+                        cap, alloc, words, shift, scratch, peak, st);
 }
 
-cudaError_t launch_bucket_sort(uint32_t *keys[2], uint32_t *vals[2], uint32_t alloc, uint32_t *words, int64_t n,
-                               int n_rows, uint32_t *scratch, uint32_t *sort_scratch, int *out_buf, cudaStream_t st) {
-    return bucket_sort(keys, vals, alloc, words, n_rows, (int64_t)n_rows * ((n + 31) / 32), scratch, sort_scratch,
-                       out_buf, st);
+cudaError_t launch_bucket_sort(uint32_t *keys[2], uint32_t alloc, uint32_t *words, int64_t n, int n_rows,
+                               uint32_t *scratch, uint32_t *sort_scratch, int *out_buf, cudaStream_t st) {
+    return bucket_sort(keys, alloc, words, n_rows, (int64_t)n_rows * ((n + 31) / 32), scratch, sort_scratch, out_buf,
+                       st);
 }
 
 cudaError_t launch_bucket_ranges(int64_t n, uint32_t *scratch, uint32_t *sort_scratch, const RenderParams &rp,

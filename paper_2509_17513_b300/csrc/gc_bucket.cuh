@@ -1,7 +1,9 @@
 // gc_bucket.cuh - binning by tile row, for one view (gc_bucket.cu) and for a batch of
 // requests (gc_batch.cu): the (tile, Gaussian) entries written straight into per-row
 // segments, so that one 8-bit radix pass on the tile column finishes the stable (tile,
-// depth rank) order.
+// depth rank) order.  An entry is one word, column << 24 | rank (the rank within its image:
+// at most 2^24 selected Gaussians per image), so the pass moves keys only and the sorted
+// words are the tile lists.
 //
 // The entries of a Gaussian are its row intervals (binning step 15): in tile row y the
 // columns [a_y, b_y].  Ordered by (tile, rank), the entries of row y are those of every
@@ -16,10 +18,10 @@
 //   k_bucket_segments  each row's segment padded to whole radix tiles (a radix block never
 //                      straddles two rows): the shift from the scanned offsets to the padded
 //                      positions, the segments in radix-block units, the padded total;
-//   k_bucket_pads      pad slots get the key 0xFFFFFFFF (column 255, which no tile uses:
+//   k_bucket_pads      pad slots get the word 0xFFFFFFFF (column 255, which no tile uses:
 //                      sorted behind the row's entries);
-//   k_bucket_place     the chunk's entries of each row at their positions, key = (row << 8)
-//                      | column, value = item (depth rank);
+//   k_bucket_place     the chunk's entries of each row at their positions, word = column <<
+//                      24 | rank;
 //   k_bucket_ranges    after the column pass, tile (row, column)'s range is the column's digit
 //                      range in the row's segment, read from the pass's scanned digit counts.
 // Within a chunk the lanes' entries of a row are laid out lane by lane (rank order); each warp
@@ -49,6 +51,7 @@ struct BucketChunk {
     int64_t stride;  // cells per row of the image (its chunk count)
     int64_t row0;    // global row of the image's row 0
     int64_t r0;      // first item of the chunk
+    int64_t v0;      // rank of the chunk's first item within its image (the list words' rank)
     int n_valid;     // lanes holding an item
 };
 
@@ -216,15 +219,12 @@ __global__ void __launch_bounds__(1024) k_bucket_segments(const uint32_t *__rest
     }
 }
 
-// Pad slots of global row blockIdx.x: key 0xFFFFFFFF, value 0.
+// Pad slots of global row blockIdx.x: word 0xFFFFFFFF.
 __global__ void __launch_bounds__(256) k_bucket_pads(const uint2 *__restrict__ pads, const uint32_t *words,
-                                                     uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                                                     uint32_t *__restrict__ keys) {
     if (words[3] == 0u) return;  // nothing placed (empty frame or overflow)
     const uint2 p = pads[blockIdx.x];
-    for (uint32_t i = threadIdx.x; i < p.y; i += 256) {
-        keys[p.x + i] = 0xffffffffu;
-        vals[p.x + i] = 0u;
-    }
+    for (uint32_t i = threadIdx.x; i < p.y; i += 256) keys[p.x + i] = 0xffffffffu;
 }
 
 // The chunk's entries of every row at their positions: scanned[cell0 + row * stride] +
@@ -242,8 +242,7 @@ __global__ void __launch_bounds__(kBucketWarps * 32) k_bucket_place(const float4
                                                                     const uint32_t *__restrict__ scanned,
                                                                     const uint32_t *__restrict__ shift,
                                                                     const uint32_t *words, uint32_t alloc,
-                                                                    uint32_t *__restrict__ keys,
-                                                                    uint32_t *__restrict__ vals) {
+                                                                    uint32_t *__restrict__ keys) {
     __shared__ uint32_t m[kBucketWarps][kWin][33];   // counts, then start positions
     __shared__ uint8_t col[kBucketWarps][kWin][36];  // first column of each lane's interval
     __shared__ uint32_t rtot[kBucketWarps][kWin];    // entries of the chunk in each row
@@ -261,7 +260,7 @@ __global__ void __launch_bounds__(kBucketWarps * 32) k_bucket_place(const float4
     const int yhi = (int)__reduce_max_sync(0xffffffffu, (uint32_t)(has ? L.ty1 + 1 : 0)) - 1;
     uint32_t(*mw)[33] = m[warp];
     uint8_t(*cw)[36] = col[warp];
-    const uint32_t r0 = (uint32_t)ci.r0;
+    const uint32_t v0 = (uint32_t)ci.v0;
     for (int w0 = (ylo / kWin) * kWin; w0 <= yhi; w0 += kWin) {
 #pragma unroll 8
         for (int j = 0; j < kWin; ++j) mw[j][lane] = 0u;
@@ -290,11 +289,13 @@ __global__ void __launch_bounds__(kBucketWarps * 32) k_bucket_place(const float4
         }
         __syncwarp();
         const int jmax = min(kWin, ci.n_rows - w0);
+        // not unrolled: a row holds one warp step of the chunk's entries or none, mostly
+#pragma unroll 1
         for (int j = 0; j < jmax; ++j) {
             const uint32_t tot = rtot[warp][j];
             if (tot == 0u) continue;  // warp-uniform
             const uint32_t p0 = mw[j][0];
-            const uint32_t key0 = (uint32_t)(w0 + j) << 8;
+#pragma unroll 1
             for (uint32_t e = lane; e < tot; e += 32) {
                 const uint32_t pe = p0 + e;
                 int o = 0;  // last lane whose start is <= pe
@@ -302,10 +303,7 @@ __global__ void __launch_bounds__(kBucketWarps * 32) k_bucket_place(const float4
                 for (int step = 16; step > 0; step >>= 1)
                     if (mw[j][o + step] <= pe) o += step;
                 const uint32_t x = (uint32_t)cw[j][o] + (pe - mw[j][o]);
-                if (pe < alloc) {
-                    keys[pe] = key0 | x;
-                    vals[pe] = r0 + (uint32_t)o;
-                }
+                if (pe < alloc) keys[pe] = (x << kListRankBits) | (v0 + (uint32_t)o);
             }
         }
         __syncwarp();
@@ -366,7 +364,7 @@ inline BucketScratch bucket_carve(uint32_t *scratch, int64_t n_cells, int n_rows
 template <class Map>
 cudaError_t bucket_place(const float4 *ranked, const uint32_t *total, const uint32_t *demand,
                          const uint32_t *touched_r, const Map &map,
-                         int64_t n_chunks, int n_rows, int64_t n_cells, uint32_t *keys, uint32_t *vals,
+                         int64_t n_chunks, int n_rows, int64_t n_cells, uint32_t *keys,
                          uint32_t cap, uint32_t alloc, uint32_t *words, uint32_t *shift, uint32_t *scratch,
                          uint32_t *peak, cudaStream_t st) {
     const BucketScratch b = bucket_carve(scratch, n_cells, n_rows);
@@ -384,24 +382,23 @@ cudaError_t bucket_place(const float4 *ranked, const uint32_t *total, const uint
                                                (uint32_t)radix_tile_keys(), cap, alloc, shift, b.segs, b.pads,
                                                words, peak);
     note_launches(1);
-    k_bucket_pads<<<(unsigned)n_rows, 256, 0, st>>>(b.pads, words, keys, vals);
+    k_bucket_pads<<<(unsigned)n_rows, 256, 0, st>>>(b.pads, words, keys);
     note_launches(1);
     if (n_chunks > 0) {
         k_bucket_place<Map><<<grid, kBucketWarps * 32, 0, st>>>(ranked, touched_r, map, n_chunks, b.scanned, shift,
-                                                                words, alloc, keys, vals);
+                                                                words, alloc, keys);
         note_launches(1);
     }
     return cudaGetLastError();
 }
 
-// One segmented stable pass on the column; the sorted keys are not kept (the ranges come from
-// the pass's digit counts).
-inline cudaError_t bucket_sort(uint32_t *keys[2], uint32_t *vals[2], uint32_t alloc, uint32_t *words, int n_rows,
-                               int64_t n_cells, uint32_t *scratch, uint32_t *sort_scratch, int *out_buf,
-                               cudaStream_t st) {
+// One segmented stable pass on the column byte of the words (keys only): the sorted words are
+// the tile lists, in keys[*out_buf]; the ranges come from the pass's digit counts.
+inline cudaError_t bucket_sort(uint32_t *keys[2], uint32_t alloc, uint32_t *words, int n_rows, int64_t n_cells,
+                               uint32_t *scratch, uint32_t *sort_scratch, int *out_buf, cudaStream_t st) {
     const BucketScratch b = bucket_carve(scratch, n_cells, n_rows);
-    return radix_sort_pairs(keys, vals, alloc, words + 3, 8, sort_scratch, out_buf, st, words + 1, false, b.segs,
-                            n_rows);
+    return radix_sort_pairs(keys, nullptr, alloc, words + 3, 32, sort_scratch, out_buf, st, words + 1, true, b.segs,
+                            n_rows, kListRankBits);
 }
 
 // Tile ranges from the column pass's digit counts (after bucket_sort with the same scratch).

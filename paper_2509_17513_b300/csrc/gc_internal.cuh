@@ -68,7 +68,16 @@ struct RenderParams {
     int ntx, nty;
     int membership;
     int alpha_cull;
+    int list_packed;  // tile-list words: 0 = the rank; 1 = column << 24 | rank (row binning)
 };
+
+// Rank of a tile-list word: the low 24 bits of a row-binned list (whose top byte holds the
+// tile column the lists were sorted on), else the whole word.
+constexpr int kListRankBits = 24;
+constexpr uint32_t kListRankMask = (1u << kListRankBits) - 1u;
+__host__ __device__ __forceinline__ uint32_t list_rank_mask(const RenderParams &rp) {
+    return rp.list_packed ? kListRankMask : 0xffffffffu;
+}
 
 // Attribute source.  FP32 arrays, or BF16/FP8 planes with per-channel scales.
 // Per-Gaussian additive residuals of one frame (Sec. 3.2, Eq. 7): log-scale, opacity logit
@@ -186,10 +195,11 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
 // blocks starts at scratch[256 b0 + d nb]; gc_bucket.cuh reads tile ranges from them).
 size_t radix_scratch_words(int64_t n_max);
 int radix_tile_keys();
+// Keys only (vals NULL): the keys are sorted on bits [begin_bit, end_bit) and always written.
 cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
                              const uint32_t *n_dev, int end_bit, uint32_t *scratch, int *out_buf,
                              cudaStream_t st, uint32_t *err, bool keys_out = true,
-                             const uint32_t *seg_block0 = nullptr, int n_seg = 0);
+                             const uint32_t *seg_block0 = nullptr, int n_seg = 0, int begin_bit = 0);
 
 // Emit (tile key, rank) for every tile of every row interval of every visible Gaussian,
 // in rank order (image W x H).  Entries at positions >= cap are dropped (fixed-capacity
@@ -199,20 +209,22 @@ cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uin
                         uint32_t cap, cudaStream_t st, const uint32_t *total = nullptr,
                         uint32_t *peak = nullptr);
 
-// Binning by tile row (gc_bucket.cu), for images of at most 256 tile columns
-// (bucket_binning_fits): the entries placed straight into per-row segments padded to whole
-// radix tiles, key (row << 8) | column, value = rank (launch_bucket_place: words[3] = padded
-// total, shift[row] = padded minus unpadded start of the row, more than `cap` entries
-// recorded in *peak); one segmented stable pass on the column (launch_bucket_sort); tile
-// ranges from its digit counts (launch_bucket_ranges; ranges must be zeroed).  Buffers hold
-// `alloc` >= entries + rows x radix_tile_keys() keys; `scratch` needs bucket_scratch_words.
-bool bucket_binning_fits(const RenderParams &rp);
+// Binning by tile row (gc_bucket.cu), for images of at most 255 tile columns and at most
+// 2^24 selected Gaussians (bucket_binning_fits): the entries placed straight into per-row
+// segments padded to whole radix tiles as one word each, column << 24 | rank
+// (launch_bucket_place: words[3] = padded total, shift[row] = padded minus unpadded start of
+// the row, more than `cap` entries recorded in *peak and nothing placed); one segmented stable
+// pass on the column byte (launch_bucket_sort: the sorted words are the tile lists, in
+// keys[*out_buf]); tile ranges from its digit counts (launch_bucket_ranges; ranges must be
+// zeroed).  Buffers hold `alloc` >= entries + rows x radix_tile_keys() words; `scratch` needs
+// bucket_scratch_words.
+bool bucket_binning_fits(const RenderParams &rp, int64_t n_sel);
 size_t bucket_scratch_words(int64_t n, int n_rows);
 cudaError_t launch_bucket_place(const float4 *ranked, const uint32_t *total, const uint32_t *touched_r, int64_t n,
-                                const RenderParams &rp, int W, int H, uint32_t *keys, uint32_t *vals, uint32_t cap,
+                                const RenderParams &rp, int W, int H, uint32_t *keys, uint32_t cap,
                                 uint32_t alloc, uint32_t *words, uint32_t *shift, uint32_t *scratch, uint32_t *peak,
                                 cudaStream_t st);
-cudaError_t launch_bucket_sort(uint32_t *keys[2], uint32_t *vals[2], uint32_t alloc, uint32_t *words, int64_t n,
+cudaError_t launch_bucket_sort(uint32_t *keys[2], uint32_t alloc, uint32_t *words, int64_t n,
                                int n_rows, uint32_t *scratch, uint32_t *sort_scratch, int *out_buf, cudaStream_t st);
 cudaError_t launch_bucket_ranges(int64_t n, uint32_t *scratch, uint32_t *sort_scratch, const RenderParams &rp,
                                  uint2 *ranges, cudaStream_t st);

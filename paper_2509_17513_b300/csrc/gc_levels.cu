@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
         {
             const int idx = b + (int)threadIdx.x;
             if (idx < n) {
-                const uint32_t r = sorted_vals[range.x + idx];
+                const uint32_t r = sorted_vals[range.x + idx] & list_rank_mask(rp);
                 const float4 a = ranked[kRec * (size_t)r];
                 const float4 bb = ranked[kRec * (size_t)r + 1];
                 const float4 c = ranked[kRec * (size_t)r + 2];
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256, 4) k_blend_levels_bwd(
         {
             const int k = lo + (int)threadIdx.x;
             if (k < hi) {
-                const uint32_t r = sorted_vals[range.x + k];
+                const uint32_t r = sorted_vals[range.x + k] & list_rank_mask(rp);
                 const float4 a = ranked[kRec * (size_t)r];
                 const float4 bb = ranked[kRec * (size_t)r + 1];
                 const float4 c = ranked[kRec * (size_t)r + 2];

@@ -219,7 +219,7 @@ extern "C" GC_API gc_status gc_render_forward_noalloc(const gc_options *opt, con
     memcpy(cp.R, cam->R, sizeof cp.R);
     memcpy(cp.t, cam->t, sizeof cp.t);
     memcpy(cp.campos, cam->campos, sizeof cp.campos);
-    gc::RenderParams rp;
+    gc::RenderParams rp{};  // list_packed = 0: the lists of this path come from the key sort
     rp.near_plane = o.near_plane; rp.dilation = o.dilation; rp.frustum_clamp = o.frustum_clamp;
     memcpy(rp.bg, o.bg, sizeof rp.bg);
     rp.tile_w = o.tile_w; rp.tile_h = o.tile_h;

@@ -84,12 +84,12 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(256) k_blend_fwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, int W, int H, int ntx, float bg0, float bg1, float bg2,
-    int membership, float *__restrict__ image, float *__restrict__ final_T,
+    int membership, uint32_t rank_mask, float *__restrict__ image, float *__restrict__ final_T,
     uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ n_blended,
     uint32_t *__restrict__ n_walked) {
     __shared__ __align__(16) FwdSmem sm;
     const int tile = blockIdx.x;
-    const TileOut o{image, final_T, n_contrib, n_blended, n_walked, bg0, bg1, bg2, W, H, membership};
+    const TileOut o{image, final_T, n_contrib, n_blended, n_walked, bg0, bg1, bg2, W, H, membership, rank_mask, 0u};
     blend_fwd_tile<TW, TH, true>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, o, sm);
 }
 
@@ -144,7 +144,7 @@ cudaError_t launch_blend_fwd(const uint2 *ranges, const uint32_t *sorted_vals,
     if (tiles == 0) return cudaSuccess;
 #define GC_BLEND_ARGS                                                                          \
     ranges, sorted_vals, ranked, cam.width, cam.height, rp.ntx, rp.bg[0], rp.bg[1], rp.bg[2], \
-        rp.membership, image, final_T, n_contrib, n_blended, n_walked
+        rp.membership, list_rank_mask(rp), image, final_T, n_contrib, n_blended, n_walked
     if (rp.tile_w == 16 && rp.tile_h == 16)
         k_blend_fwd<16, 16><<<tiles, 256, 0, st>>>(GC_BLEND_ARGS);
     else if (rp.tile_w == 8 && rp.tile_h == 32)

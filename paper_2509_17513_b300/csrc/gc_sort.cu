@@ -326,13 +326,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
 // row (match.any or ballot multisplit), the CTA turns warp counts into each warp's tile
 // positions per digit, places the (key, value) pairs digit-sorted back into the tile's
 // buffer as 8-byte pairs and writes them out in contiguous runs.  keys_out may be NULL
-// (last pass of a sort whose keys are not kept).
+// (last pass of a sort whose keys are not kept).  Without kPairs the keys alone are moved
+// (vals_in and vals_out unused; half the shared staging).
+template <bool kPairs>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *n_dev,
     int64_t n_max, int shift, uint32_t mask, const uint32_t *__restrict__ scanned, int nblocks,
     uint32_t *err, SegIndex sg) {
-    __shared__ __align__(128) uint32_t skv[2][2][kSortTile];  // per stage: keys, values (then key-value pairs)
+    // per stage: keys, values (then key-value pairs); keys only without kPairs
+    __shared__ __align__(128) uint32_t skv[2][kPairs ? 2 : 1][kSortTile];
     __shared__ uint32_t wcnt[kWarps][256];
     __shared__ uint32_t gbase[256];
     __shared__ uint32_t ws[33];
@@ -356,9 +359,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         const int nv = (int)((n - base) < kSortTile ? (n - base) : kSortTile);
         const uint32_t bytes = (uint32_t)((nv * 4 + 15) & ~15);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(&bar[stage], 2 * bytes);
+        mbar_arrive_expect_tx(&bar[stage], (kPairs ? 2 : 1) * bytes);
         bulk_copy_g2s(skv[stage][0], keys_in + base, bytes, &bar[stage]);
-        bulk_copy_g2s(skv[stage][1], vals_in + base, bytes, &bar[stage]);
+        if (kPairs) bulk_copy_g2s(skv[stage][kPairs ? 1 : 0], vals_in + base, bytes, &bar[stage]);
     };
     if (threadIdx.x == 0) issue(blockIdx.x, 0);
 
@@ -390,7 +393,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
             for (int r = 0; r < kSortItems; ++r) {
                 const int li = wseg + r * 32 + lane;
                 key[r] = skv[stage][0][li];
-                val[r] = skv[stage][1][li];
+                if (kPairs) val[r] = skv[stage][kPairs ? 1 : 0][li];
                 const uint32_t d = (key[r] >> shift) & 0xffu;
                 const uint32_t peers = digit_peers8(d, 0xffffffffu);
                 const uint32_t before = wcnt[warp][d];
@@ -405,7 +408,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
                 const int li = wseg + r * 32 + lane;
                 const bool valid = li < nvalid;
                 key[r] = valid ? skv[stage][0][li] : 0xffffffffu;
-                val[r] = valid ? skv[stage][1][li] : 0u;
+                if (kPairs) val[r] = valid ? skv[stage][kPairs ? 1 : 0][li] : 0u;
                 const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
                 const uint32_t d = (key[r] >> shift) & mask;
                 // narrow digits: one match instruction; 8-bit digits: ballots per digit bit
@@ -441,15 +444,21 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
             if (li < nvalid) {
                 const uint32_t d = (key[r] >> shift) & mask;
                 const uint32_t pos = wcnt[warp][d] + loc[r];
-                reinterpret_cast<uint2 *>(&skv[stage][0][0])[pos] = make_uint2(key[r], val[r]);
+                if (kPairs) reinterpret_cast<uint2 *>(&skv[stage][0][0])[pos] = make_uint2(key[r], val[r]);
+                else skv[stage][0][pos] = key[r];
             }
         }
         __syncthreads();
         for (int p = threadIdx.x; p < nvalid; p += kSortThreads) {
-            const uint2 kv = reinterpret_cast<const uint2 *>(&skv[stage][0][0])[p];
-            const uint32_t o = gbase[(kv.x >> shift) & mask] + (uint32_t)p;
-            if (keys_out) keys_out[o] = kv.x;
-            vals_out[o] = kv.y;
+            if (kPairs) {
+                const uint2 kv = reinterpret_cast<const uint2 *>(&skv[stage][0][0])[p];
+                const uint32_t o = gbase[(kv.x >> shift) & mask] + (uint32_t)p;
+                if (keys_out) keys_out[o] = kv.x;
+                vals_out[o] = kv.y;
+            } else {
+                const uint32_t kk = skv[stage][0][p];
+                keys_out[gbase[(kk >> shift) & mask] + (uint32_t)p] = kk;
+            }
         }
         __syncthreads();
     }
@@ -694,16 +703,19 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
 int radix_tile_keys() { return kSortTile; }
 
 // Grid of the persistent scatter: every CTA that fits at once with the shared-memory carveout
-// at its maximum (at 48 registers and 42 KB of shared memory, five CTAs per SM), queried once.
+// at its maximum (pairs: 48 registers and 42 KB of shared memory, five CTAs per SM), queried
+// once per variant.
+template <bool kPairs>
 static int scatter_grid() {
     static int cached = 0;
     if (!cached) {
         int per_sm = 0, dev = 0, sms = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
-        cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_radix_scatter<kPairs>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radix_scatter, kSortThreads, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radix_scatter<kPairs>, kSortThreads, 0) !=
+                cudaSuccess ||
             per_sm < 1)
             per_sm = 4;
         cudaGetLastError();
@@ -729,15 +741,17 @@ size_t radix_scratch_words(int64_t n_max) {
 cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
                              const uint32_t *n_dev, int end_bit, uint32_t *scratch, int *out_buf,
                              cudaStream_t st, uint32_t *err, bool keys_out,
-                             const uint32_t *seg_block0, int n_seg) {
+                             const uint32_t *seg_block0, int n_seg, int begin_bit) {
     int cur = 0;
-    if (n_max <= 0 || end_bit <= 0) {
+    if (n_max <= 0 || end_bit <= begin_bit) {
         *out_buf = 0;
         return cudaSuccess;
     }
+    const bool pairs = vals != nullptr && vals[0] != nullptr;
+    if (!pairs) keys_out = true;
     const int nblocks = (int)((n_max + kSortTile - 1) / kSortTile);
-    const int passes = (end_bit + 7) / 8;
-    if (!seg_block0 && n_max <= kOnesweepMaxKeys && passes <= kMaxPasses) {
+    const int passes = (end_bit - begin_bit + 7) / 8;
+    if (pairs && begin_bit == 0 && !seg_block0 && n_max <= kOnesweepMaxKeys && passes <= kMaxPasses) {
         // one-sweep: zero the counts, tickets and status words; one histogram kernel;
         // one scatter launch per pass
         DigitPlan plan;
@@ -770,7 +784,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
         *out_buf = cur;
         return cudaGetLastError();
     }
-    const int grid = std::min(nblocks, scatter_grid());
+    const int grid = std::min(nblocks, pairs ? scatter_grid<true>() : scatter_grid<false>());
     uint32_t *counts = scratch;
     uint32_t *partials = scratch + (size_t)256 * nblocks;
     SegIndex sg{seg_block0, nullptr, n_seg};
@@ -785,8 +799,8 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
         }
         sg.blk = blk;
     }
-    // balanced digit widths: ceil(end_bit / 8) passes of nearly equal width
-    int shift = 0;
+    // balanced digit widths: ceil((end_bit - begin_bit) / 8) passes of nearly equal width
+    int shift = begin_bit;
     for (int pass = 0; pass < passes; ++pass) {
         const int bits = (end_bit - shift + (passes - pass) - 1) / (passes - pass);
         const uint32_t mask = (1u << bits) - 1u;
@@ -797,10 +811,14 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
                                               partials, st, err);
         if (e != cudaSuccess) return e;
         const bool last = pass == passes - 1;
-        k_radix_scatter<<<grid, kSortThreads, 0, st>>>(keys[cur], vals[cur],
-                                                       (last && !keys_out) ? nullptr : keys[cur ^ 1],
-                                                       vals[cur ^ 1], n_dev, n_max, shift, mask,
-                                                       counts, nblocks, err, sg);
+        if (pairs)
+            k_radix_scatter<true><<<grid, kSortThreads, 0, st>>>(keys[cur], vals[cur],
+                                                                 (last && !keys_out) ? nullptr : keys[cur ^ 1],
+                                                                 vals[cur ^ 1], n_dev, n_max, shift, mask, counts,
+                                                                 nblocks, err, sg);
+        else
+            k_radix_scatter<false><<<grid, kSortThreads, 0, st>>>(keys[cur], nullptr, keys[cur ^ 1], nullptr, n_dev,
+                                                                  n_max, shift, mask, counts, nblocks, err, sg);
         note_launches(1);
         cur ^= 1;
         shift += bits;

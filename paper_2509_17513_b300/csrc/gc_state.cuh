@@ -83,6 +83,11 @@ struct gc_saved {
     DevBuf lv_T, lv_last;   // its per-level final transmittance and list position
     bool row_binned = false;  // lists binned by tile row: row segments padded to radix tiles
     DevBuf row_shift;         // per tile row: padded minus unpadded start of its segment
+    // The sorted tile lists: the keys buffer of the last pass for row-binned lists (one word
+    // per entry, column << 24 | rank), else the values of the key sort.
+    uint32_t *lists() const {
+        return row_binned ? tkeys[tile_buf].as<uint32_t>() : tvals[tile_buf].as<uint32_t>();
+    }
 };
 
 

@@ -141,6 +141,8 @@ struct TileOut {
     uint32_t *n_contrib, *n_blended, *n_walked;
     float bg0, bg1, bg2;
     int W, H, membership;
+    uint32_t rank_mask;  // of the tile-list words (list_rank_mask)
+    uint32_t rank_base;  // added to a list word's rank: the record index of rank 0
 };
 
 // Front-to-back compositing (Eq. 2) of tile (tx, ty) of one image by a CTA of 256
@@ -173,7 +175,7 @@ __device__ __forceinline__ void blend_fwd_tile(int tx, int ty, uint2 range,
         {
             const int idx = b + (int)threadIdx.x;
             if (idx < n) {
-                const uint32_t r = sorted_vals[range.x + idx];
+                const uint32_t r = (sorted_vals[range.x + idx] & o.rank_mask) + o.rank_base;
                 const float4 a = ranked[kRec * (size_t)r];
                 const float4 bb = ranked[kRec * (size_t)r + 1];
                 const float4 c = ranked[kRec * (size_t)r + 2];
@@ -263,6 +265,7 @@ struct TileBwd {
     RenderParams rp;  // background, tile shape, membership, alpha cull
     int W, H;
     uint32_t entry_shift;
+    uint32_t rank_base;  // added to a list word's rank: the record index of rank 0
 };
 
 // Mask of the 8 x 4 pixel block at tile column c0 and row r0 (bit 8 r + c = pixel
@@ -360,7 +363,7 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
             const int slot = (int)threadIdx.x + kBwdThreads * h;
             const int k = lo + slot;
             if (k < hi) {
-                const uint32_t r = sorted_vals[range.x + k];
+                const uint32_t r = (sorted_vals[range.x + k] & list_rank_mask(o.rp)) + o.rank_base;
                 const float4 a = ranked[kRec * (size_t)r];
                 const float4 bb = ranked[kRec * (size_t)r + 1];
                 const float4 c = ranked[kRec * (size_t)r + 2];
