@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
 // (last pass of a sort whose keys are not kept).  Without kPairs the keys alone are moved
 // (vals_in and vals_out unused; half the shared staging).
 template <bool kPairs>
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+__global__ void __launch_bounds__(kSortThreads, kPairs ? 5 : 6) k_radix_scatter(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *n_dev,
     int64_t n_max, int shift, uint32_t mask, const uint32_t *__restrict__ scanned, int nblocks,
