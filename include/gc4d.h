@@ -393,9 +393,13 @@ GC_API gc_status gc_batch_graph_destroy(gc_batch_graph *graph);
  * capacity (the context's option, or with 0 the largest frame's exact need plus 5 %,
  * measured by one eager forward pass), runs the step eagerly once at that capacity
  * (sizing every buffer), then captures it; launching replays every kernel with no host
- * work, images identical to the eager calls.  The graph reads and writes the same
- * device arrays as at creation: update their contents in place.  It owns its saved
- * state and must be destroyed before the context.  An overflow of any frame and
+ * work, images identical to the eager calls.  chains (1..4): frame f runs on chain
+ * f mod chains, each chain with a saved state of its own, as an independent branch of
+ * the graph, so that the short sort and binning kernels of one frame run beside another
+ * frame's blend; the backwards stay in frame order, so images and gradients equal those
+ * of chains = 1 (chains > n_frames counts as n_frames).  The graph reads and writes the
+ * same device arrays as at creation: update their contents in place.  It owns its saved
+ * states and must be destroyed before the context.  An overflow of any frame and
  * bounded-wait timeouts are reported by gc_levels_graph_check.  The context's options
  * are read at creation and restored afterwards; profiling is off inside the graph.
  * Errors: GC_ERR_INVALID_ARG (missing arrays, n_frames or levels < 1), any error of the
@@ -407,7 +411,7 @@ typedef struct gc_levels_graph gc_levels_graph;
 GC_API gc_status gc_levels_graph_create(gc_context *ctx, const gc_gaussians *g, const gc_motion *motions,
                                         int32_t n_frames, const gc_camera *cameras, int32_t levels,
                                         float *const *level_images, const float *const *dL_dimages,
-                                        gc_grads *grads, void *stream, gc_levels_graph **out);
+                                        gc_grads *grads, int32_t chains, void *stream, gc_levels_graph **out);
 GC_API gc_status gc_levels_graph_launch(gc_levels_graph *graph, void *stream);
 /* Key capacity per frame and kernel nodes in the graph; either may be NULL. */
 GC_API gc_status gc_levels_graph_info(const gc_levels_graph *graph, int64_t *key_capacity,

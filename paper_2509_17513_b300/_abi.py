@@ -121,7 +121,7 @@ SIGNATURES = {
     "gc_batch_graph_info": (C.c_int, [P, P, P, P]),
     "gc_batch_graph_check": (C.c_int, [P, P]),
     "gc_batch_graph_destroy": (C.c_int, [P]),
-    "gc_levels_graph_create": (C.c_int, [P, P, P, C.c_int32, P, C.c_int32, P, P, P, P, P]),
+    "gc_levels_graph_create": (C.c_int, [P, P, P, C.c_int32, P, C.c_int32, P, P, P, C.c_int32, P, P]),
     "gc_levels_graph_launch": (C.c_int, [P, P]),
     "gc_levels_graph_info": (C.c_int, [P, P, P]),
     "gc_levels_graph_check": (C.c_int, [P, P]),

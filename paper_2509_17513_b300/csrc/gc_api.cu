@@ -82,7 +82,8 @@ static void saved_release(gc_context *ctx, gc_saved *s) {
     DevBuf *bufs[] = {&s->rec, &s->ranked, &s->dkeys[0], &s->dkeys[1], &s->dvals[0], &s->dvals[1],
                       &s->touched, &s->touched_r, &s->offsets, &s->tkeys[0], &s->tkeys[1],
                       &s->tvals[0], &s->tvals[1], &s->ranges, &s->final_T, &s->n_contrib,
-                      &s->n_blended, &s->n_walked, &s->words, &s->lv_T, &s->lv_last, &s->row_shift};
+                      &s->n_blended, &s->n_walked, &s->words, &s->lv_T, &s->lv_last, &s->row_shift,
+                      &s->scratch, &s->bwd_part, &s->bwd_g2d, &s->bwd_motion, &s->bwd_group};
     for (DevBuf *b : bufs) release(*b);
     s->valid = false;
 }
@@ -93,9 +94,8 @@ gc_status gc_destroy(gc_context *ctx) {
         DeviceGuard dg(ctx->device);
         saved_release(ctx, &ctx->internal);
         ctx->internal.batch.reset();
-        DevBuf *bufs[] = {&ctx->scratch, &ctx->bwd_part, &ctx->bwd_g2d, &ctx->bwd_motion,
-                          &ctx->bwd_group, &ctx->field_part, &ctx->field_h, &ctx->kde_scratch,
-                          &ctx->prof_flush, &ctx->loss_part};
+        DevBuf *bufs[] = {&ctx->field_part, &ctx->field_h, &ctx->kde_scratch, &ctx->prof_flush,
+                          &ctx->loss_part};
         for (DevBuf *b : bufs) release(*b);
         if (ctx->host_word) cudaFreeHost(ctx->host_word);
         for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
@@ -220,8 +220,8 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
     uint32_t *words = S.words.as<uint32_t>();  // [0] = K, [1] = error flags
     int64_t K = 0;
     if (n_sel > 0) {
-        GC_CUDA(ctx, grow(ctx->scratch, 4 * std::max(gc::radix_scratch_words(nn), scan_words)));
-        uint32_t *scratch = ctx->scratch.as<uint32_t>();
+        GC_CUDA(ctx, grow(S.scratch, 4 * std::max(gc::radix_scratch_words(nn), scan_words)));
+        uint32_t *scratch = S.scratch.as<uint32_t>();
         GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_PREPROCESS));
         GC_CUDA(ctx, gc::launch_preprocess(src, S.sel, n_sel, cp, rp, S.rec.as<float4>(),
                                            S.dkeys[0].as<uint32_t>(), S.dvals[0].as<uint32_t>(),
@@ -256,8 +256,8 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
             if (!rows) GC_CUDA(ctx, grow(S.tvals[b], (size_t)kalloc * 4));  // row-binned lists: one word per entry
         }
         const size_t bucket_words = rows ? ((gc::bucket_scratch_words(n_sel, rp.nty) + 63) & ~size_t(63)) : 0;
-        GC_CUDA(ctx, grow(ctx->scratch, 4 * (bucket_words + std::max(gc::radix_scratch_words(kalloc), scan_words))));
-        scratch = ctx->scratch.as<uint32_t>();
+        GC_CUDA(ctx, grow(S.scratch, 4 * (bucket_words + std::max(gc::radix_scratch_words(kalloc), scan_words))));
+        scratch = S.scratch.as<uint32_t>();
         S.row_binned = false;
         if (K > 0) {
             uint32_t *tk[2] = {S.tkeys[0].as<uint32_t>(), S.tkeys[1].as<uint32_t>()};
@@ -530,50 +530,50 @@ static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, co
     }
     const int64_t K = S.K > 0 ? S.K : 1;
     {
-        void *before = ctx->bwd_part.p;
-        GC_CUDA(ctx, grow(ctx->bwd_part, (size_t)K * 9 * 4));
-        if (ctx->bwd_part.p != before) ctx->bwd_part_clean = false;
+        void *before = S.bwd_part.p;
+        GC_CUDA(ctx, grow(S.bwd_part, (size_t)K * 9 * 4));
+        if (S.bwd_part.p != before) S.bwd_part_clean = false;
     }
-    if (!ctx->bwd_part_clean) GC_CUDA(ctx, cudaMemsetAsync(ctx->bwd_part.p, 0, ctx->bwd_part.cap, s));
-    GC_CUDA(ctx, grow(ctx->bwd_g2d, (size_t)S.n_sel * 9 * 4));
-    GC_CUDA(ctx, grow(ctx->bwd_motion, (size_t)S.n_sel * 7 * 4));
-    if (G && !S.per_gaussian) GC_CUDA(ctx, grow(ctx->bwd_group, gc::group_partial_floats(S.n_sel, G) * 4));
+    if (!S.bwd_part_clean) GC_CUDA(ctx, cudaMemsetAsync(S.bwd_part.p, 0, S.bwd_part.cap, s));
+    GC_CUDA(ctx, grow(S.bwd_g2d, (size_t)S.n_sel * 9 * 4));
+    GC_CUDA(ctx, grow(S.bwd_motion, (size_t)S.n_sel * 7 * 4));
+    if (G && !S.per_gaussian) GC_CUDA(ctx, grow(S.bwd_group, gc::group_partial_floats(S.n_sel, G) * 4));
     const uint32_t *sorted_vals = S.K > 0 ? S.lists() : nullptr;
 
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_BLEND_BWD));
-    ctx->bwd_part_clean = false;
+    S.bwd_part_clean = false;
     if (dL_levels) {
         gc::LevelGrads lg{};
         for (int l = 0; l < S.levels; ++l) lg.g[l] = dL_levels[l];
         GC_CUDA(ctx, gc::launch_blend_levels_bwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(),
                                                  S.offsets.as<uint32_t>(), S.cam, S.rp, S.levels, S.lv_T.as<float>(),
-                                                 S.lv_last.as<uint32_t>(), lg, ctx->bwd_part.as<float>(), s));
+                                                 S.lv_last.as<uint32_t>(), lg, S.bwd_part.as<float>(), s));
     } else {
         GC_CUDA(ctx, gc::launch_blend_bwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(),
                                           S.offsets.as<uint32_t>(), S.cam, S.rp, S.final_T.as<float>(),
-                                          S.n_contrib.as<uint32_t>(), dL_dimage, ctx->bwd_part.as<float>(), s));
+                                          S.n_contrib.as<uint32_t>(), dL_dimage, S.bwd_part.as<float>(), s));
     }
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_REDUCE));
-    GC_CUDA(ctx, gc::launch_reduce_entries(ctx->bwd_part.as<float>(), S.offsets.as<uint32_t>(),
+    GC_CUDA(ctx, gc::launch_reduce_entries(S.bwd_part.as<float>(), S.offsets.as<uint32_t>(),
                                            S.touched_r.as<uint32_t>(), S.dvals[S.depth_buf].as<uint32_t>(),
                                            S.n_sel, (uint32_t)std::min<int64_t>(K, 0xFFFFFFFFll),
-                                           ctx->bwd_g2d.as<float>(), s));
-    ctx->bwd_part_clean = true;
+                                           S.bwd_g2d.as<float>(), s));
+    S.bwd_part_clean = true;
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_PREPROCESS_BWD));
-    GC_CUDA(ctx, gc::launch_preprocess_bwd(src, S.sel, S.n_sel, S.cam, S.rp, ctx->bwd_g2d.as<float>(),
+    GC_CUDA(ctx, gc::launch_preprocess_bwd(src, S.sel, S.n_sel, S.cam, S.rp, S.bwd_g2d.as<float>(),
                                            S.touched.as<uint32_t>(), *out,
-                                           G ? ctx->bwd_motion.as<float>() : nullptr, s));
+                                           G ? S.bwd_motion.as<float>() : nullptr, s));
     if (G && S.per_gaussian) {
         // one motion per Gaussian: its motion terms are its gradient (zero when not selected)
         GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_GROUP_REDUCE));
         if (out->d_group_q) GC_CUDA(ctx, cudaMemsetAsync(out->d_group_q, 0, (size_t)G * 16, s));
         if (out->d_group_t) GC_CUDA(ctx, cudaMemsetAsync(out->d_group_t, 0, (size_t)G * 12, s));
-        GC_CUDA(ctx, gc::launch_motion_scatter(ctx->bwd_motion.as<float>(), S.sel, S.n_sel, out->d_group_q,
+        GC_CUDA(ctx, gc::launch_motion_scatter(S.bwd_motion.as<float>(), S.sel, S.n_sel, out->d_group_q,
                                                out->d_group_t, s));
     } else if (G) {
         GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_GROUP_REDUCE));
-        GC_CUDA(ctx, gc::launch_group_reduce(ctx->bwd_motion.as<float>(), src.group_id, S.sel, S.n_sel, G,
-                                             ctx->bwd_group.as<float>(), out->d_group_q, out->d_group_t, s));
+        GC_CUDA(ctx, gc::launch_group_reduce(S.bwd_motion.as<float>(), src.group_id, S.sel, S.n_sel, G,
+                                             S.bwd_group.as<float>(), out->d_group_q, out->d_group_t, s));
     }
     GC_CUDA(ctx, prof_mark(ctx, s, -1));
     return GC_OK;

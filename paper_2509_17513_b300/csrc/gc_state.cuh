@@ -83,6 +83,13 @@ struct gc_saved {
     DevBuf lv_T, lv_last;   // its per-level final transmittance and list position
     bool row_binned = false;  // lists binned by tile row: row segments padded to radix tiles
     DevBuf row_shift;         // per tile row: padded minus unpadded start of its segment
+    // Working memory of this state's forward (scan and sort scratch) and backward (per-entry
+    // partials, per-Gaussian screen-space and motion gradients, group partials): owned by the
+    // state, so that distinct states may run on different streams at once.  The backward's
+    // buffers are scratch, not results (mutable: a backward reads a const state).
+    DevBuf scratch;
+    mutable DevBuf bwd_part, bwd_g2d, bwd_motion, bwd_group;
+    mutable bool bwd_part_clean = false;  // bwd_part holds only zeros (see the reduce)
     // The sorted tile lists: the keys buffer of the last pass for row-binned lists (one word
     // per entry, column << 24 | rank), else the values of the key sort.
     uint32_t *lists() const {
@@ -108,12 +115,10 @@ struct gc_context {
     uint64_t launch_base = 0;
     gc_options opt{};
     gc_saved internal;
-    DevBuf scratch, bwd_part, bwd_g2d, bwd_motion, bwd_group;
     DevBuf field_part;              // per-block partial gradients of the motion source
     DevBuf field_h;                 // hash-grid encodings of the motion source (backward)
     DevBuf kde_scratch;             // KDE training form: histograms, bandwidths, partial sums
     DevBuf loss_part;               // L1 loss: one FP64 partial sum per CTA
-    bool bwd_part_clean = false;  // bwd_part holds only zeros (see the reduce)
     uint32_t *host_word = nullptr;  // pinned
     const gc_saved *last = nullptr; // state written by the most recent forward
     std::string err;

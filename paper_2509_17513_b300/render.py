@@ -557,12 +557,14 @@ class LevelsGraph:
     (gc_levels_graph): per frame the images of levels 1..levels and, with dL_dimages, their
     backward into that frame's gradient set.  frames: one MotionFrame (or None) per frame;
     outs / dL_dimages: n_frames * levels tensors (3, H, W), frame-major; grads: one dict per
-    frame (the same dict may repeat).  The tensors given here are the ones every launch
-    reads and writes: update them in place."""
+    frame (the same dict may repeat).  chains: independent branches of the graph (frame f
+    on chain f mod chains, each with its own saved state), so that one frame's sorts run
+    beside another frame's blend; results equal those of chains = 1.  The tensors given here
+    are the ones every launch reads and writes: update them in place."""
 
     def __init__(self, renderer: Renderer, gs: GaussianSet, frames: list, cameras: list, levels: int,
                  outs: list | None = None, dL_dimages: list | None = None, grads: list | None = None,
-                 stream=None):
+                 chains: int = 1, stream=None):
         nf = len(cameras)
         if len(frames) != nf:
             raise ValueError("one motion frame (or None) per camera")
@@ -596,7 +598,7 @@ class LevelsGraph:
         self._dls, self._gstructs = dls, gstructs
         h = C.c_void_p()
         st = lib().gc_levels_graph_create(renderer.ctx, C.byref(gs.struct), motions, nf, self._cams, self.levels,
-                                          self._imgs, dls, gstructs, _stream(stream), C.byref(h))
+                                          self._imgs, dls, gstructs, int(chains), _stream(stream), C.byref(h))
         check(st, renderer.ctx)
         self.handle = h
         cap, nodes = C.c_int64(), C.c_int64()

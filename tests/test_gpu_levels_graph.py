@@ -99,6 +99,46 @@ def test_graph_forward_backward_per_frame_gradients(gc, small):
     g.close()
 
 
+@pytest.mark.parametrize("chains", [2, 3])
+def test_chains_equal_one_chain(gc, small, chains):
+    """Frames split over independent graph branches (each with its own saved state) give
+    the images of one chain bit for bit; with a gradient set shared by every frame the
+    backwards stay in frame order, so it ends as the last frame's, equal to one chain's.
+    Five frames (uneven over the chains), three resolutions, forward and training step."""
+    scene, motion = small
+    r = gc.Renderer(0, tile=(8, 32), bg=(0.1, 0.2, 0.3))
+    gs = gc.GaussianSet.from_scene(scene)
+    frames = [gc.MotionFrame.from_motion(motion, f % 3) for f in range(5)]
+    cams = [_cams()[f % 3] for f in range(5)]
+    L = 6
+    gen = torch.Generator(device="cuda").manual_seed(17)
+    dls = [torch.randn((3, c.height, c.width), generator=gen, device="cuda") for c in cams for _ in range(L)]
+    results = []
+    for nc in (1, chains):
+        shared = r._single_grads(gs, frames[0])
+        own = [r._single_grads(gs, frames[f]) for f in range(5)]
+        gf = gc.LevelsGraph(r, gs, frames, cams, L, chains=nc)
+        gs_ = gc.LevelsGraph(r, gs, frames, cams, L, dL_dimages=dls, grads=[shared] * 5, chains=nc)
+        go = gc.LevelsGraph(r, gs, frames, cams, L, dL_dimages=dls, grads=own, chains=nc)
+        for g in (gf, gs_, go):
+            for o in g.outs:
+                o.fill_(-1.0)
+            g.launch()
+            g.check()
+        torch.cuda.synchronize()
+        results.append(([o.clone() for o in gf.outs], {k: v.clone() for k, v in shared.items()},
+                        [{k: v.clone() for k, v in gr.items()} for gr in own]))
+        for g in (gf, gs_, go):
+            g.close()
+    (i1, s1, o1), (i2, s2, o2) = results
+    for a, b in zip(i1, i2):
+        assert torch.equal(a, b)
+    for k in NAMES:
+        assert torch.equal(s1[k], s2[k]), k
+        for f in range(5):
+            assert torch.equal(o1[f][k], o2[f][k]), (f, k)
+
+
 def test_overflow_in_any_frame_is_reported(gc, small):
     r0, gs, frames, cams = _setup(gc, small)
     need = []
