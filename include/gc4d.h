@@ -356,7 +356,10 @@ GC_API gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *saved
  * depth); the graph holds, per batch, one gc_render_batch_forward and, when
  * dL_dimages is not NULL, one gc_render_batch_backward (the first batch overwrites
  * `grads`, the others add to them, so the gradient is summed over all requests in
- * order).  Creation runs the step eagerly (with key_capacity 0 it first measures
+ * order).  Each batch has a saved state of its own; batch b is captured on branch
+ * b mod min(batches, 4) of the graph, so the batches of different branches overlap on
+ * the GPU (one batch's sorts beside another's blend), while the backwards stay in batch
+ * order.  Creation runs the step eagerly (with key_capacity 0 it first measures
  * every batch's key count and fixes the capacity at the largest plus 5 %), then
  * captures it; launching replays every kernel with no host work.  The graph reads
  * and writes the same device arrays as at creation (Gaussians, motion, images,

@@ -1062,11 +1062,20 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
 
 // --------------------------------------------------------------------------- graphs
 
+namespace {
+constexpr int kGraphBranches = 4;  // capture streams of a batch graph
+}
+
 struct gc_batch_graph {
     gc_context *ctx = nullptr;
     std::vector<gc_saved *> states;  // one per batch of `depth` requests
     int depth = 0, n_req = 0;
     bool backward = false;
+    // batch b is captured on branch b mod branches (branch 0: the caller's stream); the
+    // backwards are chained in batch order by bwd_done
+    int branches = 1;
+    cudaStream_t side[kGraphBranches] = {};
+    cudaEvent_t fork = nullptr, bwd_done = nullptr, joins[kGraphBranches] = {};
     int64_t key_capacity = 0;
     int64_t kernel_nodes = 0;
     cudaStream_t own_stream = nullptr;
@@ -1082,28 +1091,38 @@ void graph_free(gc_batch_graph *G) {
     if (G->exec) cudaGraphExecDestroy(G->exec);
     if (G->graph) cudaGraphDestroy(G->graph);
     for (gc_saved *s : G->states) gc_saved_destroy(G->ctx, s);
+    for (int c = 0; c < kGraphBranches; ++c) {
+        if (G->side[c]) cudaStreamDestroy(G->side[c]);
+        if (G->joins[c]) cudaEventDestroy(G->joins[c]);
+    }
+    if (G->fork) cudaEventDestroy(G->fork);
+    if (G->bwd_done) cudaEventDestroy(G->bwd_done);
     if (G->own_stream) cudaStreamDestroy(G->own_stream);
     delete G;
 }
 
-// One pass over all batches: forwards, then backwards (the first overwrites the
-// gradients, the others add to them, so the step's gradient is summed in order).
+// One pass over all batches: per batch its forward and, for a training step, its backward
+// (the first overwrites the gradients, the others add to them, so the step's gradient is
+// summed in batch order: each backward waits for the previous one).  Batch b runs on
+// streams[b mod branches]; its state is its own, so the batches of different branches may
+// overlap on the GPU.
 gc_status graph_pass(gc_batch_graph *G, const gc_gaussians *g, const gc_motion *frames, int n_frames,
-                     const gc_request *reqs, const float *const *dL, gc_grads *grads, cudaStream_t s) {
+                     const gc_request *reqs, const float *const *dL, gc_grads *grads, const cudaStream_t *streams) {
     gc_status st;
     const int nb = (int)G->states.size();
     for (int b = 0; b < nb; ++b) {
+        const cudaStream_t s = streams[b % G->branches];
         const int q0 = b * G->depth, cnt = std::min(G->depth, G->n_req - q0);
         if ((st = gc_render_batch_forward(G->ctx, g, frames, n_frames, reqs + q0, cnt, G->states[b], s)) != GC_OK)
             return st;
-    }
-    if (G->backward)
-        for (int b = 0; b < nb; ++b) {
-            const int q0 = b * G->depth;
+        if (G->backward) {
+            if (G->branches > 1 && b > 0) GC_CUDA(G->ctx, cudaStreamWaitEvent(s, G->bwd_done, 0));
             if ((st = gc_render_batch_backward(G->ctx, G->states[b], g, frames, n_frames, dL + q0, b > 0 ? 1 : 0,
                                                grads, s)) != GC_OK)
                 return st;
+            if (G->branches > 1) GC_CUDA(G->ctx, cudaEventRecord(G->bwd_done, s));
         }
+    }
     return GC_OK;
 }
 
@@ -1148,6 +1167,23 @@ extern "C" gc_status gc_batch_graph_create(gc_context *ctx, const gc_gaussians *
         }
         s = G->own_stream;
     }
+    G->branches = std::min(nb, kGraphBranches);
+    {
+        bool ok = cudaEventCreateWithFlags(&G->fork, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&G->bwd_done, cudaEventDisableTiming) == cudaSuccess;
+        for (int c = 1; c < G->branches && ok; ++c)
+            ok = cudaStreamCreateWithFlags(&G->side[c], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&G->joins[c], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return bail(fail(ctx, GC_ERR_CUDA, "stream or event creation failed"));
+        }
+    }
+    cudaStream_t eager[kGraphBranches], capture[kGraphBranches];
+    for (int c = 0; c < kGraphBranches; ++c) {
+        eager[c] = s;
+        capture[c] = c == 0 ? s : G->side[c];
+    }
     // 1. key capacity: the caller's, or the largest batch's exact need plus 5 %
     int64_t cap = saved_opt.key_capacity;
     if (cap <= 0) {
@@ -1170,24 +1206,31 @@ extern "C" gc_status gc_batch_graph_create(gc_context *ctx, const gc_gaussians *
     }
     G->key_capacity = cap;
     ctx->opt.key_capacity = cap;
-    // 2. eager pass: sizes every buffer, uploads the request tables
-    if ((st = graph_pass(G, g, frames, n_frames, reqs, dL_dimages, grads, s)) != GC_OK) return bail(st);
+    // 2. eager pass on the caller's stream: sizes every buffer, uploads the request tables
+    if ((st = graph_pass(G, g, frames, n_frames, reqs, dL_dimages, grads, eager)) != GC_OK) return bail(st);
     if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ctx, GC_ERR_CUDA, "eager pass failed"));
     for (gc_saved *x : G->states)
         if ((st = batch_check(ctx, *x, s)) != GC_OK) return bail(st);
-    // 3. capture the same pass
+    // 3. capture the same pass, branch c on capture[c] (forked from s, joined back into s)
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(ctx, GC_ERR_CUDA, "cannot begin stream capture"));
     }
-    st = graph_pass(G, g, frames, n_frames, reqs, dL_dimages, grads, s);
+    cudaError_t ce = cudaEventRecord(G->fork, s);
+    for (int c = 1; c < G->branches && ce == cudaSuccess; ++c) ce = cudaStreamWaitEvent(G->side[c], G->fork, 0);
+    if (ce == cudaSuccess) st = graph_pass(G, g, frames, n_frames, reqs, dL_dimages, grads, capture);
+    for (int c = 1; c < G->branches && ce == cudaSuccess; ++c) {
+        ce = cudaEventRecord(G->joins[c], G->side[c]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, G->joins[c], 0);
+    }
     cudaGraph_t graph = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    const cudaError_t ee = cudaStreamEndCapture(s, &graph);
     G->graph = graph;
     if (st != GC_OK) return bail(st);
-    if (ce != cudaSuccess || !graph) {
+    if (ce != cudaSuccess || ee != cudaSuccess || !graph) {
         cudaGetLastError();
-        return bail(fail(ctx, GC_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ce)));
+        return bail(fail(ctx, GC_ERR_CUDA, "stream capture failed: %s",
+                         cudaGetErrorString(ce != cudaSuccess ? ce : ee)));
     }
     size_t n_nodes = 0;
     cudaGraphGetNodes(graph, nullptr, &n_nodes);

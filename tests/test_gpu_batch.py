@@ -285,9 +285,10 @@ def test_batch_workload_at_scale(gc):
 
 
 def test_batch_graph_step(gc, small):
-    """A step of 6 requests in batches of 2 as one native CUDA graph: images equal the
-    single renders bit for bit after a replay; gradients equal one eager batch over all
-    requests up to float summation order."""
+    """A step of 6 requests in batches of 2 as one native CUDA graph (three batches on three
+    branches of the graph): images equal the single renders bit for bit after a replay;
+    gradients equal the eager batches summed in batch order bit for bit, and one eager batch
+    over all requests up to float summation order."""
     scene, motion, reqs = small
     gs = gc.GaussianSet.from_scene(scene)
     frames = _frames(gc, motion)
@@ -311,6 +312,15 @@ def test_batch_graph_step(gc, small):
     for k, b in ref_g.items():
         a = graph.grads[k]
         assert torch.allclose(a, b, rtol=0, atol=1e-5 * float(b.abs().max()) + 1e-7), k
+    # the same batches eagerly, one after the other: the branched graph sums in batch order
+    seq = r.batch_grads(gs, frames)
+    for b in range(3):
+        sb = gc.Saved(r)
+        r.batch_forward(gs, frames, trip[2 * b:2 * b + 2], sb)
+        r.batch_backward(sb, gs, frames, dls[2 * b:2 * b + 2], grads=seq, accumulate=b > 0)
+    torch.cuda.synchronize()
+    for k in seq:
+        assert torch.equal(seq[k], graph.grads[k]), k
     graph.launch()  # replays are deterministic
     g1 = {k: v.clone() for k, v in graph.grads.items()}
     graph.launch()
