@@ -84,10 +84,10 @@ def stage_work(stage: str, w: dict):
         return n * 16, "bytes", n * (4 + 4 * 16)   # one-sweep: histogram read + 4 passes
     if stage == "scan":                # rank gather of record + count, scan of the counts
         return n * (4 + 2 * (REC_BYTES + 4) + 8), "bytes", None
-    if stage == "emit":                # record read per Gaussian, (tile, rank) pair written
-        return n * (REC_BYTES + 8) + k * 8, "bytes", None
-    if stage == "tile_sort":           # one read + one write of 8 B pairs; 2 passes x 20 B
-        return k * 16, "bytes", k * 40
+    if stage == "emit":                # record read per Gaussian; 12 B per (tile, Gaussian) pair
+        return n * (REC_BYTES + 8) + k * 12, "bytes", n * (REC_BYTES + 8) + k * 4  # one-word entries
+    if stage == "tile_sort":           # 24 B per pair: one read + one write of a 12 B key-value pair;
+        return k * 24, "bytes", k * 12  # one keys-only pass: histogram read 4 + read 4 + write 4
     if stage == "ranges":  # row-binned lists: two scanned digit counts read, one range written per tile
         return w["tiles"] * 16, "bytes", None
     if stage == "reduce":              # 36 B of partials per entry in, 36 B per Gaussian out

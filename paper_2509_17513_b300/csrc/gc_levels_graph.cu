@@ -5,7 +5,7 @@
 // gc_render_levels_backward, on a saved state that the graph owns.  With a fixed key
 // capacity neither call synchronises, allocates or copies to the host once the buffers are
 // sized, so the whole step is captured after one eager pass and replayed with no host work:
-// the launch gaps between the ~15 kernels of every frame disappear.  The emit kernel keeps
+// the launch gaps between the ~15 kernels of every frame disappear.  The binning keeps
 // the largest key count of any frame on the state, which gc_levels_graph_check compares
 // with the capacity.
 //
