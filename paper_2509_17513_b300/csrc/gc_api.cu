@@ -484,9 +484,14 @@ gc_status gc_check(gc_context *ctx, void *stream) {
 
 }  // extern "C"
 
+// order_wait / order_done (internal callers; NULL for the public entry points): the
+// backward's writes into the caller's gradient buffers (the zeros of unselected layers, the
+// chain rule, the motion sums) wait for order_wait and are followed by a record of order_done;
+// the reverse blend and the reduce, which touch only the state's own buffers, do not wait.
 static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, const gc_gaussians *g,
                                       const gc_motion *motion, const float *dL_dimage,
-                                      const float *const *dL_levels, gc_grads *out, void *stream) {
+                                      const float *const *dL_levels, gc_grads *out, void *stream,
+                                      cudaEvent_t order_wait = nullptr, cudaEvent_t order_done = nullptr) {
     if (!ctx) return GC_ERR_INVALID_ARG;
     if ((!dL_dimage && !dL_levels) || !out) return fail(ctx, GC_ERR_INVALID_ARG, "dL_dimage or grads is NULL");
     const gc_saved &S = saved ? *saved : ctx->internal;
@@ -511,21 +516,33 @@ static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, co
     cudaStream_t s = (cudaStream_t)stream;
     const int K3 = 3 * (g->sh_degree + 1) * (g->sh_degree + 1);
 
-    // Gaussians outside the selected layers receive zero gradient
-    for (int l = 0; l < S.n_layers; ++l) {
-        if ((S.layer_mask >> l) & 1u) continue;
-        const int64_t a = S.layer_offsets[l], b = S.layer_offsets[l + 1];
-        if (b <= a) continue;
-        if (out->d_means) GC_CUDA(ctx, cudaMemsetAsync(out->d_means + 3 * a, 0, (size_t)(b - a) * 12, s));
-        if (out->d_log_scales) GC_CUDA(ctx, cudaMemsetAsync(out->d_log_scales + 3 * a, 0, (size_t)(b - a) * 12, s));
-        if (out->d_quats) GC_CUDA(ctx, cudaMemsetAsync(out->d_quats + 4 * a, 0, (size_t)(b - a) * 16, s));
-        if (out->d_opacity_logits) GC_CUDA(ctx, cudaMemsetAsync(out->d_opacity_logits + a, 0, (size_t)(b - a) * 4, s));
-        if (out->d_sh) GC_CUDA(ctx, cudaMemsetAsync(out->d_sh + (int64_t)K3 * a, 0, (size_t)(b - a) * K3 * 4, s));
-    }
+    // Gaussians outside the selected layers receive zero gradient (written after the blend and
+    // the reduce, with the other writes into the caller's buffers)
+    auto zero_unselected = [&]() -> cudaError_t {
+        for (int l = 0; l < S.n_layers; ++l) {
+            if ((S.layer_mask >> l) & 1u) continue;
+            const int64_t a = S.layer_offsets[l], b = S.layer_offsets[l + 1];
+            if (b <= a) continue;
+            cudaError_t e = cudaSuccess;
+            if (out->d_means && e == cudaSuccess) e = cudaMemsetAsync(out->d_means + 3 * a, 0, (size_t)(b - a) * 12, s);
+            if (out->d_log_scales && e == cudaSuccess)
+                e = cudaMemsetAsync(out->d_log_scales + 3 * a, 0, (size_t)(b - a) * 12, s);
+            if (out->d_quats && e == cudaSuccess) e = cudaMemsetAsync(out->d_quats + 4 * a, 0, (size_t)(b - a) * 16, s);
+            if (out->d_opacity_logits && e == cudaSuccess)
+                e = cudaMemsetAsync(out->d_opacity_logits + a, 0, (size_t)(b - a) * 4, s);
+            if (out->d_sh && e == cudaSuccess)
+                e = cudaMemsetAsync(out->d_sh + (int64_t)K3 * a, 0, (size_t)(b - a) * K3 * 4, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
     const int G = S.has_motion ? S.n_groups : 0;
     if (S.n_sel == 0) {
+        if (order_wait) GC_CUDA(ctx, cudaStreamWaitEvent(s, order_wait, 0));
+        GC_CUDA(ctx, zero_unselected());
         if (G && out->d_group_q) GC_CUDA(ctx, cudaMemsetAsync(out->d_group_q, 0, (size_t)G * 16, s));
         if (G && out->d_group_t) GC_CUDA(ctx, cudaMemsetAsync(out->d_group_t, 0, (size_t)G * 12, s));
+        if (order_done) GC_CUDA(ctx, cudaEventRecord(order_done, s));
         return GC_OK;
     }
     const int64_t K = S.K > 0 ? S.K : 1;
@@ -560,6 +577,8 @@ static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, co
                                            S.bwd_g2d.as<float>(), s));
     S.bwd_part_clean = true;
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_PREPROCESS_BWD));
+    if (order_wait) GC_CUDA(ctx, cudaStreamWaitEvent(s, order_wait, 0));
+    GC_CUDA(ctx, zero_unselected());
     GC_CUDA(ctx, gc::launch_preprocess_bwd(src, S.sel, S.n_sel, S.cam, S.rp, S.bwd_g2d.as<float>(),
                                            S.touched.as<uint32_t>(), *out,
                                            G ? S.bwd_motion.as<float>() : nullptr, s));
@@ -575,8 +594,17 @@ static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, co
         GC_CUDA(ctx, gc::launch_group_reduce(S.bwd_motion.as<float>(), src.group_id, S.sel, S.n_sel, G,
                                              S.bwd_group.as<float>(), out->d_group_q, out->d_group_t, s));
     }
+    if (order_done) GC_CUDA(ctx, cudaEventRecord(order_done, s));
     GC_CUDA(ctx, prof_mark(ctx, s, -1));
     return GC_OK;
+}
+
+gc_status levels_backward_ordered(gc_context *ctx, const gc_saved *saved, const gc_gaussians *g,
+                                  const gc_motion *motion, const float *const *dL_dimages, gc_grads *out,
+                                  cudaStream_t stream, cudaEvent_t order_wait, cudaEvent_t order_done) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    if (!dL_dimages) return fail(ctx, GC_ERR_INVALID_ARG, "dL_dimages is NULL");
+    return render_backward_impl(ctx, saved, g, motion, nullptr, dL_dimages, out, stream, order_wait, order_done);
 }
 
 extern "C" gc_status gc_render_backward(gc_context *ctx, const gc_saved *saved, const gc_gaussians *g,

@@ -13,9 +13,10 @@
 // lists, scratch and backward buffers) and its own capture stream forked from the caller's,
 // so the graph holds C independent sequences of frames.  A frame's preprocess, sorts and
 // binning are short, latency-bound kernels that leave most of the GPU idle; with C > 1 they
-// run beside another frame's blend.  The backwards stay in frame order (frame f's waits for
-// frame f-1's), so gradient sets shared by several frames are written exactly as by one
-// chain; images and gradients equal those of C = 1.
+// run beside another frame's blend.  The backwards' writes into the gradient sets stay in frame
+// order (frame f's wait for frame f-1's; its reverse blend and reduce do not wait), so gradient
+// sets shared by several frames are written exactly as by one chain; images and gradients equal
+// those of C = 1.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -70,7 +71,7 @@ struct LevelsStep {
 };
 
 // Every frame on its chain's state and stream (streams[c]; all the caller's stream outside
-// capture).  Backwards are ordered by bwd_done.
+// capture).  The backwards' gradient writes are ordered by bwd_done.
 gc_status levels_pass(gc_levels_graph *G, const LevelsStep &P, const cudaStream_t *streams, int64_t *max_keys) {
     for (int f = 0; f < P.n_frames; ++f) {
         const int c = f % G->chains;
@@ -82,10 +83,12 @@ gc_status levels_pass(gc_levels_graph *G, const LevelsStep &P, const cudaStream_
         if (st != GC_OK) return st;
         if (max_keys) *max_keys = std::max<int64_t>(*max_keys, state->K);
         if (P.dL) {
-            if (G->chains > 1 && f > 0) GC_CUDA(G->ctx, cudaStreamWaitEvent(s, G->bwd_done, 0));
-            st = gc_render_levels_backward(G->ctx, state, P.g, m, P.dL + (size_t)f * P.levels, &P.grads[f], s);
+            // the writes into the gradient set wait for the previous frame's; the reverse blend
+            // and the reduce run as soon as this chain reaches them
+            const bool ordered = G->chains > 1;
+            st = levels_backward_ordered(G->ctx, state, P.g, m, P.dL + (size_t)f * P.levels, &P.grads[f], s,
+                                         ordered && f > 0 ? G->bwd_done : nullptr, ordered ? G->bwd_done : nullptr);
             if (st != GC_OK) return st;
-            if (G->chains > 1) GC_CUDA(G->ctx, cudaEventRecord(G->bwd_done, s));
         }
     }
     return GC_OK;

@@ -148,6 +148,12 @@ inline gc_status fail(gc_context *ctx, gc_status s, const char *fmt, ...) {
 // GC_ERR_CAPACITY if a forward on S since the last check needed more keys than its fixed
 // capacity (synchronises `stream`, the stream of those forwards; S must have a fixed capacity).
 gc_status capacity_check(gc_context *ctx, const gc_saved &S, cudaStream_t stream);
+// gc_render_levels_backward whose writes into `out` wait for order_wait and are followed by a
+// record of order_done (either may be NULL); the reverse blend and reduce before them do not
+// wait (gc_api.cu; used by the multi-frame graphs to keep shared gradient sets in frame order).
+gc_status levels_backward_ordered(gc_context *ctx, const gc_saved *saved, const gc_gaussians *g,
+                                  const gc_motion *motion, const float *const *dL_dimages, gc_grads *out,
+                                  cudaStream_t stream, cudaEvent_t order_wait, cudaEvent_t order_done);
 
 inline cudaError_t prof_event(gc_context *ctx, cudaStream_t s, int &idx) {
     idx = ctx->prof_used;
