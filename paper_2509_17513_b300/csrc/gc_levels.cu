@@ -46,6 +46,12 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
     uint32_t lv = inside ? ((1u << L) - 1u) : 0u;  // levels still blending
     uint32_t act = lv ? (1u << lane) : 0u;
     float T[NL], C0[NL], C1[NL], C2[NL];
+    // Transmittance of the highest level still blending.  Level l blends a subset of level
+    // l + 1's entries with the same alphas, so T[l] >= T[l + 1]: the levels still blending
+    // are always 0..k, only level k can be the first to stop, and an entry that reaches any
+    // of them reaches level k.  Ttop follows T[k] with the same operations, so one test
+    // decides whether any level stops at an entry; the levels are only walked when one does.
+    float Ttop = 1.f;
     uint32_t last[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
@@ -96,22 +102,31 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
                 const float alpha = fminf(kAlphaMax, blend_raw_alpha(bb.y, p2, G));
                 if (alpha < kAlphaMin) continue;
                 const float4 col = sm.c[k];
+                const float om = 1.f - alpha;
+                uint32_t bl = lm;  // the levels that blend the entry
+                if (Ttop * om < kTStop) {
+                    // some levels stop here: those whose transmittance would fall below the
+                    // threshold (a top run of lm), then Ttop moves to the new highest level
+#pragma unroll
+                    for (int l = 0; l < NL; ++l)
+                        if (((lm >> l) & 1u) && T[l] * om < kTStop) bl &= ~(1u << l);
+                    lv &= ~(lm & ~bl);
+#pragma unroll
+                    for (int l = 0; l < NL; ++l)
+                        if ((lv >> l) & 1u) Ttop = T[l];
+                    if (!lv) act = 0u;
+                }
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
-                    if (!((lm >> l) & 1u)) continue;
-                    const float Tn = T[l] * (1.f - alpha);
-                    if (Tn < kTStop) {
-                        lv &= ~(1u << l);
-                        continue;
-                    }
+                    if (!((bl >> l) & 1u)) continue;
                     const float w = alpha * T[l];
                     C0[l] = fmaf(col.x, w, C0[l]);
                     C1[l] = fmaf(col.y, w, C1[l]);
                     C2[l] = fmaf(col.z, w, C2[l]);
-                    T[l] = Tn;
+                    T[l] = T[l] * om;
                     last[l] = (uint32_t)(b + k + 1);
                 }
-                if (!lv) act = 0u;
+                if (bl) Ttop = Ttop * om;
             }
         }
     }
