@@ -171,7 +171,10 @@ __global__ void __launch_bounds__(256, 4) k_blend_levels_bwd(
         uint32_t e[256];
         uint8_t lay[256];
         float wpart[64][8][9];
-        uint8_t wrote[64][8];      // per entry of the group and warp: partial written
+        // per entry of the group and warp: partial written; byte (warp & 3) of word
+        // wrote[warp >> 2][entry], so that the 32 lanes of a relevance step write 32
+        // consecutive words (distinct banks)
+        uint32_t wrote[2][64];
         uint32_t last[NL][256];    // per level and pixel: list position after the last blend
         uint32_t wsuf[8][16];      // per warp: max over its pixels and levels l >= m of last[l]
         uint32_t last_max;
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(256, 4) k_blend_levels_bwd(
                 if (kq < stop) {
                     const int sq = kq - lo;
                     rel = (sm.m[warp * 256 + sq] & wpix) != 0u && (uint32_t)kq < sm.wsuf[warp][sm.lay[sq]];
-                    sm.wrote[kq - gbot][warp] = rel ? 1 : 0;
+                    reinterpret_cast<uint8_t *>(&sm.wrote[warp >> 2][kq - gbot])[warp & 3] = rel ? 1 : 0;
                 }
                 uint32_t todo = __ballot_sync(0xffffffffu, rel);
                 while (todo) {
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(256, 4) k_blend_levels_bwd(
             __syncthreads();
             for (int idx = threadIdx.x; idx < (gtop - gbot) * 9; idx += 256) {
                 const int q = idx / 9, c = idx - q * 9;
-                const uint2 wr = *reinterpret_cast<const uint2 *>(&sm.wrote[q][0]);
+                const uint2 wr = make_uint2(sm.wrote[0][q], sm.wrote[1][q]);
                 float acc = 0.f;
 #pragma unroll
                 for (int w2 = 0; w2 < 8; ++w2) {
