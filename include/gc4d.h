@@ -457,6 +457,19 @@ GC_API gc_status gc_motion_field_backward(gc_context *ctx, const gc_motion_field
                                           int64_t n, const float *d_q, const float *d_t,
                                           gc_motion_field_grads *out, void *stream);
 
+/* The same pair with the hash-grid encodings kept between them (a training step): the forward
+ * also writes every Gaussian's encoding to `encodings` (device, n x 32 FP32 rows, levels
+ * beyond n_levels zero, 16-byte aligned, caller-owned), and the backward reads them instead of
+ * gathering the table again.  The backward's results equal gc_motion_field_backward's bit for
+ * bit when `encodings` holds the forward's for the same means and table.  Errors: those of
+ * the pair above, GC_ERR_INVALID_ARG for a NULL or unaligned `encodings`. */
+GC_API gc_status gc_motion_field_forward_save(gc_context *ctx, const gc_motion_field *field, const float *means,
+                                              int64_t n, float *q, float *t, float *encodings, void *stream);
+GC_API gc_status gc_motion_field_backward_saved(gc_context *ctx, const gc_motion_field *field,
+                                                const float *means, int64_t n, const float *encodings,
+                                                const float *d_q, const float *d_t, gc_motion_field_grads *out,
+                                                void *stream);
+
 /* KDE rate estimate of the keyframe RD loss (Sec. 3.3, the PMF equation): for each of
  * n_channels channels of n FP32 values (channel c at y + c * stride, device), the bits per
  * symbol of its quantised symbols s_i = round(y_i) (half to even) under the Gaussian kernel

@@ -111,6 +111,8 @@ SIGNATURES = {
     "gc_render_levels_backward": (C.c_int, [P, P, P, P, P, P, P]),
     "gc_motion_field_forward": (C.c_int, [P, P, P, C.c_int64, P, P, P]),
     "gc_motion_field_backward": (C.c_int, [P, P, P, C.c_int64, P, P, P, P]),
+    "gc_motion_field_forward_save": (C.c_int, [P, P, P, C.c_int64, P, P, P, P]),
+    "gc_motion_field_backward_saved": (C.c_int, [P, P, P, C.c_int64, P, P, P, P, P]),
     "gc_kde_rate": (C.c_int, [P, P, C.c_int32, C.c_int64, C.c_int64, P, P]),
     "gc_kde_rate_grad": (C.c_int, [P, P, C.c_int32, C.c_int64, C.c_int64, P, P, P, P]),
     "gc_l1_loss": (C.c_int, [P, P, P, C.c_int64, C.c_float, P, P, P]),

@@ -118,8 +118,11 @@ __device__ __forceinline__ void encode(const Field &F, const float *mu, float h[
     }
 }
 
+// hrows: NULL, or the encodings to keep for the backward (kIn floats per Gaussian, as written
+// by k_field_encode).
 __global__ void __launch_bounds__(kFT) k_field_fwd(Field F, const float *__restrict__ means, int64_t n,
-                                                   float *__restrict__ q, float *__restrict__ t) {
+                                                   float *__restrict__ q, float *__restrict__ t,
+                                                   float4 *__restrict__ hrows) {
     __shared__ __align__(16) FieldSmem s;
     stage_weights(F, s);
     __syncthreads();
@@ -128,6 +131,12 @@ __global__ void __launch_bounds__(kFT) k_field_fwd(Field F, const float *__restr
     const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
     float h[kIn];
     encode(F, mu, h);
+    if (hrows) {
+        float4 *row = hrows + (size_t)i * (kIn / 4);
+#pragma unroll
+        for (int q4 = 0; q4 < kIn / 4; ++q4)
+            row[q4] = make_float4(h[4 * q4], h[4 * q4 + 1], h[4 * q4 + 2], h[4 * q4 + 3]);
+    }
     float o[7];
 #pragma unroll
     for (int c = 0; c < 7; ++c) o[c] = s.b2[c];
@@ -408,8 +417,8 @@ gc_status make_field(gc_context *ctx, const gc_motion_field *f, Field &F) {
 
 }  // namespace gc
 
-extern "C" gc_status gc_motion_field_forward(gc_context *ctx, const gc_motion_field *field, const float *means,
-                                             int64_t n, float *q, float *t, void *stream) {
+static gc_status field_forward(gc_context *ctx, const gc_motion_field *field, const float *means, int64_t n,
+                               float *q, float *t, float *encodings, void *stream) {
     if (!ctx) return GC_ERR_INVALID_ARG;
     gc::Field F;
     gc_status st = gc::make_field(ctx, field, F);
@@ -417,17 +426,30 @@ extern "C" gc_status gc_motion_field_forward(gc_context *ctx, const gc_motion_fi
     if (n < 0) return fail(ctx, GC_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return GC_OK;
     if (!means || !q || !t) return fail(ctx, GC_ERR_INVALID_ARG, "means, q or t is NULL");
+    if (reinterpret_cast<uintptr_t>(encodings) & 15) return fail(ctx, GC_ERR_INVALID_ARG, "encodings must be 16-byte aligned");
     DeviceGuard dg(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    gc::k_field_fwd<<<(unsigned)((n + gc::kFT - 1) / gc::kFT), gc::kFT, 0, s>>>(F, means, n, q, t);
+    gc::k_field_fwd<<<(unsigned)((n + gc::kFT - 1) / gc::kFT), gc::kFT, 0, s>>>(F, means, n, q, t,
+                                                                              reinterpret_cast<float4 *>(encodings));
     gc::note_launches(1);
     GC_CUDA(ctx, cudaGetLastError());
     return GC_OK;
 }
 
-extern "C" gc_status gc_motion_field_backward(gc_context *ctx, const gc_motion_field *field, const float *means,
-                                              int64_t n, const float *d_q, const float *d_t,
-                                              gc_motion_field_grads *out, void *stream) {
+extern "C" gc_status gc_motion_field_forward(gc_context *ctx, const gc_motion_field *field, const float *means,
+                                             int64_t n, float *q, float *t, void *stream) {
+    return field_forward(ctx, field, means, n, q, t, nullptr, stream);
+}
+
+extern "C" gc_status gc_motion_field_forward_save(gc_context *ctx, const gc_motion_field *field, const float *means,
+                                                  int64_t n, float *q, float *t, float *encodings, void *stream) {
+    if (ctx && !encodings) return fail(ctx, GC_ERR_INVALID_ARG, "encodings is NULL");
+    return field_forward(ctx, field, means, n, q, t, encodings, stream);
+}
+
+static gc_status field_backward(gc_context *ctx, const gc_motion_field *field, const float *means, int64_t n,
+                                const float *encodings, const float *d_q, const float *d_t,
+                                gc_motion_field_grads *out, void *stream) {
     if (!ctx) return GC_ERR_INVALID_ARG;
     gc::Field F;
     gc_status st = gc::make_field(ctx, field, F);
@@ -451,16 +473,36 @@ extern "C" gc_status gc_motion_field_backward(gc_context *ctx, const gc_motion_f
     const int64_t nchunks = (n + gc::kFT - 1) / gc::kFT;
     const int nblocks = (int)std::min<int64_t>(nchunks, gc::kBwdGrid);
     GC_CUDA(ctx, grow(ctx->field_part, (size_t)nblocks * gc::kPartials * 4));
-    GC_CUDA(ctx, grow(ctx->field_h, (size_t)n * gc::kIn * 4));
     GC_CUDA(ctx, cudaFuncSetAttribute(gc::k_field_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)gc::kBwdDyn));
-    float4 *hrows = ctx->field_h.as<float4>();
-    gc::k_field_encode<<<(unsigned)nchunks, gc::kFT, 0, s>>>(F, means, n, hrows);
+    const float4 *hrows = reinterpret_cast<const float4 *>(encodings);
+    if (!hrows) {  // recompute the encodings (latency-bound table gathers)
+        GC_CUDA(ctx, grow(ctx->field_h, (size_t)n * gc::kIn * 4));
+        gc::k_field_encode<<<(unsigned)nchunks, gc::kFT, 0, s>>>(F, means, n, ctx->field_h.as<float4>());
+        gc::note_launches(1);
+        hrows = ctx->field_h.as<float4>();
+    }
     gc::k_field_bwd<<<nblocks, gc::kFT, gc::kBwdDyn, s>>>(F, means, hrows, n, d_q, d_t,
                                                           ctx->field_part.as<float>(), out->table);
     gc::FieldGrads g{{out->w1t, out->w1r}, {out->b1t, out->b1r}, {out->w2t, out->w2r}, {out->b2t, out->b2r}};
     gc::k_field_reduce<<<(gc::kPartials + 255) / 256, 256, 0, s>>>(ctx->field_part.as<float>(), nblocks, din, g);
-    gc::note_launches(3);
+    gc::note_launches(2);
     GC_CUDA(ctx, cudaGetLastError());
     return GC_OK;
+}
+
+extern "C" gc_status gc_motion_field_backward(gc_context *ctx, const gc_motion_field *field, const float *means,
+                                              int64_t n, const float *d_q, const float *d_t,
+                                              gc_motion_field_grads *out, void *stream) {
+    return field_backward(ctx, field, means, n, nullptr, d_q, d_t, out, stream);
+}
+
+extern "C" gc_status gc_motion_field_backward_saved(gc_context *ctx, const gc_motion_field *field,
+                                                    const float *means, int64_t n, const float *encodings,
+                                                    const float *d_q, const float *d_t, gc_motion_field_grads *out,
+                                                    void *stream) {
+    if (!ctx) return GC_ERR_INVALID_ARG;
+    if (n > 0 && !encodings) return fail(ctx, GC_ERR_INVALID_ARG, "encodings is NULL");
+    if (reinterpret_cast<uintptr_t>(encodings) & 15) return fail(ctx, GC_ERR_INVALID_ARG, "encodings must be 16-byte aligned");
+    return field_backward(ctx, field, means, n, encodings, d_q, d_t, out, stream);
 }

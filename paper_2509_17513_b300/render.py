@@ -340,27 +340,39 @@ class Renderer:
 
     # ---- per-Gaussian motion source ---------------------------------------------------
 
-    def motion_field_forward(self, field: "MotionField", means: torch.Tensor, stream=None):
+    def motion_field_forward(self, field: "MotionField", means: torch.Tensor, encodings: torch.Tensor | None = None,
+                             stream=None):
         """(q (n,4), t (n,3)): each Gaussian's rotation and translation from the motion source
-        at the frame t-1 positions ``means``; use as MotionFrame(q, t, per_gaussian=True)."""
+        at the frame t-1 positions ``means``; use as MotionFrame(q, t, per_gaussian=True).
+        encodings: optional (n, 32) FP32 tensor that receives the hash-grid encodings for
+        motion_field_backward (a training step)."""
         n = int(means.shape[0])
         dev = means.device
         q = torch.empty((n, 4), device=dev)
         t = torch.empty((n, 3), device=dev)
-        check(lib().gc_motion_field_forward(self.ctx, C.byref(field.struct), means.contiguous().data_ptr(), n,
-                                            q.data_ptr(), t.data_ptr(), _stream(stream)), self.ctx)
+        if encodings is None:
+            check(lib().gc_motion_field_forward(self.ctx, C.byref(field.struct), means.contiguous().data_ptr(), n,
+                                                q.data_ptr(), t.data_ptr(), _stream(stream)), self.ctx)
+        else:
+            check(lib().gc_motion_field_forward_save(self.ctx, C.byref(field.struct), means.contiguous().data_ptr(),
+                                                     n, q.data_ptr(), t.data_ptr(), encodings.data_ptr(),
+                                                     _stream(stream)), self.ctx)
         return q, t
 
     def motion_field_backward(self, field: "MotionField", means: torch.Tensor, d_q: torch.Tensor,
-                              d_t: torch.Tensor, stream=None) -> dict:
-        """Gradients of the motion source's table and weights given dL/dq, dL/dt."""
+                              d_t: torch.Tensor, encodings: torch.Tensor | None = None, stream=None) -> dict:
+        """Gradients of the motion source's table and weights given dL/dq, dL/dt; with the
+        forward's saved ``encodings`` the table is not gathered again."""
         g = {k: torch.empty_like(v) for k, v in field.t.items()}
         s = _abi.MotionFieldGrads()
         for k in MotionField.NAMES:
             setattr(s, k, g[k].data_ptr())
-        check(lib().gc_motion_field_backward(self.ctx, C.byref(field.struct), means.contiguous().data_ptr(),
-                                             int(means.shape[0]), d_q.contiguous().data_ptr(),
-                                             d_t.contiguous().data_ptr(), C.byref(s), _stream(stream)), self.ctx)
+        args = (self.ctx, C.byref(field.struct), means.contiguous().data_ptr(), int(means.shape[0]))
+        tail = (d_q.contiguous().data_ptr(), d_t.contiguous().data_ptr(), C.byref(s), _stream(stream))
+        if encodings is None:
+            check(lib().gc_motion_field_backward(*args, *tail), self.ctx)
+        else:
+            check(lib().gc_motion_field_backward_saved(*args, encodings.data_ptr(), *tail), self.ctx)
         return g
 
     # ---- KDE rate estimate --------------------------------------------------------------

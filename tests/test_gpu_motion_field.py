@@ -37,7 +37,12 @@ def test_field_forward_backward_matches_oracle(gc, levels, log2_T, n):
     field = gc.MotionField(p)
     mu_d = torch.from_numpy(mu).cuda()
     q, t = r.motion_field_forward(field, mu_d)
+    # the training form keeps the encodings: same q and t bit for bit
+    enc = torch.full((n, 32), float("nan"), device="cuda")
+    q_s, t_s = r.motion_field_forward(field, mu_d, encodings=enc)
     torch.cuda.synchronize()
+    assert torch.equal(q_s, q) and torch.equal(t_s, t)
+    assert bool(torch.isfinite(enc).all()) and not enc[:, 2 * levels:].any()
     q, t = q.cpu().numpy().astype(np.float64), t.cpu().numpy().astype(np.float64)
     assert np.abs(t - t_ref).max() <= 1e-5 * np.abs(t_ref).max() + 1e-7
     assert np.abs(q - q_ref).max() <= 1e-5 * np.abs(q_ref).max() + 1e-7
@@ -51,9 +56,20 @@ def test_field_forward_backward_matches_oracle(gc, levels, log2_T, n):
         assert _rel(a, want[k]) <= 1e-4, (k, _rel(a, want[k]))
     # the weight gradients are summed in a fixed order: bit-reproducible
     again = r.motion_field_backward(field, mu_d, torch.from_numpy(d_q).cuda(), torch.from_numpy(d_t).cuda())
+    # with the forward's encodings: the same weight gradients bit for bit, the table gradient
+    # (vector atomics, order not fixed) within float summation order
+    saved = r.motion_field_backward(field, mu_d, torch.from_numpy(d_q).cuda(), torch.from_numpy(d_t).cuda(),
+                                    encodings=enc)
     torch.cuda.synchronize()
     for k in ("w1t", "b1t", "w2t", "b2t", "w1r", "b1r", "w2r", "b2r"):
         assert torch.equal(got[k], again[k]), k
+        assert torch.equal(got[k], saved[k]), k
+    # (each table entry sums up to hundreds of Gaussians' corner terms with float atomics in
+    # no fixed order: a few 1e-6 relative between two runs)
+    a, b = saved["table"].double(), got["table"].double()
+    assert float((a - b).norm() / b.norm()) <= 1e-5
+    sv_t = saved["table"].cpu().numpy().astype(np.float64)
+    assert _rel(sv_t, want["table"]) <= 1e-4
 
 
 def test_field_drives_the_renderer(gc):
@@ -106,6 +122,13 @@ def test_field_argument_errors(gc):
     p = scenes.motion_field_params(rng, n_levels=4, log2_T=10)
     r = gc.Renderer(0)
     field = gc.MotionField(p)
+    # saved encodings must be 16-byte aligned rows
+    buf = torch.zeros(4 * 32 + 1, device="cuda")
+    with pytest.raises(gc.GCError, match="aligned"):
+        r.motion_field_forward(field, torch.zeros((4, 3), device="cuda"), encodings=buf[1:].view(4, 32))
+    with pytest.raises(gc.GCError, match="aligned"):
+        r.motion_field_backward(field, torch.zeros((4, 3), device="cuda"), torch.zeros((4, 4), device="cuda"),
+                                torch.zeros((4, 3), device="cuda"), encodings=buf[1:].view(4, 32))
     field.struct.n_levels = 17
     with pytest.raises(gc.GCError, match="n_levels"):
         r.motion_field_forward(field, torch.zeros((4, 3), device="cuda"))
