@@ -182,7 +182,8 @@ size_t scan_partials_size(int64_t n);
 cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
                                   uint32_t *partials, cudaStream_t st, uint32_t *err = nullptr);
 
-// Stable LSD radix sort of (key, value) pairs on key bits [0, end_bit).
+// Stable LSD radix sort of (key, value) pairs on key bits [begin_bit, end_bit), or of keys
+// alone (vals NULL: the keys are always written).
 // keys[0]/vals[0] hold the input; the sorted output ends in buffer *out_buf.
 // n_dev: optional device count (<= n_max) read by the kernels; n_max sizes the grid.
 // keys_out = false: the last pass writes only the values (the sorted keys are not kept).
@@ -195,7 +196,8 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
 // blocks starts at scratch[256 b0 + d nb]; gc_bucket.cuh reads tile ranges from them).
 size_t radix_scratch_words(int64_t n_max);
 int radix_tile_keys();
-// Keys only (vals NULL): the keys are sorted on bits [begin_bit, end_bit) and always written.
+// scratch: radix_scratch_words(n_max) words, 8-byte aligned (the segmented mode keeps a
+// per-block table of count-array bases and strides there).
 cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
                              const uint32_t *n_dev, int end_bit, uint32_t *scratch, int *out_buf,
                              cudaStream_t st, uint32_t *err, bool keys_out = true,
