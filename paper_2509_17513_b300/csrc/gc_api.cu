@@ -248,7 +248,7 @@ static gc_status render_forward_impl(gc_context *ctx, const gc_gaussians *g, con
         const int64_t kk = K > 0 ? K : 1;
         // binning by tile row pads every row's segment to whole radix tiles: room for that
         // beyond the entries (the capacity counts entries only)
-        const int64_t kpad = (kk + (int64_t)rp.nty * gc::radix_tile_keys() + 3) & ~int64_t(3);
+        const int64_t kpad = (kk + (int64_t)rp.nty * gc::radix_tile_keys(true) + 3) & ~int64_t(3);
         const bool rows = gc::bucket_binning_fits(rp, n_sel) && kpad <= 0xFFFFFFF0ll;
         const int64_t kalloc = rows ? kpad : kk;
         for (int b = 0; b < 2; ++b) {

@@ -848,7 +848,7 @@ extern "C" gc_status gc_render_batch_forward(gc_context *ctx, const gc_gaussians
     // row binning (every request within 255 tile columns): the lists in per-(request, tile row)
     // segments padded to whole radix tiles, one segmented pass on the column; room for the
     // padding beyond the capacity K (which counts the entries, padded per request)
-    const int64_t kpad = (kk + rows * T + 3) & ~int64_t(3);
+    const int64_t kpad = (kk + rows * gc::radix_tile_keys(true) + 3) & ~int64_t(3);
     const bool by_rows = rows_fit;
     if (by_rows && kpad > 0xFFFFFFF0ll)
         return fail(ctx, GC_ERR_CAPACITY, "batch needs more than 2^32 - 16 list words with its row padding");

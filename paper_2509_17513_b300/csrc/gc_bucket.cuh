@@ -379,7 +379,7 @@ cudaError_t bucket_place(const float4 *ranked, const uint32_t *total, const uint
     cudaError_t e = launch_exclusive_scan(b.counts, b.scanned, n_cells, nullptr, b.partials, st, words + 1);
     if (e != cudaSuccess) return e;
     k_bucket_segments<Map><<<1, 1024, 0, st>>>(b.scanned, total, demand, map, n_rows, n_cells,
-                                               (uint32_t)radix_tile_keys(), cap, alloc, shift, b.segs, b.pads,
+                                               (uint32_t)radix_tile_keys(true), cap, alloc, shift, b.segs, b.pads,
                                                words, peak);
     note_launches(1);
     k_bucket_pads<<<(unsigned)n_rows, 256, 0, st>>>(b.pads, words, keys);

@@ -190,12 +190,14 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
 // Buffers must hold n_max rounded up to 4 elements (tiles are copied in 16-byte units).
 // A bounded wait that runs out sets kErrTimeout in *err (device word).
 // Segmented mode (seg_block0 != NULL, device array of n_seg + 1 block indices in units
-// of radix_tile_keys()): every segment is sorted on its own and stays in place; the last
+// of radix_tile_keys(keys only)): every segment is sorted on its own and stays in place; the last
 // pass leaves its scanned per-block digit counts at the start of `scratch`, segment-major
 // and digit-major within a segment (digit d of the segment with first block b0 and nb
 // blocks starts at scratch[256 b0 + d nb]; gc_bucket.cuh reads tile ranges from them).
 size_t radix_scratch_words(int64_t n_max);
-int radix_tile_keys();
+// Keys per radix tile: of a sort of (key, value) pairs, or of a keys-only sort (which
+// segmented callers pad their segments to).
+int radix_tile_keys(bool keys_only = false);
 // scratch: radix_scratch_words(n_max) words, 8-byte aligned (the segmented mode keeps a
 // per-block table of count-array bases and strides there).
 cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
@@ -218,7 +220,7 @@ cudaError_t launch_emit(const float4 *ranked, const uint32_t *offsets, const uin
 // the row, more than `cap` entries recorded in *peak and nothing placed); one segmented stable
 // pass on the column byte (launch_bucket_sort: the sorted words are the tile lists, in
 // keys[*out_buf]); tile ranges from its digit counts (launch_bucket_ranges; ranges must be
-// zeroed).  Buffers hold `alloc` >= entries + rows x radix_tile_keys() words; `scratch` needs
+// zeroed).  Buffers hold `alloc` >= entries + rows x radix_tile_keys(true) words; `scratch` needs
 // bucket_scratch_words.
 bool bucket_binning_fits(const RenderParams &rp, int64_t n_sel);
 size_t bucket_scratch_words(int64_t n, int n_rows);

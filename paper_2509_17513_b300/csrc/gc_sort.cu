@@ -30,12 +30,20 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kScanChunk = kScanThreads * 16;  // 4096, 16 contiguous elements per thread
 
+#ifndef GC_KEYS_MINB
+#define GC_KEYS_MINB 5  // CTAs per SM of the keys-only scatter (registers bound accordingly)
+#endif
 #ifndef GC_SORT_ITEMS
 #define GC_SORT_ITEMS 8  // keys per thread in a radix tile
 #endif
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = GC_SORT_ITEMS;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048: sorts of (key, value) pairs
+// keys-only sorts (the column pass of the row-binned lists) take twice the keys per tile:
+// half the per-tile work (digit scan, offsets, barriers) per key and twice the length of the
+// runs written per digit, in the shared memory a pair tile uses
+constexpr int kKeysItems = 2 * GC_SORT_ITEMS;
+constexpr int kKeysTile = kSortThreads * kKeysItems;  // 4096
 constexpr int kWarps = kSortThreads / 32;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -284,6 +292,7 @@ __device__ __forceinline__ uint32_t digit_peers8(uint32_t d, uint32_t valid) {
 
 // Per-CTA digit histogram, digit-major: counts[d * nblocks + b].  Keys are read with
 // 16-byte loads when the tile is full; each warp counts into its own shared row.
+template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__restrict__ keys,
                                                              const uint32_t *n_dev, int64_t n_max,
                                                              int shift, uint32_t mask,
@@ -295,11 +304,12 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
     for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0;
     __syncthreads();
     const int64_t n = device_count(n_dev, n_max);
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    if (base + kSortTile <= n) {
+    constexpr int kTile = kSortThreads * ITEMS;
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    if (base + kTile <= n) {
         const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + base);
 #pragma unroll
-        for (int r = 0; r < kSortItems / 4; ++r) {
+        for (int r = 0; r < ITEMS / 4; ++r) {
             const uint4 q = k4[r * kSortThreads + threadIdx.x];
             atomicAdd(&wh[warp][(q.x >> shift) & mask], 1u);
             atomicAdd(&wh[warp][(q.y >> shift) & mask], 1u);
@@ -307,7 +317,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
             atomicAdd(&wh[warp][(q.w >> shift) & mask], 1u);
         }
     } else {
-        for (int r = 0; r < kSortItems; ++r) {
+        for (int r = 0; r < ITEMS; ++r) {
             const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
             if (i < n) atomicAdd(&wh[warp][(keys[i] >> shift) & mask], 1u);
         }
@@ -328,14 +338,15 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
 // buffer as 8-byte pairs and writes them out in contiguous runs.  keys_out may be NULL
 // (last pass of a sort whose keys are not kept).  Without kPairs the keys alone are moved
 // (vals_in and vals_out unused; half the shared staging).
-template <bool kPairs>
-__global__ void __launch_bounds__(kSortThreads, kPairs ? 5 : 6) k_radix_scatter(
+template <bool kPairs, int ITEMS>
+__global__ void __launch_bounds__(kSortThreads, kPairs ? 5 : GC_KEYS_MINB) k_radix_scatter(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *n_dev,
     int64_t n_max, int shift, uint32_t mask, const uint32_t *__restrict__ scanned, int nblocks,
     uint32_t *err, SegIndex sg) {
+    constexpr int kTile = kSortThreads * ITEMS;
     // per stage: keys, values (then key-value pairs); keys only without kPairs
-    __shared__ __align__(128) uint32_t skv[2][kPairs ? 2 : 1][kSortTile];
+    __shared__ __align__(128) uint32_t skv[2][kPairs ? 2 : 1][kTile];
     __shared__ uint32_t wcnt[kWarps][256];
     __shared__ uint32_t gbase[256];
     __shared__ uint32_t ws[33];
@@ -343,7 +354,7 @@ __global__ void __launch_bounds__(kSortThreads, kPairs ? 5 : 6) k_radix_scatter(
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n = device_count(n_dev, n_max);
-    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    const int ntiles = (int)((n + kTile - 1) / kTile);
     const int bits = __popc(mask);
     const uint32_t lt = lanemask_lt();
     if ((int)blockIdx.x >= ntiles) return;
@@ -355,8 +366,8 @@ __global__ void __launch_bounds__(kSortThreads, kPairs ? 5 : 6) k_radix_scatter(
     }
     __syncthreads();
     auto issue = [&](int t, int stage) {  // one thread
-        const int64_t base = (int64_t)t * kSortTile;
-        const int nv = (int)((n - base) < kSortTile ? (n - base) : kSortTile);
+        const int64_t base = (int64_t)t * kTile;
+        const int nv = (int)((n - base) < kTile ? (n - base) : kTile);
         const uint32_t bytes = (uint32_t)((nv * 4 + 15) & ~15);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&bar[stage], (kPairs ? 2 : 1) * bytes);
@@ -368,8 +379,8 @@ __global__ void __launch_bounds__(kSortThreads, kPairs ? 5 : 6) k_radix_scatter(
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const int stage = it & 1;
-        const int64_t base = (int64_t)t * kSortTile;
-        const int nvalid = (int)((n - base) < kSortTile ? (n - base) : kSortTile);
+        const int64_t base = (int64_t)t * kTile;
+        const int nvalid = (int)((n - base) < kTile ? (n - base) : kTile);
         const bool has_next = t + (int)gridDim.x < ntiles;
         if (threadIdx.x == 0 && has_next) issue(t + gridDim.x, stage ^ 1);
         const uint2 ci = count_index(t, nblocks, sg);  // in flight while the tile is ranked
@@ -385,12 +396,12 @@ __global__ void __launch_bounds__(kSortThreads, kPairs ? 5 : 6) k_radix_scatter(
             __syncthreads();
             return;
         }
-        uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
-        const int wseg = warp * (32 * kSortItems);
-        if (nvalid == kSortTile && bits == 8) {
+        uint32_t key[ITEMS], val[ITEMS], loc[ITEMS];
+        const int wseg = warp * (32 * ITEMS);
+        if (nvalid == kTile && bits == 8) {
             // full tile of 8-bit digits (every key valid, the bit count fixed): the common case
 #pragma unroll
-            for (int r = 0; r < kSortItems; ++r) {
+            for (int r = 0; r < ITEMS; ++r) {
                 const int li = wseg + r * 32 + lane;
                 key[r] = skv[stage][0][li];
                 if (kPairs) val[r] = skv[stage][kPairs ? 1 : 0][li];
@@ -404,7 +415,7 @@ __global__ void __launch_bounds__(kSortThreads, kPairs ? 5 : 6) k_radix_scatter(
             }
         } else {
 #pragma unroll
-            for (int r = 0; r < kSortItems; ++r) {
+            for (int r = 0; r < ITEMS; ++r) {
                 const int li = wseg + r * 32 + lane;
                 const bool valid = li < nvalid;
                 key[r] = valid ? skv[stage][0][li] : 0xffffffffu;
@@ -439,7 +450,7 @@ __global__ void __launch_bounds__(kSortThreads, kPairs ? 5 : 6) k_radix_scatter(
         }
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < kSortItems; ++r) {
+        for (int r = 0; r < ITEMS; ++r) {
             const int li = wseg + r * 32 + lane;
             if (li < nvalid) {
                 const uint32_t d = (key[r] >> shift) & mask;
@@ -700,21 +711,21 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, 
     return cudaGetLastError();
 }
 
-int radix_tile_keys() { return kSortTile; }
+int radix_tile_keys(bool keys_only) { return keys_only ? kKeysTile : kSortTile; }
 
 // Grid of the persistent scatter: every CTA that fits at once with the shared-memory carveout
 // at its maximum (pairs: 48 registers and 42 KB of shared memory, five CTAs per SM), queried
 // once per variant.
-template <bool kPairs>
+template <bool kPairs, int ITEMS>
 static int scatter_grid() {
     static int cached = 0;
     if (!cached) {
         int per_sm = 0, dev = 0, sms = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
-        cudaFuncSetAttribute(k_radix_scatter<kPairs>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_radix_scatter<kPairs, ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radix_scatter<kPairs>, kSortThreads, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radix_scatter<kPairs, ITEMS>, kSortThreads, 0) !=
                 cudaSuccess ||
             per_sm < 1)
             per_sm = 4;
@@ -749,7 +760,8 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
     }
     const bool pairs = vals != nullptr && vals[0] != nullptr;
     if (!pairs) keys_out = true;
-    const int nblocks = (int)((n_max + kSortTile - 1) / kSortTile);
+    const int tile = pairs ? kSortTile : kKeysTile;
+    const int nblocks = (int)((n_max + tile - 1) / tile);
     const int passes = (end_bit - begin_bit + 7) / 8;
     if (pairs && begin_bit == 0 && !seg_block0 && n_max <= kOnesweepMaxKeys && passes <= kMaxPasses) {
         // one-sweep: zero the counts, tickets and status words; one histogram kernel;
@@ -784,7 +796,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
         *out_buf = cur;
         return cudaGetLastError();
     }
-    const int grid = std::min(nblocks, pairs ? scatter_grid<true>() : scatter_grid<false>());
+    const int grid = std::min(nblocks, pairs ? scatter_grid<true, kSortItems>() : scatter_grid<false, kKeysItems>());
     uint32_t *counts = scratch;
     uint32_t *partials = scratch + (size_t)256 * nblocks;
     SegIndex sg{seg_block0, nullptr, n_seg};
@@ -804,20 +816,24 @@ cudaError_t radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max
     for (int pass = 0; pass < passes; ++pass) {
         const int bits = (end_bit - shift + (passes - pass) - 1) / (passes - pass);
         const uint32_t mask = (1u << bits) - 1u;
-        k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(keys[cur], n_dev, n_max, shift, mask, counts,
-                                                       nblocks, sg);
+        if (pairs)
+            k_radix_hist<kSortItems><<<nblocks, kSortThreads, 0, st>>>(keys[cur], n_dev, n_max, shift, mask, counts,
+                                                                       nblocks, sg);
+        else
+            k_radix_hist<kKeysItems><<<nblocks, kSortThreads, 0, st>>>(keys[cur], n_dev, n_max, shift, mask, counts,
+                                                                       nblocks, sg);
         note_launches(1);
         cudaError_t e = launch_exclusive_scan(counts, counts, (int64_t)256 * nblocks, nullptr,
                                               partials, st, err);
         if (e != cudaSuccess) return e;
         const bool last = pass == passes - 1;
         if (pairs)
-            k_radix_scatter<true><<<grid, kSortThreads, 0, st>>>(keys[cur], vals[cur],
+            k_radix_scatter<true, kSortItems><<<grid, kSortThreads, 0, st>>>(keys[cur], vals[cur],
                                                                  (last && !keys_out) ? nullptr : keys[cur ^ 1],
                                                                  vals[cur ^ 1], n_dev, n_max, shift, mask, counts,
                                                                  nblocks, err, sg);
         else
-            k_radix_scatter<false><<<grid, kSortThreads, 0, st>>>(keys[cur], nullptr, keys[cur ^ 1], nullptr, n_dev,
+            k_radix_scatter<false, kKeysItems><<<grid, kSortThreads, 0, st>>>(keys[cur], nullptr, keys[cur ^ 1], nullptr, n_dev,
                                                                   n_max, shift, mask, counts, nblocks, err, sg);
         note_launches(1);
         cur ^= 1;
