@@ -31,7 +31,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanChunk = kScanThreads * 16;  // 4096, 16 contiguous elements per thread
 
 #ifndef GC_KEYS_MINB
-#define GC_KEYS_MINB 5  // CTAs per SM of the keys-only scatter (registers bound accordingly)
+#define GC_KEYS_MINB 3  // CTAs per SM of the keys-only scatter (80 registers, 75 KB of shared memory)
 #endif
 #ifndef GC_SORT_ITEMS
 #define GC_SORT_ITEMS 8  // keys per thread in a radix tile
@@ -39,11 +39,16 @@ constexpr int kScanChunk = kScanThreads * 16;  // 4096, 16 contiguous elements p
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = GC_SORT_ITEMS;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 2048: sorts of (key, value) pairs
-// keys-only sorts (the column pass of the row-binned lists) take twice the keys per tile:
-// half the per-tile work (digit scan, offsets, barriers) per key and twice the length of the
-// runs written per digit, in the shared memory a pair tile uses
-constexpr int kKeysItems = 2 * GC_SORT_ITEMS;
-constexpr int kKeysTile = kSortThreads * kKeysItems;  // 4096
+// keys-only sorts (the column pass of the row-binned lists) take four times the keys per
+// tile: a quarter of the per-tile work (digit scan, offsets, barriers) per key and four times
+// the length of the runs written per digit.  Measured on B300 (column pass of 180 batched
+// 1080p renders): 2,048 keys 10.45 ms, 4,096 8.18, 6,144 8.00, 8,192 7.40, 12,288 7.47,
+// 16,384 9.05 (occupancy falls to one CTA per SM).
+#ifndef GC_KEYS_ITEMS
+#define GC_KEYS_ITEMS (4 * GC_SORT_ITEMS)
+#endif
+constexpr int kKeysItems = GC_KEYS_ITEMS;
+constexpr int kKeysTile = kSortThreads * kKeysItems;  // 8192
 constexpr int kWarps = kSortThreads / 32;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
