@@ -195,15 +195,14 @@ __device__ __forceinline__ void blend_fwd_tile(int tx, int ty, uint2 range,
 #pragma unroll 4
             for (int k = k0; k < k1; ++k) {
                 const uint32_t wm = sm.m[8 * k + warp];
-                if ((wm & act) == 0u) continue;
                 const float4 a = sm.a[k];
                 const float2 bb = sm.b[k];
                 const float dx = pcx - a.x, dy = pcy - a.y;
                 const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
-                if (p2 > 0.f) continue;
                 float G;
                 const float alpha = fminf(kAlphaMax, blend_raw_alpha(bb.y, p2, G));
-                if (alpha < kAlphaMin) continue;
+                // one test instead of three branches: footprint, exponent, alpha at least 1/255
+                if (!(((wm & act) != 0u) & (p2 <= 0.f) & (alpha >= kAlphaMin))) continue;
                 const float Tn = T * (1.f - alpha);
                 if (Tn < kTStop) {
                     act = 0u;
@@ -404,14 +403,12 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
                     const float2 bb = sm.b[s];
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
-                        if (!(i == 0 ? m0 : m1)) continue;
                         const float dx = pcx - a.x, dy = ((float)(py0 + 4 * i) + 0.5f) - a.y;
                         const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
-                        if (p2 > 0.f) continue;
                         float G;
                         const float a0 = blend_raw_alpha(bb.y, p2, G);
                         const float alpha = fminf(kAlphaMax, a0);
-                        if (alpha < kAlphaMin) continue;
+                        if (!((i == 0 ? m0 : m1) & (p2 <= 0.f) & (alpha >= kAlphaMin))) continue;
                         contrib = true;
                         bwd_blend(P[i], dx, dy, alpha, a0, G, sm.c[s], sm.d[s], v);
                     }
