@@ -180,6 +180,30 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
     }
 }
 
+constexpr int kPartStride = 73;  // words per entry of the reverse pass's partial staging
+
+// Shared memory of the reverse pass (dynamic: past 48 KB at eight levels).
+template <int NL>
+struct LvBwdSmem {
+    float4 a[256];
+    float2 b[256];
+    float4 c[256];
+    float2 d[256];
+    uint32_t m[256 * 8];
+    uint32_t e[256];
+    uint8_t lay[256];
+    // per entry of the group: 8 warps x 9 partials at a stride of 73 words, so that the
+    // cross-warp sum (thread i reads entry i / 9, partial i % 9) hits bank i mod 32
+    float wpart[64 * kPartStride];
+    // per entry of the group and warp: partial written; byte (warp & 3) of word
+    // wrote[warp >> 2][entry], so that the 32 lanes of a relevance step write 32
+    // consecutive words (distinct banks)
+    uint32_t wrote[2][64];
+    uint32_t last[NL][256];    // per level and pixel: list position after the last blend
+    uint32_t wsuf[8][16];      // per warp: max over its pixels and levels l >= m of last[l]
+    uint32_t last_max;
+};
+
 // Reverse: one CTA of 256 threads per tile, one pixel per thread; NL levels.
 //
 // Per pixel and level the reverse step of Eq. 2 needs the transmittance T_l before the entry
@@ -197,24 +221,8 @@ __global__ void __launch_bounds__(256, 4) k_blend_levels_bwd(
     const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, RenderParams rp,
     const float *__restrict__ lv_T, const uint32_t *__restrict__ lv_last, LevelGrads dimg,
     float *__restrict__ part) {
-    struct Smem {
-        float4 a[256];
-        float2 b[256];
-        float4 c[256];
-        float2 d[256];
-        uint32_t m[256 * 8];
-        uint32_t e[256];
-        uint8_t lay[256];
-        float wpart[64][8][9];
-        // per entry of the group and warp: partial written; byte (warp & 3) of word
-        // wrote[warp >> 2][entry], so that the 32 lanes of a relevance step write 32
-        // consecutive words (distinct banks)
-        uint32_t wrote[2][64];
-        uint32_t last[NL][256];    // per level and pixel: list position after the last blend
-        uint32_t wsuf[8][16];      // per warp: max over its pixels and levels l >= m of last[l]
-        uint32_t last_max;
-    };
-    __shared__ __align__(16) Smem sm;
+    extern __shared__ __align__(16) unsigned char lv_bwd_smem[];
+    LvBwdSmem<NL> &sm = *reinterpret_cast<LvBwdSmem<NL> *>(lv_bwd_smem);
     const int tile = blockIdx.x, ntx = rp.ntx, tx = tile % ntx, ty = tile / ntx;
     const uint2 range = ranges[tile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -413,8 +421,9 @@ __global__ void __launch_bounds__(256, 4) k_blend_levels_bwd(
                         for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
                         out8 = x;
                     }
-                    if ((lane & 3) == 0) sm.wpart[k - gbot][warp][lane >> 2] = out0;
-                    if (lane == 1) sm.wpart[k - gbot][warp][8] = out8;
+                    float *wp = &sm.wpart[(k - gbot) * kPartStride + warp * 9];
+                    if ((lane & 3) == 0) wp[lane >> 2] = out0;
+                    if (lane == 1) wp[8] = out8;
                 }
             }
             __syncthreads();
@@ -425,7 +434,7 @@ __global__ void __launch_bounds__(256, 4) k_blend_levels_bwd(
 #pragma unroll
                 for (int w2 = 0; w2 < 8; ++w2) {
                     const uint32_t byte = ((w2 < 4 ? wr.x : wr.y) >> (8 * (w2 & 3))) & 0xffu;
-                    if (byte) acc += sm.wpart[q][w2][c];
+                    if (byte) acc += sm.wpart[q * kPartStride + w2 * 9 + c];
                 }
                 part[(int64_t)sm.e[gbot + q - lo] * 9 + c] = acc;
             }
@@ -459,6 +468,26 @@ cudaError_t launch_blend_levels_fwd(const uint2 *ranges, const uint32_t *sorted_
     return cudaGetLastError();
 }
 
+namespace {
+
+// One reverse-pass launch; the shared memory is dynamic, with the opt-in where it passes 48 KB.
+template <int TW, int TH, int NL>
+cudaError_t lv_bwd_launch(unsigned tiles, cudaStream_t st, const uint2 *ranges, const uint32_t *sorted_vals,
+                          const float4 *ranked, const uint32_t *offsets, int W, int H, const RenderParams &rp,
+                          const float *lv_T, const uint32_t *lv_last, const LevelGrads &dimg, float *part) {
+    constexpr size_t bytes = sizeof(LvBwdSmem<NL>);
+    if constexpr (bytes > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_blend_levels_bwd<TW, TH, NL>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+    }
+    k_blend_levels_bwd<TW, TH, NL><<<tiles, 256, bytes, st>>>(ranges, sorted_vals, ranked, offsets, W, H, rp, lv_T,
+                                                               lv_last, dimg, part);
+    return cudaSuccess;
+}
+
+}  // namespace
+
 cudaError_t launch_blend_levels_bwd(const uint2 *ranges, const uint32_t *sorted_vals, const float4 *ranked,
                                     const uint32_t *offsets, const CamParams &cam, const RenderParams &rp, int L,
                                     const float *lv_T, const uint32_t *lv_last, const LevelGrads &dimg,
@@ -468,10 +497,11 @@ cudaError_t launch_blend_levels_bwd(const uint2 *ranges, const uint32_t *sorted_
 #define GC_LV_ARGS ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp, lv_T, lv_last, dimg, part
 #define GC_LV_CASE(NLV)                                                                                       \
     case NLV:                                                                                                 \
-        if (rp.tile_w == 16) k_blend_levels_bwd<16, 16, NLV><<<tiles, 256, 0, st>>>(GC_LV_ARGS);             \
-        else if (rp.tile_w == 8) k_blend_levels_bwd<8, 32, NLV><<<tiles, 256, 0, st>>>(GC_LV_ARGS);          \
-        else k_blend_levels_bwd<32, 8, NLV><<<tiles, 256, 0, st>>>(GC_LV_ARGS);                               \
+        e = rp.tile_w == 16  ? lv_bwd_launch<16, 16, NLV>(tiles, st, GC_LV_ARGS)                              \
+            : rp.tile_w == 8 ? lv_bwd_launch<8, 32, NLV>(tiles, st, GC_LV_ARGS)                               \
+                             : lv_bwd_launch<32, 8, NLV>(tiles, st, GC_LV_ARGS);                              \
         break;
+    cudaError_t e;
     switch (L) {
         GC_LV_CASE(1) GC_LV_CASE(2) GC_LV_CASE(3) GC_LV_CASE(4) GC_LV_CASE(5) GC_LV_CASE(6) GC_LV_CASE(7)
         GC_LV_CASE(8)
@@ -479,6 +509,7 @@ cudaError_t launch_blend_levels_bwd(const uint2 *ranges, const uint32_t *sorted_
     }
 #undef GC_LV_CASE
 #undef GC_LV_ARGS
+    if (e != cudaSuccess) return e;
     note_launches(1);
     return cudaGetLastError();
 }

@@ -85,6 +85,40 @@ def test_levels_backward_matches_single_sum_and_oracle(gc, small, tile):
         assert np.abs(a - b).max() <= 1e-3 * np.abs(b).max() + 1e-6, k
 
 
+@pytest.mark.parametrize("L", [7, 8])
+def test_seven_and_eight_levels(gc, L):
+    """The largest level counts (the reverse pass's shared memory passes 48 KB at eight): the
+    level images equal the single renders bit for bit, and the one-pass backward equals the
+    in-order sum of the single-level backwards."""
+    rng = np.random.default_rng(211)
+    scene = scenes.make_hier_scene(rng, 6000, 8, 1, 4)
+    cam = scenes.orbit_camera(0.9, 4.0, 160, 120)
+    r = gc.Renderer(0, tile=(8, 32))
+    gs = gc.GaussianSet.from_scene(scene)
+    saved = gc.Saved(r)
+    imgs = [x.clone() for x in r.levels_forward(gs, None, L, cam, saved)]
+    g = torch.Generator(device="cuda").manual_seed(5)
+    dls = [torch.randn(imgs[0].shape, generator=g, device="cuda") for _ in range(L)]
+    got = {k: v.clone() for k, v in r.levels_backward(saved, gs, None, dls).items()}
+    acc = None
+    for l in range(1, L + 1):
+        s1 = gc.Saved(r)
+        one = r.forward(gs, None, scenes.level_mask(l), cam, s1)
+        torch.cuda.synchronize()
+        assert torch.equal(imgs[l - 1], one), l
+        g1 = r.backward(s1, gs, None, dls[l - 1])
+        acc = {k: v.clone() for k, v in g1.items()} if acc is None else {k: acc[k] + g1[k] for k in acc}
+    torch.cuda.synchronize()
+    # FP32 summation order only (per entry over the levels here, per level over the entries
+    # there), on unmasked N(0, 1) upstream gradients for every level; the rotation's chain
+    # rule cancels large terms, so the bound is on the relative L2 norm and a few units of
+    # 1e-5 of the largest element.  A level missing or blended twice is off by O(1).
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        a, b = got[k].double(), acc[k].double()
+        assert float((a - b).norm()) <= 3e-5 * float(b.norm()), k
+        assert float((a - b).abs().max()) <= 5e-5 * float(b.abs().max()) + 1e-6, k
+
+
 def test_levels_argument_errors(gc, small):
     scene, motion = small
     cam = scenes.orbit_camera(0.4, 4.0, 64, 48)
