@@ -24,29 +24,16 @@ namespace {
 
 // Forward: one CTA of 256 threads per tile, one pixel per thread (the forward layout);
 // NL = number of levels (compile time, so that the per-level state fits in registers).
-//
-// An entry of layer m blends into the levels m .. NL-1 that are still blending.  m is the
-// same for the whole warp (one entry at a time), so the update enters a fall-through switch
-// at level m and runs the levels above it without a per-level test: a level that has
-// stopped has its transmittance parked at 0 (the true value moves to shared memory), so
-// its weight alpha * T is 0 and its colour and transmittance stay exactly as they were.
-// The list position after a level's last blend is kept per layer instead of per level:
-// an entry of layer m reached some level only if it reached every still-blending level
-// >= m, so level l's last position is the largest of layers 0..l's, read when l stops or
-// at the end.
 template <int TW, int TH, int NL>
 __global__ void __launch_bounds__(256) k_blend_levels_fwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, int W, int H, RenderParams rp, LevelPtrs out, float *__restrict__ lv_T,
     uint32_t *__restrict__ lv_last) {
-    static_assert(NL >= 1 && NL <= 8, "levels");
+    constexpr int L = NL;
     const int ntx = rp.ntx;
     const float bg0 = rp.bg[0], bg1 = rp.bg[1], bg2 = rp.bg[2];
     __shared__ __align__(16) FwdSmem sm;
     __shared__ uint8_t lay[256];
-    __shared__ uint32_t last_lay[NL][256];  // per layer and pixel: position after its last blend
-    __shared__ uint32_t last_stop[NL][256];  // per level and pixel: the same, when it stopped
-    __shared__ float T_stop[NL][256];        // per level and pixel: transmittance when it stopped
     const int tile = blockIdx.x, tx = tile % ntx, ty = tile / ntx;
     const uint2 range = ranges[tile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -56,7 +43,7 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
     const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
     const int n = (int)(range.y - range.x);
     const bool inside = px < W && py < H;
-    uint32_t lv = inside ? ((1u << NL) - 1u) : 0u;  // levels still blending
+    uint32_t lv = inside ? ((1u << L) - 1u) : 0u;  // levels still blending
     uint32_t act = lv ? (1u << lane) : 0u;
     float T[NL], C0[NL], C1[NL], C2[NL];
     // Transmittance of the highest level still blending.  Level l blends a subset of level
@@ -65,11 +52,12 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
     // of them reaches level k.  Ttop follows T[k] with the same operations, so one test
     // decides whether any level stops at an entry; the levels are only walked when one does.
     float Ttop = 1.f;
+    uint32_t last[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         T[l] = 1.f;
         C0[l] = C1[l] = C2[l] = 0.f;
-        last_lay[l][threadIdx.x] = 0u;
+        last[l] = 0u;
     }
     for (int b = 0; b < n; b += 256) {
         if (__syncthreads_count(act != 0u) == 0) break;
@@ -102,80 +90,57 @@ __global__ void __launch_bounds__(256) k_blend_levels_fwd(
                 const int k = k0 + __ffs(todo) - 1;
                 todo &= todo - 1u;
                 const uint32_t wm = sm.m[warp * 256 + k];
-                const int m = lay[k];  // the entry's layer (the same in the warp)
+                const uint32_t lm = lv & (0xffffffffu << lay[k]);  // active levels >= the entry's layer
                 const float4 a = sm.a[k];
                 const float2 bb = sm.b[k];
                 const float dx = pcx - a.x, dy = pcy - a.y;
                 const float p2 = blend_power2(a.z, a.w, bb.x, dx, dy);
                 float G;
                 const float alpha = fminf(kAlphaMax, blend_raw_alpha(bb.y, p2, G));
-                // one test instead of four branches: the pixel is in the entry's footprint, a level >= m
-                // still blends, and the entry's alpha reaches 1/255 there
-                const bool ok = ((wm & act) != 0u) & (((lv >> m) & 1u) != 0u) & (p2 <= 0.f) & (alpha >= kAlphaMin);
+                // one test instead of four branches: the pixel is in the entry's footprint, a level >= its
+                // layer still blends, and the entry's alpha reaches 1/255 there
+                const bool ok = ((wm & act) != 0u) & (lm != 0u) & (p2 <= 0.f) & (alpha >= kAlphaMin);
                 if (!ok) continue;
+                const float4 col = sm.c[k];
                 const float om = 1.f - alpha;
+                uint32_t bl = lm;  // the levels that blend the entry
                 if (Ttop * om < kTStop) {
-                    // the levels of m..k whose transmittance would fall below the threshold (a
-                    // top run) stop here without blending the entry; Ttop moves to the new k
-                    uint32_t run = 0u;
+                    // some levels stop here: those whose transmittance would fall below the
+                    // threshold (a top run of lm), then Ttop moves to the new highest level
 #pragma unroll
-                    for (int l = 0; l < NL; ++l) {
-                        run = max(run, last_lay[l][threadIdx.x]);
-                        if (l >= m && ((lv >> l) & 1u) && T[l] * om < kTStop) {
-                            T_stop[l][threadIdx.x] = T[l];
-                            last_stop[l][threadIdx.x] = run;
-                            T[l] = 0.f;
-                            lv &= ~(1u << l);
-                        }
-                    }
-                    Ttop = 0.f;
+                    for (int l = 0; l < NL; ++l)
+                        if (((lm >> l) & 1u) && T[l] * om < kTStop) bl &= ~(1u << l);
+                    lv &= ~(lm & ~bl);
 #pragma unroll
                     for (int l = 0; l < NL; ++l)
                         if ((lv >> l) & 1u) Ttop = T[l];
                     if (!lv) act = 0u;
-                    if (!((lv >> m) & 1u)) continue;  // every level >= m stopped
                 }
-                Ttop = Ttop * om;
-                last_lay[m][threadIdx.x] = (uint32_t)(b + k + 1);
-                const float4 col = sm.c[k];
-#define GC_LV_BLEND(l)                                    \
-    if constexpr ((l) < NL) {                             \
-        const float w = alpha * T[l];                     \
-        C0[l] = fmaf(col.x, w, C0[l]);                    \
-        C1[l] = fmaf(col.y, w, C1[l]);                    \
-        C2[l] = fmaf(col.z, w, C2[l]);                    \
-        T[l] = T[l] * om;                                 \
-    }
-                switch (m) {
-                    case 0: GC_LV_BLEND(0) [[fallthrough]];
-                    case 1: GC_LV_BLEND(1) [[fallthrough]];
-                    case 2: GC_LV_BLEND(2) [[fallthrough]];
-                    case 3: GC_LV_BLEND(3) [[fallthrough]];
-                    case 4: GC_LV_BLEND(4) [[fallthrough]];
-                    case 5: GC_LV_BLEND(5) [[fallthrough]];
-                    case 6: GC_LV_BLEND(6) [[fallthrough]];
-                    case 7: GC_LV_BLEND(7) [[fallthrough]];
-                    default: break;
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    if (!((bl >> l) & 1u)) continue;
+                    const float w = alpha * T[l];
+                    C0[l] = fmaf(col.x, w, C0[l]);
+                    C1[l] = fmaf(col.y, w, C1[l]);
+                    C2[l] = fmaf(col.z, w, C2[l]);
+                    T[l] = T[l] * om;
+                    last[l] = (uint32_t)(b + k + 1);
                 }
-#undef GC_LV_BLEND
+                if (bl) Ttop = Ttop * om;
             }
         }
     }
     if (inside) {
         const size_t hw = (size_t)W * H;
         const size_t p = (size_t)py * W + px;
-        uint32_t run = 0u;
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
-            run = max(run, last_lay[l][threadIdx.x]);
-            const bool blending = (lv >> l) & 1u;
-            const float Tl = blending ? T[l] : T_stop[l][threadIdx.x];
             float *img = out.img[l];
-            img[p] = fmaf(Tl, bg0, C0[l]);
-            img[hw + p] = fmaf(Tl, bg1, C1[l]);
-            img[2 * hw + p] = fmaf(Tl, bg2, C2[l]);
-            lv_T[l * hw + p] = Tl;
-            lv_last[l * hw + p] = blending ? run : last_stop[l][threadIdx.x];
+            img[p] = fmaf(T[l], bg0, C0[l]);
+            img[hw + p] = fmaf(T[l], bg1, C1[l]);
+            img[2 * hw + p] = fmaf(T[l], bg2, C2[l]);
+            lv_T[l * hw + p] = T[l];
+            lv_last[l * hw + p] = last[l];
         }
     }
 }
