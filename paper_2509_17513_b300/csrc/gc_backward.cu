@@ -57,36 +57,53 @@ __global__ void __launch_bounds__(256) k_reduce_entries(float *__restrict__ part
 }
 
 // Thread per selected Gaussian in index order (coalesced attribute reads and
-// gradient writes); g2d and touched are by compact position.
+// gradient writes); g2d and touched are by compact position.  The SH gradient (up to 48
+// floats per Gaussian) is staged in shared memory, one row per thread at a pitch of 49 words
+// (the rows' k-th words of a warp fall on distinct banks), and each warp then writes its 32
+// rows with consecutive lanes on consecutive words: a thread storing its own row would put
+// one word in each of 32 sectors per store instruction.
+constexpr int kShPitch = 49;
+
 template <int PREC>
 __global__ void __launch_bounds__(128) k_preprocess_bwd(GaussSrc G, Selection sel, int64_t n_sel,
                                                         CamParams cam, RenderParams rp,
                                                         const float *__restrict__ g2d,
                                                         const uint32_t *__restrict__ touched,
                                                         gc_grads out, float *__restrict__ mcontrib) {
+    __shared__ float s_dsh[128 * kShPitch];
+    __shared__ int64_t s_row[128];
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_sel) return;
-    const int64_t i = sel_global(sel, j);
+    const bool valid = j < n_sel;
+    const int64_t i = valid ? sel_global(sel, j) : 0;
     const int K3 = 3 * G.K;
-    GradAcc acc;
-    for (int k = 0; k < 3; ++k) { acc.dmu[k] = 0.f; acc.dls[k] = 0.f; }
-    for (int k = 0; k < 4; ++k) acc.dq[k] = 0.f;
-    acc.dlogit = 0.f;
-    float m7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    // the SH gradient goes straight to its output (one chain rule per Gaussian here)
-    float sh_scratch[48];
-    float *dsh = out.d_sh ? out.d_sh + i * K3 : sh_scratch;
-    if (touched[j] != 0) {
-        const int g = G.per_gaussian ? (int)i : ((G.group_q && G.group_id) ? G.group_id[i] : 0);
-        chain_rule<PREC>(G, i, G.group_q, G.group_t, g, cam, rp, g2d + 9 * j, acc, m7, G.res, dsh);
-    } else if (out.d_sh) {
-        for (int k = 0; k < K3; ++k) dsh[k] = 0.f;
+    float *dsh = &s_dsh[threadIdx.x * kShPitch];
+    if (valid) {
+        GradAcc acc;
+        for (int k = 0; k < 3; ++k) { acc.dmu[k] = 0.f; acc.dls[k] = 0.f; }
+        for (int k = 0; k < 4; ++k) acc.dq[k] = 0.f;
+        acc.dlogit = 0.f;
+        float m7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (touched[j] != 0) {
+            const int g = G.per_gaussian ? (int)i : ((G.group_q && G.group_id) ? G.group_id[i] : 0);
+            chain_rule<PREC>(G, i, G.group_q, G.group_t, g, cam, rp, g2d + 9 * j, acc, m7, G.res, dsh);
+        } else {
+            for (int k = 0; k < K3; ++k) dsh[k] = 0.f;
+        }
+        if (out.d_means) for (int k = 0; k < 3; ++k) out.d_means[3 * i + k] = acc.dmu[k];
+        if (out.d_log_scales) for (int k = 0; k < 3; ++k) out.d_log_scales[3 * i + k] = acc.dls[k];
+        if (out.d_quats) for (int k = 0; k < 4; ++k) out.d_quats[4 * i + k] = acc.dq[k];
+        if (out.d_opacity_logits) out.d_opacity_logits[i] = acc.dlogit;
+        if (mcontrib) for (int k = 0; k < 7; ++k) mcontrib[7 * j + k] = m7[k];
     }
-    if (out.d_means) for (int k = 0; k < 3; ++k) out.d_means[3 * i + k] = acc.dmu[k];
-    if (out.d_log_scales) for (int k = 0; k < 3; ++k) out.d_log_scales[3 * i + k] = acc.dls[k];
-    if (out.d_quats) for (int k = 0; k < 4; ++k) out.d_quats[4 * i + k] = acc.dq[k];
-    if (out.d_opacity_logits) out.d_opacity_logits[i] = acc.dlogit;
-    if (mcontrib) for (int k = 0; k < 7; ++k) mcontrib[7 * j + k] = m7[k];
+    if (!out.d_sh) return;  // uniform over the grid
+    s_row[threadIdx.x] = valid ? i : -1;
+    __syncwarp();
+    const int w0 = threadIdx.x & ~31;
+    for (int e = threadIdx.x & 31; e < 32 * K3; e += 32) {
+        const int r = e / K3, c = e - r * K3;
+        const int64_t row = s_row[w0 + r];
+        if (row >= 0) out.d_sh[row * K3 + c] = s_dsh[(w0 + r) * kShPitch + c];
+    }
 }
 
 // Per-Gaussian motion: scatter each selected Gaussian's motion terms to its own rows.
