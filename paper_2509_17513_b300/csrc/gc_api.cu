@@ -83,7 +83,7 @@ static void saved_release(gc_context *ctx, gc_saved *s) {
                       &s->touched, &s->touched_r, &s->offsets, &s->tkeys[0], &s->tkeys[1],
                       &s->tvals[0], &s->tvals[1], &s->ranges, &s->final_T, &s->n_contrib,
                       &s->n_blended, &s->n_walked, &s->words, &s->lv_T, &s->lv_last, &s->row_shift,
-                      &s->scratch, &s->bwd_part, &s->bwd_g2d, &s->bwd_motion, &s->bwd_group};
+                      &s->scratch, &s->bwd_part, &s->bwd_flag, &s->bwd_g2d, &s->bwd_motion, &s->bwd_group};
     for (DevBuf *b : bufs) release(*b);
     s->valid = false;
 }
@@ -547,11 +547,15 @@ static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, co
     }
     const int64_t K = S.K > 0 ? S.K : 1;
     {
-        void *before = S.bwd_part.p;
+        void *before = S.bwd_part.p, *before_flag = S.bwd_flag.p;
         GC_CUDA(ctx, grow(S.bwd_part, (size_t)K * 9 * 4));
-        if (S.bwd_part.p != before) S.bwd_part_clean = false;
+        GC_CUDA(ctx, grow(S.bwd_flag, (size_t)K));
+        if (S.bwd_part.p != before || S.bwd_flag.p != before_flag) S.bwd_part_clean = false;
     }
-    if (!S.bwd_part_clean) GC_CUDA(ctx, cudaMemsetAsync(S.bwd_part.p, 0, S.bwd_part.cap, s));
+    if (!S.bwd_part_clean) {
+        GC_CUDA(ctx, cudaMemsetAsync(S.bwd_part.p, 0, S.bwd_part.cap, s));
+        GC_CUDA(ctx, cudaMemsetAsync(S.bwd_flag.p, 0, S.bwd_flag.cap, s));
+    }
     GC_CUDA(ctx, grow(S.bwd_g2d, (size_t)S.n_sel * 9 * 4));
     GC_CUDA(ctx, grow(S.bwd_motion, (size_t)S.n_sel * 7 * 4));
     if (G && !S.per_gaussian) GC_CUDA(ctx, grow(S.bwd_group, gc::group_partial_floats(S.n_sel, G) * 4));
@@ -564,17 +568,19 @@ static gc_status render_backward_impl(gc_context *ctx, const gc_saved *saved, co
         for (int l = 0; l < S.levels; ++l) lg.g[l] = dL_levels[l];
         GC_CUDA(ctx, gc::launch_blend_levels_bwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(),
                                                  S.offsets.as<uint32_t>(), S.cam, S.rp, S.levels, S.lv_T.as<float>(),
-                                                 S.lv_last.as<uint32_t>(), lg, S.bwd_part.as<float>(), s));
+                                                 S.lv_last.as<uint32_t>(), lg, S.bwd_part.as<float>(),
+                                                 S.bwd_flag.as<uint8_t>(), s));
     } else {
         GC_CUDA(ctx, gc::launch_blend_bwd(S.ranges.as<uint2>(), sorted_vals, S.ranked.as<float4>(),
                                           S.offsets.as<uint32_t>(), S.cam, S.rp, S.final_T.as<float>(),
-                                          S.n_contrib.as<uint32_t>(), dL_dimage, S.bwd_part.as<float>(), s));
+                                          S.n_contrib.as<uint32_t>(), dL_dimage, S.bwd_part.as<float>(),
+                                          S.bwd_flag.as<uint8_t>(), s));
     }
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_REDUCE));
     GC_CUDA(ctx, gc::launch_reduce_entries(S.bwd_part.as<float>(), S.offsets.as<uint32_t>(),
                                            S.touched_r.as<uint32_t>(), S.dvals[S.depth_buf].as<uint32_t>(),
                                            S.n_sel, (uint32_t)std::min<int64_t>(K, 0xFFFFFFFFll),
-                                           S.bwd_g2d.as<float>(), s));
+                                           S.bwd_flag.as<uint8_t>(), S.bwd_g2d.as<float>(), s));
     S.bwd_part_clean = true;
     GC_CUDA(ctx, prof_mark(ctx, s, GC_STAGE_PREPROCESS_BWD));
     if (order_wait) GC_CUDA(ctx, cudaStreamWaitEvent(s, order_wait, 0));

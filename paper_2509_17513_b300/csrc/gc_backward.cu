@@ -34,10 +34,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_blend_bwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, RenderParams rp,
     const float *__restrict__ final_T, const uint32_t *__restrict__ n_contrib,
-    const float *__restrict__ dimg, float *__restrict__ part) {
+    const float *__restrict__ dimg, float *__restrict__ part, uint8_t *__restrict__ flag) {
     __shared__ __align__(16) BwdSmem sm;
     const int tile = blockIdx.x, ntx = rp.ntx;
-    const TileBwd o{final_T, n_contrib, dimg, rp, W, H, 0u, 0u};
+    const TileBwd o{final_T, n_contrib, dimg, rp, W, H, 0u, 0u, flag};
     blend_bwd_tile<TW, TH>(tile % ntx, tile / ntx, ranges[tile], sorted_vals, ranked, offsets, o, part, sm);
 }
 
@@ -48,11 +48,12 @@ __global__ void __launch_bounds__(256) k_reduce_entries(float *__restrict__ part
                                                         const uint32_t *__restrict__ offsets,
                                                         const uint32_t *__restrict__ touched_r,
                                                         const uint32_t *__restrict__ perm, int64_t n,
-                                                        uint32_t cap, float *__restrict__ g2d) {
+                                                        uint32_t cap, uint8_t *__restrict__ flag,
+                                                        float *__restrict__ g2d) {
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= n) return;
     float out0, out8;
-    reduce_entries_warp(part, offsets[r], touched_r[r], cap, out0, out8);
+    reduce_entries_warp(part, offsets[r], touched_r[r], cap, flag, out0, out8);
     store_reduced(g2d + 9 * (int64_t)perm[r], out0, out8);
 }
 
@@ -183,12 +184,12 @@ __global__ void __launch_bounds__(256) k_group_final(const float *__restrict__ p
 cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
                              const float4 *ranked, const uint32_t *offsets, const CamParams &cam,
                              const RenderParams &rp, const float *final_T,
-                             const uint32_t *n_contrib, const float *dL_dimg, float *part,
+                             const uint32_t *n_contrib, const float *dL_dimg, float *part, uint8_t *flag,
                              cudaStream_t st) {
     const unsigned tiles = (unsigned)(rp.ntx * rp.nty);
     if (tiles == 0) return cudaSuccess;
 #define GC_BWD_ARGS                                                                           \
-    ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp, final_T, n_contrib, dL_dimg, part
+    ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp, final_T, n_contrib, dL_dimg, part, flag
     if (rp.tile_w == 16 && rp.tile_h == 16)
         k_blend_bwd<16, 16><<<tiles, kBwdThreads, 0, st>>>(GC_BWD_ARGS);
     else if (rp.tile_w == 8 && rp.tile_h == 32)
@@ -203,11 +204,12 @@ cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
 }
 
 cudaError_t launch_reduce_entries(float *part, const uint32_t *offsets, const uint32_t *touched_r,
-                                  const uint32_t *perm, int64_t n, uint32_t cap, float *g2d, cudaStream_t st) {
+                                  const uint32_t *perm, int64_t n, uint32_t cap, uint8_t *flag, float *g2d,
+                                  cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int64_t threads = n * 32;
     k_reduce_entries<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(part, offsets, touched_r, perm, n, cap,
-                                                                         g2d);
+                                                                         flag, g2d);
     note_launches(1);
     return cudaGetLastError();
 }

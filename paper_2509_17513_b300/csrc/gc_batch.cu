@@ -321,7 +321,8 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_batch_blend_bwd(const BatchR
                                                          const float *__restrict__ final_T,
                                                          const uint32_t *__restrict__ n_contrib,
                                                          const float *const *__restrict__ dimgs,
-                                                         float *__restrict__ part, unsigned long long *counter) {
+                                                         float *__restrict__ part, uint8_t *__restrict__ flag,
+                                                         unsigned long long *counter) {
     __shared__ __align__(16) BwdSmem sm;
     __shared__ TileBwd s_in;
     __shared__ int4 s_tile;    // tx, ty, range start, range end (tx < 0: no tile left)
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_batch_blend_bwd(const BatchR
                 const uint2 rg = ranges[t];
                 s_tile = make_int4(local % R.rp.ntx, local / R.rp.ntx, (int)rg.x, (int)rg.y);
                 s_in = TileBwd{final_T + R.pixel_base, n_contrib + R.pixel_base, dimgs[q], R.rp, R.cam.width,
-                               R.cam.height, eshift[q], R.rp.list_packed ? (uint32_t)R.item_base : 0u};
+                               R.cam.height, eshift[q], R.rp.list_packed ? (uint32_t)R.item_base : 0u, flag};
             } else {
                 s_tile = make_int4(-1, 0, 0, 0);
             }
@@ -356,13 +357,13 @@ __global__ void __launch_bounds__(256) k_batch_reduce(float *__restrict__ part,
                                                       const uint32_t *__restrict__ perm,
                                                       const int64_t *__restrict__ item_base, int n_req,
                                                       const uint32_t *__restrict__ eshift, int64_t n, uint32_t cap,
-                                                      float *__restrict__ g2d) {
+                                                      uint8_t *__restrict__ flag, float *__restrict__ g2d) {
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= n) return;
     const uint32_t cnt = touched_r[r];
     const uint32_t base = cnt ? offsets[r] + eshift[find_req(item_base, n_req, r)] : 0u;
     float out0, out8;
-    reduce_entries_warp(part, base, cnt, cap, out0, out8);
+    reduce_entries_warp(part, base, cnt, cap, flag, out0, out8);
     store_reduced(g2d + 9 * (int64_t)perm[r], out0, out8);
 }
 
@@ -509,15 +510,15 @@ struct BatchState {
     }
     DevBuf rec, ranked, dkeys[2], dvals[2], touched, touched_r, offsets, tkeys[2], tvals[2], ranges,
         final_T, n_contrib, words, counter, scratch, act;
-    DevBuf part, g2d, mcontrib, gpartial;
-    bool part_clean = false;  // part holds only zeros (see the reduce)
+    DevBuf part, flag, g2d, mcontrib, gpartial;
+    bool part_clean = false;  // part and flag (one byte per entry) hold only zeros (see the reduce)
 
     ~BatchState() {
         DevBuf *bufs[] = {&reqs_dev, &item_base, &tile_base, &seg_items, &ebase, &eshift, &ecount,
                           &seg_entries, &dimg_dev, &row_base, &row_shift, &rec, &ranked, &dkeys[0], &dkeys[1], &dvals[0],
                           &dvals[1], &touched, &touched_r, &offsets, &tkeys[0], &tkeys[1], &tvals[0],
                           &tvals[1], &ranges, &final_T, &n_contrib, &words, &counter, &scratch, &act,
-                          &part, &g2d, &mcontrib, &gpartial};
+                          &part, &flag, &g2d, &mcontrib, &gpartial};
         for (DevBuf *b : bufs) release(*b);
         if (staging) cudaFreeHost(staging);
         if (staging_base) cudaFreeHost(staging_base);
@@ -977,9 +978,10 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
     Sizer need{ctx, fixed};
     need(B.dimg_dev, sizeof(float *) * n_req);
     {
-        void *before = B.part.p;
+        void *before = B.part.p, *before_flag = B.flag.p;
         need(B.part, (size_t)K * 9 * 4 + 64);
-        if (B.part.p != before) B.part_clean = false;
+        need(B.flag, (size_t)K + 64);
+        if (B.part.p != before || B.flag.p != before_flag) B.part_clean = false;
     }
     need(B.g2d, (size_t)ni * 9 * 4);
     need(B.mcontrib, (size_t)ni * 7 * 4);
@@ -1002,6 +1004,7 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
     if (!B.part_clean) {
         if (capturing) return fail(ctx, GC_ERR_STATE, "the partials buffer is not clean; run the backward eagerly first");
         GC_CUDA(ctx, cudaMemsetAsync(B.part.p, 0, B.part.cap, s));
+        GC_CUDA(ctx, cudaMemsetAsync(B.flag.p, 0, B.flag.cap, s));
     }
     GC_CUDA(ctx, mark(GC_STAGE_BLEND_BWD));
     B.part_clean = false;
@@ -1013,7 +1016,8 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
         auto grid = [&](int64_t g) { return (unsigned)std::min<int64_t>(std::max<int64_t>(B.n_tiles, 1), g); };
 #define GC_BB_ARGS rq_dev, tb_dev, n_req, B.n_tiles, B.ranges.as<uint2>(), sv, B.ranked.as<float4>(),            \
                    B.offsets.as<uint32_t>(), B.eshift.as<uint32_t>(), B.final_T.as<float>(),                     \
-                   B.n_contrib.as<uint32_t>(), B.dimg_dev.as<const float *>(), B.part.as<float>(), ctr
+                   B.n_contrib.as<uint32_t>(), B.dimg_dev.as<const float *>(), B.part.as<float>(),          \
+                   B.flag.as<uint8_t>(), ctr
         if (B.opt.tile_w == 16)
             gc::k_batch_blend_bwd<16, 16><<<grid(gc::persistent_grid<gc::k_batch_blend_bwd<16, 16>, gc::kBwdThreads>()), gc::kBwdThreads, 0, s>>>(GC_BB_ARGS);
         else if (B.opt.tile_w == 8)
@@ -1029,7 +1033,7 @@ extern "C" gc_status gc_render_batch_backward(gc_context *ctx, const gc_saved *s
         gc::k_batch_reduce<<<(unsigned)((items * 32 + 255) / 256), 256, 0, s>>>(
             B.part.as<float>(), B.offsets.as<uint32_t>(), B.touched_r.as<uint32_t>(),
             B.dvals[B.depth_buf].as<uint32_t>(), ib_dev, n_req, B.eshift.as<uint32_t>(), items,
-            (uint32_t)std::min<int64_t>(B.K_cap, 0xFFFFFFFFll), B.g2d.as<float>());
+            (uint32_t)std::min<int64_t>(B.K_cap, 0xFFFFFFFFll), B.flag.as<uint8_t>(), B.g2d.as<float>());
         gc::note_launches(1);
         GC_CUDA(ctx, cudaGetLastError());
     }

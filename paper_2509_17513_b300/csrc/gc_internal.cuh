@@ -250,14 +250,14 @@ cudaError_t launch_blend_fwd(const uint2 *ranges, const uint32_t *sorted_vals,
 
 // Multi-level blends (levels 1..L of one view from one list): per-level images, final
 // transmittances lv_T[l * H * W + p] and list positions lv_last; the reverse pass writes
-// the partials of every entry summed over the levels (layout of launch_blend_bwd).
+// the partials of every entry summed over the levels (layout and flags of launch_blend_bwd).
 cudaError_t launch_blend_levels_fwd(const uint2 *ranges, const uint32_t *sorted_vals, const float4 *ranked,
                                     const CamParams &cam, const RenderParams &rp, int L, const LevelPtrs &out,
                                     float *lv_T, uint32_t *lv_last, cudaStream_t st);
 cudaError_t launch_blend_levels_bwd(const uint2 *ranges, const uint32_t *sorted_vals, const float4 *ranked,
                                     const uint32_t *offsets, const CamParams &cam, const RenderParams &rp, int L,
                                     const float *lv_T, const uint32_t *lv_last, const LevelGrads &dimg,
-                                    float *part, cudaStream_t st);
+                                    float *part, uint8_t *flag, cudaStream_t st);
 
 // sorted list entry (rank) -> global Gaussian index, int64
 cudaError_t launch_entries_to_global(const uint32_t *sorted_vals, const uint32_t *perm,
@@ -270,19 +270,23 @@ cudaError_t launch_entries_to_global(const uint32_t *sorted_vals, const uint32_t
 // entry at the entry's emit position e = offsets[r] + (index of the tile among the
 // Gaussian's row intervals): part[9 * e + c], c = du, dv, da, db, dc, dopacity,
 // dr, dg, db.  Entries behind every pixel's last blended one are not written: the
-// buffer must hold zeros there (the reduce leaves it all zero).
+// buffer must hold zeros there (the reduce leaves it all zero).  flag (one byte per entry,
+// all zero on entry, or NULL): only nonzero partials are stored, and their entries' flags
+// set to 1.
 cudaError_t launch_blend_bwd(const uint2 *ranges, const uint32_t *sorted_vals,
                              const float4 *ranked, const uint32_t *offsets, const CamParams &cam,
                              const RenderParams &rp, const float *final_T,
-                             const uint32_t *n_contrib, const float *dL_dimg, float *part,
+                             const uint32_t *n_contrib, const float *dL_dimg, float *part, uint8_t *flag,
                              cudaStream_t st);
 
 // Per-rank sum of the partials over the Gaussian's entries -> g2d[9 * j + c] at the
 // Gaussian's compact position j = perm[r]; zeroes the partials it read (all of them
 // nonzero are reset, so the buffer is all zero afterwards).  cap: buffer capacity in
-// entries (Gaussians whose entries pass it contribute zero).
+// entries (Gaussians whose entries pass it contribute zero).  flag (the reverse pass's, or
+// NULL): only flagged entries are read, and their flags cleared.
 cudaError_t launch_reduce_entries(float *part, const uint32_t *offsets, const uint32_t *touched_r,
-                                  const uint32_t *perm, int64_t n, uint32_t cap, float *g2d, cudaStream_t st);
+                                  const uint32_t *perm, int64_t n, uint32_t cap, uint8_t *flag, float *g2d,
+                                  cudaStream_t st);
 
 // Chain rule from the 2D gradients (by compact position) to the attributes (by
 // global index) and to per-Gaussian motion terms (7 floats per compact position:

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256, 4) k_blend_levels_bwd(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_vals,
     const float4 *__restrict__ ranked, const uint32_t *__restrict__ offsets, int W, int H, RenderParams rp,
     const float *__restrict__ lv_T, const uint32_t *__restrict__ lv_last, LevelGrads dimg,
-    float *__restrict__ part) {
+    float *__restrict__ part, uint8_t *__restrict__ flag) {
     extern __shared__ __align__(16) unsigned char lv_bwd_smem[];
     LvBwdSmem<NL> &sm = *reinterpret_cast<LvBwdSmem<NL> *>(lv_bwd_smem);
     const int tile = blockIdx.x, ntx = rp.ntx, tx = tile % ntx, ty = tile / ntx;
@@ -401,7 +401,13 @@ __global__ void __launch_bounds__(256, 4) k_blend_levels_bwd(
                     const uint32_t byte = ((w2 < 4 ? wr.x : wr.y) >> (8 * (w2 & 3))) & 0xffu;
                     if (byte) acc += sm.wpart[q * kPartStride + w2 * 9 + c];
                 }
-                part[(int64_t)sm.e[gbot + q - lo] * 9 + c] = acc;
+                const uint32_t e = sm.e[gbot + q - lo];
+                if (!flag) {
+                    part[(int64_t)e * 9 + c] = acc;
+                } else if (acc != 0.f) {  // the buffer holds zeros: a zero partial needs no store
+                    part[(int64_t)e * 9 + c] = acc;
+                    flag[e] = 1;
+                }
             }
             __syncthreads();
         }
@@ -439,7 +445,8 @@ namespace {
 template <int TW, int TH, int NL>
 cudaError_t lv_bwd_launch(unsigned tiles, cudaStream_t st, const uint2 *ranges, const uint32_t *sorted_vals,
                           const float4 *ranked, const uint32_t *offsets, int W, int H, const RenderParams &rp,
-                          const float *lv_T, const uint32_t *lv_last, const LevelGrads &dimg, float *part) {
+                          const float *lv_T, const uint32_t *lv_last, const LevelGrads &dimg, float *part,
+                          uint8_t *flag) {
     constexpr size_t bytes = sizeof(LvBwdSmem<NL>);
     if constexpr (bytes > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(k_blend_levels_bwd<TW, TH, NL>,
@@ -447,7 +454,7 @@ cudaError_t lv_bwd_launch(unsigned tiles, cudaStream_t st, const uint2 *ranges, 
         if (e != cudaSuccess) return e;
     }
     k_blend_levels_bwd<TW, TH, NL><<<tiles, 256, bytes, st>>>(ranges, sorted_vals, ranked, offsets, W, H, rp, lv_T,
-                                                               lv_last, dimg, part);
+                                                               lv_last, dimg, part, flag);
     return cudaSuccess;
 }
 
@@ -456,10 +463,10 @@ cudaError_t lv_bwd_launch(unsigned tiles, cudaStream_t st, const uint2 *ranges, 
 cudaError_t launch_blend_levels_bwd(const uint2 *ranges, const uint32_t *sorted_vals, const float4 *ranked,
                                     const uint32_t *offsets, const CamParams &cam, const RenderParams &rp, int L,
                                     const float *lv_T, const uint32_t *lv_last, const LevelGrads &dimg,
-                                    float *part, cudaStream_t st) {
+                                    float *part, uint8_t *flag, cudaStream_t st) {
     const unsigned tiles = (unsigned)(rp.ntx * rp.nty);
     if (tiles == 0) return cudaSuccess;
-#define GC_LV_ARGS ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp, lv_T, lv_last, dimg, part
+#define GC_LV_ARGS ranges, sorted_vals, ranked, offsets, cam.width, cam.height, rp, lv_T, lv_last, dimg, part, flag
 #define GC_LV_CASE(NLV)                                                                                       \
     case NLV:                                                                                                 \
         e = rp.tile_w == 16  ? lv_bwd_launch<16, 16, NLV>(tiles, st, GC_LV_ARGS)                              \

@@ -593,13 +593,20 @@ __device__ __forceinline__ uint32_t entry_index(const RowGeom &g, const float4 &
 // sum is a transposing butterfly: afterwards lane 4 c holds value c (c < 8) and every
 // lane holds value 8.
 __device__ __forceinline__ void reduce_entries_warp(float *__restrict__ part, uint32_t base, uint32_t cnt,
-                                                    uint32_t cap, float &out0, float &out8) {
+                                                    uint32_t cap, uint8_t *__restrict__ flag, float &out0,
+                                                    float &out8) {
     const int lane = threadIdx.x & 31;
     float v[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) v[c] = 0.f;
     if ((uint64_t)base + cnt <= cap) {
         for (uint32_t k = lane; k < cnt; k += 32) {
+            // with flags, an entry whose partials were not stored holds zeros: adding them
+            // changes no sum (no partial sum is -0), so it is skipped unread
+            if (flag) {
+                if (!flag[base + k]) continue;
+                flag[base + k] = 0;
+            }
             float *p = part + (int64_t)(base + k) * 9;
             float x[9];
             bool nz = false;

@@ -88,8 +88,9 @@ struct gc_saved {
     // state, so that distinct states may run on different streams at once.  The backward's
     // buffers are scratch, not results (mutable: a backward reads a const state).
     DevBuf scratch;
-    mutable DevBuf bwd_part, bwd_g2d, bwd_motion, bwd_group;
-    mutable bool bwd_part_clean = false;  // bwd_part holds only zeros (see the reduce)
+    mutable DevBuf bwd_part, bwd_flag, bwd_g2d, bwd_motion, bwd_group;
+    // bwd_part holds only zeros and bwd_flag (one byte per entry) too (see the reduce)
+    mutable bool bwd_part_clean = false;
     // The sorted tile lists: the keys buffer of the last pass for row-binned lists (one word
     // per entry, column << 24 | rank), else the values of the key sort.
     uint32_t *lists() const {

@@ -265,6 +265,9 @@ struct TileBwd {
     int W, H;
     uint32_t entry_shift;
     uint32_t rank_base;  // added to a list word's rank: the record index of rank 0
+    // per entry: 1 where a nonzero partial was written (only those are stored); NULL: every
+    // entry of the walked range is stored, zeros included
+    uint8_t *flag;
 };
 
 // Mask of the 8 x 4 pixel block at tile column c0 and row r0 (bit 8 r + c = pixel
@@ -455,7 +458,13 @@ __device__ __forceinline__ void blend_bwd_tile(int tx, int ty, uint2 range,
             for (int idx = threadIdx.x; idx < (gtop - gbot) * 9; idx += kBwdThreads) {
                 const int q = idx / 9, c = idx - q * 9;
                 const float acc = ((sm.wpart[q][0][c] + sm.wpart[q][1][c]) + sm.wpart[q][2][c]) + sm.wpart[q][3][c];
-                part[(int64_t)sm.e[gbot + q - lo] * 9 + c] = acc;
+                const uint32_t e = sm.e[gbot + q - lo];
+                if (!o.flag) {
+                    part[(int64_t)e * 9 + c] = acc;
+                } else if (acc != 0.f) {  // the buffer holds zeros: a zero partial needs no store
+                    part[(int64_t)e * 9 + c] = acc;
+                    o.flag[e] = 1;
+                }
             }
             __syncthreads();
         }
