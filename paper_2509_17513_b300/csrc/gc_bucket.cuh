@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(kBucketWarps * 32) k_bucket_place(const float4
     __shared__ uint32_t m[kBucketWarps][kWin][33];   // counts, then start positions
     __shared__ uint8_t col[kBucketWarps][kWin][36];  // first column of each lane's interval
     __shared__ uint32_t rtot[kBucketWarps][kWin];    // entries of the chunk in each row
+    __shared__ uint32_t bw[kBucketWarps][32];         // per owner of a row: its base word
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * kBucketWarps + warp;
     if (c >= n_chunks) return;   // whole warp
@@ -289,22 +290,39 @@ __global__ void __launch_bounds__(kBucketWarps * 32) k_bucket_place(const float4
         }
         __syncwarp();
         const int jmax = min(kWin, ci.n_rows - w0);
+        const uint32_t lane_le = 0xffffffffu >> (31 - lane);  // bits 0..lane
         // not unrolled: a row holds one warp step of the chunk's entries or none, mostly
 #pragma unroll 1
         for (int j = 0; j < jmax; ++j) {
             const uint32_t tot = rtot[warp][j];
             if (tot == 0u) continue;  // warp-uniform
-            const uint32_t p0 = mw[j][0];
+            // lane l's entries of the row are [rel, end) of the row's run, in lane order
+            const uint32_t p0 = mw[j][0], s = mw[j][lane];
+            const uint32_t rel = s - p0, end = lane < 31 ? mw[j][lane + 1] - p0 : tot;
+            const bool own = end > rel;
+            const uint32_t owners = __ballot_sync(0xffffffffu, own);
+            // owner k (k-th lane with entries): word of its element e = base + (e << 24), base =
+            // ((first column - rel) << 24) + rank; the column stays in 0..254, so the sum mod 2^32
+            // is the word
+            if (own)
+                bw[warp][__popc(owners & (lane_le >> 1))] =
+                    (((uint32_t)cw[j][lane] - rel) << kListRankBits) + v0 + (uint32_t)lane;
+            __syncwarp();
 #pragma unroll 1
-            for (uint32_t e = lane; e < tot; e += 32) {
-                const uint32_t pe = p0 + e;
-                int o = 0;  // last lane whose start is <= pe
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (mw[j][o + step] <= pe) o += step;
-                const uint32_t x = (uint32_t)cw[j][o] + (pe - mw[j][o]);
-                if (pe < alloc) keys[pe] = (x << kListRankBits) | (v0 + (uint32_t)o);
+            for (uint32_t e0 = 0; e0 < tot; e0 += 32) {
+                // the owners' run starts in this window of 32 elements (bit rel - e0), and the
+                // number of owners starting before it: element e's owner is the last start <= e
+                const uint32_t starts =
+                    __reduce_or_sync(0xffffffffu, (own && rel - e0 < 32u) ? 1u << (rel - e0) : 0u);
+                const uint32_t before = __popc(__ballot_sync(0xffffffffu, own && rel < e0));
+                const uint32_t e = e0 + lane;
+                if (e < tot) {
+                    const uint32_t pe = p0 + e;
+                    const int k = (int)(before + __popc(starts & lane_le)) - 1;
+                    if (pe < alloc) keys[pe] = bw[warp][k] + (e << kListRankBits);
+                }
             }
+            __syncwarp();
         }
         __syncwarp();
     }
