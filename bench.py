@@ -652,11 +652,11 @@ def summary_line(args, world, w, tile, cap_levels, hl, d):
         c = d["c5_prec4k"]
         line["C5"] = {"fp32": [c["fp32"]["fwd"], c["fp32"]["fwd_bwd"]],
                       "bf16_fp8": [c["bf16_fp8"]["fwd"], c["bf16_fp8"]["fwd_bwd"]],
-                      "psnr_bf16_vs_fp32_db": c["psnr_bf16_fp8_vs_fp32_db"],
+                      "psnr_bf16_vs_fp32_db": c["psnr_bf16_fp8_vs_fp32_db"], "tile": c.get("tile"),
                       "stages_fb": compact_stages(c["stages"]["flushed"], c["stages"]["warm"])}
     if "c3_diff" in d:
         c = d["c3_diff"]
-        line["C3"] = {k: c[k] for k in ("value", "fps", "ms_per_step")}
+        line["C3"] = {k: c.get(k) for k in ("value", "fps", "ms_per_step", "tile")}
         line["C3"]["blend_bwd_frac"] = c["stages"]["blend_bwd"]["frac"]
     line["stages_fb"] = {"note": "per frame [ms,frac] L2 flushed, then warm; HBM or FP32 (20/50 FLOP/pair)",
                          **compact_stages(hl["stages_per_frame"]["flushed"], hl["stages_per_frame"]["warm"])}
@@ -1051,6 +1051,30 @@ def run_c1(args, r, timer, world):
             "mpix_s_graph": round(n * px / (g_ms / 1e3) / 1e6, 1)}
 
 
+def pick_tile(r, make_step, tiles=((16, 16), (8, 32), (32, 8)), reps=3):
+    """Tile shape of a single-view form, chosen as the batched path's autotuner chooses its
+    own: per shape, make_step() builds a step (with its own saved state), which runs twice to
+    size its buffers and then `reps` times timed on the host around device synchronisations;
+    the fastest shape is kept (key capacity back to grow-as-needed).
+    Returns (tile, {"16x16": ms, ...})."""
+    import torch
+    ms = {}
+    for tile in tiles:
+        r.set_options(key_capacity=0, tile=tile)
+        step = make_step()
+        step()
+        step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            step()
+        torch.cuda.synchronize()
+        ms[tile] = (time.perf_counter() - t0) * 1e3 / reps
+    best = min(ms, key=ms.get)
+    r.set_options(key_capacity=0, tile=best)
+    return best, {f"{t[0]}x{t[1]}": round(v, 3) for t, v in ms.items()}
+
+
 def run_c3(args, r, timer, world, peaks):
     """The differentiation step (200k Gaussians, SH 3, 32 groups, 1352x1014, FP32): forward
     of frame 1 at level L6, L1 loss against the target (the scene with perturbed means,
@@ -1074,6 +1098,17 @@ def run_c3(args, r, timer, world, peaks):
     img = torch.empty_like(target)
     dl = torch.empty_like(target)
     loss = torch.empty(1, device=dev)
+
+    def tune_step():
+        s, g = gc.Saved(rd), [None]
+
+        def step():
+            rd.forward(gs, mo, 63, cam, s, out=img)
+            rd.l1_loss(img, target, grad=dl, loss=loss)
+            g[0] = rd.backward(s, gs, mo, dl, g[0])
+        return step
+
+    tile, tile_ms = pick_tile(rd, tune_step)
     rd.forward(gs, mo, 63, cam, out=img)
     st = rd.stats()
     rd.set_options(key_capacity=int(st["n_keys"] * 1.05) + 4096)
@@ -1105,8 +1140,8 @@ def run_c3(args, r, timer, world, peaks):
                         "against the perturbed-means target, backward",
             "value": round(whole_job_rate(px, args.steps, world, ms) / 1e6, 1), "unit": UNIT,
             "fps": round(args.steps * world / (ms / 1e3), 1), "ms_per_step": round(ms / args.steps, 4),
-            "loss": round(lv, 6), "keys": st["n_keys"], "clocks": clk,
-            "stages": stage_table(prof, wk, peaks)}
+            "loss": round(lv, 6), "keys": st["n_keys"], "clocks": clk, "tile": f"{tile[0]}x{tile[1]}",
+            "tile_sweep_ms": tile_ms, "stages": stage_table(prof, wk, peaks)}
 
 
 def run_c5(args, r, timer, world, peaks):
@@ -1129,6 +1164,17 @@ def run_c5(args, r, timer, world, peaks):
     mo = gc.MotionFrame.from_motion(w5.motion, 1, dev)
     gen = torch.Generator(device=dev).manual_seed(13)
     up = torch.randn((3, cam.height, cam.width), generator=gen, device=dev) * 1e-3
+
+    def tune_step():
+        s, g = gc.Saved(r5), [None]
+        o = torch.empty((3, cam.height, cam.width), device=dev)
+
+        def step():
+            r5.forward(sets["fp32"], mo, 63, cam, s, out=o)
+            g[0] = r5.backward(s, sets["fp32"], mo, up, g[0])
+        return step
+
+    tile5, tile_ms = pick_tile(r5, tune_step)
     res, imgs, wk = {}, {}, None
     steps = max(2, min(args.steps, 10))
     for name, gset in sets.items():
@@ -1177,10 +1223,13 @@ def run_c5(args, r, timer, world, peaks):
     res["psnr_bf16_fp8_vs_fp32_db"] = psnr_db(imgs["bf16_fp8"], imgs["fp32"])
     res["max_abs_bf16_fp8_vs_fp32"] = round(float((imgs["bf16_fp8"] - imgs["fp32"]).abs().max()), 5)
     res["workload"] = ("prec4k: 1M Gaussians, 6 layers, SH 3, 256 groups, 3840x2160, frame 1, level L6, "
-                       "single view, 16x16 tiles")
+                       f"single view, {tile5[0]}x{tile5[1]} tiles (the fastest of three in tile_sweep_ms)")
+    res["tile"] = f"{tile5[0]}x{tile5[1]}"
+    res["tile_sweep_ms"] = tile_ms
     res["unit"] = UNIT
     res["work"] = wk
-    state = {"w": w5, "q": q, "cam": cam, "img_fp32": imgs["fp32"].cpu(), "img_bf16_fp8": imgs["bf16_fp8"].cpu()}
+    state = {"w": w5, "q": q, "cam": cam, "img_fp32": imgs["fp32"].cpu(), "img_bf16_fp8": imgs["bf16_fp8"].cpu(),
+             "tile": tile5}
     r5.close()
     del sets
     return res, state
@@ -1374,7 +1423,7 @@ def cpu_baseline(w=None, gpu_frame0=None, c5=None, n_pix=131072) -> dict:
     if c5 is not None:
         w5, cam5 = c5["w"], c5["cam"]
         pix = scenes.sample_pixels(2024, cam5.width, cam5.height, 2048)
-        o5 = oracle.default_options()
+        o5 = oracle.default_options(tile=c5["tile"])
         deq = oracle.dequantize(c5["q"], w5.scene)
         for key, scene, img in (("c5_fp32", w5.scene, c5["img_fp32"]),
                                 ("c5_bf16_fp8_vs_dequantised", deq, c5["img_bf16_fp8"]),
