@@ -186,6 +186,14 @@ __global__ void __launch_bounds__(kFT) k_field_encode(Field F, const float *__re
 // db2).  Each block writes one partial vector at the end, summed over the blocks in block
 // order by k_field_reduce, so the weight gradients are reproducible bit for bit for a given n.
 // The table gradient is scattered with atomic additions.
+// 16-byte global -> shared copy that completes asynchronously (src_bytes 0: zero fill).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, uint32_t src_bytes) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 constexpr int kHP = kIn + 4;       // 36 floats: row pitch of the encodings
 constexpr int kOP = 8;             // row pitch of the output gradients (7 used)
 constexpr int kAP = kHidden + 4;   // 68 floats: row pitch of the hidden rows
@@ -214,33 +222,42 @@ __global__ void __launch_bounds__(kFT, kBwdBlocksPerSm) k_field_bwd(
         g2[net][0] = g2[net][1] = gb1[net] = 0.f;
     }
     const int64_t nchunks = (n + kFT - 1) / kFT;
+    // A chunk's inputs: its encodings into the padded shared rows by asynchronous copies (zero
+    // rows past n), its means and output gradients into registers.  The next chunk's are
+    // fetched before this chunk's table atomics are issued, so they do not queue behind them.
+    auto fetch = [&](int64_t ch, float *mu_n, float *dout_n) {
+        const int64_t row0 = ch * kFT;
+#pragma unroll
+        for (int e = tid; e < kFT * (kIn / 4); e += kFT) {
+            const int r = e / (kIn / 4), q4 = e % (kIn / 4);
+            const bool in = row0 + r < n;
+            cp_async16(HT + r * kHP + 4 * q4, hrows + (in ? (size_t)(row0 + r) * (kIn / 4) + q4 : 0), in ? 16u : 0u);
+        }
+        cp_async_commit();
+        const int64_t i = ch * kFT + tid;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) mu_n[a] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) dout_n[c] = 0.f;
+        if (i < n) {
+            for (int a = 0; a < 3; ++a) mu_n[a] = means[3 * i + a];
+            for (int c = 0; c < 3; ++c) dout_n[c] = d_t[3 * i + c];
+            for (int c = 0; c < 4; ++c) dout_n[3 + c] = d_q[4 * i + c];
+        }
+    };
+    float mu[3], dout[8];
+    if ((int64_t)blockIdx.x < nchunks) fetch(blockIdx.x, mu, dout);
     for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
         const int64_t i = chunk * kFT + tid;
         const bool valid = i < n;
-        float mu[3] = {0.f, 0.f, 0.f};
-        float h[kIn], dout[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) dout[c] = 0.f;
-        if (valid) {
-            for (int a = 0; a < 3; ++a) mu[a] = means[3 * i + a];
-            for (int c = 0; c < 3; ++c) dout[c] = d_t[3 * i + c];
-            for (int c = 0; c < 4; ++c) dout[3 + c] = d_q[4 * i + c];
-        }
-        __syncthreads();  // the previous chunk's readers of the rows are done
+        float h[kIn];
+        cp_async_wait_all();
         {
-            // the chunk's encodings: contiguous in global memory, one padded shared row each
-            const int64_t row0 = chunk * kFT;
-#pragma unroll
-            for (int e = tid; e < kFT * (kIn / 4); e += kFT) {
-                const int r = e / (kIn / 4), q4 = e % (kIn / 4);
-                const float4 v = row0 + r < n ? hrows[(size_t)(row0 + r) * (kIn / 4) + q4] : make_float4(0.f, 0.f, 0.f, 0.f);
-                *reinterpret_cast<float4 *>(HT + r * kHP + 4 * q4) = v;
-            }
             float4 *orow = reinterpret_cast<float4 *>(DOT + tid * kOP);
             orow[0] = make_float4(dout[0], dout[1], dout[2], dout[3]);
             orow[1] = make_float4(dout[4], dout[5], dout[6], 0.f);
         }
-        __syncthreads();
+        __syncthreads();  // the chunk's encodings and output gradients are in shared memory
         {
             const float4 *hr = reinterpret_cast<const float4 *>(HT + tid * kHP);
 #pragma unroll
@@ -313,10 +330,13 @@ __global__ void __launch_bounds__(kFT, kBwdBlocksPerSm) k_field_bwd(
             if (net == 0 && tid < 7)
                 for (int r = 0; r < kFT; ++r) gb2 += DOT[r * kOP + tid];
         }
+        __syncthreads();  // every reader of this chunk's shared rows is done
+        const float mu_c[3] = {mu[0], mu[1], mu[2]};
+        if (chunk + (int64_t)gridDim.x < nchunks) fetch(chunk + gridDim.x, mu, dout);
         // table gradient: each corner's weight times the feature gradient
         if (valid && d_table) {
             float x[3];
-            unit_pos(F, mu, x);
+            unit_pos(F, mu_c, x);
             const uint32_t T = 1u << F.log2T;
 #pragma unroll
             for (int l = 0; l < kMaxLv; ++l) {
