@@ -154,3 +154,41 @@ def test_diff_workload_at_scale(gc):
     _, g = _run(gc, w.scene, w.motion, 1, cam, mask, up)
     og = oracle.grad(w.scene, w.motion, 1, cam, opts, up, mask, bins=bins)
     _compare(g, og, NAMES + ("group_q", "group_t"), "diff at scale")
+
+
+@pytest.mark.parametrize("levels", [0, 6])
+def test_second_backward_on_one_state_equals_a_fresh_one(gc, levels):
+    """The partials buffer and the per-entry flags must be all zero again after a backward:
+    a second backward on the same saved state, with another upstream gradient, gives the
+    same bits as that backward on a fresh state (single-level and six-level passes)."""
+    rng = np.random.default_rng(71)
+    scene = scenes.make_hier_scene(rng, 4000, 6, 2, 4)
+    cam = scenes.orbit_camera(0.7, 4.0, 144, 112)
+    r = gc.Renderer(0, tile=(8, 32))
+    gs = gc.GaussianSet.from_scene(scene)
+    gen = torch.Generator(device="cuda").manual_seed(9)
+    n_img = levels if levels else 1
+    ups = [[torch.randn((3, cam.height, cam.width), generator=gen, device="cuda") for _ in range(n_img)]
+           for _ in range(2)]
+
+    def fwd(saved):
+        if levels:
+            r.levels_forward(gs, None, levels, cam, saved)
+        else:
+            r.forward(gs, None, scenes.level_mask(6), cam, saved)
+
+    def bwd(saved, up):
+        g = r.levels_backward(saved, gs, None, up) if levels else r.backward(saved, gs, None, up[0])
+        torch.cuda.synchronize()
+        return {k: v.clone() for k, v in g.items()}
+
+    s1 = gc.Saved(r)
+    fwd(s1)
+    first = bwd(s1, ups[0])
+    second = bwd(s1, ups[1])
+    s2 = gc.Saved(r)
+    fwd(s2)
+    fresh = bwd(s2, ups[1])
+    for k in NAMES:
+        assert torch.equal(second[k], fresh[k]), k
+        assert not torch.equal(first[k], second[k]), k
