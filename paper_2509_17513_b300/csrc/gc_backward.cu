@@ -9,7 +9,8 @@
 //                     Gaussian's partials are contiguous.  Entries behind the last
 //                     blended one of every pixel are not written; the tile records the
 //                     largest rank that may have contributed.
-//  k_reduce_entries   one warp per Gaussian sums its entries' partials.
+//  k_reduce_entries   one warp per Gaussian sums its entries' partials (the flagged ones:
+//                     only entries with a nonzero partial are stored and flagged).
 //  k_preprocess_bwd   chain rule from (u, v, conic, opacity, rgb) to mean, log-scale,
 //                     quaternion, opacity logit, SH and the group motion (Sec. 3.2).
 //  k_group_partial /  per-group sums of the motion terms: each thread owns a group and

@@ -588,7 +588,10 @@ __device__ __forceinline__ uint32_t entry_index(const RowGeom &g, const float4 &
 // One warp sums the partials of one Gaussian's entries (positions base .. base + cnt - 1,
 // nine floats each, contiguous) and sets every nonzero one back to zero, so that the
 // partials buffer is all zeros again for the next reverse pass (entries the reverse
-// blend does not reach are never written and must read as zero).  Entries past `cap`
+// blend does not reach are never written and must read as zero).  With the reverse pass's
+// flags (one byte per entry, 1 where it stored a nonzero partial), only flagged entries are
+// read, and their partials and flags are cleared; without (NULL), every entry is read.
+// Entries past `cap`
 // (an overflowed fixed capacity) are skipped.  Lanes stride over the entries; the warp
 // sum is a transposing butterfly: afterwards lane 4 c holds value c (c < 8) and every
 // lane holds value 8.
