@@ -50,13 +50,13 @@ WORKLOAD = ("hier1080: 300k Gaussians in 6 layers of 50k, SH degree 3, 64 motion
 FP32_LANES_PER_SM = 128
 N_SMS = 148
 
-# ---- algorithmic work per unit (the same table is in the design notes, section 7) ----
+# ---- algorithmic work per unit ----
 # Blends (FP32 ALU).  Two FLOP units, both reported:
 #  * per evaluated (pixel, entry) pair, 20 FLOPs forward, 50 reverse (2.5 x forward);
 #  * the finer split: 14 FLOPs to evaluate a walked pair up to the 1/255 test, plus 10 per
 #    blended (pair, level) forward or 51 reverse (FMA = 2 FLOPs).
-SURVEY_FWD_FLOPS_PER_PAIR = 20
-SURVEY_BWD_FLOPS_PER_PAIR = 50
+REF_FWD_FLOPS_PER_PAIR = 20
+REF_BWD_FLOPS_PER_PAIR = 50
 EVAL_FLOPS_PER_PAIR = 14
 FWD_BLEND_FLOPS_PER_PAIR = 10
 BWD_BLEND_FLOPS_PER_PAIR = 51
@@ -97,10 +97,10 @@ def stage_work(stage: str, w: dict):
     if stage == "group_reduce":
         return n * 32, "bytes", None
     if stage == "blend":
-        return (SURVEY_FWD_FLOPS_PER_PAIR * w["walked"], "flops",
+        return (REF_FWD_FLOPS_PER_PAIR * w["walked"], "flops",
                 EVAL_FLOPS_PER_PAIR * w["walked"] + FWD_BLEND_FLOPS_PER_PAIR * w["blended"])
     if stage == "blend_bwd":
-        return (SURVEY_BWD_FLOPS_PER_PAIR * w["bwd_walked"], "flops",
+        return (REF_BWD_FLOPS_PER_PAIR * w["bwd_walked"], "flops",
                 EVAL_FLOPS_PER_PAIR * w["bwd_walked"] + BWD_BLEND_FLOPS_PER_PAIR * w["blended"])
     return 0, "bytes", None
 
@@ -386,7 +386,7 @@ def blend_roofline(stage, per_launch_ms, work, peaks, sgemm, units_per_launch, t
     return {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32, 2), "unit": "TFLOP/s",
             "frac": round(ach / fp32, 4), "traffic": load_traffic(kern, units_per_launch, tile),
             "kernel": kern, "launch_ms": round(per_launch_ms, 4),
-            "flop_unit": f"{SURVEY_FWD_FLOPS_PER_PAIR if stage == 'blend' else SURVEY_BWD_FLOPS_PER_PAIR}"
+            "flop_unit": f"{REF_FWD_FLOPS_PER_PAIR if stage == 'blend' else REF_BWD_FLOPS_PER_PAIR}"
                          " per evaluated pair",
             "frac_split": round(impl / (per_launch_ms / 1e3) / 1e12 / fp32, 4),
             "split_unit": f"14 per walked pair + {FWD_BLEND_FLOPS_PER_PAIR if stage == 'blend' else BWD_BLEND_FLOPS_PER_PAIR}"
