@@ -1,7 +1,7 @@
 """Host logic of the benchmark that decides which committed ncu figures a bench line may use:
 a kernel's source hash follows the file that defines it and the kernel sources it includes
 (and nothing else), and a DRAM-traffic figure is used only while that hash matches and for the
-tile shape it was captured with."""
+tile shape it was captured with; the single-view forms keep the fastest of their tile shapes."""
 import json
 import os
 import sys
@@ -71,3 +71,34 @@ def test_committed_traffic_entries_are_well_formed():
         assert e["unit"], k
     for k in ("k_blend_levels_fwd", "k_blend_levels_bwd"):
         assert d["kernels"][k]["tile"] == "%dx%d" % bench.HEADLINE_TILE
+
+
+def test_pick_tile_keeps_the_fastest_shape(monkeypatch):
+    """The single-view forms' tile sweep: each shape gets its own step (built after the shape is
+    set), and the fastest shape is the one left set, with grow-as-needed key capacity."""
+    import time
+
+    import torch
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+
+    class FakeRenderer:
+        def __init__(self):
+            self.opts = {}
+
+        def set_options(self, **kw):
+            self.opts.update(kw)
+
+    r = FakeRenderer()
+    cost = {(16, 16): 0.004, (8, 32): 0.001, (32, 8): 0.003}
+    built = []
+
+    def make_step():
+        tile = r.opts["tile"]
+        built.append(tile)
+        return lambda: time.sleep(cost[tile])
+
+    best, ms = bench.pick_tile(r, make_step, reps=2)
+    assert best == (8, 32)
+    assert built == [(16, 16), (8, 32), (32, 8)]
+    assert r.opts == {"key_capacity": 0, "tile": (8, 32)}
+    assert set(ms) == {"16x16", "8x32", "32x8"} and ms["8x32"] < ms["32x8"] < ms["16x16"]
